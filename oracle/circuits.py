@@ -1,0 +1,218 @@
+"""Comparison circuits over the oracle's BGV operations.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+BoostCom Sec. 2.1 ("Non-arithmetic Comparison of uFHE-based BGV"): operands
+are split into digits; LT and EQ are computed for every digit independently
+("the computation of LT and EQ for each digit is independent"), and the digit
+results are combined in lexicographic order into an encryption of 1 when
+a < b and 0 otherwise.  The univariate circuit is used (Table 3 lists both;
+its digit bases (p+1)/2 are what make 64-bit operands out of the listed
+(d, l) pairs).  The paper gives no evaluation schedule; the readings fixed here
+(and mirrored exactly by the CUDA path, since bit-exact agreement depends on
+them) are:
+
+  * levels: every ciphertext product is tensor -> relinearise -> modulus
+    switch by one prime when the level is > 1; an operand at a higher level is
+    first switched down, one prime at a time, to the other operand's level
+    (lowered copies are cached); additions align the same way;
+  * scalar constants c in Z_p are lifted to the centred representative in
+    (-p/2, p/2];
+  * powers z^n: n = 1 is z; n a power of two squares z^(n/2); otherwise
+    z^(2^a) * z^(n-2^a) with 2^a the largest power of two below n;
+  * Paterson-Stockmeyer for f(z) = c_{p-1} z^(p-1) + O(z), O odd: baby odd
+    powers z^1 .. z^(B-1), B = 2^b, b = ceil(log2(p-1) / 2); block k of O is
+    the leaf L_k(z) = sum_{odd r < B} c_{Bk+r} z^r (terms with c = 0
+    skipped); blocks are combined by  E(k0,t) = E(k0,t-1) + z^(B 2^(t-1)) *
+    E(k0 + 2^(t-1), t-1), an empty half dropping its product or sum;
+  * per digit: z = x_k - y_k; LT_k = f(z); EQ_k = 1 - z^(p-1);
+  * merge: digits (least significant first) are paired (2i+1, 2i) ->
+    (L_hi + E_hi L_lo, E_hi E_lo), an odd last node passes up unchanged, and
+    the root computes the E product only when EQ is wanted;
+  * max/min: L = LT(x, y); t_k = L (y_k - x_k); max_k = x_k + t_k,
+    min_k = y_k - t_k (equal operands give the common value).
+
+Every operation appends (name, level) to ``trace``; the CUDA path emits the
+same trace, and a test compares them.  The multiplication count is pinned
+against the Paterson-Stockmeyer count (8 / 23 / 30 for p = 17 / 131 / 257) and
+the depth against ceil(log2(p-1)).
+"""
+from __future__ import annotations
+
+from .bgv import Ct, Oracle
+from .ltpoly import lt_coefficients
+
+
+def centred(c: int, p: int) -> int:
+    c %= p
+    return c - p if c > p // 2 else c
+
+
+def baby_log(p: int) -> int:
+    """b = ceil(log2(p-1) / 2)."""
+    lg = (p - 2).bit_length()  # ceil(log2(p-1)) for p >= 3
+    return (lg + 1) // 2
+
+
+class Evaluator:
+    def __init__(self, orc: Oracle, rlk, galois_keys=None):
+        self.o = orc
+        self.p = orc.p
+        self.rlk = rlk
+        self.gk = dict(galois_keys or {})
+        self.trace = []
+        self._lowered = {}
+
+    # ---- level alignment -----------------------------------------------------
+    def lower(self, ct: Ct, level: int) -> Ct:
+        if ct.level == level:
+            return ct
+        assert ct.level > level >= 1
+        key = (id(ct), level)
+        hit = self._lowered.get(key)
+        if hit is not None:
+            return hit[1]
+        above = self.lower(ct, level + 1)
+        out = self.o.modswitch(above)
+        self._lowered[key] = (ct, out)  # keep ct alive so id() stays unique
+        return out
+
+    def _align(self, a: Ct, b: Ct):
+        lv = min(a.level, b.level)
+        return self.lower(a, lv), self.lower(b, lv), lv
+
+    # ---- traced operations ---------------------------------------------------
+    def mul(self, a: Ct, b: Ct) -> Ct:
+        a2, b2, lv = self._align(a, b)
+        c = self.o.relin(self.o.tensor(a2, b2), self.rlk)
+        if lv > 1:
+            c = self.o.modswitch(c)
+        self.trace.append(("mul", lv))
+        return c
+
+    def add(self, a: Ct, b: Ct) -> Ct:
+        a2, b2, lv = self._align(a, b)
+        self.trace.append(("add", lv))
+        return self.o.add(a2, b2)
+
+    def sub(self, a: Ct, b: Ct) -> Ct:
+        a2, b2, lv = self._align(a, b)
+        self.trace.append(("sub", lv))
+        return self.o.sub(a2, b2)
+
+    def mul_const(self, a: Ct, c: int) -> Ct:
+        self.trace.append(("cmul", a.level))
+        return self.o.mul_const(a, centred(c, self.p))
+
+    def add_const(self, a: Ct, c: int) -> Ct:
+        self.trace.append(("cadd", a.level))
+        return self.o.add_const(a, centred(c, self.p))
+
+    def neg(self, a: Ct) -> Ct:
+        self.trace.append(("neg", a.level))
+        return self.o.neg(a)
+
+    def rotate(self, a: Ct, g: int) -> Ct:
+        self.trace.append(("rot", a.level))
+        return self.o.rotate(a, g, self.gk[g])
+
+    def mul_count(self) -> int:
+        return sum(1 for t in self.trace if t[0] == "mul")
+
+    # ---- per-digit circuit ---------------------------------------------------
+    def digit(self, x: Ct, y: Ct, want_lt: bool, want_eq: bool):
+        """(LT_k, EQ_k) for one digit pair (either may be None if unwanted)."""
+        p = self.p
+        z = self.sub(x, y)
+        pw = {1: z}
+
+        def power(n: int) -> Ct:
+            if n in pw:
+                return pw[n]
+            if n & (n - 1) == 0:
+                h = power(n // 2)
+                r = self.mul(h, h)
+            else:
+                a = 1 << (n.bit_length() - 1)
+                r = self.mul(power(a), power(n - a))
+            pw[n] = r
+            return r
+
+        lt = None
+        if want_lt:
+            c = lt_coefficients(p)
+            B = 1 << baby_log(p)
+            nblocks = (p - 2) // B + 1  # odd exponents go up to p-2
+
+            def leaf(k: int):
+                terms = [(r, c[B * k + r]) for r in range(1, B, 2) if B * k + r <= p - 2 and c[B * k + r]]
+                if not terms:
+                    return None
+                cts = [power(r) for r, _ in terms]
+                lv = min(t.level for t in cts)
+                acc = None
+                for (r, cr), t in zip(terms, cts):
+                    term = self.mul_const(self.lower(t, lv), cr)
+                    acc = term if acc is None else self.add(acc, term)
+                return acc
+
+            def tree(k0: int, t: int):
+                if k0 >= nblocks:
+                    return None
+                if t == 0:
+                    return leaf(k0)
+                half = 1 << (t - 1)
+                lo = tree(k0, t - 1)
+                hi = tree(k0 + half, t - 1)
+                if hi is None:
+                    return lo
+                prod = self.mul(power(B * half), hi)
+                return prod if lo is None else self.add(lo, prod)
+
+            t = 0
+            while (1 << t) < nblocks:
+                t += 1
+            odd = tree(0, t)
+            zp = power(p - 1)
+            lead = self.mul_const(zp, c[p - 1])
+            lt = lead if odd is None else self.add(lead, odd)
+        eq = None
+        if want_eq:
+            eq = self.add_const(self.neg(power(p - 1)), 1)
+        return lt, eq
+
+    # ---- merge of digits -----------------------------------------------------
+    def compare(self, xs, ys, want_lt=True, want_eq=False):
+        """LT(x, y) and/or EQ(x, y) for digit lists (least significant first)."""
+        nodes = []
+        for x, y in zip(xs, ys):
+            nodes.append(self.digit(x, y, want_lt, True if len(xs) > 1 or want_eq else False))
+        while len(nodes) > 1:
+            root = len(nodes) == 2
+            nxt = []
+            for i in range(len(nodes) // 2):
+                (llo, elo), (lhi, ehi) = nodes[2 * i], nodes[2 * i + 1]
+                L = self.add(lhi, self.mul(ehi, llo)) if want_lt else None
+                E = self.mul(ehi, elo) if (want_eq or not root) else None
+                nxt.append((L, E))
+            if len(nodes) % 2:
+                nxt.append(nodes[-1])
+            nodes = nxt
+        L, E = nodes[0]
+        return (L if want_lt else None), (E if want_eq else None)
+
+    def compare_lt(self, xs, ys) -> Ct:
+        return self.compare(xs, ys, True, False)[0]
+
+    def compare_eq(self, xs, ys) -> Ct:
+        return self.compare(xs, ys, False, True)[1]
+
+    def max_min(self, xs, ys):
+        """(max digits, min digits) of the two operands."""
+        L = self.compare_lt(xs, ys)
+        mx, mn = [], []
+        for x, y in zip(xs, ys):
+            t = self.mul(L, self.sub(y, x))
+            mx.append(self.add(x, t))
+            mn.append(self.sub(y, t))
+        return mx, mn

@@ -1,0 +1,36 @@
+"""Builds oracle contexts, keys and ciphertexts from the shared seeded inputs."""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle.bgv import Oracle
+from oracle.circuits import Evaluator
+from oracle.encoding import SlotStructure
+from paper_2407_07308_gb300 import synth
+
+
+class OracleSetup:
+    def __init__(self, logN, p, L, K, U, lo, hi, seed=1, galois=(), d=1):
+        self.o = Oracle(logN, p, L, K, U, lo, hi)
+        self.N, self.p, self.L, self.K = self.o.N, p, L, K
+        self.ss = SlotStructure(p, self.N)
+        self.galois = list(galois)
+        self.km = synth.KeyMaterial(seed, self.o.primes, L, K, self.N, n_galois=len(self.galois))
+        self.s = self.km.s
+        self.pk = self.o.keygen(self.s, self.km.a_pk, self.km.e_pk)
+        self.rlk = self.o.relin_key(self.s, self.km.a_ksk[0], self.km.e_ksk[0])
+        self.gks = {g: self.o.galois_key(self.s, g, self.km.a_ksk[1 + i], self.km.e_ksk[1 + i])
+                    for i, g in enumerate(self.galois)}
+
+    def evaluator(self) -> Evaluator:
+        return Evaluator(self.o, self.rlk, self.gks)
+
+    def encrypt_slots(self, slot_rows, seed):
+        """Encrypt each row of slot values (len n_s) into one ciphertext."""
+        rows = np.asarray(slot_rows, dtype=np.int64).reshape(-1, self.ss.ns)
+        r = synth.EncRandomness(seed, rows.shape[0], self.N)
+        return [self.o.encrypt(self.pk, self.ss.encode(row), r.u[i], r.e0[i], r.e1[i])
+                for i, row in enumerate(rows)]
+
+    def decrypt_slots(self, ct):
+        return self.ss.decode(self.o.decrypt_coeffs(ct, self.s))

@@ -1,0 +1,260 @@
+"""Pins of the oracle's BGV operations.
+
+Checked against properties computed here with Python big integers (CRT), not
+against the oracle's own formulas: basis conversion gives X + u Q with small
+u; modulus switching and ModDown divide exactly and keep the plaintext; key
+switching gives x s' + p * (small); every operation decrypts to the plaintext
+result; the noise stays below q_0 / 2.
+"""
+import random
+
+import numpy as np
+import pytest
+
+from oracle.circuits import Evaluator
+from tests.oracle_setup import OracleSetup
+from tests.params import CHAIN36, CHAIN50
+
+
+def crt(residues, primes):
+    Q = 1
+    for q in primes:
+        Q *= q
+    x = 0
+    for r, q in zip(residues, primes):
+        Qi = Q // q
+        x += int(r) * Qi * pow(Qi % q, -1, q)
+    return x % Q, Q
+
+
+def centred(x, Q):
+    x %= Q
+    return x - Q if x > Q // 2 else x
+
+
+@pytest.fixture(scope="module")
+def small17():
+    return OracleSetup(logN=6, p=17, L=4, K=2, seed=11, galois=(5, 127), **CHAIN50)
+
+
+def test_fbc_is_crt_plus_small_multiple(small17):
+    o = small17.o
+    g = np.random.default_rng(1)
+    src, dst = [1, 2], [0, 3, 4, 5]
+    x = np.stack([g.integers(0, o.primes[i], size=o.N, dtype=np.uint64) for i in src])
+    y = o.fbc(x, src, dst)
+    qs = [o.primes[i] for i in src]
+    qd = [o.primes[i] for i in dst]
+    QS = qs[0] * qs[1]
+    us = set()
+    for n in range(o.N):
+        X, _ = crt([x[a][n] for a in range(2)], qs)
+        Y, T = crt([y[b][n] for b in range(4)], qd)
+        assert T > 2 * QS
+        assert (Y - X) % QS == 0
+        u = (Y - X) // QS
+        assert 0 <= u < 2
+        us.add(u)
+    assert us == {0, 1}  # both overflow counts occur on random inputs
+
+
+def test_encrypt_decrypt(small17):
+    st = small17
+    rnd = random.Random(2)
+    vals = [[rnd.randrange(17) for _ in range(st.ss.ns)] for _ in range(3)]
+    for v, ct in zip(vals, st.encrypt_slots(vals, seed=5)):
+        assert st.decrypt_slots(ct) == v
+        assert st.o.noise_bits(ct, st.s) < 30
+
+
+def test_modswitch_divides_exactly_and_keeps_plaintext(small17):
+    st, o = small17, small17.o
+    ct = st.encrypt_slots([[3] * st.ss.ns], seed=6)[0]
+    out = o.modswitch(ct)
+    ql = o.primes[ct.level - 1]
+    for k in range(2):
+        for n in range(0, o.N, 7):
+            X, Q = crt([ct.data[k, i, n] for i in range(ct.level)], o.primes[: ct.level])
+            Xp, _ = crt([out.data[k, i, n] for i in range(out.level)], o.primes[: out.level])
+            D = (X - Xp * ql) % Q  # the integer delta that was removed
+            assert D % st.p == 0 and D % ql == X % ql and 0 <= D < st.p * ql
+    assert st.decrypt_slots(out) == [3] * st.ss.ns
+    # decryption residues at the new level are those of the old level
+    # divided by q_l, up to the removed delta (same message mod p)
+    assert st.o.decrypt_coeffs(out, st.s).tolist() == st.o.decrypt_coeffs(ct, st.s).tolist()
+
+
+def test_keyswitch_gives_x_sprime_plus_p_small(small17):
+    st, o = small17, small17.o
+    g = np.random.default_rng(3)
+    for level in (4, 3, 1):
+        x = np.stack([g.integers(0, o.primes[i], size=o.N, dtype=np.uint64) for i in range(level)])
+        out = o.keyswitch(x, level, st.rlk)
+        s2 = o.polymul_int(st.s, st.s)
+        res = []
+        for i in range(level):
+            q = o.primes[i]
+            sq = np.array([v % q for v in st.s.tolist()], dtype=np.uint64)
+            s2q = np.array([v % q for v in s2.tolist()], dtype=np.uint64)
+            t = (o.polymul(i, out[1, i], sq).astype(object) + out[0, i].astype(object)
+                 - o.polymul(i, x[i], s2q).astype(object)) % q
+            res.append(t)
+        for n in range(o.N):
+            E, Q = crt([res[i][n] for i in range(level)], o.primes[:level])
+            e = centred(E, Q)
+            assert e % st.p == 0
+            assert abs(e) < 2 ** 40
+
+
+def test_tensor_relin_mul_decrypt(small17):
+    st = small17
+    ev = st.evaluator()
+    rnd = random.Random(4)
+    a = [rnd.randrange(17) for _ in range(st.ss.ns)]
+    b = [rnd.randrange(17) for _ in range(st.ss.ns)]
+    ca, cb = st.encrypt_slots([a, b], seed=7)
+    c = ev.mul(ca, cb)
+    assert c.level == 3
+    assert st.decrypt_slots(c) == [(x * y) % 17 for x, y in zip(a, b)]
+    assert st.decrypt_slots(ev.add(c, ca)) == [(x * y + x) % 17 for x, y in zip(a, b)]
+    assert st.decrypt_slots(ev.sub(ca, cb)) == [(x - y) % 17 for x, y in zip(a, b)]
+    assert st.decrypt_slots(ev.mul_const(ca, 16)) == [(16 * x) % 17 for x in a]
+    assert st.decrypt_slots(ev.add_const(ca, 5)) == [(x + 5) % 17 for x in a]
+    assert st.decrypt_slots(ev.neg(cb)) == [(-x) % 17 for x in b]
+
+
+def test_rotation_decrypts_to_rotated_slots(small17):
+    st = small17
+    ev = st.evaluator()
+    v = list(range(1, st.ss.ns + 1))
+    ct = st.encrypt_slots([v], seed=8)[0]
+    cols = st.ss.M // 2
+    r5 = st.decrypt_slots(ev.rotate(ct, 5))
+    assert r5 == [v[r * cols + (c + 1) % cols] for r in range(2) for c in range(cols)]
+    rs = st.decrypt_slots(ev.rotate(ct, 2 * st.N - 1))
+    assert rs == v[cols:] + v[:cols]
+
+
+class _Lv:
+    def __init__(self, level, npoly=2):
+        self.level, self.npoly = level, npoly
+
+
+class LevelOnly:
+    """Stand-in backend that tracks levels only (for schedule counting)."""
+
+    def __init__(self, p, L):
+        self.p, self.L = p, L
+
+    def modswitch(self, a):
+        assert a.level > 1
+        return _Lv(a.level - 1, a.npoly)
+
+    def tensor(self, a, b):
+        assert a.level == b.level
+        return _Lv(a.level, 3)
+
+    def relin(self, d, rlk):
+        return _Lv(d.level, 2)
+
+    def add(self, a, b):
+        assert a.level == b.level
+        return _Lv(a.level)
+
+    sub = add
+
+    def neg(self, a):
+        return _Lv(a.level)
+
+    def mul_const(self, a, c):
+        return _Lv(a.level)
+
+    def add_const(self, a, c):
+        return _Lv(a.level)
+
+
+@pytest.mark.parametrize("p,mults,depth", [(17, 8, 4), (131, 23, 8), (257, 30, 8)])
+def test_ps_schedule_counts(p, mults, depth):
+    L = 30
+    ev = Evaluator(LevelOnly(p, L), None)
+    lt, eq = ev.digit(_Lv(L), _Lv(L), True, True)
+    assert ev.mul_count() == mults
+    assert L - lt.level == depth and L - eq.level == depth
+    # order of the univariate cost sqrt(p-3) + O(log p) (Sec. 1): well below
+    # the bivariate 2p - 6 for the larger p
+    assert mults < 2 * p - 6 or p < 20
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_merge_counts(d):
+    # d-1 pair nodes; each computes L_hi + E_hi L_lo and, except at the root
+    # when EQ is not wanted, E_hi E_lo
+    p, L = 17, 40
+    ev = Evaluator(LevelOnly(p, L), None)
+    xs = [_Lv(L) for _ in range(d)]
+    ev.compare(xs, xs, True, False)
+    assert ev.mul_count() == 8 * d + max(0, 2 * (d - 1) - 1)
+    ev2 = Evaluator(LevelOnly(p, L), None)
+    ev2.compare(xs, xs, True, True)
+    assert ev2.mul_count() == 8 * d + 2 * (d - 1)
+    ev3 = Evaluator(LevelOnly(p, L), None)
+    ev3.compare(xs, xs, False, True)
+    assert ev3.mul_count() == 4 * d + (d - 1)  # z^16 by four squarings per digit
+
+
+def _compare_case(st, d, count, seed):
+    rnd = random.Random(seed)
+    b = (st.p + 1) // 2
+    ns = st.ss.ns
+    xs_v = [[rnd.randrange(b ** d) for _ in range(ns)] for _ in range(count)]
+    ys_v = [[rnd.randrange(b ** d) if rnd.random() < 0.7 else xs_v[c][s] for s in range(ns)] for c in range(count)]
+    return xs_v, ys_v
+
+
+def _digits(vals, b, d):
+    return [[(v // b ** k) % b for v in vals] for k in range(d)]
+
+
+@pytest.mark.parametrize("p,d,L", [(17, 2, 6), (131, 1, 9)])
+def test_compare_lt_eq_small_ring(p, d, L):
+    st = OracleSetup(logN=8, p=p, L=L, K=2, seed=21, **CHAIN50)
+    b = (p + 1) // 2
+    xs_v, ys_v = _compare_case(st, d, 1, seed=p)
+    x = st.encrypt_slots(_digits(xs_v[0], b, d), seed=30)
+    y = st.encrypt_slots(_digits(ys_v[0], b, d), seed=31)
+    ev = st.evaluator()
+    lt, eq = ev.compare(x, y, True, True)
+    assert st.decrypt_slots(lt) == [int(a < c) for a, c in zip(xs_v[0], ys_v[0])]
+    assert st.decrypt_slots(eq) == [int(a == c) for a, c in zip(xs_v[0], ys_v[0])]
+    assert st.o.noise_bits(lt, st.s) < np.log2(st.o.primes[0]) - 1
+
+
+def test_max_min_small_ring():
+    p, d = 17, 2
+    st = OracleSetup(logN=8, p=p, L=8, K=2, seed=22, **CHAIN50)
+    b = (p + 1) // 2
+    xs_v, ys_v = _compare_case(st, d, 1, seed=3)
+    x = st.encrypt_slots(_digits(xs_v[0], b, d), seed=40)
+    y = st.encrypt_slots(_digits(ys_v[0], b, d), seed=41)
+    ev = st.evaluator()
+    mx, mn = ev.max_min(x, y)
+    got_max = [sum(st.decrypt_slots(mx[k])[s] * b ** k for k in range(d)) for s in range(st.ss.ns)]
+    got_min = [sum(st.decrypt_slots(mn[k])[s] * b ** k for k in range(d)) for s in range(st.ss.ns)]
+    assert got_max == [max(a, c) for a, c in zip(xs_v[0], ys_v[0])]
+    assert got_min == [min(a, c) for a, c in zip(xs_v[0], ys_v[0])]
+
+
+def test_small_config_full_size_lt():
+    """N=2^12, p=17, d=1, 4 x 36-bit primes + 1 special: one encrypted LT of
+    two packed ciphertexts, decrypted against plaintext, noise below q0/2."""
+    st = OracleSetup(logN=12, p=17, L=4, K=1, seed=1, **CHAIN36)
+    rnd = random.Random(1)
+    xv = [rnd.randrange(9) for _ in range(st.ss.ns)]
+    yv = [rnd.randrange(9) for _ in range(st.ss.ns)]
+    x = st.encrypt_slots([xv], seed=2)
+    y = st.encrypt_slots([yv], seed=3)
+    ev = st.evaluator()
+    lt = ev.compare_lt(x, y)
+    assert st.decrypt_slots(lt) == [int(a < c) for a, c in zip(xv, yv)]
+    nb = st.o.noise_bits(lt, st.s)
+    assert nb < np.log2(st.o.primes[0]) - 1, nb
