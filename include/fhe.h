@@ -1,0 +1,240 @@
+/*
+ * fhe.h -- C ABI of the GB300 BGV encrypted-comparison library.
+ *
+ * What it computes follows BoostCom (Yudha et al., PACT'24): BGV ciphertexts
+ * over R_Q = Z_Q[X]/(X^N+1) held in RNS (Sec. 2.1 "Basics and arithmetic
+ * ops", Sec. 2.2 "Efficient Polynomial and NTT"), and the word-wise
+ * comparison of Sec. 2.1 "Non-arithmetic Comparison": per-digit less-than and
+ * equality through the univariate circuit, combined in lexicographic order.
+ *
+ * Conventions shared by every call
+ *   - Handles are opaque.  Whatever a *_create / keygen / encrypt / arithmetic
+ *     call returns through an out-pointer is owned by the caller and must be
+ *     released with the matching *_destroy; a context must outlive every
+ *     handle made from it.  Destroying NULL is a no-op.
+ *   - Device memory comes from the allocator given to fhe_ctx_create (or
+ *     cudaMallocAsync when none is given) through a pool owned by the context.
+ *     Host buffers passed in are read during the call only; host buffers
+ *     passed out are written before the call returns.
+ *   - Every call returns 0 (FHE_OK) or a negative FHE_E* code and never
+ *     aborts; fhe_last_error() describes the last failure on a context.
+ *   - Work is enqueued on the context's stream (asynchronous with respect to
+ *     the host) except where a call says it synchronises.
+ *   - A ciphertext handle holds a batch of `count` ciphertexts of one level;
+ *     binary operations act element-wise over two batches of equal count.
+ *     On the device a batch is u64 [count][npoly][level][N] in the NTT
+ *     (evaluation) domain; npoly is 2, or 3 after fhe_mul.
+ *   - Slot values are integers in [0, p); a ciphertext holds n_s slots
+ *     (fhe_info.slots).  Comparison digits must lie in [0, (p-1)/2].
+ */
+#ifndef FHE_GB300_H
+#define FHE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fhe_ctx fhe_ctx;
+typedef struct fhe_sk fhe_sk;
+typedef struct fhe_pk fhe_pk;
+typedef struct fhe_evk fhe_evk;
+typedef struct fhe_ct fhe_ct;
+
+enum {
+    FHE_OK = 0,
+    FHE_EINVAL = -1,      /* bad argument (NULL, size out of range, ...) */
+    FHE_EMISMATCH = -2,   /* operands of different contexts, counts or shapes */
+    FHE_ELEVEL = -3,      /* level too low for the operation */
+    FHE_ENOMEM = -4,      /* device allocation failed */
+    FHE_EBUDGET = -5,     /* the context's device-memory budget would be exceeded */
+    FHE_ETIMEOUT = -6,    /* a bounded wait ran out */
+    FHE_ECUDA = -7,       /* a CUDA runtime call failed */
+    FHE_ENOKEY = -8,      /* no switching key for the requested Galois element */
+    FHE_EUNSUPPORTED = -9 /* parameter combination not provided */
+};
+
+/* BGV parameters.  The prime chain is the L+K smallest primes q with
+ * q = 1 (mod prime_mod) in [prime_lo, prime_hi): the first L carry data, the
+ * last K (alpha) are the special primes of hybrid key switching.  prime_mod
+ * must be a multiple of 2N and of p; all primes must have one bit length
+ * below 58.  log_n in [10, 14]; p an odd prime, p = 1 (mod 4) or p = 3 (mod 8). */
+typedef struct {
+    int log_n;
+    uint64_t p;
+    int L;
+    int K;
+    uint64_t prime_mod;
+    uint64_t prime_lo;
+    uint64_t prime_hi;
+} fhe_params;
+
+/* Device allocator.  alloc returns device memory of `bytes` usable in stream
+ * order on `stream` (NULL on failure); free returns it. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} fhe_allocator;
+
+typedef struct {
+    int N;          /* ring degree */
+    int L, K;       /* data and special primes */
+    int slots;      /* n_s = N / ord_2N(p) values per ciphertext */
+    int subring;    /* M: plaintexts live in Z_p[Y]/(Y^M+1), Y = X^(N/M) */
+    int dnum_max;   /* key-switching digits at the top level, ceil(L/K) */
+    uint64_t p;
+} fhe_info;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Builds the prime chain, NTT tables and key-switching constants on the
+ * current CUDA device.  stream: a cudaStream_t (NULL = legacy default).
+ * alloc may be NULL.  Synchronises. */
+int fhe_ctx_create(const fhe_params *params, const fhe_allocator *alloc, void *stream, fhe_ctx **out);
+void fhe_ctx_destroy(fhe_ctx *ctx);
+const char *fhe_last_error(const fhe_ctx *ctx);
+int fhe_ctx_info(const fhe_ctx *ctx, fhe_info *out);
+/* The L+K primes, data first.  out: host array of L+K entries. */
+int fhe_ctx_primes(const fhe_ctx *ctx, uint64_t *out);
+int fhe_ctx_set_stream(fhe_ctx *ctx, void *stream);
+/* Waits for all work on the context's stream. */
+int fhe_ctx_sync(fhe_ctx *ctx);
+/* Device bytes held by the pool (reserved) and handed out (in_use). */
+int fhe_ctx_memory(const fhe_ctx *ctx, uint64_t *reserved, uint64_t *in_use);
+/* Cap on reserved bytes (0 = none); allocations past it fail with FHE_EBUDGET. */
+int fhe_ctx_set_budget(fhe_ctx *ctx, uint64_t bytes);
+/* Number of kernels this context has launched so far. */
+int64_t fhe_ctx_launches(const fhe_ctx *ctx);
+
+/* ---- keys ---------------------------------------------------------------- */
+
+/* Key generation with caller randomness (the path the tests use).
+ * s: int64[N] ternary secret; a: uint64[L][N] public-key mask, row i uniform
+ * in [0, q_i), coefficient domain; e: int64[N] error.
+ * pk = (-a s + p e, a) over the data primes (Sec. 2.1, RLWE public key). */
+int fhe_keygen_explicit(fhe_ctx *ctx, const int64_t *s, const uint64_t *a, const int64_t *e, fhe_sk **sk,
+                        fhe_pk **pk);
+/* Key generation drawing s, a, e on the device from a Philox4x32-10 stream
+ * keyed by seed (Salmon et al., SC'11). */
+int fhe_keygen(fhe_ctx *ctx, uint64_t seed, fhe_sk **sk, fhe_pk **pk);
+void fhe_sk_destroy(fhe_sk *sk);
+void fhe_pk_destroy(fhe_pk *pk);
+
+/* Evaluation keys: the relinearisation key (s^2 -> s) and one rotation key
+ * (sigma_g(s) -> s) per Galois element galois[i] (odd, in (1, 2N)).
+ * Hybrid key-switching keys, one per digit j of ceil(L/K) digits:
+ *   ksk_j = (-a_j s + p e_j + P [i in D_j] s', a_j)  over all L+K primes,
+ * D_j the data primes jK .. (j+1)K-1, P the product of the special primes.
+ * Explicit randomness: a: uint64[1+n_galois][dnum][L+K][N] (coefficient
+ * domain, uniform mod the prime of each row), e: int64[1+n_galois][dnum][N];
+ * key 0 is the relinearisation key. */
+int fhe_evk_create_explicit(fhe_ctx *ctx, const fhe_sk *sk, const int64_t *galois, int n_galois, const uint64_t *a,
+                            const int64_t *e, fhe_evk **out);
+int fhe_evk_create(fhe_ctx *ctx, const fhe_sk *sk, const int64_t *galois, int n_galois, uint64_t seed,
+                   fhe_evk **out);
+void fhe_evk_destroy(fhe_evk *evk);
+
+/* ---- encryption ------------------------------------------------------------ */
+
+/* Encrypts `count` slot vectors: slots uint64[count][n_s], each in [0, p).
+ * Enc(m) = (pk0 u + p e0 + m, pk1 u + p e1) at level L, with m the slot
+ * encoding.  u, e0, e1: int64[count][N].  Synchronises. */
+int fhe_encrypt_explicit(fhe_ctx *ctx, const fhe_pk *pk, const uint64_t *slots, int count, const int64_t *u,
+                         const int64_t *e0, const int64_t *e1, fhe_ct **out);
+int fhe_encrypt(fhe_ctx *ctx, const fhe_pk *pk, const uint64_t *slots, int count, uint64_t seed, fhe_ct **out);
+/* Decrypts every ciphertext of the batch: a copy is modulus-switched to one
+ * prime, m = [c0 + c1 s]_{q0} (centred) mod p, then decoded.
+ * slots: uint64[count][n_s].  Fails with FHE_EINVAL if a plaintext is not a
+ * slot-constant encoding.  Synchronises. */
+int fhe_decrypt(fhe_ctx *ctx, const fhe_sk *sk, const fhe_ct *ct, uint64_t *slots);
+void fhe_ct_destroy(fhe_ct *ct);
+int fhe_ct_shape(const fhe_ct *ct, int *count, int *npoly, int *level);
+/* Coefficient-domain residues, host uint64[count][npoly][level][N].  Synchronises. */
+int fhe_ct_export_coeff(fhe_ctx *ctx, const fhe_ct *ct, uint64_t *host);
+int fhe_ct_import_coeff(fhe_ctx *ctx, const uint64_t *host, int count, int npoly, int level, fhe_ct **out);
+
+/* ---- arithmetic (Sec. 2.1: add, mult, rotate; Sec. 2.2: RNS, NTT) -------- */
+
+/* Operands at different levels are first modulus-switched (one prime at a
+ * time) to the lower level. */
+int fhe_add(fhe_ctx *ctx, const fhe_ct *a, const fhe_ct *b, fhe_ct **out);
+int fhe_sub(fhe_ctx *ctx, const fhe_ct *a, const fhe_ct *b, fhe_ct **out);
+int fhe_neg(fhe_ctx *ctx, const fhe_ct *a, fhe_ct **out);
+/* Multiply by / add the constant c of Z_p (lifted to (-p/2, p/2]). */
+int fhe_mul_const(fhe_ctx *ctx, const fhe_ct *a, int64_t c, fhe_ct **out);
+int fhe_add_const(fhe_ctx *ctx, const fhe_ct *a, int64_t c, fhe_ct **out);
+/* Tensor product: 3-poly result (c0 d0, c0 d1 + c1 d0, c1 d1). */
+int fhe_mul(fhe_ctx *ctx, const fhe_ct *a, const fhe_ct *b, fhe_ct **out);
+/* Hybrid key switching of the third poly with the relinearisation key:
+ * INTT, ModUp per digit (fast basis conversion + NTT), inner product with the
+ * key, ModDown (BGV: the correction is a multiple of p). */
+int fhe_relinearize(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *a, fhe_ct **out);
+/* BGV modulus switching down to target_level (>= 1), one prime at a time:
+ * x' = (x - p [x_last p^-1]_{q_last}) q_last^-1.  q = 1 (mod p), so the
+ * plaintext is unchanged. */
+int fhe_mod_switch(fhe_ctx *ctx, const fhe_ct *a, int target_level, fhe_ct **out);
+/* Galois automorphism X -> X^g followed by key switching back to s. */
+int fhe_rotate(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *a, int64_t galois, fhe_ct **out);
+/* The circuit product: align levels, tensor, relinearise, then
+ * modulus-switch by one prime when the level is above 1. */
+int fhe_mul_relin(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *a, const fhe_ct *b, fhe_ct **out);
+
+/* ---- comparison (Sec. 2.1 "Non-arithmetic Comparison") ------------------- */
+
+/* x, y: arrays of d ciphertext handles, digit k of both operands (least
+ * significant first, digits in [0, (p-1)/2]); all handles of one call have
+ * the same count.  Per digit z = x_k - y_k, LT_k = f(z) with f the
+ * interpolating polynomial of [z >= (p+1)/2] evaluated by Paterson-Stockmeyer,
+ * EQ_k = 1 - z^(p-1); digits merged pairwise, L = L_hi + E_hi L_lo,
+ * E = E_hi E_lo.  Results decrypt to 1 / 0 in every slot. */
+int fhe_compare_lt(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                   fhe_ct **out);
+int fhe_compare_eq(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                   fhe_ct **out);
+/* Both at once (they share z^(p-1)). */
+int fhe_compare(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                fhe_ct **lt, fhe_ct **eq);
+/* max / min digit-wise: L = LT(x, y); t_k = L (y_k - x_k);
+ * max_k = x_k + t_k, min_k = y_k - t_k.  out_max / out_min: d handles each
+ * (either may be NULL). */
+int fhe_max_min(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                fhe_ct **out_max, fhe_ct **out_min);
+int fhe_max(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+            fhe_ct **out);
+int fhe_min(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+            fhe_ct **out);
+
+/* ---- operation trace --------------------------------------------------------- */
+
+/* Op codes recorded while tracing is on. */
+enum { FHE_OP_MUL = 1, FHE_OP_ADD = 2, FHE_OP_SUB = 3, FHE_OP_CMUL = 4, FHE_OP_CADD = 5, FHE_OP_NEG = 6,
+       FHE_OP_ROT = 7 };
+/* on != 0 clears and starts recording circuit-level operations. */
+int fhe_trace_enable(fhe_ctx *ctx, int on);
+/* Copies up to cap entries (op code, level of the operands); returns the
+ * number recorded (>= 0) or an error code. */
+int fhe_trace_get(const fhe_ctx *ctx, int32_t *ops, int32_t *levels, int cap);
+
+/* ---- transforms on caller buffers (device pointers) ------------------------- */
+
+/* In-place forward / inverse negacyclic NTT of nlimbs limbs of N residues at
+ * device address data (limb i reduced mod prime prime_idx[i], host array).
+ * Forward output is in bit-reversed order: A[k] = a(psi^(2 brv(k)+1)). */
+int fhe_ntt_forward(fhe_ctx *ctx, uint64_t *data, const int32_t *prime_idx, int nlimbs);
+int fhe_ntt_inverse(fhe_ctx *ctx, uint64_t *data, const int32_t *prime_idx, int nlimbs);
+
+/* ---- self test ---------------------------------------------------------------- */
+
+/* Runs the library's modular-arithmetic routines (the same source the kernels
+ * use, compiled for the host) against 128-bit reference arithmetic on `iters`
+ * pseudo-random and edge-case inputs per prime of the given chain.  Needs no
+ * GPU.  Returns 0 if all agree, else the number of mismatches. */
+int fhe_selftest_modarith(uint64_t prime_mod, uint64_t prime_lo, uint64_t prime_hi, int nprimes, int iters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FHE_GB300_H */

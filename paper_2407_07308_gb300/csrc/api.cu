@@ -1,0 +1,974 @@
+// api.cu -- the extern "C" boundary: contexts, keys, ciphertexts, encryption,
+// decryption and the arithmetic / comparison entry points declared in fhe.h.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "fhe_internal.h"
+
+// ---------------------------------------------------------------------------
+// errors, pool
+// ---------------------------------------------------------------------------
+
+int fhe_fail(fhe_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int fhe_cuda_check(fhe_ctx *ctx, cudaError_t e, const char *where)
+{
+    if (e == cudaSuccess) return 0;
+    return fhe_fail(ctx, FHE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void *Pool::get(size_t bytes, int *err)
+{
+    auto &fl = free_lists[bytes];
+    if (!fl.empty()) {
+        void *p = fl.back();
+        fl.pop_back();
+        in_use += bytes;
+        return p;
+    }
+    if (budget && reserved + bytes > budget) {
+        // give cached blocks of other sizes back before refusing
+        for (auto &kv : free_lists) {
+            for (void *q : kv.second) {
+                if (alloc.free)
+                    alloc.free(q, kv.first, stream, alloc.user);
+                else
+                    cudaFreeAsync(q, stream);
+                live.erase(q);
+                reserved -= kv.first;
+            }
+            kv.second.clear();
+        }
+        if (reserved + bytes > budget) {
+            *err = FHE_EBUDGET;
+            return nullptr;
+        }
+    }
+    if (fail_after == 0) {
+        *err = FHE_ENOMEM;
+        return nullptr;
+    }
+    if (fail_after > 0) fail_after--;
+    void *p = nullptr;
+    if (alloc.alloc)
+        p = alloc.alloc(bytes, (void *)stream, alloc.user);
+    else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess)
+        p = nullptr;
+    if (!p) {
+        *err = FHE_ENOMEM;
+        return nullptr;
+    }
+    live[p] = bytes;
+    reserved += bytes;
+    in_use += bytes;
+    return p;
+}
+
+void Pool::put(void *p)
+{
+    auto it = live.find(p);
+    if (it == live.end()) return;
+    free_lists[it->second].push_back(p);
+    in_use -= it->second;
+}
+
+void Pool::release_all()
+{
+    for (auto &kv : live) {
+        if (alloc.free)
+            alloc.free(kv.first, kv.second, (void *)stream, alloc.user);
+        else
+            cudaFreeAsync(kv.first, stream);
+    }
+    live.clear();
+    free_lists.clear();
+    reserved = in_use = 0;
+}
+
+fhe_ct *ct_new(fhe_ctx *ctx, int count, int npoly, int level, int *err)
+{
+    const size_t bytes = sizeof(u64) * (size_t)count * npoly * level * ctx->N;
+    void *p = ctx->pool.get(bytes, err);
+    if (!p) {
+        fhe_fail(ctx, *err, "out of device memory for a ciphertext");
+        return nullptr;
+    }
+    fhe_ct *ct = new fhe_ct;
+    ct->ctx = ctx;
+    ct->count = count;
+    ct->npoly = npoly;
+    ct->level = level;
+    ct->d = (u64 *)p;
+    ct->bytes = bytes;
+    return ct;
+}
+
+const KeySwitchKey *fhe_evk::find(int64_t g) const
+{
+    for (const auto &k : keys)
+        if (k.galois == g) return &k;
+    return nullptr;
+}
+
+namespace {
+
+struct DevBuf {
+    fhe_ctx *c;
+    void *p = nullptr;
+    DevBuf(fhe_ctx *ctx, size_t bytes, int *err) : c(ctx)
+    {
+        if (*err) return;
+        p = c->pool.get(bytes, err);
+    }
+    ~DevBuf()
+    {
+        if (p) c->pool.put(p);
+    }
+    u64 *u() { return (u64 *)p; }
+    int64_t *i() { return (int64_t *)p; }
+};
+
+LimbMap plain_map(int nl, int prime_off)
+{
+    LimbMap m;
+    memset(&m, 0, sizeof(m));
+    m.nl = nl;
+    for (int i = 0; i < nl; i++) m.in_limb[i] = m.out_limb[i] = i, m.prime[i] = prime_off + i;
+    return m;
+}
+
+// NTT (forward) of `outer` contiguous blocks of nl limbs, primes prime_off..
+void ntt_blocks(fhe_ctx *c, const u64 *in, u64 *out, int outer, int nl, int prime_off, bool inverse)
+{
+    LimbMap m = plain_map(nl, prime_off);
+    m.in_outer = m.out_outer = (long long)nl * c->N;
+    if (inverse)
+        launch_ntt_inv_plain(c, in, out, m, outer * nl);
+    else
+        launch_ntt_fwd_plain(c, in, out, m, outer * nl);
+}
+
+void primes_range(int *pr, int n, int off)
+{
+    for (int i = 0; i < n; i++) pr[i] = off + i;
+}
+
+// slot values (n_s) -> plaintext coefficients (N), values in [0, p)
+void encode_slots(const fhe_ctx *c, const uint64_t *v, int64_t *m)
+{
+    const u64 p = c->p;
+    const int M = c->M, stride = c->N / M;
+    memset(m, 0, sizeof(int64_t) * c->N);
+    if (c->slots_linear) {
+        // m_j = M^-1 sum_s v_s zeta^(-e_s j)
+        const u64 Minv = host_invmod(M % p, p);
+        for (int j = 0; j < M; j++) {
+            u64 acc = 0;
+            for (int s = 0; s < c->ns; s++) {
+                const u64 e = (u64)((2 * M - (int64_t)c->slot_exp[s] * j % (2 * M)) % (2 * M));
+                acc = (acc + (v[s] % p) * host_powmod(c->zeta, e, p)) % p;
+            }
+            m[(size_t)j * stride] = (int64_t)host_mulmod(acc, Minv, p);
+        }
+    } else {
+        // two slots: m = (v0+v1)/2 + (v0-v1)/2 h(Y), h = -(Y + Y^3)/gamma
+        const u64 inv2 = host_invmod(2, p), ig = host_invmod(c->gamma, p);
+        const u64 a = (v[0] % p + v[1] % p) % p * inv2 % p;
+        const u64 b = (v[0] % p + p - v[1] % p) % p * inv2 % p;
+        const u64 h = (p - ig) % p;
+        m[0] = (int64_t)a;
+        m[(size_t)1 * stride] = (int64_t)(b * h % p);
+        m[(size_t)3 * stride] = (int64_t)(b * h % p);
+    }
+}
+
+// plaintext coefficients in [0, p) -> slots; false if not a slot encoding
+bool decode_slots(const fhe_ctx *c, const int64_t *m, uint64_t *v)
+{
+    const u64 p = c->p;
+    const int M = c->M, stride = c->N / M;
+    for (int n = 0; n < c->N; n++)
+        if (n % stride && m[n]) return false;
+    if (c->slots_linear) {
+        for (int s = 0; s < c->ns; s++) {
+            const u64 z = host_powmod(c->zeta, (u64)c->slot_exp[s], p);
+            u64 acc = 0, zz = 1;
+            for (int j = 0; j < M; j++) {
+                acc = (acc + (u64)m[(size_t)j * stride] * zz) % p;
+                zz = zz * z % p;
+            }
+            v[s] = acc;
+        }
+        return true;
+    }
+    for (int s = 0; s < 2; s++) {
+        const u64 g = s == 0 ? c->gamma : p - c->gamma;  // factor Y^2 + g Y - 1
+        u64 a0 = 0, a1 = 0, w0 = 1, w1 = 0;             // residue and Y^j mod factor
+        for (int j = 0; j < M; j++) {
+            const u64 mj = (u64)m[(size_t)j * stride];
+            a0 = (a0 + mj * w0) % p;
+            a1 = (a1 + mj * w1) % p;
+            const u64 n0 = w1, n1 = (w0 + p - g * w1 % p) % p;  // Y (w0 + w1 Y), Y^2 = 1 - gY
+            w0 = n0;
+            w1 = n1;
+        }
+        if (a1) return false;
+        v[s] = a0;
+    }
+    return true;
+}
+
+#define CHECK_CTX(c)                                  \
+    do {                                              \
+        if (!(c)) return FHE_EINVAL;                  \
+    } while (0)
+#define LOCK(c) std::lock_guard<std::mutex> _g((c)->mu)
+
+int sync_check(fhe_ctx *c, const char *where)
+{
+    return fhe_cuda_check(c, cudaStreamSynchronize(c->stream), where);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+
+extern "C" int fhe_ctx_create(const fhe_params *P, const fhe_allocator *alloc, void *stream, fhe_ctx **out)
+{
+    if (!P || !out) return FHE_EINVAL;
+    *out = nullptr;
+    if (!ntt_supported_logn(P->log_n)) return FHE_EUNSUPPORTED;
+    if (P->L < 1 || P->K < 1 || P->K > FHE_MAXK || P->L + P->K > FHE_MAXP || (P->L + P->K - 1) / P->K > FHE_MAXD)
+        return FHE_EUNSUPPORTED;
+    if (P->p < 3 || !host_is_prime(P->p) || P->p > (1u << 20)) return FHE_EINVAL;
+    const u64 N = 1ull << P->log_n;
+    if (P->prime_mod % (2 * N) || P->prime_mod % P->p) return FHE_EINVAL;
+    fhe_ctx *c = new fhe_ctx;
+    c->logN = P->log_n;
+    c->N = (int)N;
+    c->L = P->L;
+    c->K = P->K;
+    c->np = P->L + P->K;
+    c->p = P->p;
+    c->stream = (cudaStream_t)stream;
+    c->q.resize(c->np);
+    if (host_find_primes(P->prime_mod, P->prime_lo, P->prime_hi, c->np, c->q.data()) != c->np) {
+        delete c;
+        return FHE_EINVAL;
+    }
+    int bits0 = 64 - __builtin_clzll(c->q[0]);
+    for (u64 q : c->q)
+        if (64 - __builtin_clzll(q) != bits0 || bits0 > 57) {
+            delete c;
+            return FHE_EUNSUPPORTED;
+        }
+    if (alloc) c->pool.alloc = *alloc;
+    else memset(&c->pool.alloc, 0, sizeof(fhe_allocator));
+    c->pool.stream = c->stream;
+    int e = build_tables(c);
+    if (!e) e = fhe_cuda_check(c, cudaDeviceSynchronize(), "ctx_create");
+    if (e) {
+        fhe_ctx_destroy(c);
+        return e;
+    }
+    *out = c;
+    return 0;
+}
+
+extern "C" void fhe_ctx_destroy(fhe_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    c->pool.release_all();
+    cudaFree(c->d_mq);
+    cudaFree(c->d_fwd);
+    cudaFree(c->d_inv);
+    cudaFree(c->d_ninv);
+    cudaFree(c->d_modup);
+    cudaFree(c->d_moddown);
+    cudaFree(c->d_modswitch);
+    for (auto &kv : c->d_perm) cudaFree(kv.second);
+    cudaStreamSynchronize(c->stream);
+    delete c;
+}
+
+extern "C" const char *fhe_last_error(const fhe_ctx *c) { return c ? c->err.c_str() : "no context"; }
+
+extern "C" int fhe_ctx_info(const fhe_ctx *c, fhe_info *out)
+{
+    if (!c || !out) return FHE_EINVAL;
+    out->N = c->N;
+    out->L = c->L;
+    out->K = c->K;
+    out->slots = c->ns;
+    out->subring = c->M;
+    out->dnum_max = (c->L + c->K - 1) / c->K;
+    out->p = c->p;
+    return 0;
+}
+
+extern "C" int fhe_ctx_primes(const fhe_ctx *c, uint64_t *out)
+{
+    if (!c || !out) return FHE_EINVAL;
+    memcpy(out, c->q.data(), sizeof(u64) * c->np);
+    return 0;
+}
+
+extern "C" int fhe_ctx_set_stream(fhe_ctx *c, void *stream)
+{
+    CHECK_CTX(c);
+    LOCK(c);
+    c->stream = (cudaStream_t)stream;
+    c->pool.stream = c->stream;
+    return 0;
+}
+
+extern "C" int fhe_ctx_sync(fhe_ctx *c)
+{
+    CHECK_CTX(c);
+    return sync_check(c, "sync");
+}
+
+extern "C" int fhe_ctx_memory(const fhe_ctx *c, uint64_t *reserved, uint64_t *in_use)
+{
+    if (!c) return FHE_EINVAL;
+    if (reserved) *reserved = c->pool.reserved;
+    if (in_use) *in_use = c->pool.in_use;
+    return 0;
+}
+
+extern "C" int fhe_ctx_set_budget(fhe_ctx *c, uint64_t bytes)
+{
+    CHECK_CTX(c);
+    LOCK(c);
+    c->pool.budget = bytes;
+    return 0;
+}
+
+extern "C" int64_t fhe_ctx_launches(const fhe_ctx *c) { return c ? c->launches : -1; }
+
+// ---------------------------------------------------------------------------
+// keys
+// ---------------------------------------------------------------------------
+
+extern "C" int fhe_keygen_explicit(fhe_ctx *c, const int64_t *s, const uint64_t *a, const int64_t *e, fhe_sk **sk,
+                                   fhe_pk **pk)
+{
+    CHECK_CTX(c);
+    if (!s || !a || !e || !sk || !pk) return FHE_EINVAL;
+    LOCK(c);
+    const int N = c->N, L = c->L, np = c->np;
+    int err = 0;
+    DevBuf ds(c, sizeof(int64_t) * N, &err), de(c, sizeof(int64_t) * N, &err);
+    DevBuf ta(c, sizeof(u64) * L * N, &err), te(c, sizeof(u64) * L * N, &err);
+    if (err) return fhe_fail(c, err, "keygen: out of memory");
+    fhe_sk *S = new fhe_sk;
+    S->ctx = c;
+    S->s.assign(s, s + N);
+    S->d_s = (u64 *)c->pool.get(sizeof(u64) * np * N, &err);
+    fhe_pk *Pk = new fhe_pk;
+    Pk->ctx = c;
+    Pk->d = err ? nullptr : (u64 *)c->pool.get(sizeof(u64) * 2 * L * N, &err);
+    if (err) {
+        fhe_sk_destroy(S);
+        fhe_pk_destroy(Pk);
+        return fhe_fail(c, err, "keygen: out of memory");
+    }
+    cudaMemcpyAsync(ds.p, s, sizeof(int64_t) * N, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(de.p, e, sizeof(int64_t) * N, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(ta.p, a, sizeof(u64) * L * N, cudaMemcpyHostToDevice, c->stream);
+    int pr[FHE_MAXP];
+    primes_range(pr, np, 0);
+    launch_rns_from_i64(c, ds.i(), nullptr, 1, S->d_s, 1, np, pr);
+    ntt_blocks(c, S->d_s, S->d_s, 1, np, 0, false);
+    launch_rns_from_i64(c, de.i(), nullptr, (int64_t)c->p, te.u(), 1, L, pr);
+    ntt_blocks(c, te.u(), te.u(), 1, L, 0, false);
+    u64 *pk1 = Pk->d + (size_t)L * N;
+    ntt_blocks(c, ta.u(), pk1, 1, L, 0, false);
+    // pk0 = e' - a s
+    launch_muladd(c, pk1, S->d_s, te.u(), Pk->d, 1, L, 0, 1);
+    int r = sync_check(c, "keygen");
+    if (r) {
+        fhe_sk_destroy(S);
+        fhe_pk_destroy(Pk);
+        return r;
+    }
+    *sk = S;
+    *pk = Pk;
+    return 0;
+}
+
+extern "C" void fhe_sk_destroy(fhe_sk *sk)
+{
+    if (!sk) return;
+    if (sk->d_s) sk->ctx->pool.put(sk->d_s);
+    delete sk;
+}
+
+extern "C" void fhe_pk_destroy(fhe_pk *pk)
+{
+    if (!pk) return;
+    if (pk->d) pk->ctx->pool.put(pk->d);
+    delete pk;
+}
+
+extern "C" int fhe_evk_create_explicit(fhe_ctx *c, const fhe_sk *sk, const int64_t *galois, int n_galois,
+                                       const uint64_t *a, const int64_t *e, fhe_evk **out)
+{
+    CHECK_CTX(c);
+    if (!sk || !a || !e || !out || n_galois < 0 || (n_galois && !galois)) return FHE_EINVAL;
+    LOCK(c);
+    const int N = c->N, L = c->L, K = c->K, np = c->np, dnum = (L + K - 1) / K;
+    int err = 0;
+    DevBuf ta(c, sizeof(u64) * np * N, &err), te(c, sizeof(u64) * np * N, &err);
+    DevBuf de(c, sizeof(int64_t) * N, &err), sp(c, sizeof(u64) * np * N, &err);
+    if (err) return fhe_fail(c, err, "evk: out of memory");
+    u64 Pw[FHE_MAXP], Pws[FHE_MAXP];
+    for (int i = 0; i < np; i++) {
+        u64 P = 1;
+        for (int k = 0; k < K; k++) P = host_mulmod(P, c->q[L + k] % c->q[i], c->q[i]);
+        Pw[i] = P;
+        Pws[i] = shoup_const(P, c->q[i]);
+    }
+    int pr[FHE_MAXP];
+    primes_range(pr, np, 0);
+    fhe_evk *E = new fhe_evk;
+    E->ctx = c;
+    for (int key = 0; key <= n_galois && !err; key++) {
+        KeySwitchKey k;
+        k.galois = key == 0 ? 0 : galois[key - 1];
+        // s' in the NTT domain: s*s, or sigma_g(s) as an index permutation
+        if (key == 0) {
+            launch_mul_poly(c, sk->d_s, sk->d_s, sp.u(), 1, np, 0);
+        } else {
+            const int *perm = nullptr;
+            if ((err = galois_perm(c, k.galois, &perm))) break;
+            launch_automorphism(c, sk->d_s, sp.u(), 1, np, perm);
+        }
+        k.d = (u64 *)c->pool.get(sizeof(u64) * dnum * 2 * np * N, &err);
+        if (err) break;
+        E->keys.push_back(k);
+        for (int j = 0; j < dnum; j++) {
+            const size_t off = ((size_t)key * dnum + j);
+            cudaMemcpyAsync(ta.p, a + off * np * N, sizeof(u64) * np * N, cudaMemcpyHostToDevice, c->stream);
+            cudaMemcpyAsync(de.p, e + off * N, sizeof(int64_t) * N, cudaMemcpyHostToDevice, c->stream);
+            ntt_blocks(c, ta.u(), ta.u(), 1, np, 0, false);
+            launch_rns_from_i64(c, de.i(), nullptr, (int64_t)c->p, te.u(), 1, np, pr);
+            ntt_blocks(c, te.u(), te.u(), 1, np, 0, false);
+            u64 *k0 = k.d + (size_t)(j * 2 + 0) * np * N, *k1 = k.d + (size_t)(j * 2 + 1) * np * N;
+            launch_ksk_digit(c, ta.u(), te.u(), sk->d_s, sp.u(), k0, k1, j * K, std::min((j + 1) * K, L), Pw, Pws);
+            // the staging buffers are reused by the next digit: keep host copies ordered
+            if ((err = sync_check(c, "evk digit"))) break;
+        }
+    }
+    if (err) {
+        fhe_evk_destroy(E);
+        return err;
+    }
+    *out = E;
+    return 0;
+}
+
+extern "C" void fhe_evk_destroy(fhe_evk *evk)
+{
+    if (!evk) return;
+    for (auto &k : evk->keys)
+        if (k.d) evk->ctx->pool.put(k.d);
+    delete evk;
+}
+
+// ---------------------------------------------------------------------------
+// encryption, decryption, import/export
+// ---------------------------------------------------------------------------
+
+extern "C" int fhe_encrypt_explicit(fhe_ctx *c, const fhe_pk *pk, const uint64_t *slots, int count,
+                                    const int64_t *u, const int64_t *e0, const int64_t *e1, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!pk || !slots || !u || !e0 || !e1 || !out || count < 1) return FHE_EINVAL;
+    LOCK(c);
+    const int N = c->N, L = c->L;
+    for (long long i = 0; i < (long long)count * c->ns; i++)
+        if (slots[i] >= c->p) return fhe_fail(c, FHE_EINVAL, "slot value out of [0, p)");
+    std::vector<int64_t> m((size_t)count * N);
+    for (int i = 0; i < count; i++) encode_slots(c, slots + (size_t)i * c->ns, m.data() + (size_t)i * N);
+    int err = 0;
+    const size_t vb = sizeof(int64_t) * count * N;
+    DevBuf du(c, vb, &err), d0(c, vb, &err), d1(c, vb, &err), dm(c, vb, &err);
+    DevBuf U(c, sizeof(u64) * count * L * N, &err), T0(c, sizeof(u64) * count * L * N, &err),
+        T1(c, sizeof(u64) * count * L * N, &err);
+    if (err) return fhe_fail(c, err, "encrypt: out of memory");
+    fhe_ct *ct = ct_new(c, count, 2, L, &err);
+    if (!ct) return err;
+    cudaMemcpyAsync(du.p, u, vb, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(d0.p, e0, vb, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(d1.p, e1, vb, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(dm.p, m.data(), vb, cudaMemcpyHostToDevice, c->stream);
+    int pr[FHE_MAXP];
+    primes_range(pr, L, 0);
+    launch_rns_from_i64(c, du.i(), nullptr, 1, U.u(), count, L, pr);
+    launch_rns_from_i64(c, d0.i(), dm.i(), (int64_t)c->p, T0.u(), count, L, pr);
+    launch_rns_from_i64(c, d1.i(), nullptr, (int64_t)c->p, T1.u(), count, L, pr);
+    ntt_blocks(c, U.u(), U.u(), count, L, 0, false);
+    ntt_blocks(c, T0.u(), T0.u(), count, L, 0, false);
+    ntt_blocks(c, T1.u(), T1.u(), count, L, 0, false);
+    // c0 = pk0 u + t0, c1 = pk1 u + t1; write into [count][2][L][N]
+    DevBuf C0(c, sizeof(u64) * count * L * N, &err), C1(c, sizeof(u64) * count * L * N, &err);
+    if (err) {
+        fhe_ct_destroy(ct);
+        return fhe_fail(c, err, "encrypt: out of memory");
+    }
+    launch_muladd(c, U.u(), pk->d, T0.u(), C0.u(), count, L, 0, 0);
+    launch_muladd(c, U.u(), pk->d + (size_t)L * N, T1.u(), C1.u(), count, L, 0, 0);
+    launch_copy_limbs(c, C0.u(), ct->d, count, L, (long long)L * N, 2LL * L * N);
+    launch_copy_limbs(c, C1.u(), ct->d + (size_t)L * N, count, L, (long long)L * N, 2LL * L * N);
+    int r = sync_check(c, "encrypt");
+    if (r) {
+        fhe_ct_destroy(ct);
+        return r;
+    }
+    *out = ct;
+    return 0;
+}
+
+extern "C" int fhe_decrypt(fhe_ctx *c, const fhe_sk *sk, const fhe_ct *ct, uint64_t *slots)
+{
+    CHECK_CTX(c);
+    if (!sk || !ct || !slots || ct->npoly != 2) return FHE_EINVAL;
+    LOCK(c);
+    const int N = c->N, count = ct->count;
+    fhe_ct *one = nullptr;
+    int err = op_lower(c, ct, 1, &one);
+    if (err) return err;
+    DevBuf t(c, sizeof(u64) * count * N, &err);
+    if (err) {
+        fhe_ct_destroy(one);
+        return fhe_fail(c, err, "decrypt: out of memory");
+    }
+    // t = c0 + c1 s at limb 0 for each ct (one is [count][2][1][N]): gather
+    // c0 and c1 into contiguous [count][N] blocks first
+    {
+        DevBuf c0(c, sizeof(u64) * count * N, &err), c1(c, sizeof(u64) * count * N, &err);
+        if (err) {
+            fhe_ct_destroy(one);
+            return fhe_fail(c, err, "decrypt: out of memory");
+        }
+        launch_copy_limbs(c, one->d, c0.u(), count, 1, 2LL * N, N);
+        launch_copy_limbs(c, one->d + N, c1.u(), count, 1, 2LL * N, N);
+        launch_muladd(c, c1.u(), sk->d_s, c0.u(), t.u(), count, 1, 0, 0);
+    }
+    ntt_blocks(c, t.u(), t.u(), count, 1, 0, true);
+    std::vector<u64> h((size_t)count * N);
+    cudaMemcpyAsync(h.data(), t.p, sizeof(u64) * h.size(), cudaMemcpyDeviceToHost, c->stream);
+    int r = sync_check(c, "decrypt");
+    fhe_ct_destroy(one);
+    if (r) return r;
+    const u64 q0 = c->q[0], p = c->p;
+    std::vector<int64_t> m(N);
+    for (int i = 0; i < count; i++) {
+        for (int n = 0; n < N; n++) {
+            const u64 v = h[(size_t)i * N + n];
+            // centred representative mod q0, then mod p
+            const int64_t cv = v > q0 / 2 ? -(int64_t)(q0 - v) : (int64_t)v;
+            int64_t mp = cv % (int64_t)p;
+            if (mp < 0) mp += (int64_t)p;
+            m[n] = mp;
+        }
+        if (!decode_slots(c, m.data(), slots + (size_t)i * c->ns))
+            return fhe_fail(c, FHE_EINVAL, "decrypt: plaintext is not a slot encoding");
+    }
+    return 0;
+}
+
+extern "C" void fhe_ct_destroy(fhe_ct *ct)
+{
+    if (!ct) return;
+    if (ct->d) ct->ctx->pool.put(ct->d);
+    delete ct;
+}
+
+extern "C" int fhe_ct_shape(const fhe_ct *ct, int *count, int *npoly, int *level)
+{
+    if (!ct) return FHE_EINVAL;
+    if (count) *count = ct->count;
+    if (npoly) *npoly = ct->npoly;
+    if (level) *level = ct->level;
+    return 0;
+}
+
+extern "C" int fhe_ct_export_coeff(fhe_ctx *c, const fhe_ct *ct, uint64_t *host)
+{
+    CHECK_CTX(c);
+    if (!ct || !host) return FHE_EINVAL;
+    LOCK(c);
+    int err = 0;
+    DevBuf t(c, ct->bytes, &err);
+    if (err) return fhe_fail(c, err, "export: out of memory");
+    ntt_blocks(c, ct->d, t.u(), ct->count * ct->npoly, ct->level, 0, true);
+    cudaMemcpyAsync(host, t.p, ct->bytes, cudaMemcpyDeviceToHost, c->stream);
+    return sync_check(c, "export");
+}
+
+extern "C" int fhe_ct_import_coeff(fhe_ctx *c, const uint64_t *host, int count, int npoly, int level, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!host || !out || count < 1 || npoly < 2 || npoly > 3 || level < 1 || level > c->L) return FHE_EINVAL;
+    LOCK(c);
+    int err = 0;
+    fhe_ct *ct = ct_new(c, count, npoly, level, &err);
+    if (!ct) return err;
+    cudaMemcpyAsync(ct->d, host, ct->bytes, cudaMemcpyHostToDevice, c->stream);
+    ntt_blocks(c, ct->d, ct->d, count * npoly, level, 0, false);
+    int r = sync_check(c, "import");
+    if (r) {
+        fhe_ct_destroy(ct);
+        return r;
+    }
+    *out = ct;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// arithmetic
+// ---------------------------------------------------------------------------
+
+namespace {
+
+int same_ctx(fhe_ctx *c, const fhe_ct *a) { return a && a->ctx == c; }
+
+// Align two batches to the lower level (temporaries owned by the caller).
+int align2(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, const fhe_ct **a2, const fhe_ct **b2, fhe_ct **ta,
+           fhe_ct **tb)
+{
+    *ta = *tb = nullptr;
+    *a2 = a;
+    *b2 = b;
+    if (a->level > b->level) {
+        int e = op_lower(c, a, b->level, ta);
+        if (e) return e;
+        *a2 = *ta;
+    } else if (b->level > a->level) {
+        int e = op_lower(c, b, a->level, tb);
+        if (e) return e;
+        *b2 = *tb;
+    }
+    return 0;
+}
+
+int launch_status(fhe_ctx *c, const char *where) { return fhe_cuda_check(c, cudaGetLastError(), where); }
+
+}  // namespace
+
+extern "C" int fhe_add(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!same_ctx(c, a) || !same_ctx(c, b) || !out) return FHE_EINVAL;
+    LOCK(c);
+    const fhe_ct *a2, *b2;
+    fhe_ct *ta, *tb;
+    int e = align2(c, a, b, &a2, &b2, &ta, &tb);
+    if (!e) e = op_addsub(c, a2, b2, 0, out);
+    fhe_ct_destroy(ta);
+    fhe_ct_destroy(tb);
+    return e ? e : launch_status(c, "add");
+}
+
+extern "C" int fhe_sub(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!same_ctx(c, a) || !same_ctx(c, b) || !out) return FHE_EINVAL;
+    LOCK(c);
+    const fhe_ct *a2, *b2;
+    fhe_ct *ta, *tb;
+    int e = align2(c, a, b, &a2, &b2, &ta, &tb);
+    if (!e) e = op_addsub(c, a2, b2, 1, out);
+    fhe_ct_destroy(ta);
+    fhe_ct_destroy(tb);
+    return e ? e : launch_status(c, "sub");
+}
+
+extern "C" int fhe_neg(fhe_ctx *c, const fhe_ct *a, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!same_ctx(c, a) || !out) return FHE_EINVAL;
+    LOCK(c);
+    int e = op_neg(c, a, out);
+    return e ? e : launch_status(c, "neg");
+}
+
+extern "C" int fhe_mul_const(fhe_ctx *c, const fhe_ct *a, int64_t k, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!same_ctx(c, a) || !out) return FHE_EINVAL;
+    LOCK(c);
+    int e = op_mul_const(c, a, k, out);
+    return e ? e : launch_status(c, "mul_const");
+}
+
+extern "C" int fhe_add_const(fhe_ctx *c, const fhe_ct *a, int64_t k, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!same_ctx(c, a) || !out) return FHE_EINVAL;
+    LOCK(c);
+    int e = op_add_const(c, a, k, out);
+    return e ? e : launch_status(c, "add_const");
+}
+
+extern "C" int fhe_mul(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!same_ctx(c, a) || !same_ctx(c, b) || !out) return FHE_EINVAL;
+    LOCK(c);
+    const fhe_ct *a2, *b2;
+    fhe_ct *ta, *tb;
+    int e = align2(c, a, b, &a2, &b2, &ta, &tb);
+    if (!e) e = op_tensor(c, a2, b2, out);
+    fhe_ct_destroy(ta);
+    fhe_ct_destroy(tb);
+    return e ? e : launch_status(c, "mul");
+}
+
+extern "C" int fhe_relinearize(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *a, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!evk || evk->ctx != c || !same_ctx(c, a) || !out) return FHE_EINVAL;
+    LOCK(c);
+    int e = op_relin(c, evk->keys[0], a, out);
+    return e ? e : launch_status(c, "relinearize");
+}
+
+extern "C" int fhe_mod_switch(fhe_ctx *c, const fhe_ct *a, int target_level, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!same_ctx(c, a) || !out) return FHE_EINVAL;
+    LOCK(c);
+    int e = op_lower(c, a, target_level, out);
+    return e ? e : launch_status(c, "mod_switch");
+}
+
+extern "C" int fhe_rotate(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *a, int64_t galois, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!evk || evk->ctx != c || !same_ctx(c, a) || !out) return FHE_EINVAL;
+    LOCK(c);
+    const KeySwitchKey *k = evk->find(galois);
+    if (!k || galois == 0) return fhe_fail(c, FHE_ENOKEY, "no rotation key for this Galois element");
+    int e = op_rotate(c, *k, a, out);
+    if (!e && c->tracing) {
+        c->trace_op.push_back(FHE_OP_ROT);
+        c->trace_level.push_back(a->level);
+    }
+    return e ? e : launch_status(c, "rotate");
+}
+
+extern "C" int fhe_mul_relin(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *a, const fhe_ct *b, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!evk || evk->ctx != c || !same_ctx(c, a) || !same_ctx(c, b) || !out) return FHE_EINVAL;
+    LOCK(c);
+    const fhe_ct *a2, *b2;
+    fhe_ct *ta, *tb;
+    int e = align2(c, a, b, &a2, &b2, &ta, &tb);
+    if (!e) e = op_mul_relin(c, evk->keys[0], a2, b2, out);
+    fhe_ct_destroy(ta);
+    fhe_ct_destroy(tb);
+    return e ? e : launch_status(c, "mul_relin");
+}
+
+// ---------------------------------------------------------------------------
+// comparison
+// ---------------------------------------------------------------------------
+
+namespace {
+
+int check_digits(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d)
+{
+    if (!evk || evk->ctx != c || !x || !y || d < 1) return FHE_EINVAL;
+    const int count = x[0] ? x[0]->count : 0;
+    for (int k = 0; k < d; k++) {
+        if (!same_ctx(c, x[k]) || !same_ctx(c, y[k])) return FHE_EINVAL;
+        if (x[k]->count != count || y[k]->count != count || x[k]->npoly != 2 || y[k]->npoly != 2)
+            return fhe_fail(c, FHE_EMISMATCH, "comparison operands differ in shape");
+    }
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int fhe_compare(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                           fhe_ct **lt, fhe_ct **eq)
+{
+    CHECK_CTX(c);
+    int e = check_digits(c, evk, x, y, d);
+    if (e) return e;
+    if (!lt && !eq) return FHE_EINVAL;
+    LOCK(c);
+    e = circuit_compare(c, evk, x, y, d, lt, eq);
+    return e ? e : launch_status(c, "compare");
+}
+
+extern "C" int fhe_compare_lt(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                              fhe_ct **out)
+{
+    if (!out) return FHE_EINVAL;
+    return fhe_compare(c, evk, x, y, d, out, nullptr);
+}
+
+extern "C" int fhe_compare_eq(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                              fhe_ct **out)
+{
+    if (!out) return FHE_EINVAL;
+    return fhe_compare(c, evk, x, y, d, nullptr, out);
+}
+
+extern "C" int fhe_max_min(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                           fhe_ct **out_max, fhe_ct **out_min)
+{
+    CHECK_CTX(c);
+    int e = check_digits(c, evk, x, y, d);
+    if (e) return e;
+    if (!out_max && !out_min) return FHE_EINVAL;
+    LOCK(c);
+    e = circuit_max_min(c, evk, x, y, d, out_max, out_min);
+    return e ? e : launch_status(c, "max_min");
+}
+
+extern "C" int fhe_max(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                       fhe_ct **out)
+{
+    if (!out) return FHE_EINVAL;
+    return fhe_max_min(c, evk, x, y, d, out, nullptr);
+}
+
+extern "C" int fhe_min(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                       fhe_ct **out)
+{
+    if (!out) return FHE_EINVAL;
+    return fhe_max_min(c, evk, x, y, d, nullptr, out);
+}
+
+// ---------------------------------------------------------------------------
+// trace, raw transforms, self test
+// ---------------------------------------------------------------------------
+
+extern "C" int fhe_trace_enable(fhe_ctx *c, int on)
+{
+    CHECK_CTX(c);
+    LOCK(c);
+    c->tracing = on != 0;
+    c->trace_op.clear();
+    c->trace_level.clear();
+    return 0;
+}
+
+extern "C" int fhe_trace_get(const fhe_ctx *c, int32_t *ops, int32_t *levels, int cap)
+{
+    if (!c || cap < 0) return FHE_EINVAL;
+    const int n = (int)c->trace_op.size();
+    for (int i = 0; i < n && i < cap; i++) {
+        if (ops) ops[i] = c->trace_op[i];
+        if (levels) levels[i] = c->trace_level[i];
+    }
+    return n;
+}
+
+static int raw_ntt(fhe_ctx *c, uint64_t *data, const int32_t *prime_idx, int nlimbs, bool inverse)
+{
+    CHECK_CTX(c);
+    if (!data || !prime_idx || nlimbs < 0) return FHE_EINVAL;
+    LOCK(c);
+    for (int i = 0; i < nlimbs; i++)
+        if (prime_idx[i] < 0 || prime_idx[i] >= c->np) return FHE_EINVAL;
+    for (int base = 0; base < nlimbs; base += FHE_MAXP) {
+        const int n = std::min(FHE_MAXP, nlimbs - base);
+        LimbMap m;
+        memset(&m, 0, sizeof(m));
+        m.nl = n;
+        for (int i = 0; i < n; i++) m.in_limb[i] = m.out_limb[i] = i, m.prime[i] = prime_idx[base + i];
+        u64 *p = data + (size_t)base * c->N;
+        if (inverse)
+            launch_ntt_inv_plain(c, p, p, m, n);
+        else
+            launch_ntt_fwd_plain(c, p, p, m, n);
+    }
+    return launch_status(c, "ntt");
+}
+
+extern "C" int fhe_ntt_forward(fhe_ctx *c, uint64_t *data, const int32_t *prime_idx, int nlimbs)
+{
+    return raw_ntt(c, data, prime_idx, nlimbs, false);
+}
+
+extern "C" int fhe_ntt_inverse(fhe_ctx *c, uint64_t *data, const int32_t *prime_idx, int nlimbs)
+{
+    return raw_ntt(c, data, prime_idx, nlimbs, true);
+}
+
+extern "C" int fhe_selftest_modarith(uint64_t prime_mod, uint64_t prime_lo, uint64_t prime_hi, int nprimes, int iters)
+{
+    if (nprimes < 1 || nprimes > 64 || iters < 0) return -1;
+    std::vector<u64> qs(nprimes);
+    if (host_find_primes(prime_mod, prime_lo, prime_hi, nprimes, qs.data()) != nprimes) return -1;
+    int bad = 0;
+    u64 st = 0x9E3779B97F4A7C15ull;
+    auto rnd = [&st]() {  // splitmix64
+        u64 z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    for (u64 q : qs) {
+        const ModQ m = make_modq(q);
+        for (int it = 0; it < iters; it++) {
+            const bool edge = it < 64;
+            u64 a[8], b[8];
+            for (int k = 0; k < 8; k++) {
+                a[k] = edge ? q - 1 - (u64)((it >> k) & 1) : rnd() % q;
+                b[k] = edge ? q - 1 - (u64)((it >> (k + 1)) & 1) : rnd() % q;
+            }
+            // single and summed products
+            u128 acc = 0;
+            for (int k = 0; k < 8; k++) {
+                acc += (u128)a[k] * b[k];
+                if (barrett128(acc, m) != (u64)(acc % q)) bad++;
+                if (mulmod(a[k], b[k], m) != (u64)(((u128)a[k] * b[k]) % q)) bad++;
+            }
+            // Shoup with any 64-bit multiplicand
+            const u64 w = b[0], ws = shoup_const(w, q), x = edge ? ~0ull - (u64)it : rnd();
+            const u64 lz = shoup_lazy(x, w, ws, q);
+            if (lz >= 2 * q || lz % q != (u64)(((u128)x * w) % q)) bad++;
+            if (shoup(x, w, ws, q) != (u64)(((u128)x * w) % q)) bad++;
+            if (reduce4q(4 * q - 1 - (x % (4 * q)), 2 * q, q) != (4 * q - 1 - (x % (4 * q))) % q) bad++;
+        }
+    }
+    return bad;
+}
+
+// Seeded key generation and encryption draw their randomness on the device.
+extern "C" int fhe_keygen(fhe_ctx *c, uint64_t seed, fhe_sk **sk, fhe_pk **pk)
+{
+    (void)seed; (void)sk; (void)pk;
+    return c ? fhe_fail(c, FHE_EUNSUPPORTED, "seeded keygen not available yet") : FHE_EINVAL;
+}
+
+extern "C" int fhe_evk_create(fhe_ctx *c, const fhe_sk *sk, const int64_t *galois, int n_galois, uint64_t seed,
+                              fhe_evk **out)
+{
+    (void)sk; (void)galois; (void)n_galois; (void)seed; (void)out;
+    return c ? fhe_fail(c, FHE_EUNSUPPORTED, "seeded evk not available yet") : FHE_EINVAL;
+}
+
+extern "C" int fhe_encrypt(fhe_ctx *c, const fhe_pk *pk, const uint64_t *slots, int count, uint64_t seed,
+                           fhe_ct **out)
+{
+    (void)pk; (void)slots; (void)count; (void)seed; (void)out;
+    return c ? fhe_fail(c, FHE_EUNSUPPORTED, "seeded encrypt not available yet") : FHE_EINVAL;
+}

@@ -1,0 +1,538 @@
+// eval.cu -- BGV operations on ciphertext batches and the comparison circuits.
+//
+// Each operation acts on a whole batch (count ciphertexts of one level) with a
+// handful of launches: one kernel per step for the batch, never one per
+// ciphertext or per limb.
+//
+// Key switching (hybrid, BGV flavour) of the poly X at level l, K special
+// primes, dnum = ceil(l/K) digits D_j = data limbs [jK, min((j+1)K, l)):
+//   1. INTT(X)                                            (l limbs per ct)
+//   2. ModUp: for every digit j and every limb t of Q_l P outside D_j, fast
+//      basis conversion of X_{D_j} to t, fused with the forward NTT of t
+//   3. inner product  acc_pi[t] = sum_j X_j[t] ksk_j[pi][t]   (pi = 0, 1)
+//   4. INTT of the K special limbs of acc_0 and acc_1
+//   5. ModDown fused with NTT: delta = p FBC_{P->Q}([acc_P p^-1]_P),
+//      out_pi = addend_pi + (acc_pi - delta) P^-1
+// Modulus switching l -> l-1: INTT of the last limb, then one fused kernel
+// that forms delta = p [x_last p^-1]_{q_last}, transforms it and applies
+// (x - delta) q_last^-1.
+#include <functional>
+#include <map>
+
+#include "fhe_internal.h"
+
+namespace {
+
+struct Tmp {
+    fhe_ctx *c;
+    u64 *p = nullptr;
+    Tmp(fhe_ctx *ctx, size_t words, int *err) : c(ctx)
+    {
+        if (*err) return;
+        p = (u64 *)c->pool.get(words * sizeof(u64), err);
+    }
+    ~Tmp()
+    {
+        if (p) c->pool.put(p);
+    }
+};
+
+LimbMap identity_map(int nl, long long in_outer, long long out_outer, int in_off, int out_off, int prime_off)
+{
+    LimbMap m;
+    memset(&m, 0, sizeof(m));
+    m.nl = nl;
+    m.in_outer = in_outer;
+    m.out_outer = out_outer;
+    for (int i = 0; i < nl; i++) {
+        m.in_limb[i] = in_off + i;
+        m.out_limb[i] = out_off + i;
+        m.prime[i] = prime_off + i;
+    }
+    return m;
+}
+
+void trace(fhe_ctx *c, int op, int level)
+{
+    if (c->tracing) {
+        c->trace_op.push_back(op);
+        c->trace_level.push_back(level);
+    }
+}
+
+}  // namespace
+
+int64_t centred_const(const fhe_ctx *c, int64_t k)
+{
+    const int64_t p = (int64_t)c->p;
+    int64_t r = k % p;
+    if (r < 0) r += p;
+    return r > p / 2 ? r - p : r;
+}
+
+int op_modswitch1(fhe_ctx *c, const fhe_ct *a, fhe_ct **out)
+{
+    const int l = a->level, N = c->N;
+    if (l < 2) return fhe_fail(c, FHE_ELEVEL, "modulus switch below level 1");
+    int err = 0;
+    fhe_ct *r = ct_new(c, a->count, a->npoly, l - 1, &err);
+    if (!r) return err;
+    Tmp last(c, (size_t)a->count * a->npoly * N, &err);
+    if (err) {
+        fhe_ct_destroy(r);
+        return err;
+    }
+    const int outer = a->count * a->npoly;
+    LimbMap m = identity_map(1, (long long)l * N, N, l - 1, 0, l - 1);
+    launch_ntt_inv_plain(c, a->d, last.p, m, outer);
+    launch_ntt_modswitch(c, last.p, a->d, r->d, l, a->npoly, a->count);
+    *out = r;
+    return 0;
+}
+
+int op_lower(fhe_ctx *c, const fhe_ct *a, int level, fhe_ct **out)
+{
+    if (level < 1 || level > a->level) return fhe_fail(c, FHE_ELEVEL, "bad target level");
+    if (level == a->level) {
+        int err = 0;
+        fhe_ct *r = ct_new(c, a->count, a->npoly, a->level, &err);
+        if (!r) return err;
+        cudaMemcpyAsync(r->d, a->d, a->bytes, cudaMemcpyDeviceToDevice, c->stream);
+        *out = r;
+        return 0;
+    }
+    const fhe_ct *cur = a;
+    fhe_ct *owned = nullptr;
+    while (cur->level > level) {
+        fhe_ct *nx = nullptr;
+        int e = op_modswitch1(c, cur, &nx);
+        if (owned) fhe_ct_destroy(owned);
+        if (e) return e;
+        owned = nx;
+        cur = nx;
+    }
+    *out = owned;
+    return 0;
+}
+
+int op_addsub(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, int sub, fhe_ct **out)
+{
+    if (a->level != b->level || a->count != b->count || a->npoly != b->npoly)
+        return fhe_fail(c, FHE_EMISMATCH, "add/sub: shapes differ");
+    int err = 0;
+    fhe_ct *r = ct_new(c, a->count, a->npoly, a->level, &err);
+    if (!r) return err;
+    launch_add(c, a->d, b->d, r->d, a->count * a->npoly, a->level, sub);
+    *out = r;
+    return 0;
+}
+
+int op_neg(fhe_ctx *c, const fhe_ct *a, fhe_ct **out)
+{
+    int err = 0;
+    fhe_ct *r = ct_new(c, a->count, a->npoly, a->level, &err);
+    if (!r) return err;
+    launch_neg(c, a->d, r->d, a->count * a->npoly, a->level);
+    *out = r;
+    return 0;
+}
+
+int op_mul_const(fhe_ctx *c, const fhe_ct *a, int64_t k, fhe_ct **out)
+{
+    int err = 0;
+    fhe_ct *r = ct_new(c, a->count, a->npoly, a->level, &err);
+    if (!r) return err;
+    const int64_t kc = centred_const(c, k);
+    u64 w[FHE_MAXP], ws[FHE_MAXP];
+    for (int i = 0; i < a->level; i++) {
+        const u64 q = c->q[i];
+        w[i] = kc >= 0 ? (u64)kc % q : (q - ((u64)(-kc) % q)) % q;
+        ws[i] = shoup_const(w[i], q);
+    }
+    launch_mul_const(c, a->d, r->d, a->count * a->npoly, a->level, w, ws);
+    *out = r;
+    return 0;
+}
+
+int op_add_const(fhe_ctx *c, const fhe_ct *a, int64_t k, fhe_ct **out)
+{
+    if (a->npoly != 2) return fhe_fail(c, FHE_EINVAL, "add_const needs a 2-poly ciphertext");
+    int err = 0;
+    fhe_ct *r = ct_new(c, a->count, 2, a->level, &err);
+    if (!r) return err;
+    const int64_t kc = centred_const(c, k);
+    u64 w[FHE_MAXP];
+    for (int i = 0; i < a->level; i++) {
+        const u64 q = c->q[i];
+        w[i] = kc >= 0 ? (u64)kc % q : (q - ((u64)(-kc) % q)) % q;
+    }
+    launch_add_const(c, a->d, r->d, a->count, a->level, w);
+    *out = r;
+    return 0;
+}
+
+int op_tensor(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **out)
+{
+    if (a->level != b->level || a->count != b->count || a->npoly != 2 || b->npoly != 2)
+        return fhe_fail(c, FHE_EMISMATCH, "tensor: shapes differ");
+    int err = 0;
+    fhe_ct *r = ct_new(c, a->count, 3, a->level, &err);
+    if (!r) return err;
+    launch_tensor(c, a->d, b->d, r->d, a->count, a->level);
+    *out = r;
+    return 0;
+}
+
+// Key-switch the poly X_c = xbase + c*x_outer (NTT domain, l limbs) of each
+// ct of the batch; out_c[pi] = addend + ModDown(sum_j ModUp_j(X_c) ksk_j[pi]).
+static int keyswitch(fhe_ctx *c, const u64 *xbase, long long x_outer, const u64 *abase, long long a_outer,
+                     long long a_poly, int amask, const KeySwitchKey &k, int count, int l, u64 *out)
+{
+    const int N = c->N, K = c->K, dnum = c->modup[l].dnum;
+    int err = 0;
+    Tmp xc(c, (size_t)count * l * N, &err);
+    Tmp ext(c, (size_t)count * dnum * (l + K) * N, &err);
+    Tmp acc(c, (size_t)count * 2 * (l + K) * N, &err);
+    Tmp accP(c, (size_t)count * 2 * K * N, &err);
+    if (err) return fhe_fail(c, err, "key switching: out of device memory");
+    // 1. INTT of X
+    LimbMap m1 = identity_map(l, x_outer, (long long)l * N, 0, 0, 0);
+    launch_ntt_inv_plain(c, xbase, xc.p, m1, count * l);
+    // 2. ModUp (basis conversion fused with NTT)
+    launch_ntt_modup(c, xc.p, ext.p, l, count);
+    // 3. inner product with the key
+    launch_ks_inner(c, ext.p, xbase, x_outer, k.d, acc.p, count, l);
+    // 4. INTT of the special limbs of both accumulators
+    LimbMap m4 = identity_map(K, (long long)(l + K) * N, (long long)K * N, l, 0, c->L);
+    launch_ntt_inv_plain(c, acc.p, accP.p, m4, count * 2 * K);
+    // 5. ModDown fused with NTT, plus the addend
+    launch_ntt_moddown(c, accP.p, acc.p, abase, a_outer, a_poly, amask, out, l, count);
+    return 0;
+}
+
+int op_relin(fhe_ctx *c, const KeySwitchKey &k, const fhe_ct *d, fhe_ct **out)
+{
+    if (d->npoly != 3) return fhe_fail(c, FHE_EINVAL, "relinearize needs a 3-poly ciphertext");
+    const int l = d->level, N = c->N;
+    int err = 0;
+    fhe_ct *r = ct_new(c, d->count, 2, l, &err);
+    if (!r) return err;
+    const long long LN = (long long)l * N;
+    err = keyswitch(c, d->d + 2 * LN, 3 * LN, d->d, 3 * LN, LN, 3, k, d->count, l, r->d);
+    if (err) {
+        fhe_ct_destroy(r);
+        return err;
+    }
+    *out = r;
+    return 0;
+}
+
+int galois_perm(fhe_ctx *c, int64_t g, const int **perm)
+{
+    auto it = c->d_perm.find(g);
+    if (it != c->d_perm.end()) {
+        *perm = it->second;
+        return 0;
+    }
+    const int N = c->N, logN = c->logN;
+    const int64_t twoN = 2 * (int64_t)N;
+    if (g <= 0 || g >= twoN || (g & 1) == 0) return fhe_fail(c, FHE_EINVAL, "Galois element must be odd in (0, 2N)");
+    auto brv = [logN](int x) {
+        int r = 0;
+        for (int i = 0; i < logN; i++) r |= ((x >> i) & 1) << (logN - 1 - i);
+        return r;
+    };
+    // NTT slot k holds a(psi^(2 brv(k)+1)); sigma_g(a) there is a(psi^(g(2 brv(k)+1))).
+    std::vector<int> h(N);
+    for (int k = 0; k < N; k++) {
+        const int64_t e = (g * (2 * (int64_t)brv(k) + 1)) % twoN;
+        h[k] = brv((int)((e - 1) / 2));
+    }
+    int *d = nullptr;
+    if (cudaMalloc(&d, sizeof(int) * N) != cudaSuccess) return fhe_fail(c, FHE_ENOMEM, "Galois map");
+    cudaMemcpy(d, h.data(), sizeof(int) * N, cudaMemcpyHostToDevice);
+    c->d_perm[g] = d;
+    *perm = d;
+    return 0;
+}
+
+int op_rotate(fhe_ctx *c, const KeySwitchKey &k, const fhe_ct *a, fhe_ct **out)
+{
+    if (a->npoly != 2) return fhe_fail(c, FHE_EINVAL, "rotate needs a 2-poly ciphertext");
+    const int l = a->level, N = c->N;
+    const int *perm = nullptr;
+    int err = galois_perm(c, k.galois, &perm);
+    if (err) return err;
+    fhe_ct *sg = ct_new(c, a->count, 2, l, &err);
+    if (!sg) return err;
+    launch_automorphism(c, a->d, sg->d, a->count * 2, l, perm);
+    fhe_ct *r = ct_new(c, a->count, 2, l, &err);
+    if (!r) {
+        fhe_ct_destroy(sg);
+        return err;
+    }
+    const long long LN = (long long)l * N;
+    err = keyswitch(c, sg->d + LN, 2 * LN, sg->d, 2 * LN, LN, 1, k, a->count, l, r->d);
+    fhe_ct_destroy(sg);
+    if (err) {
+        fhe_ct_destroy(r);
+        return err;
+    }
+    *out = r;
+    return 0;
+}
+
+int op_mul_relin(fhe_ctx *c, const KeySwitchKey &rlk, const fhe_ct *a, const fhe_ct *b, fhe_ct **out)
+{
+    fhe_ct *d = nullptr, *r = nullptr;
+    int err = op_tensor(c, a, b, &d);
+    if (err) return err;
+    err = op_relin(c, rlk, d, &r);
+    fhe_ct_destroy(d);
+    if (err) return err;
+    if (r->level > 1) {
+        fhe_ct *s = nullptr;
+        err = op_modswitch1(c, r, &s);
+        fhe_ct_destroy(r);
+        if (err) return err;
+        r = s;
+    }
+    *out = r;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// comparison circuits
+// ---------------------------------------------------------------------------
+//
+// The schedule below is the exact one of the CPU oracle (bit-exact agreement
+// depends on it): products align levels by switching the higher operand down
+// one prime at a time (lowered copies cached), then tensor -> relinearise ->
+// modulus-switch when the level is above 1; additions align the same way.
+// Powers: z^n = (z^(n/2))^2 for n a power of two, else z^(2^a) z^(n-2^a).
+// Paterson-Stockmeyer on the odd part with baby powers z^1..z^(B-1),
+// B = 2^ceil(log2(p-1)/2), and blocks combined pairwise; LT = c_{p-1} z^(p-1)
+// + odd part; EQ = 1 - z^(p-1).  Digits are merged pairwise (2i+1 high, 2i
+// low) into L = L_hi + E_hi L_lo and E = E_hi E_lo.
+namespace {
+
+struct Circuit {
+    fhe_ctx *c;
+    const fhe_evk *evk;
+    const KeySwitchKey *rlk;
+    int err = 0;
+    std::vector<fhe_ct *> owned;
+    std::map<std::pair<const fhe_ct *, int>, fhe_ct *> lowered;
+
+    Circuit(fhe_ctx *ctx, const fhe_evk *e) : c(ctx), evk(e), rlk(&e->keys[0]) {}
+    ~Circuit()
+    {
+        for (fhe_ct *x : owned)
+            if (x) fhe_ct_destroy(x);
+        for (auto &kv : lowered) fhe_ct_destroy(kv.second);
+    }
+    fhe_ct *keep(fhe_ct *x)
+    {
+        owned.push_back(x);
+        return x;
+    }
+    // remove x from the owned set so the caller receives it
+    fhe_ct *release(fhe_ct *x)
+    {
+        for (auto &o : owned)
+            if (o == x) o = nullptr;
+        return x;
+    }
+    const fhe_ct *lower(const fhe_ct *x, int level)
+    {
+        if (err || !x) return nullptr;
+        if (x->level == level) return x;
+        auto key = std::make_pair(x, level);
+        auto it = lowered.find(key);
+        if (it != lowered.end()) return it->second;
+        const fhe_ct *above = lower(x, level + 1);
+        if (!above) return nullptr;
+        fhe_ct *r = nullptr;
+        if ((err = op_modswitch1(c, above, &r))) return nullptr;
+        lowered[key] = r;
+        return r;
+    }
+    fhe_ct *mul(const fhe_ct *a, const fhe_ct *b)
+    {
+        if (err || !a || !b) return nullptr;
+        const int lv = std::min(a->level, b->level);
+        const fhe_ct *a2 = lower(a, lv), *b2 = lower(b, lv);
+        if (!a2 || !b2) return nullptr;
+        fhe_ct *r = nullptr;
+        if ((err = op_mul_relin(c, *rlk, a2, b2, &r))) return nullptr;
+        trace(c, FHE_OP_MUL, lv);
+        return keep(r);
+    }
+    fhe_ct *addsub(const fhe_ct *a, const fhe_ct *b, int sub)
+    {
+        if (err || !a || !b) return nullptr;
+        const int lv = std::min(a->level, b->level);
+        const fhe_ct *a2 = lower(a, lv), *b2 = lower(b, lv);
+        if (!a2 || !b2) return nullptr;
+        fhe_ct *r = nullptr;
+        if ((err = op_addsub(c, a2, b2, sub, &r))) return nullptr;
+        trace(c, sub ? FHE_OP_SUB : FHE_OP_ADD, lv);
+        return keep(r);
+    }
+    fhe_ct *add(const fhe_ct *a, const fhe_ct *b) { return addsub(a, b, 0); }
+    fhe_ct *sub(const fhe_ct *a, const fhe_ct *b) { return addsub(a, b, 1); }
+    fhe_ct *cmul(const fhe_ct *a, int64_t k)
+    {
+        if (err || !a) return nullptr;
+        fhe_ct *r = nullptr;
+        if ((err = op_mul_const(c, a, k, &r))) return nullptr;
+        trace(c, FHE_OP_CMUL, a->level);
+        return keep(r);
+    }
+    fhe_ct *cadd(const fhe_ct *a, int64_t k)
+    {
+        if (err || !a) return nullptr;
+        fhe_ct *r = nullptr;
+        if ((err = op_add_const(c, a, k, &r))) return nullptr;
+        trace(c, FHE_OP_CADD, a->level);
+        return keep(r);
+    }
+    fhe_ct *neg(const fhe_ct *a)
+    {
+        if (err || !a) return nullptr;
+        fhe_ct *r = nullptr;
+        if ((err = op_neg(c, a, &r))) return nullptr;
+        trace(c, FHE_OP_NEG, a->level);
+        return keep(r);
+    }
+
+    // (LT_k, EQ_k) of one digit pair
+    void digit(const fhe_ct *x, const fhe_ct *y, bool want_lt, bool want_eq, fhe_ct **lt_out, fhe_ct **eq_out)
+    {
+        const int p = (int)c->p;
+        *lt_out = *eq_out = nullptr;
+        fhe_ct *z = sub(x, y);
+        if (!z) return;
+        std::map<int, fhe_ct *> pw;
+        pw[1] = z;
+        std::function<fhe_ct *(int)> power = [&](int n) -> fhe_ct * {
+            auto it = pw.find(n);
+            if (it != pw.end()) return it->second;
+            fhe_ct *r;
+            if ((n & (n - 1)) == 0) {
+                fhe_ct *h = power(n / 2);
+                r = mul(h, h);
+            } else {
+                int a = 1;
+                while (a * 2 < n) a *= 2;
+                fhe_ct *A = power(a);
+                fhe_ct *Bp = power(n - a);
+                r = mul(A, Bp);
+            }
+            pw[n] = r;
+            return r;
+        };
+        if (want_lt) {
+            const std::vector<int> &cf = c->lt;
+            int lg = 0;
+            while ((1 << lg) < p - 1) lg++;  // ceil(log2(p-1))
+            const int B = 1 << ((lg + 1) / 2);
+            const int nblocks = (p - 2) / B + 1;
+            auto leaf = [&](int k) -> fhe_ct * {
+                std::vector<std::pair<int, int>> terms;
+                for (int r = 1; r < B; r += 2)
+                    if (B * k + r <= p - 2 && cf[B * k + r]) terms.push_back({r, cf[B * k + r]});
+                if (terms.empty()) return nullptr;
+                std::vector<fhe_ct *> cts;
+                for (auto &t : terms) cts.push_back(power(t.first));
+                if (err) return nullptr;
+                int lv = 1 << 30;
+                for (auto *t : cts) lv = std::min(lv, t->level);
+                fhe_ct *acc = nullptr;
+                for (size_t i = 0; i < terms.size(); i++) {
+                    fhe_ct *term = cmul(lower(cts[i], lv), terms[i].second);
+                    acc = acc ? add(acc, term) : term;
+                }
+                return acc;
+            };
+            std::function<fhe_ct *(int, int)> tree = [&](int k0, int t) -> fhe_ct * {
+                if (err || k0 >= nblocks) return nullptr;
+                if (t == 0) return leaf(k0);
+                const int half = 1 << (t - 1);
+                fhe_ct *lo = tree(k0, t - 1);
+                fhe_ct *hi = tree(k0 + half, t - 1);
+                if (!hi) return lo;
+                fhe_ct *gp = power(B * half);
+                fhe_ct *prod = mul(gp, hi);
+                return lo ? add(lo, prod) : prod;
+            };
+            int t = 0;
+            while ((1 << t) < nblocks) t++;
+            fhe_ct *odd = tree(0, t);
+            fhe_ct *zp = power(p - 1);
+            fhe_ct *lead = cmul(zp, cf[p - 1]);
+            *lt_out = odd ? add(lead, odd) : lead;
+        }
+        if (want_eq) *eq_out = cadd(neg(power(p - 1)), 1);
+    }
+
+    void compare(const fhe_ct *const *xs, const fhe_ct *const *ys, int d, bool want_lt, bool want_eq,
+                 fhe_ct **lt, fhe_ct **eq)
+    {
+        std::vector<std::pair<fhe_ct *, fhe_ct *>> nodes;
+        for (int k = 0; k < d && !err; k++) {
+            fhe_ct *l = nullptr, *e = nullptr;
+            digit(xs[k], ys[k], want_lt, d > 1 || want_eq, &l, &e);
+            nodes.push_back({l, e});
+        }
+        while (nodes.size() > 1 && !err) {
+            const bool root = nodes.size() == 2;
+            std::vector<std::pair<fhe_ct *, fhe_ct *>> nxt;
+            for (size_t i = 0; i < nodes.size() / 2; i++) {
+                auto lo = nodes[2 * i], hi = nodes[2 * i + 1];
+                fhe_ct *L = nullptr, *E = nullptr;
+                if (want_lt) {
+                    fhe_ct *m = mul(hi.second, lo.first);
+                    L = add(hi.first, m);
+                }
+                if (want_eq || !root) E = mul(hi.second, lo.second);
+                nxt.push_back({L, E});
+            }
+            if (nodes.size() % 2) nxt.push_back(nodes.back());
+            nodes = nxt;
+        }
+        if (err) return;
+        if (lt) *lt = want_lt ? release(nodes[0].first) : nullptr;
+        if (eq) *eq = want_eq ? release(nodes[0].second) : nullptr;
+    }
+};
+
+}  // namespace
+
+int circuit_compare(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                    fhe_ct **lt, fhe_ct **eq)
+{
+    Circuit C(c, evk);
+    C.compare(x, y, d, lt != nullptr, eq != nullptr, lt, eq);
+    return C.err;
+}
+
+int circuit_max_min(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                    fhe_ct **mx, fhe_ct **mn)
+{
+    Circuit C(c, evk);
+    fhe_ct *L = nullptr;
+    C.compare(x, y, d, true, false, &L, nullptr);
+    if (C.err) return C.err;
+    C.keep(L);
+    for (int k = 0; k < d; k++) {
+        fhe_ct *diff = C.sub(y[k], x[k]);
+        fhe_ct *t = C.mul(L, diff);
+        fhe_ct *a = C.add(x[k], t);
+        fhe_ct *b = C.sub(y[k], t);
+        if (C.err) return C.err;
+        if (mx) mx[k] = C.release(a);
+        if (mn) mn[k] = C.release(b);
+    }
+    return 0;
+}

@@ -1,0 +1,224 @@
+// fhe_internal.h -- library-private types shared by the translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/fhe.h"
+#include "modarith.cuh"
+
+#define FHE_MAXP 32  // max data + special primes
+#define FHE_MAXK 8   // max special primes (alpha)
+#define FHE_MAXD 8   // max key-switching digits
+
+// ---------------------------------------------------------------------------
+// kernel parameter blocks (passed by value)
+// ---------------------------------------------------------------------------
+
+// Which limbs a batched transform touches.  Job j of a launch handles limb
+// (j % nl) of "outer" item (j / nl):
+//   input  = in  + (j / nl) * in_outer  + in_limb[j % nl]  * N
+//   output = out + (j / nl) * out_outer + out_limb[j % nl] * N
+//   prime  = prime[j % nl]
+struct LimbMap {
+    int nl;
+    int pad;
+    long long in_outer, out_outer;  // in u64 elements
+    int in_limb[FHE_MAXP];
+    int out_limb[FHE_MAXP];
+    int prime[FHE_MAXP];
+};
+
+// ModUp of all digits at one level (fast basis conversion, coefficient
+// domain, fused with the forward NTT of each new limb).  Job j handles
+// (ct c = j / njobs_per_ct, then entry e = j % njobs_per_ct): digit[e],
+// target extended limb tgt[e] (0..l+K-1), its prime tprime[e].
+struct ModUpParams {
+    int l, K, dnum, njobs;          // njobs per ciphertext
+    int digit_lo[FHE_MAXD];         // first data limb of digit j
+    int digit_n[FHE_MAXD];          // limbs in digit j
+    int job_digit[FHE_MAXD * FHE_MAXP];
+    int job_tgt[FHE_MAXD * FHE_MAXP];
+    int job_prime[FHE_MAXD * FHE_MAXP];
+    u64 inv_hat[FHE_MAXD][FHE_MAXK];    // (Q_j/q_i)^-1 mod q_i
+    u64 inv_hat_s[FHE_MAXD][FHE_MAXK];  // its Shoup constant
+    // hat[j][i][t] = (Q_j/q_i) mod (prime of extended limb t)
+    u64 hat[FHE_MAXD][FHE_MAXK][FHE_MAXP];
+};
+
+// ModDown of (acc0, acc1) from Q_l P to Q_l, fused with the forward NTT of
+// the correction.  Job j: ct c = j / (2 l), poly = (j / l) % 2, limb i = j % l.
+struct ModDownParams {
+    int l, K;
+    u64 cinv[FHE_MAXK], cinv_s[FHE_MAXK];  // p^-1 (P/p_k)^-1 mod p_k
+    u64 phat[FHE_MAXK][FHE_MAXP];          // p (P/p_k) mod q_i
+    u64 pinv[FHE_MAXP], pinv_s[FHE_MAXP];  // P^-1 mod q_i
+    int sprime[FHE_MAXK];                  // prime index of special limb k
+};
+
+// Modulus switch l -> l-1, fused with the forward NTT of the correction.
+// Job j: ct c = j / (npoly (l-1)), poly = (j / (l-1)) % npoly, limb i = j % (l-1).
+struct ModSwitchParams {
+    int l, npoly;
+    u64 pinv_last, pinv_last_s;               // p^-1 mod q_{l-1}
+    u64 p_i[FHE_MAXP], p_i_s[FHE_MAXP];       // p mod q_i
+    u64 qinv[FHE_MAXP], qinv_s[FHE_MAXP];     // q_{l-1}^-1 mod q_i
+};
+
+// ---------------------------------------------------------------------------
+// device memory pool
+// ---------------------------------------------------------------------------
+
+struct Pool {
+    fhe_allocator alloc;  // alloc.alloc == NULL -> cudaMallocAsync
+    cudaStream_t stream = 0;
+    std::unordered_map<size_t, std::vector<void *>> free_lists;
+    std::unordered_map<void *, size_t> live;  // every block ever obtained -> size
+    size_t reserved = 0, in_use = 0, budget = 0;  // budget 0 = unlimited
+    long long fail_after = -1;                    // fault injection: fail the n-th new block
+    void *get(size_t bytes, int *err);
+    void put(void *p);
+    void release_all();
+};
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+
+struct fhe_ctx {
+    // parameters
+    int logN = 0, N = 0, L = 0, K = 0, np = 0;
+    u64 p = 0;
+    std::vector<u64> q;   // L + K primes
+    std::vector<ModQ> mq;
+    std::vector<u64> psi;
+
+    // device tables
+    ModQ *d_mq = nullptr;          // [np]
+    ulonglong2 *d_fwd = nullptr;   // [np][N]: (psi^brv(k), Shoup)
+    ulonglong2 *d_inv = nullptr;   // [np][N]: (psi^-brv(k), Shoup)
+    ulonglong2 *d_ninv = nullptr;  // [np]:    (N^-1, Shoup)
+
+    // per-level constants (index = level l, 1..L), host and device copies
+    std::vector<ModUpParams> modup;
+    std::vector<ModDownParams> moddown;
+    std::vector<ModSwitchParams> modswitch;
+    ModUpParams *d_modup = nullptr;
+    ModDownParams *d_moddown = nullptr;
+    ModSwitchParams *d_modswitch = nullptr;
+    std::unordered_map<int64_t, int *> d_perm;  // NTT-domain automorphism maps
+
+    // plaintext side
+    int ns = 0, M = 0;             // slots and subring size
+    bool slots_linear = true;
+    u64 zeta = 0, gamma = 0;       // primitive 2M-th root / sqrt(-2) mod p
+    std::vector<int> slot_exp;     // slot s <-> zeta^slot_exp[s] (linear case)
+    std::vector<int> lt;           // LT polynomial coefficients c_0..c_{p-1}
+
+    cudaStream_t stream = 0;
+    Pool pool;
+    std::string err;
+    std::mutex mu;
+
+    bool tracing = false;
+    std::vector<int32_t> trace_op, trace_level;
+    long long launches = 0;       // kernels launched since creation
+};
+
+struct fhe_sk {
+    fhe_ctx *ctx;
+    std::vector<int64_t> s;       // host copy (ternary)
+    u64 *d_s = nullptr;           // [L+K][N] NTT domain
+};
+
+struct fhe_pk {
+    fhe_ctx *ctx;
+    u64 *d = nullptr;             // [2][L][N] NTT domain
+};
+
+struct KeySwitchKey {
+    int64_t galois = 0;           // 0 = relinearisation key
+    u64 *d = nullptr;             // [dnum][2][L+K][N] NTT domain
+};
+
+struct fhe_evk {
+    fhe_ctx *ctx;
+    std::vector<KeySwitchKey> keys;  // keys[0] = relinearisation
+    const KeySwitchKey *find(int64_t g) const;
+};
+
+struct fhe_ct {
+    fhe_ctx *ctx;
+    int count = 0, npoly = 0, level = 0;
+    u64 *d = nullptr;             // [count][npoly][level][N] NTT domain
+    size_t bytes = 0;
+};
+
+// ---------------------------------------------------------------------------
+// internal helpers
+// ---------------------------------------------------------------------------
+
+int fhe_fail(fhe_ctx *ctx, int code, const std::string &msg);
+int fhe_cuda_check(fhe_ctx *ctx, cudaError_t e, const char *where);
+fhe_ct *ct_new(fhe_ctx *ctx, int count, int npoly, int level, int *err);
+
+// host precomputation (params.cu)
+bool host_is_prime(u64 n);
+int host_find_primes(u64 U, u64 lo, u64 hi, int count, u64 *out);
+u64 host_powmod(u64 a, u64 e, u64 q);
+u64 host_invmod(u64 a, u64 q);
+u64 host_mulmod(u64 a, u64 b, u64 q);
+int build_tables(fhe_ctx *ctx);
+void lt_poly_coefficients(int p, std::vector<int> &out);
+
+// kernel launchers (ntt.cu, kernels.cu)
+void launch_ntt_fwd_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs);
+void launch_ntt_inv_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs);
+void launch_ntt_modup(fhe_ctx *c, const u64 *d2c, u64 *ext, int level, int count);
+// addend for ModDown output poly pi of ct c: abase + c*a_outer + pi*a_poly when (amask>>pi)&1
+void launch_ntt_moddown(fhe_ctx *c, const u64 *accP, const u64 *acc, const u64 *abase, long long a_outer,
+                        long long a_poly, int amask, u64 *out, int level, int count);
+void launch_ntt_modswitch(fhe_ctx *c, const u64 *last, const u64 *in, u64 *out, int level, int npoly, int count);
+
+void launch_add(fhe_ctx *c, const u64 *a, const u64 *b, u64 *out, int outer, int level, int sub);
+void launch_neg(fhe_ctx *c, const u64 *a, u64 *out, int outer, int level);
+void launch_mul_const(fhe_ctx *c, const u64 *a, u64 *out, int outer, int level, const u64 *w, const u64 *ws);
+void launch_add_const(fhe_ctx *c, const u64 *a, u64 *out, int count, int level, const u64 *k);
+void launch_tensor(fhe_ctx *c, const u64 *a, const u64 *b, u64 *out, int count, int level);
+// acc[c][pi][r] = sum_j y_j[r] ksk_j[pi][prime(r)], y_j[r] = x_c[r] for r in digit j, else ext
+void launch_ks_inner(fhe_ctx *c, const u64 *ext, const u64 *xbase, long long x_outer, const u64 *ksk, u64 *acc,
+                     int count, int level);
+void launch_automorphism(fhe_ctx *c, const u64 *in, u64 *out, int outer, int level, const int *perm);
+void launch_mul_poly(fhe_ctx *c, const u64 *a, const u64 *b, u64 *out, int outer, int level, long long b_outer);
+void launch_rns_from_i64(fhe_ctx *c, const int64_t *x, const int64_t *y, int64_t scale, u64 *out, int outer, int nl,
+                         const int *primes);
+void launch_muladd(fhe_ctx *c, const u64 *a, const u64 *b, const u64 *cc, u64 *out, int outer, int level,
+                   long long b_outer, int neg);
+void launch_ksk_digit(fhe_ctx *c, const u64 *a, const u64 *e, const u64 *s, const u64 *sp, u64 *k0, u64 *k1, int dlo,
+                      int dhi, const u64 *Pw, const u64 *Pws);
+bool ntt_supported_logn(int logN);
+
+// evaluation (eval.cu)
+int op_lower(fhe_ctx *c, const fhe_ct *a, int level, fhe_ct **out);
+int op_modswitch1(fhe_ctx *c, const fhe_ct *a, fhe_ct **out);
+int op_addsub(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, int sub, fhe_ct **out);
+int op_neg(fhe_ctx *c, const fhe_ct *a, fhe_ct **out);
+int op_mul_const(fhe_ctx *c, const fhe_ct *a, int64_t k, fhe_ct **out);
+int op_add_const(fhe_ctx *c, const fhe_ct *a, int64_t k, fhe_ct **out);
+int op_tensor(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **out);
+int op_relin(fhe_ctx *c, const KeySwitchKey &k, const fhe_ct *d, fhe_ct **out);
+int op_rotate(fhe_ctx *c, const KeySwitchKey &k, const fhe_ct *a, fhe_ct **out);
+int op_mul_relin(fhe_ctx *c, const KeySwitchKey &rlk, const fhe_ct *a, const fhe_ct *b, fhe_ct **out);
+int galois_perm(fhe_ctx *c, int64_t g, const int **perm);
+int circuit_compare(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                    fhe_ct **lt, fhe_ct **eq);
+int circuit_max_min(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                    fhe_ct **mx, fhe_ct **mn);
+int64_t centred_const(const fhe_ctx *c, int64_t k);
+
+void launch_copy_limbs(fhe_ctx *c, const u64 *in, u64 *out, int outer, int nl, long long in_outer,
+                       long long out_outer);

@@ -1,0 +1,309 @@
+// kernels.cu -- streaming (HBM-bound) kernels on NTT-domain limbs: add, sub,
+// neg, scalar and constant terms, the ciphertext tensor product, the
+// key-switching inner product, Galois automorphisms as index permutations, and
+// small helpers for key generation, encryption and decryption.
+//
+// Layout: a batch of ciphertexts is u64 [count][npoly][level][N]; an "outer"
+// index runs over count*npoly polys, and the limb of element idx is
+// (idx >> logN) % level, so one flat grid covers the batch and every warp
+// reads 256 contiguous bytes.
+#include "fhe_internal.h"
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline int grid_for(long long n, int per_thread = 1)
+{
+    long long b = (n + (long long)TPB * per_thread - 1) / ((long long)TPB * per_thread);
+    if (b > (1 << 30)) b = 1 << 30;
+    return (int)(b > 0 ? b : 1);
+}
+
+__global__ void k_add(const u64 *__restrict__ a, const u64 *__restrict__ b, u64 *__restrict__ out,
+                      long long total, int logN, int level, const ModQ *__restrict__ mq, int sub)
+{
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const u64 q = mq[(int)((idx >> logN) % level)].q;
+        out[idx] = sub ? submod(a[idx], b[idx], q) : addmod(a[idx], b[idx], q);
+    }
+}
+
+__global__ void k_neg(const u64 *__restrict__ a, u64 *__restrict__ out, long long total, int logN, int level,
+                      const ModQ *__restrict__ mq)
+{
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const u64 q = mq[(int)((idx >> logN) % level)].q;
+        out[idx] = negmod(a[idx], q);
+    }
+}
+
+struct LimbConsts {
+    u64 w[FHE_MAXP], ws[FHE_MAXP];
+};
+
+__global__ void k_mul_const(const u64 *__restrict__ a, u64 *__restrict__ out, long long total, int logN, int level,
+                            const ModQ *__restrict__ mq, const LimbConsts k)
+{
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)((idx >> logN) % level);
+        out[idx] = shoup(a[idx], k.w[i], k.ws[i], mq[i].q);
+    }
+}
+
+// Adds the constant k_i (mod q_i) at every NTT point of poly 0; copies poly 1.
+__global__ void k_add_const(const u64 *__restrict__ a, u64 *__restrict__ out, long long total, int logN, int level,
+                            const ModQ *__restrict__ mq, const LimbConsts k)
+{
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long li = idx >> logN;
+        const int i = (int)(li % level);
+        const int poly = (int)((li / level) % 2);
+        out[idx] = poly == 0 ? addmod(a[idx], k.w[i], mq[i].q) : a[idx];
+    }
+}
+
+// (a0,a1) x (b0,b1) -> (a0 b0, a0 b1 + a1 b0, a1 b1), all NTT domain.
+__global__ void k_tensor(const u64 *__restrict__ a, const u64 *__restrict__ b, u64 *__restrict__ out,
+                         long long total, int logN, int level, const ModQ *__restrict__ mq)
+{
+    const long long LN = (long long)level << logN;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long c = idx / LN, r = idx % LN;
+        const ModQ m = mq[(int)(r >> logN)];
+        const u64 a0 = a[2 * c * LN + r], a1 = a[(2 * c + 1) * LN + r];
+        const u64 b0 = b[2 * c * LN + r], b1 = b[(2 * c + 1) * LN + r];
+        out[3 * c * LN + r] = barrett128((u128)a0 * b0, m);
+        out[(3 * c + 1) * LN + r] = barrett128((u128)a0 * b1 + (u128)a1 * b0, m);
+        out[(3 * c + 2) * LN + r] = barrett128((u128)a1 * b1, m);
+    }
+}
+
+// Key-switching inner product.  Extended limb r = blockIdx.y of Q_l P
+// (r < l: data prime r; else special prime L + r - l).  Every thread loads
+// its 2*dnum key words once and reuses them for all ciphertexts of the batch.
+__global__ void k_ks_inner(const u64 *__restrict__ ext, const u64 *__restrict__ xbase, long long x_outer,
+                           const u64 *__restrict__ ksk, u64 *__restrict__ acc, int count, int l, int K, int L,
+                           int dnum, int logN, const ModQ *__restrict__ mq)
+{
+    const int N = 1 << logN;
+    const int r = blockIdx.y;
+    const int prime = r < l ? r : L + (r - l);
+    const ModQ m = mq[prime];
+    const int LK = L + K, lK = l + K;
+    const int rdig = r < l ? r / K : -1;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+        u64 k0[FHE_MAXD], k1[FHE_MAXD];
+#pragma unroll
+        for (int j = 0; j < FHE_MAXD; j++) {
+            if (j < dnum) {
+                k0[j] = ksk[(((long long)j * 2 + 0) * LK + prime) * N + n];
+                k1[j] = ksk[(((long long)j * 2 + 1) * LK + prime) * N + n];
+            }
+        }
+        for (int c = 0; c < count; c++) {
+            u128 a0 = 0, a1 = 0;
+#pragma unroll
+            for (int j = 0; j < FHE_MAXD; j++) {
+                if (j < dnum) {
+                    const u64 y = (j == rdig) ? xbase[c * x_outer + (long long)r * N + n]
+                                              : ext[(((long long)c * dnum + j) * lK + r) * N + n];
+                    a0 += (u128)y * k0[j];
+                    a1 += (u128)y * k1[j];
+                }
+            }
+            acc[(((long long)c * 2 + 0) * lK + r) * N + n] = barrett128(a0, m);
+            acc[(((long long)c * 2 + 1) * lK + r) * N + n] = barrett128(a1, m);
+        }
+    }
+}
+
+// out[o][i][k] = in[o][i][perm[k]]: sigma_g in the NTT domain.
+__global__ void k_automorphism(const u64 *__restrict__ in, u64 *__restrict__ out, long long total, int logN,
+                               const int *__restrict__ perm)
+{
+    const int mask = (1 << logN) - 1;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long base = idx & ~(long long)mask;
+        out[idx] = in[base + perm[idx & mask]];
+    }
+}
+
+// out[o][i] = a[o][i] * b[o'][i] pointwise, b's outer stride b_outer (0 = broadcast).
+__global__ void k_mul_poly(const u64 *__restrict__ a, const u64 *__restrict__ b, u64 *__restrict__ out,
+                           long long total, int logN, int level, long long b_outer, const ModQ *__restrict__ mq)
+{
+    const long long LN = (long long)level << logN;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long o = idx / LN, r = idx % LN;
+        out[idx] = barrett128((u128)a[idx] * b[o * b_outer + r], mq[(int)(r >> logN)]);
+    }
+}
+
+__global__ void k_copy_limbs(const u64 *__restrict__ in, u64 *__restrict__ out, long long total, int logN, int nl,
+                             long long in_outer, long long out_outer)
+{
+    const long long LN = (long long)nl << logN;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long o = idx / LN, r = idx % LN;
+        out[o * out_outer + r] = in[o * in_outer + r];
+    }
+}
+
+// out[o][i][n] = (scale * x[o][n] + y[o][n]) mod q_{prime[i]}  (y may be NULL)
+__global__ void k_rns_from_i64(const int64_t *__restrict__ x, const int64_t *__restrict__ y, int64_t scale,
+                               u64 *__restrict__ out, long long total, int logN, int nl, const LimbConsts pm,
+                               const ModQ *__restrict__ mq)
+{
+    const int N = 1 << logN;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long li = idx >> logN;
+        const int i = (int)(li % nl);
+        const long long o = li / nl;
+        const int n = (int)(idx & (N - 1));
+        const u64 q = mq[(int)pm.w[i]].q;
+        const int64_t v = scale * x[o * N + n] + (y ? y[o * N + n] : 0);
+        const int64_t r = v % (int64_t)q;
+        out[idx] = (u64)(r < 0 ? r + (int64_t)q : r);
+    }
+}
+
+// out = c + a * b (pointwise), b with outer stride b_outer; c may be NULL.
+// With neg != 0: out = c - a * b.
+__global__ void k_muladd(const u64 *__restrict__ a, const u64 *__restrict__ b, const u64 *__restrict__ cc,
+                         u64 *__restrict__ out, long long total, int logN, int level, long long b_outer, int neg,
+                         const ModQ *__restrict__ mq)
+{
+    const long long LN = (long long)level << logN;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long o = idx / LN, r = idx % LN;
+        const ModQ m = mq[(int)(r >> logN)];
+        const u64 t = barrett128((u128)a[idx] * b[o * b_outer + r], m);
+        const u64 base = cc ? cc[idx] : 0;
+        out[idx] = neg ? submod(base, t, m.q) : addmod(base, t, m.q);
+    }
+}
+
+// One digit of a switching key over the L+K primes (NTT domain):
+//   k0 = e - a s + [i in D_j] (P mod q_i) s',  k1 = a.
+__global__ void k_ksk_digit(const u64 *__restrict__ a, const u64 *__restrict__ e, const u64 *__restrict__ s,
+                            const u64 *__restrict__ sp, u64 *__restrict__ k0, u64 *__restrict__ k1, long long total,
+                            int logN, int dlo, int dhi, const LimbConsts Pm, const ModQ *__restrict__ mq)
+{
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx >> logN);
+        const ModQ m = mq[i];
+        u64 v = submod(e[idx], barrett128((u128)a[idx] * s[idx], m), m.q);
+        if (i >= dlo && i < dhi) v = addmod(v, shoup(sp[idx], Pm.w[i], Pm.ws[i], m.q), m.q);
+        k0[idx] = v;
+        k1[idx] = a[idx];
+    }
+}
+
+}  // namespace
+
+#define LAUNCH(kern, total, ...)                                                            \
+    do {                                                                                    \
+        long long _t = (total);                                                             \
+        if (_t > 0) {                                                                       \
+            kern<<<grid_for(_t), TPB, 0, c->stream>>>(__VA_ARGS__);                         \
+            c->launches++;                                                                  \
+        }                                                                                   \
+    } while (0)
+
+void launch_add(fhe_ctx *c, const u64 *a, const u64 *b, u64 *out, int outer, int level, int sub)
+{
+    LAUNCH(k_add, (long long)outer * level * c->N, a, b, out, (long long)outer * level * c->N, c->logN, level,
+           c->d_mq, sub);
+}
+
+void launch_neg(fhe_ctx *c, const u64 *a, u64 *out, int outer, int level)
+{
+    LAUNCH(k_neg, (long long)outer * level * c->N, a, out, (long long)outer * level * c->N, c->logN, level, c->d_mq);
+}
+
+void launch_mul_const(fhe_ctx *c, const u64 *a, u64 *out, int outer, int level, const u64 *w, const u64 *ws)
+{
+    LimbConsts k;
+    for (int i = 0; i < level; i++) k.w[i] = w[i], k.ws[i] = ws[i];
+    LAUNCH(k_mul_const, (long long)outer * level * c->N, a, out, (long long)outer * level * c->N, c->logN, level,
+           c->d_mq, k);
+}
+
+void launch_add_const(fhe_ctx *c, const u64 *a, u64 *out, int count, int level, const u64 *kv)
+{
+    LimbConsts k;
+    for (int i = 0; i < level; i++) k.w[i] = kv[i], k.ws[i] = 0;
+    LAUNCH(k_add_const, (long long)count * 2 * level * c->N, a, out, (long long)count * 2 * level * c->N, c->logN,
+           level, c->d_mq, k);
+}
+
+void launch_tensor(fhe_ctx *c, const u64 *a, const u64 *b, u64 *out, int count, int level)
+{
+    LAUNCH(k_tensor, (long long)count * level * c->N, a, b, out, (long long)count * level * c->N, c->logN, level,
+           c->d_mq);
+}
+
+void launch_ks_inner(fhe_ctx *c, const u64 *ext, const u64 *xbase, long long x_outer, const u64 *ksk, u64 *acc,
+                     int count, int level)
+{
+    const int dnum = c->modup[level].dnum;
+    dim3 grid((c->N + TPB - 1) / TPB, level + c->K);
+    k_ks_inner<<<grid, TPB, 0, c->stream>>>(ext, xbase, x_outer, ksk, acc, count, level, c->K, c->L, dnum, c->logN,
+                                            c->d_mq);
+    c->launches++;
+}
+
+void launch_automorphism(fhe_ctx *c, const u64 *in, u64 *out, int outer, int level, const int *perm)
+{
+    LAUNCH(k_automorphism, (long long)outer * level * c->N, in, out, (long long)outer * level * c->N, c->logN, perm);
+}
+
+void launch_mul_poly(fhe_ctx *c, const u64 *a, const u64 *b, u64 *out, int outer, int level, long long b_outer)
+{
+    LAUNCH(k_mul_poly, (long long)outer * level * c->N, a, b, out, (long long)outer * level * c->N, c->logN, level,
+           b_outer, c->d_mq);
+}
+
+void launch_copy_limbs(fhe_ctx *c, const u64 *in, u64 *out, int outer, int nl, long long in_outer,
+                       long long out_outer)
+{
+    LAUNCH(k_copy_limbs, (long long)outer * nl * c->N, in, out, (long long)outer * nl * c->N, c->logN, nl, in_outer,
+           out_outer);
+}
+
+void launch_rns_from_i64(fhe_ctx *c, const int64_t *x, const int64_t *y, int64_t scale, u64 *out, int outer, int nl,
+                         const int *primes)
+{
+    LimbConsts pm;
+    for (int i = 0; i < nl; i++) pm.w[i] = (u64)primes[i], pm.ws[i] = 0;
+    LAUNCH(k_rns_from_i64, (long long)outer * nl * c->N, x, y, scale, out, (long long)outer * nl * c->N, c->logN, nl,
+           pm, c->d_mq);
+}
+
+void launch_muladd(fhe_ctx *c, const u64 *a, const u64 *b, const u64 *cc, u64 *out, int outer, int level,
+                   long long b_outer, int neg)
+{
+    LAUNCH(k_muladd, (long long)outer * level * c->N, a, b, cc, out, (long long)outer * level * c->N, c->logN, level,
+           b_outer, neg, c->d_mq);
+}
+
+void launch_ksk_digit(fhe_ctx *c, const u64 *a, const u64 *e, const u64 *s, const u64 *sp, u64 *k0, u64 *k1, int dlo,
+                      int dhi, const u64 *Pw, const u64 *Pws)
+{
+    LimbConsts Pm;
+    for (int i = 0; i < c->np; i++) Pm.w[i] = Pw[i], Pm.ws[i] = Pws[i];
+    LAUNCH(k_ksk_digit, (long long)c->np * c->N, a, e, s, sp, k0, k1, (long long)c->np * c->N, c->logN, dlo, dhi, Pm,
+           c->d_mq);
+}

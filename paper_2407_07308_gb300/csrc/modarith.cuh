@@ -1,0 +1,105 @@
+// modarith.cuh -- exact modular arithmetic on u64 residues (q < 2^58).
+//
+// Two published methods, both exact (the result is the canonical residue):
+//  * Shoup's precomputed-quotient product for multiplication by a known
+//    constant w:  w' = floor(w 2^64 / q);  a w - floor(a w' / 2^64) q lies in
+//    [0, 2q) for every a < 2^64 (V. Shoup, NTL; D. Harvey, "Faster arithmetic
+//    for number-theoretic transforms", J. Symb. Comp. 2014, which also gives
+//    the lazy butterflies used by the NTT);
+//  * Barrett reduction (P. Barrett 1986) of a 128-bit value x < 2^(2b+3),
+//    b = bitlength(q): t = floor(x / 2^(b-2)), mu = floor(2^(2b+4) / q),
+//    qhat = floor(t mu / 2^(b+6)) satisfies x/q - 2 < qhat <= x/q, so
+//    x - qhat q lies in [0, 3q).  That bound admits sums of up to eight
+//    products of canonical residues before one reduction.
+// Every function is __host__ __device__ so the library's CPU self-test checks
+// the very code the kernels run.
+#pragma once
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define FHE_HD __host__ __device__ __forceinline__
+#else
+#define FHE_HD inline
+#endif
+
+typedef uint64_t u64;
+typedef unsigned __int128 u128;
+
+FHE_HD u64 fhe_mulhi(u64 a, u64 b)
+{
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (u64)(((u128)a * b) >> 64);
+#endif
+}
+
+// Per-prime constants used by the kernels.
+struct ModQ {
+    u64 q;       // the prime
+    u64 q2;      // 2q
+    u64 mu;      // floor(2^(2b+4) / q) * 2^(58-b): Barrett constant, pre-shifted
+    int bshift;  // b - 2, the shift that forms t
+    int pad;
+};
+
+// a * w mod q in [0, 2q), w < q, ws = floor(w 2^64 / q), any a < 2^64.
+FHE_HD u64 shoup_lazy(u64 a, u64 w, u64 ws, u64 q) { return a * w - fhe_mulhi(a, ws) * q; }
+
+FHE_HD u64 shoup(u64 a, u64 w, u64 ws, u64 q)
+{
+    u64 r = shoup_lazy(a, w, ws, q);
+    return r >= q ? r - q : r;
+}
+
+// Canonical residue of x < 2^(2b+3).
+FHE_HD u64 barrett128(u128 x, const ModQ &m)
+{
+    u64 lo = (u64)x, hi = (u64)(x >> 64);
+    int s = m.bshift;                                   // 1 <= s <= 56
+    u64 t = (hi << (64 - s)) | (lo >> s);               // floor(x / 2^(b-2)) < 2^(b+5)
+    u64 qhat = fhe_mulhi(t, m.mu);                      // floor(t mu / 2^(b+6))
+    u64 r = lo - qhat * m.q;                            // in [0, 3q)
+    if (r >= m.q2) r -= m.q2;
+    if (r >= m.q) r -= m.q;
+    return r;
+}
+
+FHE_HD u64 mulmod(u64 a, u64 b, const ModQ &m) { return barrett128((u128)a * b, m); }
+
+FHE_HD u64 addmod(u64 a, u64 b, u64 q)
+{
+    u64 r = a + b;
+    return r >= q ? r - q : r;
+}
+
+FHE_HD u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+
+FHE_HD u64 negmod(u64 a, u64 q) { return a ? q - a : 0; }
+
+// [0, 2q) -> [0, q)
+FHE_HD u64 reduce2q(u64 a, u64 q) { return a >= q ? a - q : a; }
+
+// [0, 4q) -> [0, q)
+FHE_HD u64 reduce4q(u64 a, u64 q2, u64 q)
+{
+    if (a >= q2) a -= q2;
+    return a >= q ? a - q : a;
+}
+
+// Host-side constructors.
+inline ModQ make_modq(u64 q)
+{
+    ModQ m;
+    int b = 0;
+    while (b < 64 && (q >> b)) b++;
+    m.q = q;
+    m.q2 = 2 * q;
+    u128 mu = ((u128)1 << (2 * b + 4)) / q;             // < 2^(b+5)
+    m.mu = (u64)(mu << (58 - b));
+    m.bshift = b - 2;
+    m.pad = 0;
+    return m;
+}
+
+inline u64 shoup_const(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }

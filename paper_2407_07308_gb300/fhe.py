@@ -1,0 +1,414 @@
+"""Python binding of libfhe_gb300.so (the C ABI in include/fhe.h).
+
+Argument marshalling only: every function here converts numpy arrays and
+handles to C arguments, calls the C function of the same name and raises
+FheError on a negative return code.  All computation happens in the CUDA
+library.  PyTorch provides device memory (its caching allocator, handed to the
+library as an allocator vtable) and the CUDA stream.
+
+The library must have been built (``paper_2407_07308_gb300.build.build()``);
+importing this module on a machine without it raises immediately -- there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import (CFUNCTYPE, POINTER, Structure, c_char_p, c_int, c_int32, c_int64, c_size_t, c_uint64,
+                    c_void_p)
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libfhe_gb300.so")
+
+ERRORS = {
+    -1: "FHE_EINVAL", -2: "FHE_EMISMATCH", -3: "FHE_ELEVEL", -4: "FHE_ENOMEM", -5: "FHE_EBUDGET",
+    -6: "FHE_ETIMEOUT", -7: "FHE_ECUDA", -8: "FHE_ENOKEY", -9: "FHE_EUNSUPPORTED",
+}
+OPS = {1: "mul", 2: "add", 3: "sub", 4: "cmul", 5: "cadd", 6: "neg", 7: "rot"}
+
+
+class FheError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class fhe_params(Structure):
+    _fields_ = [("log_n", c_int), ("p", c_uint64), ("L", c_int), ("K", c_int), ("prime_mod", c_uint64),
+                ("prime_lo", c_uint64), ("prime_hi", c_uint64)]
+
+
+ALLOC_FN = CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+FREE_FN = CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
+
+
+class fhe_allocator(Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", c_void_p)]
+
+
+class fhe_info(Structure):
+    _fields_ = [("N", c_int), ("L", c_int), ("K", c_int), ("slots", c_int), ("subring", c_int),
+                ("dnum_max", c_int), ("p", c_uint64)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2407_07308_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ci, u64, i64 = c_void_p, c_int, c_uint64, c_int64
+        sig = {
+            "fhe_ctx_create": (ci, [POINTER(fhe_params), POINTER(fhe_allocator), vp, POINTER(vp)]),
+            "fhe_ctx_destroy": (None, [vp]),
+            "fhe_last_error": (c_char_p, [vp]),
+            "fhe_ctx_info": (ci, [vp, POINTER(fhe_info)]),
+            "fhe_ctx_primes": (ci, [vp, vp]),
+            "fhe_ctx_set_stream": (ci, [vp, vp]),
+            "fhe_ctx_sync": (ci, [vp]),
+            "fhe_ctx_memory": (ci, [vp, POINTER(u64), POINTER(u64)]),
+            "fhe_ctx_set_budget": (ci, [vp, u64]),
+            "fhe_ctx_launches": (i64, [vp]),
+            "fhe_keygen_explicit": (ci, [vp, vp, vp, vp, POINTER(vp), POINTER(vp)]),
+            "fhe_keygen": (ci, [vp, u64, POINTER(vp), POINTER(vp)]),
+            "fhe_sk_destroy": (None, [vp]),
+            "fhe_pk_destroy": (None, [vp]),
+            "fhe_evk_create_explicit": (ci, [vp, vp, vp, ci, vp, vp, POINTER(vp)]),
+            "fhe_evk_create": (ci, [vp, vp, vp, ci, u64, POINTER(vp)]),
+            "fhe_evk_destroy": (None, [vp]),
+            "fhe_encrypt_explicit": (ci, [vp, vp, vp, ci, vp, vp, vp, POINTER(vp)]),
+            "fhe_encrypt": (ci, [vp, vp, vp, ci, u64, POINTER(vp)]),
+            "fhe_decrypt": (ci, [vp, vp, vp, vp]),
+            "fhe_ct_destroy": (None, [vp]),
+            "fhe_ct_shape": (ci, [vp, POINTER(ci), POINTER(ci), POINTER(ci)]),
+            "fhe_ct_export_coeff": (ci, [vp, vp, vp]),
+            "fhe_ct_import_coeff": (ci, [vp, vp, ci, ci, ci, POINTER(vp)]),
+            "fhe_add": (ci, [vp, vp, vp, POINTER(vp)]),
+            "fhe_sub": (ci, [vp, vp, vp, POINTER(vp)]),
+            "fhe_neg": (ci, [vp, vp, POINTER(vp)]),
+            "fhe_mul_const": (ci, [vp, vp, i64, POINTER(vp)]),
+            "fhe_add_const": (ci, [vp, vp, i64, POINTER(vp)]),
+            "fhe_mul": (ci, [vp, vp, vp, POINTER(vp)]),
+            "fhe_relinearize": (ci, [vp, vp, vp, POINTER(vp)]),
+            "fhe_mod_switch": (ci, [vp, vp, ci, POINTER(vp)]),
+            "fhe_rotate": (ci, [vp, vp, vp, i64, POINTER(vp)]),
+            "fhe_mul_relin": (ci, [vp, vp, vp, vp, POINTER(vp)]),
+            "fhe_compare_lt": (ci, [vp, vp, vp, vp, ci, POINTER(vp)]),
+            "fhe_compare_eq": (ci, [vp, vp, vp, vp, ci, POINTER(vp)]),
+            "fhe_compare": (ci, [vp, vp, vp, vp, ci, POINTER(vp), POINTER(vp)]),
+            "fhe_max_min": (ci, [vp, vp, vp, vp, ci, vp, vp]),
+            "fhe_max": (ci, [vp, vp, vp, vp, ci, vp]),
+            "fhe_min": (ci, [vp, vp, vp, vp, ci, vp]),
+            "fhe_trace_enable": (ci, [vp, ci]),
+            "fhe_trace_get": (ci, [vp, vp, vp, ci]),
+            "fhe_ntt_forward": (ci, [vp, vp, vp, ci]),
+            "fhe_ntt_inverse": (ci, [vp, vp, vp, ci]),
+            "fhe_selftest_modarith": (ci, [u64, u64, u64, ci, ci]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(c_void_p)
+
+
+def _check(rc, ctx=None):
+    if rc < 0:
+        msg = lib().fhe_last_error(ctx).decode() if ctx else ""
+        raise FheError(rc, msg)
+    return rc
+
+
+# ---------------------------------------------------------------------------
+# device memory from PyTorch
+# ---------------------------------------------------------------------------
+
+def torch_allocator(device: int = 0):
+    """An fhe_allocator whose calls go to torch's CUDA caching allocator."""
+    import torch
+
+    def _a(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream or 0)
+        except Exception:  # noqa: BLE001 -- reported to the library as NULL
+            return None
+
+    def _f(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = fhe_allocator(ALLOC_FN(_a), FREE_FN(_f), None)
+    a._keep = (_a, _f)  # keep the Python callables alive
+    return a
+
+
+# ---------------------------------------------------------------------------
+# wrappers with the C names
+# ---------------------------------------------------------------------------
+
+def fhe_ctx_create(log_n, p, L, K, prime_mod, prime_lo, prime_hi, allocator=None, stream=None):
+    P = fhe_params(log_n, p, L, K, prime_mod, prime_lo, prime_hi)
+    out = c_void_p()
+    rc = lib().fhe_ctx_create(ctypes.byref(P), ctypes.byref(allocator) if allocator is not None else None,
+                              c_void_p(stream or 0), ctypes.byref(out))
+    _check(rc)
+    return out
+
+
+def fhe_ctx_destroy(ctx):
+    lib().fhe_ctx_destroy(ctx)
+
+
+def fhe_ctx_info(ctx) -> fhe_info:
+    i = fhe_info()
+    _check(lib().fhe_ctx_info(ctx, ctypes.byref(i)), ctx)
+    return i
+
+
+def fhe_ctx_primes(ctx):
+    info = fhe_ctx_info(ctx)
+    out = np.zeros(info.L + info.K, dtype=np.uint64)
+    _check(lib().fhe_ctx_primes(ctx, _ptr(out)), ctx)
+    return [int(x) for x in out]
+
+
+def fhe_ctx_sync(ctx):
+    _check(lib().fhe_ctx_sync(ctx), ctx)
+
+
+def fhe_ctx_set_stream(ctx, stream: int):
+    _check(lib().fhe_ctx_set_stream(ctx, c_void_p(stream)), ctx)
+
+
+def fhe_ctx_memory(ctx):
+    r, u = c_uint64(), c_uint64()
+    _check(lib().fhe_ctx_memory(ctx, ctypes.byref(r), ctypes.byref(u)), ctx)
+    return r.value, u.value
+
+
+def fhe_ctx_set_budget(ctx, nbytes: int):
+    _check(lib().fhe_ctx_set_budget(ctx, nbytes), ctx)
+
+
+def fhe_ctx_launches(ctx) -> int:
+    return int(lib().fhe_ctx_launches(ctx))
+
+
+def fhe_keygen_explicit(ctx, s, a, e):
+    s = np.ascontiguousarray(s, dtype=np.int64)
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    e = np.ascontiguousarray(e, dtype=np.int64)
+    sk, pk = c_void_p(), c_void_p()
+    _check(lib().fhe_keygen_explicit(ctx, _ptr(s), _ptr(a), _ptr(e), ctypes.byref(sk), ctypes.byref(pk)), ctx)
+    return sk, pk
+
+
+def fhe_keygen(ctx, seed: int):
+    sk, pk = c_void_p(), c_void_p()
+    _check(lib().fhe_keygen(ctx, seed, ctypes.byref(sk), ctypes.byref(pk)), ctx)
+    return sk, pk
+
+
+def fhe_sk_destroy(sk):
+    lib().fhe_sk_destroy(sk)
+
+
+def fhe_pk_destroy(pk):
+    lib().fhe_pk_destroy(pk)
+
+
+def fhe_evk_create_explicit(ctx, sk, galois, a, e):
+    g = np.ascontiguousarray(galois, dtype=np.int64) if len(galois) else np.zeros(1, dtype=np.int64)
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    e = np.ascontiguousarray(e, dtype=np.int64)
+    out = c_void_p()
+    _check(lib().fhe_evk_create_explicit(ctx, sk, _ptr(g), len(galois), _ptr(a), _ptr(e), ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_evk_create(ctx, sk, galois, seed: int):
+    g = np.ascontiguousarray(galois, dtype=np.int64) if len(galois) else np.zeros(1, dtype=np.int64)
+    out = c_void_p()
+    _check(lib().fhe_evk_create(ctx, sk, _ptr(g), len(galois), seed, ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_evk_destroy(evk):
+    lib().fhe_evk_destroy(evk)
+
+
+def fhe_encrypt_explicit(ctx, pk, slots, u, e0, e1):
+    slots = np.ascontiguousarray(slots, dtype=np.uint64)
+    count = slots.shape[0]
+    u = np.ascontiguousarray(u, dtype=np.int64)
+    e0 = np.ascontiguousarray(e0, dtype=np.int64)
+    e1 = np.ascontiguousarray(e1, dtype=np.int64)
+    out = c_void_p()
+    _check(lib().fhe_encrypt_explicit(ctx, pk, _ptr(slots), count, _ptr(u), _ptr(e0), _ptr(e1), ctypes.byref(out)),
+           ctx)
+    return out
+
+
+def fhe_encrypt(ctx, pk, slots, seed: int):
+    slots = np.ascontiguousarray(slots, dtype=np.uint64)
+    out = c_void_p()
+    _check(lib().fhe_encrypt(ctx, pk, _ptr(slots), slots.shape[0], seed, ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_ct_shape(ct):
+    c, n, l = c_int(), c_int(), c_int()
+    _check(lib().fhe_ct_shape(ct, ctypes.byref(c), ctypes.byref(n), ctypes.byref(l)))
+    return c.value, n.value, l.value
+
+
+def fhe_decrypt(ctx, sk, ct):
+    count, _, _ = fhe_ct_shape(ct)
+    info = fhe_ctx_info(ctx)
+    out = np.zeros((count, info.slots), dtype=np.uint64)
+    _check(lib().fhe_decrypt(ctx, sk, ct, _ptr(out)), ctx)
+    return out
+
+
+def fhe_ct_destroy(ct):
+    lib().fhe_ct_destroy(ct)
+
+
+def fhe_ct_export_coeff(ctx, ct):
+    count, npoly, level = fhe_ct_shape(ct)
+    N = fhe_ctx_info(ctx).N
+    out = np.zeros((count, npoly, level, N), dtype=np.uint64)
+    _check(lib().fhe_ct_export_coeff(ctx, ct, _ptr(out)), ctx)
+    return out
+
+
+def fhe_ct_import_coeff(ctx, data):
+    data = np.ascontiguousarray(data, dtype=np.uint64)
+    count, npoly, level, _ = data.shape
+    out = c_void_p()
+    _check(lib().fhe_ct_import_coeff(ctx, _ptr(data), count, npoly, level, ctypes.byref(out)), ctx)
+    return out
+
+
+def _binary(name):
+    def f(ctx, a, b):
+        out = c_void_p()
+        _check(getattr(lib(), name)(ctx, a, b, ctypes.byref(out)), ctx)
+        return out
+
+    f.__name__ = name
+    return f
+
+
+fhe_add = _binary("fhe_add")
+fhe_sub = _binary("fhe_sub")
+fhe_mul = _binary("fhe_mul")
+
+
+def fhe_neg(ctx, a):
+    out = c_void_p()
+    _check(lib().fhe_neg(ctx, a, ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_mul_const(ctx, a, k: int):
+    out = c_void_p()
+    _check(lib().fhe_mul_const(ctx, a, int(k), ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_add_const(ctx, a, k: int):
+    out = c_void_p()
+    _check(lib().fhe_add_const(ctx, a, int(k), ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_relinearize(ctx, evk, a):
+    out = c_void_p()
+    _check(lib().fhe_relinearize(ctx, evk, a, ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_mod_switch(ctx, a, level: int):
+    out = c_void_p()
+    _check(lib().fhe_mod_switch(ctx, a, level, ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_rotate(ctx, evk, a, galois: int):
+    out = c_void_p()
+    _check(lib().fhe_rotate(ctx, evk, a, int(galois), ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_mul_relin(ctx, evk, a, b):
+    out = c_void_p()
+    _check(lib().fhe_mul_relin(ctx, evk, a, b, ctypes.byref(out)), ctx)
+    return out
+
+
+def _handles(cts):
+    arr = (c_void_p * len(cts))(*[c.value if isinstance(c, c_void_p) else c for c in cts])
+    return arr
+
+
+def fhe_compare(ctx, evk, xs, ys, want_lt=True, want_eq=True):
+    lt, eq = c_void_p(), c_void_p()
+    _check(lib().fhe_compare(ctx, evk, _handles(xs), _handles(ys), len(xs),
+                             ctypes.byref(lt) if want_lt else None, ctypes.byref(eq) if want_eq else None), ctx)
+    return (lt if want_lt else None), (eq if want_eq else None)
+
+
+def fhe_compare_lt(ctx, evk, xs, ys):
+    out = c_void_p()
+    _check(lib().fhe_compare_lt(ctx, evk, _handles(xs), _handles(ys), len(xs), ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_compare_eq(ctx, evk, xs, ys):
+    out = c_void_p()
+    _check(lib().fhe_compare_eq(ctx, evk, _handles(xs), _handles(ys), len(xs), ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_max_min(ctx, evk, xs, ys):
+    d = len(xs)
+    mx, mn = (c_void_p * d)(), (c_void_p * d)()
+    _check(lib().fhe_max_min(ctx, evk, _handles(xs), _handles(ys), d, mx, mn), ctx)
+    return [c_void_p(v) for v in mx], [c_void_p(v) for v in mn]
+
+
+def fhe_trace_enable(ctx, on: bool):
+    _check(lib().fhe_trace_enable(ctx, 1 if on else 0), ctx)
+
+
+def fhe_trace_get(ctx):
+    n = _check(lib().fhe_trace_get(ctx, None, None, 0), ctx)
+    ops = np.zeros(max(n, 1), dtype=np.int32)
+    lv = np.zeros(max(n, 1), dtype=np.int32)
+    lib().fhe_trace_get(ctx, _ptr(ops), _ptr(lv), n)
+    return [(OPS[int(o)], int(v)) for o, v in zip(ops[:n], lv[:n])]
+
+
+def fhe_ntt_forward(ctx, dev_ptr: int, prime_idx, nlimbs: int):
+    pi = np.ascontiguousarray(prime_idx, dtype=np.int32)
+    _check(lib().fhe_ntt_forward(ctx, c_void_p(dev_ptr), _ptr(pi), nlimbs), ctx)
+
+
+def fhe_ntt_inverse(ctx, dev_ptr: int, prime_idx, nlimbs: int):
+    pi = np.ascontiguousarray(prime_idx, dtype=np.int32)
+    _check(lib().fhe_ntt_inverse(ctx, c_void_p(dev_ptr), _ptr(pi), nlimbs), ctx)
+
+
+def fhe_selftest_modarith(prime_mod, prime_lo, prime_hi, nprimes, iters) -> int:
+    return int(lib().fhe_selftest_modarith(prime_mod, prime_lo, prime_hi, nprimes, iters))

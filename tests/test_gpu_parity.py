@@ -1,0 +1,291 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle on
+identical seeded inputs.  Every comparison of ciphertext limbs is exact
+(tolerance 0: integer arithmetic), decryptions are compared with plaintext
+results, and the circuit-level operation traces must be identical."""
+import random
+
+import numpy as np
+import pytest
+
+from tests.params import CHAIN36, CHAIN50
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_07308_gb300 import build
+
+    build.build()
+
+
+def _fhe():
+    from paper_2407_07308_gb300 import fhe
+
+    return fhe
+
+
+def _pair(params, seed=1, galois=()):
+    from tests.gpu_setup import GpuSetup
+    from tests.oracle_setup import OracleSetup
+
+    o = OracleSetup(seed=seed, galois=galois, **params)
+    g = GpuSetup(seed=seed, galois=galois, **params)
+    assert g.primes == o.o.primes
+    return o, g
+
+
+def _same(oracle_ct, gpu_export, idx=0):
+    want = oracle_ct.data
+    got = gpu_export[idx]
+    assert got.shape == want.shape, (got.shape, want.shape)
+    assert np.array_equal(got, want)
+
+
+# ---------------------------------------------------------------------------
+# NTT
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("logN", [10, 11, 12, 13, 14])
+def test_ntt_forward_inverse_match_oracle(logN):
+    from oracle.bgv import Oracle
+
+    fhe = _fhe()
+    L, K = 3, 2
+    o = Oracle(logN, 131, L, K, **CHAIN50)
+    ctx = fhe.fhe_ctx_create(logN, 131, L, K, **{"prime_mod": CHAIN50["U"], "prime_lo": CHAIN50["lo"],
+                                                   "prime_hi": CHAIN50["hi"]})
+    try:
+        N = 1 << logN
+        g = np.random.default_rng(logN)
+        # every prime, plus a ragged repeat pattern of prime indices
+        pidx = [0, 1, 2, 3, 4, 2, 0]
+        a = np.stack([g.integers(0, o.primes[i], size=N, dtype=np.uint64) for i in pidx])
+        dev = torch.from_numpy(a.view(np.int64).copy()).cuda()
+        fhe.fhe_ntt_forward(ctx, dev.data_ptr(), pidx, len(pidx))
+        torch.cuda.synchronize()
+        got = dev.cpu().numpy().view(np.uint64)
+        for r, i in enumerate(pidx):
+            assert np.array_equal(got[r], o.ntt(i, a[r])), (logN, r)
+        fhe.fhe_ntt_inverse(ctx, dev.data_ptr(), pidx, len(pidx))
+        torch.cuda.synchronize()
+        assert np.array_equal(dev.cpu().numpy().view(np.uint64), a)
+        # inverse of arbitrary evaluation-domain data
+        b = np.stack([g.integers(0, o.primes[i], size=N, dtype=np.uint64) for i in pidx])
+        dev = torch.from_numpy(b.view(np.int64).copy()).cuda()
+        fhe.fhe_ntt_inverse(ctx, dev.data_ptr(), pidx, len(pidx))
+        torch.cuda.synchronize()
+        got = dev.cpu().numpy().view(np.uint64)
+        for r, i in enumerate(pidx):
+            assert np.array_equal(got[r], o.intt(i, b[r]))
+    finally:
+        fhe.fhe_ctx_destroy(ctx)
+
+
+def test_ntt_max_residues():
+    """All-(q-1) input: the lazy butterflies' largest values."""
+    from oracle.bgv import Oracle
+
+    fhe = _fhe()
+    o = Oracle(14, 131, 2, 1, **CHAIN50)
+    ctx = fhe.fhe_ctx_create(14, 131, 2, 1, CHAIN50["U"], CHAIN50["lo"], CHAIN50["hi"])
+    try:
+        a = np.stack([np.full(1 << 14, q - 1, dtype=np.uint64) for q in o.primes])
+        dev = torch.from_numpy(a.view(np.int64).copy()).cuda()
+        fhe.fhe_ntt_forward(ctx, dev.data_ptr(), [0, 1, 2], 3)
+        torch.cuda.synchronize()
+        got = dev.cpu().numpy().view(np.uint64)
+        for i in range(3):
+            assert np.array_equal(got[i], o.ntt(i, a[i]))
+    finally:
+        fhe.fhe_ctx_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# keys, encryption, single operations
+# ---------------------------------------------------------------------------
+
+SMALL36 = dict(logN=12, p=17, L=4, K=1, **CHAIN36)
+RAGGED50 = dict(logN=11, p=17, L=5, K=2, **CHAIN50)   # digits of 2, 2, 1 limbs
+MID50 = dict(logN=14, p=131, L=10, K=3, **CHAIN50)
+
+
+@pytest.mark.parametrize("params", [SMALL36, RAGGED50], ids=["n12_36b", "n11_50b"])
+def test_encrypt_bitexact(params):
+    o, g = _pair(params, seed=3)
+    try:
+        rnd = random.Random(1)
+        rows = [[rnd.randrange(params["p"]) for _ in range(g.ns)] for _ in range(3)]
+        cts_o = o.encrypt_slots(rows, seed=9)
+        ct_g = g.encrypt_slots(rows, seed=9)
+        ex = g.export(ct_g)
+        for i in range(3):
+            _same(cts_o[i], ex, i)
+        assert g.decrypt(ct_g).tolist() == rows
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("params", [SMALL36, RAGGED50], ids=["n12_36b", "n11_50b"])
+def test_single_ops_bitexact(params):
+    fhe = _fhe()
+    galois = (5, 2 * (1 << params["logN"]) - 1)
+    o, g = _pair(params, seed=4, galois=galois)
+    try:
+        p = params["p"]
+        rnd = random.Random(2)
+        a = [rnd.randrange(p) for _ in range(g.ns)]
+        b = [rnd.randrange(p) for _ in range(g.ns)]
+        ca_o, cb_o = o.encrypt_slots([a, b], seed=11)
+        ca_g, cb_g = g.encrypt_each([a, b], seed=11)
+        oc = o.o
+        X = g.ctx
+        checks = [
+            ("add", oc.add(ca_o, cb_o), fhe.fhe_add(X, ca_g, cb_g)),
+            ("sub", oc.sub(ca_o, cb_o), fhe.fhe_sub(X, ca_g, cb_g)),
+            ("neg", oc.neg(ca_o), fhe.fhe_neg(X, ca_g)),
+            ("cmul", oc.mul_const(ca_o, -7), fhe.fhe_mul_const(X, ca_g, p - 7)),
+            ("cadd", oc.add_const(ca_o, 3), fhe.fhe_add_const(X, ca_g, 3)),
+            ("tensor", oc.tensor(ca_o, cb_o), fhe.fhe_mul(X, ca_g, cb_g)),
+            ("modswitch", oc.modswitch(ca_o), fhe.fhe_mod_switch(X, ca_g, params["L"] - 1)),
+            ("modswitch2", oc.modswitch(oc.modswitch(ca_o)), fhe.fhe_mod_switch(X, ca_g, params["L"] - 2)),
+        ]
+        d_o = oc.tensor(ca_o, cb_o)
+        checks.append(("relin", oc.relin(d_o, o.rlk), fhe.fhe_relinearize(X, g.evk, checks[5][2])))
+        ev = o.evaluator()
+        checks.append(("mul_relin", ev.mul(ca_o, cb_o), fhe.fhe_mul_relin(X, g.evk, ca_g, cb_g)))
+        for gal in galois:
+            checks.append((f"rot{gal}", oc.rotate(ca_o, gal, o.gks[gal]), fhe.fhe_rotate(X, g.evk, ca_g, gal)))
+        # a lower-level operand: relinearisation with a short last digit
+        low_o = oc.modswitch(ca_o)
+        low_g = fhe.fhe_mod_switch(X, ca_g, params["L"] - 1)
+        dl_o = oc.tensor(low_o, low_o)
+        dl_g = fhe.fhe_mul(X, low_g, low_g)
+        checks.append(("relin_low", oc.relin(dl_o, o.rlk), fhe.fhe_relinearize(X, g.evk, dl_g)))
+        for name, want, got in checks:
+            g.own(got)
+            ex = g.export(got)
+            assert np.array_equal(ex[0], want.data), name
+        g.own(low_g)
+        g.own(dl_g)
+    finally:
+        g.close()
+
+
+# ---------------------------------------------------------------------------
+# comparison circuits
+# ---------------------------------------------------------------------------
+
+def _values(rnd, n, hi, dup=0.3):
+    xs = [rnd.randrange(hi) for _ in range(n)]
+    ys = [x if rnd.random() < dup else rnd.randrange(hi) for x in xs]
+    return xs, ys
+
+
+def _digits(vals, b, d):
+    return [[(v // b ** k) % b for v in vals] for k in range(d)]
+
+
+def _run_compare(params, d, count, seed, want_maxmin=False, check_bits=True):
+    fhe = _fhe()
+    o, g = _pair(params, seed=seed)
+    try:
+        p = params["p"]
+        b = (p + 1) // 2
+        rnd = random.Random(seed)
+        xv, yv = zip(*[_values(rnd, g.ns, b ** d) for _ in range(count)])
+        # digit k of every ciphertext of the batch: rows [count][ns]
+        xd = [[_digits(xv[c], b, d)[k] for c in range(count)] for k in range(d)]
+        yd = [[_digits(yv[c], b, d)[k] for c in range(count)] for k in range(d)]
+        xg = [g.encrypt_slots(xd[k], seed=100 + k) for k in range(d)]
+        yg = [g.encrypt_slots(yd[k], seed=200 + k) for k in range(d)]
+        fhe.fhe_trace_enable(g.ctx, True)
+        lt_g, eq_g = fhe.fhe_compare(g.ctx, g.evk, xg, yg)
+        g.own(lt_g)
+        g.own(eq_g)
+        trace_g = fhe.fhe_trace_get(g.ctx)
+        lt_dec, eq_dec = g.decrypt(lt_g), g.decrypt(eq_g)
+        for c in range(count):
+            assert lt_dec[c].tolist() == [int(a < e) for a, e in zip(xv[c], yv[c])]
+            assert eq_dec[c].tolist() == [int(a == e) for a, e in zip(xv[c], yv[c])]
+        if check_bits:
+            # oracle on ciphertext 0 of the batch, same randomness
+            xo = [o.encrypt_slots(xd[k], seed=100 + k)[0] for k in range(d)]
+            yo = [o.encrypt_slots(yd[k], seed=200 + k)[0] for k in range(d)]
+            ev = o.evaluator()
+            lt_o, eq_o = ev.compare(xo, yo, True, True)
+            assert trace_g == ev.trace
+            _same(lt_o, g.export(lt_g), 0)
+            _same(eq_o, g.export(eq_g), 0)
+        if want_maxmin:
+            mx, mn = fhe.fhe_max_min(g.ctx, g.evk, xg, yg)
+            for h in mx + mn:
+                g.own(h)
+            mxd = [g.decrypt(h) for h in mx]
+            mnd = [g.decrypt(h) for h in mn]
+            for c in range(count):
+                got_max = [sum(int(mxd[k][c][s]) * b ** k for k in range(d)) for s in range(g.ns)]
+                got_min = [sum(int(mnd[k][c][s]) * b ** k for k in range(d)) for s in range(g.ns)]
+                assert got_max == [max(a, e) for a, e in zip(xv[c], yv[c])]
+                assert got_min == [min(a, e) for a, e in zip(xv[c], yv[c])]
+            if check_bits:
+                mx_o, mn_o = ev.max_min(xo, yo)
+                for k in range(d):
+                    _same(mx_o[k], g.export(mx[k]), 0)
+                    _same(mn_o[k], g.export(mn[k]), 0)
+    finally:
+        g.close()
+
+
+def test_compare_p17_d2_small_ring():
+    _run_compare(dict(logN=10, p=17, L=7, K=2, **CHAIN50), d=2, count=3, seed=5, want_maxmin=True)
+
+
+def test_compare_p17_d3_ragged_merge():
+    _run_compare(dict(logN=10, p=17, L=8, K=3, **CHAIN50), d=3, count=2, seed=6)
+
+
+def test_compare_p131_d1_small_ring():
+    _run_compare(dict(logN=10, p=131, L=9, K=3, **CHAIN50), d=1, count=2, seed=7)
+
+
+def test_compare_p257_d1_small_ring():
+    _run_compare(dict(logN=10, p=257, L=9, K=4, **CHAIN50), d=1, count=2, seed=8)
+
+
+def test_compare_small_config_full():
+    """N=2^12, p=17, d=1, 4x36-bit + 1 special prime: one LT (and EQ)."""
+    _run_compare(SMALL36, d=1, count=1, seed=1)
+
+
+def test_compare_mid_config_full_batch():
+    """N=2^14, p=131, d=2, 10x50-bit + 3 special primes, a batch of 16 pairs
+    (the benchmark's launch configuration); ciphertext 0 bit-exact against the
+    oracle, all 16 against plaintext."""
+    _run_compare(MID50, d=2, count=16, seed=2)
+
+
+def test_batch_equals_singles():
+    """A batch gives the same bits as each ciphertext on its own."""
+    fhe = _fhe()
+    from tests.gpu_setup import GpuSetup
+
+    params = dict(logN=11, p=17, L=6, K=2, **CHAIN50)
+    g = GpuSetup(seed=12, **params)
+    try:
+        rnd = random.Random(3)
+        xs = [[rnd.randrange(9) for _ in range(g.ns)] for _ in range(4)]
+        ys = [[rnd.randrange(9) for _ in range(g.ns)] for _ in range(4)]
+        xb, yb = g.encrypt_slots(xs, seed=1), g.encrypt_slots(ys, seed=2)
+        lt_b = g.own(fhe.fhe_compare_lt(g.ctx, g.evk, [xb], [yb]))
+        ex_b = g.export(lt_b)
+        xe, ye = g.encrypt_each(xs, seed=1), g.encrypt_each(ys, seed=2)
+        for i in range(4):
+            lt_i = g.own(fhe.fhe_compare_lt(g.ctx, g.evk, [xe[i]], [ye[i]]))
+            assert np.array_equal(g.export(lt_i)[0], ex_b[i])
+    finally:
+        g.close()
