@@ -1,0 +1,490 @@
+#!/usr/bin/env python3
+"""Encrypted comparison benchmark on GB300.
+
+Workload (the paper's comparison microbenchmark shape, Sec. 6, on a
+power-of-two ring): BGV with N = 2^14, plaintext prime p = 131, values split
+into d = 2 digits of base (p+1)/2 = 66 (values uniform in [0, 4356)),
+10 x 50-bit data primes + 3 special primes, hybrid key switching.  One step is
+one batch of 16 ciphertext pairs (each pair: 2 digit ciphertexts per operand,
+n_s = 2 slots each) through the whole comparison: per-digit LT and EQ by
+Paterson-Stockmeyer (23 ciphertext products per digit) and the digit merge,
+i.e. 48 products per pair, each tensor -> relinearise (NTT, ModUp, inner
+product, ModDown) -> modulus switch.
+
+Metric: encrypted slot-comparisons per second (one LT+EQ of a ciphertext pair
+counts n_s slot comparisons), batched form; the plain form (one request at a
+time, op by op) and per-request p50/p99 latency are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Inputs are synthetic and seeded; everything is resident in HBM before the
+timed region (inputs are 168 MB of ciphertexts, larger than the 129 MB L2).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "encrypted slot-comparisons/sec at N=2^14,p=131,d=2; batched vs plain; p99 ms"
+UNIT = "slot-comparisons/s"
+U50 = 2 ** 16 * 17 * 131 * 257
+W = dict(logN=14, p=131, d=2, L=10, K=3, U=U50, lo=2 ** 49, hi=2 ** 50, pairs=16, seed=2)
+CONFIG = {
+    "workload": "BGV N=2^14 p=131 d=2 LT+EQ, 16 ciphertext pairs per batch, 10x50-bit + 3 special primes",
+    "N": 2 ** 14, "p": 131, "d": 2, "slots_per_ct": 2, "pairs_per_step": 16, "data_primes": 10, "special_primes": 3,
+    "l2": "inputs 168 MB > L2 (129 MB); intermediates ~10 GB per step",
+}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ---------------------------------------------------------------------------
+# inputs (shared by both arms; seeded)
+# ---------------------------------------------------------------------------
+
+def make_values(pairs, ns, seed):
+    from paper_2407_07308_gb300 import synth
+
+    g = synth.rng(seed + 1000)
+    b = (W["p"] + 1) // 2
+    hi = b ** W["d"]
+    xv = synth.values(g, pairs * ns, hi).reshape(pairs, ns)
+    yv = synth.values(g, pairs * ns, hi).reshape(pairs, ns)
+    xd = [synth.to_digits(xv.ravel(), b, W["d"])[k].reshape(pairs, ns) for k in range(W["d"])]
+    yd = [synth.to_digits(yv.ravel(), b, W["d"])[k].reshape(pairs, ns) for k in range(W["d"])]
+    return xv, yv, xd, yd
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and the CPU baseline): one process per pair
+# ---------------------------------------------------------------------------
+
+_STATE = {}
+
+
+def _oracle_init():
+    """Worker set-up (untimed): oracle context, keys, the batch's values."""
+    sys.path.insert(0, ROOT)
+    from oracle.bgv import Oracle
+    from oracle.encoding import SlotStructure
+    from paper_2407_07308_gb300 import synth
+
+    o = Oracle(W["logN"], W["p"], W["L"], W["K"], W["U"], W["lo"], W["hi"])
+    ss = SlotStructure(W["p"], o.N)
+    km = synth.KeyMaterial(W["seed"], o.primes, W["L"], W["K"], o.N)
+    _STATE.update(o=o, ss=ss, km=km, pk=o.keygen(km.s, km.a_pk, km.e_pk),
+                  rlk=o.relin_key(km.s, km.a_ksk[0], km.e_ksk[0]), vals=make_values(W["pairs"], ss.ns, W["seed"]),
+                  cts={})
+
+
+def _oracle_pair(i):
+    """LT and EQ of pair i with the oracle; returns (compare seconds, ok)."""
+    from oracle.circuits import Evaluator
+    from paper_2407_07308_gb300 import synth
+
+    st = _STATE
+    o, ss, km = st["o"], st["ss"], st["km"]
+    xv, yv, xd, yd = st["vals"]
+    if i not in st["cts"]:
+        cts = []
+        for k in range(W["d"]):
+            for rows, sd in ((xd[k], 100 + k), (yd[k], 200 + k)):
+                r = synth.EncRandomness(sd, W["pairs"], o.N)
+                cts.append(o.encrypt(st["pk"], ss.encode(rows[i]), r.u[i], r.e0[i], r.e1[i]))
+        st["cts"][i] = cts
+    cts = st["cts"][i]
+    ev = Evaluator(o, st["rlk"])
+    t = time.perf_counter()
+    lt, eq = ev.compare(cts[0::2], cts[1::2], True, True)
+    dt = time.perf_counter() - t
+    ok = (ss.decode(o.decrypt_coeffs(lt, km.s)) == [int(a < c) for a, c in zip(xv[i], yv[i])]
+          and ss.decode(o.decrypt_coeffs(eq, km.s)) == [int(a == c) for a, c in zip(xv[i], yv[i])])
+    return dt, ok
+
+
+class OraclePool:
+    """`workers` spawned processes (spawned before any GPU work), each holding
+    the oracle's context and keys; a sample runs one pair per process
+    concurrently and completes in the largest per-pair time."""
+
+    def __init__(self, workers):
+        import oracle
+
+        oracle.build()
+        self.workers = workers
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_oracle_init)
+
+    def sample(self, npairs):
+        res = self.pool.map(_oracle_pair, list(range(npairs)), chunksize=1)
+        assert all(ok for _, ok in res), "oracle decryption mismatch"
+        return [d for d, _ in res]
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for ln in fh:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2407_07308_gb300 import fhe, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # CPU baseline first (processes spawned before this process's first kernel)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        workers = max(1, min(W["pairs"], os.cpu_count() or 1, args.cpu_workers))
+        npairs = workers
+        op = OraclePool(workers)
+        per = op.sample(npairs)
+        op.close()
+        cpu = {"value": round(npairs * 2 / max(per), 4), "unit": UNIT, "cores": workers, "kind": "oracle",
+               "sample": f"{npairs} of the 16 pairs (LT+EQ, d=2, N=2^14) run concurrently, one spawned process "
+                         f"per pair; {statistics.mean(per):.1f} s per pair on average"}
+
+    stream = torch.cuda.Stream()
+    alloc = fhe.torch_allocator(local)
+    with torch.cuda.stream(stream):
+        ctx = fhe.fhe_ctx_create(W["logN"], W["p"], W["L"], W["K"], W["U"], W["lo"], W["hi"], allocator=alloc,
+                                 stream=stream.cuda_stream)
+    info = fhe.fhe_ctx_info(ctx)
+    ns, N, pairs = info.slots, info.N, W["pairs"]
+    primes = fhe.fhe_ctx_primes(ctx)
+    km = synth.KeyMaterial(W["seed"], primes, W["L"], W["K"], N)
+    sk, pk = fhe.fhe_keygen_explicit(ctx, km.s, km.a_pk, km.e_pk)
+    evk = fhe.fhe_evk_create_explicit(ctx, sk, [], km.a_ksk, km.e_ksk)
+    xv, yv, xd, yd = make_values(pairs, ns, W["seed"])
+
+    def enc(rows, sd):
+        r = synth.EncRandomness(sd, pairs, N)
+        return fhe.fhe_encrypt_explicit(ctx, pk, rows, r.u, r.e0, r.e1)
+
+    def enc_each(rows, sd):
+        r = synth.EncRandomness(sd, pairs, N)
+        return [fhe.fhe_encrypt_explicit(ctx, pk, rows[i:i + 1], r.u[i:i + 1], r.e0[i:i + 1], r.e1[i:i + 1])
+                for i in range(pairs)]
+
+    xs = [enc(xd[k], 100 + k) for k in range(W["d"])]
+    ys = [enc(yd[k], 200 + k) for k in range(W["d"])]
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def step():
+        lt, eq = fhe.fhe_compare(ctx, evk, xs, ys)
+        fhe.fhe_ct_destroy(lt)
+        fhe.fhe_ct_destroy(eq)
+
+    # correctness of the timed configuration
+    lt, eq = fhe.fhe_compare(ctx, evk, xs, ys)
+    ltd, eqd = fhe.fhe_decrypt(ctx, sk, lt), fhe.fhe_decrypt(ctx, sk, eq)
+    assert (ltd == (xv < yv)).all() and (eqd == (xv == yv)).all(), "batched result mismatch"
+    fhe.fhe_ct_destroy(lt)
+    fhe.fhe_ct_destroy(eq)
+
+    for _ in range(args.warmup):
+        step()
+    fhe.fhe_ctx_sync(ctx)
+
+    # ---- timed region: batched form ---------------------------------------
+    evs = [ev() for _ in range(args.steps + 1)]
+    barrier()
+    torch.cuda.synchronize()
+    l0 = fhe.fhe_ctx_launches(ctx)
+    with Clocks(local) as clk:
+        evs[0].record(stream)
+        for i in range(args.steps):
+            step()
+            evs[i + 1].record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    launches = fhe.fhe_ctx_launches(ctx) - l0
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * pairs * ns * args.steps / (total_ms / 1e3)
+
+    # ---- per-kernel device time over a second, profiled pass ----------------
+    fhe.fhe_ctx_profile(ctx, True)
+    pe0, pe1 = ev(), ev()
+    pe0.record(stream)
+    for _ in range(args.steps):
+        step()
+    pe1.record(stream)
+    prof = fhe.fhe_ctx_profile_read(ctx)
+    fhe.fhe_ctx_profile(ctx, False)
+    stream.synchronize()
+    prof_ms_per_step = pe0.elapsed_time(pe1) / args.steps
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms_k, n_k, by_k, bf_k = prof[dom]
+    hbm_peak, peak_kind = peaks()
+    achieved = by_k / (ms_k / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(achieved / hbm_peak, 4), "peak_source": peak_kind, "traffic": None,
+            "launches": n_k, "avg_launch_us": round(1e3 * ms_k / max(n_k, 1), 2),
+            "algorithmic_bytes_per_launch": round(by_k / max(n_k, 1)),
+            "share_of_step": round(ms_k / sum(v[0] for v in prof.values()), 3)}
+    if bf_k:
+        roof["butterflies_per_s"] = bf_k / (ms_k / 1e3)
+    kernels = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches_per_step": v[1] // args.steps,
+                   "GBps": round(v[2] / (v[0] / 1e3) / 1e9, 1) if v[0] else 0.0}
+               for k, v in prof.items() if v[1]}
+
+    # ---- plain form: one request at a time, op by op ----------------------
+    plain_value, lat = None, [float("nan")]
+    xs1, ys1 = [], []
+    if not args.no_plain:
+        plain_value, lat, xs1, ys1 = run_plain(fhe, ctx, evk, xd, yd, enc_each, pairs, ns, stream, ev)
+
+    def pct(v, q):
+        return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(fhe, ctx, evk, xs, ys, pairs, ns, N, args, world, barrier)
+
+    clocks = clk.summary()
+    res, used = fhe.fhe_ctx_memory(ctx)
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded BGV keys, noise and values)",
+        "config": dict(CONFIG, parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "plain": None if plain_value is None else {
+            "value": round(plain_value, 2), "unit": UNIT, "ms_per_request_p50": round(pct(lat, 0.5), 3),
+            "ms_per_request_p99": round(pct(lat, 0.99), 3)},
+        "batched_step_ms_p50": round(pct(sorted(step_ms), 0.5), 3),
+        "batched_step_ms_p99": round(pct(sorted(step_ms), 0.99), 3),
+        "p99_ms": round(pct(sorted(step_ms), 0.99), 3),
+        "roofline": roof, "kernels": kernels, "profiled_ms_per_step": round(prof_ms_per_step, 3),
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "memory_gb": {"pool_reserved": round(res / 1e9, 2)},
+    }
+    for h in xs + ys + [c for x in xs1 + ys1 for c in x]:
+        fhe.fhe_ct_destroy(h)
+    fhe.fhe_evk_destroy(evk)
+    fhe.fhe_sk_destroy(sk)
+    fhe.fhe_pk_destroy(pk)
+    fhe.fhe_ctx_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_plain(fhe, ctx, evk, xd, yd, enc_each, pairs, ns, stream, ev):
+    """One request at a time: each pair is its own single-ciphertext call."""
+    import torch
+
+    xs1 = [enc_each(xd[k], 100 + k) for k in range(W["d"])]
+    ys1 = [enc_each(yd[k], 200 + k) for k in range(W["d"])]
+
+    def plain_one(i):
+        lt, eq = fhe.fhe_compare(ctx, evk, [x[i] for x in xs1], [y[i] for y in ys1])
+        fhe.fhe_ct_destroy(lt)
+        fhe.fhe_ct_destroy(eq)
+
+    plain_one(0)
+    fhe.fhe_ctx_sync(ctx)
+    pev = [ev() for _ in range(pairs + 1)]
+    torch.cuda.synchronize()
+    pev[0].record(stream)
+    for i in range(pairs):
+        plain_one(i)
+        pev[i + 1].record(stream)
+    stream.synchronize()
+    lat = sorted(pev[i].elapsed_time(pev[i + 1]) for i in range(pairs))
+    plain_total = pev[0].elapsed_time(pev[-1])
+    return pairs * ns / (plain_total / 1e3), lat, xs1, ys1
+
+
+def run_e2e(fhe, ctx, evk, xs, ys, pairs, ns, N, args, world, barrier):
+    """Host ciphertexts in (pinned), compare, host ciphertexts out, per step."""
+    import numpy as np
+    import torch
+
+    host_in = []
+    for h in xs + ys:
+        a = fhe.fhe_ct_export_coeff(ctx, h)
+        pinned = torch.empty(a.shape, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+        pinned[...] = a
+        host_in.append(pinned)
+    out_shape = (pairs, 2, 1, N)
+    host_out = [torch.empty(out_shape, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+                for _ in range(2)]
+    bi = sum(a.nbytes for a in host_in)
+    bo = sum(a.nbytes for a in host_out)
+
+    def e2e_step():
+        hs = [fhe.fhe_ct_import_coeff(ctx, a) for a in host_in]
+        d = W["d"]
+        lt, eq = fhe.fhe_compare(ctx, evk, hs[:d], hs[d:])
+        for h, buf in ((lt, host_out[0]), (eq, host_out[1])):
+            assert fhe.fhe_ct_shape(h) == (pairs, 2, 1)
+            fhe._check(fhe.lib().fhe_ct_export_coeff(ctx, h, fhe._ptr(buf)), ctx)
+            fhe.fhe_ct_destroy(h)
+        for h in hs:
+            fhe.fhe_ct_destroy(h)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    return {"value": round(world * pairs * ns * args.steps / e2e_s, 2), "unit": UNIT, "h2d_bytes_per_step": bi,
+            "d2h_bytes_per_step": bo}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle, as it stands
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    workers = max(1, min(W["pairs"], os.cpu_count() or 1, args.cpu_workers))
+    npairs = workers  # one pair per core per step: a bounded sample of the 16-pair batch
+    op = OraclePool(workers)
+    for _ in range(args.warmup):
+        op.sample(npairs)
+    walls = []
+    for _ in range(args.steps):
+        walls.append(max(op.sample(npairs)))
+    op.close()
+    total = sum(walls)
+    value = npairs * 2 * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded BGV keys, noise and values)", "config": dict(CONFIG, parallelism="host cores"),
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": workers, "kind": "oracle",
+                         "sample": f"{npairs} of the 16 pairs per step, one spawned process per pair"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-workers", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pairs", type=int, default=16, help="ciphertext pairs per batch (16 = the workload)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the one-request-at-a-time form")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    W["pairs"] = args.pairs
+    CONFIG["pairs_per_step"] = args.pairs
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

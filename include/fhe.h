@@ -226,6 +226,21 @@ int fhe_trace_get(const fhe_ctx *ctx, int32_t *ops, int32_t *levels, int cap);
 int fhe_ntt_forward(fhe_ctx *ctx, uint64_t *data, const int32_t *prime_idx, int nlimbs);
 int fhe_ntt_inverse(fhe_ctx *ctx, uint64_t *data, const int32_t *prime_idx, int nlimbs);
 
+/* ---- kernel timing ------------------------------------------------------------- */
+
+/* Kernel classes timed by fhe_ctx_profile_read. */
+enum { FHE_K_NTT_FWD = 0, FHE_K_NTT_INV = 1, FHE_K_NTT_MODUP = 2, FHE_K_NTT_MODDOWN = 3, FHE_K_NTT_MODSWITCH = 4,
+       FHE_K_KS_INNER = 5, FHE_K_TENSOR = 6, FHE_K_ELEMWISE = 7, FHE_K_AUTOMORPHISM = 8, FHE_K_COUNT = 9 };
+/* on != 0: record a CUDA event pair on the context's stream around every
+ * kernel launch (for per-class device time); off by default. */
+int fhe_ctx_profile(fhe_ctx *ctx, int on);
+/* Synchronises, then writes per class (arrays of ncls entries, any may be
+ * NULL) the summed device milliseconds, the number of launches, the
+ * algorithmic bytes moved (global words each kernel must read and write, x8)
+ * and the NTT butterflies executed, for the launches recorded since the last
+ * read; then forgets the records.  Returns FHE_K_COUNT. */
+int fhe_ctx_profile_read(fhe_ctx *ctx, double *ms, int64_t *count, double *bytes, double *bfly, int ncls);
+
 /* ---- self test ---------------------------------------------------------------- */
 
 /* Runs the library's modular-arithmetic routines (the same source the kernels

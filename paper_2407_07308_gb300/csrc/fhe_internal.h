@@ -124,6 +124,15 @@ struct fhe_ctx {
     std::string err;
     std::mutex mu;
 
+    // per-kernel-class CUDA-event timing (off unless requested)
+    bool prof_on = false;
+    int prof_cls = 0;
+    std::vector<cudaEvent_t> prof_events;      // recycled
+    std::vector<int> prof_rec_cls;             // class of each recorded launch
+    std::vector<double> prof_rec_bytes;        // algorithmic bytes of each launch
+    std::vector<double> prof_rec_bfly;         // NTT butterflies of each launch
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_rec;
+
     bool tracing = false;
     std::vector<int32_t> trace_op, trace_level;
     long long launches = 0;       // kernels launched since creation
@@ -157,6 +166,10 @@ struct fhe_ct {
     u64 *d = nullptr;             // [count][npoly][level][N] NTT domain
     size_t bytes = 0;
 };
+
+// kernel classes for fhe_ctx_profile_read (index = FHE_K_* in fhe.h)
+void prof_begin(fhe_ctx *c, int cls, double bytes = 0, double bfly = 0);
+void prof_end(fhe_ctx *c);
 
 // ---------------------------------------------------------------------------
 // internal helpers

@@ -213,18 +213,23 @@ __global__ void k_ksk_digit(const u64 *__restrict__ a, const u64 *__restrict__ e
 
 }  // namespace
 
-#define LAUNCH(kern, total, ...)                                                            \
+// words: u64 words read + written per element (algorithmic traffic)
+#define LAUNCH_CLS_W(cls, words, kern, total, ...)                                          \
     do {                                                                                    \
         long long _t = (total);                                                             \
         if (_t > 0) {                                                                       \
+            prof_begin(c, cls, 8.0 * (words) * (double)_t);                                 \
             kern<<<grid_for(_t), TPB, 0, c->stream>>>(__VA_ARGS__);                         \
+            prof_end(c);                                                                    \
             c->launches++;                                                                  \
         }                                                                                   \
     } while (0)
+#define LAUNCH_CLS(cls, kern, total, ...) LAUNCH_CLS_W(cls, 2, kern, total, __VA_ARGS__)
+#define LAUNCH(kern, total, ...) LAUNCH_CLS_W(FHE_K_ELEMWISE, 2, kern, total, __VA_ARGS__)
 
 void launch_add(fhe_ctx *c, const u64 *a, const u64 *b, u64 *out, int outer, int level, int sub)
 {
-    LAUNCH(k_add, (long long)outer * level * c->N, a, b, out, (long long)outer * level * c->N, c->logN, level,
+    LAUNCH_CLS_W(FHE_K_ELEMWISE, 3, k_add, (long long)outer * level * c->N, a, b, out, (long long)outer * level * c->N, c->logN, level,
            c->d_mq, sub);
 }
 
@@ -251,7 +256,7 @@ void launch_add_const(fhe_ctx *c, const u64 *a, u64 *out, int count, int level, 
 
 void launch_tensor(fhe_ctx *c, const u64 *a, const u64 *b, u64 *out, int count, int level)
 {
-    LAUNCH(k_tensor, (long long)count * level * c->N, a, b, out, (long long)count * level * c->N, c->logN, level,
+    LAUNCH_CLS_W(FHE_K_TENSOR, 7, k_tensor, (long long)count * level * c->N, a, b, out, (long long)count * level * c->N, c->logN, level,
            c->d_mq);
 }
 
@@ -260,14 +265,17 @@ void launch_ks_inner(fhe_ctx *c, const u64 *ext, const u64 *xbase, long long x_o
 {
     const int dnum = c->modup[level].dnum;
     dim3 grid((c->N + TPB - 1) / TPB, level + c->K);
+    // per (r, n): 2 dnum key words once, dnum inputs and 2 outputs per ciphertext
+    prof_begin(c, FHE_K_KS_INNER, 8.0 * (double)(level + c->K) * c->N * (2.0 * dnum + count * (dnum + 2.0)));
     k_ks_inner<<<grid, TPB, 0, c->stream>>>(ext, xbase, x_outer, ksk, acc, count, level, c->K, c->L, dnum, c->logN,
                                             c->d_mq);
+    prof_end(c);
     c->launches++;
 }
 
 void launch_automorphism(fhe_ctx *c, const u64 *in, u64 *out, int outer, int level, const int *perm)
 {
-    LAUNCH(k_automorphism, (long long)outer * level * c->N, in, out, (long long)outer * level * c->N, c->logN, perm);
+    LAUNCH_CLS(FHE_K_AUTOMORPHISM, k_automorphism, (long long)outer * level * c->N, in, out, (long long)outer * level * c->N, c->logN, perm);
 }
 
 void launch_mul_poly(fhe_ctx *c, const u64 *a, const u64 *b, u64 *out, int outer, int level, long long b_outer)
@@ -306,4 +314,74 @@ void launch_ksk_digit(fhe_ctx *c, const u64 *a, const u64 *e, const u64 *s, cons
     for (int i = 0; i < c->np; i++) Pm.w[i] = Pw[i], Pm.ws[i] = Pws[i];
     LAUNCH(k_ksk_digit, (long long)c->np * c->N, a, e, s, sp, k0, k1, (long long)c->np * c->N, c->logN, dlo, dhi, Pm,
            c->d_mq);
+}
+
+// ---------------------------------------------------------------------------
+// per-class event timing
+// ---------------------------------------------------------------------------
+
+static cudaEvent_t prof_event(fhe_ctx *c)
+{
+    if (!c->prof_events.empty()) {
+        cudaEvent_t e = c->prof_events.back();
+        c->prof_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(fhe_ctx *c, int cls, double bytes, double bfly)
+{
+    if (!c->prof_on) return;
+    cudaEvent_t a = prof_event(c), b = prof_event(c);
+    cudaEventRecord(a, c->stream);
+    c->prof_rec.push_back({a, b});
+    c->prof_rec_cls.push_back(cls);
+    c->prof_rec_bytes.push_back(bytes);
+    c->prof_rec_bfly.push_back(bfly);
+}
+
+void prof_end(fhe_ctx *c)
+{
+    if (!c->prof_on || c->prof_rec.empty()) return;
+    cudaEventRecord(c->prof_rec.back().second, c->stream);
+}
+
+extern "C" int fhe_ctx_profile(fhe_ctx *c, int on)
+{
+    if (!c) return FHE_EINVAL;
+    c->prof_on = on != 0;
+    return 0;
+}
+
+extern "C" int fhe_ctx_profile_read(fhe_ctx *c, double *ms, int64_t *count, double *bytes, double *bfly, int ncls)
+{
+    if (!c || ncls < 0) return FHE_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FHE_ECUDA;
+    for (int i = 0; i < ncls; i++) {
+        if (ms) ms[i] = 0;
+        if (count) count[i] = 0;
+        if (bytes) bytes[i] = 0;
+        if (bfly) bfly[i] = 0;
+    }
+    for (size_t r = 0; r < c->prof_rec.size(); r++) {
+        float t = 0;
+        cudaEventElapsedTime(&t, c->prof_rec[r].first, c->prof_rec[r].second);
+        const int k = c->prof_rec_cls[r];
+        if (k >= 0 && k < ncls) {
+            if (ms) ms[k] += t;
+            if (count) count[k] += 1;
+            if (bytes) bytes[k] += c->prof_rec_bytes[r];
+            if (bfly) bfly[k] += c->prof_rec_bfly[r];
+        }
+        c->prof_events.push_back(c->prof_rec[r].first);
+        c->prof_events.push_back(c->prof_rec[r].second);
+    }
+    c->prof_rec.clear();
+    c->prof_rec_cls.clear();
+    c->prof_rec_bytes.clear();
+    c->prof_rec_bfly.clear();
+    return FHE_K_COUNT;
 }

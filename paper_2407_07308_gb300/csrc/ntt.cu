@@ -8,26 +8,33 @@
 //            twiddle psi^brv(2^s + (j >> (logN - s)));
 //   inverse  the stages undone in reverse order with psi^-brv(.), then N^-1.
 //
-// GB300 mapping: one CTA per limb, N/32 threads, every thread keeps 32
-// residues in registers.  The logN stages are split into 2-3 rounds of up to
-// five stages; within a round each thread runs all butterflies of its groups
-// of 2^R elements in registers, and the rounds exchange data through shared
-// memory (padded by one word per 32 so every round's access pattern is
-// bank-conflict free).  The first forward round reads global memory directly
-// in coalesced strided order, and the last inverse round writes it the same
-// way; the other end goes through shared memory so global accesses are always
-// coalesced.  Butterflies are Harvey's lazy ones (values in [0,4q) forward,
-// [0,2q) inverse) with Shoup twiddles.
+// GB300 mapping: N = 2^n is split as 2^n1 x 2^n2 (n1 = ceil(n/2)).  The
+// forward transform is two kernels: "columns" runs global stages 0..n1-1,
+// which only combine residues j = e 2^n2 + lo of one column lo, and "rows"
+// runs stages n1..n-1 inside contiguous rows of 2^n2 residues.  Each is a
+// sub-transform of size 2^M (M = n1 or n2) whose twiddles are entries of the
+// full table: at local stage u, element e of a sub-transform with block index
+// hi uses psi^brv(2^(S+u) + hi 2^u + (e >> (M-u))), S its first global stage.
+// A CTA holds 16 sub-transforms in shared memory ([16][2^M], padded), every
+// thread 16 residues in registers; a sub-transform runs as one radix-16 round
+// (4 stages, strided residues) and one round of the remaining M-4 stages
+// (contiguous blocks), with shared-memory exchanges in between.  Global
+// memory is always read and written in coalesced runs of 16 residues or more
+// (128 B).  The inverse runs the same kernels in reverse order (rows first),
+// undoing stages n-1..0.  ~17 KB of shared memory and 128 threads per CTA
+// (n = 14) leave room for many CTAs per SM; N up to 2^16 needs no cluster.
+// Butterflies are Harvey's lazy ones (values in [0,4q) forward, [0,2q)
+// inverse) with Shoup twiddles.
 //
 // Load/store functors let one kernel body serve the plain transform and the
 // fused variants: ModUp (basis conversion of a key-switching digit computed
 // while loading, then NTT), ModDown and modulus switching (correction
-// computed while loading, subtract-and-scale applied while storing).
+// computed while loading, subtract-and-scale applied while storing).  The
+// half-transformed limb between the two kernels lives in the job's output
+// limb.
 #include "fhe_internal.h"
 
 namespace {
-
-__device__ __forceinline__ int padi(int j) { return j + (j >> 5); }
 
 __device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 q, u64 q2)
 {
@@ -86,99 +93,173 @@ __device__ __forceinline__ void inv_round(u64 (&x)[1 << R], int s0, int hi, cons
     }
 }
 
-// One round held in shared memory: groups j = hi 2^(LOGN-S0) + e 2^LOB + lo.
-template <int LOGN, int S0, int R, bool FWD>
-__device__ __forceinline__ void smem_round(u64 *sm, int tid, const ulonglong2 *__restrict__ W, u64 q, u64 q2)
+// ---------------------------------------------------------------------------
+// 16 sub-transforms of size 2^M in shared memory
+// ---------------------------------------------------------------------------
+
+// smem layout: sub-transform c at c*P(M), element e at e + (e >> 4); P is odd
+// mod 16 in u64 units, so the strided, blocked and row-wise access patterns
+// below all spread over the banks.
+template <int M>
+struct Sub {
+    static constexpr int SZ = 1 << M;                 // elements per sub-transform
+    static constexpr int G = SZ / 16;                 // threads per sub-transform
+    static constexpr int T = 16 * G;                  // threads per CTA
+    static constexpr int R2 = M - 4;                  // stages of the second round
+    static constexpr int P = SZ + SZ / 16 + 1;        // padded stride
+    static constexpr int WORDS = 16 * P;              // shared memory words
+    static_assert(M >= 5 && M <= 8, "sub-transform size");
+    __device__ static int at(int c, int e) { return c * P + e + (e >> 4); }
+};
+
+// Round 1: thread t = (g, c) with c = t % 16, g = t / 16 holds elements
+// e = k G + g (k < 16) of sub-transform c: local stages 0..3.
+// Round 2: thread t = (c, g') with c = t / G, g' = t % G holds the 16/G
+// blocks b = g' (16/G) + i of G contiguous elements: local stages 4..M-1.
+// hi of sub-transform c is hi0 + c * hstep.
+template <int M, bool FWD>
+__device__ __forceinline__ void sub16(u64 *sm, int tid, const ulonglong2 *__restrict__ W, int S, int hi0, int hstep,
+                                      u64 q, u64 q2)
 {
-    constexpr int N = 1 << LOGN, T = N / 32, E = 1 << R, G = N / E, PER = G / T;
-    constexpr int LOB = LOGN - S0 - R;
+    using C = Sub<M>;
+    constexpr int G = C::G, R2 = C::R2, NB = 16 / G;
+    auto round1 = [&]() {
+        const int c = tid & 15, g = tid >> 4;
+        const int hi = hi0 + c * hstep;
+        u64 x[16];
 #pragma unroll
-    for (int gi = 0; gi < PER; gi++) {
-        const int g = tid + gi * T;
-        const int hi = g >> LOB, lo = g & ((1 << LOB) - 1);
-        const int base = (hi << (LOGN - S0)) + lo;
-        u64 x[E];
-#pragma unroll
-        for (int e = 0; e < E; e++) x[e] = sm[padi(base + (e << LOB))];
+        for (int k = 0; k < 16; k++) x[k] = sm[C::at(c, k * G + g)];
         if (FWD)
-            fwd_round<R>(x, S0, hi, W, q, q2);
+            fwd_round<4>(x, S, hi, W, q, q2);
         else
-            inv_round<R>(x, S0, hi, W, q, q2);
+            inv_round<4>(x, S, hi, W, q, q2);
 #pragma unroll
-        for (int e = 0; e < E; e++) sm[padi(base + (e << LOB))] = x[e];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// forward kernel: rounds R0, R1, R2 (R2 may be 0)
-// ---------------------------------------------------------------------------
-template <int LOGN, int R0, int R1, int R2, class IO>
-__global__ void __launch_bounds__((1 << LOGN) / 32)
-    k_ntt_fwd(const IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
-{
-    constexpr int N = 1 << LOGN, T = N / 32;
-    static_assert(R0 + R1 + R2 == LOGN, "rounds must cover every stage");
-    extern __shared__ u64 sm[];
-    const int tid = threadIdx.x;
-    const typename IO::St st = io.begin(blockIdx.x, N);
-    const u64 q = mq[st.prime].q, q2 = 2 * q;
-    const ulonglong2 *W = tw + (size_t)st.prime * N;
-    {
-        constexpr int E = 1 << R0, G = N / E, PER = G / T;
+        for (int k = 0; k < 16; k++) sm[C::at(c, k * G + g)] = x[k];
+    };
+    auto round2 = [&]() {
+        const int c = tid / G, gp = tid % G;
+        const int hi = hi0 + c * hstep;
 #pragma unroll
-        for (int gi = 0; gi < PER; gi++) {
-            const int lo = tid + gi * T;
-            u64 x[E];
+        for (int i = 0; i < NB; i++) {
+            const int b = gp * NB + i;
+            u64 x[1 << R2];
 #pragma unroll
-            for (int e = 0; e < E; e++) x[e] = io.load(st, e * G + lo);
-            fwd_round<R0>(x, 0, 0, W, q, q2);
+            for (int f = 0; f < (1 << R2); f++) x[f] = sm[C::at(c, b * G + f)];
+            if (FWD)
+                fwd_round<R2>(x, S + 4, hi * 16 + b, W, q, q2);
+            else
+                inv_round<R2>(x, S + 4, hi * 16 + b, W, q, q2);
 #pragma unroll
-            for (int e = 0; e < E; e++) sm[padi(e * G + lo)] = x[e];
+            for (int f = 0; f < (1 << R2); f++) sm[C::at(c, b * G + f)] = x[f];
         }
-    }
-    __syncthreads();
-    smem_round<LOGN, R0, R1, true>(sm, tid, W, q, q2);
-    if constexpr (R2 > 0) {
+    };
+    if (FWD) {
+        round1();
         __syncthreads();
-        smem_round<LOGN, R0 + R1, R2, true>(sm, tid, W, q, q2);
+        round2();
+    } else {
+        round2();
+        __syncthreads();
+        round1();
     }
-    __syncthreads();
-    for (int k = tid; k < N; k += T) io.store(st, k, reduce4q(sm[padi(k)], q2, q));
 }
 
-template <int LOGN, int R0, int R1, int R2, class IO>
-__global__ void __launch_bounds__((1 << LOGN) / 32)
-    k_ntt_inv(const IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw,
-              const ulonglong2 *__restrict__ ninv)
+// ---------------------------------------------------------------------------
+// kernels.  Grid: one CTA per (job, block of 16 columns / rows).
+// ---------------------------------------------------------------------------
+
+// Forward, columns: global stages 0..N1-1 on columns lo0..lo0+15.
+template <int N1, int N2, class IO>
+__global__ void __launch_bounds__(Sub<N1>::T)
+    k_fwd_cols(const IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
 {
-    constexpr int N = 1 << LOGN, T = N / 32;
-    static_assert(R0 + R1 + R2 == LOGN, "rounds must cover every stage");
-    extern __shared__ u64 sm[];
-    const int tid = threadIdx.x;
-    const typename IO::St st = io.begin(blockIdx.x, N);
+    using C = Sub<N1>;
+    constexpr int NN = 1 << (N1 + N2), BLK = (1 << N2) / 16;
+    __shared__ u64 sm[C::WORDS];
+    const int job = blockIdx.x / BLK, lo0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
+    const typename IO::St st = io.begin(job, NN);
     const u64 q = mq[st.prime].q, q2 = 2 * q;
-    const ulonglong2 *W = tw + (size_t)st.prime * N;
+    const ulonglong2 *W = tw + (size_t)st.prime * NN;
+    for (int r = tid; r < 16 * C::SZ; r += C::T) {
+        const int c = r & 15, e = r >> 4;
+        sm[C::at(c, e)] = io.load(st, (e << N2) + lo0 + c);
+    }
+    __syncthreads();
+    sub16<N1, true>(sm, tid, W, 0, 0, 0, q, q2);
+    __syncthreads();
+    u64 *mid = io.inter(st);
+    for (int r = tid; r < 16 * C::SZ; r += C::T) {
+        const int c = r & 15, e = r >> 4;
+        mid[(e << N2) + lo0 + c] = sm[C::at(c, e)];
+    }
+}
+
+// Forward, rows: global stages N1..N1+N2-1 on rows hi0..hi0+15.
+template <int N1, int N2, class IO>
+__global__ void __launch_bounds__(Sub<N2>::T)
+    k_fwd_rows(const IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
+{
+    using C = Sub<N2>;
+    constexpr int NN = 1 << (N1 + N2), BLK = (1 << N1) / 16;
+    __shared__ u64 sm[C::WORDS];
+    const int job = blockIdx.x / BLK, hi0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
+    const typename IO::St st = io.begin(job, NN);
+    const u64 q = mq[st.prime].q, q2 = 2 * q;
+    const ulonglong2 *W = tw + (size_t)st.prime * NN;
+    const u64 *mid = io.inter(st) + ((size_t)hi0 << N2);
+    for (int r = tid; r < 16 * C::SZ; r += C::T) sm[C::at(r >> N2, r & (C::SZ - 1))] = mid[r];
+    __syncthreads();
+    sub16<N2, true>(sm, tid, W, N1, hi0, 1, q, q2);
+    __syncthreads();
+    for (int r = tid; r < 16 * C::SZ; r += C::T)
+        io.store(st, (hi0 << N2) + r, reduce4q(sm[C::at(r >> N2, r & (C::SZ - 1))], q2, q));
+}
+
+// Inverse, rows first: undoes global stages N1+N2-1..N1.
+template <int N1, int N2, class IO>
+__global__ void __launch_bounds__(Sub<N2>::T)
+    k_inv_rows(const IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
+{
+    using C = Sub<N2>;
+    constexpr int NN = 1 << (N1 + N2), BLK = (1 << N1) / 16;
+    __shared__ u64 sm[C::WORDS];
+    const int job = blockIdx.x / BLK, hi0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
+    const typename IO::St st = io.begin(job, NN);
+    const u64 q = mq[st.prime].q, q2 = 2 * q;
+    const ulonglong2 *W = tw + (size_t)st.prime * NN;
+    for (int r = tid; r < 16 * C::SZ; r += C::T) sm[C::at(r >> N2, r & (C::SZ - 1))] = io.load(st, (hi0 << N2) + r);
+    __syncthreads();
+    sub16<N2, false>(sm, tid, W, N1, hi0, 1, q, q2);
+    __syncthreads();
+    u64 *mid = io.inter(st) + ((size_t)hi0 << N2);
+    for (int r = tid; r < 16 * C::SZ; r += C::T) mid[r] = sm[C::at(r >> N2, r & (C::SZ - 1))];
+}
+
+// Inverse, columns: undoes global stages N1-1..0, then scales by N^-1.
+template <int N1, int N2, class IO>
+__global__ void __launch_bounds__(Sub<N1>::T)
+    k_inv_cols(const IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw,
+               const ulonglong2 *__restrict__ ninv)
+{
+    using C = Sub<N1>;
+    constexpr int NN = 1 << (N1 + N2), BLK = (1 << N2) / 16;
+    __shared__ u64 sm[C::WORDS];
+    const int job = blockIdx.x / BLK, lo0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
+    const typename IO::St st = io.begin(job, NN);
+    const u64 q = mq[st.prime].q, q2 = 2 * q;
+    const ulonglong2 *W = tw + (size_t)st.prime * NN;
     const ulonglong2 ni = ninv[st.prime];
-    for (int k = tid; k < N; k += T) sm[padi(k)] = io.load(st, k);
-    __syncthreads();
-    if constexpr (R2 > 0) {
-        smem_round<LOGN, R0 + R1, R2, false>(sm, tid, W, q, q2);
-        __syncthreads();
+    const u64 *mid = io.inter(st);
+    for (int r = tid; r < 16 * C::SZ; r += C::T) {
+        const int c = r & 15, e = r >> 4;
+        sm[C::at(c, e)] = mid[(e << N2) + lo0 + c];
     }
-    smem_round<LOGN, R0, R1, false>(sm, tid, W, q, q2);
     __syncthreads();
-    {
-        constexpr int E = 1 << R0, G = N / E, PER = G / T;
-#pragma unroll
-        for (int gi = 0; gi < PER; gi++) {
-            const int lo = tid + gi * T;
-            u64 x[E];
-#pragma unroll
-            for (int e = 0; e < E; e++) x[e] = sm[padi(e * G + lo)];
-            inv_round<R0>(x, 0, 0, W, q, q2);
-#pragma unroll
-            for (int e = 0; e < E; e++) io.store(st, e * G + lo, reduce2q(shoup_lazy(x[e], ni.x, ni.y, q), q));
-        }
+    sub16<N1, false>(sm, tid, W, 0, 0, 0, q, q2);
+    __syncthreads();
+    for (int r = tid; r < 16 * C::SZ; r += C::T) {
+        const int c = r & 15, e = r >> 4;
+        io.store(st, (e << N2) + lo0 + c, reduce2q(shoup_lazy(sm[C::at(c, e)], ni.x, ni.y, q), q));
     }
 }
 
@@ -206,6 +287,7 @@ struct IOPlain {
     }
     __device__ u64 load(const St &s, int i) const { return s.in[i]; }
     __device__ void store(const St &s, int i, u64 v) const { s.out[i] = v; }
+    __device__ u64 *inter(const St &s) const { return s.out; }
 };
 
 // ModUp: extended limb t of digit j of ct c, from the coefficient-domain
@@ -259,6 +341,7 @@ struct IOModUp {
         return barrett128(acc, s.mt);
     }
     __device__ void store(const St &s, int k, u64 v) const { s.dst[k] = v; }
+    __device__ u64 *inter(const St &s) const { return s.dst; }
     int stride;  // N
 };
 
@@ -325,6 +408,7 @@ struct IOModDown {
         if (s.add) r = addmod(r, s.add[k], q);
         s.out[k] = r;
     }
+    __device__ u64 *inter(const St &s) const { return s.out; }
 };
 
 // Modulus switch l -> l-1 of poly pi of ct c, limb i < l-1:
@@ -370,74 +454,76 @@ struct IOModSwitch {
     {
         s.out[k] = shoup(submod(s.in[k], v, s.q), s.qi, s.qis, s.q);
     }
+    __device__ u64 *inter(const St &s) const { return s.out; }
 };
 
+template <int N1, int N2, class IO>
+void fwd_pair(fhe_ctx *c, const IO &io, int njobs)
+{
+    k_fwd_cols<N1, N2, IO><<<njobs * ((1 << N2) / 16), Sub<N1>::T, 0, c->stream>>>(io, c->d_mq, c->d_fwd);
+    k_fwd_rows<N1, N2, IO><<<njobs * ((1 << N1) / 16), Sub<N2>::T, 0, c->stream>>>(io, c->d_mq, c->d_fwd);
+}
+
+template <int N1, int N2, class IO>
+void inv_pair(fhe_ctx *c, const IO &io, int njobs)
+{
+    k_inv_rows<N1, N2, IO><<<njobs * ((1 << N1) / 16), Sub<N2>::T, 0, c->stream>>>(io, c->d_mq, c->d_inv);
+    k_inv_cols<N1, N2, IO><<<njobs * ((1 << N2) / 16), Sub<N1>::T, 0, c->stream>>>(io, c->d_mq, c->d_inv,
+                                                                                    c->d_ninv);
+}
+
+// words_per_job: u64 words of global traffic per limb job (algorithmic: the
+// transform reads and writes each limb once; fused variants add their operands)
 template <class IO>
-void run_fwd(fhe_ctx *c, const IO &io, int njobs)
+void run_fwd(fhe_ctx *c, const IO &io, int njobs, int cls, double words_per_job = 2.0)
 {
     if (njobs <= 0) return;
-    const int N = c->N;
-    const size_t smem = sizeof(u64) * (N + N / 32);
+    prof_begin(c, cls, 8.0 * words_per_job * c->N * njobs, (double)njobs * (c->N / 2) * c->logN);
     switch (c->logN) {
-#define FWD_CASE(LG, A, B, C)                                                                       \
-    case LG: {                                                                                      \
-        auto k = k_ntt_fwd<LG, A, B, C, IO>;                                                        \
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);            \
-        k<<<njobs, (1 << LG) / 32, smem, c->stream>>>(io, c->d_mq, c->d_fwd);                       \
-        break;                                                                                      \
+    case 10: fwd_pair<5, 5>(c, io, njobs); break;
+    case 11: fwd_pair<6, 5>(c, io, njobs); break;
+    case 12: fwd_pair<6, 6>(c, io, njobs); break;
+    case 13: fwd_pair<7, 6>(c, io, njobs); break;
+    case 14: fwd_pair<7, 7>(c, io, njobs); break;
+    case 15: fwd_pair<8, 7>(c, io, njobs); break;
+    default: break;
     }
-        FWD_CASE(10, 5, 5, 0)
-        FWD_CASE(11, 4, 4, 3)
-        FWD_CASE(12, 4, 4, 4)
-        FWD_CASE(13, 5, 4, 4)
-        FWD_CASE(14, 5, 5, 4)
-#undef FWD_CASE
-    default:
-        break;
-    }
-    c->launches++;
+    prof_end(c);
+    c->launches += 2;
 }
 
 template <class IO>
-void run_inv(fhe_ctx *c, const IO &io, int njobs)
+void run_inv(fhe_ctx *c, const IO &io, int njobs, int cls, double words_per_job = 2.0)
 {
     if (njobs <= 0) return;
-    const int N = c->N;
-    const size_t smem = sizeof(u64) * (N + N / 32);
+    prof_begin(c, cls, 8.0 * words_per_job * c->N * njobs, (double)njobs * (c->N / 2) * c->logN);
     switch (c->logN) {
-#define INV_CASE(LG, A, B, C)                                                                       \
-    case LG: {                                                                                      \
-        auto k = k_ntt_inv<LG, A, B, C, IO>;                                                        \
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);            \
-        k<<<njobs, (1 << LG) / 32, smem, c->stream>>>(io, c->d_mq, c->d_inv, c->d_ninv);            \
-        break;                                                                                      \
+    case 10: inv_pair<5, 5>(c, io, njobs); break;
+    case 11: inv_pair<6, 5>(c, io, njobs); break;
+    case 12: inv_pair<6, 6>(c, io, njobs); break;
+    case 13: inv_pair<7, 6>(c, io, njobs); break;
+    case 14: inv_pair<7, 7>(c, io, njobs); break;
+    case 15: inv_pair<8, 7>(c, io, njobs); break;
+    default: break;
     }
-        INV_CASE(10, 5, 5, 0)
-        INV_CASE(11, 4, 4, 3)
-        INV_CASE(12, 4, 4, 4)
-        INV_CASE(13, 5, 4, 4)
-        INV_CASE(14, 5, 5, 4)
-#undef INV_CASE
-    default:
-        break;
-    }
-    c->launches++;
+    prof_end(c);
+    c->launches += 2;
 }
 
 }  // namespace
 
-bool ntt_supported_logn(int logN) { return logN >= 10 && logN <= 14; }
+bool ntt_supported_logn(int logN) { return logN >= 10 && logN <= 15; }
 
 void launch_ntt_fwd_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs)
 {
     IOPlain io{in, out, m};
-    run_fwd(c, io, njobs);
+    run_fwd(c, io, njobs, FHE_K_NTT_FWD);
 }
 
 void launch_ntt_inv_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs)
 {
     IOPlain io{in, out, m};
-    run_inv(c, io, njobs);
+    run_inv(c, io, njobs, FHE_K_NTT_INV);
 }
 
 void launch_ntt_modup(fhe_ctx *c, const u64 *d2c, u64 *ext, int level, int count)
@@ -453,7 +539,9 @@ void launch_ntt_modup(fhe_ctx *c, const u64 *d2c, u64 *ext, int level, int count
     io.dnum = P.dnum;
     io.njobs = P.njobs;
     io.stride = c->N;
-    run_fwd(c, io, P.njobs * count);
+    double words = 0;
+    for (int e = 0; e < P.njobs; e++) words += P.digit_n[P.job_digit[e]] + 1.0;
+    run_fwd(c, io, P.njobs * count, FHE_K_NTT_MODUP, words / P.njobs);
 }
 
 void launch_ntt_moddown(fhe_ctx *c, const u64 *accP, const u64 *acc, const u64 *abase, long long a_outer,
@@ -472,7 +560,9 @@ void launch_ntt_moddown(fhe_ctx *c, const u64 *accP, const u64 *acc, const u64 *
     io.l = level;
     io.K = c->K;
     io.stride = c->N;
-    run_fwd(c, io, 2 * level * count);
+    // reads K special limbs, acc_i and (for masked polys) the addend; writes out_i
+    const double add_frac = ((amask & 1) + ((amask >> 1) & 1)) / 2.0;
+    run_fwd(c, io, 2 * level * count, FHE_K_NTT_MODDOWN, c->K + 2.0 + add_frac);
 }
 
 void launch_ntt_modswitch(fhe_ctx *c, const u64 *last, const u64 *in, u64 *out, int level, int npoly, int count)
@@ -485,5 +575,5 @@ void launch_ntt_modswitch(fhe_ctx *c, const u64 *last, const u64 *in, u64 *out, 
     io.mq = c->d_mq;
     io.l = level;
     io.npoly = npoly;
-    run_fwd(c, io, npoly * (level - 1) * count);
+    run_fwd(c, io, npoly * (level - 1) * count, FHE_K_NTT_MODSWITCH, 3.0);
 }

@@ -109,6 +109,8 @@ def lib() -> ctypes.CDLL:
             "fhe_ntt_forward": (ci, [vp, vp, vp, ci]),
             "fhe_ntt_inverse": (ci, [vp, vp, vp, ci]),
             "fhe_selftest_modarith": (ci, [u64, u64, u64, ci, ci]),
+            "fhe_ctx_profile": (ci, [vp, ci]),
+            "fhe_ctx_profile_read": (ci, [vp, vp, vp, vp, vp, ci]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -408,6 +410,25 @@ def fhe_ntt_forward(ctx, dev_ptr: int, prime_idx, nlimbs: int):
 def fhe_ntt_inverse(ctx, dev_ptr: int, prime_idx, nlimbs: int):
     pi = np.ascontiguousarray(prime_idx, dtype=np.int32)
     _check(lib().fhe_ntt_inverse(ctx, c_void_p(dev_ptr), _ptr(pi), nlimbs), ctx)
+
+
+KERNEL_CLASSES = ["ntt_fwd", "ntt_inv", "ntt_modup", "ntt_moddown", "ntt_modswitch", "ks_inner", "tensor",
+                  "elementwise", "automorphism"]
+
+
+def fhe_ctx_profile(ctx, on: bool):
+    _check(lib().fhe_ctx_profile(ctx, 1 if on else 0), ctx)
+
+
+def fhe_ctx_profile_read(ctx):
+    """{class: (ms, launches, algorithmic bytes, butterflies)} since the last read."""
+    n = len(KERNEL_CLASSES)
+    ms = np.zeros(n, dtype=np.float64)
+    cnt = np.zeros(n, dtype=np.int64)
+    by = np.zeros(n, dtype=np.float64)
+    bf = np.zeros(n, dtype=np.float64)
+    _check(lib().fhe_ctx_profile_read(ctx, _ptr(ms), _ptr(cnt), _ptr(by), _ptr(bf), n), ctx)
+    return {k: (float(ms[i]), int(cnt[i]), float(by[i]), float(bf[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
 
 def fhe_selftest_modarith(prime_mod, prime_lo, prime_hi, nprimes, iters) -> int:
