@@ -226,6 +226,24 @@ int fhe_trace_get(const fhe_ctx *ctx, int32_t *ops, int32_t *levels, int cap);
 int fhe_ntt_forward(fhe_ctx *ctx, uint64_t *data, const int32_t *prime_idx, int nlimbs);
 int fhe_ntt_inverse(fhe_ctx *ctx, uint64_t *data, const int32_t *prime_idx, int nlimbs);
 
+/* ---- modulus switching without allocation -------------------------------------- */
+
+/* No counterpart in the paper.  For callers that cannot allocate device
+ * memory -- a host framework that owns all of it and lends fixed buffers, or
+ * a loop that must not pay for a cudaMalloc -- one modulus switch
+ * level -> level-1 of caller-owned device buffers:
+ *   in  = uint64[count][npoly][level][N]    (NTT domain, read only)
+ *   out = uint64[count][npoly][level-1][N]  (NTT domain, must not overlap in)
+ * with npoly 2 or 3 and 2 <= level <= L.  Its only temporary is a fixed
+ * device array of 2^20 words (8 MiB) inside the library, held on every device
+ * that loads the library until the process exits; count*npoly*N above 2^20
+ * fails with FHE_EINVAL.  It calls no allocator.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and should come
+ * before any stream capture.  All calls share the array, so calls whose GPU
+ * work overlaps (other streams or contexts on the same device) race and must
+ * be serialised by the caller.  The result equals fhe_mod_switch(.., level-1). */
+int fhe_mod_switch_noalloc(fhe_ctx *ctx, const uint64_t *in, uint64_t *out, int count, int npoly, int level);
+
 /* ---- kernel timing ------------------------------------------------------------- */
 
 /* Kernel classes timed by fhe_ctx_profile_read. */

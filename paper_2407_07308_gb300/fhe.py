@@ -110,6 +110,7 @@ def lib() -> ctypes.CDLL:
             "fhe_ntt_inverse": (ci, [vp, vp, vp, ci]),
             "fhe_selftest_modarith": (ci, [u64, u64, u64, ci, ci]),
             "fhe_ctx_profile": (ci, [vp, ci]),
+            "fhe_mod_switch_noalloc": (ci, [vp, vp, vp, ci, ci, ci]),
             "fhe_ctx_profile_read": (ci, [vp, vp, vp, vp, vp, ci]),
         }
         for name, (res, args) in sig.items():
@@ -410,6 +411,12 @@ def fhe_ntt_forward(ctx, dev_ptr: int, prime_idx, nlimbs: int):
 def fhe_ntt_inverse(ctx, dev_ptr: int, prime_idx, nlimbs: int):
     pi = np.ascontiguousarray(prime_idx, dtype=np.int32)
     _check(lib().fhe_ntt_inverse(ctx, c_void_p(dev_ptr), _ptr(pi), nlimbs), ctx)
+
+
+def fhe_mod_switch_noalloc(ctx, in_ptr: int, out_ptr: int, count: int, npoly: int, level: int):
+    """Modulus switch of caller-owned device buffers (raw device addresses),
+    for callers that cannot allocate device memory; see include/fhe.h."""
+    _check(lib().fhe_mod_switch_noalloc(ctx, c_void_p(in_ptr), c_void_p(out_ptr), count, npoly, level), ctx)
 
 
 KERNEL_CLASSES = ["ntt_fwd", "ntt_inv", "ntt_modup", "ntt_moddown", "ntt_modswitch", "ks_inner", "tensor",
