@@ -255,23 +255,20 @@ def run_gpu(args):
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
-    def step():
-        lt, eq = fhe.fhe_compare(ctx, evk, xs, ys)
-        fhe.fhe_ct_destroy(lt)
-        fhe.fhe_ct_destroy(eq)
-
-    # correctness of the timed configuration
-    lt, eq = fhe.fhe_compare(ctx, evk, xs, ys)
-    ltd, eqd = fhe.fhe_decrypt(ctx, sk, lt), fhe.fhe_decrypt(ctx, sk, eq)
+    # ---- batched form: the whole 16-pair comparison as one captured graph ----
+    plan = fhe.fhe_compare_plan(ctx, evk, xs, ys)
+    outs = [fhe.fhe_plan_result(plan, 0), fhe.fhe_plan_result(plan, 1)]
+    fhe.fhe_plan_run(plan, ctx)
+    ltd, eqd = fhe.fhe_decrypt(ctx, sk, outs[0]), fhe.fhe_decrypt(ctx, sk, outs[1])
     assert (ltd == (xv < yv)).all() and (eqd == (xv == yv)).all(), "batched result mismatch"
-    fhe.fhe_ct_destroy(lt)
-    fhe.fhe_ct_destroy(eq)
+
+    def step():
+        fhe.fhe_plan_run(plan, ctx)
 
     for _ in range(args.warmup):
         step()
     fhe.fhe_ctx_sync(ctx)
 
-    # ---- timed region: batched form ---------------------------------------
     evs = [ev() for _ in range(args.steps + 1)]
     barrier()
     torch.cuda.synchronize()
@@ -294,29 +291,33 @@ def run_gpu(args):
     ms_per_step = total_ms / args.steps
     value = world * pairs * ns * args.steps / (total_ms / 1e3)
 
-    # ---- per-kernel device time over a second, profiled pass ----------------
+    # ---- per-kernel device time: a second capture with an event pair around
+    # every kernel (event-record nodes in the graph), replayed K times; the
+    # events hold the last replay's times ------------------------------------
     fhe.fhe_ctx_profile(ctx, True)
+    pplan = fhe.fhe_compare_plan(ctx, evk, xs, ys)
+    fhe.fhe_ctx_profile(ctx, False)
     pe0, pe1 = ev(), ev()
     pe0.record(stream)
     for _ in range(args.steps):
-        step()
+        fhe.fhe_plan_run(pplan, ctx)
     pe1.record(stream)
-    prof = fhe.fhe_ctx_profile_read(ctx)
-    fhe.fhe_ctx_profile(ctx, False)
+    prof = fhe.fhe_ctx_profile_read(ctx)  # one replay's worth of records
     stream.synchronize()
     prof_ms_per_step = pe0.elapsed_time(pe1) / args.steps
+    fhe.fhe_plan_destroy(pplan)
     dom = max(prof, key=lambda k: prof[k][0])
     ms_k, n_k, by_k, bf_k = prof[dom]
     hbm_peak, peak_kind = peaks()
     achieved = by_k / (ms_k / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(achieved / hbm_peak, 4), "peak_source": peak_kind, "traffic": None,
-            "launches": n_k, "avg_launch_us": round(1e3 * ms_k / max(n_k, 1), 2),
+            "launches_per_step": n_k, "avg_launch_us": round(1e3 * ms_k / max(n_k, 1), 2),
             "algorithmic_bytes_per_launch": round(by_k / max(n_k, 1)),
             "share_of_step": round(ms_k / sum(v[0] for v in prof.values()), 3)}
     if bf_k:
         roof["butterflies_per_s"] = bf_k / (ms_k / 1e3)
-    kernels = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches_per_step": v[1] // args.steps,
+    kernels = {k: {"ms_per_step": round(v[0], 3), "launches_per_step": v[1],
                    "GBps": round(v[2] / (v[0] / 1e3) / 1e9, 1) if v[0] else 0.0}
                for k, v in prof.items() if v[1]}
 
@@ -332,7 +333,7 @@ def run_gpu(args):
     # ---- end to end through the C ABI with host buffers -------------------
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(fhe, ctx, evk, xs, ys, pairs, ns, N, args, world, barrier)
+        e2e = run_e2e(fhe, ctx, plan, outs, xs, ys, pairs, ns, N, args, world, barrier)
 
     clocks = clk.summary()
     res, used = fhe.fhe_ctx_memory(ctx)
@@ -340,7 +341,9 @@ def run_gpu(args):
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded BGV keys, noise and values)",
-        "config": dict(CONFIG, parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "config": dict(CONFIG, parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                       batched_form="one CUDA graph per 16-pair batch (fhe_compare_plan)",
+                       plain_form="one request at a time, op-by-op launches, no graph"),
         "plain": None if plain_value is None else {
             "value": round(plain_value, 2), "unit": UNIT, "ms_per_request_p50": round(pct(lat, 0.5), 3),
             "ms_per_request_p99": round(pct(lat, 0.99), 3)},
@@ -351,6 +354,7 @@ def run_gpu(args):
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         "memory_gb": {"pool_reserved": round(res / 1e9, 2)},
     }
+    fhe.fhe_plan_destroy(plan)
     for h in xs + ys + [c for x in xs1 + ys1 for c in x]:
         fhe.fhe_ct_destroy(h)
     fhe.fhe_evk_destroy(evk)
@@ -389,13 +393,15 @@ def run_plain(fhe, ctx, evk, xd, yd, enc_each, pairs, ns, stream, ev):
     return pairs * ns / (plain_total / 1e3), lat, xs1, ys1
 
 
-def run_e2e(fhe, ctx, evk, xs, ys, pairs, ns, N, args, world, barrier):
-    """Host ciphertexts in (pinned), compare, host ciphertexts out, per step."""
+def run_e2e(fhe, ctx, plan, outs, xs, ys, pairs, ns, N, args, world, barrier):
+    """Per step: host ciphertexts (pinned) into the plan's input handles,
+    one replay, both results back to pinned host memory."""
     import numpy as np
     import torch
 
+    handles = xs + ys
     host_in = []
-    for h in xs + ys:
+    for h in handles:
         a = fhe.fhe_ct_export_coeff(ctx, h)
         pinned = torch.empty(a.shape, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
         pinned[...] = a
@@ -407,15 +413,11 @@ def run_e2e(fhe, ctx, evk, xs, ys, pairs, ns, N, args, world, barrier):
     bo = sum(a.nbytes for a in host_out)
 
     def e2e_step():
-        hs = [fhe.fhe_ct_import_coeff(ctx, a) for a in host_in]
-        d = W["d"]
-        lt, eq = fhe.fhe_compare(ctx, evk, hs[:d], hs[d:])
-        for h, buf in ((lt, host_out[0]), (eq, host_out[1])):
-            assert fhe.fhe_ct_shape(h) == (pairs, 2, 1)
+        for h, a in zip(handles, host_in):
+            fhe._check(fhe.lib().fhe_ct_load_coeff(ctx, h, fhe._ptr(a)), ctx)
+        fhe.fhe_plan_run(plan, ctx)
+        for h, buf in zip(outs, host_out):
             fhe._check(fhe.lib().fhe_ct_export_coeff(ctx, h, fhe._ptr(buf)), ctx)
-            fhe.fhe_ct_destroy(h)
-        for h in hs:
-            fhe.fhe_ct_destroy(h)
 
     e2e_step()
     torch.cuda.synchronize()

@@ -155,6 +155,11 @@ int fhe_ct_shape(const fhe_ct *ct, int *count, int *npoly, int *level);
 /* Coefficient-domain residues, host uint64[count][npoly][level][N].  Synchronises. */
 int fhe_ct_export_coeff(fhe_ctx *ctx, const fhe_ct *ct, uint64_t *host);
 int fhe_ct_import_coeff(fhe_ctx *ctx, const uint64_t *host, int count, int npoly, int level, fhe_ct **out);
+/* Overwrites an existing ciphertext batch in place from host coefficient-domain
+ * residues of its own shape (uint64[count][npoly][level][N]); asynchronous on
+ * the context's stream (host must stay valid until the stream reaches it).
+ * This is how new inputs reach a captured plan (fhe_compare_plan). */
+int fhe_ct_load_coeff(fhe_ctx *ctx, fhe_ct *ct, const uint64_t *host);
 
 /* ---- arithmetic (Sec. 2.1: add, mult, rotate; Sec. 2.2: RNS, NTT) -------- */
 
@@ -206,6 +211,26 @@ int fhe_max(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, const fhe_
             fhe_ct **out);
 int fhe_min(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
             fhe_ct **out);
+
+/* ---- captured batches (CUDA graphs) -------------------------------------------- */
+
+typedef struct fhe_plan fhe_plan;
+
+/* Records fhe_compare(x, y) (the LT and/or EQ outputs selected by want_lt /
+ * want_eq) as one CUDA graph on the context's stream: one warm run, then a
+ * capture.  The plan owns its outputs and every temporary the graph reuses;
+ * x and y stay bound to the plan (the caller keeps them alive and may
+ * overwrite their contents between runs).  Synchronises. */
+int fhe_compare_plan(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                     int want_lt, int want_eq, fhe_plan **out);
+/* Enqueues one replay of the recorded comparison on the context's stream. */
+int fhe_plan_run(fhe_plan *plan);
+/* Borrowed handle of output `which` (0 = LT, 1 = EQ), valid until the plan is
+ * destroyed; each run overwrites it. */
+int fhe_plan_result(const fhe_plan *plan, int which, const fhe_ct **out);
+/* Kernel nodes in the recorded graph. */
+int fhe_plan_nodes(const fhe_plan *plan);
+void fhe_plan_destroy(fhe_plan *plan);
 
 /* ---- operation trace --------------------------------------------------------- */
 

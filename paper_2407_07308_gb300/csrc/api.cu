@@ -25,6 +25,14 @@ int fhe_cuda_check(fhe_ctx *ctx, cudaError_t e, const char *where)
 
 void *Pool::get(size_t bytes, int *err)
 {
+    if (cap_free) {
+        auto &cf = (*cap_free)[bytes];
+        if (!cf.empty()) {
+            void *p = cf.back();
+            cf.pop_back();
+            return p;  // still counted in in_use
+        }
+    }
     auto &fl = free_lists[bytes];
     if (!fl.empty()) {
         void *p = fl.back();
@@ -74,6 +82,10 @@ void Pool::put(void *p)
 {
     auto it = live.find(p);
     if (it == live.end()) return;
+    if (cap_free) {  // a graph being captured keeps using this block on every replay
+        (*cap_free)[it->second].push_back(p);
+        return;
+    }
     free_lists[it->second].push_back(p);
     in_use -= it->second;
 }
@@ -588,6 +600,16 @@ extern "C" int fhe_decrypt(fhe_ctx *c, const fhe_sk *sk, const fhe_ct *ct, uint6
     return 0;
 }
 
+extern "C" int fhe_ct_load_coeff(fhe_ctx *c, fhe_ct *ct, const uint64_t *host)
+{
+    CHECK_CTX(c);
+    if (!ct || ct->ctx != c || !host) return FHE_EINVAL;
+    LOCK(c);
+    cudaMemcpyAsync(ct->d, host, ct->bytes, cudaMemcpyHostToDevice, c->stream);
+    ntt_blocks(c, ct->d, ct->d, ct->count * ct->npoly, ct->level, 0, false);
+    return fhe_cuda_check(c, cudaGetLastError(), "load_coeff");
+}
+
 extern "C" void fhe_ct_destroy(fhe_ct *ct)
 {
     if (!ct) return;
@@ -971,4 +993,106 @@ extern "C" int fhe_encrypt(fhe_ctx *c, const fhe_pk *pk, const uint64_t *slots, 
 {
     (void)pk; (void)slots; (void)count; (void)seed; (void)out;
     return c ? fhe_fail(c, FHE_EUNSUPPORTED, "seeded encrypt not available yet") : FHE_EINVAL;
+}
+
+// ---------------------------------------------------------------------------
+// captured comparison plans (CUDA graphs)
+// ---------------------------------------------------------------------------
+
+extern "C" int fhe_compare_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y,
+                                int d, int want_lt, int want_eq, fhe_plan **out)
+{
+    CHECK_CTX(c);
+    if (!out || (!want_lt && !want_eq)) return FHE_EINVAL;
+    int e = check_digits(c, evk, x, y, d);
+    if (e) return e;
+    LOCK(c);
+    // warm run: fills the pool with every block size the circuit needs and
+    // builds any lazily created table, so the captured run allocates nothing
+    const bool prof = c->prof_on, tr = c->tracing;
+    c->prof_on = false;
+    c->tracing = false;
+    {
+        fhe_ct *lt = nullptr, *eq = nullptr;
+        e = circuit_compare(c, evk, x, y, d, want_lt ? &lt : nullptr, want_eq ? &eq : nullptr);
+        fhe_ct_destroy(lt);
+        fhe_ct_destroy(eq);
+        if (!e) e = sync_check(c, "plan warm-up");
+        if (e) {
+            c->prof_on = prof;
+            c->tracing = tr;
+            return e;
+        }
+    }
+    fhe_plan *P = new fhe_plan;
+    P->ctx = c;
+    // with profiling on, the per-kernel event pairs become event-record nodes
+    // of the graph and hold the times of the latest replay
+    c->prof_on = prof;
+    c->pool.cap_free = &P->held;
+    // record on a private stream (the legacy NULL stream cannot be captured);
+    // the graph is launched on the context's stream, whatever it is
+    cudaStream_t user = c->stream, cap = nullptr;
+    e = fhe_cuda_check(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+    if (!e) {
+        c->stream = cap;
+        c->pool.stream = cap;
+        e = fhe_cuda_check(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed), "begin capture");
+        if (!e) {
+            e = circuit_compare(c, evk, x, y, d, want_lt ? &P->out[0] : nullptr, want_eq ? &P->out[1] : nullptr);
+            cudaGraph_t g = nullptr;
+            const int e2 = fhe_cuda_check(c, cudaStreamEndCapture(cap, &g), "end capture");
+            if (!e) e = e2;
+            P->graph = g;
+        }
+        c->stream = user;
+        c->pool.stream = user;
+        cudaStreamDestroy(cap);
+    }
+    c->pool.cap_free = nullptr;
+    c->prof_on = prof;
+    c->tracing = tr;
+    if (!e) e = fhe_cuda_check(c, cudaGraphInstantiate(&P->exec, P->graph, 0), "graph instantiate");
+    if (!e) {
+        size_t n = 0;
+        cudaGraphGetNodes(P->graph, nullptr, &n);
+        P->nodes = (int)n;
+    }
+    if (e) {
+        fhe_plan_destroy(P);
+        return e;
+    }
+    *out = P;
+    return 0;
+}
+
+extern "C" int fhe_plan_run(fhe_plan *P)
+{
+    if (!P || !P->exec) return FHE_EINVAL;
+    fhe_ctx *c = P->ctx;
+    LOCK(c);
+    c->launches += P->nodes;
+    return fhe_cuda_check(c, cudaGraphLaunch(P->exec, c->stream), "graph launch");
+}
+
+extern "C" int fhe_plan_result(const fhe_plan *P, int which, const fhe_ct **out)
+{
+    if (!P || !out || which < 0 || which > 1 || !P->out[which]) return FHE_EINVAL;
+    *out = P->out[which];
+    return 0;
+}
+
+extern "C" int fhe_plan_nodes(const fhe_plan *P) { return P ? P->nodes : FHE_EINVAL; }
+
+extern "C" void fhe_plan_destroy(fhe_plan *P)
+{
+    if (!P) return;
+    fhe_ctx *c = P->ctx;
+    cudaStreamSynchronize(c->stream);
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    for (int i = 0; i < 2; i++) fhe_ct_destroy(P->out[i]);
+    for (auto &kv : P->held)
+        for (void *p : kv.second) c->pool.put(p);
+    delete P;
 }

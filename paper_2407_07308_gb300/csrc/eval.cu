@@ -83,8 +83,9 @@ int op_modswitch1(fhe_ctx *c, const fhe_ct *a, fhe_ct **out)
         return err;
     }
     const int outer = a->count * a->npoly;
+    // last = [x_{l-1} p^-1]_{q_{l-1}} in the coefficient domain
     LimbMap m = identity_map(1, (long long)l * N, N, l - 1, 0, l - 1);
-    launch_ntt_inv_plain(c, a->d, last.p, m, outer);
+    launch_ntt_inv_scaled(c, a->d, last.p, m, &c->ms_lastscale[l], outer);
     launch_ntt_modswitch(c, last.p, a->d, r->d, l, a->npoly, a->count);
     *out = r;
     return 0;
@@ -171,6 +172,31 @@ int op_add_const(fhe_ctx *c, const fhe_ct *a, int64_t k, fhe_ct **out)
     return 0;
 }
 
+// sum_t k_t x_t for n <= 8 batches of one shape, constants lifted to (-p/2, p/2]
+int op_lincomb(fhe_ctx *c, const fhe_ct *const *x, const int64_t *k, int n, fhe_ct **out)
+{
+    if (n < 1 || n > 8) return fhe_fail(c, FHE_EINVAL, "lincomb: 1..8 terms");
+    for (int t = 1; t < n; t++)
+        if (x[t]->level != x[0]->level || x[t]->count != x[0]->count || x[t]->npoly != x[0]->npoly)
+            return fhe_fail(c, FHE_EMISMATCH, "lincomb: shapes differ");
+    int err = 0;
+    fhe_ct *r = ct_new(c, x[0]->count, x[0]->npoly, x[0]->level, &err);
+    if (!r) return err;
+    const u64 *ptr[8];
+    u64 w[8][FHE_MAXP];
+    for (int t = 0; t < n; t++) {
+        ptr[t] = x[t]->d;
+        const int64_t kc = centred_const(c, k[t]);
+        for (int i = 0; i < x[0]->level; i++) {
+            const u64 q = c->q[i];
+            w[t][i] = kc >= 0 ? (u64)kc % q : (q - ((u64)(-kc) % q)) % q;
+        }
+    }
+    launch_lincomb(c, ptr, w, n, r->d, x[0]->count * x[0]->npoly, x[0]->level);
+    *out = r;
+    return 0;
+}
+
 int op_tensor(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **out)
 {
     if (a->level != b->level || a->count != b->count || a->npoly != 2 || b->npoly != 2)
@@ -195,16 +221,17 @@ static int keyswitch(fhe_ctx *c, const u64 *xbase, long long x_outer, const u64 
     Tmp acc(c, (size_t)count * 2 * (l + K) * N, &err);
     Tmp accP(c, (size_t)count * 2 * K * N, &err);
     if (err) return fhe_fail(c, err, "key switching: out of device memory");
-    // 1. INTT of X
+    // 1. INTT of X, each limb i of digit j times (Q_j/q_i)^-1 (the first step of
+    //    the basis conversion)
     LimbMap m1 = identity_map(l, x_outer, (long long)l * N, 0, 0, 0);
-    launch_ntt_inv_plain(c, xbase, xc.p, m1, count * l);
+    launch_ntt_inv_scaled(c, xbase, xc.p, m1, c->ks_xscale[l].data(), count * l);
     // 2. ModUp (basis conversion fused with NTT)
     launch_ntt_modup(c, xc.p, ext.p, l, count);
     // 3. inner product with the key
     launch_ks_inner(c, ext.p, xbase, x_outer, k.d, acc.p, count, l);
-    // 4. INTT of the special limbs of both accumulators
+    // 4. INTT of the special limbs of both accumulators, times p^-1 (P/p_k)^-1
     LimbMap m4 = identity_map(K, (long long)(l + K) * N, (long long)K * N, l, 0, c->L);
-    launch_ntt_inv_plain(c, acc.p, accP.p, m4, count * 2 * K);
+    launch_ntt_inv_scaled(c, acc.p, accP.p, m4, c->ks_pscale.data(), count * 2 * K);
     // 5. ModDown fused with NTT, plus the addend
     launch_ntt_moddown(c, accP.p, acc.p, abase, a_outer, a_poly, amask, out, l, count);
     return 0;
@@ -406,6 +433,33 @@ struct Circuit {
         return keep(r);
     }
 
+    // sum_i c_i lower(x_i, lv): one fused kernel for the scalar products and
+    // additions; the trace records them as the individual operations
+    // (cmul, cmul, add, cmul, add, ...).
+    fhe_ct *lincomb(const std::vector<fhe_ct *> &xs, const std::vector<std::pair<int, int>> &terms, int lv)
+    {
+        if (err) return nullptr;
+        const fhe_ct *low[8];
+        int64_t k[8];
+        const int n = (int)xs.size();
+        if (n > 8) {
+            err = fhe_fail(c, FHE_EUNSUPPORTED, "leaf with more than 8 terms");
+            return nullptr;
+        }
+        for (int i = 0; i < n; i++) {
+            low[i] = lower(xs[i], lv);
+            if (!low[i]) return nullptr;
+            k[i] = terms[i].second;
+        }
+        fhe_ct *r = nullptr;
+        if ((err = op_lincomb(c, low, k, n, &r))) return nullptr;
+        for (int i = 0; i < n; i++) {
+            trace(c, FHE_OP_CMUL, lv);
+            if (i) trace(c, FHE_OP_ADD, lv);
+        }
+        return keep(r);
+    }
+
     // (LT_k, EQ_k) of one digit pair
     void digit(const fhe_ct *x, const fhe_ct *y, bool want_lt, bool want_eq, fhe_ct **lt_out, fhe_ct **eq_out)
     {
@@ -448,12 +502,7 @@ struct Circuit {
                 if (err) return nullptr;
                 int lv = 1 << 30;
                 for (auto *t : cts) lv = std::min(lv, t->level);
-                fhe_ct *acc = nullptr;
-                for (size_t i = 0; i < terms.size(); i++) {
-                    fhe_ct *term = cmul(lower(cts[i], lv), terms[i].second);
-                    acc = acc ? add(acc, term) : term;
-                }
-                return acc;
+                return lincomb(cts, terms, lv);
             };
             std::function<fhe_ct *(int, int)> tree = [&](int k0, int t) -> fhe_ct * {
                 if (err || k0 >= nblocks) return nullptr;

@@ -80,6 +80,10 @@ struct Pool {
     std::unordered_map<void *, size_t> live;  // every block ever obtained -> size
     size_t reserved = 0, in_use = 0, budget = 0;  // budget 0 = unlimited
     long long fail_after = -1;                    // fault injection: fail the n-th new block
+    // While a graph is captured, freed blocks go to this capture-private free
+    // list (reused within the capture, in stream order) instead of the pool's;
+    // the plan keeps them afterwards because every replay reuses them.
+    std::unordered_map<size_t, std::vector<void *>> *cap_free = nullptr;
     void *get(size_t bytes, int *err);
     void put(void *p);
     void release_all();
@@ -111,6 +115,10 @@ struct fhe_ctx {
     ModDownParams *d_moddown = nullptr;
     ModSwitchParams *d_modswitch = nullptr;
     std::unordered_map<int64_t, int *> d_perm;  // NTT-domain automorphism maps
+    // constants folded into the final N^-1 scaling of inverse NTTs (value, Shoup)
+    std::vector<std::vector<ulonglong2>> ks_xscale;  // [level][i]: N^-1 (Q_j/q_i)^-1 mod q_i, i in digit j
+    std::vector<ulonglong2> ks_pscale;               // [k]: N^-1 p^-1 (P/p_k)^-1 mod p_k
+    std::vector<ulonglong2> ms_lastscale;            // [level]: N^-1 p^-1 mod q_{level-1}
 
     // plaintext side
     int ns = 0, M = 0;             // slots and subring size
@@ -160,6 +168,15 @@ struct fhe_evk {
     const KeySwitchKey *find(int64_t g) const;
 };
 
+struct fhe_plan {
+    fhe_ctx *ctx;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    fhe_ct *out[2] = {nullptr, nullptr};  // LT, EQ (either may be NULL)
+    std::unordered_map<size_t, std::vector<void *>> held;  // temporaries the graph reuses on every replay
+    int nodes = 0;
+};
+
 struct fhe_ct {
     fhe_ctx *ctx;
     int count = 0, npoly = 0, level = 0;
@@ -191,6 +208,10 @@ void lt_poly_coefficients(int p, std::vector<int> &out);
 // kernel launchers (ntt.cu, kernels.cu)
 void launch_ntt_fwd_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs);
 void launch_ntt_inv_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs);
+// inverse NTT whose output limb l (of the map) is also multiplied by scale[l]/N^-1:
+// scale[l] = (N^-1 c_l mod q, Shoup word)
+void launch_ntt_inv_scaled(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, const ulonglong2 *scale,
+                           int njobs);
 void launch_ntt_modup(fhe_ctx *c, const u64 *d2c, u64 *ext, int level, int count);
 // addend for ModDown output poly pi of ct c: abase + c*a_outer + pi*a_poly when (amask>>pi)&1
 void launch_ntt_moddown(fhe_ctx *c, const u64 *accP, const u64 *acc, const u64 *abase, long long a_outer,
@@ -214,6 +235,10 @@ void launch_muladd(fhe_ctx *c, const u64 *a, const u64 *b, const u64 *cc, u64 *o
 void launch_ksk_digit(fhe_ctx *c, const u64 *a, const u64 *e, const u64 *s, const u64 *sp, u64 *k0, u64 *k1, int dlo,
                       int dhi, const u64 *Pw, const u64 *Pws);
 bool ntt_supported_logn(int logN);
+// out = sum_{t<n} w[t] x[t], n <= 8, every x[t] an [outer][level][N] batch
+void launch_lincomb(fhe_ctx *c, const u64 *const *x, const u64 (*w)[FHE_MAXP], int n, u64 *out, int outer,
+                    int level);
+int op_lincomb(fhe_ctx *c, const fhe_ct *const *x, const int64_t *k, int n, fhe_ct **out);
 
 // evaluation (eval.cu)
 int op_lower(fhe_ctx *c, const fhe_ct *a, int level, fhe_ct **out);

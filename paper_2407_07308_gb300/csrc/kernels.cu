@@ -7,6 +7,8 @@
 // index runs over count*npoly polys, and the limb of element idx is
 // (idx >> logN) % level, so one flat grid covers the batch and every warp
 // reads 256 contiguous bytes.
+#include <string.h>
+
 #include "fhe_internal.h"
 
 namespace {
@@ -211,6 +213,29 @@ __global__ void k_ksk_digit(const u64 *__restrict__ a, const u64 *__restrict__ e
     }
 }
 
+// out = sum_t w_t x_t (mod q_i), up to 8 ciphertext batches of one shape;
+// w[t][i] is the scalar of term t reduced mod q_i.  Eight products of
+// canonical residues stay below the Barrett bound, so one reduction suffices.
+struct LinComb {
+    const u64 *x[8];
+    u64 w[8][FHE_MAXP];
+    int n;
+};
+
+__global__ void k_lincomb(const LinComb lc, u64 *__restrict__ out, long long total, int logN, int level,
+                          const ModQ *__restrict__ mq)
+{
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)((idx >> logN) % level);
+        u128 acc = 0;
+#pragma unroll
+        for (int t = 0; t < 8; t++)
+            if (t < lc.n) acc += (u128)lc.x[t][idx] * lc.w[t][i];
+        out[idx] = barrett128(acc, mq[i]);
+    }
+}
+
 }  // namespace
 
 // words: u64 words read + written per element (algorithmic traffic)
@@ -332,11 +357,23 @@ static cudaEvent_t prof_event(fhe_ctx *c)
     return e;
 }
 
+// Inside a stream capture a plain event record is only a dependency marker;
+// recorded as external it becomes an event-record node of the graph.
+static void prof_record(fhe_ctx *c, cudaEvent_t e)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->stream, &st);
+    if (st == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, c->stream);
+}
+
 void prof_begin(fhe_ctx *c, int cls, double bytes, double bfly)
 {
     if (!c->prof_on) return;
     cudaEvent_t a = prof_event(c), b = prof_event(c);
-    cudaEventRecord(a, c->stream);
+    prof_record(c, a);
     c->prof_rec.push_back({a, b});
     c->prof_rec_cls.push_back(cls);
     c->prof_rec_bytes.push_back(bytes);
@@ -346,7 +383,7 @@ void prof_begin(fhe_ctx *c, int cls, double bytes, double bfly)
 void prof_end(fhe_ctx *c)
 {
     if (!c->prof_on || c->prof_rec.empty()) return;
-    cudaEventRecord(c->prof_rec.back().second, c->stream);
+    prof_record(c, c->prof_rec.back().second);
 }
 
 extern "C" int fhe_ctx_profile(fhe_ctx *c, int on)
@@ -384,4 +421,18 @@ extern "C" int fhe_ctx_profile_read(fhe_ctx *c, double *ms, int64_t *count, doub
     c->prof_rec_bytes.clear();
     c->prof_rec_bfly.clear();
     return FHE_K_COUNT;
+}
+
+void launch_lincomb(fhe_ctx *c, const u64 *const *x, const u64 (*w)[FHE_MAXP], int n, u64 *out, int outer,
+                    int level)
+{
+    LinComb lc;
+    memset(&lc, 0, sizeof(lc));
+    lc.n = n;
+    for (int t = 0; t < n; t++) {
+        lc.x[t] = x[t];
+        for (int i = 0; i < level; i++) lc.w[t][i] = w[t][i];
+    }
+    LAUNCH_CLS_W(FHE_K_ELEMWISE, n + 1, k_lincomb, (long long)outer * level * c->N, lc, out,
+                 (long long)outer * level * c->N, c->logN, level, c->d_mq);
 }

@@ -55,16 +55,15 @@ __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 
 
 // Stages s0 .. s0+R-1 of the forward transform on one group x[0..2^R) whose
 // block index is hi.
-template <int R>
-__device__ __forceinline__ void fwd_round(u64 (&x)[1 << R], int s0, int hi, const ulonglong2 *__restrict__ W,
-                                          u64 q, u64 q2)
+template <int R, class TW>
+__device__ __forceinline__ void fwd_round(u64 (&x)[1 << R], int s0, int hi, TW W, u64 q, u64 q2)
 {
 #pragma unroll
     for (int u = 0; u < R; u++) {
         const int half = 1 << (R - 1 - u);
 #pragma unroll
         for (int t = 0; t < (1 << u); t++) {
-            const ulonglong2 w = __ldg(W + (1 << (s0 + u)) + (hi << u) + t);
+            const ulonglong2 w = W[(1 << (s0 + u)) + (hi << u) + t];
 #pragma unroll
             for (int k = 0; k < half; k++) {
                 const int e = t * 2 * half + k;
@@ -74,16 +73,15 @@ __device__ __forceinline__ void fwd_round(u64 (&x)[1 << R], int s0, int hi, cons
     }
 }
 
-template <int R>
-__device__ __forceinline__ void inv_round(u64 (&x)[1 << R], int s0, int hi, const ulonglong2 *__restrict__ W,
-                                          u64 q, u64 q2)
+template <int R, class TW>
+__device__ __forceinline__ void inv_round(u64 (&x)[1 << R], int s0, int hi, TW W, u64 q, u64 q2)
 {
 #pragma unroll
     for (int u = R - 1; u >= 0; u--) {
         const int half = 1 << (R - 1 - u);
 #pragma unroll
         for (int t = 0; t < (1 << u); t++) {
-            const ulonglong2 w = __ldg(W + (1 << (s0 + u)) + (hi << u) + t);
+            const ulonglong2 w = W[(1 << (s0 + u)) + (hi << u) + t];
 #pragma unroll
             for (int k = 0; k < half; k++) {
                 const int e = t * 2 * half + k;
@@ -96,6 +94,12 @@ __device__ __forceinline__ void inv_round(u64 (&x)[1 << R], int s0, int hi, cons
 // ---------------------------------------------------------------------------
 // 16 sub-transforms of size 2^M in shared memory
 // ---------------------------------------------------------------------------
+
+// Twiddles read from global memory through the read-only path.
+struct GTw {
+    const ulonglong2 *__restrict__ p;
+    __device__ ulonglong2 operator[](int i) const { return __ldg(p + i); }
+};
 
 // smem layout: sub-transform c at c*P(M), element e at e + (e >> 4); P is odd
 // mod 16 in u64 units, so the strided, blocked and row-wise access patterns
@@ -117,9 +121,8 @@ struct Sub {
 // Round 2: thread t = (c, g') with c = t / G, g' = t % G holds the 16/G
 // blocks b = g' (16/G) + i of G contiguous elements: local stages 4..M-1.
 // hi of sub-transform c is hi0 + c * hstep.
-template <int M, bool FWD>
-__device__ __forceinline__ void sub16(u64 *sm, int tid, const ulonglong2 *__restrict__ W, int S, int hi0, int hstep,
-                                      u64 q, u64 q2)
+template <int M, bool FWD, class TW>
+__device__ __forceinline__ void sub16(u64 *sm, int tid, TW W, int S, int hi0, int hstep, u64 q, u64 q2)
 {
     using C = Sub<M>;
     constexpr int G = C::G, R2 = C::R2, NB = 16 / G;
@@ -176,10 +179,11 @@ __global__ void __launch_bounds__(Sub<N1>::T)
     using C = Sub<N1>;
     constexpr int NN = 1 << (N1 + N2), BLK = (1 << N2) / 16;
     __shared__ u64 sm[C::WORDS];
+    __shared__ ulonglong2 W[1 << N1];  // stages 0..N1-1 use only the table's prefix
     const int job = blockIdx.x / BLK, lo0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
     const typename IO::St st = io.begin(job, NN);
     const u64 q = mq[st.prime].q, q2 = 2 * q;
-    const ulonglong2 *W = tw + (size_t)st.prime * NN;
+    for (int r = tid; r < (1 << N1); r += C::T) W[r] = tw[(size_t)st.prime * NN + r];
     for (int r = tid; r < 16 * C::SZ; r += C::T) {
         const int c = r & 15, e = r >> 4;
         sm[C::at(c, e)] = io.load(st, (e << N2) + lo0 + c);
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(Sub<N2>::T)
     const int job = blockIdx.x / BLK, hi0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
     const typename IO::St st = io.begin(job, NN);
     const u64 q = mq[st.prime].q, q2 = 2 * q;
-    const ulonglong2 *W = tw + (size_t)st.prime * NN;
+    const GTw W{tw + (size_t)st.prime * NN};
     const u64 *mid = io.inter(st) + ((size_t)hi0 << N2);
     for (int r = tid; r < 16 * C::SZ; r += C::T) sm[C::at(r >> N2, r & (C::SZ - 1))] = mid[r];
     __syncthreads();
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(Sub<N2>::T)
     const int job = blockIdx.x / BLK, hi0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
     const typename IO::St st = io.begin(job, NN);
     const u64 q = mq[st.prime].q, q2 = 2 * q;
-    const ulonglong2 *W = tw + (size_t)st.prime * NN;
+    const GTw W{tw + (size_t)st.prime * NN};
     for (int r = tid; r < 16 * C::SZ; r += C::T) sm[C::at(r >> N2, r & (C::SZ - 1))] = io.load(st, (hi0 << N2) + r);
     __syncthreads();
     sub16<N2, false>(sm, tid, W, N1, hi0, 1, q, q2);
@@ -244,11 +248,12 @@ __global__ void __launch_bounds__(Sub<N1>::T)
     using C = Sub<N1>;
     constexpr int NN = 1 << (N1 + N2), BLK = (1 << N2) / 16;
     __shared__ u64 sm[C::WORDS];
+    __shared__ ulonglong2 W[1 << N1];
     const int job = blockIdx.x / BLK, lo0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
     const typename IO::St st = io.begin(job, NN);
     const u64 q = mq[st.prime].q, q2 = 2 * q;
-    const ulonglong2 *W = tw + (size_t)st.prime * NN;
-    const ulonglong2 ni = ninv[st.prime];
+    for (int r = tid; r < (1 << N1); r += C::T) W[r] = tw[(size_t)st.prime * NN + r];
+    const ulonglong2 ni = io.final_scale(st, ninv);
     const u64 *mid = io.inter(st);
     for (int r = tid; r < 16 * C::SZ; r += C::T) {
         const int c = r & 15, e = r >> 4;
@@ -288,10 +293,40 @@ struct IOPlain {
     __device__ u64 load(const St &s, int i) const { return s.in[i]; }
     __device__ void store(const St &s, int i, u64 v) const { s.out[i] = v; }
     __device__ u64 *inter(const St &s) const { return s.out; }
+    __device__ ulonglong2 final_scale(const St &s, const ulonglong2 *ninv) const { return ninv[s.prime]; }
 };
 
-// ModUp: extended limb t of digit j of ct c, from the coefficient-domain
-// limbs of the digit:  y = sum_a [x_a (Q_j/q_a)^-1]_{q_a} (Q_j/q_a) mod r.
+// Inverse transform whose output limb l is also multiplied by a constant:
+// the final scaling uses N^-1 c_l (and its Shoup word) from scale[l].
+struct IOScaled {
+    const u64 *in;
+    u64 *out;
+    LimbMap m;
+    ulonglong2 scale[FHE_MAXP];
+    struct St {
+        const u64 *in;
+        u64 *out;
+        int prime, limb;
+    };
+    __device__ St begin(int job, int N) const
+    {
+        const int o = job / m.nl, l = job % m.nl;
+        St s;
+        s.in = in + o * m.in_outer + (long long)m.in_limb[l] * N;
+        s.out = out + o * m.out_outer + (long long)m.out_limb[l] * N;
+        s.prime = m.prime[l];
+        s.limb = l;
+        return s;
+    }
+    __device__ u64 load(const St &s, int i) const { return s.in[i]; }
+    __device__ void store(const St &s, int i, u64 v) const { s.out[i] = v; }
+    __device__ u64 *inter(const St &s) const { return s.out; }
+    __device__ ulonglong2 final_scale(const St &s, const ulonglong2 *) const { return scale[s.limb]; }
+};
+
+// ModUp: extended limb t of digit j of ct c:  y = sum_a t_a (Q_j/q_a) mod r,
+// where the source limbs already hold t_a = [x_a (Q_j/q_a)^-1]_{q_a} (the
+// inverse NTT that produced them applied that factor).
 struct IOModUp {
     const u64 *d2c;  // [count][l][N] coefficient domain
     u64 *ext;        // [count][dnum][l+K][N]
@@ -303,7 +338,7 @@ struct IOModUp {
         u64 *dst;
         int nsrc, prime;
         ModQ mt;
-        u64 inv[FHE_MAXK], invs[FHE_MAXK], hat[FHE_MAXK], qs[FHE_MAXK];
+        u64 hat[FHE_MAXK];
     };
     __device__ St begin(int job, int N) const
     {
@@ -317,27 +352,16 @@ struct IOModUp {
         s.prime = P->job_prime[e];
         s.mt = mq[s.prime];
 #pragma unroll
-        for (int a = 0; a < FHE_MAXK; a++) {
-            if (a < s.nsrc) {
-                s.inv[a] = P->inv_hat[j][a];
-                s.invs[a] = P->inv_hat_s[j][a];
-                s.hat[a] = P->hat[j][a][t];
-                s.qs[a] = mq[lo + a].q;
-            }
-        }
+        for (int a = 0; a < FHE_MAXK; a++)
+            if (a < s.nsrc) s.hat[a] = P->hat[j][a][t];
         return s;
     }
     __device__ u64 load(const St &s, int n) const
     {
         u128 acc = 0;
 #pragma unroll
-        for (int a = 0; a < FHE_MAXK; a++) {
-            if (a < s.nsrc) {
-                const u64 x = s.src[(long long)a * stride + n];
-                const u64 t = shoup(x, s.inv[a], s.invs[a], s.qs[a]);
-                acc += (u128)t * s.hat[a];
-            }
-        }
+        for (int a = 0; a < FHE_MAXK; a++)
+            if (a < s.nsrc) acc += (u128)s.src[(long long)a * stride + n] * s.hat[a];
         return barrett128(acc, s.mt);
     }
     __device__ void store(const St &s, int k, u64 v) const { s.dst[k] = v; }
@@ -346,8 +370,9 @@ struct IOModUp {
 };
 
 // ModDown of poly pi of ct c, data limb i:
-//   delta_i = sum_k [w_k c_k]_{p_k} * (p P/p_k mod q_i)   (w = INTT'd special limbs)
-//   out_i   = (acc_i - delta_i) P^-1 + addend_i
+//   delta_i = sum_k t_k * (p P/p_k mod q_i),  out_i = (acc_i - delta_i) P^-1 + addend_i,
+// where the special limbs already hold t_k = [acc_{P,k} p^-1 (P/p_k)^-1]_{p_k}
+// (applied by the inverse NTT that produced them).
 struct IOModDown {
     const u64 *accP;  // [count][2][K][N] coefficient domain
     const u64 *acc;   // [count][2][l+K][N] NTT domain
@@ -364,7 +389,7 @@ struct IOModDown {
         int prime;
         ModQ mi;
         u64 pinv, pinv_s;
-        u64 cinv[FHE_MAXK], cinv_s[FHE_MAXK], phat[FHE_MAXK], qk[FHE_MAXK];
+        u64 phat[FHE_MAXK];
     };
     __device__ St begin(int job, int N) const
     {
@@ -379,26 +404,16 @@ struct IOModDown {
         s.pinv = P->pinv[i];
         s.pinv_s = P->pinv_s[i];
 #pragma unroll
-        for (int k = 0; k < FHE_MAXK; k++) {
-            if (k < K) {
-                s.cinv[k] = P->cinv[k];
-                s.cinv_s[k] = P->cinv_s[k];
-                s.phat[k] = P->phat[k][i];
-                s.qk[k] = mq[P->sprime[k]].q;
-            }
-        }
+        for (int k = 0; k < FHE_MAXK; k++)
+            if (k < K) s.phat[k] = P->phat[k][i];
         return s;
     }
     __device__ u64 load(const St &s, int n) const
     {
         u128 a = 0;
 #pragma unroll
-        for (int k = 0; k < FHE_MAXK; k++) {
-            if (k < K) {
-                const u64 t = shoup(s.w[(long long)k * stride + n], s.cinv[k], s.cinv_s[k], s.qk[k]);
-                a += (u128)t * s.phat[k];
-            }
-        }
+        for (int k = 0; k < FHE_MAXK; k++)
+            if (k < K) a += (u128)s.w[(long long)k * stride + n] * s.phat[k];
         return barrett128(a, s.mi);
     }
     __device__ void store(const St &s, int k, u64 v) const
@@ -412,8 +427,9 @@ struct IOModDown {
 };
 
 // Modulus switch l -> l-1 of poly pi of ct c, limb i < l-1:
-//   w = [x_{l-1} p^-1]_{q_{l-1}} (coefficient domain), delta_i = p w mod q_i,
-//   out_i = (x_i - delta_i) q_{l-1}^-1.
+//   delta_i = p w mod q_i,  out_i = (x_i - delta_i) q_{l-1}^-1,
+// where `last` already holds w = [x_{l-1} p^-1]_{q_{l-1}} in the coefficient
+// domain (applied by the inverse NTT that produced it).
 struct IOModSwitch {
     const u64 *last;  // [count][npoly][N] coefficient domain
     const u64 *in;    // [count][npoly][l][N]
@@ -445,11 +461,7 @@ struct IOModSwitch {
         s.qis = P->qinv_s[i];
         return s;
     }
-    __device__ u64 load(const St &s, int n) const
-    {
-        const u64 w = shoup(s.last[n], s.pl, s.pls, s.ql);
-        return shoup(w, s.pi, s.pis, s.q);
-    }
+    __device__ u64 load(const St &s, int n) const { return shoup(s.last[n], s.pi, s.pis, s.q); }
     __device__ void store(const St &s, int k, u64 v) const
     {
         s.out[k] = shoup(submod(s.in[k], v, s.q), s.qi, s.qis, s.q);
@@ -523,6 +535,17 @@ void launch_ntt_fwd_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m,
 void launch_ntt_inv_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs)
 {
     IOPlain io{in, out, m};
+    run_inv(c, io, njobs, FHE_K_NTT_INV);
+}
+
+void launch_ntt_inv_scaled(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, const ulonglong2 *scale,
+                           int njobs)
+{
+    IOScaled io;
+    io.in = in;
+    io.out = out;
+    io.m = m;
+    for (int i = 0; i < m.nl; i++) io.scale[i] = scale[i];
     run_inv(c, io, njobs, FHE_K_NTT_INV);
 }
 

@@ -257,6 +257,30 @@ int build_tables(fhe_ctx *c)
     if ((e = upload(c, (void **)&c->d_modswitch, c->modswitch.data(), sizeof(ModSwitchParams) * (L + 1))))
         return e;
 
+    // constants folded into inverse NTTs
+    auto sc = [](u64 v, u64 q) { return make_ulonglong2(v, shoup_const(v, q)); };
+    c->ks_xscale.assign(L + 1, std::vector<ulonglong2>());
+    c->ms_lastscale.assign(L + 1, make_ulonglong2(0, 0));
+    for (int l = 1; l <= L; l++) {
+        const ModUpParams &U = c->modup[l];
+        c->ks_xscale[l].resize(l);
+        for (int j = 0; j < U.dnum; j++)
+            for (int a = 0; a < U.digit_n[j]; a++) {
+                const int i = U.digit_lo[j] + a;
+                const u64 qi = c->q[i];
+                c->ks_xscale[l][i] = sc(host_mulmod(ninv[i].x, U.inv_hat[j][a], qi), qi);
+            }
+        if (l >= 2) {
+            const u64 ql = c->q[l - 1];
+            c->ms_lastscale[l] = sc(host_mulmod(ninv[l - 1].x, c->modswitch[l].pinv_last, ql), ql);
+        }
+    }
+    c->ks_pscale.resize(K);
+    for (int k = 0; k < K; k++) {
+        const u64 pk = c->q[L + k];
+        c->ks_pscale[k] = sc(host_mulmod(ninv[L + k].x, c->moddown[L].cinv[k], pk), pk);
+    }
+
     lt_poly_coefficients((int)c->p, c->lt);
     if (slot_structure(c)) return FHE_EUNSUPPORTED;
     if (c->N % c->M) return FHE_EUNSUPPORTED;

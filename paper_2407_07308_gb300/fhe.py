@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
             "fhe_ct_shape": (ci, [vp, POINTER(ci), POINTER(ci), POINTER(ci)]),
             "fhe_ct_export_coeff": (ci, [vp, vp, vp]),
             "fhe_ct_import_coeff": (ci, [vp, vp, ci, ci, ci, POINTER(vp)]),
+            "fhe_ct_load_coeff": (ci, [vp, vp, vp]),
             "fhe_add": (ci, [vp, vp, vp, POINTER(vp)]),
             "fhe_sub": (ci, [vp, vp, vp, POINTER(vp)]),
             "fhe_neg": (ci, [vp, vp, POINTER(vp)]),
@@ -110,6 +111,11 @@ def lib() -> ctypes.CDLL:
             "fhe_ntt_inverse": (ci, [vp, vp, vp, ci]),
             "fhe_selftest_modarith": (ci, [u64, u64, u64, ci, ci]),
             "fhe_ctx_profile": (ci, [vp, ci]),
+            "fhe_compare_plan": (ci, [vp, vp, vp, vp, ci, ci, ci, POINTER(vp)]),
+            "fhe_plan_run": (ci, [vp]),
+            "fhe_plan_result": (ci, [vp, ci, POINTER(vp)]),
+            "fhe_plan_nodes": (ci, [vp]),
+            "fhe_plan_destroy": (None, [vp]),
             "fhe_mod_switch_noalloc": (ci, [vp, vp, vp, ci, ci, ci]),
             "fhe_ctx_profile_read": (ci, [vp, vp, vp, vp, vp, ci]),
         }
@@ -303,6 +309,11 @@ def fhe_ct_import_coeff(ctx, data):
     return out
 
 
+def fhe_ct_load_coeff(ctx, ct, data):
+    data = np.ascontiguousarray(data, dtype=np.uint64)
+    _check(lib().fhe_ct_load_coeff(ctx, ct, _ptr(data)), ctx)
+
+
 def _binary(name):
     def f(ctx, a, b):
         out = c_void_p()
@@ -389,6 +400,31 @@ def fhe_max_min(ctx, evk, xs, ys):
     mx, mn = (c_void_p * d)(), (c_void_p * d)()
     _check(lib().fhe_max_min(ctx, evk, _handles(xs), _handles(ys), d, mx, mn), ctx)
     return [c_void_p(v) for v in mx], [c_void_p(v) for v in mn]
+
+
+def fhe_compare_plan(ctx, evk, xs, ys, want_lt=True, want_eq=True):
+    out = c_void_p()
+    _check(lib().fhe_compare_plan(ctx, evk, _handles(xs), _handles(ys), len(xs), int(want_lt), int(want_eq),
+                                  ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_plan_run(plan, ctx=None):
+    _check(lib().fhe_plan_run(plan), ctx)
+
+
+def fhe_plan_result(plan, which: int):
+    out = c_void_p()
+    _check(lib().fhe_plan_result(plan, which, ctypes.byref(out)))
+    return out
+
+
+def fhe_plan_nodes(plan) -> int:
+    return int(lib().fhe_plan_nodes(plan))
+
+
+def fhe_plan_destroy(plan):
+    lib().fhe_plan_destroy(plan)
 
 
 def fhe_trace_enable(ctx, on: bool):

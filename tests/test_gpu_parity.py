@@ -50,7 +50,7 @@ def _same(oracle_ct, gpu_export, idx=0):
 # NTT
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("logN", [10, 11, 12, 13, 14])
+@pytest.mark.parametrize("logN", [10, 11, 12, 13, 14, 15])
 def test_ntt_forward_inverse_match_oracle(logN):
     from oracle.bgv import Oracle
 
@@ -287,5 +287,51 @@ def test_batch_equals_singles():
         for i in range(4):
             lt_i = g.own(fhe.fhe_compare_lt(g.ctx, g.evk, [xe[i]], [ye[i]]))
             assert np.array_equal(g.export(lt_i)[0], ex_b[i])
+    finally:
+        g.close()
+
+
+def test_compare_plan_graph_matches_direct_and_is_isolated():
+    """The captured (graph) form gives the bits of the direct call, replays
+    deterministically, picks up inputs refreshed in place, and never aliases
+    memory handed out after capture."""
+    fhe = _fhe()
+    from tests.gpu_setup import GpuSetup
+
+    params = dict(logN=12, p=17, L=6, K=2, **CHAIN50)
+    g = GpuSetup(seed=13, **params)
+    try:
+        rnd = random.Random(9)
+        rows = lambda: [[rnd.randrange(9) for _ in range(g.ns)] for _ in range(4)]
+        xs = [g.encrypt_slots(rows(), seed=1 + k) for k in range(2)]
+        ys = [g.encrypt_slots(rows(), seed=3 + k) for k in range(2)]
+        lt_d, eq_d = fhe.fhe_compare(g.ctx, g.evk, xs, ys)
+        g.own(lt_d)
+        g.own(eq_d)
+        want_lt, want_eq = g.export(lt_d), g.export(eq_d)
+        plan = fhe.fhe_compare_plan(g.ctx, g.evk, xs, ys)
+        try:
+            assert fhe.fhe_plan_nodes(plan) > 50
+            for _ in range(2):
+                fhe.fhe_plan_run(plan, g.ctx)
+                assert np.array_equal(g.export(fhe.fhe_plan_result(plan, 0)), want_lt)
+                assert np.array_equal(g.export(fhe.fhe_plan_result(plan, 1)), want_eq)
+            # memory obtained after capture is not reused by the graph
+            other = g.encrypt_slots(rows(), seed=99)
+            before = g.export(other)
+            fhe.fhe_plan_run(plan, g.ctx)
+            fhe.fhe_ctx_sync(g.ctx)
+            assert np.array_equal(g.export(other), before)
+            # refresh one input in place: the replay follows it
+            new_x0 = g.encrypt_slots(rows(), seed=50)
+            fhe.fhe_ct_load_coeff(g.ctx, xs[0], g.export(new_x0))
+            fhe.fhe_plan_run(plan, g.ctx)
+            lt2, eq2 = fhe.fhe_compare(g.ctx, g.evk, xs, ys)
+            g.own(lt2)
+            g.own(eq2)
+            assert np.array_equal(g.export(fhe.fhe_plan_result(plan, 0)), g.export(lt2))
+            assert np.array_equal(g.export(fhe.fhe_plan_result(plan, 1)), g.export(eq2))
+        finally:
+            fhe.fhe_plan_destroy(plan)
     finally:
         g.close()
