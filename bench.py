@@ -293,9 +293,10 @@ def run_gpu(args):
 
     # ---- per-kernel device time: a second capture with an event pair around
     # every kernel (event-record nodes in the graph), replayed K times; the
-    # events hold the last replay's times ------------------------------------
+    # events hold the last replay's times.  Recorded serially (no parallel
+    # branches) so that each event pair brackets one kernel alone. -----------
     fhe.fhe_ctx_profile(ctx, True)
-    pplan = fhe.fhe_compare_plan(ctx, evk, xs, ys)
+    pplan = fhe.fhe_compare_plan(ctx, evk, xs, ys, flags=fhe.FHE_PLAN_SERIAL)
     fhe.fhe_ctx_profile(ctx, False)
     pe0, pe1 = ev(), ev()
     pe0.record(stream)

@@ -216,13 +216,17 @@ int fhe_min(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, const fhe_
 
 typedef struct fhe_plan fhe_plan;
 
+/* Plan flags. */
+enum { FHE_PLAN_SERIAL = 1 /* record every kernel on one stream (no parallel branches) */ };
+
 /* Records fhe_compare(x, y) (the LT and/or EQ outputs selected by want_lt /
- * want_eq) as one CUDA graph on the context's stream: one warm run, then a
- * capture.  The plan owns its outputs and every temporary the graph reuses;
- * x and y stay bound to the plan (the caller keeps them alive and may
+ * want_eq) as one CUDA graph: one warm run, then a capture.  Independent
+ * digit circuits become parallel branches of the graph unless flags has
+ * FHE_PLAN_SERIAL.  The plan owns its outputs and every temporary the graph
+ * reuses; x and y stay bound to the plan (the caller keeps them alive and may
  * overwrite their contents between runs).  Synchronises. */
 int fhe_compare_plan(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
-                     int want_lt, int want_eq, fhe_plan **out);
+                     int want_lt, int want_eq, int flags, fhe_plan **out);
 /* Enqueues one replay of the recorded comparison on the context's stream. */
 int fhe_plan_run(fhe_plan *plan);
 /* Borrowed handle of output `which` (0 = LT, 1 = EQ), valid until the plan is

@@ -308,6 +308,8 @@ extern "C" void fhe_ctx_destroy(fhe_ctx *c)
     cudaFree(c->d_moddown);
     cudaFree(c->d_modswitch);
     for (auto &kv : c->d_perm) cudaFree(kv.second);
+    for (cudaStream_t s : c->branch_streams) cudaStreamDestroy(s);
+    for (cudaEvent_t ev : c->branch_events) cudaEventDestroy(ev);
     cudaStreamSynchronize(c->stream);
     delete c;
 }
@@ -969,6 +971,8 @@ extern "C" int fhe_selftest_modarith(uint64_t prime_mod, uint64_t prime_lo, uint
             if (lz >= 2 * q || lz % q != (u64)(((u128)x * w) % q)) bad++;
             if (shoup(x, w, ws, q) != (u64)(((u128)x * w) % q)) bad++;
             if (reduce4q(4 * q - 1 - (x % (4 * q)), 2 * q, q) != (4 * q - 1 - (x % (4 * q))) % q) bad++;
+            const u64 v = edge ? (it < 32 ? ~0ull - (u64)it : 31 * q - 1 - (u64)it) : rnd();
+            if (reduce64(v, m) != v % q) bad++;
         }
     }
     return bad;
@@ -1000,7 +1004,7 @@ extern "C" int fhe_encrypt(fhe_ctx *c, const fhe_pk *pk, const uint64_t *slots, 
 // ---------------------------------------------------------------------------
 
 extern "C" int fhe_compare_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y,
-                                int d, int want_lt, int want_eq, fhe_plan **out)
+                                int d, int want_lt, int want_eq, int flags, fhe_plan **out)
 {
     CHECK_CTX(c);
     if (!out || (!want_lt && !want_eq)) return FHE_EINVAL;
@@ -1039,7 +1043,9 @@ extern "C" int fhe_compare_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *co
         c->pool.stream = cap;
         e = fhe_cuda_check(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed), "begin capture");
         if (!e) {
+            c->capturing = !(flags & FHE_PLAN_SERIAL);
             e = circuit_compare(c, evk, x, y, d, want_lt ? &P->out[0] : nullptr, want_eq ? &P->out[1] : nullptr);
+            c->capturing = false;
             cudaGraph_t g = nullptr;
             const int e2 = fhe_cuda_check(c, cudaStreamEndCapture(cap, &g), "end capture");
             if (!e) e = e2;

@@ -343,6 +343,65 @@ int op_mul_relin(fhe_ctx *c, const KeySwitchKey &rlk, const fhe_ct *a, const fhe
 // low) into L = L_hi + E_hi L_lo and E = E_hi E_lo.
 namespace {
 
+// Fork/join of n parallel branches during plan capture.  enter(k) issues the
+// following work on branch k's stream with branch k's free list; join()
+// makes the original stream wait for every branch and hands the branches'
+// freed blocks back to it.  With n == 1 it does nothing.
+struct Branches {
+    fhe_ctx *c;
+    int n;
+    cudaStream_t main = nullptr;
+    std::unordered_map<size_t, std::vector<void *>> *main_free = nullptr;
+    std::vector<std::unordered_map<size_t, std::vector<void *>>> frees;
+    int err = 0;
+    Branches(fhe_ctx *ctx, int nb) : c(ctx), n(nb)
+    {
+        if (n <= 1) return;
+        main = c->stream;
+        main_free = c->pool.cap_free;
+        frees.resize(n);
+        while ((int)c->branch_streams.size() < n) {
+            cudaStream_t s;
+            cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+            c->branch_streams.push_back(s);
+        }
+        while ((int)c->branch_events.size() < n + 1) {
+            cudaEvent_t ev;
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            c->branch_events.push_back(ev);
+        }
+        err = fhe_cuda_check(c, cudaEventRecord(c->branch_events[n], main), "branch fork");
+        for (int k = 0; k < n && !err; k++)
+            err = fhe_cuda_check(c, cudaStreamWaitEvent(c->branch_streams[k], c->branch_events[n], 0), "branch fork");
+    }
+    void enter(int k)
+    {
+        if (n <= 1) return;
+        c->stream = c->branch_streams[k];
+        c->pool.stream = c->stream;
+        c->pool.cap_free = &frees[k];
+    }
+    int join()
+    {
+        if (n <= 1) return 0;
+        for (int k = 0; k < n && !err; k++) {
+            err = fhe_cuda_check(c, cudaEventRecord(c->branch_events[k], c->branch_streams[k]), "branch join");
+            if (!err) err = fhe_cuda_check(c, cudaStreamWaitEvent(main, c->branch_events[k], 0), "branch join");
+        }
+        c->stream = main;
+        c->pool.stream = main;
+        c->pool.cap_free = main_free;
+        for (auto &f : frees)
+            for (auto &kv : f) {
+                auto &dst = (*main_free)[kv.first];
+                dst.insert(dst.end(), kv.second.begin(), kv.second.end());
+            }
+        n = 1;
+        return err;
+    }
+    ~Branches() { join(); }
+};
+
 struct Circuit {
     fhe_ctx *c;
     const fhe_evk *evk;
@@ -528,12 +587,13 @@ struct Circuit {
     void compare(const fhe_ct *const *xs, const fhe_ct *const *ys, int d, bool want_lt, bool want_eq,
                  fhe_ct **lt, fhe_ct **eq)
     {
-        std::vector<std::pair<fhe_ct *, fhe_ct *>> nodes;
+        std::vector<std::pair<fhe_ct *, fhe_ct *>> nodes(d, {nullptr, nullptr});
+        Branches br(c, c->capturing ? d : 1);
         for (int k = 0; k < d && !err; k++) {
-            fhe_ct *l = nullptr, *e = nullptr;
-            digit(xs[k], ys[k], want_lt, d > 1 || want_eq, &l, &e);
-            nodes.push_back({l, e});
+            br.enter(k);
+            digit(xs[k], ys[k], want_lt, d > 1 || want_eq, &nodes[k].first, &nodes[k].second);
         }
+        if (int e2 = br.join()) err = err ? err : e2;
         while (nodes.size() > 1 && !err) {
             const bool root = nodes.size() == 2;
             std::vector<std::pair<fhe_ct *, fhe_ct *>> nxt;

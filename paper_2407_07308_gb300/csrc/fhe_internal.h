@@ -143,6 +143,14 @@ struct fhe_ctx {
 
     bool tracing = false;
     std::vector<int32_t> trace_op, trace_level;
+
+    // Parallel branches while a plan is captured: independent parts of a
+    // circuit (the digits of a comparison) are issued on their own streams,
+    // forked from and joined back into the capture stream, so the graph runs
+    // them concurrently.  Each branch has its own capture-private free list.
+    bool capturing = false;
+    std::vector<cudaStream_t> branch_streams;
+    std::vector<cudaEvent_t> branch_events;
     long long launches = 0;       // kernels launched since creation
 };
 

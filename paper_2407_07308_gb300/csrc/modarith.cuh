@@ -41,6 +41,7 @@ struct ModQ {
     u64 mu;      // floor(2^(2b+4) / q) * 2^(58-b): Barrett constant, pre-shifted
     int bshift;  // b - 2, the shift that forms t
     int pad;
+    u64 mu64;    // floor(2^64 / q)
 };
 
 // a * w mod q in [0, 2q), w < q, ws = floor(w 2^64 / q), any a < 2^64.
@@ -77,6 +78,13 @@ FHE_HD u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
 
 FHE_HD u64 negmod(u64 a, u64 q) { return a ? q - a : 0; }
 
+// Any v < 2^64 -> [0, q): v - floor(v mu64 / 2^64) q lies in [0, 2q).
+FHE_HD u64 reduce64(u64 v, const ModQ &m)
+{
+    const u64 r = v - fhe_mulhi(v, m.mu64) * m.q;
+    return r >= m.q ? r - m.q : r;
+}
+
 // [0, 2q) -> [0, q)
 FHE_HD u64 reduce2q(u64 a, u64 q) { return a >= q ? a - q : a; }
 
@@ -99,6 +107,7 @@ inline ModQ make_modq(u64 q)
     m.mu = (u64)(mu << (58 - b));
     m.bshift = b - 2;
     m.pad = 0;
+    m.mu64 = (u64)((((u128)1) << 64) / q);
     return m;
 }
 

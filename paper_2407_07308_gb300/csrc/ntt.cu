@@ -36,10 +36,14 @@
 
 namespace {
 
+// Forward butterfly without normalisation: t = [Y w] in [0, 2q) for any
+// 64-bit Y, so if X, Y < B then X + t and X - t + 2q lie in [0, B + 2q).
+// After s stages every value is below (2s + 1) q <= 31 q < 2^63 (primes
+// below 2^58, s <= 15); one reduction at the end brings it to [0, q).
 __device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 q, u64 q2)
 {
-    u64 x = X >= q2 ? X - q2 : X;
-    u64 t = shoup_lazy(Y, w.x, w.y, q);
+    const u64 t = shoup_lazy(Y, w.x, w.y, q);
+    const u64 x = X;
     X = x + t;
     Y = x - t + q2;
 }
@@ -63,7 +67,7 @@ __device__ __forceinline__ void fwd_round(u64 (&x)[1 << R], int s0, int hi, TW W
         const int half = 1 << (R - 1 - u);
 #pragma unroll
         for (int t = 0; t < (1 << u); t++) {
-            const ulonglong2 w = W[(1 << (s0 + u)) + (hi << u) + t];
+            const ulonglong2 w = W.get(s0 + u, (hi << u) + t);
 #pragma unroll
             for (int k = 0; k < half; k++) {
                 const int e = t * 2 * half + k;
@@ -81,7 +85,7 @@ __device__ __forceinline__ void inv_round(u64 (&x)[1 << R], int s0, int hi, TW W
         const int half = 1 << (R - 1 - u);
 #pragma unroll
         for (int t = 0; t < (1 << u); t++) {
-            const ulonglong2 w = W[(1 << (s0 + u)) + (hi << u) + t];
+            const ulonglong2 w = W.get(s0 + u, (hi << u) + t);
 #pragma unroll
             for (int k = 0; k < half; k++) {
                 const int e = t * 2 * half + k;
@@ -95,10 +99,16 @@ __device__ __forceinline__ void inv_round(u64 (&x)[1 << R], int s0, int hi, TW W
 // 16 sub-transforms of size 2^M in shared memory
 // ---------------------------------------------------------------------------
 
-// Twiddles read from global memory through the read-only path.
-struct GTw {
+// Twiddle accessors: get(s, j) = psi^brv(2^s + j), the twiddle of global
+// stage s with in-stage index j < 2^s.
+struct GTw {  // the full table in global memory, read-only path
     const ulonglong2 *__restrict__ p;
-    __device__ ulonglong2 operator[](int i) const { return __ldg(p + i); }
+    __device__ ulonglong2 get(int s, int j) const { return __ldg(p + (1 << s) + j); }
+};
+
+struct PrefixTw {  // the first entries of the table, copied to shared memory
+    const ulonglong2 *sm;
+    __device__ ulonglong2 get(int s, int j) const { return sm[(1 << s) + j]; }
 };
 
 // smem layout: sub-transform c at c*P(M), element e at e + (e >> 4); P is odd
@@ -126,34 +136,38 @@ __device__ __forceinline__ void sub16(u64 *sm, int tid, TW W, int S, int hi0, in
 {
     using C = Sub<M>;
     constexpr int G = C::G, R2 = C::R2, NB = 16 / G;
+    // Addresses as a per-thread base plus compile-time offsets: for e = kG + g
+    // (g < G <= 16, kG a multiple of G) e >> 4 = (kG) >> 4, and for
+    // e = 16 g' + iG + f (iG + f < 16) e >> 4 = g'.
     auto round1 = [&]() {
         const int c = tid & 15, g = tid >> 4;
         const int hi = hi0 + c * hstep;
+        u64 *b1 = sm + c * C::P + g;
         u64 x[16];
 #pragma unroll
-        for (int k = 0; k < 16; k++) x[k] = sm[C::at(c, k * G + g)];
+        for (int k = 0; k < 16; k++) x[k] = b1[k * G + ((k * G) >> 4)];
         if (FWD)
             fwd_round<4>(x, S, hi, W, q, q2);
         else
             inv_round<4>(x, S, hi, W, q, q2);
 #pragma unroll
-        for (int k = 0; k < 16; k++) sm[C::at(c, k * G + g)] = x[k];
+        for (int k = 0; k < 16; k++) b1[k * G + ((k * G) >> 4)] = x[k];
     };
     auto round2 = [&]() {
         const int c = tid / G, gp = tid % G;
         const int hi = hi0 + c * hstep;
+        u64 *b2 = sm + c * C::P + gp * 17;
 #pragma unroll
         for (int i = 0; i < NB; i++) {
-            const int b = gp * NB + i;
             u64 x[1 << R2];
 #pragma unroll
-            for (int f = 0; f < (1 << R2); f++) x[f] = sm[C::at(c, b * G + f)];
+            for (int f = 0; f < (1 << R2); f++) x[f] = b2[i * G + f];
             if (FWD)
-                fwd_round<R2>(x, S + 4, hi * 16 + b, W, q, q2);
+                fwd_round<R2>(x, S + 4, hi * 16 + gp * NB + i, W, q, q2);
             else
-                inv_round<R2>(x, S + 4, hi * 16 + b, W, q, q2);
+                inv_round<R2>(x, S + 4, hi * 16 + gp * NB + i, W, q, q2);
 #pragma unroll
-            for (int f = 0; f < (1 << R2); f++) sm[C::at(c, b * G + f)] = x[f];
+            for (int f = 0; f < (1 << R2); f++) b2[i * G + f] = x[f];
         }
     };
     if (FWD) {
@@ -166,6 +180,19 @@ __device__ __forceinline__ void sub16(u64 *sm, int tid, TW W, int S, int hi0, in
         round1();
     }
 }
+
+// Grouped row kernels: all 16 sub-transforms of the CTA are row hi of 16
+// limbs with one prime, so the CTA needs only the 2^N2 - 1 twiddles of that
+// row: stage N1+u, in-stage index hi 2^u + t, at offset 2^u - 1 + t.
+struct RowTw {
+    const ulonglong2 *sm;
+    int N1, hi;
+    __device__ ulonglong2 get(int s, int j) const
+    {
+        const int u = s - N1;
+        return sm[(1 << u) - 1 + j - (hi << u)];
+    }
+};
 
 // ---------------------------------------------------------------------------
 // kernels.  Grid: one CTA per (job, block of 16 columns / rows).
@@ -189,7 +216,7 @@ __global__ void __launch_bounds__(Sub<N1>::T)
         sm[C::at(c, e)] = io.load(st, (e << N2) + lo0 + c);
     }
     __syncthreads();
-    sub16<N1, true>(sm, tid, W, 0, 0, 0, q, q2);
+    sub16<N1, true>(sm, tid, PrefixTw{W}, 0, 0, 0, q, q2);
     __syncthreads();
     u64 *mid = io.inter(st);
     for (int r = tid; r < 16 * C::SZ; r += C::T) {
@@ -215,8 +242,9 @@ __global__ void __launch_bounds__(Sub<N2>::T)
     __syncthreads();
     sub16<N2, true>(sm, tid, W, N1, hi0, 1, q, q2);
     __syncthreads();
+    const ModQ mqp = mq[st.prime];
     for (int r = tid; r < 16 * C::SZ; r += C::T)
-        io.store(st, (hi0 << N2) + r, reduce4q(sm[C::at(r >> N2, r & (C::SZ - 1))], q2, q));
+        io.store(st, (hi0 << N2) + r, reduce64(sm[C::at(r >> N2, r & (C::SZ - 1))], mqp));
 }
 
 // Inverse, rows first: undoes global stages N1+N2-1..N1.
@@ -237,6 +265,77 @@ __global__ void __launch_bounds__(Sub<N2>::T)
     __syncthreads();
     u64 *mid = io.inter(st) + ((size_t)hi0 << N2);
     for (int r = tid; r < 16 * C::SZ; r += C::T) mid[r] = sm[C::at(r >> N2, r & (C::SZ - 1))];
+}
+
+// Grouped rows.  Jobs j and j + stride share a prime; the launch holds
+// `groups` x 16 such jobs per residue class of j mod stride.  CTA
+// (group g, row hi): sub-transform c is row hi of job base + (16 kb + c) stride
+// with base = g % stride, kb = g / stride.
+template <int N1, int N2, class IO>
+__global__ void __launch_bounds__(Sub<N2>::T)
+    k_fwd_rows_grp(const IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw, int stride)
+{
+    using C = Sub<N2>;
+    constexpr int NN = 1 << (N1 + N2), ROWS = 1 << N1;
+    __shared__ u64 sm[C::WORDS];
+    __shared__ ulonglong2 tws[(1 << N2) - 1];
+    __shared__ typename IO::St sts[16];
+    const int tid = threadIdx.x, hi = blockIdx.x % ROWS, g = blockIdx.x / ROWS;
+    const int base = g % stride, kb = g / stride;
+    if (tid < 16) sts[tid] = io.begin(base + (16 * kb + tid) * stride, NN);
+    __syncthreads();
+    const int prime = sts[0].prime;
+    const ModQ mqp = mq[prime];
+    const u64 q = mqp.q, q2 = 2 * q;
+    const ulonglong2 *W = tw + (size_t)prime * NN;
+    for (int k = tid; k < (1 << N2) - 1; k += C::T) {
+        const int u = 31 - __clz(k + 1);  // stage of entry k
+        tws[k] = __ldg(W + (1 << (N1 + u)) + (hi << u) + (k + 1 - (1 << u)));
+    }
+    for (int r = tid; r < 16 * C::SZ; r += C::T) {
+        const int c = r >> N2, f = r & (C::SZ - 1);
+        sm[C::at(c, f)] = io.inter(sts[c])[(hi << N2) + f];
+    }
+    __syncthreads();
+    sub16<N2, true>(sm, tid, RowTw{tws, N1, hi}, N1, hi, 0, q, q2);
+    __syncthreads();
+    for (int r = tid; r < 16 * C::SZ; r += C::T) {
+        const int c = r >> N2, f = r & (C::SZ - 1);
+        io.store(sts[c], (hi << N2) + f, reduce64(sm[C::at(c, f)], mqp));
+    }
+}
+
+template <int N1, int N2, class IO>
+__global__ void __launch_bounds__(Sub<N2>::T)
+    k_inv_rows_grp(const IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw, int stride)
+{
+    using C = Sub<N2>;
+    constexpr int NN = 1 << (N1 + N2), ROWS = 1 << N1;
+    __shared__ u64 sm[C::WORDS];
+    __shared__ ulonglong2 tws[(1 << N2) - 1];
+    __shared__ typename IO::St sts[16];
+    const int tid = threadIdx.x, hi = blockIdx.x % ROWS, g = blockIdx.x / ROWS;
+    const int base = g % stride, kb = g / stride;
+    if (tid < 16) sts[tid] = io.begin(base + (16 * kb + tid) * stride, NN);
+    __syncthreads();
+    const int prime = sts[0].prime;
+    const u64 q = mq[prime].q, q2 = 2 * q;
+    const ulonglong2 *W = tw + (size_t)prime * NN;
+    for (int k = tid; k < (1 << N2) - 1; k += C::T) {
+        const int u = 31 - __clz(k + 1);
+        tws[k] = __ldg(W + (1 << (N1 + u)) + (hi << u) + (k + 1 - (1 << u)));
+    }
+    for (int r = tid; r < 16 * C::SZ; r += C::T) {
+        const int c = r >> N2, f = r & (C::SZ - 1);
+        sm[C::at(c, f)] = io.load(sts[c], (hi << N2) + f);
+    }
+    __syncthreads();
+    sub16<N2, false>(sm, tid, RowTw{tws, N1, hi}, N1, hi, 0, q, q2);
+    __syncthreads();
+    for (int r = tid; r < 16 * C::SZ; r += C::T) {
+        const int c = r >> N2, f = r & (C::SZ - 1);
+        io.inter(sts[c])[(hi << N2) + f] = sm[C::at(c, f)];
+    }
 }
 
 // Inverse, columns: undoes global stages N1-1..0, then scales by N^-1.
@@ -260,7 +359,7 @@ __global__ void __launch_bounds__(Sub<N1>::T)
         sm[C::at(c, e)] = mid[(e << N2) + lo0 + c];
     }
     __syncthreads();
-    sub16<N1, false>(sm, tid, W, 0, 0, 0, q, q2);
+    sub16<N1, false>(sm, tid, PrefixTw{W}, 0, 0, 0, q, q2);
     __syncthreads();
     for (int r = tid; r < 16 * C::SZ; r += C::T) {
         const int c = r & 15, e = r >> 4;
@@ -294,6 +393,7 @@ struct IOPlain {
     __device__ void store(const St &s, int i, u64 v) const { s.out[i] = v; }
     __device__ u64 *inter(const St &s) const { return s.out; }
     __device__ ulonglong2 final_scale(const St &s, const ulonglong2 *ninv) const { return ninv[s.prime]; }
+    int prime_stride() const { return m.nl; }  // jobs j and j + nl use one prime
 };
 
 // Inverse transform whose output limb l is also multiplied by a constant:
@@ -322,6 +422,7 @@ struct IOScaled {
     __device__ void store(const St &s, int i, u64 v) const { s.out[i] = v; }
     __device__ u64 *inter(const St &s) const { return s.out; }
     __device__ ulonglong2 final_scale(const St &s, const ulonglong2 *) const { return scale[s.limb]; }
+    int prime_stride() const { return m.nl; }
 };
 
 // ModUp: extended limb t of digit j of ct c:  y = sum_a t_a (Q_j/q_a) mod r,
@@ -366,6 +467,7 @@ struct IOModUp {
     }
     __device__ void store(const St &s, int k, u64 v) const { s.dst[k] = v; }
     __device__ u64 *inter(const St &s) const { return s.dst; }
+    int prime_stride() const { return njobs; }  // one entry per (digit, target) and ct
     int stride;  // N
 };
 
@@ -424,6 +526,7 @@ struct IOModDown {
         s.out[k] = r;
     }
     __device__ u64 *inter(const St &s) const { return s.out; }
+    int prime_stride() const { return l; }  // job = (ct, poly) * l + limb
 };
 
 // Modulus switch l -> l-1 of poly pi of ct c, limb i < l-1:
@@ -467,19 +570,37 @@ struct IOModSwitch {
         s.out[k] = shoup(submod(s.in[k], v, s.q), s.qi, s.qis, s.q);
     }
     __device__ u64 *inter(const St &s) const { return s.out; }
+    int prime_stride() const { return l - 1; }  // job = (ct, poly) * (l-1) + limb
 };
+
+// Row kernels take the grouped form when every prime of the launch has a
+// multiple of 16 jobs (the batched case); otherwise 16 rows of one limb.
+template <class IO>
+bool groupable(const IO &io, int njobs)
+{
+    const int st = io.prime_stride();
+    return st > 0 && njobs % st == 0 && (njobs / st) % 16 == 0;
+}
 
 template <int N1, int N2, class IO>
 void fwd_pair(fhe_ctx *c, const IO &io, int njobs)
 {
     k_fwd_cols<N1, N2, IO><<<njobs * ((1 << N2) / 16), Sub<N1>::T, 0, c->stream>>>(io, c->d_mq, c->d_fwd);
-    k_fwd_rows<N1, N2, IO><<<njobs * ((1 << N1) / 16), Sub<N2>::T, 0, c->stream>>>(io, c->d_mq, c->d_fwd);
+    if (groupable(io, njobs))
+        k_fwd_rows_grp<N1, N2, IO><<<(njobs / 16) * (1 << N1), Sub<N2>::T, 0, c->stream>>>(io, c->d_mq, c->d_fwd,
+                                                                                             io.prime_stride());
+    else
+        k_fwd_rows<N1, N2, IO><<<njobs * ((1 << N1) / 16), Sub<N2>::T, 0, c->stream>>>(io, c->d_mq, c->d_fwd);
 }
 
 template <int N1, int N2, class IO>
 void inv_pair(fhe_ctx *c, const IO &io, int njobs)
 {
-    k_inv_rows<N1, N2, IO><<<njobs * ((1 << N1) / 16), Sub<N2>::T, 0, c->stream>>>(io, c->d_mq, c->d_inv);
+    if (groupable(io, njobs))
+        k_inv_rows_grp<N1, N2, IO><<<(njobs / 16) * (1 << N1), Sub<N2>::T, 0, c->stream>>>(io, c->d_mq, c->d_inv,
+                                                                                             io.prime_stride());
+    else
+        k_inv_rows<N1, N2, IO><<<njobs * ((1 << N1) / 16), Sub<N2>::T, 0, c->stream>>>(io, c->d_mq, c->d_inv);
     k_inv_cols<N1, N2, IO><<<njobs * ((1 << N2) / 16), Sub<N1>::T, 0, c->stream>>>(io, c->d_mq, c->d_inv,
                                                                                     c->d_ninv);
 }

@@ -111,7 +111,7 @@ def lib() -> ctypes.CDLL:
             "fhe_ntt_inverse": (ci, [vp, vp, vp, ci]),
             "fhe_selftest_modarith": (ci, [u64, u64, u64, ci, ci]),
             "fhe_ctx_profile": (ci, [vp, ci]),
-            "fhe_compare_plan": (ci, [vp, vp, vp, vp, ci, ci, ci, POINTER(vp)]),
+            "fhe_compare_plan": (ci, [vp, vp, vp, vp, ci, ci, ci, ci, POINTER(vp)]),
             "fhe_plan_run": (ci, [vp]),
             "fhe_plan_result": (ci, [vp, ci, POINTER(vp)]),
             "fhe_plan_nodes": (ci, [vp]),
@@ -402,10 +402,13 @@ def fhe_max_min(ctx, evk, xs, ys):
     return [c_void_p(v) for v in mx], [c_void_p(v) for v in mn]
 
 
-def fhe_compare_plan(ctx, evk, xs, ys, want_lt=True, want_eq=True):
+FHE_PLAN_SERIAL = 1
+
+
+def fhe_compare_plan(ctx, evk, xs, ys, want_lt=True, want_eq=True, flags=0):
     out = c_void_p()
     _check(lib().fhe_compare_plan(ctx, evk, _handles(xs), _handles(ys), len(xs), int(want_lt), int(want_eq),
-                                  ctypes.byref(out)), ctx)
+                                  int(flags), ctypes.byref(out)), ctx)
     return out
 
 
