@@ -44,10 +44,14 @@ void *Pool::get(size_t bytes, int *err)
         // give cached blocks of other sizes back before refusing
         for (auto &kv : free_lists) {
             for (void *q : kv.second) {
-                if (alloc.free)
+                if (raw.count(q)) {
+                    cudaFree(q);
+                    raw.erase(q);
+                } else if (alloc.free) {
                     alloc.free(q, kv.first, stream, alloc.user);
-                else
+                } else {
                     cudaFreeAsync(q, stream);
+                }
                 live.erase(q);
                 reserved -= kv.first;
             }
@@ -64,10 +68,16 @@ void *Pool::get(size_t bytes, int *err)
     }
     if (fail_after > 0) fail_after--;
     void *p = nullptr;
-    if (alloc.alloc)
+    if (cap_free) {
+        // a miss while a graph is captured: plain cudaMalloc (permitted in a
+        // relaxed capture), never the caller's allocator on a capturing stream
+        if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+        if (p) raw[p] = true;
+    } else if (alloc.alloc) {
         p = alloc.alloc(bytes, (void *)stream, alloc.user);
-    else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess)
+    } else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
         p = nullptr;
+    }
     if (!p) {
         *err = FHE_ENOMEM;
         return nullptr;
@@ -93,11 +103,14 @@ void Pool::put(void *p)
 void Pool::release_all()
 {
     for (auto &kv : live) {
-        if (alloc.free)
+        if (raw.count(kv.first))
+            cudaFree(kv.first);
+        else if (alloc.free)
             alloc.free(kv.first, kv.second, (void *)stream, alloc.user);
         else
             cudaFreeAsync(kv.first, stream);
     }
+    raw.clear();
     live.clear();
     free_lists.clear();
     reserved = in_use = 0;

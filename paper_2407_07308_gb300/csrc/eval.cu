@@ -343,50 +343,84 @@ int op_mul_relin(fhe_ctx *c, const KeySwitchKey &rlk, const fhe_ct *a, const fhe
 // low) into L = L_hi + E_hi L_lo and E = E_hi E_lo.
 namespace {
 
-// Fork/join of n parallel branches during plan capture.  enter(k) issues the
-// following work on branch k's stream with branch k's free list; join()
-// makes the original stream wait for every branch and hands the branches'
-// freed blocks back to it.  With n == 1 it does nothing.
-struct Branches {
+// Dependency-driven streams while a plan is captured.  Every circuit op is
+// issued on one of S streams (round robin) after waiting for the events of
+// its inputs, and records an event for its output; the capture therefore
+// holds the circuit's true dependency graph and the replay runs independent
+// products (both digits, the baby powers of one wave, the leaves, the tree
+// nodes of one level) concurrently.  Scratch freed on a stream goes to that
+// stream's capture-private free list, so no block crosses streams before the
+// final join, where the original stream waits for every stream used.
+struct Dag {
+    static constexpr int S = 8;
     fhe_ctx *c;
-    int n;
+    bool on = false;
     cudaStream_t main = nullptr;
     std::unordered_map<size_t, std::vector<void *>> *main_free = nullptr;
     std::vector<std::unordered_map<size_t, std::vector<void *>>> frees;
-    int err = 0;
-    Branches(fhe_ctx *ctx, int nb) : c(ctx), n(nb)
+    bool used[S] = {false};
+    int rr = 0, ev_next = 0, err = 0;
+    std::vector<fhe_ct *> marked;
+    cudaEvent_t origin = nullptr;
+
+    explicit Dag(fhe_ctx *ctx) : c(ctx)
     {
-        if (n <= 1) return;
+        if (!c->capturing) return;
+        on = true;
         main = c->stream;
         main_free = c->pool.cap_free;
-        frees.resize(n);
-        while ((int)c->branch_streams.size() < n) {
+        frees.resize(S);
+        while ((int)c->branch_streams.size() < S) {
             cudaStream_t s;
             cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
             c->branch_streams.push_back(s);
         }
-        while ((int)c->branch_events.size() < n + 1) {
+        origin = event();
+        err = fhe_cuda_check(c, cudaEventRecord(origin, main), "dag fork");
+    }
+    cudaEvent_t event()
+    {
+        if (ev_next == (int)c->branch_events.size()) {
             cudaEvent_t ev;
             cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
             c->branch_events.push_back(ev);
         }
-        err = fhe_cuda_check(c, cudaEventRecord(c->branch_events[n], main), "branch fork");
-        for (int k = 0; k < n && !err; k++)
-            err = fhe_cuda_check(c, cudaStreamWaitEvent(c->branch_streams[k], c->branch_events[n], 0), "branch fork");
+        return c->branch_events[ev_next++];
     }
-    void enter(int k)
+    // issue the next op after its inputs
+    void begin(std::initializer_list<const fhe_ct *> ins)
     {
-        if (n <= 1) return;
-        c->stream = c->branch_streams[k];
-        c->pool.stream = c->stream;
+        if (!on || err) return;
+        const int k = rr;
+        rr = (rr + 1) % S;
+        cudaStream_t s = c->branch_streams[k];
+        if (!used[k]) {
+            used[k] = true;
+            err = fhe_cuda_check(c, cudaStreamWaitEvent(s, origin, 0), "dag fork");
+        }
+        for (const fhe_ct *x : ins)
+            if (x && x->ready && x->on != s) err = err ? err : fhe_cuda_check(c, cudaStreamWaitEvent(s, x->ready, 0), "dag wait");
+        c->stream = s;
+        c->pool.stream = s;
         c->pool.cap_free = &frees[k];
+    }
+    void end(fhe_ct *out)
+    {
+        if (!on || err || !out) return;
+        cudaEvent_t ev = event();
+        err = fhe_cuda_check(c, cudaEventRecord(ev, c->stream), "dag record");
+        out->ready = ev;
+        out->on = c->stream;
+        marked.push_back(out);
     }
     int join()
     {
-        if (n <= 1) return 0;
-        for (int k = 0; k < n && !err; k++) {
-            err = fhe_cuda_check(c, cudaEventRecord(c->branch_events[k], c->branch_streams[k]), "branch join");
-            if (!err) err = fhe_cuda_check(c, cudaStreamWaitEvent(main, c->branch_events[k], 0), "branch join");
+        if (!on) return 0;
+        for (int k = 0; k < S; k++) {
+            if (!used[k]) continue;
+            cudaEvent_t ev = event();
+            if (!err) err = fhe_cuda_check(c, cudaEventRecord(ev, c->branch_streams[k]), "dag join");
+            if (!err) err = fhe_cuda_check(c, cudaStreamWaitEvent(main, ev, 0), "dag join");
         }
         c->stream = main;
         c->pool.stream = main;
@@ -396,10 +430,11 @@ struct Branches {
                 auto &dst = (*main_free)[kv.first];
                 dst.insert(dst.end(), kv.second.begin(), kv.second.end());
             }
-        n = 1;
+        for (fhe_ct *x : marked) x->ready = nullptr, x->on = nullptr;
+        on = false;
         return err;
     }
-    ~Branches() { join(); }
+    ~Dag() { join(); }
 };
 
 struct Circuit {
@@ -409,13 +444,21 @@ struct Circuit {
     int err = 0;
     std::vector<fhe_ct *> owned;
     std::map<std::pair<const fhe_ct *, int>, fhe_ct *> lowered;
+    Dag dag;
 
-    Circuit(fhe_ctx *ctx, const fhe_evk *e) : c(ctx), evk(e), rlk(&e->keys[0]) {}
+    Circuit(fhe_ctx *ctx, const fhe_evk *e) : c(ctx), evk(e), rlk(&e->keys[0]), dag(ctx) {}
     ~Circuit()
     {
+        finish();
         for (fhe_ct *x : owned)
             if (x) fhe_ct_destroy(x);
         for (auto &kv : lowered) fhe_ct_destroy(kv.second);
+    }
+    // joins the captured streams (before anything is freed or returned)
+    void finish()
+    {
+        const int e2 = dag.join();
+        if (!err) err = e2;
     }
     fhe_ct *keep(fhe_ct *x)
     {
@@ -439,7 +482,9 @@ struct Circuit {
         const fhe_ct *above = lower(x, level + 1);
         if (!above) return nullptr;
         fhe_ct *r = nullptr;
+        dag.begin({above});
         if ((err = op_modswitch1(c, above, &r))) return nullptr;
+        dag.end(r);
         lowered[key] = r;
         return r;
     }
@@ -450,7 +495,9 @@ struct Circuit {
         const fhe_ct *a2 = lower(a, lv), *b2 = lower(b, lv);
         if (!a2 || !b2) return nullptr;
         fhe_ct *r = nullptr;
+        dag.begin({a2, b2});
         if ((err = op_mul_relin(c, *rlk, a2, b2, &r))) return nullptr;
+        dag.end(r);
         trace(c, FHE_OP_MUL, lv);
         return keep(r);
     }
@@ -461,7 +508,9 @@ struct Circuit {
         const fhe_ct *a2 = lower(a, lv), *b2 = lower(b, lv);
         if (!a2 || !b2) return nullptr;
         fhe_ct *r = nullptr;
+        dag.begin({a2, b2});
         if ((err = op_addsub(c, a2, b2, sub, &r))) return nullptr;
+        dag.end(r);
         trace(c, sub ? FHE_OP_SUB : FHE_OP_ADD, lv);
         return keep(r);
     }
@@ -471,7 +520,9 @@ struct Circuit {
     {
         if (err || !a) return nullptr;
         fhe_ct *r = nullptr;
+        dag.begin({a});
         if ((err = op_mul_const(c, a, k, &r))) return nullptr;
+        dag.end(r);
         trace(c, FHE_OP_CMUL, a->level);
         return keep(r);
     }
@@ -479,7 +530,9 @@ struct Circuit {
     {
         if (err || !a) return nullptr;
         fhe_ct *r = nullptr;
+        dag.begin({a});
         if ((err = op_add_const(c, a, k, &r))) return nullptr;
+        dag.end(r);
         trace(c, FHE_OP_CADD, a->level);
         return keep(r);
     }
@@ -487,7 +540,9 @@ struct Circuit {
     {
         if (err || !a) return nullptr;
         fhe_ct *r = nullptr;
+        dag.begin({a});
         if ((err = op_neg(c, a, &r))) return nullptr;
+        dag.end(r);
         trace(c, FHE_OP_NEG, a->level);
         return keep(r);
     }
@@ -511,7 +566,12 @@ struct Circuit {
             k[i] = terms[i].second;
         }
         fhe_ct *r = nullptr;
+        dag.begin({});
+        for (int i = 0; i < n && !dag.err; i++)  // inputs of any arity
+            if (low[i]->ready && low[i]->on != c->stream)
+                dag.err = fhe_cuda_check(c, cudaStreamWaitEvent(c->stream, low[i]->ready, 0), "dag wait");
         if ((err = op_lincomb(c, low, k, n, &r))) return nullptr;
+        dag.end(r);
         for (int i = 0; i < n; i++) {
             trace(c, FHE_OP_CMUL, lv);
             if (i) trace(c, FHE_OP_ADD, lv);
@@ -588,12 +648,8 @@ struct Circuit {
                  fhe_ct **lt, fhe_ct **eq)
     {
         std::vector<std::pair<fhe_ct *, fhe_ct *>> nodes(d, {nullptr, nullptr});
-        Branches br(c, c->capturing ? d : 1);
-        for (int k = 0; k < d && !err; k++) {
-            br.enter(k);
+        for (int k = 0; k < d && !err; k++)
             digit(xs[k], ys[k], want_lt, d > 1 || want_eq, &nodes[k].first, &nodes[k].second);
-        }
-        if (int e2 = br.join()) err = err ? err : e2;
         while (nodes.size() > 1 && !err) {
             const bool root = nodes.size() == 2;
             std::vector<std::pair<fhe_ct *, fhe_ct *>> nxt;
@@ -623,6 +679,7 @@ int circuit_compare(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, cons
 {
     Circuit C(c, evk);
     C.compare(x, y, d, lt != nullptr, eq != nullptr, lt, eq);
+    C.finish();
     return C.err;
 }
 
@@ -643,5 +700,6 @@ int circuit_max_min(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, cons
         if (mx) mx[k] = C.release(a);
         if (mn) mn[k] = C.release(b);
     }
-    return 0;
+    C.finish();
+    return C.err;
 }

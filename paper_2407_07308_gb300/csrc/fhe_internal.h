@@ -78,6 +78,7 @@ struct Pool {
     cudaStream_t stream = 0;
     std::unordered_map<size_t, std::vector<void *>> free_lists;
     std::unordered_map<void *, size_t> live;  // every block ever obtained -> size
+    std::unordered_map<void *, bool> raw;     // blocks from cudaMalloc (misses during a capture)
     size_t reserved = 0, in_use = 0, budget = 0;  // budget 0 = unlimited
     long long fail_after = -1;                    // fault injection: fail the n-th new block
     // While a graph is captured, freed blocks go to this capture-private free
@@ -150,7 +151,7 @@ struct fhe_ctx {
     // them concurrently.  Each branch has its own capture-private free list.
     bool capturing = false;
     std::vector<cudaStream_t> branch_streams;
-    std::vector<cudaEvent_t> branch_events;
+    std::vector<cudaEvent_t> branch_events;  // reused by every capture
     long long launches = 0;       // kernels launched since creation
 };
 
@@ -190,6 +191,10 @@ struct fhe_ct {
     int count = 0, npoly = 0, level = 0;
     u64 *d = nullptr;             // [count][npoly][level][N] NTT domain
     size_t bytes = 0;
+    // set only while a plan is captured: the event after the kernel that
+    // produced this ciphertext, and the stream it was issued on
+    cudaEvent_t ready = nullptr;
+    cudaStream_t on = nullptr;
 };
 
 // kernel classes for fhe_ctx_profile_read (index = FHE_K_* in fhe.h)
