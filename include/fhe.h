@@ -150,6 +150,18 @@ int fhe_encrypt(fhe_ctx *ctx, const fhe_pk *pk, const uint64_t *slots, int count
  * slots: uint64[count][n_s].  Fails with FHE_EINVAL if a plaintext is not a
  * slot-constant encoding.  Synchronises. */
 int fhe_decrypt(fhe_ctx *ctx, const fhe_sk *sk, const fhe_ct *ct, uint64_t *slots);
+/* Refresh: a stand-in for bootstrapping, which the paper does not cover (it
+ * needs the secret key).  Every ciphertext's plaintext is recovered on the
+ * device (as in fhe_decrypt) and encrypted again at level L with fresh
+ * randomness: explicit u, e0, e1 (int64[count][N]) or the seeded samplers.
+ * Used by long max/min tournaments whose depth exceeds the modulus chain. */
+int fhe_refresh_explicit(fhe_ctx *ctx, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct *ct, const int64_t *u,
+                         const int64_t *e0, const int64_t *e1, fhe_ct **out);
+int fhe_refresh(fhe_ctx *ctx, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct *ct, uint64_t seed, fhe_ct **out);
+/* n blocks of Philox4x32-10 (4 words each) of stream `tag` under `seed`,
+ * computed on the current device: the generator behind the seeded calls.
+ * out: host uint32[4n].  Synchronises. */
+int fhe_philox_blocks(uint64_t seed, uint32_t tag, int n, uint32_t *out);
 void fhe_ct_destroy(fhe_ct *ct);
 int fhe_ct_shape(const fhe_ct *ct, int *count, int *npoly, int *level);
 /* Coefficient-domain residues, host uint64[count][npoly][level][N].  Synchronises. */
@@ -235,6 +247,25 @@ int fhe_plan_result(const fhe_plan *plan, int which, const fhe_ct **out);
 /* Kernel nodes in the recorded graph. */
 int fhe_plan_nodes(const fhe_plan *plan);
 void fhe_plan_destroy(fhe_plan *plan);
+
+/* ---- tournament max / min -------------------------------------------------------- */
+
+/* Galois elements the tournament rotates by (write up to cap; returns how
+ * many): 5^(2^i) mod 2N for 2^i = n_s/4 .. 1, then 2N-1.  The evaluation keys
+ * passed to fhe_tournament must include all of them. */
+int fhe_tournament_galois(const fhe_ctx *ctx, int64_t *galois, int cap);
+/* Max and/or min over every slot of every ciphertext of the batches x[0..d-1]
+ * (digit k of all values, least significant first; count n ciphertexts of
+ * n_s slots each).  The maximum over max_min of Sec. 2.1 "Non-arithmetic
+ * Comparison" (min/max of the BGV comparison work): cross rounds pair
+ * ciphertexts [0, h) with [h, 2h) (h = n/2, an odd last one passes on), then
+ * in-slot rounds combine each ciphertext with its rotation by the elements of
+ * fhe_tournament_galois.  out_max / out_min: d single-ciphertext handles whose
+ * every slot holds the result (either may be NULL).  A round that would end
+ * below level 1 is preceded by fhe_refresh with seeds derived from `seed`
+ * (needs sk and pk; without them such a round fails with FHE_ELEVEL). */
+int fhe_tournament(fhe_ctx *ctx, const fhe_evk *evk, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct *const *x,
+                   int d, uint64_t seed, fhe_ct **out_max, fhe_ct **out_min);
 
 /* ---- operation trace --------------------------------------------------------- */
 

@@ -30,7 +30,16 @@ them) are:
     (L_hi + E_hi L_lo, E_hi E_lo), an odd last node passes up unchanged, and
     the root computes the E product only when EQ is wanted;
   * max/min: L = LT(x, y); t_k = L (y_k - x_k); max_k = x_k + t_k,
-    min_k = y_k - t_k (equal operands give the common value).
+    min_k = y_k - t_k (equal operands give the common value);
+  * tournament over n ciphertexts (each digit a list of n): cross rounds
+    pair ciphertexts [0, h) with [h, 2h), h = n // 2, an odd last one
+    passing on after the winners; then in-slot rounds x <- sel(x, rot(x))
+    with the column rotations sigma_{5^(2^i)} for 2^i = cols/2, .., 1
+    (cols = n_s / 2), then the row swap sigma_{2N-1}.  When max and min
+    are both wanted the first cross round shares one LT; afterwards the two
+    tournaments run separately.  Before a round whose depth
+    (ceil(log2(p-1)) + ceil(log2 d) + 1) would leave less than one level,
+    every ciphertext is refreshed (a stand-in for bootstrapping).
 
 Every operation appends (name, level) to ``trace``; the CUDA path emits the
 same trace, and a test compares them.  The multiplication count is pinned
@@ -216,3 +225,95 @@ class Evaluator:
             mx.append(self.add(x, t))
             mn.append(self.sub(y, t))
         return mx, mn
+
+
+def round_depth(p: int, d: int) -> int:
+    """Levels one max/min round consumes: LT (PS depth + merge depth) + select."""
+    lg = (p - 2).bit_length()
+    return lg + (d - 1).bit_length() + 1
+
+
+def galois_schedule(ns: int, N: int, linear: bool = True):
+    """In-slot rounds: column rotations by cols/2, .., 1, then the row swap."""
+    if not linear or ns <= 2:
+        return [2 * N - 1] if ns == 2 else []
+    cols = ns // 2
+    out, step = [], cols // 2
+    while step >= 1:
+        out.append(pow(5, step, 2 * N))
+        step //= 2
+    out.append(2 * N - 1)
+    return out
+
+
+class Tournament:
+    """max and/or min over every slot of n ciphertexts (per digit)."""
+
+    def __init__(self, ev: "Evaluator", d: int, ns: int, N: int, refresh=None):
+        self.ev, self.d, self.ns, self.N = ev, d, ns, N
+        self.refresh = refresh  # callable(list of Ct) -> list of Ct, or None
+        self.depth = round_depth(ev.p, d)
+        self.refreshes = 0
+
+    def _maybe_refresh(self, digits):
+        lv = min(c.level for dig in digits for c in dig)
+        if lv - self.depth >= 1:  # the round ends at level >= 1
+            return digits
+        assert self.refresh is not None, "round needs more levels than remain and no refresh is given"
+        self.refreshes += 1
+        return [self.refresh(dig) for dig in digits]
+
+    def _select(self, xs, ys, want_max):
+        mx, mn = self.ev.max_min(xs, ys)
+        return mx if want_max else mn
+
+    def run(self, digits, want_max=True, want_min=True):
+        """digits[k] is the list of n ciphertexts of digit k."""
+        n = len(digits[0])
+        out = {}
+        cur = {}
+        first = True
+        while n > 1:
+            h = n // 2
+            kinds = [k for k, w in (("max", want_max), ("min", want_min)) if w]
+            if first:
+                src = self._maybe_refresh(digits)
+                A = [dig[:h] for dig in src]
+                B = [dig[h:2 * h] for dig in src]
+                R = [dig[2 * h:] for dig in src]
+                res = {"max": [[] for _ in range(self.d)], "min": [[] for _ in range(self.d)]}
+                for i in range(h):
+                    mx, mn = self.ev.max_min([A[k][i] for k in range(self.d)], [B[k][i] for k in range(self.d)])
+                    for k in range(self.d):
+                        res["max"][k].append(mx[k])
+                        res["min"][k].append(mn[k])
+                for kind in kinds:
+                    cur[kind] = [res[kind][k] + R[k] for k in range(self.d)]
+                first = False
+            else:
+                for kind in kinds:
+                    src = self._maybe_refresh(cur[kind])
+                    A = [dig[:h] for dig in src]
+                    B = [dig[h:2 * h] for dig in src]
+                    R = [dig[2 * h:] for dig in src]
+                    sel = [[] for _ in range(self.d)]
+                    for i in range(h):
+                        r = self._select([A[k][i] for k in range(self.d)], [B[k][i] for k in range(self.d)],
+                                         kind == "max")
+                        for k in range(self.d):
+                            sel[k].append(r[k])
+                    cur[kind] = [sel[k] + R[k] for k in range(self.d)]
+            n = h + (n % 2)
+        if first:  # a single ciphertext: no cross round
+            for kind, w in (("max", want_max), ("min", want_min)):
+                if w:
+                    cur[kind] = [list(dig) for dig in digits]
+        for g in galois_schedule(self.ns, self.N):
+            for kind in [k for k, w in (("max", want_max), ("min", want_min)) if w]:
+                src = self._maybe_refresh(cur[kind])
+                x = [dig[0] for dig in src]
+                r = [self.ev.rotate(c, g) for c in x]
+                cur[kind] = [[c] for c in self._select(x, r, kind == "max")]
+        for kind in cur:
+            out[kind] = [dig[0] for dig in cur[kind]]
+        return out

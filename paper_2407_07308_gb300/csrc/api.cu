@@ -262,6 +262,9 @@ int sync_check(fhe_ctx *c, const char *where)
 
 }  // namespace
 
+// Stream tags of the seeded samplers (see sample.cu).
+enum { TAG_S = 1, TAG_E_PK = 2, TAG_A_PK = 3, TAG_U = 16, TAG_E0 = 17, TAG_E1 = 18, TAG_KSK = 1024 };
+
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
@@ -386,20 +389,17 @@ extern "C" int64_t fhe_ctx_launches(const fhe_ctx *c) { return c ? c->launches :
 // keys
 // ---------------------------------------------------------------------------
 
-extern "C" int fhe_keygen_explicit(fhe_ctx *c, const int64_t *s, const uint64_t *a, const int64_t *e, fhe_sk **sk,
-                                   fhe_pk **pk)
+// Key generation from device-resident s, e (int64[N]) and a (u64[L][N],
+// coefficient domain): pk = (-a s + p e, a).
+static int keygen_dev(fhe_ctx *c, const int64_t *ds, const u64 *da, const int64_t *de, fhe_sk **sk, fhe_pk **pk)
 {
-    CHECK_CTX(c);
-    if (!s || !a || !e || !sk || !pk) return FHE_EINVAL;
-    LOCK(c);
     const int N = c->N, L = c->L, np = c->np;
     int err = 0;
-    DevBuf ds(c, sizeof(int64_t) * N, &err), de(c, sizeof(int64_t) * N, &err);
     DevBuf ta(c, sizeof(u64) * L * N, &err), te(c, sizeof(u64) * L * N, &err);
     if (err) return fhe_fail(c, err, "keygen: out of memory");
     fhe_sk *S = new fhe_sk;
     S->ctx = c;
-    S->s.assign(s, s + N);
+    S->s.assign(N, 0);
     S->d_s = (u64 *)c->pool.get(sizeof(u64) * np * N, &err);
     fhe_pk *Pk = new fhe_pk;
     Pk->ctx = c;
@@ -409,19 +409,17 @@ extern "C" int fhe_keygen_explicit(fhe_ctx *c, const int64_t *s, const uint64_t 
         fhe_pk_destroy(Pk);
         return fhe_fail(c, err, "keygen: out of memory");
     }
-    cudaMemcpyAsync(ds.p, s, sizeof(int64_t) * N, cudaMemcpyHostToDevice, c->stream);
-    cudaMemcpyAsync(de.p, e, sizeof(int64_t) * N, cudaMemcpyHostToDevice, c->stream);
-    cudaMemcpyAsync(ta.p, a, sizeof(u64) * L * N, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(ta.p, da, sizeof(u64) * L * N, cudaMemcpyDeviceToDevice, c->stream);
     int pr[FHE_MAXP];
     primes_range(pr, np, 0);
-    launch_rns_from_i64(c, ds.i(), nullptr, 1, S->d_s, 1, np, pr);
+    launch_rns_from_i64(c, ds, nullptr, 1, S->d_s, 1, np, pr);
     ntt_blocks(c, S->d_s, S->d_s, 1, np, 0, false);
-    launch_rns_from_i64(c, de.i(), nullptr, (int64_t)c->p, te.u(), 1, L, pr);
+    launch_rns_from_i64(c, de, nullptr, (int64_t)c->p, te.u(), 1, L, pr);
     ntt_blocks(c, te.u(), te.u(), 1, L, 0, false);
     u64 *pk1 = Pk->d + (size_t)L * N;
     ntt_blocks(c, ta.u(), pk1, 1, L, 0, false);
-    // pk0 = e' - a s
-    launch_muladd(c, pk1, S->d_s, te.u(), Pk->d, 1, L, 0, 1);
+    launch_muladd(c, pk1, S->d_s, te.u(), Pk->d, 1, L, 0, 1);  // pk0 = e' - a s
+    cudaMemcpyAsync(S->s.data(), ds, sizeof(int64_t) * N, cudaMemcpyDeviceToHost, c->stream);
     int r = sync_check(c, "keygen");
     if (r) {
         fhe_sk_destroy(S);
@@ -431,6 +429,37 @@ extern "C" int fhe_keygen_explicit(fhe_ctx *c, const int64_t *s, const uint64_t 
     *sk = S;
     *pk = Pk;
     return 0;
+}
+
+extern "C" int fhe_keygen_explicit(fhe_ctx *c, const int64_t *s, const uint64_t *a, const int64_t *e, fhe_sk **sk,
+                                   fhe_pk **pk)
+{
+    CHECK_CTX(c);
+    if (!s || !a || !e || !sk || !pk) return FHE_EINVAL;
+    LOCK(c);
+    const int N = c->N, L = c->L;
+    int err = 0;
+    DevBuf ds(c, sizeof(int64_t) * N, &err), de(c, sizeof(int64_t) * N, &err), da(c, sizeof(u64) * L * N, &err);
+    if (err) return fhe_fail(c, err, "keygen: out of memory");
+    cudaMemcpyAsync(ds.p, s, sizeof(int64_t) * N, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(de.p, e, sizeof(int64_t) * N, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(da.p, a, sizeof(u64) * L * N, cudaMemcpyHostToDevice, c->stream);
+    return keygen_dev(c, ds.i(), da.u(), de.i(), sk, pk);
+}
+
+extern "C" int fhe_keygen(fhe_ctx *c, uint64_t seed, fhe_sk **sk, fhe_pk **pk)
+{
+    CHECK_CTX(c);
+    if (!sk || !pk) return FHE_EINVAL;
+    LOCK(c);
+    const int N = c->N, L = c->L;
+    int err = 0;
+    DevBuf ds(c, sizeof(int64_t) * N, &err), de(c, sizeof(int64_t) * N, &err), da(c, sizeof(u64) * L * N, &err);
+    if (err) return fhe_fail(c, err, "keygen: out of memory");
+    sample_ternary(c, ds.i(), N, seed, TAG_S);
+    sample_gaussian(c, de.i(), N, seed, TAG_E_PK);
+    sample_uniform(c, da.u(), 1, L, seed, TAG_A_PK);
+    return keygen_dev(c, ds.i(), da.u(), de.i(), sk, pk);
 }
 
 extern "C" void fhe_sk_destroy(fhe_sk *sk)
@@ -447,12 +476,11 @@ extern "C" void fhe_pk_destroy(fhe_pk *pk)
     delete pk;
 }
 
-extern "C" int fhe_evk_create_explicit(fhe_ctx *c, const fhe_sk *sk, const int64_t *galois, int n_galois,
-                                       const uint64_t *a, const int64_t *e, fhe_evk **out)
+// Switching keys; the masks a_j and errors e_j of key `key`, digit j come
+// from the host arrays (explicit) or from the seeded samplers.
+static int evk_create(fhe_ctx *c, const fhe_sk *sk, const int64_t *galois, int n_galois, const uint64_t *a,
+                      const int64_t *e, bool seeded, uint64_t seed, fhe_evk **out)
 {
-    CHECK_CTX(c);
-    if (!sk || !a || !e || !out || n_galois < 0 || (n_galois && !galois)) return FHE_EINVAL;
-    LOCK(c);
     const int N = c->N, L = c->L, K = c->K, np = c->np, dnum = (L + K - 1) / K;
     int err = 0;
     DevBuf ta(c, sizeof(u64) * np * N, &err), te(c, sizeof(u64) * np * N, &err);
@@ -485,14 +513,19 @@ extern "C" int fhe_evk_create_explicit(fhe_ctx *c, const fhe_sk *sk, const int64
         E->keys.push_back(k);
         for (int j = 0; j < dnum; j++) {
             const size_t off = ((size_t)key * dnum + j);
-            cudaMemcpyAsync(ta.p, a + off * np * N, sizeof(u64) * np * N, cudaMemcpyHostToDevice, c->stream);
-            cudaMemcpyAsync(de.p, e + off * N, sizeof(int64_t) * N, cudaMemcpyHostToDevice, c->stream);
+            if (seeded) {
+                sample_uniform(c, ta.u(), 1, np, seed, TAG_KSK + 2 * (uint32_t)off);
+                sample_gaussian(c, de.i(), N, seed, TAG_KSK + 2 * (uint32_t)off + 1);
+            } else {
+                cudaMemcpyAsync(ta.p, a + off * np * N, sizeof(u64) * np * N, cudaMemcpyHostToDevice, c->stream);
+                cudaMemcpyAsync(de.p, e + off * N, sizeof(int64_t) * N, cudaMemcpyHostToDevice, c->stream);
+            }
             ntt_blocks(c, ta.u(), ta.u(), 1, np, 0, false);
             launch_rns_from_i64(c, de.i(), nullptr, (int64_t)c->p, te.u(), 1, np, pr);
             ntt_blocks(c, te.u(), te.u(), 1, np, 0, false);
             u64 *k0 = k.d + (size_t)(j * 2 + 0) * np * N, *k1 = k.d + (size_t)(j * 2 + 1) * np * N;
             launch_ksk_digit(c, ta.u(), te.u(), sk->d_s, sp.u(), k0, k1, j * K, std::min((j + 1) * K, L), Pw, Pws);
-            // the staging buffers are reused by the next digit: keep host copies ordered
+            // the staging buffers are reused by the next digit
             if ((err = sync_check(c, "evk digit"))) break;
         }
     }
@@ -502,6 +535,24 @@ extern "C" int fhe_evk_create_explicit(fhe_ctx *c, const fhe_sk *sk, const int64
     }
     *out = E;
     return 0;
+}
+
+extern "C" int fhe_evk_create_explicit(fhe_ctx *c, const fhe_sk *sk, const int64_t *galois, int n_galois,
+                                       const uint64_t *a, const int64_t *e, fhe_evk **out)
+{
+    CHECK_CTX(c);
+    if (!sk || !a || !e || !out || n_galois < 0 || (n_galois && !galois)) return FHE_EINVAL;
+    LOCK(c);
+    return evk_create(c, sk, galois, n_galois, a, e, false, 0, out);
+}
+
+extern "C" int fhe_evk_create(fhe_ctx *c, const fhe_sk *sk, const int64_t *galois, int n_galois, uint64_t seed,
+                              fhe_evk **out)
+{
+    CHECK_CTX(c);
+    if (!sk || !out || n_galois < 0 || (n_galois && !galois)) return FHE_EINVAL;
+    LOCK(c);
+    return evk_create(c, sk, galois, n_galois, nullptr, nullptr, true, seed, out);
 }
 
 extern "C" void fhe_evk_destroy(fhe_evk *evk)
@@ -516,47 +567,62 @@ extern "C" void fhe_evk_destroy(fhe_evk *evk)
 // encryption, decryption, import/export
 // ---------------------------------------------------------------------------
 
+// Encryption from device-resident inputs: m, u, e0, e1 are int64[count][N].
+// Enc(m) = (pk0 u + p e0 + m, pk1 u + p e1) at level L.
+static int encrypt_dev(fhe_ctx *c, const fhe_pk *pk, const int64_t *dm, const int64_t *du, const int64_t *d0,
+                       const int64_t *d1, int count, fhe_ct **out)
+{
+    const int N = c->N, L = c->L;
+    int err = 0;
+    DevBuf U(c, sizeof(u64) * count * L * N, &err), T0(c, sizeof(u64) * count * L * N, &err),
+        T1(c, sizeof(u64) * count * L * N, &err);
+    DevBuf C0(c, sizeof(u64) * count * L * N, &err), C1(c, sizeof(u64) * count * L * N, &err);
+    if (err) return fhe_fail(c, err, "encrypt: out of memory");
+    fhe_ct *ct = ct_new(c, count, 2, L, &err);
+    if (!ct) return err;
+    int pr[FHE_MAXP];
+    primes_range(pr, L, 0);
+    launch_rns_from_i64(c, du, nullptr, 1, U.u(), count, L, pr);
+    launch_rns_from_i64(c, d0, dm, (int64_t)c->p, T0.u(), count, L, pr);
+    launch_rns_from_i64(c, d1, nullptr, (int64_t)c->p, T1.u(), count, L, pr);
+    ntt_blocks(c, U.u(), U.u(), count, L, 0, false);
+    ntt_blocks(c, T0.u(), T0.u(), count, L, 0, false);
+    ntt_blocks(c, T1.u(), T1.u(), count, L, 0, false);
+    launch_muladd(c, U.u(), pk->d, T0.u(), C0.u(), count, L, 0, 0);
+    launch_muladd(c, U.u(), pk->d + (size_t)L * N, T1.u(), C1.u(), count, L, 0, 0);
+    launch_copy_limbs(c, C0.u(), ct->d, count, L, (long long)L * N, 2LL * L * N);
+    launch_copy_limbs(c, C1.u(), ct->d + (size_t)L * N, count, L, (long long)L * N, 2LL * L * N);
+    *out = ct;
+    return 0;
+}
+
+static int encode_batch(fhe_ctx *c, const uint64_t *slots, int count, std::vector<int64_t> &m)
+{
+    for (long long i = 0; i < (long long)count * c->ns; i++)
+        if (slots[i] >= c->p) return fhe_fail(c, FHE_EINVAL, "slot value out of [0, p)");
+    m.assign((size_t)count * c->N, 0);
+    for (int i = 0; i < count; i++) encode_slots(c, slots + (size_t)i * c->ns, m.data() + (size_t)i * c->N);
+    return 0;
+}
+
 extern "C" int fhe_encrypt_explicit(fhe_ctx *c, const fhe_pk *pk, const uint64_t *slots, int count,
                                     const int64_t *u, const int64_t *e0, const int64_t *e1, fhe_ct **out)
 {
     CHECK_CTX(c);
     if (!pk || !slots || !u || !e0 || !e1 || !out || count < 1) return FHE_EINVAL;
     LOCK(c);
-    const int N = c->N, L = c->L;
-    for (long long i = 0; i < (long long)count * c->ns; i++)
-        if (slots[i] >= c->p) return fhe_fail(c, FHE_EINVAL, "slot value out of [0, p)");
-    std::vector<int64_t> m((size_t)count * N);
-    for (int i = 0; i < count; i++) encode_slots(c, slots + (size_t)i * c->ns, m.data() + (size_t)i * N);
-    int err = 0;
-    const size_t vb = sizeof(int64_t) * count * N;
+    std::vector<int64_t> m;
+    int err = encode_batch(c, slots, count, m);
+    if (err) return err;
+    const size_t vb = sizeof(int64_t) * count * c->N;
     DevBuf du(c, vb, &err), d0(c, vb, &err), d1(c, vb, &err), dm(c, vb, &err);
-    DevBuf U(c, sizeof(u64) * count * L * N, &err), T0(c, sizeof(u64) * count * L * N, &err),
-        T1(c, sizeof(u64) * count * L * N, &err);
     if (err) return fhe_fail(c, err, "encrypt: out of memory");
-    fhe_ct *ct = ct_new(c, count, 2, L, &err);
-    if (!ct) return err;
     cudaMemcpyAsync(du.p, u, vb, cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(d0.p, e0, vb, cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(d1.p, e1, vb, cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(dm.p, m.data(), vb, cudaMemcpyHostToDevice, c->stream);
-    int pr[FHE_MAXP];
-    primes_range(pr, L, 0);
-    launch_rns_from_i64(c, du.i(), nullptr, 1, U.u(), count, L, pr);
-    launch_rns_from_i64(c, d0.i(), dm.i(), (int64_t)c->p, T0.u(), count, L, pr);
-    launch_rns_from_i64(c, d1.i(), nullptr, (int64_t)c->p, T1.u(), count, L, pr);
-    ntt_blocks(c, U.u(), U.u(), count, L, 0, false);
-    ntt_blocks(c, T0.u(), T0.u(), count, L, 0, false);
-    ntt_blocks(c, T1.u(), T1.u(), count, L, 0, false);
-    // c0 = pk0 u + t0, c1 = pk1 u + t1; write into [count][2][L][N]
-    DevBuf C0(c, sizeof(u64) * count * L * N, &err), C1(c, sizeof(u64) * count * L * N, &err);
-    if (err) {
-        fhe_ct_destroy(ct);
-        return fhe_fail(c, err, "encrypt: out of memory");
-    }
-    launch_muladd(c, U.u(), pk->d, T0.u(), C0.u(), count, L, 0, 0);
-    launch_muladd(c, U.u(), pk->d + (size_t)L * N, T1.u(), C1.u(), count, L, 0, 0);
-    launch_copy_limbs(c, C0.u(), ct->d, count, L, (long long)L * N, 2LL * L * N);
-    launch_copy_limbs(c, C1.u(), ct->d + (size_t)L * N, count, L, (long long)L * N, 2LL * L * N);
+    fhe_ct *ct = nullptr;
+    if ((err = encrypt_dev(c, pk, dm.i(), du.i(), d0.i(), d1.i(), count, &ct))) return err;
     int r = sync_check(c, "encrypt");
     if (r) {
         fhe_ct_destroy(ct);
@@ -566,53 +632,125 @@ extern "C" int fhe_encrypt_explicit(fhe_ctx *c, const fhe_pk *pk, const uint64_t
     return 0;
 }
 
+extern "C" int fhe_encrypt(fhe_ctx *c, const fhe_pk *pk, const uint64_t *slots, int count, uint64_t seed, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!pk || !slots || !out || count < 1) return FHE_EINVAL;
+    LOCK(c);
+    std::vector<int64_t> m;
+    int err = encode_batch(c, slots, count, m);
+    if (err) return err;
+    const long long n = (long long)count * c->N;
+    DevBuf du(c, sizeof(int64_t) * n, &err), d0(c, sizeof(int64_t) * n, &err), d1(c, sizeof(int64_t) * n, &err),
+        dm(c, sizeof(int64_t) * n, &err);
+    if (err) return fhe_fail(c, err, "encrypt: out of memory");
+    cudaMemcpyAsync(dm.p, m.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->stream);
+    sample_ternary(c, du.i(), n, seed, TAG_U);
+    sample_gaussian(c, d0.i(), n, seed, TAG_E0);
+    sample_gaussian(c, d1.i(), n, seed, TAG_E1);
+    fhe_ct *ct = nullptr;
+    if ((err = encrypt_dev(c, pk, dm.i(), du.i(), d0.i(), d1.i(), count, &ct))) return err;
+    int r = sync_check(c, "encrypt");
+    if (r) {
+        fhe_ct_destroy(ct);
+        return r;
+    }
+    *out = ct;
+    return 0;
+}
+
+// Plaintext coefficients of a batch, on the device: modulus switch a copy to
+// one prime, t = c0 + c1 s (limb 0), INTT, centred mod q0, then mod p.
+static int decrypt_coeffs_dev(fhe_ctx *c, const fhe_sk *sk, const fhe_ct *ct, int64_t *dm)
+{
+    const int N = c->N, count = ct->count;
+    fhe_ct *one = nullptr;
+    int err = op_lower(c, ct, 1, &one);
+    if (err) return err;
+    DevBuf t(c, sizeof(u64) * count * N, &err), c0(c, sizeof(u64) * count * N, &err),
+        c1(c, sizeof(u64) * count * N, &err);
+    if (err) {
+        fhe_ct_destroy(one);
+        return fhe_fail(c, err, "decrypt: out of memory");
+    }
+    launch_copy_limbs(c, one->d, c0.u(), count, 1, 2LL * N, N);
+    launch_copy_limbs(c, one->d + N, c1.u(), count, 1, 2LL * N, N);
+    launch_muladd(c, c1.u(), sk->d_s, c0.u(), t.u(), count, 1, 0, 0);
+    ntt_blocks(c, t.u(), t.u(), count, 1, 0, true);
+    launch_centre_mod_p(c, t.u(), dm, (long long)count * N);
+    fhe_ct_destroy(one);
+    return 0;
+}
+
 extern "C" int fhe_decrypt(fhe_ctx *c, const fhe_sk *sk, const fhe_ct *ct, uint64_t *slots)
 {
     CHECK_CTX(c);
     if (!sk || !ct || !slots || ct->npoly != 2) return FHE_EINVAL;
     LOCK(c);
     const int N = c->N, count = ct->count;
-    fhe_ct *one = nullptr;
-    int err = op_lower(c, ct, 1, &one);
-    if (err) return err;
-    DevBuf t(c, sizeof(u64) * count * N, &err);
-    if (err) {
-        fhe_ct_destroy(one);
-        return fhe_fail(c, err, "decrypt: out of memory");
-    }
-    // t = c0 + c1 s at limb 0 for each ct (one is [count][2][1][N]): gather
-    // c0 and c1 into contiguous [count][N] blocks first
-    {
-        DevBuf c0(c, sizeof(u64) * count * N, &err), c1(c, sizeof(u64) * count * N, &err);
-        if (err) {
-            fhe_ct_destroy(one);
-            return fhe_fail(c, err, "decrypt: out of memory");
-        }
-        launch_copy_limbs(c, one->d, c0.u(), count, 1, 2LL * N, N);
-        launch_copy_limbs(c, one->d + N, c1.u(), count, 1, 2LL * N, N);
-        launch_muladd(c, c1.u(), sk->d_s, c0.u(), t.u(), count, 1, 0, 0);
-    }
-    ntt_blocks(c, t.u(), t.u(), count, 1, 0, true);
-    std::vector<u64> h((size_t)count * N);
-    cudaMemcpyAsync(h.data(), t.p, sizeof(u64) * h.size(), cudaMemcpyDeviceToHost, c->stream);
-    int r = sync_check(c, "decrypt");
-    fhe_ct_destroy(one);
-    if (r) return r;
-    const u64 q0 = c->q[0], p = c->p;
-    std::vector<int64_t> m(N);
-    for (int i = 0; i < count; i++) {
-        for (int n = 0; n < N; n++) {
-            const u64 v = h[(size_t)i * N + n];
-            // centred representative mod q0, then mod p
-            const int64_t cv = v > q0 / 2 ? -(int64_t)(q0 - v) : (int64_t)v;
-            int64_t mp = cv % (int64_t)p;
-            if (mp < 0) mp += (int64_t)p;
-            m[n] = mp;
-        }
-        if (!decode_slots(c, m.data(), slots + (size_t)i * c->ns))
+    int err = 0;
+    DevBuf dm(c, sizeof(int64_t) * count * N, &err);
+    if (err) return fhe_fail(c, err, "decrypt: out of memory");
+    if ((err = decrypt_coeffs_dev(c, sk, ct, dm.i()))) return err;
+    std::vector<int64_t> m((size_t)count * N);
+    cudaMemcpyAsync(m.data(), dm.p, sizeof(int64_t) * m.size(), cudaMemcpyDeviceToHost, c->stream);
+    if ((err = sync_check(c, "decrypt"))) return err;
+    for (int i = 0; i < count; i++)
+        if (!decode_slots(c, m.data() + (size_t)i * N, slots + (size_t)i * c->ns))
             return fhe_fail(c, FHE_EINVAL, "decrypt: plaintext is not a slot encoding");
-    }
     return 0;
+}
+
+// Refresh (a stand-in for bootstrapping, which the paper does not cover): the
+// plaintext of every ciphertext is recovered with the secret key on the
+// device and encrypted again at the top level with fresh randomness.
+static int refresh_dev(fhe_ctx *c, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct *ct, const int64_t *du,
+                       const int64_t *d0, const int64_t *d1, fhe_ct **out)
+{
+    int err = 0;
+    DevBuf dm(c, sizeof(int64_t) * ct->count * c->N, &err);
+    if (err) return fhe_fail(c, err, "refresh: out of memory");
+    if ((err = decrypt_coeffs_dev(c, sk, ct, dm.i()))) return err;
+    return encrypt_dev(c, pk, dm.i(), du, d0, d1, ct->count, out);
+}
+
+extern "C" int fhe_refresh_explicit(fhe_ctx *c, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct *ct,
+                                    const int64_t *u, const int64_t *e0, const int64_t *e1, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!sk || !pk || !ct || ct->npoly != 2 || !u || !e0 || !e1 || !out) return FHE_EINVAL;
+    LOCK(c);
+    const size_t vb = sizeof(int64_t) * ct->count * c->N;
+    int err = 0;
+    DevBuf du(c, vb, &err), d0(c, vb, &err), d1(c, vb, &err);
+    if (err) return fhe_fail(c, err, "refresh: out of memory");
+    cudaMemcpyAsync(du.p, u, vb, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(d0.p, e0, vb, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(d1.p, e1, vb, cudaMemcpyHostToDevice, c->stream);
+    if ((err = refresh_dev(c, sk, pk, ct, du.i(), d0.i(), d1.i(), out))) return err;
+    return sync_check(c, "refresh");
+}
+
+int refresh_seeded(fhe_ctx *c, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct *ct, uint64_t seed, fhe_ct **out)
+{
+    const long long n = (long long)ct->count * c->N;
+    int err = 0;
+    DevBuf du(c, sizeof(int64_t) * n, &err), d0(c, sizeof(int64_t) * n, &err), d1(c, sizeof(int64_t) * n, &err);
+    if (err) return fhe_fail(c, err, "refresh: out of memory");
+    sample_ternary(c, du.i(), n, seed, TAG_U);
+    sample_gaussian(c, d0.i(), n, seed, TAG_E0);
+    sample_gaussian(c, d1.i(), n, seed, TAG_E1);
+    return refresh_dev(c, sk, pk, ct, du.i(), d0.i(), d1.i(), out);
+}
+
+extern "C" int fhe_refresh(fhe_ctx *c, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct *ct, uint64_t seed,
+                           fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!sk || !pk || !ct || ct->npoly != 2 || !out) return FHE_EINVAL;
+    LOCK(c);
+    int err = refresh_seeded(c, sk, pk, ct, seed, out);
+    return err ? err : fhe_cuda_check(c, cudaGetLastError(), "refresh");
 }
 
 extern "C" int fhe_ct_load_coeff(fhe_ctx *c, fhe_ct *ct, const uint64_t *host)
@@ -991,27 +1129,6 @@ extern "C" int fhe_selftest_modarith(uint64_t prime_mod, uint64_t prime_lo, uint
     return bad;
 }
 
-// Seeded key generation and encryption draw their randomness on the device.
-extern "C" int fhe_keygen(fhe_ctx *c, uint64_t seed, fhe_sk **sk, fhe_pk **pk)
-{
-    (void)seed; (void)sk; (void)pk;
-    return c ? fhe_fail(c, FHE_EUNSUPPORTED, "seeded keygen not available yet") : FHE_EINVAL;
-}
-
-extern "C" int fhe_evk_create(fhe_ctx *c, const fhe_sk *sk, const int64_t *galois, int n_galois, uint64_t seed,
-                              fhe_evk **out)
-{
-    (void)sk; (void)galois; (void)n_galois; (void)seed; (void)out;
-    return c ? fhe_fail(c, FHE_EUNSUPPORTED, "seeded evk not available yet") : FHE_EINVAL;
-}
-
-extern "C" int fhe_encrypt(fhe_ctx *c, const fhe_pk *pk, const uint64_t *slots, int count, uint64_t seed,
-                           fhe_ct **out)
-{
-    (void)pk; (void)slots; (void)count; (void)seed; (void)out;
-    return c ? fhe_fail(c, FHE_EUNSUPPORTED, "seeded encrypt not available yet") : FHE_EINVAL;
-}
-
 // ---------------------------------------------------------------------------
 // captured comparison plans (CUDA graphs)
 // ---------------------------------------------------------------------------
@@ -1114,4 +1231,29 @@ extern "C" void fhe_plan_destroy(fhe_plan *P)
     for (auto &kv : P->held)
         for (void *p : kv.second) c->pool.put(p);
     delete P;
+}
+
+// ---------------------------------------------------------------------------
+// tournament
+// ---------------------------------------------------------------------------
+
+extern "C" int fhe_tournament_galois(const fhe_ctx *c, int64_t *galois, int cap)
+{
+    if (!c || cap < 0) return FHE_EINVAL;
+    const std::vector<int64_t> g = tournament_galois(c);
+    for (int i = 0; i < (int)g.size() && i < cap; i++) galois[i] = g[i];
+    return (int)g.size();
+}
+
+extern "C" int fhe_tournament(fhe_ctx *c, const fhe_evk *evk, const fhe_sk *sk, const fhe_pk *pk,
+                              const fhe_ct *const *x, int d, uint64_t seed, fhe_ct **out_max, fhe_ct **out_min)
+{
+    CHECK_CTX(c);
+    if (!evk || evk->ctx != c || !x || d < 1 || (!out_max && !out_min)) return FHE_EINVAL;
+    for (int k = 0; k < d; k++)
+        if (!same_ctx(c, x[k]) || x[k]->npoly != 2 || x[k]->count != x[0]->count || x[k]->level != x[0]->level)
+            return fhe_fail(c, FHE_EMISMATCH, "tournament operands differ in shape");
+    LOCK(c);
+    int e = circuit_tournament(c, evk, sk, pk, x, d, out_max != nullptr, out_min != nullptr, seed, out_max, out_min);
+    return e ? e : fhe_cuda_check(c, cudaGetLastError(), "tournament");
 }

@@ -703,3 +703,211 @@ int circuit_max_min(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, cons
     C.finish();
     return C.err;
 }
+
+// ---------------------------------------------------------------------------
+// tournament max / min
+// ---------------------------------------------------------------------------
+//
+// Same schedule as the CPU oracle: cross rounds pair ciphertexts [0, h) with
+// [h, 2h) of the batch (h = n / 2, an odd last one passes on after the
+// winners), then in-slot rounds x <- sel(x, rotate(x, g)) with
+// g = 5^(2^i) mod 2N for 2^i = cols/2 .. 1 and finally g = 2N - 1.  The first
+// cross round computes max and min from one LT; afterwards the two
+// tournaments run separately.  A round that would end below level 1 is
+// preceded by a refresh of the batch (a stand-in for bootstrapping).
+
+int op_slice(fhe_ctx *c, const fhe_ct *a, int start, int n, fhe_ct **out)
+{
+    if (start < 0 || n < 1 || start + n > a->count) return fhe_fail(c, FHE_EINVAL, "slice out of range");
+    int err = 0;
+    fhe_ct *r = ct_new(c, n, a->npoly, a->level, &err);
+    if (!r) return err;
+    const size_t per = (size_t)a->npoly * a->level * c->N;
+    cudaMemcpyAsync(r->d, a->d + per * start, sizeof(u64) * per * n, cudaMemcpyDeviceToDevice, c->stream);
+    *out = r;
+    return 0;
+}
+
+int op_concat(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **out)
+{
+    if (a->level != b->level || a->npoly != b->npoly) return fhe_fail(c, FHE_EMISMATCH, "concat: shapes differ");
+    int err = 0;
+    fhe_ct *r = ct_new(c, a->count + b->count, a->npoly, a->level, &err);
+    if (!r) return err;
+    cudaMemcpyAsync(r->d, a->d, a->bytes, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(r->d + a->bytes / sizeof(u64), b->d, b->bytes, cudaMemcpyDeviceToDevice, c->stream);
+    *out = r;
+    return 0;
+}
+
+namespace {
+
+struct Tourney {
+    fhe_ctx *c;
+    const fhe_evk *evk;
+    const fhe_sk *sk;
+    const fhe_pk *pk;
+    int d, depth;
+    uint64_t seed;
+    int refreshes = 0, err = 0;
+    std::vector<fhe_ct *> owned;
+
+    fhe_ct *own(fhe_ct *x)
+    {
+        owned.push_back(x);
+        return x;
+    }
+    ~Tourney()
+    {
+        for (fhe_ct *x : owned)
+            if (x) fhe_ct_destroy(x);
+    }
+    fhe_ct *release(fhe_ct *x)
+    {
+        for (auto &o : owned)
+            if (o == x) o = nullptr;
+        return x;
+    }
+    // refresh every digit batch when the next round would end below level 1
+    bool ready(std::vector<fhe_ct *> &digs)
+    {
+        if (err) return false;
+        if (digs[0]->level - depth >= 1) return true;
+        if (!sk || !pk) {
+            err = fhe_fail(c, FHE_ELEVEL, "tournament round needs a refresh: pass the secret and public keys");
+            return false;
+        }
+        for (int k = 0; k < d && !err; k++) {
+            fhe_ct *r = nullptr;
+            if ((err = refresh_seeded(c, sk, pk, digs[k], seed + 1000003ull * (uint64_t)refreshes + k, &r)))
+                return false;
+            digs[k] = own(r);
+        }
+        refreshes++;
+        return !err;
+    }
+    // one cross round on the batch: winners of [0,h) vs [h,2h), leftover after
+    void cross(std::vector<fhe_ct *> &src, bool both, std::vector<fhe_ct *> *mx, std::vector<fhe_ct *> *mn)
+    {
+        const int n = src[0]->count, h = n / 2;
+        std::vector<fhe_ct *> A(d), B(d), R(d, nullptr), smx(d, nullptr), smn(d, nullptr);
+        for (int k = 0; k < d && !err; k++) {
+            fhe_ct *t = nullptr;
+            if ((err = op_slice(c, src[k], 0, h, &t))) return;
+            A[k] = own(t);
+            if ((err = op_slice(c, src[k], h, h, &t))) return;
+            B[k] = own(t);
+            if (n % 2) {
+                if ((err = op_slice(c, src[k], 2 * h, 1, &t))) return;
+                R[k] = own(t);
+            }
+        }
+        if ((err = circuit_max_min(c, evk, A.data(), B.data(), d, mx ? smx.data() : nullptr,
+                                   mn ? smn.data() : nullptr)))
+            return;
+        (void)both;
+        for (int s = 0; s < 2; s++) {
+            std::vector<fhe_ct *> *dst = s == 0 ? mx : mn;
+            std::vector<fhe_ct *> &sel = s == 0 ? smx : smn;
+            if (!dst) continue;
+            for (int k = 0; k < d && !err; k++) {
+                own(sel[k]);
+                if (!R[k]) {
+                    (*dst)[k] = sel[k];
+                    continue;
+                }
+                fhe_ct *low = nullptr, *cat = nullptr;
+                if ((err = op_lower(c, R[k], sel[k]->level, &low))) return;
+                own(low);
+                if ((err = op_concat(c, sel[k], low, &cat))) return;
+                (*dst)[k] = own(cat);
+            }
+        }
+    }
+    // in-slot round: x <- sel(x, sigma_g(x))
+    void inslot(std::vector<fhe_ct *> &cur, int64_t g, bool want_max)
+    {
+        const KeySwitchKey *key = evk->find(g);
+        if (!key) {
+            err = fhe_fail(c, FHE_ENOKEY, "tournament: missing rotation key");
+            return;
+        }
+        std::vector<fhe_ct *> r(d), sel(d, nullptr);
+        for (int k = 0; k < d && !err; k++) {
+            fhe_ct *t = nullptr;
+            if ((err = op_rotate(c, *key, cur[k], &t))) return;
+            r[k] = own(t);
+        }
+        if ((err = circuit_max_min(c, evk, cur.data(), r.data(), d, want_max ? sel.data() : nullptr,
+                                   want_max ? nullptr : sel.data())))
+            return;
+        for (int k = 0; k < d; k++) cur[k] = own(sel[k]);
+    }
+};
+
+}  // namespace
+
+std::vector<int64_t> tournament_galois(const fhe_ctx *c)
+{
+    std::vector<int64_t> g;
+    const int64_t twoN = 2 * (int64_t)c->N;
+    if (!c->slots_linear || c->ns <= 2) {
+        if (c->ns == 2) g.push_back(twoN - 1);
+        return g;
+    }
+    for (int step = c->ns / 4; step >= 1; step /= 2) g.push_back((int64_t)host_powmod(5, step, twoN));
+    g.push_back(twoN - 1);
+    return g;
+}
+
+int circuit_tournament(fhe_ctx *c, const fhe_evk *evk, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct *const *x,
+                       int d, bool want_max, bool want_min, uint64_t seed, fhe_ct **out_max, fhe_ct **out_min)
+{
+    Tourney T{c, evk, sk, pk, d, 0, seed};
+    int lg = 0;
+    while ((1 << lg) < (int)c->p - 1) lg++;
+    int ld = 0;
+    while ((1 << ld) < d) ld++;
+    T.depth = lg + ld + 1;
+    std::vector<fhe_ct *> mx(d), mn(d);
+    int n = x[0]->count;
+    bool first = true;
+    while (n > 1 && !T.err) {
+        if (first) {
+            std::vector<fhe_ct *> src(d);  // read only: slices and refreshes make new batches
+            for (int k = 0; k < d; k++) src[k] = const_cast<fhe_ct *>(x[k]);
+            if (!T.ready(src)) break;
+            T.cross(src, want_max && want_min, want_max ? &mx : nullptr, want_min ? &mn : nullptr);
+            first = false;
+        } else {
+            if (want_max && T.ready(mx)) {
+                std::vector<fhe_ct *> src = mx;
+                T.cross(src, false, &mx, nullptr);
+            }
+            if (want_min && T.ready(mn)) {
+                std::vector<fhe_ct *> src = mn;
+                T.cross(src, false, nullptr, &mn);
+            }
+        }
+        n = n / 2 + n % 2;
+    }
+    if (first && !T.err)
+        for (int k = 0; k < d; k++) {
+            fhe_ct *cp = nullptr;
+            if ((T.err = op_lower(c, x[k], x[k]->level, &cp))) break;  // a copy
+            mx[k] = T.own(cp);
+            if ((T.err = op_lower(c, x[k], x[k]->level, &cp))) break;
+            mn[k] = T.own(cp);
+        }
+    for (int64_t g : tournament_galois(c)) {
+        if (T.err) break;
+        if (want_max && T.ready(mx)) T.inslot(mx, g, true);
+        if (want_min && T.ready(mn)) T.inslot(mn, g, false);
+    }
+    if (T.err) return T.err;
+    for (int k = 0; k < d; k++) {
+        if (want_max) out_max[k] = T.release(mx[k]);
+        if (want_min) out_min[k] = T.release(mn[k]);
+    }
+    return 0;
+}

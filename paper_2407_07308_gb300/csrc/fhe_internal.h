@@ -253,6 +253,14 @@ void launch_lincomb(fhe_ctx *c, const u64 *const *x, const u64 (*w)[FHE_MAXP], i
                     int level);
 int op_lincomb(fhe_ctx *c, const fhe_ct *const *x, const int64_t *k, int n, fhe_ct **out);
 
+// seeded samplers (sample.cu)
+void sample_ternary(fhe_ctx *c, int64_t *out, long long n, uint64_t seed, uint32_t tag);
+void sample_gaussian(fhe_ctx *c, int64_t *out, long long n, uint64_t seed, uint32_t tag);
+void sample_uniform(fhe_ctx *c, u64 *out, int outer, int nl, uint64_t seed, uint32_t tag);
+// out[i] = centred(x[i] mod q0) mod p, as int64 in [0, p)
+void launch_centre_mod_p(fhe_ctx *c, const u64 *x, int64_t *out, long long n);
+int refresh_seeded(fhe_ctx *c, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct *ct, uint64_t seed, fhe_ct **out);
+
 // evaluation (eval.cu)
 int op_lower(fhe_ctx *c, const fhe_ct *a, int level, fhe_ct **out);
 int op_modswitch1(fhe_ctx *c, const fhe_ct *a, fhe_ct **out);
@@ -270,6 +278,11 @@ int circuit_compare(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, cons
 int circuit_max_min(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
                     fhe_ct **mx, fhe_ct **mn);
 int64_t centred_const(const fhe_ctx *c, int64_t k);
+int op_slice(fhe_ctx *c, const fhe_ct *a, int start, int n, fhe_ct **out);
+int op_concat(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **out);
+std::vector<int64_t> tournament_galois(const fhe_ctx *c);
+int circuit_tournament(fhe_ctx *c, const fhe_evk *evk, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct *const *x,
+                       int d, bool want_max, bool want_min, uint64_t seed, fhe_ct **out_max, fhe_ct **out_min);
 
 void launch_copy_limbs(fhe_ctx *c, const u64 *in, u64 *out, int outer, int nl, long long in_outer,
                        long long out_outer);

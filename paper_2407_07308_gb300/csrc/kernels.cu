@@ -213,6 +213,18 @@ __global__ void k_ksk_digit(const u64 *__restrict__ a, const u64 *__restrict__ e
     }
 }
 
+// Decryption residues (limb 0, canonical mod q0) -> plaintext coefficients:
+// the centred representative in (-q0/2, q0/2], reduced mod p into [0, p).
+__global__ void k_centre_mod_p(const u64 *__restrict__ x, int64_t *__restrict__ out, long long n, u64 q0, int64_t p)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const u64 v = x[i];
+        const int64_t cv = v > q0 / 2 ? -(int64_t)(q0 - v) : (int64_t)v;
+        int64_t r = cv % p;
+        out[i] = r < 0 ? r + p : r;
+    }
+}
+
 // out = sum_t w_t x_t (mod q_i), up to 8 ciphertext batches of one shape;
 // w[t][i] is the scalar of term t reduced mod q_i.  Eight products of
 // canonical residues stay below the Barrett bound, so one reduction suffices.
@@ -435,4 +447,9 @@ void launch_lincomb(fhe_ctx *c, const u64 *const *x, const u64 (*w)[FHE_MAXP], i
     }
     LAUNCH_CLS_W(FHE_K_ELEMWISE, n + 1, k_lincomb, (long long)outer * level * c->N, lc, out,
                  (long long)outer * level * c->N, c->logN, level, c->d_mq);
+}
+
+void launch_centre_mod_p(fhe_ctx *c, const u64 *x, int64_t *out, long long n)
+{
+    LAUNCH(k_centre_mod_p, n, x, out, n, c->q[0], (int64_t)c->p);
 }

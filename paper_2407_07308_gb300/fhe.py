@@ -111,6 +111,11 @@ def lib() -> ctypes.CDLL:
             "fhe_ntt_inverse": (ci, [vp, vp, vp, ci]),
             "fhe_selftest_modarith": (ci, [u64, u64, u64, ci, ci]),
             "fhe_ctx_profile": (ci, [vp, ci]),
+            "fhe_tournament_galois": (ci, [vp, vp, ci]),
+            "fhe_tournament": (ci, [vp, vp, vp, vp, vp, ci, u64, vp, vp]),
+            "fhe_refresh_explicit": (ci, [vp, vp, vp, vp, vp, vp, vp, POINTER(vp)]),
+            "fhe_refresh": (ci, [vp, vp, vp, vp, u64, POINTER(vp)]),
+            "fhe_philox_blocks": (ci, [u64, ctypes.c_uint32, ci, vp]),
             "fhe_compare_plan": (ci, [vp, vp, vp, vp, ci, ci, ci, ci, POINTER(vp)]),
             "fhe_plan_run": (ci, [vp]),
             "fhe_plan_result": (ci, [vp, ci, POINTER(vp)]),
@@ -289,6 +294,27 @@ def fhe_decrypt(ctx, sk, ct):
     return out
 
 
+def fhe_refresh_explicit(ctx, sk, pk, ct, u, e0, e1):
+    u = np.ascontiguousarray(u, dtype=np.int64)
+    e0 = np.ascontiguousarray(e0, dtype=np.int64)
+    e1 = np.ascontiguousarray(e1, dtype=np.int64)
+    out = c_void_p()
+    _check(lib().fhe_refresh_explicit(ctx, sk, pk, ct, _ptr(u), _ptr(e0), _ptr(e1), ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_refresh(ctx, sk, pk, ct, seed: int):
+    out = c_void_p()
+    _check(lib().fhe_refresh(ctx, sk, pk, ct, seed, ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_philox_blocks(seed: int, tag: int, n: int):
+    out = np.zeros(4 * n, dtype=np.uint32)
+    _check(lib().fhe_philox_blocks(seed, tag, n, _ptr(out)))
+    return out.reshape(n, 4)
+
+
 def fhe_ct_destroy(ct):
     lib().fhe_ct_destroy(ct)
 
@@ -428,6 +454,21 @@ def fhe_plan_nodes(plan) -> int:
 
 def fhe_plan_destroy(plan):
     lib().fhe_plan_destroy(plan)
+
+
+def fhe_tournament_galois(ctx):
+    n = _check(lib().fhe_tournament_galois(ctx, None, 0), ctx)
+    out = np.zeros(max(n, 1), dtype=np.int64)
+    lib().fhe_tournament_galois(ctx, _ptr(out), n)
+    return [int(v) for v in out[:n]]
+
+
+def fhe_tournament(ctx, evk, sk, pk, xs, seed: int, want_max=True, want_min=True):
+    d = len(xs)
+    mx, mn = (c_void_p * d)(), (c_void_p * d)()
+    _check(lib().fhe_tournament(ctx, evk, sk, pk, _handles(xs), d, seed, mx if want_max else None,
+                                mn if want_min else None), ctx)
+    return ([c_void_p(v) for v in mx] if want_max else None), ([c_void_p(v) for v in mn] if want_min else None)
 
 
 def fhe_trace_enable(ctx, on: bool):
