@@ -267,6 +267,40 @@ int fhe_tournament_galois(const fhe_ctx *ctx, int64_t *galois, int cap);
 int fhe_tournament(fhe_ctx *ctx, const fhe_evk *evk, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct *const *x,
                    int d, uint64_t seed, fhe_ct **out_max, fhe_ct **out_min);
 
+/* ---- batches of uneven requests ------------------------------------------------- */
+
+enum { FHE_JOB_COMPARE = 1, /* out0 -> &LT handle, out1 -> &EQ handle (either NULL) */
+       FHE_JOB_MAXMIN = 2   /* out0 -> d max digit handles, out1 -> d min digit handles */ };
+
+/* One request: the d digit handles x[], y[] (equal count and level) of one
+ * context.  Output handles are written at submission and hold the results
+ * once fhe_batch_wait returns 0; the caller destroys them. */
+typedef struct {
+    fhe_ctx *ctx;
+    const fhe_evk *evk;
+    int kind;
+    int d;
+    const fhe_ct *const *x;
+    const fhe_ct *const *y;
+    fhe_ct **out0;
+    fhe_ct **out1;
+} fhe_job;
+
+typedef struct fhe_batch fhe_batch;
+
+/* Submits n jobs of any mix of contexts (ring degree, plaintext prime),
+ * digit counts and levels.  Jobs of one (context, keys, kind, digits, level)
+ * are concatenated into one batch; every group of a context runs in one
+ * dependency-scheduled circuit on 8 streams, so groups overlap on the device;
+ * contexts run on their own streams.  Each result equals what the job gives
+ * alone.  Enqueues and returns; `*out` tracks completion. */
+int fhe_batch_submit(const fhe_job *jobs, int n, fhe_batch **out);
+/* 0 once every job of the batch is complete; FHE_ETIMEOUT if that takes
+ * longer than timeout_ms (the batch keeps running; wait again later). */
+int fhe_batch_wait(fhe_batch *batch, int timeout_ms);
+/* Waits for the batch and releases its tracking state (not the outputs). */
+void fhe_batch_destroy(fhe_batch *batch);
+
 /* ---- operation trace --------------------------------------------------------- */
 
 /* Op codes recorded while tracing is on. */

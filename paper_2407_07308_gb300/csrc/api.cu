@@ -68,7 +68,7 @@ void *Pool::get(size_t bytes, int *err)
     }
     if (fail_after > 0) fail_after--;
     void *p = nullptr;
-    if (cap_free) {
+    if (in_capture) {
         // a miss while a graph is captured: plain cudaMalloc (permitted in a
         // relaxed capture), never the caller's allocator on a capturing stream
         if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
@@ -1164,6 +1164,7 @@ extern "C" int fhe_compare_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *co
     // of the graph and hold the times of the latest replay
     c->prof_on = prof;
     c->pool.cap_free = &P->held;
+    c->pool.in_capture = true;
     // record on a private stream (the legacy NULL stream cannot be captured);
     // the graph is launched on the context's stream, whatever it is
     cudaStream_t user = c->stream, cap = nullptr;
@@ -1186,6 +1187,7 @@ extern "C" int fhe_compare_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *co
         cudaStreamDestroy(cap);
     }
     c->pool.cap_free = nullptr;
+    c->pool.in_capture = false;
     c->prof_on = prof;
     c->tracing = tr;
     if (!e) e = fhe_cuda_check(c, cudaGraphInstantiate(&P->exec, P->graph, 0), "graph instantiate");

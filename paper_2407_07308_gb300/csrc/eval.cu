@@ -343,14 +343,17 @@ int op_mul_relin(fhe_ctx *c, const KeySwitchKey &rlk, const fhe_ct *a, const fhe
 // low) into L = L_hi + E_hi L_lo and E = E_hi E_lo.
 namespace {
 
-// Dependency-driven streams while a plan is captured.  Every circuit op is
-// issued on one of S streams (round robin) after waiting for the events of
-// its inputs, and records an event for its output; the capture therefore
-// holds the circuit's true dependency graph and the replay runs independent
-// products (both digits, the baby powers of one wave, the leaves, the tree
-// nodes of one level) concurrently.  Scratch freed on a stream goes to that
-// stream's capture-private free list, so no block crosses streams before the
-// final join, where the original stream waits for every stream used.
+// Dependency-driven streams while a plan is captured (or a batch runs with
+// c->multistream).  Every circuit op is issued on one of S streams (round
+// robin) after waiting for the events of its inputs, and records an event for
+// its output; a capture therefore holds the circuit's true dependency graph,
+// and independent products (digits, the baby powers of one wave, the leaves,
+// the tree nodes of one level, other requests of a batch) run concurrently.
+// Every stream first waits for an event recorded on the original stream, so
+// blocks freed there earlier are idle.  Scratch freed on a stream goes to
+// that stream's private free list, so no block crosses streams before the
+// final join, where the original stream waits for every stream used and the
+// blocks go back to the plan (capture) or to the pool (direct).
 struct Dag {
     static constexpr int S = 8;
     fhe_ctx *c;
@@ -365,7 +368,7 @@ struct Dag {
 
     explicit Dag(fhe_ctx *ctx) : c(ctx)
     {
-        if (!c->capturing) return;
+        if (!c->capturing && !c->multistream) return;
         on = true;
         main = c->stream;
         main_free = c->pool.cap_free;
@@ -427,8 +430,14 @@ struct Dag {
         c->pool.cap_free = main_free;
         for (auto &f : frees)
             for (auto &kv : f) {
-                auto &dst = (*main_free)[kv.first];
-                dst.insert(dst.end(), kv.second.begin(), kv.second.end());
+                if (main_free) {  // capture: the plan keeps them
+                    auto &dst = (*main_free)[kv.first];
+                    dst.insert(dst.end(), kv.second.begin(), kv.second.end());
+                } else {  // direct: back to the pool, usable on the original stream
+                    auto &dst = c->pool.free_lists[kv.first];
+                    dst.insert(dst.end(), kv.second.begin(), kv.second.end());
+                    c->pool.in_use -= kv.first * kv.second.size();
+                }
             }
         for (fhe_ct *x : marked) x->ready = nullptr, x->on = nullptr;
         on = false;
@@ -674,19 +683,10 @@ struct Circuit {
 
 }  // namespace
 
-int circuit_compare(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
-                    fhe_ct **lt, fhe_ct **eq)
+// max / min digits of one pair of operands inside an open circuit
+static int circuit_max_min_in(Circuit &C, const fhe_ct *const *x, const fhe_ct *const *y, int d, fhe_ct **mx,
+                              fhe_ct **mn)
 {
-    Circuit C(c, evk);
-    C.compare(x, y, d, lt != nullptr, eq != nullptr, lt, eq);
-    C.finish();
-    return C.err;
-}
-
-int circuit_max_min(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
-                    fhe_ct **mx, fhe_ct **mn)
-{
-    Circuit C(c, evk);
     fhe_ct *L = nullptr;
     C.compare(x, y, d, true, false, &L, nullptr);
     if (C.err) return C.err;
@@ -700,6 +700,39 @@ int circuit_max_min(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, cons
         if (mx) mx[k] = C.release(a);
         if (mn) mn[k] = C.release(b);
     }
+    return 0;
+}
+
+// Several independent comparisons in one circuit (one dependency scheduler),
+// so that with c->multistream their operations interleave on the streams.
+int circuit_multi(fhe_ctx *c, const fhe_evk *evk, const std::vector<MultiItem> &items)
+{
+    Circuit C(c, evk);
+    for (const MultiItem &it : items) {
+        if (C.err) break;
+        if (it.maxmin)
+            circuit_max_min_in(C, it.x, it.y, it.d, it.out0, it.out1);
+        else
+            C.compare(it.x, it.y, it.d, it.out0 != nullptr, it.out1 != nullptr, it.out0, it.out1);
+    }
+    C.finish();
+    return C.err;
+}
+
+int circuit_compare(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                    fhe_ct **lt, fhe_ct **eq)
+{
+    Circuit C(c, evk);
+    C.compare(x, y, d, lt != nullptr, eq != nullptr, lt, eq);
+    C.finish();
+    return C.err;
+}
+
+int circuit_max_min(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                    fhe_ct **mx, fhe_ct **mn)
+{
+    Circuit C(c, evk);
+    circuit_max_min_in(C, x, y, d, mx, mn);
     C.finish();
     return C.err;
 }

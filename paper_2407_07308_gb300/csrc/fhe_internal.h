@@ -85,6 +85,7 @@ struct Pool {
     // list (reused within the capture, in stream order) instead of the pool's;
     // the plan keeps them afterwards because every replay reuses them.
     std::unordered_map<size_t, std::vector<void *>> *cap_free = nullptr;
+    bool in_capture = false;                      // misses use cudaMalloc (never the caller's allocator)
     void *get(size_t bytes, int *err);
     void put(void *p);
     void release_all();
@@ -150,10 +151,13 @@ struct fhe_ctx {
     // forked from and joined back into the capture stream, so the graph runs
     // them concurrently.  Each branch has its own capture-private free list.
     bool capturing = false;
+    bool multistream = false;  // the same scheduling without capture (batch execution)
     std::vector<cudaStream_t> branch_streams;
     std::vector<cudaEvent_t> branch_events;  // reused by every capture
     long long launches = 0;       // kernels launched since creation
 };
+
+struct fhe_batch;
 
 struct fhe_sk {
     fhe_ctx *ctx;
@@ -278,6 +282,17 @@ int circuit_compare(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, cons
 int circuit_max_min(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
                     fhe_ct **mx, fhe_ct **mn);
 int64_t centred_const(const fhe_ctx *c, int64_t k);
+// one comparison (LT -> out0, EQ -> out1; either NULL) or max/min (digits to
+// out0 / out1) of an independent batch
+struct MultiItem {
+    const fhe_ct *const *x;
+    const fhe_ct *const *y;
+    int d;
+    bool maxmin;
+    fhe_ct **out0;
+    fhe_ct **out1;
+};
+int circuit_multi(fhe_ctx *c, const fhe_evk *evk, const std::vector<MultiItem> &items);
 int op_slice(fhe_ctx *c, const fhe_ct *a, int start, int n, fhe_ct **out);
 int op_concat(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **out);
 std::vector<int64_t> tournament_galois(const fhe_ctx *c);

@@ -48,6 +48,14 @@ class fhe_allocator(Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", c_void_p)]
 
 
+class fhe_job(Structure):
+    _fields_ = [("ctx", c_void_p), ("evk", c_void_p), ("kind", c_int), ("d", c_int), ("x", c_void_p),
+                ("y", c_void_p), ("out0", c_void_p), ("out1", c_void_p)]
+
+
+FHE_JOB_COMPARE, FHE_JOB_MAXMIN = 1, 2
+
+
 class fhe_info(Structure):
     _fields_ = [("N", c_int), ("L", c_int), ("K", c_int), ("slots", c_int), ("subring", c_int),
                 ("dnum_max", c_int), ("p", c_uint64)]
@@ -111,6 +119,9 @@ def lib() -> ctypes.CDLL:
             "fhe_ntt_inverse": (ci, [vp, vp, vp, ci]),
             "fhe_selftest_modarith": (ci, [u64, u64, u64, ci, ci]),
             "fhe_ctx_profile": (ci, [vp, ci]),
+            "fhe_batch_submit": (ci, [vp, ci, POINTER(vp)]),
+            "fhe_batch_wait": (ci, [vp, ci]),
+            "fhe_batch_destroy": (None, [vp]),
             "fhe_tournament_galois": (ci, [vp, vp, ci]),
             "fhe_tournament": (ci, [vp, vp, vp, vp, vp, ci, u64, vp, vp]),
             "fhe_refresh_explicit": (ci, [vp, vp, vp, vp, vp, vp, vp, POINTER(vp)]),
@@ -469,6 +480,53 @@ def fhe_tournament(ctx, evk, sk, pk, xs, seed: int, want_max=True, want_min=True
     _check(lib().fhe_tournament(ctx, evk, sk, pk, _handles(xs), d, seed, mx if want_max else None,
                                 mn if want_min else None), ctx)
     return ([c_void_p(v) for v in mx] if want_max else None), ([c_void_p(v) for v in mn] if want_min else None)
+
+
+class Job:
+    """A request for fhe_batch_submit; after the batch completes, .out0 and
+    .out1 hold the result handles (LT / EQ, or the max / min digits)."""
+
+    def __init__(self, ctx, evk, kind, xs, ys, want0=True, want1=True):
+        self.ctx, self.evk, self.kind, self.d = ctx, evk, kind, len(xs)
+        self._x, self._y = _handles(xs), _handles(ys)
+        n = self.d if kind == FHE_JOB_MAXMIN else 1
+        self._o0 = (c_void_p * n)() if want0 else None
+        self._o1 = (c_void_p * n)() if want1 else None
+
+    def struct(self):
+        return fhe_job(self.ctx.value if isinstance(self.ctx, c_void_p) else self.ctx,
+                       self.evk.value if isinstance(self.evk, c_void_p) else self.evk, self.kind, self.d,
+                       ctypes.cast(self._x, c_void_p), ctypes.cast(self._y, c_void_p),
+                       ctypes.cast(self._o0, c_void_p) if self._o0 is not None else None,
+                       ctypes.cast(self._o1, c_void_p) if self._o1 is not None else None)
+
+    @property
+    def out0(self):
+        return None if self._o0 is None else [c_void_p(v) for v in self._o0]
+
+    @property
+    def out1(self):
+        return None if self._o1 is None else [c_void_p(v) for v in self._o1]
+
+
+def fhe_batch_submit(jobs):
+    arr = (fhe_job * len(jobs))(*[j.struct() for j in jobs])
+    out = c_void_p()
+    _check(lib().fhe_batch_submit(ctypes.cast(arr, c_void_p), len(jobs), ctypes.byref(out)),
+           jobs[0].ctx if jobs else None)
+    return out
+
+
+def fhe_batch_wait(batch, timeout_ms: int) -> int:
+    """0 when complete, FHE_ETIMEOUT (-6) if still running after timeout_ms."""
+    rc = lib().fhe_batch_wait(batch, int(timeout_ms))
+    if rc < 0 and rc != -6:
+        _check(rc)
+    return rc
+
+
+def fhe_batch_destroy(batch):
+    lib().fhe_batch_destroy(batch)
 
 
 def fhe_trace_enable(ctx, on: bool):

@@ -1,0 +1,115 @@
+"""GPU: uneven batches (fhe_batch_submit) give, job by job, the bits of the
+same job run alone; mixed ring degrees, plaintext primes, digit counts and
+levels in one submission."""
+import random
+
+import numpy as np
+import pytest
+
+from tests.params import CHAIN50
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_07308_gb300 import build
+
+    build.build()
+
+
+def test_uneven_batch_matches_alone():
+    from paper_2407_07308_gb300 import fhe
+
+    specs = [(12, 17), (13, 257)]  # (logN, p)
+    ctxs = []
+    rnd = random.Random(3)
+    try:
+        for logN, p in specs:
+            ctx = fhe.fhe_ctx_create(logN, p, 12, 4, CHAIN50["U"], CHAIN50["lo"], CHAIN50["hi"])
+            sk, pk = fhe.fhe_keygen(ctx, 10 + logN)
+            evk = fhe.fhe_evk_create(ctx, sk, [], 20 + logN)
+            ctxs.append((ctx, sk, pk, evk, p, fhe.fhe_ctx_info(ctx).slots))
+        jobs, meta, handles = [], [], []
+        for i in range(10):
+            ctx, sk, pk, evk, p, ns = ctxs[i % 2]
+            b = (p + 1) // 2
+            d = 1 + rnd.randrange(2)
+            count = 1 + rnd.randrange(3)
+            level = rnd.choice([12, 11, 10]) if p == 17 else 12
+            xv = np.array([[rnd.randrange(b ** d) for _ in range(ns)] for _ in range(count)])
+            yv = np.array([[x if rnd.random() < 0.3 else rnd.randrange(b ** d) for x in row] for row in xv])
+            xs, ys = [], []
+            for k in range(d):
+                xk = fhe.fhe_encrypt(ctx, pk, (xv // b ** k) % b, 100 * i + k)
+                yk = fhe.fhe_encrypt(ctx, pk, (yv // b ** k) % b, 100 * i + 50 + k)
+                if level < 12:
+                    xk2, yk2 = fhe.fhe_mod_switch(ctx, xk, level), fhe.fhe_mod_switch(ctx, yk, level)
+                    handles += [xk, yk]
+                    xk, yk = xk2, yk2
+                xs.append(xk)
+                ys.append(yk)
+                handles += [xk, yk]
+            kind = fhe.FHE_JOB_MAXMIN if i % 3 == 2 else fhe.FHE_JOB_COMPARE
+            jobs.append(fhe.Job(ctx, evk, kind, xs, ys))
+            meta.append((ctx, sk, evk, kind, xs, ys, xv, yv, b, d))
+        batch = fhe.fhe_batch_submit(jobs)
+        assert fhe.fhe_batch_wait(batch, 120000) == 0
+        fhe.fhe_batch_destroy(batch)
+        for job, (ctx, sk, evk, kind, xs, ys, xv, yv, b, d) in zip(jobs, meta):
+            if kind == fhe.FHE_JOB_COMPARE:
+                lt, eq = fhe.fhe_compare(ctx, evk, xs, ys)
+                assert np.array_equal(fhe.fhe_ct_export_coeff(ctx, job.out0[0]), fhe.fhe_ct_export_coeff(ctx, lt))
+                assert np.array_equal(fhe.fhe_ct_export_coeff(ctx, job.out1[0]), fhe.fhe_ct_export_coeff(ctx, eq))
+                assert (fhe.fhe_decrypt(ctx, sk, job.out0[0]) == (xv < yv)).all()
+                assert (fhe.fhe_decrypt(ctx, sk, job.out1[0]) == (xv == yv)).all()
+                handles += [lt, eq] + job.out0 + job.out1
+            else:
+                mx, mn = fhe.fhe_max_min(ctx, evk, xs, ys)
+                for k in range(d):
+                    assert np.array_equal(fhe.fhe_ct_export_coeff(ctx, job.out0[k]),
+                                          fhe.fhe_ct_export_coeff(ctx, mx[k]))
+                    assert np.array_equal(fhe.fhe_ct_export_coeff(ctx, job.out1[k]),
+                                          fhe.fhe_ct_export_coeff(ctx, mn[k]))
+                got = sum(fhe.fhe_decrypt(ctx, sk, job.out0[k]).astype(np.int64) * b ** k for k in range(d))
+                assert (got == np.maximum(xv, yv)).all()
+                handles += mx + mn + job.out0 + job.out1
+        for h in handles:
+            fhe.fhe_ct_destroy(h)
+    finally:
+        for ctx, sk, pk, evk, _, _ in ctxs:
+            fhe.fhe_evk_destroy(evk)
+            fhe.fhe_sk_destroy(sk)
+            fhe.fhe_pk_destroy(pk)
+            fhe.fhe_ctx_destroy(ctx)
+
+
+def test_batch_wait_timeout_is_bounded():
+    from paper_2407_07308_gb300 import fhe
+
+    ctx = fhe.fhe_ctx_create(14, 131, 10, 3, CHAIN50["U"], CHAIN50["lo"], CHAIN50["hi"])
+    try:
+        sk, pk = fhe.fhe_keygen(ctx, 1)
+        evk = fhe.fhe_evk_create(ctx, sk, [], 2)
+        ns = fhe.fhe_ctx_info(ctx).slots
+        v = np.zeros((16, ns), dtype=np.uint64)
+        xs = [fhe.fhe_encrypt(ctx, pk, v, 3 + k) for k in range(2)]
+        ys = [fhe.fhe_encrypt(ctx, pk, v, 5 + k) for k in range(2)]
+        job = fhe.Job(ctx, evk, fhe.FHE_JOB_COMPARE, xs, ys)
+        batch = fhe.fhe_batch_submit([job])
+        rc = fhe.fhe_batch_wait(batch, 0)
+        assert rc in (0, -6)
+        assert fhe.fhe_batch_wait(batch, 120000) == 0
+        fhe.fhe_batch_destroy(batch)
+        assert (fhe.fhe_decrypt(ctx, sk, job.out1[0]) == 1).all()
+        for h in xs + ys + job.out0 + job.out1:
+            fhe.fhe_ct_destroy(h)
+        fhe.fhe_evk_destroy(evk)
+        fhe.fhe_sk_destroy(sk)
+        fhe.fhe_pk_destroy(pk)
+    finally:
+        fhe.fhe_ctx_destroy(ctx)
