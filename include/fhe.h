@@ -338,6 +338,20 @@ int fhe_ntt_inverse(fhe_ctx *ctx, uint64_t *data, const int32_t *prime_idx, int 
  * be serialised by the caller.  The result equals fhe_mod_switch(.., level-1). */
 int fhe_mod_switch_noalloc(fhe_ctx *ctx, const uint64_t *in, uint64_t *out, int count, int npoly, int level);
 
+/* ---- NTT autotuning ------------------------------------------------------------ */
+
+/* The NTT runs as a column pass and a row pass over N = 2^n1 x 2^n2; each ring
+ * degree has two factorisations (variant 0: n1 = ceil(n/2), variant 1 the
+ * other one within the supported tile sizes).  fhe_ctx_create times both on
+ * a representative batch and keeps the faster; fhe_ctx_autotune(ctx, njobs)
+ * re-times them on njobs limbs.  Both return the chosen variant.
+ * fhe_ctx_ntt_variant(ctx, set, ms): set >= 0 forces a variant (set < 0 only
+ * reads); ms[2] (may be NULL) receives the last timings in milliseconds.
+ * njobs counts limb transforms: polynomials of min(L+K, 10) limbs, rounded
+ * to a multiple of 16 polynomials once there are 16 or more. */
+int fhe_ctx_autotune(fhe_ctx *ctx, int njobs);
+int fhe_ctx_ntt_variant(fhe_ctx *ctx, int set, float *ms);
+
 /* ---- kernel timing ------------------------------------------------------------- */
 
 /* Kernel classes timed by fhe_ctx_profile_read. */

@@ -303,6 +303,9 @@ extern "C" int fhe_ctx_create(const fhe_params *P, const fhe_allocator *alloc, v
     c->pool.stream = c->stream;
     int e = build_tables(c);
     if (!e) e = fhe_cuda_check(c, cudaDeviceSynchronize(), "ctx_create");
+    // choose the NTT factorisation for this ring degree on 32 polynomials
+    // (16 ciphertexts) of up to 10 limbs, the scale of batched use
+    if (!e) e = ntt_autotune(c, 32 * 10, c->ntt_ms);
     if (e) {
         fhe_ctx_destroy(c);
         return e;
@@ -1258,4 +1261,25 @@ extern "C" int fhe_tournament(fhe_ctx *c, const fhe_evk *evk, const fhe_sk *sk, 
     LOCK(c);
     int e = circuit_tournament(c, evk, sk, pk, x, d, out_max != nullptr, out_min != nullptr, seed, out_max, out_min);
     return e ? e : fhe_cuda_check(c, cudaGetLastError(), "tournament");
+}
+
+extern "C" int fhe_ctx_ntt_variant(fhe_ctx *c, int set, float *ms)
+{
+    CHECK_CTX(c);
+    LOCK(c);
+    if (set >= 0) {
+        if (set >= ntt_variants(c->logN)) return FHE_EINVAL;
+        c->ntt_variant = set;
+    }
+    if (ms) ms[0] = c->ntt_ms[0], ms[1] = c->ntt_ms[1];
+    return c->ntt_variant;
+}
+
+extern "C" int fhe_ctx_autotune(fhe_ctx *c, int njobs)
+{
+    CHECK_CTX(c);
+    if (njobs < 1) return FHE_EINVAL;
+    LOCK(c);
+    int e = ntt_autotune(c, njobs, c->ntt_ms);
+    return e ? e : c->ntt_variant;
 }

@@ -605,6 +605,38 @@ void inv_pair(fhe_ctx *c, const IO &io, int njobs)
                                                                                     c->d_ninv);
 }
 
+// Two factorisations N = 2^n1 x 2^n2 per ring degree (the autotuner picks
+// one per context; both compute the same transform).
+template <class IO>
+void fwd_dispatch(fhe_ctx *c, const IO &io, int njobs)
+{
+    const int v = c->ntt_variant;
+    switch (c->logN) {
+    case 10: fwd_pair<5, 5>(c, io, njobs); break;
+    case 11: v ? fwd_pair<5, 6>(c, io, njobs) : fwd_pair<6, 5>(c, io, njobs); break;
+    case 12: v ? fwd_pair<7, 5>(c, io, njobs) : fwd_pair<6, 6>(c, io, njobs); break;
+    case 13: v ? fwd_pair<6, 7>(c, io, njobs) : fwd_pair<7, 6>(c, io, njobs); break;
+    case 14: v ? fwd_pair<8, 6>(c, io, njobs) : fwd_pair<7, 7>(c, io, njobs); break;
+    case 15: v ? fwd_pair<7, 8>(c, io, njobs) : fwd_pair<8, 7>(c, io, njobs); break;
+    default: break;
+    }
+}
+
+template <class IO>
+void inv_dispatch(fhe_ctx *c, const IO &io, int njobs)
+{
+    const int v = c->ntt_variant;
+    switch (c->logN) {
+    case 10: inv_pair<5, 5>(c, io, njobs); break;
+    case 11: v ? inv_pair<5, 6>(c, io, njobs) : inv_pair<6, 5>(c, io, njobs); break;
+    case 12: v ? inv_pair<7, 5>(c, io, njobs) : inv_pair<6, 6>(c, io, njobs); break;
+    case 13: v ? inv_pair<6, 7>(c, io, njobs) : inv_pair<7, 6>(c, io, njobs); break;
+    case 14: v ? inv_pair<8, 6>(c, io, njobs) : inv_pair<7, 7>(c, io, njobs); break;
+    case 15: v ? inv_pair<7, 8>(c, io, njobs) : inv_pair<8, 7>(c, io, njobs); break;
+    default: break;
+    }
+}
+
 // words_per_job: u64 words of global traffic per limb job (algorithmic: the
 // transform reads and writes each limb once; fused variants add their operands)
 template <class IO>
@@ -612,15 +644,7 @@ void run_fwd(fhe_ctx *c, const IO &io, int njobs, int cls, double words_per_job 
 {
     if (njobs <= 0) return;
     prof_begin(c, cls, 8.0 * words_per_job * c->N * njobs, (double)njobs * (c->N / 2) * c->logN);
-    switch (c->logN) {
-    case 10: fwd_pair<5, 5>(c, io, njobs); break;
-    case 11: fwd_pair<6, 5>(c, io, njobs); break;
-    case 12: fwd_pair<6, 6>(c, io, njobs); break;
-    case 13: fwd_pair<7, 6>(c, io, njobs); break;
-    case 14: fwd_pair<7, 7>(c, io, njobs); break;
-    case 15: fwd_pair<8, 7>(c, io, njobs); break;
-    default: break;
-    }
+    fwd_dispatch(c, io, njobs);
     prof_end(c);
     c->launches += 2;
 }
@@ -630,15 +654,7 @@ void run_inv(fhe_ctx *c, const IO &io, int njobs, int cls, double words_per_job 
 {
     if (njobs <= 0) return;
     prof_begin(c, cls, 8.0 * words_per_job * c->N * njobs, (double)njobs * (c->N / 2) * c->logN);
-    switch (c->logN) {
-    case 10: inv_pair<5, 5>(c, io, njobs); break;
-    case 11: inv_pair<6, 5>(c, io, njobs); break;
-    case 12: inv_pair<6, 6>(c, io, njobs); break;
-    case 13: inv_pair<7, 6>(c, io, njobs); break;
-    case 14: inv_pair<7, 7>(c, io, njobs); break;
-    case 15: inv_pair<8, 7>(c, io, njobs); break;
-    default: break;
-    }
+    inv_dispatch(c, io, njobs);
     prof_end(c);
     c->launches += 2;
 }
@@ -720,4 +736,65 @@ void launch_ntt_modswitch(fhe_ctx *c, const u64 *last, const u64 *in, u64 *out, 
     io.l = level;
     io.npoly = npoly;
     run_fwd(c, io, npoly * (level - 1) * count, FHE_K_NTT_MODSWITCH, 3.0);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: times both factorisations on a representative batch
+// ---------------------------------------------------------------------------
+
+int ntt_variants(int logN) { return logN >= 11 && logN <= 15 ? 2 : 1; }
+
+// Times forward + inverse of `outer` x nl limbs (nl = min(primes, 10)),
+// `outer` rounded to a multiple of 16 when >= 16 so that the row kernels take
+// their grouped form as in batched use; keeps the faster variant.
+int ntt_autotune(fhe_ctx *c, int njobs, float *ms_out)
+{
+    const int nv = ntt_variants(c->logN);
+    LimbMap m;
+    memset(&m, 0, sizeof(m));
+    m.nl = std::min(c->np, 10);
+    int outer = std::max(1, njobs / m.nl);
+    if (outer >= 16) outer -= outer % 16;
+    const int jobs = outer * m.nl;
+    m.in_outer = m.out_outer = (long long)m.nl * c->N;
+    for (int i = 0; i < m.nl; i++) m.in_limb[i] = m.out_limb[i] = i, m.prime[i] = i;
+    u64 *buf = nullptr;
+    const size_t words = (size_t)jobs * c->N;
+    if (cudaMalloc(&buf, words * sizeof(u64)) != cudaSuccess) return FHE_ENOMEM;
+    cudaMemsetAsync(buf, 0, words * sizeof(u64), c->stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool prof = c->prof_on;
+    const long long launches = c->launches;
+    c->prof_on = false;
+    float best = 1e30f;
+    int best_v = 0;
+    for (int v = 0; v < nv; v++) {
+        c->ntt_variant = v;
+        IOPlain io{buf, buf, m};
+        for (int w = 0; w < 2; w++) {
+            fwd_dispatch(c, io, jobs);
+            inv_dispatch(c, io, jobs);
+        }
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 5; r++) {
+            fwd_dispatch(c, io, jobs);
+            inv_dispatch(c, io, jobs);
+        }
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 5;
+        if (ms_out) ms_out[v] = ms;
+        if (ms < best) best = ms, best_v = v;
+    }
+    c->ntt_variant = best_v;
+    c->prof_on = prof;
+    c->launches = launches;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    return fhe_cuda_check(c, cudaGetLastError(), "autotune");
 }

@@ -119,6 +119,8 @@ def lib() -> ctypes.CDLL:
             "fhe_ntt_inverse": (ci, [vp, vp, vp, ci]),
             "fhe_selftest_modarith": (ci, [u64, u64, u64, ci, ci]),
             "fhe_ctx_profile": (ci, [vp, ci]),
+            "fhe_ctx_autotune": (ci, [vp, ci]),
+            "fhe_ctx_ntt_variant": (ci, [vp, ci, vp]),
             "fhe_batch_submit": (ci, [vp, ci, POINTER(vp)]),
             "fhe_batch_wait": (ci, [vp, ci]),
             "fhe_batch_destroy": (None, [vp]),
@@ -527,6 +529,17 @@ def fhe_batch_wait(batch, timeout_ms: int) -> int:
 
 def fhe_batch_destroy(batch):
     lib().fhe_batch_destroy(batch)
+
+
+def fhe_ctx_autotune(ctx, njobs: int) -> int:
+    return _check(lib().fhe_ctx_autotune(ctx, njobs), ctx)
+
+
+def fhe_ctx_ntt_variant(ctx, set_variant: int = -1):
+    """(chosen variant, [ms of variant 0, ms of variant 1])."""
+    ms = np.zeros(2, dtype=np.float32)
+    v = _check(lib().fhe_ctx_ntt_variant(ctx, set_variant, _ptr(ms)), ctx)
+    return v, [float(x) for x in ms]
 
 
 def fhe_trace_enable(ctx, on: bool):

@@ -50,8 +50,9 @@ def _same(oracle_ct, gpu_export, idx=0):
 # NTT
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("logN", [10, 11, 12, 13, 14, 15])
-def test_ntt_forward_inverse_match_oracle(logN):
+@pytest.mark.parametrize("logN,variant", [(10, 0), (11, 0), (11, 1), (12, 0), (12, 1), (13, 0), (13, 1),
+                                           (14, 0), (14, 1), (15, 0), (15, 1)])
+def test_ntt_forward_inverse_match_oracle(logN, variant):
     from oracle.bgv import Oracle
 
     fhe = _fhe()
@@ -60,6 +61,7 @@ def test_ntt_forward_inverse_match_oracle(logN):
     ctx = fhe.fhe_ctx_create(logN, 131, L, K, **{"prime_mod": CHAIN50["U"], "prime_lo": CHAIN50["lo"],
                                                    "prime_hi": CHAIN50["hi"]})
     try:
+        fhe.fhe_ctx_ntt_variant(ctx, variant)
         N = 1 << logN
         g = np.random.default_rng(logN)
         # every prime, plus a ragged repeat pattern of prime indices
@@ -287,6 +289,39 @@ def test_batch_equals_singles():
         for i in range(4):
             lt_i = g.own(fhe.fhe_compare_lt(g.ctx, g.evk, [xe[i]], [ye[i]]))
             assert np.array_equal(g.export(lt_i)[0], ex_b[i])
+    finally:
+        g.close()
+
+
+def test_ntt_variants_and_autotuner():
+    """Both NTT factorisations give the same bits through the whole compare
+    path (16 ciphertexts, so the grouped row kernels run), and the autotuner
+    picks one of them from positive timings."""
+    fhe = _fhe()
+    from tests.gpu_setup import GpuSetup
+
+    g = GpuSetup(seed=13, logN=13, p=17, L=6, K=2, **CHAIN50)
+    try:
+        v, ms = fhe.fhe_ctx_ntt_variant(g.ctx)
+        assert v in (0, 1) and ms[0] > 0 and ms[1] > 0 and ms[v] == min(ms)
+        assert fhe.fhe_ctx_autotune(g.ctx, 64) in (0, 1)
+        rnd = random.Random(4)
+        xs = [[rnd.randrange(9) for _ in range(g.ns)] for _ in range(16)]
+        ys = [[x if rnd.random() < 0.3 else rnd.randrange(9) for x in row] for row in xs]
+        xb, yb = g.encrypt_slots(xs, seed=1), g.encrypt_slots(ys, seed=2)
+        out = []
+        for variant in (0, 1):
+            fhe.fhe_ctx_ntt_variant(g.ctx, variant)
+            lt, eq = fhe.fhe_compare(g.ctx, g.evk, [xb], [yb])
+            g.own(lt)
+            g.own(eq)
+            out.append((g.export(lt), g.export(eq)))
+            lt_dec = g.decrypt(lt)
+            for c in range(16):
+                assert lt_dec[c].tolist() == [int(a < b) for a, b in zip(xs[c], ys[c])]
+        assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+        with pytest.raises(fhe.FheError):
+            fhe.fhe_ctx_ntt_variant(g.ctx, 2)
     finally:
         g.close()
 
