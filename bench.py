@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import multiprocessing as mp
 import os
 import statistics
@@ -467,6 +468,268 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# uneven requests (256 requests of mixed ring degree, plaintext prime, digit
+# count and start level) and the serving loop (Poisson arrivals)
+# ---------------------------------------------------------------------------
+
+UNEVEN = dict(requests=256, logNs=(13, 14, 15), ps=(17, 131, 257), ds=(1, 2, 3, 4), L=20, K=4, seed=3)
+SERVE = dict(requests=48, logNs=(13, 14, 15), ps=(17, 131, 257), d=2, L=20, K=4, seed=5, budget=150e9,
+             nmin=16, nmax=4096, chunk=16)
+
+
+def circuit_depth(p, d, maxmin=False):
+    """Levels the comparison of d digits consumes: the LT/EQ polynomial, the
+    digit merge tree, and the select step of max/min."""
+    return (p - 2).bit_length() + (d - 1).bit_length() + (1 if maxmin else 0)
+
+
+def lowest_level(logN, p, d, maxmin=False):
+    """Lowest start level that decrypts correctly: the circuit depth (at
+    least 4); for p = 257 at N >= 2^14 the polynomial's last product, whose
+    operands carry its centred coefficients (up to 128 in size), must not
+    fall on the last prime, so at least ceil(log2(p-1)) + 2 = 10."""
+    lv = max(4, circuit_depth(p, d, maxmin))
+    if p == 257 and logN >= 14:
+        lv = max(lv, (p - 2).bit_length() + 2)
+    return lv
+
+
+class Contexts:
+    """One context (own stream, keys resident) per (ring degree, prime) on
+    the universal 50-bit chain."""
+
+    def __init__(self, fhe, torch, local, specs, L, K, seed):
+        self.fhe, self.items = fhe, {}
+        for logN, p in specs:
+            stream = torch.cuda.Stream()
+            ctx = fhe.fhe_ctx_create(logN, p, L, K, U50, 2 ** 49, 2 ** 50, allocator=fhe.torch_allocator(local),
+                                     stream=stream.cuda_stream)
+            sk, pk = fhe.fhe_keygen(ctx, seed * 1000 + logN * 300 + p)
+            evk = fhe.fhe_evk_create(ctx, sk, [], seed * 1000 + logN * 300 + p + 1)
+            self.items[(logN, p)] = dict(ctx=ctx, sk=sk, pk=pk, evk=evk, stream=stream,
+                                         ns=fhe.fhe_ctx_info(ctx).slots)
+
+    def launches(self):
+        return sum(self.fhe.fhe_ctx_launches(c["ctx"]) for c in self.items.values())
+
+    def sync(self):
+        for c in self.items.values():
+            self.fhe.fhe_ctx_sync(c["ctx"])
+
+    def close(self):
+        for c in self.items.values():
+            self.fhe.fhe_evk_destroy(c["evk"])
+            self.fhe.fhe_sk_destroy(c["sk"])
+            self.fhe.fhe_pk_destroy(c["pk"])
+            self.fhe.fhe_ctx_destroy(c["ctx"])
+
+
+def _encrypt_request(fhe, c, xv, yv, b, d, level, seed):
+    xs, ys = [], []
+    for k in range(d):
+        for vals, out, sd in ((xv, xs, seed + k), (yv, ys, seed + 50 + k)):
+            h = fhe.fhe_encrypt(c["ctx"], c["pk"], (vals // b ** k) % b, sd)
+            if level < fhe.fhe_ct_shape(h)[2]:
+                h2 = fhe.fhe_mod_switch(c["ctx"], h, level)
+                fhe.fhe_ct_destroy(h)
+                h = h2
+            out.append(h)
+    return xs, ys
+
+
+def run_uneven(args):
+    """256 uneven comparison requests (LT and EQ, one ciphertext tuple pair
+    each): batched = all of them in one fhe_batch_submit, plain = one at a
+    time through fhe_compare."""
+    import numpy as np
+    import torch
+
+    from paper_2407_07308_gb300 import fhe, synth
+
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    U = UNEVEN
+    g = synth.rng(U["seed"])
+    cs = Contexts(fhe, torch, local, [(n, p) for n in U["logNs"] for p in U["ps"]], U["L"], U["K"], U["seed"])
+    reqs = []
+    for i in range(U["requests"]):
+        logN, p, d = int(g.choice(U["logNs"])), int(g.choice(U["ps"])), int(g.choice(U["ds"]))
+        level = int(g.integers(lowest_level(logN, p, d), U["L"] + 1))
+        c = cs.items[(logN, p)]
+        b, ns = (p + 1) // 2, c["ns"]
+        xv = synth.values(g, ns, b ** d).reshape(1, ns)
+        yv = np.where(g.random((1, ns)) < 0.3, xv, synth.values(g, ns, b ** d).reshape(1, ns))
+        xs, ys = _encrypt_request(fhe, c, xv, yv, b, d, level, 10000 + 100 * i)
+        reqs.append(dict(c=c, p=p, d=d, level=level, xs=xs, ys=ys, xv=xv, yv=yv, logN=logN))
+    slot_cmps = sum(r["c"]["ns"] for r in reqs)
+    cs.sync()
+
+    def batched_step(check=False):
+        jobs = [fhe.Job(r["c"]["ctx"], r["c"]["evk"], fhe.FHE_JOB_COMPARE, r["xs"], r["ys"]) for r in reqs]
+        t = time.perf_counter()
+        bt = fhe.fhe_batch_submit(jobs)
+        t_enq = time.perf_counter() - t
+        assert fhe.fhe_batch_wait(bt, 600000) == 0
+        dt = time.perf_counter() - t
+        fhe.fhe_batch_destroy(bt)
+        if check:
+            for r, j in zip(reqs, jobs):
+                ctx, sk = r["c"]["ctx"], r["c"]["sk"]
+                assert (fhe.fhe_decrypt(ctx, sk, j.out0[0]) == (r["xv"] < r["yv"])).all(), "uneven LT mismatch"
+                assert (fhe.fhe_decrypt(ctx, sk, j.out1[0]) == (r["xv"] == r["yv"])).all(), "uneven EQ mismatch"
+        for j in jobs:
+            for h in j.out0 + j.out1:
+                fhe.fhe_ct_destroy(h)
+        return dt, t_enq
+
+    batched_step(check=True)
+    for _ in range(args.warmup - 1):
+        batched_step()
+    l0 = cs.launches()
+    with Clocks(local) as clk:
+        times = [batched_step() for _ in range(args.steps)]
+    launches = cs.launches() - l0
+    walls = [t for t, _ in times]
+    value = slot_cmps * args.steps / sum(walls)
+
+    plain = None
+    if not args.no_plain:
+        lat = []
+        for r in reqs:
+            c = r["c"]
+            t = time.perf_counter()
+            lt, eq = fhe.fhe_compare(c["ctx"], c["evk"], r["xs"], r["ys"])
+            fhe.fhe_ctx_sync(c["ctx"])
+            lat.append(1e3 * (time.perf_counter() - t))
+            fhe.fhe_ct_destroy(lt)
+            fhe.fhe_ct_destroy(eq)
+        lat.sort()
+        plain = {"value": round(slot_cmps / (sum(lat) / 1e3), 2), "unit": UNIT,
+                 "ms_per_request_p50": round(lat[len(lat) // 2], 3),
+                 "ms_per_request_p99": round(lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))], 3)}
+    shapes = {}
+    for r in reqs:
+        k = f"N=2^{r['logN']},p={r['p']}"
+        shapes[k] = shapes.get(k, 0) + 1
+    line = {
+        "metric": "encrypted slot-comparisons/sec, 256 uneven requests; batched vs plain", "value": round(value, 2),
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * sum(walls) / args.steps, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded BGV keys, noise and values)",
+        "config": {"workload": "256 LT+EQ requests, N in {2^13,2^14,2^15}, p in {17,131,257}, d in 1..4, start "
+                               "level uniform in [lowest decryptable level, 20], 20x50-bit + 4 special primes, one "
+                               "ciphertext tuple pair per request", "requests": len(reqs), "by_shape": shapes,
+                   "slot_comparisons_per_step": slot_cmps,
+                   "batched_form": "all requests in one fhe_batch_submit (grouped by context, digits, level; "
+                                   "8 streams per context), host wall time of submit + wait",
+                   "plain_form": "one request at a time through fhe_compare, synchronised",
+                   "l2": "inputs and intermediates of every step exceed L2"},
+        "plain": plain, "enqueue_ms_p50": round(1e3 * sorted(t for _, t in times)[len(times) // 2], 1),
+        "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": None, "roofline": None,
+    }
+    for r in reqs:
+        for h in r["xs"] + r["ys"]:
+            fhe.fhe_ct_destroy(h)
+    cs.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """The serving loop: requests of n values (log-uniform in [16, 4096];
+    ceil(n / n_s) ciphertexts, split by the client into jobs of at most 64
+    ciphertexts) arrive as a Poisson process; 3 of 4 are LT+EQ compares, 1 of
+    4 max/min selections; the server admits them under a 150 GB footprint
+    budget and batches continuously."""
+    import numpy as np
+    import torch
+
+    from paper_2407_07308_gb300 import fhe, synth
+
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    S = SERVE
+    g = synth.rng(S["seed"])
+    cs = Contexts(fhe, torch, local, [(n, p) for n in S["logNs"] for p in S["ps"]], S["L"], S["K"], S["seed"])
+    d = S["d"]
+    reqs = []
+    for i in range(S["requests"]):
+        logN, p = int(g.choice(S["logNs"])), int(g.choice(S["ps"]))
+        c = cs.items[(logN, p)]
+        ns, b = c["ns"], (p + 1) // 2
+        n = int(round(math.exp(g.uniform(math.log(S["nmin"]), math.log(S["nmax"])))))
+        count = -(-n // ns)
+        kind = fhe.FHE_JOB_MAXMIN if g.random() < 0.25 else fhe.FHE_JOB_COMPARE
+        level = max(lowest_level(logN, p, d, kind == fhe.FHE_JOB_MAXMIN), circuit_depth(p, d) + 1)
+        parts = []
+        for lo in range(0, count, S["chunk"]):
+            cnt = min(S["chunk"], count - lo)
+            xv = synth.values(g, cnt * ns, b ** d).reshape(cnt, ns)
+            yv = np.where(g.random((cnt, ns)) < 0.3, xv, synth.values(g, cnt * ns, b ** d).reshape(cnt, ns))
+            xs, ys = _encrypt_request(fhe, c, xv, yv, b, d, level, 20000 + 1000 * i + lo)
+            parts.append(dict(xs=xs, ys=ys, xv=xv, yv=yv))
+        reqs.append(dict(c=c, p=p, logN=logN, n=n, slots=count * ns, kind=kind, parts=parts, b=b))
+    cs.sync()
+    rate = args.serve_rate
+    gaps = g.exponential(1.0 / rate, size=len(reqs))
+    srv = fhe.fhe_server_start(hbm_budget=int(S["budget"]))
+    jobs = []
+    l0 = cs.launches()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        due = 0.0
+        for r, gap in zip(reqs, gaps):
+            due += gap
+            wait = due - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            r["t_arrive"] = time.perf_counter()
+            r["jobs"] = [fhe.Job(r["c"]["ctx"], r["c"]["evk"], r["kind"], pt["xs"], pt["ys"]) for pt in r["parts"]]
+            r["tickets"] = [fhe.fhe_server_submit(srv, j) for j in r["jobs"]]
+        for r in reqs:
+            for t in r["tickets"]:
+                done, info = fhe.fhe_server_poll(srv, t, 600000)
+                assert done and info.error == 0, f"request failed: {info.error}"
+            r["t_done"] = time.perf_counter()
+        wall = time.perf_counter() - t0
+    st = fhe.fhe_server_stats(srv)
+    fhe.fhe_server_stop(srv)
+    launches = cs.launches() - l0
+    # correctness of every request (after the timed region)
+    for r in reqs:
+        ctx, sk = r["c"]["ctx"], r["c"]["sk"]
+        for j, pt in zip(r["jobs"], r["parts"]):
+            if r["kind"] == fhe.FHE_JOB_COMPARE:
+                assert (fhe.fhe_decrypt(ctx, sk, j.out0[0]) == (pt["xv"] < pt["yv"])).all(), "serve LT mismatch"
+            else:
+                got = sum(fhe.fhe_decrypt(ctx, sk, j.out0[k]).astype(np.int64) * r["b"] ** k for k in range(d))
+                assert (got == np.maximum(pt["xv"], pt["yv"])).all(), "serve max mismatch"
+            for h in (j.out0 or []) + (j.out1 or []):
+                fhe.fhe_ct_destroy(h)
+            for h in pt["xs"] + pt["ys"]:
+                fhe.fhe_ct_destroy(h)
+    lat = sorted(1e3 * (r["t_done"] - r["t_arrive"]) for r in reqs)
+    slots = sum(r["slots"] for r in reqs)
+    line = {
+        "metric": "served encrypted slot-comparisons/sec under Poisson arrivals; p50/p99 request ms",
+        "value": round(slots / wall, 2), "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": round(1e3 * wall, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic (seeded BGV keys, noise and values)",
+        "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {rate} req/s, n log-uniform in "
+                               f"[{S['nmin']}, {S['nmax']}] values, N in {{2^13,2^14,2^15}}, p in {{17,131,257}}, "
+                               f"d=2, 3/4 LT+EQ and 1/4 max/min, 20x50-bit + 4 special primes, start level = "
+                               f"lowest decryptable level, client chunks of <= {S['chunk']} ciphertexts",
+                   "hbm_budget_gb": S["budget"] / 1e9, "arrival_rate_per_s": rate},
+        "latency_ms_p50": round(lat[len(lat) // 2], 1),
+        "latency_ms_p99": round(lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))], 1),
+        "server": {"batches": st.batches, "admitted_peak_gb": round(st.admitted_peak_bytes / 1e9, 2),
+                   "completed_jobs": st.completed},
+        "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": None, "roofline": None, "e2e": None,
+    }
+    cs.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -478,6 +741,9 @@ def main():
     ap.add_argument("--pairs", type=int, default=16, help="ciphertext pairs per batch (16 = the workload)")
     ap.add_argument("--no-plain", action="store_true", help="skip the one-request-at-a-time form")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    ap.add_argument("--workload", default="compare", choices=["compare", "uneven", "serve"],
+                    help="compare: the 16-pair batch (default); uneven: 256 mixed requests; serve: serving loop")
+    ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate (requests/s) for serve")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -485,6 +751,10 @@ def main():
     CONFIG["pairs_per_step"] = args.pairs
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "uneven":
+        run_uneven(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

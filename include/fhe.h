@@ -104,6 +104,17 @@ int fhe_ctx_set_stream(fhe_ctx *ctx, void *stream);
 int fhe_ctx_sync(fhe_ctx *ctx);
 /* Device bytes held by the pool (reserved) and handed out (in_use). */
 int fhe_ctx_memory(const fhe_ctx *ctx, uint64_t *reserved, uint64_t *in_use);
+/* Largest in_use since the last reset; reset != 0 restarts it from the
+ * current in_use. */
+int fhe_ctx_memory_peak(fhe_ctx *ctx, uint64_t *peak, int reset);
+/* Waits for the context's stream and returns the pool's cached free blocks
+ * to the allocator (blocks held by handles and plans stay). */
+int fhe_ctx_trim(fhe_ctx *ctx);
+/* Host-side fault injection for tests of the error paths: the n-th device
+ * block the pool has to obtain from now on (0 = the next one) fails as if
+ * the device were out of memory (FHE_ENOMEM); n < 0 switches it off.  No
+ * device fault is involved; the context stays usable. */
+int fhe_ctx_inject_alloc_failure(fhe_ctx *ctx, int64_t n);
 /* Cap on reserved bytes (0 = none); allocations past it fail with FHE_EBUDGET. */
 int fhe_ctx_set_budget(fhe_ctx *ctx, uint64_t bytes);
 /* Number of kernels this context has launched so far. */
@@ -300,6 +311,61 @@ int fhe_batch_submit(const fhe_job *jobs, int n, fhe_batch **out);
 int fhe_batch_wait(fhe_batch *batch, int timeout_ms);
 /* Waits for the batch and releases its tracking state (not the outputs). */
 void fhe_batch_destroy(fhe_batch *batch);
+
+/* ---- serving loop ---------------------------------------------------------------- */
+
+/* A worker thread that serves requests (fhe_job) submitted from any thread.
+ * It admits queued requests in arrival order while the sum of their
+ * footprint estimates (fhe_job_footprint) stays within hbm_budget bytes (a
+ * request that arrives at an empty server is always admitted; one whose
+ * estimate alone exceeds the budget is refused with FHE_EBUDGET at
+ * submission), and submits all requests admitted at one time as one
+ * fhe_batch_submit; it enqueues the next batch while earlier ones still run
+ * (continuous batching).  Contexts and keys stay resident and belong to the
+ * caller, as do the input handles (valid until the request is done) and the
+ * outputs: the handles are written to the job's out0/out1 arrays, which must
+ * stay valid until fhe_server_poll reports the request done. */
+enum { FHE_REQ_QUEUED = 0, FHE_REQ_RUNNING = 1, FHE_REQ_DONE = 2 };
+
+typedef struct {
+    uint64_t hbm_budget; /* bytes; 0 = no limit */
+    int max_batch;       /* most requests per submission; 0 = no limit */
+    int reserved;
+} fhe_server_config;
+
+typedef struct {
+    int state;           /* FHE_REQ_* */
+    int error;           /* 0, or the FHE_E* code the request ended with */
+    double t_submit_ms;  /* server clock (ms since fhe_server_start) */
+    double t_start_ms;   /* admitted and submitted */
+    double t_done_ms;    /* completion seen by the worker (polled every 50 us) */
+    uint64_t est_bytes;  /* fhe_job_footprint */
+} fhe_request_info;
+
+typedef struct {
+    long long queued, running, completed, failed, batches;
+    uint64_t admitted_bytes, admitted_peak_bytes;
+} fhe_server_status;
+
+typedef struct fhe_server fhe_server;
+
+/* Estimated device bytes a request allocates while it runs: the circuit's
+ * working set per digit, the key-switching scratch of up to 8 concurrent
+ * digits and the outputs (0 for an invalid job). */
+uint64_t fhe_job_footprint(const fhe_job *job);
+/* cfg may be NULL (no budget, no batch limit). */
+int fhe_server_start(const fhe_server_config *cfg, fhe_server **out);
+/* Validates and queues a copy of *job (and of its x/y arrays); *ticket
+ * identifies it.  FHE_EINVAL after fhe_server_stop has begun. */
+int fhe_server_submit(fhe_server *server, const fhe_job *job, uint64_t *ticket);
+/* Waits up to timeout_ms (0: does not wait) for the request; returns 1 when
+ * it is done (the ticket is then retired), 0 when not yet, FHE_EINVAL for an
+ * unknown ticket.  info may be NULL. */
+int fhe_server_poll(fhe_server *server, uint64_t ticket, int timeout_ms, fhe_request_info *info);
+int fhe_server_stats(fhe_server *server, fhe_server_status *status);
+/* Serves every request already submitted, joins the worker and frees the
+ * server; tickets not yet polled are retired with it. */
+int fhe_server_stop(fhe_server *server);
 
 /* ---- operation trace --------------------------------------------------------- */
 

@@ -38,25 +38,11 @@ void *Pool::get(size_t bytes, int *err)
         void *p = fl.back();
         fl.pop_back();
         in_use += bytes;
+        if (in_use > peak) peak = in_use;
         return p;
     }
     if (budget && reserved + bytes > budget) {
-        // give cached blocks of other sizes back before refusing
-        for (auto &kv : free_lists) {
-            for (void *q : kv.second) {
-                if (raw.count(q)) {
-                    cudaFree(q);
-                    raw.erase(q);
-                } else if (alloc.free) {
-                    alloc.free(q, kv.first, stream, alloc.user);
-                } else {
-                    cudaFreeAsync(q, stream);
-                }
-                live.erase(q);
-                reserved -= kv.first;
-            }
-            kv.second.clear();
-        }
+        trim();  // give cached blocks of other sizes back before refusing
         if (reserved + bytes > budget) {
             *err = FHE_EBUDGET;
             return nullptr;
@@ -78,6 +64,19 @@ void *Pool::get(size_t bytes, int *err)
     } else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
         p = nullptr;
     }
+    if (!p && !in_capture) {
+        // out of device memory: wait for all queued work, hand every cached
+        // free block (this pool's, and those of contexts not busy on another
+        // thread) back to the allocator, and try once more
+        cudaDeviceSynchronize();
+        trim();
+        trim_other_pools(this);
+        if (alloc.alloc) {
+            p = alloc.alloc(bytes, (void *)stream, alloc.user);
+        } else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+            p = nullptr;
+        }
+    }
     if (!p) {
         *err = FHE_ENOMEM;
         return nullptr;
@@ -85,6 +84,7 @@ void *Pool::get(size_t bytes, int *err)
     live[p] = bytes;
     reserved += bytes;
     in_use += bytes;
+    if (in_use > peak) peak = in_use;
     return p;
 }
 
@@ -98,6 +98,49 @@ void Pool::put(void *p)
     }
     free_lists[it->second].push_back(p);
     in_use -= it->second;
+}
+
+// Frees the cached (not handed out) blocks.
+void Pool::trim()
+{
+    for (auto &kv : free_lists) {
+        for (void *q : kv.second) {
+            if (raw.count(q)) {
+                cudaFree(q);
+                raw.erase(q);
+            } else if (alloc.free) {
+                alloc.free(q, kv.first, (void *)stream, alloc.user);
+            } else {
+                cudaFreeAsync(q, stream);
+            }
+            live.erase(q);
+            reserved -= kv.first;
+        }
+        kv.second.clear();
+    }
+}
+
+// every live context, so that a pool out of memory can trim the others
+static std::mutex g_ctx_mu;
+static std::vector<fhe_ctx *> g_ctxs;
+
+static void register_ctx(fhe_ctx *c, bool add)
+{
+    std::lock_guard<std::mutex> g(g_ctx_mu);
+    if (add)
+        g_ctxs.push_back(c);
+    else
+        g_ctxs.erase(std::remove(g_ctxs.begin(), g_ctxs.end(), c), g_ctxs.end());
+}
+
+void trim_other_pools(Pool *self)
+{
+    std::lock_guard<std::mutex> g(g_ctx_mu);
+    for (fhe_ctx *o : g_ctxs) {
+        if (&o->pool == self || !o->mu.try_lock()) continue;  // busy contexts keep theirs
+        o->pool.trim();
+        o->mu.unlock();
+    }
 }
 
 void Pool::release_all()
@@ -310,6 +353,7 @@ extern "C" int fhe_ctx_create(const fhe_params *P, const fhe_allocator *alloc, v
         fhe_ctx_destroy(c);
         return e;
     }
+    register_ctx(c, true);
     *out = c;
     return 0;
 }
@@ -317,6 +361,7 @@ extern "C" int fhe_ctx_create(const fhe_params *P, const fhe_allocator *alloc, v
 extern "C" void fhe_ctx_destroy(fhe_ctx *c)
 {
     if (!c) return;
+    register_ctx(c, false);
     cudaStreamSynchronize(c->stream);
     c->pool.release_all();
     cudaFree(c->d_mq);
@@ -375,6 +420,32 @@ extern "C" int fhe_ctx_memory(const fhe_ctx *c, uint64_t *reserved, uint64_t *in
     if (!c) return FHE_EINVAL;
     if (reserved) *reserved = c->pool.reserved;
     if (in_use) *in_use = c->pool.in_use;
+    return 0;
+}
+
+extern "C" int fhe_ctx_memory_peak(fhe_ctx *c, uint64_t *peak, int reset)
+{
+    CHECK_CTX(c);
+    LOCK(c);
+    if (peak) *peak = c->pool.peak;
+    if (reset) c->pool.peak = c->pool.in_use;
+    return 0;
+}
+
+extern "C" int fhe_ctx_trim(fhe_ctx *c)
+{
+    CHECK_CTX(c);
+    LOCK(c);
+    int e = sync_check(c, "trim");
+    if (!e) c->pool.trim();
+    return e;
+}
+
+extern "C" int fhe_ctx_inject_alloc_failure(fhe_ctx *c, int64_t n)
+{
+    CHECK_CTX(c);
+    LOCK(c);
+    c->pool.fail_after = n < 0 ? -1 : n;
     return 0;
 }
 

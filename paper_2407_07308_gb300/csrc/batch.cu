@@ -32,7 +32,9 @@ struct Group {
     std::vector<fhe_ct *> out0, out1;        // group outputs (owned, sliced to jobs)
 };
 
-int check_job(const fhe_job &j)
+}  // namespace
+
+int batch_check_job(const fhe_job &j)
 {
     if (!j.ctx || !j.evk || j.evk->ctx != j.ctx || !j.x || !j.y || j.d < 1) return FHE_EINVAL;
     if (j.kind != FHE_JOB_COMPARE && j.kind != FHE_JOB_MAXMIN) return FHE_EINVAL;
@@ -48,6 +50,8 @@ int check_job(const fhe_job &j)
     }
     return 0;
 }
+
+namespace {
 
 // concatenation of the jobs' digit-k operands (one allocation, one copy per part)
 int gather(fhe_ctx *c, const fhe_job *jobs, const std::vector<int> &ids, int k, bool ys, fhe_ct **out, bool *owned)
@@ -163,7 +167,7 @@ extern "C" int fhe_batch_submit(const fhe_job *jobs, int n, fhe_batch **out)
 {
     if (!jobs || n < 1 || !out) return FHE_EINVAL;
     for (int i = 0; i < n; i++) {
-        int e = check_job(jobs[i]);
+        int e = batch_check_job(jobs[i]);
         if (e) return e;
     }
     std::vector<fhe_ctx *> order;

@@ -80,6 +80,7 @@ struct Pool {
     std::unordered_map<void *, size_t> live;  // every block ever obtained -> size
     std::unordered_map<void *, bool> raw;     // blocks from cudaMalloc (misses during a capture)
     size_t reserved = 0, in_use = 0, budget = 0;  // budget 0 = unlimited
+    size_t peak = 0;                              // largest in_use since the last reset
     long long fail_after = -1;                    // fault injection: fail the n-th new block
     // While a graph is captured, freed blocks go to this capture-private free
     // list (reused within the capture, in stream order) instead of the pool's;
@@ -88,8 +89,11 @@ struct Pool {
     bool in_capture = false;                      // misses use cudaMalloc (never the caller's allocator)
     void *get(size_t bytes, int *err);
     void put(void *p);
+    void trim();
     void release_all();
 };
+
+void trim_other_pools(Pool *self);
 
 // ---------------------------------------------------------------------------
 // handles
@@ -301,6 +305,7 @@ int circuit_multi(fhe_ctx *c, const fhe_evk *evk, const std::vector<MultiItem> &
 int op_slice(fhe_ctx *c, const fhe_ct *a, int start, int n, fhe_ct **out);
 int op_concat(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **out);
 std::vector<int64_t> tournament_galois(const fhe_ctx *c);
+int batch_check_job(const fhe_job &j);
 int circuit_tournament(fhe_ctx *c, const fhe_evk *evk, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct *const *x,
                        int d, bool want_max, bool want_min, uint64_t seed, fhe_ct **out_max, fhe_ct **out_min);
 

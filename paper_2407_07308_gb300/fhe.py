@@ -48,6 +48,24 @@ class fhe_allocator(Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", c_void_p)]
 
 
+class fhe_server_config(Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_batch", c_int), ("reserved", c_int)]
+
+
+class fhe_request_info(Structure):
+    _fields_ = [("state", c_int), ("error", c_int), ("t_submit_ms", ctypes.c_double),
+                ("t_start_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double), ("est_bytes", ctypes.c_uint64)]
+
+
+class fhe_server_status(Structure):
+    _fields_ = [("queued", ctypes.c_longlong), ("running", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong), ("batches", ctypes.c_longlong), ("admitted_bytes", ctypes.c_uint64),
+                ("admitted_peak_bytes", ctypes.c_uint64)]
+
+
+FHE_REQ_QUEUED, FHE_REQ_RUNNING, FHE_REQ_DONE = 0, 1, 2
+
+
 class fhe_job(Structure):
     _fields_ = [("ctx", c_void_p), ("evk", c_void_p), ("kind", c_int), ("d", c_int), ("x", c_void_p),
                 ("y", c_void_p), ("out0", c_void_p), ("out1", c_void_p)]
@@ -124,6 +142,15 @@ def lib() -> ctypes.CDLL:
             "fhe_batch_submit": (ci, [vp, ci, POINTER(vp)]),
             "fhe_batch_wait": (ci, [vp, ci]),
             "fhe_batch_destroy": (None, [vp]),
+            "fhe_job_footprint": (ctypes.c_uint64, [vp]),
+            "fhe_ctx_inject_alloc_failure": (ci, [vp, ctypes.c_int64]),
+            "fhe_ctx_trim": (ci, [vp]),
+            "fhe_ctx_memory_peak": (ci, [vp, POINTER(ctypes.c_uint64), ci]),
+            "fhe_server_start": (ci, [vp, POINTER(vp)]),
+            "fhe_server_submit": (ci, [vp, vp, POINTER(ctypes.c_uint64)]),
+            "fhe_server_poll": (ci, [vp, ctypes.c_uint64, ci, vp]),
+            "fhe_server_stats": (ci, [vp, vp]),
+            "fhe_server_stop": (ci, [vp]),
             "fhe_tournament_galois": (ci, [vp, vp, ci]),
             "fhe_tournament": (ci, [vp, vp, vp, vp, vp, ci, u64, vp, vp]),
             "fhe_refresh_explicit": (ci, [vp, vp, vp, vp, vp, vp, vp, POINTER(vp)]),
@@ -183,17 +210,25 @@ def torch_allocator(device: int = 0):
 # wrappers with the C names
 # ---------------------------------------------------------------------------
 
+# allocator callbacks of live contexts: the library calls them until
+# fhe_ctx_destroy, so they must not be garbage-collected before
+_ALLOCATORS = {}
+
+
 def fhe_ctx_create(log_n, p, L, K, prime_mod, prime_lo, prime_hi, allocator=None, stream=None):
     P = fhe_params(log_n, p, L, K, prime_mod, prime_lo, prime_hi)
     out = c_void_p()
     rc = lib().fhe_ctx_create(ctypes.byref(P), ctypes.byref(allocator) if allocator is not None else None,
                               c_void_p(stream or 0), ctypes.byref(out))
     _check(rc)
+    if allocator is not None:
+        _ALLOCATORS[out.value] = allocator
     return out
 
 
 def fhe_ctx_destroy(ctx):
     lib().fhe_ctx_destroy(ctx)
+    _ALLOCATORS.pop(ctx.value if isinstance(ctx, c_void_p) else ctx, None)
 
 
 def fhe_ctx_info(ctx) -> fhe_info:
@@ -529,6 +564,58 @@ def fhe_batch_wait(batch, timeout_ms: int) -> int:
 
 def fhe_batch_destroy(batch):
     lib().fhe_batch_destroy(batch)
+
+
+def fhe_ctx_trim(ctx):
+    _check(lib().fhe_ctx_trim(ctx), ctx)
+
+
+def fhe_ctx_inject_alloc_failure(ctx, n: int):
+    _check(lib().fhe_ctx_inject_alloc_failure(ctx, int(n)), ctx)
+
+
+def fhe_ctx_memory_peak(ctx, reset: bool = False) -> int:
+    v = ctypes.c_uint64()
+    _check(lib().fhe_ctx_memory_peak(ctx, ctypes.byref(v), int(reset)), ctx)
+    return v.value
+
+
+def fhe_job_footprint(job: "Job") -> int:
+    st = job.struct()
+    return int(lib().fhe_job_footprint(ctypes.byref(st)))
+
+
+def fhe_server_start(hbm_budget: int = 0, max_batch: int = 0):
+    cfg = fhe_server_config(int(hbm_budget), int(max_batch), 0)
+    out = c_void_p()
+    _check(lib().fhe_server_start(ctypes.byref(cfg), ctypes.byref(out)))
+    return out
+
+
+def fhe_server_submit(server, job: "Job") -> int:
+    """Queues the job; the Job object must stay alive (its output arrays
+    receive the handles) until fhe_server_poll reports it done."""
+    st = job.struct()
+    t = ctypes.c_uint64()
+    _check(lib().fhe_server_submit(server, ctypes.byref(st), ctypes.byref(t)), job.ctx)
+    return t.value
+
+
+def fhe_server_poll(server, ticket: int, timeout_ms: int = 0):
+    """(done, fhe_request_info)."""
+    info = fhe_request_info()
+    rc = _check(lib().fhe_server_poll(server, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(info)))
+    return rc == 1, info
+
+
+def fhe_server_stats(server) -> fhe_server_status:
+    st = fhe_server_status()
+    _check(lib().fhe_server_stats(server, ctypes.byref(st)))
+    return st
+
+
+def fhe_server_stop(server):
+    _check(lib().fhe_server_stop(server))
 
 
 def fhe_ctx_autotune(ctx, njobs: int) -> int:
