@@ -306,6 +306,14 @@ typedef struct fhe_batch fhe_batch;
  * contexts run on their own streams.  Each result equals what the job gives
  * alone.  Enqueues and returns; `*out` tracks completion. */
 int fhe_batch_submit(const fhe_job *jobs, int n, fhe_batch **out);
+/* Graph capture of recurring submissions: the second time a context receives
+ * the same group shapes (keys, kind, digits, level, ciphertexts per group),
+ * its circuit is captured into a CUDA graph with operand and result buffers
+ * of its own; later submissions of that shape copy the operands in, replay
+ * the graph and slice the results out (identical bits).  At most max_plans
+ * graphs are kept per context, least recently used evicted (default 4; 0
+ * turns capture off and frees the kept graphs). */
+int fhe_ctx_set_batch_graphs(fhe_ctx *ctx, int max_plans);
 /* 0 once every job of the batch is complete; FHE_ETIMEOUT if that takes
  * longer than timeout_ms (the batch keeps running; wait again later). */
 int fhe_batch_wait(fhe_batch *batch, int timeout_ms);

@@ -6,10 +6,15 @@
 // the dependency scheduler (c->multistream), so groups of different levels
 // and digit counts overlap on the device; different contexts (ring degrees,
 // plaintext primes) run on their own streams.  Results are sliced back into
-// per-job handles.  Completion is tracked with one event per context;
-// fhe_batch_wait polls them with a deadline and never blocks without bound.
+// per-job handles.  A context that receives a submission of the same group
+// shapes again captures the circuit once into a CUDA graph with its own
+// operand and result buffers and from then on copies the operands in,
+// replays the graph and slices the results out.  Completion is tracked with
+// one event per context; fhe_batch_wait polls them with a deadline and never
+// blocks without bound.
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <map>
 #include <thread>
@@ -78,9 +83,11 @@ int gather(fhe_ctx *c, const fhe_job *jobs, const std::vector<int> &ids, int k, 
     return 0;
 }
 
-int run_context(fhe_ctx *c, const fhe_job *jobs, const std::vector<int> &ids)
+using GroupMap = std::map<std::tuple<const fhe_evk *, int, int, int, bool, bool>, Group>;
+
+GroupMap make_groups(const fhe_job *jobs, const std::vector<int> &ids)
 {
-    std::map<std::tuple<const fhe_evk *, int, int, int, bool, bool>, Group> groups;
+    GroupMap groups;
     for (int id : ids) {
         const fhe_job &j = jobs[id];
         auto key = std::make_tuple(j.evk, j.kind, j.d, j.x[0]->level, j.out0 != nullptr, j.out1 != nullptr);
@@ -91,6 +98,191 @@ int run_context(fhe_ctx *c, const fhe_job *jobs, const std::vector<int> &ids)
         g.level = j.x[0]->level;
         g.jobs.push_back(id);
     }
+    return groups;
+}
+
+// shape of a context's submission: per group (keys, kind, digits, level,
+// ciphertexts, wanted outputs)
+std::vector<u64> signature(const fhe_job *jobs, const GroupMap &groups)
+{
+    std::vector<u64> sig;
+    for (auto &kv : groups) {
+        const Group &g = kv.second;
+        u64 cnt = 0;
+        for (int id : g.jobs) cnt += jobs[id].x[0]->count;
+        const fhe_job &j0 = jobs[g.jobs[0]];
+        sig.insert(sig.end(), {(u64)(uintptr_t)g.evk, (u64)g.kind, (u64)g.d, (u64)g.level, cnt,
+                               (u64)(j0.out0 != nullptr), (u64)(j0.out1 != nullptr)});
+    }
+    return sig;
+}
+
+std::vector<MultiItem> items_for(Group &g, const fhe_job &j0, std::vector<fhe_ct *> &X, std::vector<fhe_ct *> &Y,
+                                 std::vector<fhe_ct *> &O0, std::vector<fhe_ct *> &O1)
+{
+    O0.assign(g.kind == FHE_JOB_MAXMIN ? g.d : 1, nullptr);
+    O1.assign(g.kind == FHE_JOB_MAXMIN ? g.d : 1, nullptr);
+    MultiItem it;
+    it.x = X.data();
+    it.y = Y.data();
+    it.d = g.d;
+    it.maxmin = g.kind == FHE_JOB_MAXMIN;
+    it.out0 = j0.out0 ? O0.data() : nullptr;
+    it.out1 = j0.out1 ? O1.data() : nullptr;
+    return {it};
+}
+
+// results of group g (held in src0/src1) back to its jobs: a slice per job,
+// or (direct, one job) the handles themselves
+int scatter(fhe_ctx *c, const fhe_job *jobs, const Group &g, std::vector<fhe_ct *> &src0,
+            std::vector<fhe_ct *> &src1, bool transfer)
+{
+    int err = 0, off = 0;
+    for (int id : g.jobs) {
+        const fhe_job &j = jobs[id];
+        const int cnt = j.x[0]->count;
+        for (int s = 0; s < 2 && !err; s++) {
+            fhe_ct **dst = s == 0 ? j.out0 : j.out1;
+            std::vector<fhe_ct *> &src = s == 0 ? src0 : src1;
+            if (!dst) continue;
+            for (size_t k = 0; k < src.size() && !err; k++) {
+                if (!src[k]) continue;
+                if (transfer && g.jobs.size() == 1) {
+                    dst[k] = src[k];
+                    src[k] = nullptr;
+                } else {
+                    err = op_slice(c, src[k], off, cnt, &dst[k]);
+                }
+            }
+        }
+        off += cnt;
+    }
+    return err;
+}
+
+// each job's digit-k operands into the plan's buffer (one copy per part)
+void fill(fhe_ctx *c, const fhe_job *jobs, const Group &g, int k, bool ys, fhe_ct *dst)
+{
+    size_t off = 0;
+    for (int id : g.jobs) {
+        const fhe_ct *part = ys ? jobs[id].y[k] : jobs[id].x[k];
+        cudaMemcpyAsync((char *)dst->d + off, part->d, part->bytes, cudaMemcpyDeviceToDevice, c->stream);
+        off += part->bytes;
+    }
+}
+
+void plan_free(fhe_ctx *c, BatchPlan *P)
+{
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    for (auto *v : {&P->X, &P->Y, &P->O0, &P->O1})
+        for (auto &g : *v)
+            for (fhe_ct *x : g) fhe_ct_destroy(x);
+    for (auto &kv : P->held)
+        for (void *p : kv.second) c->pool.put(p);
+    delete P;
+}
+
+// Captures the circuit of these groups into a new plan (nothing runs).
+int capture(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups, const std::vector<u64> &sig, BatchPlan **out)
+{
+    BatchPlan *P = new BatchPlan;
+    P->sig = sig;
+    int err = 0;
+    std::map<const fhe_evk *, std::vector<MultiItem>> by_evk;
+    for (auto &kv : groups) {
+        Group &g = kv.second;
+        int cnt = 0;
+        for (int id : g.jobs) cnt += jobs[id].x[0]->count;
+        P->X.emplace_back();
+        P->Y.emplace_back();
+        P->O0.emplace_back();
+        P->O1.emplace_back();
+        for (int k = 0; k < g.d && !err; k++) {
+            fhe_ct *a = ct_new(c, cnt, 2, g.level, &err);
+            fhe_ct *b = a ? ct_new(c, cnt, 2, g.level, &err) : nullptr;
+            P->X.back().push_back(a);
+            P->Y.back().push_back(b);
+        }
+        if (err) break;
+    }
+    if (!err) {
+        size_t gi = 0;
+        for (auto &kv : groups) {
+            Group &g = kv.second;
+            auto it = items_for(g, jobs[g.jobs[0]], P->X[gi], P->Y[gi], P->O0[gi], P->O1[gi]);
+            by_evk[g.evk].push_back(it[0]);
+            gi++;
+        }
+    }
+    cudaStream_t user = c->stream, cap = nullptr;
+    if (!err) err = fhe_cuda_check(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+    if (!err) {
+        const bool prof = c->prof_on;
+        c->prof_on = false;
+        c->pool.cap_free = &P->held;
+        c->pool.in_capture = true;
+        c->stream = cap;
+        c->pool.stream = cap;
+        err = fhe_cuda_check(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed), "begin capture");
+        if (!err) {
+            c->capturing = true;
+            for (auto &kv : by_evk) {
+                if (err) break;
+                err = circuit_multi(c, kv.first, kv.second);
+            }
+            c->capturing = false;
+            cudaGraph_t gr = nullptr;
+            const int e2 = fhe_cuda_check(c, cudaStreamEndCapture(cap, &gr), "end capture");
+            if (!err) err = e2;
+            P->graph = gr;
+        }
+        c->stream = user;
+        c->pool.stream = user;
+        c->pool.cap_free = nullptr;
+        c->pool.in_capture = false;
+        c->prof_on = prof;
+        cudaStreamDestroy(cap);
+    }
+    if (!err) err = fhe_cuda_check(c, cudaGraphInstantiate(&P->exec, P->graph, 0), "graph instantiate");
+    if (!err) {
+        size_t n = 0;
+        cudaGraphGetNodes(P->graph, nullptr, &n);
+        P->nodes = (int)n;
+    }
+    if (err) {
+        plan_free(c, P);
+        return err;
+    }
+    *out = P;
+    return 0;
+}
+
+int replay(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups, BatchPlan *P)
+{
+    size_t gi = 0;
+    for (auto &kv : groups) {
+        const Group &g = kv.second;
+        for (int k = 0; k < g.d; k++) {
+            fill(c, jobs, g, k, false, P->X[gi][k]);
+            fill(c, jobs, g, k, true, P->Y[gi][k]);
+        }
+        gi++;
+    }
+    int err = fhe_cuda_check(c, cudaGraphLaunch(P->exec, c->stream), "batch graph launch");
+    c->launches += P->nodes;
+    P->last = ++c->bplan_clock;
+    gi = 0;
+    for (auto &kv : groups) {
+        if (err) break;
+        err = scatter(c, jobs, kv.second, P->O0[gi], P->O1[gi], false);
+        gi++;
+    }
+    return err;
+}
+
+int run_direct(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups)
+{
     int err = 0;
     // operands
     for (auto &kv : groups) {
@@ -98,8 +290,6 @@ int run_context(fhe_ctx *c, const fhe_job *jobs, const std::vector<int> &ids)
         g.X.assign(g.d, nullptr);
         g.Y.assign(g.d, nullptr);
         g.own_x.assign(2 * g.d, false);
-        g.out0.assign(g.kind == FHE_JOB_MAXMIN ? g.d : 1, nullptr);
-        g.out1.assign(g.kind == FHE_JOB_MAXMIN ? g.d : 1, nullptr);
         for (int k = 0; k < g.d && !err; k++) {
             bool o1 = false, o2 = false;
             err = gather(c, jobs, g.jobs, k, false, &g.X[k], &o1);
@@ -114,15 +304,8 @@ int run_context(fhe_ctx *c, const fhe_job *jobs, const std::vector<int> &ids)
     if (!err)
         for (auto &kv : groups) {
             Group &g = kv.second;
-            const fhe_job &j0 = jobs[g.jobs[0]];
-            MultiItem it;
-            it.x = g.X.data();
-            it.y = g.Y.data();
-            it.d = g.d;
-            it.maxmin = g.kind == FHE_JOB_MAXMIN;
-            it.out0 = j0.out0 ? g.out0.data() : nullptr;
-            it.out1 = j0.out1 ? g.out1.data() : nullptr;
-            by_evk[g.evk].push_back(it);
+            auto it = items_for(g, jobs[g.jobs[0]], g.X, g.Y, g.out0, g.out1);
+            by_evk[g.evk].push_back(it[0]);
         }
     c->multistream = true;
     for (auto &kv : by_evk) {
@@ -130,38 +313,60 @@ int run_context(fhe_ctx *c, const fhe_job *jobs, const std::vector<int> &ids)
         err = circuit_multi(c, kv.first, kv.second);
     }
     c->multistream = false;
-    // results back to the jobs
     for (auto &kv : groups) {
         Group &g = kv.second;
-        int off = 0;
-        for (int id : g.jobs) {
-            const fhe_job &j = jobs[id];
-            const int cnt = j.x[0]->count;
-            for (int s = 0; s < 2 && !err; s++) {
-                fhe_ct **dst = s == 0 ? j.out0 : j.out1;
-                std::vector<fhe_ct *> &src = s == 0 ? g.out0 : g.out1;
-                if (!dst) continue;
-                for (size_t k = 0; k < src.size() && !err; k++) {
-                    if (!src[k]) continue;
-                    if (g.jobs.size() == 1) {
-                        dst[k] = src[k];
-                        src[k] = nullptr;
-                    } else {
-                        err = op_slice(c, src[k], off, cnt, &dst[k]);
-                    }
-                }
-            }
-            off += cnt;
-        }
+        if (!err) err = scatter(c, jobs, g, g.out0, g.out1, true);
         for (fhe_ct *x : g.out0) fhe_ct_destroy(x);
         for (fhe_ct *x : g.out1) fhe_ct_destroy(x);
-        for (int k = 0; k < 2 * g.d; k++)
+        for (int k = 0; k < 2 * g.d && k < (int)g.own_x.size(); k++)
             if (g.own_x[k]) fhe_ct_destroy(k < g.d ? g.X[k] : g.Y[k - g.d]);
     }
     return err;
 }
 
+// A submission whose shape the context has served before is captured (once)
+// and replayed; a new shape runs directly under the multi-stream scheduler.
+int run_context(fhe_ctx *c, const fhe_job *jobs, const std::vector<int> &ids)
+{
+    GroupMap groups = make_groups(jobs, ids);
+    if (c->bplan_cap <= 0) return run_direct(c, jobs, groups);
+    const std::vector<u64> sig = signature(jobs, groups);
+    for (BatchPlan *P : c->bplans)
+        if (P->sig == sig) return replay(c, jobs, groups, P);
+    if (c->bseen.size() > 1024) c->bseen.clear();
+    if (c->bseen[sig]++ == 0) return run_direct(c, jobs, groups);
+    if ((int)c->bplans.size() >= c->bplan_cap) {  // evict the least recently used
+        auto lru = std::min_element(c->bplans.begin(), c->bplans.end(),
+                                    [](const BatchPlan *a, const BatchPlan *b) { return a->last < b->last; });
+        cudaStreamSynchronize(c->stream);
+        plan_free(c, *lru);
+        c->bplans.erase(lru);
+    }
+    BatchPlan *P = nullptr;
+    const int err = capture(c, jobs, groups, sig, &P);
+    if (err) return err;
+    c->bplans.push_back(P);
+    return replay(c, jobs, groups, P);
+}
+
 }  // namespace
+
+void batch_plans_release(fhe_ctx *c)
+{
+    for (BatchPlan *P : c->bplans) plan_free(c, P);
+    c->bplans.clear();
+    c->bseen.clear();
+}
+
+extern "C" int fhe_ctx_set_batch_graphs(fhe_ctx *c, int max_plans)
+{
+    if (!c || max_plans < 0) return FHE_EINVAL;
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaStreamSynchronize(c->stream);
+    batch_plans_release(c);
+    c->bplan_cap = max_plans;
+    return 0;
+}
 
 extern "C" int fhe_batch_submit(const fhe_job *jobs, int n, fhe_batch **out)
 {

@@ -5,6 +5,7 @@
 
 #include <mutex>
 #include <string>
+#include <map>
 #include <unordered_map>
 #include <vector>
 
@@ -99,6 +100,8 @@ void trim_other_pools(Pool *self);
 // handles
 // ---------------------------------------------------------------------------
 
+struct BatchPlan;
+
 struct fhe_ctx {
     // parameters
     int logN = 0, N = 0, L = 0, K = 0, np = 0;
@@ -161,6 +164,13 @@ struct fhe_ctx {
     bool multistream = false;  // the same scheduling without capture (batch execution)
     std::vector<cudaStream_t> branch_streams;
     std::vector<cudaEvent_t> branch_events;  // reused by every capture
+
+    // captured batches: a batch whose group shapes were seen before is
+    // captured once and replayed (least recently used first out)
+    std::vector<BatchPlan *> bplans;
+    std::map<std::vector<u64>, int> bseen;
+    int bplan_cap = 4;
+    u64 bplan_clock = 0;
     long long launches = 0;       // kernels launched since creation
 };
 
@@ -187,6 +197,19 @@ struct fhe_evk {
     std::vector<KeySwitchKey> keys;  // keys[0] = relinearisation
     const KeySwitchKey *find(int64_t g) const;
 };
+
+// A captured batch (see batch.cu): the graph of one context's circuit for a
+// recurring set of job groups, with its own operand and result buffers.
+struct BatchPlan {
+    std::vector<u64> sig;                               // the group shapes it serves
+    std::vector<std::vector<fhe_ct *>> X, Y, O0, O1;    // [group][digit]
+    std::unordered_map<size_t, std::vector<void *>> held;  // temporaries reused on every replay
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int nodes = 0;
+    u64 last = 0;
+};
+void batch_plans_release(fhe_ctx *c);
 
 struct fhe_plan {
     fhe_ctx *ctx;

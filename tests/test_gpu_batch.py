@@ -113,3 +113,70 @@ def test_batch_wait_timeout_is_bounded():
         fhe.fhe_pk_destroy(pk)
     finally:
         fhe.fhe_ctx_destroy(ctx)
+
+
+def test_recurring_batches_are_captured_and_match_alone():
+    """The same group shapes submitted again are captured into a graph and
+    replayed: every submission (direct, capture, replays, after eviction)
+    gives each job the bits of the job alone, for new operand values each
+    time."""
+    from paper_2407_07308_gb300 import fhe
+
+    ctx = fhe.fhe_ctx_create(12, 17, 8, 2, CHAIN50["U"], CHAIN50["lo"], CHAIN50["hi"])
+    try:
+        sk, pk = fhe.fhe_keygen(ctx, 7)
+        evk = fhe.fhe_evk_create(ctx, sk, [], 8)
+        ns = fhe.fhe_ctx_info(ctx).slots
+        fhe.fhe_ctx_set_batch_graphs(ctx, 1)
+        rnd = np.random.default_rng(5)
+        shapes = {"a": [(1, 2, 8, fhe.FHE_JOB_COMPARE), (2, 1, 7, fhe.FHE_JOB_MAXMIN), (1, 1, 8, fhe.FHE_JOB_COMPARE)],
+                  "b": [(2, 2, 8, fhe.FHE_JOB_COMPARE)]}
+        launches = []
+        for rep, name in enumerate(["a", "a", "a", "b", "b", "a", "a", "a"]):
+            jobs, metas, hs = [], [], []
+            for i, (d, count, level, kind) in enumerate(shapes[name]):
+                xv = rnd.integers(0, 9 ** d, size=(count, ns))
+                yv = np.where(rnd.random((count, ns)) < 0.3, xv, rnd.integers(0, 9 ** d, size=(count, ns)))
+                xs, ys = [], []
+                for k in range(d):
+                    for vals, out, sd in ((xv, xs, 100 * rep + 10 * i + k), (yv, ys, 100 * rep + 10 * i + 5 + k)):
+                        h = fhe.fhe_encrypt(ctx, pk, (vals // 9 ** k) % 9, sd)
+                        if level < 8:
+                            h2 = fhe.fhe_mod_switch(ctx, h, level)
+                            hs.append(h)
+                            h = h2
+                        out.append(h)
+                        hs.append(h)
+                jobs.append(fhe.Job(ctx, evk, kind, xs, ys))
+                metas.append((kind, xs, ys, xv, yv, d))
+            l0 = fhe.fhe_ctx_launches(ctx)
+            b = fhe.fhe_batch_submit(jobs)
+            assert fhe.fhe_batch_wait(b, 120000) == 0
+            fhe.fhe_batch_destroy(b)
+            launches.append(fhe.fhe_ctx_launches(ctx) - l0)
+            for job, (kind, xs, ys, xv, yv, d) in zip(jobs, metas):
+                if kind == fhe.FHE_JOB_COMPARE:
+                    lt, eq = fhe.fhe_compare(ctx, evk, xs, ys)
+                    alone = [lt, eq]
+                    got = job.out0 + job.out1
+                    assert (fhe.fhe_decrypt(ctx, sk, job.out0[0]) == (xv < yv)).all()
+                else:
+                    mx, mn = fhe.fhe_max_min(ctx, evk, xs, ys)
+                    alone = mx + mn
+                    got = job.out0 + job.out1
+                    m = sum(fhe.fhe_decrypt(ctx, sk, job.out0[k]).astype(np.int64) * 9 ** k for k in range(d))
+                    assert (m == np.maximum(xv, yv)).all()
+                for a, g in zip(alone, got):
+                    assert np.array_equal(fhe.fhe_ct_export_coeff(ctx, a), fhe.fhe_ct_export_coeff(ctx, g))
+                hs += alone + got
+            for h in hs:
+                fhe.fhe_ct_destroy(h)
+        # replays count the graph's nodes; the direct runs and captures do not
+        # differ by much, so only check that every run launched work
+        assert all(n > 0 for n in launches)
+        fhe.fhe_ctx_set_batch_graphs(ctx, 0)
+        fhe.fhe_evk_destroy(evk)
+        fhe.fhe_sk_destroy(sk)
+        fhe.fhe_pk_destroy(pk)
+    finally:
+        fhe.fhe_ctx_destroy(ctx)
