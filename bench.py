@@ -53,6 +53,24 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The largest x over the ranks (the slowest replica's time); x itself
+    when there is one rank."""
+    if world <= 1:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: float, world: int, steps: int, total_ms: float) -> float:
+    """Units all replicas processed per second, over the slowest replica's
+    time (weak scaling: every rank runs the same workload)."""
+    return world * units_per_rank_step * steps / (total_ms / 1e3)
+
+
 # ---------------------------------------------------------------------------
 # inputs (shared by both arms; seeded)
 # ---------------------------------------------------------------------------
@@ -284,13 +302,9 @@ def run_gpu(args):
     barrier()
     launches = fhe.fhe_ctx_launches(ctx) - l0
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), world)
     ms_per_step = total_ms / args.steps
-    value = world * pairs * ns * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(pairs * ns, world, args.steps, total_ms)
 
     # ---- per-kernel device time: a second capture with an event pair around
     # every kernel (event-record nodes in the graph), replayed K times; the
@@ -428,13 +442,9 @@ def run_e2e(fhe, ctx, plan, outs, xs, ys, pairs, ns, N, args, world, barrier):
     for _ in range(args.steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t
-    if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    return {"value": round(world * pairs * ns * args.steps / e2e_s, 2), "unit": UNIT, "h2d_bytes_per_step": bi,
-            "d2h_bytes_per_step": bo}
+    e2e_s = max_over_ranks(time.perf_counter() - t, world)
+    return {"value": round(whole_job_rate(pairs * ns, world, args.steps, 1e3 * e2e_s), 2), "unit": UNIT,
+            "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
 
 
 # ---------------------------------------------------------------------------
@@ -730,6 +740,77 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_tournament(args):
+    """Max and min of 4096 encrypted values (10% duplicates; N = 2^15,
+    p = 257, d = 2 digits of base 129, 32 ciphertexts of 128 slots, 20 x
+    50-bit + 4 special primes): 5 cross-ciphertext rounds and 7 in-slot
+    rounds with rotations, refreshed (decrypt + re-encrypt on the device)
+    whenever a round would end below level 1.  One step = one tournament."""
+    import numpy as np
+    import torch
+
+    from paper_2407_07308_gb300 import fhe, synth
+
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    ctx = fhe.fhe_ctx_create(15, 257, 20, 4, U50, 2 ** 49, 2 ** 50, allocator=fhe.torch_allocator(local),
+                             stream=stream.cuda_stream)
+    sk, pk = fhe.fhe_keygen(ctx, 4)
+    evk = fhe.fhe_evk_create(ctx, sk, fhe.fhe_tournament_galois(ctx), 5)
+    g = synth.rng(4)
+    vals = synth.values_with_duplicates(g, 4096, 129 ** 2, 0.10)
+    b, d = 129, 2
+    dig = synth.to_digits(vals, b, d)
+    xs = [fhe.fhe_encrypt(ctx, pk, dig[k].reshape(32, 128).astype(np.uint64), 100 + k) for k in range(d)]
+
+    def one(seed, check=False):
+        mx, mn = fhe.fhe_tournament(ctx, evk, sk, pk, xs, seed)
+        if check:
+            got_max = sum(fhe.fhe_decrypt(ctx, sk, mx[k]).astype(np.int64) * b ** k for k in range(d))
+            got_min = sum(fhe.fhe_decrypt(ctx, sk, mn[k]).astype(np.int64) * b ** k for k in range(d))
+            assert (got_max == vals.max()).all() and (got_min == vals.min()).all(), "tournament mismatch"
+        for h in mx + mn:
+            fhe.fhe_ct_destroy(h)
+
+    one(1, check=True)
+    for i in range(args.warmup - 1):
+        one(2 + i)
+    fhe.fhe_ctx_sync(ctx)
+    l0 = fhe.fhe_ctx_launches(ctx)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        evs[0].record(stream)
+        for i in range(args.steps):
+            one(100 + i)
+            evs[i + 1].record(stream)
+        stream.synchronize()
+    launches = fhe.fhe_ctx_launches(ctx) - l0
+    ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total = evs[0].elapsed_time(evs[-1])
+    line = {
+        "metric": "encrypted values reduced to their max and min per second (4096-value tournament)",
+        "value": round(4096 * args.steps / (total / 1e3), 1), "unit": "values/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded BGV keys, noise and values, 10% duplicates)",
+        "config": {"workload": "max and min of 4096 values in [0, 129^2), N=2^15, p=257, d=2, 32 ciphertexts x "
+                               "128 slots, 20x50-bit + 4 special primes, refresh (device decrypt + re-encrypt) "
+                               "inside the timed region", "rounds": "5 cross-ciphertext + 7 in-slot (rotations)",
+                   "l2": "ciphertexts 336 MB per digit set > L2"},
+        "tournament_ms_p50": round(sorted(ms)[len(ms) // 2], 2), "gpu_launches": launches,
+        "clocks": clk.summary(), "cpu_baseline": None, "roofline": None, "e2e": None,
+    }
+    for h in xs:
+        fhe.fhe_ct_destroy(h)
+    fhe.fhe_evk_destroy(evk)
+    fhe.fhe_sk_destroy(sk)
+    fhe.fhe_pk_destroy(pk)
+    fhe.fhe_ctx_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -741,8 +822,9 @@ def main():
     ap.add_argument("--pairs", type=int, default=16, help="ciphertext pairs per batch (16 = the workload)")
     ap.add_argument("--no-plain", action="store_true", help="skip the one-request-at-a-time form")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
-    ap.add_argument("--workload", default="compare", choices=["compare", "uneven", "serve"],
-                    help="compare: the 16-pair batch (default); uneven: 256 mixed requests; serve: serving loop")
+    ap.add_argument("--workload", default="compare", choices=["compare", "uneven", "serve", "tournament"],
+                    help="compare: the 16-pair batch (default); uneven: 256 mixed requests; serve: serving "
+                         "loop; tournament: max/min of 4096 values")
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate (requests/s) for serve")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -755,6 +837,8 @@ def main():
         run_uneven(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "tournament":
+        run_tournament(args)
     else:
         run_gpu(args)
 
