@@ -77,22 +77,26 @@ __device__ __forceinline__ void fwd_round(u64 (&x)[1 << R], int s0, int hi, TW W
     }
 }
 
+// One stage of the inverse on x[0..2^R): local stage U, butterflies of
+// half-distance 2^(R-1-U).  A template per stage keeps every index a
+// compile-time constant, so x stays in registers.
+template <int R, int U, class TW>
+__device__ __forceinline__ void inv_stage(u64 (&x)[1 << R], int s0, int hi, TW W, u64 q, u64 q2)
+{
+    constexpr int half = 1 << (R - 1 - U);
+#pragma unroll
+    for (int t = 0; t < (1 << U); t++) {
+        const ulonglong2 w = W.get(s0 + U, (hi << U) + t);
+#pragma unroll
+        for (int k = 0; k < half; k++) gs_bfly(x[t * 2 * half + k], x[t * 2 * half + k + half], w, q, q2);
+    }
+    if constexpr (U > 0) inv_stage<R, U - 1>(x, s0, hi, W, q, q2);
+}
+
 template <int R, class TW>
 __device__ __forceinline__ void inv_round(u64 (&x)[1 << R], int s0, int hi, TW W, u64 q, u64 q2)
 {
-#pragma unroll
-    for (int u = R - 1; u >= 0; u--) {
-        const int half = 1 << (R - 1 - u);
-#pragma unroll
-        for (int t = 0; t < (1 << u); t++) {
-            const ulonglong2 w = W.get(s0 + u, (hi << u) + t);
-#pragma unroll
-            for (int k = 0; k < half; k++) {
-                const int e = t * 2 * half + k;
-                gs_bfly(x[e], x[e + half], w, q, q2);
-            }
-        }
-    }
+    inv_stage<R, R - 1>(x, s0, hi, W, q, q2);
 }
 
 // ---------------------------------------------------------------------------
@@ -201,7 +205,7 @@ struct RowTw {
 // Forward, columns: global stages 0..N1-1 on columns lo0..lo0+15.
 template <int N1, int N2, class IO>
 __global__ void __launch_bounds__(Sub<N1>::T)
-    k_fwd_cols(const IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
+    k_fwd_cols(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
 {
     using C = Sub<N1>;
     constexpr int NN = 1 << (N1 + N2), BLK = (1 << N2) / 16;
@@ -228,7 +232,7 @@ __global__ void __launch_bounds__(Sub<N1>::T)
 // Forward, rows: global stages N1..N1+N2-1 on rows hi0..hi0+15.
 template <int N1, int N2, class IO>
 __global__ void __launch_bounds__(Sub<N2>::T)
-    k_fwd_rows(const IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
+    k_fwd_rows(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
 {
     using C = Sub<N2>;
     constexpr int NN = 1 << (N1 + N2), BLK = (1 << N1) / 16;
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(Sub<N2>::T)
 // Inverse, rows first: undoes global stages N1+N2-1..N1.
 template <int N1, int N2, class IO>
 __global__ void __launch_bounds__(Sub<N2>::T)
-    k_inv_rows(const IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
+    k_inv_rows(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
 {
     using C = Sub<N2>;
     constexpr int NN = 1 << (N1 + N2), BLK = (1 << N1) / 16;
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(Sub<N2>::T)
 // with base = g % stride, kb = g / stride.
 template <int N1, int N2, class IO>
 __global__ void __launch_bounds__(Sub<N2>::T)
-    k_fwd_rows_grp(const IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw, int stride)
+    k_fwd_rows_grp(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw, int stride)
 {
     using C = Sub<N2>;
     constexpr int NN = 1 << (N1 + N2), ROWS = 1 << N1;
@@ -307,7 +311,7 @@ __global__ void __launch_bounds__(Sub<N2>::T)
 
 template <int N1, int N2, class IO>
 __global__ void __launch_bounds__(Sub<N2>::T)
-    k_inv_rows_grp(const IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw, int stride)
+    k_inv_rows_grp(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw, int stride)
 {
     using C = Sub<N2>;
     constexpr int NN = 1 << (N1 + N2), ROWS = 1 << N1;
@@ -341,7 +345,7 @@ __global__ void __launch_bounds__(Sub<N2>::T)
 // Inverse, columns: undoes global stages N1-1..0, then scales by N^-1.
 template <int N1, int N2, class IO>
 __global__ void __launch_bounds__(Sub<N1>::T)
-    k_inv_cols(const IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw,
+    k_inv_cols(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw,
                const ulonglong2 *__restrict__ ninv)
 {
     using C = Sub<N1>;
