@@ -393,6 +393,11 @@ int fhe_trace_get(const fhe_ctx *ctx, int32_t *ops, int32_t *levels, int cap);
  * Forward output is in bit-reversed order: A[k] = a(psi^(2 brv(k)+1)). */
 int fhe_ntt_forward(fhe_ctx *ctx, uint64_t *data, const int32_t *prime_idx, int nlimbs);
 int fhe_ntt_inverse(fhe_ctx *ctx, uint64_t *data, const int32_t *prime_idx, int nlimbs);
+/* The same transforms over count RNS polynomials in one launch:
+ * data = uint64[count][nprimes][N] (device), limb i of every polynomial
+ * reduced mod prime i (nprimes <= L + K). */
+int fhe_ntt_forward_batch(fhe_ctx *ctx, uint64_t *data, int count, int nprimes);
+int fhe_ntt_inverse_batch(fhe_ctx *ctx, uint64_t *data, int count, int nprimes);
 
 /* ---- modulus switching without allocation -------------------------------------- */
 

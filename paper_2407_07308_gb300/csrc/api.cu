@@ -1152,6 +1152,33 @@ static int raw_ntt(fhe_ctx *c, uint64_t *data, const int32_t *prime_idx, int nli
     return launch_status(c, "ntt");
 }
 
+static int raw_ntt_batch(fhe_ctx *c, uint64_t *data, int count, int nprimes, bool inverse)
+{
+    CHECK_CTX(c);
+    if (!data || count < 1 || nprimes < 1 || nprimes > c->np) return FHE_EINVAL;
+    LOCK(c);
+    LimbMap m;
+    memset(&m, 0, sizeof(m));
+    m.nl = nprimes;
+    m.in_outer = m.out_outer = (long long)nprimes * c->N;
+    for (int i = 0; i < nprimes; i++) m.in_limb[i] = m.out_limb[i] = m.prime[i] = i;
+    if (inverse)
+        launch_ntt_inv_plain(c, data, data, m, count * nprimes);
+    else
+        launch_ntt_fwd_plain(c, data, data, m, count * nprimes);
+    return launch_status(c, "ntt batch");
+}
+
+extern "C" int fhe_ntt_forward_batch(fhe_ctx *c, uint64_t *data, int count, int nprimes)
+{
+    return raw_ntt_batch(c, data, count, nprimes, false);
+}
+
+extern "C" int fhe_ntt_inverse_batch(fhe_ctx *c, uint64_t *data, int count, int nprimes)
+{
+    return raw_ntt_batch(c, data, count, nprimes, true);
+}
+
 extern "C" int fhe_ntt_forward(fhe_ctx *c, uint64_t *data, const int32_t *prime_idx, int nlimbs)
 {
     return raw_ntt(c, data, prime_idx, nlimbs, false);

@@ -87,11 +87,15 @@ __global__ void k_tensor(const u64 *__restrict__ a, const u64 *__restrict__ b, u
 }
 
 // Key-switching inner product.  Extended limb r = blockIdx.y of Q_l P
-// (r < l: data prime r; else special prime L + r - l).  Every thread loads
-// its 2*dnum key words once and reuses them for all ciphertexts of the batch.
-__global__ void k_ks_inner(const u64 *__restrict__ ext, const u64 *__restrict__ xbase, long long x_outer,
-                           const u64 *__restrict__ ksk, u64 *__restrict__ acc, int count, int l, int K, int L,
-                           int dnum, int logN, const ModQ *__restrict__ mq)
+// (r < l: data prime r; else special prime L + r - l); ciphertexts
+// blockIdx.z * CB .. + CB - 1 of the batch.  Every thread loads its 2*dnum
+// key words once and reuses them for its CB ciphertexts, whose input words
+// are all loaded before the first product so that the loads overlap.
+template <int CB>
+__global__ void __launch_bounds__(256, 2)
+    k_ks_inner(const u64 *__restrict__ ext, const u64 *__restrict__ xbase, long long x_outer,
+               const u64 *__restrict__ ksk, u64 *__restrict__ acc, int count, int l, int K, int L, int dnum,
+               int logN, const ModQ *__restrict__ mq)
 {
     const int N = 1 << logN;
     const int r = blockIdx.y;
@@ -99,28 +103,38 @@ __global__ void k_ks_inner(const u64 *__restrict__ ext, const u64 *__restrict__ 
     const ModQ m = mq[prime];
     const int LK = L + K, lK = l + K;
     const int rdig = r < l ? r / K : -1;
+    const int c0 = blockIdx.z * CB;
+    const int ncb = min(CB, count - c0);
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
-        u64 k0[FHE_MAXD], k1[FHE_MAXD];
+        u128 a0[CB], a1[CB];
 #pragma unroll
-        for (int j = 0; j < FHE_MAXD; j++) {
-            if (j < dnum) {
-                k0[j] = ksk[(((long long)j * 2 + 0) * LK + prime) * N + n];
-                k1[j] = ksk[(((long long)j * 2 + 1) * LK + prime) * N + n];
+        for (int cc = 0; cc < CB; cc++) a0[cc] = a1[cc] = 0;
+        for (int j = 0; j < dnum; j++) {
+            const u64 k0 = ksk[(((long long)j * 2 + 0) * LK + prime) * N + n];
+            const u64 k1 = ksk[(((long long)j * 2 + 1) * LK + prime) * N + n];
+            u64 y[CB];
+#pragma unroll
+            for (int cc = 0; cc < CB; cc++) {
+                const int c = c0 + cc;
+                if (cc < ncb)
+                    y[cc] = (j == rdig) ? xbase[c * x_outer + (long long)r * N + n]
+                                        : ext[(((long long)c * dnum + j) * lK + r) * N + n];
             }
-        }
-        for (int c = 0; c < count; c++) {
-            u128 a0 = 0, a1 = 0;
 #pragma unroll
-            for (int j = 0; j < FHE_MAXD; j++) {
-                if (j < dnum) {
-                    const u64 y = (j == rdig) ? xbase[c * x_outer + (long long)r * N + n]
-                                              : ext[(((long long)c * dnum + j) * lK + r) * N + n];
-                    a0 += (u128)y * k0[j];
-                    a1 += (u128)y * k1[j];
+            for (int cc = 0; cc < CB; cc++) {
+                if (cc < ncb) {
+                    a0[cc] += (u128)y[cc] * k0;
+                    a1[cc] += (u128)y[cc] * k1;
                 }
             }
-            acc[(((long long)c * 2 + 0) * lK + r) * N + n] = barrett128(a0, m);
-            acc[(((long long)c * 2 + 1) * lK + r) * N + n] = barrett128(a1, m);
+        }
+#pragma unroll
+        for (int cc = 0; cc < CB; cc++) {
+            const int c = c0 + cc;
+            if (cc < ncb) {
+                acc[(((long long)c * 2 + 0) * lK + r) * N + n] = barrett128(a0[cc], m);
+                acc[(((long long)c * 2 + 1) * lK + r) * N + n] = barrett128(a1[cc], m);
+            }
         }
     }
 }
@@ -301,10 +315,11 @@ void launch_ks_inner(fhe_ctx *c, const u64 *ext, const u64 *xbase, long long x_o
                      int count, int level)
 {
     const int dnum = c->modup[level].dnum;
-    dim3 grid((c->N + TPB - 1) / TPB, level + c->K);
+    constexpr int CB = 4;  // ciphertexts per thread
+    dim3 grid((c->N + TPB - 1) / TPB, level + c->K, (count + CB - 1) / CB);
     // per (r, n): 2 dnum key words once, dnum inputs and 2 outputs per ciphertext
     prof_begin(c, FHE_K_KS_INNER, 8.0 * (double)(level + c->K) * c->N * (2.0 * dnum + count * (dnum + 2.0)));
-    k_ks_inner<<<grid, TPB, 0, c->stream>>>(ext, xbase, x_outer, ksk, acc, count, level, c->K, c->L, dnum, c->logN,
+    k_ks_inner<CB><<<grid, TPB, 0, c->stream>>>(ext, xbase, x_outer, ksk, acc, count, level, c->K, c->L, dnum, c->logN,
                                             c->d_mq);
     prof_end(c);
     c->launches++;

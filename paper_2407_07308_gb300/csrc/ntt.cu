@@ -103,6 +103,20 @@ __device__ __forceinline__ void inv_round(u64 (&x)[1 << R], int s0, int hi, TW W
 // 16 sub-transforms of size 2^M in shared memory
 // ---------------------------------------------------------------------------
 
+// Register cap of every NTT kernel: enough for 768 resident threads per SM
+// (85 registers a thread), measured faster than both the uncapped kernels
+// and a 64-register cap.
+#ifndef FHE_NTT_THREADS_PER_SM
+#define FHE_NTT_THREADS_PER_SM 768
+#endif
+#define FHE_MINB(T) (FHE_NTT_THREADS_PER_SM / (T) > 0 ? FHE_NTT_THREADS_PER_SM / (T) : 1)
+
+// Shared-memory twiddle tables: entry k at k + k / 8 (one 16-byte pad per 8
+// entries), so that the second round's strided twiddle reads (stride up to 8
+// entries across threads) hit distinct banks.
+__host__ __device__ constexpr int twp(int k) { return k + (k >> 3); }
+__host__ __device__ constexpr int twp_size(int n) { return n + n / 8 + 1; }
+
 // Twiddle accessors: get(s, j) = psi^brv(2^s + j), the twiddle of global
 // stage s with in-stage index j < 2^s.
 struct GTw {  // the full table in global memory, read-only path
@@ -112,7 +126,7 @@ struct GTw {  // the full table in global memory, read-only path
 
 struct PrefixTw {  // the first entries of the table, copied to shared memory
     const ulonglong2 *sm;
-    __device__ ulonglong2 get(int s, int j) const { return sm[(1 << s) + j]; }
+    __device__ ulonglong2 get(int s, int j) const { return sm[twp((1 << s) + j)]; }
 };
 
 // smem layout: sub-transform c at c*P(M), element e at e + (e >> 4); P is odd
@@ -185,6 +199,64 @@ __device__ __forceinline__ void sub16(u64 *sm, int tid, TW W, int S, int hi0, in
     }
 }
 
+// Moves a CTA's 16 x 2^M words into shared memory: word r (r = tid + k T)
+// is read by src(r) and written by dst(r, v).  Staged in chunks of CH: the
+// chunk's reads are all issued before its first write (the compiler does not
+// reorder a global read past a shared-memory write on its own), so they
+// overlap; CH = 0 keeps read/write pairs (better for loads that already hold
+// several reads each, like ModUp's basis conversion).
+template <int M, int CH = 16, class Src, class Dst>
+__device__ __forceinline__ void tile_in(int tid, Src src, Dst dst)
+{
+    using C = Sub<M>;
+    constexpr int IT = 16 * C::SZ / C::T;
+    if constexpr (CH > 0) {
+        constexpr int K = CH < IT ? CH : IT;
+#pragma unroll
+        for (int k0 = 0; k0 < IT; k0 += K) {
+            u64 v[K];
+#pragma unroll
+            for (int k = 0; k < K; k++) v[k] = src(tid + (k0 + k) * C::T);
+#pragma unroll
+            for (int k = 0; k < K; k++) dst(tid + (k0 + k) * C::T, v[k]);
+        }
+    } else {
+        for (int r = tid; r < 16 * C::SZ; r += C::T) dst(r, src(r));
+    }
+}
+
+// Stores a CTA's 16 x 2^M results of a forward row pass: word r goes to
+// index idx(r) of state st(r) with value val(r).  Staged: the operands the
+// store reads (IO::NPRE per word) are loaded for a chunk of words before
+// any of the chunk's writes, so those loads overlap (otherwise every write
+// to global memory would order the next word's reads behind it).
+template <int M, class IO, class StF, class Idx, class Val>
+__device__ __forceinline__ void tile_out(const IO &io, int tid, StF st, Idx idx, Val val)
+{
+    using C = Sub<M>;
+    constexpr int IT = 16 * C::SZ / C::T;
+    if constexpr (IO::NPRE > 0) {
+        constexpr int CH = IO::NPRE == 1 ? IT : IT / 2;
+#pragma unroll
+        for (int k0 = 0; k0 < IT; k0 += CH) {
+            u64 a[CH][IO::NPRE];
+#pragma unroll
+            for (int k = 0; k < CH; k++) {
+                const int r = tid + (k0 + k) * C::T;
+#pragma unroll
+                for (int w = 0; w < IO::NPRE; w++) a[k][w] = io.pre(st(r), idx(r), w);
+            }
+#pragma unroll
+            for (int k = 0; k < CH; k++) {
+                const int r = tid + (k0 + k) * C::T;
+                io.store_pre(st(r), idx(r), val(r), a[k]);
+            }
+        }
+    } else {
+        for (int r = tid; r < 16 * C::SZ; r += C::T) io.store(st(r), idx(r), val(r));
+    }
+}
+
 // Grouped row kernels: all 16 sub-transforms of the CTA are row hi of 16
 // limbs with one prime, so the CTA needs only the 2^N2 - 1 twiddles of that
 // row: stage N1+u, in-stage index hi 2^u + t, at offset 2^u - 1 + t.
@@ -194,7 +266,7 @@ struct RowTw {
     __device__ ulonglong2 get(int s, int j) const
     {
         const int u = s - N1;
-        return sm[(1 << u) - 1 + j - (hi << u)];
+        return sm[twp((1 << u) - 1 + j - (hi << u))];
     }
 };
 
@@ -204,21 +276,20 @@ struct RowTw {
 
 // Forward, columns: global stages 0..N1-1 on columns lo0..lo0+15.
 template <int N1, int N2, class IO>
-__global__ void __launch_bounds__(Sub<N1>::T)
+__global__ void __launch_bounds__(Sub<N1>::T, FHE_MINB(Sub<N1>::T))
     k_fwd_cols(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
 {
     using C = Sub<N1>;
     constexpr int NN = 1 << (N1 + N2), BLK = (1 << N2) / 16;
     __shared__ u64 sm[C::WORDS];
-    __shared__ ulonglong2 W[1 << N1];  // stages 0..N1-1 use only the table's prefix
+    __shared__ ulonglong2 W[twp_size(1 << N1)];  // stages 0..N1-1 use only the table's prefix
     const int job = blockIdx.x / BLK, lo0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
     const typename IO::St st = io.begin(job, NN);
     const u64 q = mq[st.prime].q, q2 = 2 * q;
-    for (int r = tid; r < (1 << N1); r += C::T) W[r] = tw[(size_t)st.prime * NN + r];
-    for (int r = tid; r < 16 * C::SZ; r += C::T) {
-        const int c = r & 15, e = r >> 4;
-        sm[C::at(c, e)] = io.load(st, (e << N2) + lo0 + c);
-    }
+    for (int r = tid; r < (1 << N1); r += C::T) W[twp(r)] = tw[(size_t)st.prime * NN + r];
+    tile_in<N1, IO::LDCH>(
+        tid, [&](int r) { return io.load(st, ((r >> 4) << N2) + lo0 + (r & 15)); },
+        [&](int r, u64 v) { sm[C::at(r & 15, r >> 4)] = v; });
     __syncthreads();
     sub16<N1, true>(sm, tid, PrefixTw{W}, 0, 0, 0, q, q2);
     __syncthreads();
@@ -231,7 +302,7 @@ __global__ void __launch_bounds__(Sub<N1>::T)
 
 // Forward, rows: global stages N1..N1+N2-1 on rows hi0..hi0+15.
 template <int N1, int N2, class IO>
-__global__ void __launch_bounds__(Sub<N2>::T)
+__global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
     k_fwd_rows(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
 {
     using C = Sub<N2>;
@@ -242,18 +313,19 @@ __global__ void __launch_bounds__(Sub<N2>::T)
     const u64 q = mq[st.prime].q, q2 = 2 * q;
     const GTw W{tw + (size_t)st.prime * NN};
     const u64 *mid = io.inter(st) + ((size_t)hi0 << N2);
-    for (int r = tid; r < 16 * C::SZ; r += C::T) sm[C::at(r >> N2, r & (C::SZ - 1))] = mid[r];
+    tile_in<N2>(tid, [&](int r) { return mid[r]; }, [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
     __syncthreads();
     sub16<N2, true>(sm, tid, W, N1, hi0, 1, q, q2);
     __syncthreads();
     const ModQ mqp = mq[st.prime];
-    for (int r = tid; r < 16 * C::SZ; r += C::T)
-        io.store(st, (hi0 << N2) + r, reduce64(sm[C::at(r >> N2, r & (C::SZ - 1))], mqp));
+    tile_out<N2>(
+        io, tid, [&](int) -> const typename IO::St & { return st; }, [&](int r) { return (hi0 << N2) + r; },
+        [&](int r) { return reduce64(sm[C::at(r >> N2, r & (C::SZ - 1))], mqp); });
 }
 
 // Inverse, rows first: undoes global stages N1+N2-1..N1.
 template <int N1, int N2, class IO>
-__global__ void __launch_bounds__(Sub<N2>::T)
+__global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
     k_inv_rows(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
 {
     using C = Sub<N2>;
@@ -263,7 +335,9 @@ __global__ void __launch_bounds__(Sub<N2>::T)
     const typename IO::St st = io.begin(job, NN);
     const u64 q = mq[st.prime].q, q2 = 2 * q;
     const GTw W{tw + (size_t)st.prime * NN};
-    for (int r = tid; r < 16 * C::SZ; r += C::T) sm[C::at(r >> N2, r & (C::SZ - 1))] = io.load(st, (hi0 << N2) + r);
+    tile_in<N2>(
+        tid, [&](int r) { return io.load(st, (hi0 << N2) + r); },
+        [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
     __syncthreads();
     sub16<N2, false>(sm, tid, W, N1, hi0, 1, q, q2);
     __syncthreads();
@@ -276,13 +350,13 @@ __global__ void __launch_bounds__(Sub<N2>::T)
 // (group g, row hi): sub-transform c is row hi of job base + (16 kb + c) stride
 // with base = g % stride, kb = g / stride.
 template <int N1, int N2, class IO>
-__global__ void __launch_bounds__(Sub<N2>::T)
+__global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
     k_fwd_rows_grp(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw, int stride)
 {
     using C = Sub<N2>;
     constexpr int NN = 1 << (N1 + N2), ROWS = 1 << N1;
     __shared__ u64 sm[C::WORDS];
-    __shared__ ulonglong2 tws[(1 << N2) - 1];
+    __shared__ ulonglong2 tws[twp_size((1 << N2) - 1)];
     __shared__ typename IO::St sts[16];
     const int tid = threadIdx.x, hi = blockIdx.x % ROWS, g = blockIdx.x / ROWS;
     const int base = g % stride, kb = g / stride;
@@ -294,29 +368,28 @@ __global__ void __launch_bounds__(Sub<N2>::T)
     const ulonglong2 *W = tw + (size_t)prime * NN;
     for (int k = tid; k < (1 << N2) - 1; k += C::T) {
         const int u = 31 - __clz(k + 1);  // stage of entry k
-        tws[k] = __ldg(W + (1 << (N1 + u)) + (hi << u) + (k + 1 - (1 << u)));
+        tws[twp(k)] = __ldg(W + (1 << (N1 + u)) + (hi << u) + (k + 1 - (1 << u)));
     }
-    for (int r = tid; r < 16 * C::SZ; r += C::T) {
-        const int c = r >> N2, f = r & (C::SZ - 1);
-        sm[C::at(c, f)] = io.inter(sts[c])[(hi << N2) + f];
-    }
+    tile_in<N2>(
+        tid, [&](int r) { return io.inter(sts[r >> N2])[(hi << N2) + (r & (C::SZ - 1))]; },
+        [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
     __syncthreads();
     sub16<N2, true>(sm, tid, RowTw{tws, N1, hi}, N1, hi, 0, q, q2);
     __syncthreads();
-    for (int r = tid; r < 16 * C::SZ; r += C::T) {
-        const int c = r >> N2, f = r & (C::SZ - 1);
-        io.store(sts[c], (hi << N2) + f, reduce64(sm[C::at(c, f)], mqp));
-    }
+    tile_out<N2>(
+        io, tid, [&](int r) -> const typename IO::St & { return sts[r >> N2]; },
+        [&](int r) { return (hi << N2) + (r & (C::SZ - 1)); },
+        [&](int r) { return reduce64(sm[C::at(r >> N2, r & (C::SZ - 1))], mqp); });
 }
 
 template <int N1, int N2, class IO>
-__global__ void __launch_bounds__(Sub<N2>::T)
+__global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
     k_inv_rows_grp(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw, int stride)
 {
     using C = Sub<N2>;
     constexpr int NN = 1 << (N1 + N2), ROWS = 1 << N1;
     __shared__ u64 sm[C::WORDS];
-    __shared__ ulonglong2 tws[(1 << N2) - 1];
+    __shared__ ulonglong2 tws[twp_size((1 << N2) - 1)];
     __shared__ typename IO::St sts[16];
     const int tid = threadIdx.x, hi = blockIdx.x % ROWS, g = blockIdx.x / ROWS;
     const int base = g % stride, kb = g / stride;
@@ -327,12 +400,11 @@ __global__ void __launch_bounds__(Sub<N2>::T)
     const ulonglong2 *W = tw + (size_t)prime * NN;
     for (int k = tid; k < (1 << N2) - 1; k += C::T) {
         const int u = 31 - __clz(k + 1);
-        tws[k] = __ldg(W + (1 << (N1 + u)) + (hi << u) + (k + 1 - (1 << u)));
+        tws[twp(k)] = __ldg(W + (1 << (N1 + u)) + (hi << u) + (k + 1 - (1 << u)));
     }
-    for (int r = tid; r < 16 * C::SZ; r += C::T) {
-        const int c = r >> N2, f = r & (C::SZ - 1);
-        sm[C::at(c, f)] = io.load(sts[c], (hi << N2) + f);
-    }
+    tile_in<N2>(
+        tid, [&](int r) { return io.load(sts[r >> N2], (hi << N2) + (r & (C::SZ - 1))); },
+        [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
     __syncthreads();
     sub16<N2, false>(sm, tid, RowTw{tws, N1, hi}, N1, hi, 0, q, q2);
     __syncthreads();
@@ -344,24 +416,23 @@ __global__ void __launch_bounds__(Sub<N2>::T)
 
 // Inverse, columns: undoes global stages N1-1..0, then scales by N^-1.
 template <int N1, int N2, class IO>
-__global__ void __launch_bounds__(Sub<N1>::T)
+__global__ void __launch_bounds__(Sub<N1>::T, FHE_MINB(Sub<N1>::T))
     k_inv_cols(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw,
                const ulonglong2 *__restrict__ ninv)
 {
     using C = Sub<N1>;
     constexpr int NN = 1 << (N1 + N2), BLK = (1 << N2) / 16;
     __shared__ u64 sm[C::WORDS];
-    __shared__ ulonglong2 W[1 << N1];
+    __shared__ ulonglong2 W[twp_size(1 << N1)];
     const int job = blockIdx.x / BLK, lo0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
     const typename IO::St st = io.begin(job, NN);
     const u64 q = mq[st.prime].q, q2 = 2 * q;
-    for (int r = tid; r < (1 << N1); r += C::T) W[r] = tw[(size_t)st.prime * NN + r];
+    for (int r = tid; r < (1 << N1); r += C::T) W[twp(r)] = tw[(size_t)st.prime * NN + r];
     const ulonglong2 ni = io.final_scale(st, ninv);
     const u64 *mid = io.inter(st);
-    for (int r = tid; r < 16 * C::SZ; r += C::T) {
-        const int c = r & 15, e = r >> 4;
-        sm[C::at(c, e)] = mid[(e << N2) + lo0 + c];
-    }
+    tile_in<N1>(
+        tid, [&](int r) { return mid[((r >> 4) << N2) + lo0 + (r & 15)]; },
+        [&](int r, u64 v) { sm[C::at(r & 15, r >> 4)] = v; });
     __syncthreads();
     sub16<N1, false>(sm, tid, PrefixTw{W}, 0, 0, 0, q, q2);
     __syncthreads();
@@ -395,6 +466,10 @@ struct IOPlain {
     }
     __device__ u64 load(const St &s, int i) const { return s.in[i]; }
     __device__ void store(const St &s, int i, u64 v) const { s.out[i] = v; }
+    static constexpr int NPRE = 0;  // operands the store reads
+    static constexpr int LDCH = 16;  // loads staged per chunk (0: not staged)
+    __device__ u64 pre(const St &, int, int) const { return 0; }
+    __device__ void store_pre(const St &s, int i, u64 v, const u64 *) const { s.out[i] = v; }
     __device__ u64 *inter(const St &s) const { return s.out; }
     __device__ ulonglong2 final_scale(const St &s, const ulonglong2 *ninv) const { return ninv[s.prime]; }
     int prime_stride() const { return m.nl; }  // jobs j and j + nl use one prime
@@ -470,6 +545,10 @@ struct IOModUp {
         return barrett128(acc, s.mt);
     }
     __device__ void store(const St &s, int k, u64 v) const { s.dst[k] = v; }
+    static constexpr int NPRE = 0;
+    static constexpr int LDCH = 0;  // each load already sums several limbs
+    __device__ u64 pre(const St &, int, int) const { return 0; }
+    __device__ void store_pre(const St &s, int k, u64 v, const u64 *) const { s.dst[k] = v; }
     __device__ u64 *inter(const St &s) const { return s.dst; }
     int prime_stride() const { return njobs; }  // one entry per (digit, target) and ct
     int stride;  // N
@@ -529,6 +608,16 @@ struct IOModDown {
         if (s.add) r = addmod(r, s.add[k], q);
         s.out[k] = r;
     }
+    static constexpr int NPRE = 2;  // accumulator, addend
+    static constexpr int LDCH = 16;
+    __device__ u64 pre(const St &s, int k, int w) const { return w == 0 ? s.acc[k] : (s.add ? s.add[k] : 0); }
+    __device__ void store_pre(const St &s, int k, u64 v, const u64 *pv) const
+    {
+        const u64 q = s.mi.q;
+        u64 r = shoup(submod(pv[0], v, q), s.pinv, s.pinv_s, q);
+        if (s.add) r = addmod(r, pv[1], q);
+        s.out[k] = r;
+    }
     __device__ u64 *inter(const St &s) const { return s.out; }
     int prime_stride() const { return l; }  // job = (ct, poly) * l + limb
 };
@@ -572,6 +661,13 @@ struct IOModSwitch {
     __device__ void store(const St &s, int k, u64 v) const
     {
         s.out[k] = shoup(submod(s.in[k], v, s.q), s.qi, s.qis, s.q);
+    }
+    static constexpr int NPRE = 1;  // the limb being switched
+    static constexpr int LDCH = 16;
+    __device__ u64 pre(const St &s, int k, int) const { return s.in[k]; }
+    __device__ void store_pre(const St &s, int k, u64 v, const u64 *pv) const
+    {
+        s.out[k] = shoup(submod(pv[0], v, s.q), s.qi, s.qis, s.q);
     }
     __device__ u64 *inter(const St &s) const { return s.out; }
     int prime_stride() const { return l - 1; }  // job = (ct, poly) * (l-1) + limb

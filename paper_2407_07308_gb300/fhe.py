@@ -134,6 +134,8 @@ def lib() -> ctypes.CDLL:
             "fhe_trace_enable": (ci, [vp, ci]),
             "fhe_trace_get": (ci, [vp, vp, vp, ci]),
             "fhe_ntt_forward": (ci, [vp, vp, vp, ci]),
+            "fhe_ntt_forward_batch": (ci, [vp, vp, ci, ci]),
+            "fhe_ntt_inverse_batch": (ci, [vp, vp, ci, ci]),
             "fhe_ntt_inverse": (ci, [vp, vp, vp, ci]),
             "fhe_selftest_modarith": (ci, [u64, u64, u64, ci, ci]),
             "fhe_ctx_profile": (ci, [vp, ci]),
@@ -649,6 +651,14 @@ def fhe_trace_get(ctx):
 def fhe_ntt_forward(ctx, dev_ptr: int, prime_idx, nlimbs: int):
     pi = np.ascontiguousarray(prime_idx, dtype=np.int32)
     _check(lib().fhe_ntt_forward(ctx, c_void_p(dev_ptr), _ptr(pi), nlimbs), ctx)
+
+
+def fhe_ntt_forward_batch(ctx, dev_ptr: int, count: int, nprimes: int):
+    _check(lib().fhe_ntt_forward_batch(ctx, c_void_p(dev_ptr), count, nprimes), ctx)
+
+
+def fhe_ntt_inverse_batch(ctx, dev_ptr: int, count: int, nprimes: int):
+    _check(lib().fhe_ntt_inverse_batch(ctx, c_void_p(dev_ptr), count, nprimes), ctx)
 
 
 def fhe_ntt_inverse(ctx, dev_ptr: int, prime_idx, nlimbs: int):
