@@ -253,6 +253,8 @@ def run_gpu(args):
                                  stream=stream.cuda_stream)
     info = fhe.fhe_ctx_info(ctx)
     ns, N, pairs = info.slots, info.N, W["pairs"]
+    variant, _ = fhe.fhe_ctx_ntt_variant(ctx)
+    split = {0: "2^7 x 2^7", 1: "2^8 x 2^6"}[variant]
     primes = fhe.fhe_ctx_primes(ctx)
     km = synth.KeyMaterial(W["seed"], primes, W["L"], W["K"], N)
     sk, pk = fhe.fhe_keygen_explicit(ctx, km.s, km.a_pk, km.e_pk)
@@ -357,7 +359,7 @@ def run_gpu(args):
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded BGV keys, noise and values)",
-        "config": dict(CONFIG, parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+        "config": dict(CONFIG, parallelism=f"replicas x{world}" if world > 1 else "single GPU", ntt_split=split,
                        batched_form="one CUDA graph per 16-pair batch (fhe_compare_plan)",
                        plain_form="one request at a time, op-by-op launches, no graph"),
         "plain": None if plain_value is None else {

@@ -888,7 +888,9 @@ int ntt_autotune(fhe_ctx *c, int njobs, float *ms_out)
         cudaEventElapsedTime(&ms, e0, e1);
         ms /= 5;
         if (ms_out) ms_out[v] = ms;
-        if (ms < best) best = ms, best_v = v;
+        // the first factorisation stays unless another is clearly faster
+        // (3%), so that near-ties do not flip from one context to the next
+        if (v == 0 || ms < 0.97f * best) best = ms, best_v = v;
     }
     c->ntt_variant = best_v;
     c->prof_on = prof;

@@ -303,7 +303,7 @@ def test_ntt_variants_and_autotuner():
     g = GpuSetup(seed=13, logN=13, p=17, L=6, K=2, **CHAIN50)
     try:
         v, ms = fhe.fhe_ctx_ntt_variant(g.ctx)
-        assert v in (0, 1) and ms[0] > 0 and ms[1] > 0 and ms[v] == min(ms)
+        assert v in (0, 1) and ms[0] > 0 and ms[1] > 0 and (v == 0 or ms[1] < 0.97 * ms[0])
         assert fhe.fhe_ctx_autotune(g.ctx, 64) in (0, 1)
         rnd = random.Random(4)
         xs = [[rnd.randrange(9) for _ in range(g.ns)] for _ in range(16)]
