@@ -419,13 +419,18 @@ int fhe_mod_switch_noalloc(fhe_ctx *ctx, const uint64_t *in, uint64_t *out, int 
 
 /* ---- NTT autotuning ------------------------------------------------------------ */
 
-/* The NTT runs as a column pass and a row pass over N = 2^n1 x 2^n2; each ring
- * degree has two factorisations (variant 0: n1 = ceil(n/2), variant 1 the
- * other one within the supported tile sizes).  fhe_ctx_create times both on
- * a representative batch and keeps the faster; fhe_ctx_autotune(ctx, njobs)
- * re-times them on njobs limbs.  Both return the chosen variant.
- * fhe_ctx_ntt_variant(ctx, set, ms): set >= 0 forces a variant (set < 0 only
- * reads); ms[2] (may be NULL) receives the last timings in milliseconds.
+/* The NTT splits N = 2^n1 x 2^n2 into a column pass and a row pass.  Variant
+ * 0 runs them as two kernels with n1 = ceil(n/2), variant 1 as two kernels
+ * with the other split (n = 11..15), variant 2 as one kernel in which a
+ * thread-block cluster holds each limb and exchanges the half-transformed
+ * limb through distributed shared memory (square splits: n = 10, 12, 14).
+ * fhe_ctx_create times the variants on a representative batch and keeps
+ * variant 0 unless another is at least 3% faster; fhe_ctx_autotune(ctx,
+ * njobs) re-times them on njobs limbs.  Both return the chosen variant.
+ * fhe_ctx_ntt_variant(ctx, set, ms): set >= 0 forces a variant (FHE_EINVAL if
+ * it does not exist for this N; set < 0 only reads); ms[3] (may be NULL)
+ * receives the last timings in milliseconds (0 for variants that do not
+ * exist).  All variants give identical results.
  * njobs counts limb transforms: polynomials of min(L+K, 10) limbs, rounded
  * to a multiple of 16 polynomials once there are 16 or more. */
 int fhe_ctx_autotune(fhe_ctx *ctx, int njobs);

@@ -1367,10 +1367,11 @@ extern "C" int fhe_ctx_ntt_variant(fhe_ctx *c, int set, float *ms)
     CHECK_CTX(c);
     LOCK(c);
     if (set >= 0) {
-        if (set >= ntt_variants(c->logN)) return FHE_EINVAL;
+        if (!ntt_variant_ok(c->logN, set)) return FHE_EINVAL;
         c->ntt_variant = set;
     }
-    if (ms) ms[0] = c->ntt_ms[0], ms[1] = c->ntt_ms[1];
+    if (ms)
+        for (int v = 0; v < FHE_NTT_VARIANTS; v++) ms[v] = c->ntt_ms[v];
     return c->ntt_variant;
 }
 

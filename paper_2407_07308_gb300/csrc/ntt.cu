@@ -32,7 +32,11 @@
 // computed while loading, subtract-and-scale applied while storing).  The
 // half-transformed limb between the two kernels lives in the job's output
 // limb.
+#include <cooperative_groups.h>
+
 #include "fhe_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -673,6 +677,115 @@ struct IOModSwitch {
     int prime_stride() const { return l - 1; }  // job = (ct, poly) * (l-1) + limb
 };
 
+// ---------------------------------------------------------------------------
+// one-launch NTT for square splits N = 2^M x 2^M (M = 5, 6, 7)
+// ---------------------------------------------------------------------------
+//
+// A cluster of CL = 2^M / 16 CTAs holds one limb.  Forward: CTA k transforms
+// columns 16k .. 16k+15 (global stages 0..M-1), writes each element (row e,
+// column 16k + c) into the shared memory of CTA e / 16 (distributed shared
+// memory), and after one cluster barrier transforms rows 16k .. 16k+15
+// (stages M..2M-1).  Inverse: rows first, then columns.  The half-transformed
+// limb never leaves the cluster, and the transform is one launch.  Every CTA
+// runs the same two barriers (no early exit), and no CTA touches another's
+// shared memory after the second one.
+
+__device__ __forceinline__ void cluster_arrive_relaxed()
+{
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
+
+template <int M, class IO>
+__global__ void __cluster_dims__((1 << M) / 16, 1, 1) __launch_bounds__(Sub<M>::T, FHE_MINB(Sub<M>::T))
+    k_fwd_fused(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
+{
+    using C = Sub<M>;
+    constexpr int CL = (1 << M) / 16, NN = 1 << (2 * M);
+    __shared__ u64 sm[C::WORDS];   // columns 16k .. 16k+15, all rows
+    __shared__ u64 sm2[C::WORDS];  // rows 16k .. 16k+15, all columns (written by the cluster)
+    __shared__ ulonglong2 W[twp_size(1 << M)];
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster_arrive_relaxed();  // matched by cluster_wait before the first remote write
+    const int k = (int)cluster.block_rank();
+    const int job = blockIdx.x / CL, lo0 = 16 * k, hi0 = 16 * k, tid = threadIdx.x;
+    const typename IO::St st = io.begin(job, NN);
+    const u64 q = mq[st.prime].q, q2 = 2 * q;
+    for (int r = tid; r < (1 << M); r += C::T) W[twp(r)] = tw[(size_t)st.prime * NN + r];
+    tile_in<M, IO::LDCH>(
+        tid, [&](int r) { return io.load(st, ((r >> 4) << M) + lo0 + (r & 15)); },
+        [&](int r, u64 v) { sm[C::at(r & 15, r >> 4)] = v; });
+    __syncthreads();
+    sub16<M, true>(sm, tid, PrefixTw{W}, 0, 0, 0, q, q2);
+    __syncthreads();
+    cluster_wait();
+    for (int r = tid; r < 16 * C::SZ; r += C::T) {
+        const int c = r & 15, e = r >> 4;
+        u64 *dst = cluster.map_shared_rank(sm2, e >> 4);
+        dst[C::at(e & 15, lo0 + c)] = sm[C::at(c, e)];
+    }
+    cluster.sync();
+    sub16<M, true>(sm2, tid, GTw{tw + (size_t)st.prime * NN}, M, hi0, 1, q, q2);
+    __syncthreads();
+    const ModQ mqp = mq[st.prime];
+    tile_out<M>(
+        io, tid, [&](int) -> const typename IO::St & { return st; }, [&](int r) { return (hi0 << M) + r; },
+        [&](int r) { return reduce64(sm2[C::at(r >> M, r & (C::SZ - 1))], mqp); });
+}
+
+template <int M, class IO>
+__global__ void __cluster_dims__((1 << M) / 16, 1, 1) __launch_bounds__(Sub<M>::T, FHE_MINB(Sub<M>::T))
+    k_inv_fused(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw,
+                const ulonglong2 *__restrict__ ninv)
+{
+    using C = Sub<M>;
+    constexpr int CL = (1 << M) / 16, NN = 1 << (2 * M);
+    __shared__ u64 sm[C::WORDS];   // rows 16k .. 16k+15
+    __shared__ u64 sm2[C::WORDS];  // columns 16k .. 16k+15 (written by the cluster)
+    __shared__ ulonglong2 W[twp_size(1 << M)];
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster_arrive_relaxed();
+    const int k = (int)cluster.block_rank();
+    const int job = blockIdx.x / CL, lo0 = 16 * k, hi0 = 16 * k, tid = threadIdx.x;
+    const typename IO::St st = io.begin(job, NN);
+    const u64 q = mq[st.prime].q, q2 = 2 * q;
+    for (int r = tid; r < (1 << M); r += C::T) W[twp(r)] = tw[(size_t)st.prime * NN + r];
+    const ulonglong2 ni = io.final_scale(st, ninv);
+    tile_in<M>(
+        tid, [&](int r) { return io.load(st, (hi0 << M) + r); },
+        [&](int r, u64 v) { sm[C::at(r >> M, r & (C::SZ - 1))] = v; });
+    __syncthreads();
+    sub16<M, false>(sm, tid, GTw{tw + (size_t)st.prime * NN}, M, hi0, 1, q, q2);
+    __syncthreads();
+    cluster_wait();
+    // element (row hi0 + rl, column f) goes to CTA f / 16 as its column f % 16
+    for (int r = tid; r < 16 * C::SZ; r += C::T) {
+        const int rl = r & 15, f = r >> 4;
+        u64 *dst = cluster.map_shared_rank(sm2, f >> 4);
+        dst[C::at(f & 15, hi0 + rl)] = sm[C::at(rl, f)];
+    }
+    cluster.sync();
+    sub16<M, false>(sm2, tid, PrefixTw{W}, 0, 0, 0, q, q2);
+    __syncthreads();
+    for (int r = tid; r < 16 * C::SZ; r += C::T) {
+        const int c = r & 15, e = r >> 4;
+        io.store(st, (e << M) + lo0 + c, reduce2q(shoup_lazy(sm2[C::at(c, e)], ni.x, ni.y, q), q));
+    }
+}
+
+template <int M, class IO>
+void fwd_fused(fhe_ctx *c, const IO &io, int njobs)
+{
+    k_fwd_fused<M, IO><<<njobs * ((1 << M) / 16), Sub<M>::T, 0, c->stream>>>(io, c->d_mq, c->d_fwd);
+}
+
+template <int M, class IO>
+void inv_fused(fhe_ctx *c, const IO &io, int njobs)
+{
+    k_inv_fused<M, IO><<<njobs * ((1 << M) / 16), Sub<M>::T, 0, c->stream>>>(io, c->d_mq, c->d_inv, c->d_ninv);
+}
+
 // Row kernels take the grouped form when every prime of the launch has a
 // multiple of 16 jobs (the batched case); otherwise 16 rows of one limb.
 template <class IO>
@@ -705,35 +818,43 @@ void inv_pair(fhe_ctx *c, const IO &io, int njobs)
                                                                                     c->d_ninv);
 }
 
-// Two factorisations N = 2^n1 x 2^n2 per ring degree (the autotuner picks
-// one per context; both compute the same transform).
+// Factorisations N = 2^n1 x 2^n2 per ring degree (the autotuner picks one
+// per context; all compute the same transform): variant 0 and 1 are the two
+// two-kernel splits, variant 2 the one-launch cluster form of a square split.
+// Returns the number of kernels launched.
 template <class IO>
-void fwd_dispatch(fhe_ctx *c, const IO &io, int njobs)
+int fwd_dispatch(fhe_ctx *c, const IO &io, int njobs)
 {
     const int v = c->ntt_variant;
     switch (c->logN) {
-    case 10: fwd_pair<5, 5>(c, io, njobs); break;
-    case 11: v ? fwd_pair<5, 6>(c, io, njobs) : fwd_pair<6, 5>(c, io, njobs); break;
-    case 12: v ? fwd_pair<7, 5>(c, io, njobs) : fwd_pair<6, 6>(c, io, njobs); break;
-    case 13: v ? fwd_pair<6, 7>(c, io, njobs) : fwd_pair<7, 6>(c, io, njobs); break;
-    case 14: v ? fwd_pair<8, 6>(c, io, njobs) : fwd_pair<7, 7>(c, io, njobs); break;
-    case 15: v ? fwd_pair<7, 8>(c, io, njobs) : fwd_pair<8, 7>(c, io, njobs); break;
-    default: break;
+    case 10: if (v == 2) return fwd_fused<5>(c, io, njobs), 1;
+        fwd_pair<5, 5>(c, io, njobs); return 2;
+    case 11: v ? fwd_pair<5, 6>(c, io, njobs) : fwd_pair<6, 5>(c, io, njobs); return 2;
+    case 12: if (v == 2) return fwd_fused<6>(c, io, njobs), 1;
+        v ? fwd_pair<7, 5>(c, io, njobs) : fwd_pair<6, 6>(c, io, njobs); return 2;
+    case 13: v ? fwd_pair<6, 7>(c, io, njobs) : fwd_pair<7, 6>(c, io, njobs); return 2;
+    case 14: if (v == 2) return fwd_fused<7>(c, io, njobs), 1;
+        v ? fwd_pair<8, 6>(c, io, njobs) : fwd_pair<7, 7>(c, io, njobs); return 2;
+    case 15: v ? fwd_pair<7, 8>(c, io, njobs) : fwd_pair<8, 7>(c, io, njobs); return 2;
+    default: return 0;
     }
 }
 
 template <class IO>
-void inv_dispatch(fhe_ctx *c, const IO &io, int njobs)
+int inv_dispatch(fhe_ctx *c, const IO &io, int njobs)
 {
     const int v = c->ntt_variant;
     switch (c->logN) {
-    case 10: inv_pair<5, 5>(c, io, njobs); break;
-    case 11: v ? inv_pair<5, 6>(c, io, njobs) : inv_pair<6, 5>(c, io, njobs); break;
-    case 12: v ? inv_pair<7, 5>(c, io, njobs) : inv_pair<6, 6>(c, io, njobs); break;
-    case 13: v ? inv_pair<6, 7>(c, io, njobs) : inv_pair<7, 6>(c, io, njobs); break;
-    case 14: v ? inv_pair<8, 6>(c, io, njobs) : inv_pair<7, 7>(c, io, njobs); break;
-    case 15: v ? inv_pair<7, 8>(c, io, njobs) : inv_pair<8, 7>(c, io, njobs); break;
-    default: break;
+    case 10: if (v == 2) return inv_fused<5>(c, io, njobs), 1;
+        inv_pair<5, 5>(c, io, njobs); return 2;
+    case 11: v ? inv_pair<5, 6>(c, io, njobs) : inv_pair<6, 5>(c, io, njobs); return 2;
+    case 12: if (v == 2) return inv_fused<6>(c, io, njobs), 1;
+        v ? inv_pair<7, 5>(c, io, njobs) : inv_pair<6, 6>(c, io, njobs); return 2;
+    case 13: v ? inv_pair<6, 7>(c, io, njobs) : inv_pair<7, 6>(c, io, njobs); return 2;
+    case 14: if (v == 2) return inv_fused<7>(c, io, njobs), 1;
+        v ? inv_pair<8, 6>(c, io, njobs) : inv_pair<7, 7>(c, io, njobs); return 2;
+    case 15: v ? inv_pair<7, 8>(c, io, njobs) : inv_pair<8, 7>(c, io, njobs); return 2;
+    default: return 0;
     }
 }
 
@@ -744,9 +865,8 @@ void run_fwd(fhe_ctx *c, const IO &io, int njobs, int cls, double words_per_job 
 {
     if (njobs <= 0) return;
     prof_begin(c, cls, 8.0 * words_per_job * c->N * njobs, (double)njobs * (c->N / 2) * c->logN);
-    fwd_dispatch(c, io, njobs);
+    c->launches += fwd_dispatch(c, io, njobs);
     prof_end(c);
-    c->launches += 2;
 }
 
 template <class IO>
@@ -754,9 +874,8 @@ void run_inv(fhe_ctx *c, const IO &io, int njobs, int cls, double words_per_job 
 {
     if (njobs <= 0) return;
     prof_begin(c, cls, 8.0 * words_per_job * c->N * njobs, (double)njobs * (c->N / 2) * c->logN);
-    inv_dispatch(c, io, njobs);
+    c->launches += inv_dispatch(c, io, njobs);
     prof_end(c);
-    c->launches += 2;
 }
 
 }  // namespace
@@ -842,14 +961,19 @@ void launch_ntt_modswitch(fhe_ctx *c, const u64 *last, const u64 *in, u64 *out, 
 // autotuner: times both factorisations on a representative batch
 // ---------------------------------------------------------------------------
 
-int ntt_variants(int logN) { return logN >= 11 && logN <= 15 ? 2 : 1; }
+bool ntt_variant_ok(int logN, int v)
+{
+    if (v == 0) return true;
+    if (v == 1) return logN >= 11 && logN <= 15;
+    if (v == 2) return logN == 10 || logN == 12 || logN == 14;
+    return false;
+}
 
 // Times forward + inverse of `outer` x nl limbs (nl = min(primes, 10)),
 // `outer` rounded to a multiple of 16 when >= 16 so that the row kernels take
 // their grouped form as in batched use; keeps the faster variant.
 int ntt_autotune(fhe_ctx *c, int njobs, float *ms_out)
 {
-    const int nv = ntt_variants(c->logN);
     LimbMap m;
     memset(&m, 0, sizeof(m));
     m.nl = std::min(c->np, 10);
@@ -870,7 +994,9 @@ int ntt_autotune(fhe_ctx *c, int njobs, float *ms_out)
     c->prof_on = false;
     float best = 1e30f;
     int best_v = 0;
-    for (int v = 0; v < nv; v++) {
+    for (int v = 0; v < FHE_NTT_VARIANTS; v++) {
+        if (ms_out) ms_out[v] = 0;
+        if (!ntt_variant_ok(c->logN, v)) continue;
         c->ntt_variant = v;
         IOPlain io{buf, buf, m};
         for (int w = 0; w < 2; w++) {

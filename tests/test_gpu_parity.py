@@ -50,8 +50,8 @@ def _same(oracle_ct, gpu_export, idx=0):
 # NTT
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("logN,variant", [(10, 0), (11, 0), (11, 1), (12, 0), (12, 1), (13, 0), (13, 1),
-                                           (14, 0), (14, 1), (15, 0), (15, 1)])
+@pytest.mark.parametrize("logN,variant", [(10, 0), (10, 2), (11, 0), (11, 1), (12, 0), (12, 1), (12, 2), (13, 0),
+                                           (13, 1), (14, 0), (14, 1), (14, 2), (15, 0), (15, 1)])
 def test_ntt_forward_inverse_match_oracle(logN, variant):
     from oracle.bgv import Oracle
 
@@ -293,24 +293,26 @@ def test_batch_equals_singles():
         g.close()
 
 
-def test_ntt_variants_and_autotuner():
-    """Both NTT factorisations give the same bits through the whole compare
-    path (16 ciphertexts, so the grouped row kernels run), and the autotuner
-    picks one of them from positive timings."""
+@pytest.mark.parametrize("logN,variants", [(13, (0, 1)), (12, (0, 1, 2)), (14, (0, 2))])
+def test_ntt_variants_and_autotuner(logN, variants):
+    """Every NTT variant gives the same bits through the whole compare path
+    (16 ciphertexts, so the grouped row kernels run), and the autotuner
+    keeps variant 0 unless another is clearly faster."""
     fhe = _fhe()
     from tests.gpu_setup import GpuSetup
 
-    g = GpuSetup(seed=13, logN=13, p=17, L=6, K=2, **CHAIN50)
+    g = GpuSetup(seed=13, logN=logN, p=17, L=6, K=2, **CHAIN50)
     try:
         v, ms = fhe.fhe_ctx_ntt_variant(g.ctx)
-        assert v in (0, 1) and ms[0] > 0 and ms[1] > 0 and (v == 0 or ms[1] < 0.97 * ms[0])
-        assert fhe.fhe_ctx_autotune(g.ctx, 64) in (0, 1)
+        assert v in variants and all(ms[u] > 0 for u in variants)
+        assert v == 0 or ms[v] < 0.97 * ms[0]
+        assert fhe.fhe_ctx_autotune(g.ctx, 64) in variants
         rnd = random.Random(4)
         xs = [[rnd.randrange(9) for _ in range(g.ns)] for _ in range(16)]
         ys = [[x if rnd.random() < 0.3 else rnd.randrange(9) for x in row] for row in xs]
         xb, yb = g.encrypt_slots(xs, seed=1), g.encrypt_slots(ys, seed=2)
         out = []
-        for variant in (0, 1):
+        for variant in variants:
             fhe.fhe_ctx_ntt_variant(g.ctx, variant)
             lt, eq = fhe.fhe_compare(g.ctx, g.evk, [xb], [yb])
             g.own(lt)
@@ -319,9 +321,13 @@ def test_ntt_variants_and_autotuner():
             lt_dec = g.decrypt(lt)
             for c in range(16):
                 assert lt_dec[c].tolist() == [int(a < b) for a, b in zip(xs[c], ys[c])]
-        assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+        for o in out[1:]:
+            assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1], o[1])
         with pytest.raises(fhe.FheError):
-            fhe.fhe_ctx_ntt_variant(g.ctx, 2)
+            fhe.fhe_ctx_ntt_variant(g.ctx, 3)
+        if 2 not in variants:
+            with pytest.raises(fhe.FheError):
+                fhe.fhe_ctx_ntt_variant(g.ctx, 2)
     finally:
         g.close()
 
@@ -370,3 +376,28 @@ def test_compare_plan_graph_matches_direct_and_is_isolated():
             fhe.fhe_plan_destroy(plan)
     finally:
         g.close()
+
+
+def test_ntt_batch_entry_matches_per_limb_entry():
+    """fhe_ntt_forward_batch / fhe_ntt_inverse_batch over [count][nprimes][N]
+    give the per-limb transforms of fhe_ntt_forward / fhe_ntt_inverse."""
+    import torch
+
+    fhe = _fhe()
+    ctx = fhe.fhe_ctx_create(12, 17, 6, 2, CHAIN50["U"], CHAIN50["lo"], CHAIN50["hi"])
+    try:
+        primes = fhe.fhe_ctx_primes(ctx)
+        N, count, npr = 1 << 12, 5, 4
+        rng = np.random.default_rng(3)
+        host = np.stack([rng.integers(0, int(primes[i]), size=(count, N), dtype=np.uint64) for i in range(npr)], 1)
+        a = torch.from_numpy(host.view(np.int64).copy()).cuda()
+        b = a.clone()
+        fhe.fhe_ntt_forward_batch(ctx, a.data_ptr(), count, npr)
+        fhe.fhe_ntt_forward(ctx, b.data_ptr(), [i % npr for i in range(count * npr)], count * npr)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+        fhe.fhe_ntt_inverse_batch(ctx, a.data_ptr(), count, npr)
+        torch.cuda.synchronize()
+        assert np.array_equal(a.cpu().numpy().view(np.uint64), host)
+    finally:
+        fhe.fhe_ctx_destroy(ctx)
