@@ -107,6 +107,14 @@ int fhe_ctx_memory(const fhe_ctx *ctx, uint64_t *reserved, uint64_t *in_use);
 /* Largest in_use since the last reset; reset != 0 restarts it from the
  * current in_use. */
 int fhe_ctx_memory_peak(fhe_ctx *ctx, uint64_t *peak, int reset);
+/* Every ciphertext product is tensor -> relinearise -> switch down one prime
+ * (when above level 1).  With on != 0 (the default) the relinearisation's
+ * ModDown and the modulus switch are carried out as one: the two
+ * corrections are combined in the coefficient domain and go through one
+ * forward NTT per kept limb, and the switched limb is never transformed
+ * back.  The results are the same residues as with on = 0, which runs the
+ * two steps separately.  Needs K + 1 <= 8 (else the steps stay separate). */
+int fhe_ctx_fused_modswitch(fhe_ctx *ctx, int on);
 /* Waits for the context's stream and returns the pool's cached free blocks
  * to the allocator (blocks held by handles and plans stay). */
 int fhe_ctx_trim(fhe_ctx *ctx);

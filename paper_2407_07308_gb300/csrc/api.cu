@@ -372,6 +372,7 @@ extern "C" void fhe_ctx_destroy(fhe_ctx *c)
     cudaFree(c->d_modup);
     cudaFree(c->d_moddown);
     cudaFree(c->d_modswitch);
+    cudaFree(c->d_rms);
     for (auto &kv : c->d_perm) cudaFree(kv.second);
     for (cudaStream_t s : c->branch_streams) cudaStreamDestroy(s);
     for (cudaEvent_t ev : c->branch_events) cudaEventDestroy(ev);
@@ -430,6 +431,14 @@ extern "C" int fhe_ctx_memory_peak(fhe_ctx *c, uint64_t *peak, int reset)
     LOCK(c);
     if (peak) *peak = c->pool.peak;
     if (reset) c->pool.peak = c->pool.in_use;
+    return 0;
+}
+
+extern "C" int fhe_ctx_fused_modswitch(fhe_ctx *c, int on)
+{
+    CHECK_CTX(c);
+    LOCK(c);
+    c->separate_ms = !on;
     return 0;
 }
 

@@ -237,6 +237,49 @@ static int keyswitch(fhe_ctx *c, const u64 *xbase, long long x_outer, const u64 
     return 0;
 }
 
+// Key switching whose ModDown also drops the last prime (l -> l-1): the same
+// residues as keyswitch() followed by op_modswitch1, with one forward NTT
+// per kept limb instead of two and no inverse NTT of the switched output
+// (see RelinMSParams).  Needs K + 1 <= FHE_MAXK.
+static int keyswitch_ms(fhe_ctx *c, const u64 *xbase, long long x_outer, const u64 *abase, long long a_outer,
+                        long long a_poly, int amask, const KeySwitchKey &k, int count, int l, u64 *out)
+{
+    const int N = c->N, K = c->K, dnum = c->modup[l].dnum;
+    int err = 0;
+    Tmp xc(c, (size_t)count * l * N, &err);
+    Tmp ext(c, (size_t)count * dnum * (l + K) * N, &err);
+    Tmp acc(c, (size_t)count * 2 * (l + K) * N, &err);
+    Tmp src(c, (size_t)count * 2 * (K + 1) * N, &err);
+    if (err) return fhe_fail(c, err, "key switching: out of device memory");
+    LimbMap m1 = identity_map(l, x_outer, (long long)l * N, 0, 0, 0);
+    launch_ntt_inv_scaled(c, xbase, xc.p, m1, c->ks_xscale[l].data(), count * l);
+    launch_ntt_modup(c, xc.p, ext.p, l, count);
+    launch_ks_inner(c, ext.p, xbase, x_outer, k.d, acc.p, count, l);
+    // y = acc_{l-1} + P add_{l-1}
+    launch_rms_y(c, acc.p, abase, a_outer, a_poly, amask, count, l);
+    // t_k = INTT(acc_P,k) p^-1 (P/p_k)^-1 and Y' = INTT(y) (p P)^-1
+    LimbMap m4;
+    memset(&m4, 0, sizeof(m4));
+    m4.nl = K + 1;
+    m4.in_outer = (long long)(l + K) * N;
+    m4.out_outer = (long long)(K + 1) * N;
+    std::vector<ulonglong2> scale(K + 1);
+    for (int j = 0; j < K; j++) {
+        m4.in_limb[j] = l + j;
+        m4.out_limb[j] = j;
+        m4.prime[j] = c->L + j;
+        scale[j] = c->ks_pscale[j];
+    }
+    m4.in_limb[K] = l - 1;
+    m4.out_limb[K] = K;
+    m4.prime[K] = l - 1;
+    scale[K] = c->rms_yscale[l];
+    launch_ntt_inv_scaled(c, acc.p, src.p, m4, scale.data(), count * 2 * (K + 1));
+    launch_rms_fold(c, src.p, count, l);
+    launch_ntt_relin_ms(c, src.p, acc.p, abase, a_outer, a_poly, amask, out, l, count);
+    return 0;
+}
+
 int op_relin(fhe_ctx *c, const KeySwitchKey &k, const fhe_ct *d, fhe_ct **out)
 {
     if (d->npoly != 3) return fhe_fail(c, FHE_EINVAL, "relinearize needs a 3-poly ciphertext");
@@ -314,6 +357,20 @@ int op_mul_relin(fhe_ctx *c, const KeySwitchKey &rlk, const fhe_ct *a, const fhe
     fhe_ct *d = nullptr, *r = nullptr;
     int err = op_tensor(c, a, b, &d);
     if (err) return err;
+    if (d->level > 1 && c->K + 1 <= FHE_MAXK && !c->separate_ms) {
+        // relinearise and switch down one prime in one ModDown
+        const int l = d->level;
+        const long long LN = (long long)l * c->N;
+        r = ct_new(c, d->count, 2, l - 1, &err);
+        if (r) err = keyswitch_ms(c, d->d + 2 * LN, 3 * LN, d->d, 3 * LN, LN, 3, rlk, d->count, l, r->d);
+        fhe_ct_destroy(d);
+        if (err) {
+            fhe_ct_destroy(r);
+            return err;
+        }
+        *out = r;
+        return 0;
+    }
     err = op_relin(c, rlk, d, &r);
     fhe_ct_destroy(d);
     if (err) return err;

@@ -70,6 +70,21 @@ struct ModSwitchParams {
     u64 qinv[FHE_MAXP], qinv_s[FHE_MAXP];     // q_{l-1}^-1 mod q_i
 };
 
+// Relinearisation and the modulus switch that follows it, as one ModDown
+// (level l -> l-1; m = l-1 the dropped prime).  The special limbs t_k =
+// [acc_k p^-1 (P/p_k)^-1]_{p_k} and w = [x_m p^-1]_{q_m} of the relinearised
+// x (computed from y = acc_m + P add_m without forming x) give every kept
+// limb's combined correction sum_k t_k h[k][i] + w h[K][i] in the
+// coefficient domain; out_i = (acc_i P^-1 + add_i - NTT(correction)_i) q_m^-1.
+struct RelinMSParams {
+    int l, K;
+    u64 h[FHE_MAXK + 1][FHE_MAXP];          // h[k][i] = p p_k^-1 mod q_i, h[K][i] = p mod q_i
+    u64 pinv[FHE_MAXP], pinv_s[FHE_MAXP];    // P^-1 mod q_i
+    u64 qminv[FHE_MAXP], qminv_s[FHE_MAXP];  // q_m^-1 mod q_i
+    u64 pkinv[FHE_MAXK];                     // p_k^-1 mod q_m
+    u64 Pm, Pm_s;                            // P mod q_m
+};
+
 // ---------------------------------------------------------------------------
 // device memory pool
 // ---------------------------------------------------------------------------
@@ -120,6 +135,10 @@ struct fhe_ctx {
     std::vector<ModUpParams> modup;
     std::vector<ModDownParams> moddown;
     std::vector<ModSwitchParams> modswitch;
+    std::vector<RelinMSParams> rms;
+    RelinMSParams *d_rms = nullptr;
+    std::vector<ulonglong2> rms_yscale;  // per level: N^-1 (p P)^-1 mod q_{l-1}
+    bool separate_ms = false;            // products: relinearise, then switch (two ModDowns)
     ModUpParams *d_modup = nullptr;
     ModDownParams *d_moddown = nullptr;
     ModSwitchParams *d_modswitch = nullptr;
@@ -263,6 +282,11 @@ void launch_ntt_modup(fhe_ctx *c, const u64 *d2c, u64 *ext, int level, int count
 // addend for ModDown output poly pi of ct c: abase + c*a_outer + pi*a_poly when (amask>>pi)&1
 void launch_ntt_moddown(fhe_ctx *c, const u64 *accP, const u64 *acc, const u64 *abase, long long a_outer,
                         long long a_poly, int amask, u64 *out, int level, int count);
+void launch_ntt_relin_ms(fhe_ctx *c, const u64 *src, const u64 *acc, const u64 *abase, long long a_outer,
+                         long long a_poly, int amask, u64 *out, int level, int count);
+void launch_rms_y(fhe_ctx *c, u64 *acc, const u64 *abase, long long a_outer, long long a_poly, int amask, int count,
+                  int level);
+void launch_rms_fold(fhe_ctx *c, u64 *src, int count, int level);
 void launch_ntt_modswitch(fhe_ctx *c, const u64 *last, const u64 *in, u64 *out, int level, int npoly, int count);
 
 void launch_add(fhe_ctx *c, const u64 *a, const u64 *b, u64 *out, int outer, int level, int sub);

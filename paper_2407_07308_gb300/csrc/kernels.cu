@@ -139,6 +139,47 @@ __global__ void __launch_bounds__(256, 2)
     }
 }
 
+// Relinearisation fused with the modulus switch, step 1: limb m = l-1 of
+// accumulator pi of ct c becomes y = acc_m + (P mod q_m) add_m (NTT domain,
+// in place; acc_m is not needed afterwards).
+__global__ void k_rms_y(u64 *__restrict__ acc, const u64 *__restrict__ abase, long long a_outer, long long a_poly,
+                        int amask, long long total, int logN, int l, int K, const RelinMSParams *__restrict__ P,
+                        const ModQ *__restrict__ mq)
+{
+    const int N = 1 << logN, m = l - 1;
+    const u64 q = mq[m].q, Pm = P->Pm, Pms = P->Pm_s;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long cp = idx >> logN;  // (ct, poly)
+        const int n = (int)(idx & (N - 1)), pi = (int)(cp & 1);
+        const long long c = cp >> 1;
+        if (!((amask >> pi) & 1)) continue;
+        u64 *y = acc + (cp * (l + K) + m) * N + n;
+        const u64 a = abase[c * a_outer + pi * a_poly + (long long)m * N + n];
+        *y = addmod(*y, shoup(a, Pm, Pms, q), q);
+    }
+}
+
+// Step 2 (after the scaled inverse NTT of the special limbs and of y): in
+// src[c][pi] = (t_0 .. t_{K-1}, Y'), Y' = INTT(y) (p P)^-1, replace Y' by
+// w = Y' - sum_k t_k p_k^-1 mod q_m, i.e. [x_m p^-1]_{q_m} of the
+// relinearised x.
+__global__ void k_rms_fold(u64 *__restrict__ src, long long total, int logN, int l, int K,
+                           const RelinMSParams *__restrict__ P, const ModQ *__restrict__ mq)
+{
+    const int N = 1 << logN;
+    const ModQ mm = mq[l - 1];
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long cp = idx >> logN;
+        const int n = (int)(idx & (N - 1));
+        u64 *base = src + cp * (K + 1) * N + n;
+        u128 a = 0;
+        for (int k = 0; k < K; k++) a += (u128)base[(long long)k * N] * P->pkinv[k];
+        base[(long long)K * N] = submod(base[(long long)K * N], barrett128(a, mm), mm.q);
+    }
+}
+
 // out[o][i][k] = in[o][i][perm[k]]: sigma_g in the NTT domain.
 __global__ void k_automorphism(const u64 *__restrict__ in, u64 *__restrict__ out, long long total, int logN,
                                const int *__restrict__ perm)
@@ -328,6 +369,21 @@ void launch_ks_inner(fhe_ctx *c, const u64 *ext, const u64 *xbase, long long x_o
 void launch_automorphism(fhe_ctx *c, const u64 *in, u64 *out, int outer, int level, const int *perm)
 {
     LAUNCH_CLS(FHE_K_AUTOMORPHISM, k_automorphism, (long long)outer * level * c->N, in, out, (long long)outer * level * c->N, c->logN, perm);
+}
+
+void launch_rms_y(fhe_ctx *c, u64 *acc, const u64 *abase, long long a_outer, long long a_poly, int amask, int count,
+                  int level)
+{
+    const long long total = (long long)count * 2 * c->N;
+    LAUNCH_CLS_W(FHE_K_ELEMWISE, 3, k_rms_y, total, acc, abase, a_outer, a_poly, amask, total, c->logN, level, c->K,
+                 c->d_rms + level, c->d_mq);
+}
+
+void launch_rms_fold(fhe_ctx *c, u64 *src, int count, int level)
+{
+    const long long total = (long long)count * 2 * c->N;
+    LAUNCH_CLS_W(FHE_K_ELEMWISE, c->K + 2.0, k_rms_fold, total, src, total, c->logN, level, c->K, c->d_rms + level,
+                 c->d_mq);
 }
 
 void launch_mul_poly(fhe_ctx *c, const u64 *a, const u64 *b, u64 *out, int outer, int level, long long b_outer)

@@ -677,6 +677,80 @@ struct IOModSwitch {
     int prime_stride() const { return l - 1; }  // job = (ct, poly) * (l-1) + limb
 };
 
+// Relinearisation fused with the modulus switch that follows it (l -> l-1)
+// for poly pi of ct c, kept limb i < l-1:
+//   correction_i = sum_{k<K} t_k h[k][i] + w h[K][i] (coefficient domain),
+//   out_i = (acc_i P^-1 + add_i - NTT(correction)_i) q_{l-1}^-1,
+// where src holds t_0..t_{K-1} (the special limbs, already scaled) and w.
+struct IORelinMS {
+    const u64 *src;  // [count][2][K+1][N] coefficient domain
+    const u64 *acc;  // [count][2][l+K][N] NTT domain
+    const u64 *abase;
+    long long a_outer, a_poly;
+    int amask;
+    u64 *out;        // [count][2][l-1][N]
+    const RelinMSParams *P;
+    const ModQ *mq;
+    int l, K, stride;
+    struct St {
+        const u64 *w, *acc, *add;
+        u64 *out;
+        int prime;
+        ModQ mi;
+        u64 pinv, pinv_s, qminv, qminv_s;
+        u64 h[FHE_MAXK];
+    };
+    __device__ St begin(int job, int N) const
+    {
+        const int m = l - 1;
+        const int c = job / (2 * m), pi = (job / m) % 2, i = job % m;
+        St s;
+        s.w = src + ((long long)c * 2 + pi) * (K + 1) * N;
+        s.acc = acc + (((long long)c * 2 + pi) * (l + K) + i) * N;
+        s.add = ((amask >> pi) & 1) ? abase + c * a_outer + pi * a_poly + (long long)i * N : nullptr;
+        s.out = out + (((long long)c * 2 + pi) * m + i) * N;
+        s.prime = i;
+        s.mi = mq[i];
+        s.pinv = P->pinv[i];
+        s.pinv_s = P->pinv_s[i];
+        s.qminv = P->qminv[i];
+        s.qminv_s = P->qminv_s[i];
+#pragma unroll
+        for (int k = 0; k < FHE_MAXK; k++)
+            if (k <= K) s.h[k] = P->h[k][i];
+        return s;
+    }
+    // K + 1 <= FHE_MAXK products of canonical residues: below 2^(2b+3)
+    __device__ u64 load(const St &s, int n) const
+    {
+        u128 a = 0;
+#pragma unroll
+        for (int k = 0; k < FHE_MAXK; k++)
+            if (k <= K) a += (u128)s.w[(long long)k * stride + n] * s.h[k];
+        return barrett128(a, s.mi);
+    }
+    __device__ u64 combine(const St &s, u64 accv, u64 addv, u64 v) const
+    {
+        const u64 q = s.mi.q;
+        u64 t = shoup(accv, s.pinv, s.pinv_s, q);
+        if (s.add) t = addmod(t, addv, q);
+        return shoup(submod(t, v, q), s.qminv, s.qminv_s, q);
+    }
+    __device__ void store(const St &s, int k, u64 v) const
+    {
+        s.out[k] = combine(s, s.acc[k], s.add ? s.add[k] : 0, v);
+    }
+    static constexpr int NPRE = 2;  // accumulator, addend
+    static constexpr int LDCH = 0;  // each load sums K + 1 limbs
+    __device__ u64 pre(const St &s, int k, int w) const { return w == 0 ? s.acc[k] : (s.add ? s.add[k] : 0); }
+    __device__ void store_pre(const St &s, int k, u64 v, const u64 *pv) const
+    {
+        s.out[k] = combine(s, pv[0], pv[1], v);
+    }
+    __device__ u64 *inter(const St &s) const { return s.out; }
+    int prime_stride() const { return l - 1; }  // job = (ct, poly) * (l-1) + limb
+};
+
 // ---------------------------------------------------------------------------
 // one-launch NTT for square splits N = 2^M x 2^M (M = 5, 6, 7)
 // ---------------------------------------------------------------------------
@@ -942,6 +1016,27 @@ void launch_ntt_moddown(fhe_ctx *c, const u64 *accP, const u64 *acc, const u64 *
     // reads K special limbs, acc_i and (for masked polys) the addend; writes out_i
     const double add_frac = ((amask & 1) + ((amask >> 1) & 1)) / 2.0;
     run_fwd(c, io, 2 * level * count, FHE_K_NTT_MODDOWN, c->K + 2.0 + add_frac);
+}
+
+void launch_ntt_relin_ms(fhe_ctx *c, const u64 *src, const u64 *acc, const u64 *abase, long long a_outer,
+                         long long a_poly, int amask, u64 *out, int level, int count)
+{
+    IORelinMS io;
+    io.src = src;
+    io.acc = acc;
+    io.abase = abase;
+    io.a_outer = a_outer;
+    io.a_poly = a_poly;
+    io.amask = amask;
+    io.out = out;
+    io.P = c->d_rms + level;
+    io.mq = c->d_mq;
+    io.l = level;
+    io.K = c->K;
+    io.stride = c->N;
+    // reads K + 1 correction sources, acc_i and (for masked polys) the addend; writes out_i
+    const double add_frac = ((amask & 1) + ((amask >> 1) & 1)) / 2.0;
+    run_fwd(c, io, 2 * (level - 1) * count, FHE_K_NTT_MODDOWN, c->K + 3.0 + add_frac);
 }
 
 void launch_ntt_modswitch(fhe_ctx *c, const u64 *last, const u64 *in, u64 *out, int level, int npoly, int count)

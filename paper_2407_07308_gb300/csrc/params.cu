@@ -252,6 +252,33 @@ int build_tables(fhe_ctx *c)
             }
         }
     }
+    // relinearisation + modulus switch (level l -> l-1)
+    c->rms.assign(L + 1, RelinMSParams());
+    for (int l = 2; l <= L; l++) {
+        RelinMSParams &R = c->rms[l];
+        memset(&R, 0, sizeof(R));
+        R.l = l;
+        R.K = K;
+        const u64 qm = c->q[l - 1];
+        u64 Pm = 1;
+        for (int k = 0; k < K; k++) {
+            const u64 pk = c->q[L + k];
+            Pm = host_mulmod(Pm, pk % qm, qm);
+            R.pkinv[k] = host_invmod(pk % qm, qm);
+        }
+        R.Pm = Pm;
+        R.Pm_s = shoup_const(Pm, qm);
+        for (int i = 0; i < l - 1; i++) {
+            const u64 qi = c->q[i], pi = c->p % qi;
+            for (int k = 0; k < K; k++) R.h[k][i] = host_mulmod(pi, host_invmod(c->q[L + k] % qi, qi), qi);
+            R.h[K][i] = pi;
+            R.pinv[i] = c->moddown[l].pinv[i];
+            R.pinv_s[i] = c->moddown[l].pinv_s[i];
+            R.qminv[i] = c->modswitch[l].qinv[i];
+            R.qminv_s[i] = c->modswitch[l].qinv_s[i];
+        }
+    }
+    if ((e = upload(c, (void **)&c->d_rms, c->rms.data(), sizeof(RelinMSParams) * (L + 1)))) return e;
     if ((e = upload(c, (void **)&c->d_modup, c->modup.data(), sizeof(ModUpParams) * (L + 1)))) return e;
     if ((e = upload(c, (void **)&c->d_moddown, c->moddown.data(), sizeof(ModDownParams) * (L + 1)))) return e;
     if ((e = upload(c, (void **)&c->d_modswitch, c->modswitch.data(), sizeof(ModSwitchParams) * (L + 1))))
@@ -261,6 +288,7 @@ int build_tables(fhe_ctx *c)
     auto sc = [](u64 v, u64 q) { return make_ulonglong2(v, shoup_const(v, q)); };
     c->ks_xscale.assign(L + 1, std::vector<ulonglong2>());
     c->ms_lastscale.assign(L + 1, make_ulonglong2(0, 0));
+    c->rms_yscale.assign(L + 1, make_ulonglong2(0, 0));
     for (int l = 1; l <= L; l++) {
         const ModUpParams &U = c->modup[l];
         c->ks_xscale[l].resize(l);
@@ -273,6 +301,9 @@ int build_tables(fhe_ctx *c)
         if (l >= 2) {
             const u64 ql = c->q[l - 1];
             c->ms_lastscale[l] = sc(host_mulmod(ninv[l - 1].x, c->modswitch[l].pinv_last, ql), ql);
+            // (p P)^-1 = p^-1 P^-1 mod q_{l-1}
+            const u64 pP_inv = host_mulmod(c->modswitch[l].pinv_last, host_invmod(c->rms[l].Pm, ql), ql);
+            c->rms_yscale[l] = sc(host_mulmod(ninv[l - 1].x, pP_inv, ql), ql);
         }
     }
     c->ks_pscale.resize(K);

@@ -147,6 +147,7 @@ def lib() -> ctypes.CDLL:
             "fhe_job_footprint": (ctypes.c_uint64, [vp]),
             "fhe_ctx_inject_alloc_failure": (ci, [vp, ctypes.c_int64]),
             "fhe_ctx_trim": (ci, [vp]),
+            "fhe_ctx_fused_modswitch": (ci, [vp, ci]),
             "fhe_ctx_set_batch_graphs": (ci, [vp, ci]),
             "fhe_ctx_memory_peak": (ci, [vp, POINTER(ctypes.c_uint64), ci]),
             "fhe_server_start": (ci, [vp, POINTER(vp)]),
@@ -571,6 +572,10 @@ def fhe_batch_destroy(batch):
 
 def fhe_ctx_set_batch_graphs(ctx, max_plans: int):
     _check(lib().fhe_ctx_set_batch_graphs(ctx, int(max_plans)), ctx)
+
+
+def fhe_ctx_fused_modswitch(ctx, on: bool):
+    _check(lib().fhe_ctx_fused_modswitch(ctx, int(bool(on))), ctx)
 
 
 def fhe_ctx_trim(ctx):

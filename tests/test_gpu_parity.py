@@ -401,3 +401,37 @@ def test_ntt_batch_entry_matches_per_limb_entry():
         assert np.array_equal(a.cpu().numpy().view(np.uint64), host)
     finally:
         fhe.fhe_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("logN,p,L,K", [(12, 17, 6, 2), (13, 257, 9, 4), (14, 131, 10, 3)])
+def test_fused_relin_modswitch_equals_separate_steps(logN, p, L, K):
+    """Relinearise + modulus switch as one ModDown gives the residues of the
+    two separate steps: product by product (every level) and through a whole
+    comparison."""
+    fhe = _fhe()
+    from tests.gpu_setup import GpuSetup
+
+    g = GpuSetup(seed=21, logN=logN, p=p, L=L, K=K, **CHAIN50)
+    try:
+        rnd = random.Random(logN + p)
+        b = (p + 1) // 2
+        xs = [[rnd.randrange(b) for _ in range(g.ns)] for _ in range(3)]
+        ys = [[rnd.randrange(b) for _ in range(g.ns)] for _ in range(3)]
+        x, y = g.encrypt_slots(xs, seed=1), g.encrypt_slots(ys, seed=2)
+        for fused in (True, False):
+            fhe.fhe_ctx_fused_modswitch(g.ctx, fused)
+            a, res = x, []
+            for _ in range(L - 1):  # repeated products down to level 1
+                a = g.own(fhe.fhe_mul_relin(g.ctx, g.evk, a, y))
+                res.append(g.export(a))
+            lt, eq = fhe.fhe_compare(g.ctx, g.evk, [x], [y])
+            g.own(lt)
+            g.own(eq)
+            res += [g.export(lt), g.export(eq)]
+            if fused:
+                first = res
+        for u, v in zip(first, res):
+            assert np.array_equal(u, v)
+    finally:
+        fhe.fhe_ctx_fused_modswitch(g.ctx, True)
+        g.close()
