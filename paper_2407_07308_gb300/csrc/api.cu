@@ -373,6 +373,7 @@ extern "C" void fhe_ctx_destroy(fhe_ctx *c)
     cudaFree(c->d_moddown);
     cudaFree(c->d_modswitch);
     cudaFree(c->d_rms);
+    cudaFree(c->d_mss);
     for (auto &kv : c->d_perm) cudaFree(kv.second);
     for (cudaStream_t s : c->branch_streams) cudaStreamDestroy(s);
     for (cudaEvent_t ev : c->branch_events) cudaEventDestroy(ev);

@@ -91,6 +91,36 @@ int op_modswitch1(fhe_ctx *c, const fhe_ct *a, fhe_ct **out)
     return 0;
 }
 
+// k single switches at once (2 <= k <= FHE_MAXK, k < level); the same residues.
+int op_modswitch_k(fhe_ctx *c, const fhe_ct *a, int k, fhe_ct **out)
+{
+    const int l = a->level, N = c->N;
+    if (k == 1) return op_modswitch1(c, a, out);
+    if (k < 1 || k > FHE_MAXK || k >= l) return fhe_fail(c, FHE_ELEVEL, "modulus switch below level 1");
+    int err = 0;
+    fhe_ct *r = ct_new(c, a->count, a->npoly, l - k, &err);
+    if (!r) return err;
+    const int outer = a->count * a->npoly;
+    Tmp src(c, (size_t)outer * k * N, &err);
+    if (err) {
+        fhe_ct_destroy(r);
+        return err;
+    }
+    // X'_j = INTT(x_{l-1-j}) p^-1 D_j^-1 into src[o][j]
+    LimbMap m;
+    memset(&m, 0, sizeof(m));
+    m.nl = k;
+    m.in_outer = (long long)l * N;
+    m.out_outer = (long long)k * N;
+    for (int j = 0; j < k; j++) m.in_limb[j] = l - 1 - j, m.out_limb[j] = j, m.prime[j] = l - 1 - j;
+    launch_ntt_inv_scaled(c, a->d, src.p, m, &c->mss_scale[((size_t)l * (FHE_MAXK + 1) + k) * FHE_MAXK],
+                          outer * k);
+    launch_ms_fold(c, src.p, outer, l, k);
+    launch_ntt_multiswitch(c, src.p, a->d, r->d, l, k, a->npoly, a->count);
+    *out = r;
+    return 0;
+}
+
 int op_lower(fhe_ctx *c, const fhe_ct *a, int level, fhe_ct **out)
 {
     if (level < 1 || level > a->level) return fhe_fail(c, FHE_ELEVEL, "bad target level");
@@ -106,7 +136,7 @@ int op_lower(fhe_ctx *c, const fhe_ct *a, int level, fhe_ct **out)
     fhe_ct *owned = nullptr;
     while (cur->level > level) {
         fhe_ct *nx = nullptr;
-        int e = op_modswitch1(c, cur, &nx);
+        int e = op_modswitch_k(c, cur, std::min(cur->level - level, FHE_MAXK), &nx);
         if (owned) fhe_ct_destroy(owned);
         if (e) return e;
         owned = nx;
@@ -255,9 +285,8 @@ static int keyswitch_ms(fhe_ctx *c, const u64 *xbase, long long x_outer, const u
     launch_ntt_inv_scaled(c, xbase, xc.p, m1, c->ks_xscale[l].data(), count * l);
     launch_ntt_modup(c, xc.p, ext.p, l, count);
     launch_ks_inner(c, ext.p, xbase, x_outer, k.d, acc.p, count, l);
-    // y = acc_{l-1} + P add_{l-1}
-    launch_rms_y(c, acc.p, abase, a_outer, a_poly, amask, count, l);
-    // t_k = INTT(acc_P,k) p^-1 (P/p_k)^-1 and Y' = INTT(y) (p P)^-1
+    // t_k = INTT(acc_P,k) p^-1 (P/p_k)^-1 and Y' = INTT(y) (p P)^-1 with
+    // y = acc_{l-1} + P add_{l-1} formed while loading
     LimbMap m4;
     memset(&m4, 0, sizeof(m4));
     m4.nl = K + 1;
@@ -274,7 +303,8 @@ static int keyswitch_ms(fhe_ctx *c, const u64 *xbase, long long x_outer, const u
     m4.out_limb[K] = K;
     m4.prime[K] = l - 1;
     scale[K] = c->rms_yscale[l];
-    launch_ntt_inv_scaled(c, acc.p, src.p, m4, scale.data(), count * 2 * (K + 1));
+    launch_ntt_inv_scaled_y(c, acc.p, src.p, m4, scale.data(), count * 2 * (K + 1), abase, a_outer, a_poly, amask,
+                            l);
     launch_rms_fold(c, src.p, count, l);
     launch_ntt_relin_ms(c, src.p, acc.p, abase, a_outer, a_poly, amask, out, l, count);
     return 0;
@@ -538,6 +568,9 @@ struct Circuit {
             if (o == x) o = nullptr;
         return x;
     }
+    // x at `level`: from the nearest cached copy above it, all remaining
+    // primes dropped in one step (op_modswitch_k: the residues of dropping
+    // them one at a time)
     const fhe_ct *lower(const fhe_ct *x, int level)
     {
         if (err || !x) return nullptr;
@@ -545,11 +578,19 @@ struct Circuit {
         auto key = std::make_pair(x, level);
         auto it = lowered.find(key);
         if (it != lowered.end()) return it->second;
-        const fhe_ct *above = lower(x, level + 1);
-        if (!above) return nullptr;
+        const fhe_ct *from = x;
+        for (int lv = level + 1; lv < x->level; lv++) {
+            auto f = lowered.find(std::make_pair(x, lv));
+            if (f != lowered.end()) {
+                from = f->second;
+                break;
+            }
+        }
+        if (from->level - level > FHE_MAXK) from = lower(x, level + FHE_MAXK);
+        if (!from) return nullptr;
         fhe_ct *r = nullptr;
-        dag.begin({above});
-        if ((err = op_modswitch1(c, above, &r))) return nullptr;
+        dag.begin({from});
+        if ((err = op_modswitch_k(c, from, from->level - level, &r))) return nullptr;
         dag.end(r);
         lowered[key] = r;
         return r;

@@ -85,6 +85,19 @@ struct RelinMSParams {
     u64 Pm, Pm_s;                            // P mod q_m
 };
 
+// k modulus switches l -> l-k at once (2 <= k <= FHE_MAXK).  With D_t the
+// product of the t last primes q_{l-1} .. q_{l-t} (D_0 = 1), the switches'
+// values w_j = [x^(j)_{l-1-j} p^-1] follow from X'_j = INTT(x_{l-1-j}) p^-1
+// D_j^-1 by w_j = X'_j - sum_{t<j} w_t F[j][t] (mod q_{l-1-j}), and
+// out_i = (x_i - NTT(sum_t w_t G[t][i])_i) D_k^-1: the residues of k single
+// switches.
+struct MultiSwitchParams {
+    int l, k;
+    u64 G[FHE_MAXK][FHE_MAXP];           // p D_t mod q_i
+    u64 Dinv[FHE_MAXP], Dinv_s[FHE_MAXP];  // D_k^-1 mod q_i
+    u64 F[FHE_MAXK][FHE_MAXK];           // D_t D_j^-1 mod q_{l-1-j}
+};
+
 // ---------------------------------------------------------------------------
 // device memory pool
 // ---------------------------------------------------------------------------
@@ -139,6 +152,9 @@ struct fhe_ctx {
     RelinMSParams *d_rms = nullptr;
     std::vector<ulonglong2> rms_yscale;  // per level: N^-1 (p P)^-1 mod q_{l-1}
     bool separate_ms = false;            // products: relinearise, then switch (two ModDowns)
+    std::vector<MultiSwitchParams> mss;  // [l * (FHE_MAXK + 1) + k]
+    MultiSwitchParams *d_mss = nullptr;
+    std::vector<ulonglong2> mss_scale;   // [(l * (FHE_MAXK + 1) + k) * FHE_MAXK + j]: N^-1 p^-1 D_j^-1
     ModUpParams *d_modup = nullptr;
     ModDownParams *d_moddown = nullptr;
     ModSwitchParams *d_modswitch = nullptr;
@@ -284,9 +300,13 @@ void launch_ntt_moddown(fhe_ctx *c, const u64 *accP, const u64 *acc, const u64 *
                         long long a_poly, int amask, u64 *out, int level, int count);
 void launch_ntt_relin_ms(fhe_ctx *c, const u64 *src, const u64 *acc, const u64 *abase, long long a_outer,
                          long long a_poly, int amask, u64 *out, int level, int count);
-void launch_rms_y(fhe_ctx *c, u64 *acc, const u64 *abase, long long a_outer, long long a_poly, int amask, int count,
-                  int level);
+void launch_ntt_inv_scaled_y(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, const ulonglong2 *scale,
+                             int njobs, const u64 *abase, long long a_outer, long long a_poly, int amask, int level);
 void launch_rms_fold(fhe_ctx *c, u64 *src, int count, int level);
+void launch_ntt_multiswitch(fhe_ctx *c, const u64 *src, const u64 *in, u64 *out, int level, int k, int npoly,
+                            int count);
+void launch_ms_fold(fhe_ctx *c, u64 *src, int outer, int level, int k);
+int op_modswitch_k(fhe_ctx *c, const fhe_ct *a, int k, fhe_ct **out);
 void launch_ntt_modswitch(fhe_ctx *c, const u64 *last, const u64 *in, u64 *out, int level, int npoly, int count);
 
 void launch_add(fhe_ctx *c, const u64 *a, const u64 *b, u64 *out, int outer, int level, int sub);

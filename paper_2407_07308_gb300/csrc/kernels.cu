@@ -139,28 +139,9 @@ __global__ void __launch_bounds__(256, 2)
     }
 }
 
-// Relinearisation fused with the modulus switch, step 1: limb m = l-1 of
-// accumulator pi of ct c becomes y = acc_m + (P mod q_m) add_m (NTT domain,
-// in place; acc_m is not needed afterwards).
-__global__ void k_rms_y(u64 *__restrict__ acc, const u64 *__restrict__ abase, long long a_outer, long long a_poly,
-                        int amask, long long total, int logN, int l, int K, const RelinMSParams *__restrict__ P,
-                        const ModQ *__restrict__ mq)
-{
-    const int N = 1 << logN, m = l - 1;
-    const u64 q = mq[m].q, Pm = P->Pm, Pms = P->Pm_s;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long cp = idx >> logN;  // (ct, poly)
-        const int n = (int)(idx & (N - 1)), pi = (int)(cp & 1);
-        const long long c = cp >> 1;
-        if (!((amask >> pi) & 1)) continue;
-        u64 *y = acc + (cp * (l + K) + m) * N + n;
-        const u64 a = abase[c * a_outer + pi * a_poly + (long long)m * N + n];
-        *y = addmod(*y, shoup(a, Pm, Pms, q), q);
-    }
-}
-
-// Step 2 (after the scaled inverse NTT of the special limbs and of y): in
+// Relinearisation fused with the modulus switch (the inverse NTT that
+// precedes this step formed y = acc_m + (P mod q_m) add_m while loading):
+// after the scaled inverse NTT of the special limbs and of y, in
 // src[c][pi] = (t_0 .. t_{K-1}, Y'), Y' = INTT(y) (p P)^-1, replace Y' by
 // w = Y' - sum_k t_k p_k^-1 mod q_m, i.e. [x_m p^-1]_{q_m} of the
 // relinearised x.
@@ -177,6 +158,33 @@ __global__ void k_rms_fold(u64 *__restrict__ src, long long total, int logN, int
         u128 a = 0;
         for (int k = 0; k < K; k++) a += (u128)base[(long long)k * N] * P->pkinv[k];
         base[(long long)K * N] = submod(base[(long long)K * N], barrett128(a, mm), mm.q);
+    }
+}
+
+// k modulus switches at once: src[o] = (X'_0 .. X'_{k-1}) becomes
+// (w_0 .. w_{k-1}), w_j = X'_j - sum_{t<j} w_t F[j][t] mod q_{l-1-j}.
+__global__ void k_ms_fold(u64 *__restrict__ src, long long total, int logN, int l, int k,
+                          const MultiSwitchParams *__restrict__ P, const ModQ *__restrict__ mq)
+{
+    const int N = 1 << logN;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long o = idx >> logN;
+        const int n = (int)(idx & (N - 1));
+        u64 *base = src + o * k * N + n;
+        u64 w[FHE_MAXK];
+#pragma unroll
+        for (int j = 0; j < FHE_MAXK; j++) {
+            if (j < k) {
+                const ModQ mj = mq[l - 1 - j];
+                u128 a = 0;
+#pragma unroll
+                for (int t = 0; t < FHE_MAXK; t++)
+                    if (t < j) a += (u128)w[t] * P->F[j][t];
+                w[j] = submod(base[(long long)j * N], barrett128(a, mj), mj.q);
+                base[(long long)j * N] = w[j];
+            }
+        }
     }
 }
 
@@ -371,12 +379,11 @@ void launch_automorphism(fhe_ctx *c, const u64 *in, u64 *out, int outer, int lev
     LAUNCH_CLS(FHE_K_AUTOMORPHISM, k_automorphism, (long long)outer * level * c->N, in, out, (long long)outer * level * c->N, c->logN, perm);
 }
 
-void launch_rms_y(fhe_ctx *c, u64 *acc, const u64 *abase, long long a_outer, long long a_poly, int amask, int count,
-                  int level)
+void launch_ms_fold(fhe_ctx *c, u64 *src, int outer, int level, int k)
 {
-    const long long total = (long long)count * 2 * c->N;
-    LAUNCH_CLS_W(FHE_K_ELEMWISE, 3, k_rms_y, total, acc, abase, a_outer, a_poly, amask, total, c->logN, level, c->K,
-                 c->d_rms + level, c->d_mq);
+    const long long total = (long long)outer * c->N;
+    LAUNCH_CLS_W(FHE_K_ELEMWISE, 2.0 * k, k_ms_fold, total, src, total, c->logN, level, k,
+                 c->d_mss + (size_t)level * (FHE_MAXK + 1) + k, c->d_mq);
 }
 
 void launch_rms_fold(fhe_ctx *c, u64 *src, int count, int level)

@@ -508,6 +508,33 @@ struct IOScaled {
     int prime_stride() const { return m.nl; }
 };
 
+// IOScaled whose last map entry (limb l-1 of the relinearisation
+// accumulators) loads y = acc + (P mod q) addend: the first step of the
+// relinearisation fused with the modulus switch.  Job = (ct, poly) * nl + entry.
+struct IOScaledY : IOScaled {
+    const u64 *abase;
+    long long a_outer, a_poly;
+    int amask, alimb;
+    u64 Pm, Pm_s, qm;
+    struct St : IOScaled::St {
+        const u64 *add;
+    };
+    __device__ St begin(int job, int N) const
+    {
+        St s;
+        static_cast<IOScaled::St &>(s) = IOScaled::begin(job, N);
+        const int o = job / m.nl, e = job % m.nl, pi = o & 1;
+        const long long c = o >> 1;
+        s.add = (e == m.nl - 1 && ((amask >> pi) & 1)) ? abase + c * a_outer + pi * a_poly + (long long)alimb * N
+                                                      : nullptr;
+        return s;
+    }
+    __device__ u64 load(const St &s, int i) const
+    {
+        return s.add ? addmod(s.in[i], shoup(s.add[i], Pm, Pm_s, qm), qm) : s.in[i];
+    }
+};
+
 // ModUp: extended limb t of digit j of ct c:  y = sum_a t_a (Q_j/q_a) mod r,
 // where the source limbs already hold t_a = [x_a (Q_j/q_a)^-1]_{q_a} (the
 // inverse NTT that produced them applied that factor).
@@ -751,6 +778,63 @@ struct IORelinMS {
     int prime_stride() const { return l - 1; }  // job = (ct, poly) * (l-1) + limb
 };
 
+// k modulus switches at once (l -> l-k), poly pi of ct c, kept limb i < l-k:
+//   correction_i = sum_{t<k} w_t G[t][i],  out_i = (x_i - NTT(correction)_i) D_k^-1.
+struct IOMultiSwitch {
+    const u64 *src;  // [count][npoly][k][N] coefficient domain: w_0 .. w_{k-1}
+    const u64 *in;   // [count][npoly][l][N]
+    u64 *out;        // [count][npoly][l-k][N]
+    const MultiSwitchParams *P;
+    const ModQ *mq;
+    int l, k, npoly, stride;
+    struct St {
+        const u64 *w, *in;
+        u64 *out;
+        int prime;
+        ModQ mi;
+        u64 dinv, dinv_s;
+        u64 g[FHE_MAXK];
+    };
+    __device__ St begin(int job, int N) const
+    {
+        const int kept = l - k;
+        const int c = job / (npoly * kept), pi = (job / kept) % npoly, i = job % kept;
+        St s;
+        s.w = src + ((long long)c * npoly + pi) * k * N;
+        s.in = in + (((long long)c * npoly + pi) * l + i) * N;
+        s.out = out + (((long long)c * npoly + pi) * kept + i) * N;
+        s.prime = i;
+        s.mi = mq[i];
+        s.dinv = P->Dinv[i];
+        s.dinv_s = P->Dinv_s[i];
+#pragma unroll
+        for (int t = 0; t < FHE_MAXK; t++)
+            if (t < k) s.g[t] = P->G[t][i];
+        return s;
+    }
+    __device__ u64 load(const St &s, int n) const
+    {
+        u128 a = 0;
+#pragma unroll
+        for (int t = 0; t < FHE_MAXK; t++)
+            if (t < k) a += (u128)s.w[(long long)t * stride + n] * s.g[t];
+        return barrett128(a, s.mi);
+    }
+    __device__ void store(const St &s, int j, u64 v) const
+    {
+        s.out[j] = shoup(submod(s.in[j], v, s.mi.q), s.dinv, s.dinv_s, s.mi.q);
+    }
+    static constexpr int NPRE = 1;
+    static constexpr int LDCH = 0;
+    __device__ u64 pre(const St &s, int j, int) const { return s.in[j]; }
+    __device__ void store_pre(const St &s, int j, u64 v, const u64 *pv) const
+    {
+        s.out[j] = shoup(submod(pv[0], v, s.mi.q), s.dinv, s.dinv_s, s.mi.q);
+    }
+    __device__ u64 *inter(const St &s) const { return s.out; }
+    int prime_stride() const { return l - k; }
+};
+
 // ---------------------------------------------------------------------------
 // one-launch NTT for square splits N = 2^M x 2^M (M = 5, 6, 7)
 // ---------------------------------------------------------------------------
@@ -979,6 +1063,25 @@ void launch_ntt_inv_scaled(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m
     run_inv(c, io, njobs, FHE_K_NTT_INV);
 }
 
+void launch_ntt_inv_scaled_y(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, const ulonglong2 *scale,
+                             int njobs, const u64 *abase, long long a_outer, long long a_poly, int amask, int level)
+{
+    IOScaledY io;
+    io.in = in;
+    io.out = out;
+    io.m = m;
+    for (int i = 0; i < m.nl; i++) io.scale[i] = scale[i];
+    io.abase = abase;
+    io.a_outer = a_outer;
+    io.a_poly = a_poly;
+    io.amask = amask;
+    io.alimb = level - 1;
+    io.qm = c->q[level - 1];
+    io.Pm = c->rms[level].Pm;
+    io.Pm_s = c->rms[level].Pm_s;
+    run_inv(c, io, njobs, FHE_K_NTT_INV);
+}
+
 void launch_ntt_modup(fhe_ctx *c, const u64 *d2c, u64 *ext, int level, int count)
 {
     const ModUpParams &P = c->modup[level];
@@ -1037,6 +1140,23 @@ void launch_ntt_relin_ms(fhe_ctx *c, const u64 *src, const u64 *acc, const u64 *
     // reads K + 1 correction sources, acc_i and (for masked polys) the addend; writes out_i
     const double add_frac = ((amask & 1) + ((amask >> 1) & 1)) / 2.0;
     run_fwd(c, io, 2 * (level - 1) * count, FHE_K_NTT_MODDOWN, c->K + 3.0 + add_frac);
+}
+
+void launch_ntt_multiswitch(fhe_ctx *c, const u64 *src, const u64 *in, u64 *out, int level, int k, int npoly,
+                            int count)
+{
+    IOMultiSwitch io;
+    io.src = src;
+    io.in = in;
+    io.out = out;
+    io.P = c->d_mss + (size_t)level * (FHE_MAXK + 1) + k;
+    io.mq = c->d_mq;
+    io.l = level;
+    io.k = k;
+    io.npoly = npoly;
+    io.stride = c->N;
+    // reads the k switch values and x_i, writes out_i
+    run_fwd(c, io, npoly * (level - k) * count, FHE_K_NTT_MODSWITCH, k + 2.0);
 }
 
 void launch_ntt_modswitch(fhe_ctx *c, const u64 *last, const u64 *in, u64 *out, int level, int npoly, int count)

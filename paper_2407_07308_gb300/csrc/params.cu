@@ -279,6 +279,38 @@ int build_tables(fhe_ctx *c)
         }
     }
     if ((e = upload(c, (void **)&c->d_rms, c->rms.data(), sizeof(RelinMSParams) * (L + 1)))) return e;
+
+    // k switches at once
+    c->mss.assign((size_t)(L + 1) * (FHE_MAXK + 1), MultiSwitchParams());
+    c->mss_scale.assign((size_t)(L + 1) * (FHE_MAXK + 1) * FHE_MAXK, make_ulonglong2(0, 0));
+    for (int l = 3; l <= L; l++)
+        for (int k = 2; k <= FHE_MAXK && k < l; k++) {
+            MultiSwitchParams &S = c->mss[(size_t)l * (FHE_MAXK + 1) + k];
+            memset(&S, 0, sizeof(S));
+            S.l = l;
+            S.k = k;
+            for (int i = 0; i < l - k; i++) {
+                const u64 qi = c->q[i];
+                u64 D = 1;
+                for (int t = 0; t < k; t++) {
+                    S.G[t][i] = host_mulmod(c->p % qi, D, qi);
+                    D = host_mulmod(D, c->q[l - 1 - t] % qi, qi);
+                }
+                S.Dinv[i] = host_invmod(D, qi);
+                S.Dinv_s[i] = shoup_const(S.Dinv[i], qi);
+            }
+            for (int j = 0; j < k; j++) {
+                const u64 qj = c->q[l - 1 - j];
+                std::vector<u64> D(j + 1, 1);  // D_t mod q_j, t <= j
+                for (int t = 1; t <= j; t++) D[t] = host_mulmod(D[t - 1], c->q[l - t] % qj, qj);
+                const u64 Djinv = host_invmod(D[j], qj);
+                for (int t = 0; t < j; t++) S.F[j][t] = host_mulmod(D[t], Djinv, qj);
+                const u64 ni = host_invmod((u64)N % qj, qj);
+                const u64 v = host_mulmod(host_mulmod(ni, host_invmod(c->p % qj, qj), qj), Djinv, qj);
+                c->mss_scale[((size_t)l * (FHE_MAXK + 1) + k) * FHE_MAXK + j] = make_ulonglong2(v, shoup_const(v, qj));
+            }
+        }
+    if ((e = upload(c, (void **)&c->d_mss, c->mss.data(), sizeof(MultiSwitchParams) * c->mss.size()))) return e;
     if ((e = upload(c, (void **)&c->d_modup, c->modup.data(), sizeof(ModUpParams) * (L + 1)))) return e;
     if ((e = upload(c, (void **)&c->d_moddown, c->moddown.data(), sizeof(ModDownParams) * (L + 1)))) return e;
     if ((e = upload(c, (void **)&c->d_modswitch, c->modswitch.data(), sizeof(ModSwitchParams) * (L + 1))))

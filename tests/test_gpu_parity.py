@@ -435,3 +435,28 @@ def test_fused_relin_modswitch_equals_separate_steps(logN, p, L, K):
     finally:
         fhe.fhe_ctx_fused_modswitch(g.ctx, True)
         g.close()
+
+
+@pytest.mark.parametrize("logN,p,L,K", [(12, 17, 12, 2), (13, 131, 10, 3)])
+def test_multi_level_switch_equals_single_steps(logN, p, L, K):
+    """Dropping k primes in one step (fhe_mod_switch to a level k below) gives
+    the residues of k single-prime switches, for every k, and decrypts."""
+    fhe = _fhe()
+    from tests.gpu_setup import GpuSetup
+
+    g = GpuSetup(seed=31, logN=logN, p=p, L=L, K=K, **CHAIN50)
+    try:
+        rnd = random.Random(p)
+        rows = [[rnd.randrange(p) for _ in range(g.ns)] for _ in range(3)]
+        x = g.encrypt_slots(rows, seed=5)
+        single = {L: g.export(x)}
+        cur = x
+        for lv in range(L - 1, 0, -1):
+            cur = g.own(fhe.fhe_mod_switch(g.ctx, cur, lv))
+            single[lv] = g.export(cur)
+        for lv in range(L - 1, 0, -1):
+            direct = g.own(fhe.fhe_mod_switch(g.ctx, x, lv))
+            assert np.array_equal(g.export(direct), single[lv]), lv
+        assert np.array_equal(g.decrypt(direct), np.array(rows, dtype=np.uint64))
+    finally:
+        g.close()
