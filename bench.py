@@ -208,6 +208,25 @@ class Clocks:
 # GPU arm
 # ---------------------------------------------------------------------------
 
+# DRAM bytes per algorithmic byte of a kernel class, measured with ncu on the
+# headline command (profiles/ntt_inverse_c2_dram.md) for the NTT source whose
+# SHA-256 starts with the given prefix; for any other source the traffic is
+# reported as null.
+DRAM_PER_ALGORITHMIC = {"ntt_inv": (1.04, "4f414403d27ef5b0")}
+
+
+def traffic_for(kernel_class: str, algorithmic_bytes: float):
+    import hashlib
+
+    rec = DRAM_PER_ALGORITHMIC.get(kernel_class)
+    if not rec:
+        return None
+    with open(os.path.join(ROOT, "paper_2407_07308_gb300", "csrc", "ntt.cu"), "rb") as f:
+        if not hashlib.sha256(f.read()).hexdigest().startswith(rec[1]):
+            return None
+    return round(rec[0] * algorithmic_bytes)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -254,7 +273,7 @@ def run_gpu(args):
     info = fhe.fhe_ctx_info(ctx)
     ns, N, pairs = info.slots, info.N, W["pairs"]
     variant, _ = fhe.fhe_ctx_ntt_variant(ctx)
-    split = {0: "2^7 x 2^7", 1: "2^8 x 2^6"}[variant]
+    split = {0: "2^7 x 2^7, two kernels", 1: "2^8 x 2^6, two kernels", 2: "2^7 x 2^7, one cluster kernel"}[variant]
     primes = fhe.fhe_ctx_primes(ctx)
     km = synth.KeyMaterial(W["seed"], primes, W["L"], W["K"], N)
     sk, pk = fhe.fhe_keygen_explicit(ctx, km.s, km.a_pk, km.e_pk)
@@ -329,7 +348,8 @@ def run_gpu(args):
     hbm_peak, peak_kind = peaks()
     achieved = by_k / (ms_k / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(achieved / hbm_peak, 4), "peak_source": peak_kind, "traffic": None,
+            "frac": round(achieved / hbm_peak, 4), "peak_source": peak_kind,
+            "traffic": traffic_for(dom, by_k / max(n_k, 1)),
             "launches_per_step": n_k, "avg_launch_us": round(1e3 * ms_k / max(n_k, 1), 2),
             "algorithmic_bytes_per_launch": round(by_k / max(n_k, 1)),
             "share_of_step": round(ms_k / sum(v[0] for v in prof.values()), 3)}

@@ -439,6 +439,9 @@ int fhe_mod_switch_noalloc(fhe_ctx *ctx, const uint64_t *in, uint64_t *out, int 
  * it does not exist for this N; set < 0 only reads); ms[3] (may be NULL)
  * receives the last timings in milliseconds (0 for variants that do not
  * exist).  All variants give identical results.
+ * The environment variable FHE_NTT_VARIANT (a digit) pins the variant for
+ * contexts created afterwards, skipping the timing (for profiling runs,
+ * whose timings would mislead the choice).
  * njobs counts limb transforms: polynomials of min(L+K, 10) limbs, rounded
  * to a multiple of 16 polynomials once there are 16 or more. */
 int fhe_ctx_autotune(fhe_ctx *ctx, int njobs);

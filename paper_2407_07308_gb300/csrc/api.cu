@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" boundary: contexts, keys, ciphertexts, encryption,
 // decryption and the arithmetic / comparison entry points declared in fhe.h.
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -348,7 +349,13 @@ extern "C" int fhe_ctx_create(const fhe_params *P, const fhe_allocator *alloc, v
     if (!e) e = fhe_cuda_check(c, cudaDeviceSynchronize(), "ctx_create");
     // choose the NTT factorisation for this ring degree on 32 polynomials
     // (16 ciphertexts) of up to 10 limbs, the scale of batched use
-    if (!e) e = ntt_autotune(c, 32 * 10, c->ntt_ms);
+    // FHE_NTT_VARIANT pins the variant (e.g. to profile the one a timed run
+    // chose: timings under a profiler are not representative)
+    const char *pin = getenv("FHE_NTT_VARIANT");
+    if (!e && pin && *pin >= '0' && *pin <= '9' && ntt_variant_ok(c->logN, atoi(pin)))
+        c->ntt_variant = atoi(pin);
+    else if (!e)
+        e = ntt_autotune(c, 32 * 10, c->ntt_ms);
     if (e) {
         fhe_ctx_destroy(c);
         return e;

@@ -1079,7 +1079,8 @@ void launch_ntt_inv_scaled_y(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap 
     io.qm = c->q[level - 1];
     io.Pm = c->rms[level].Pm;
     io.Pm_s = c->rms[level].Pm_s;
-    run_inv(c, io, njobs, FHE_K_NTT_INV);
+    // the y entry (one of nl) also reads the addend limb
+    run_inv(c, io, njobs, FHE_K_NTT_INV, 2.0 + 1.0 / m.nl);
 }
 
 void launch_ntt_modup(fhe_ctx *c, const u64 *d2c, u64 *ext, int level, int count)
