@@ -68,8 +68,10 @@ void *Pool::get(size_t bytes, int *err)
     if (!p && !in_capture) {
         // out of device memory: wait for all queued work, hand every cached
         // free block (this pool's, and those of contexts not busy on another
-        // thread) back to the allocator, and try once more
+        // thread, whose captured batch graphs are dropped too) back to the
+        // allocator, and try once more
         cudaDeviceSynchronize();
+        if (owner) batch_plans_release(owner, owner->bplan_active);
         trim();
         trim_other_pools(this);
         if (alloc.alloc) {
@@ -139,6 +141,8 @@ void trim_other_pools(Pool *self)
     std::lock_guard<std::mutex> g(g_ctx_mu);
     for (fhe_ctx *o : g_ctxs) {
         if (&o->pool == self || !o->mu.try_lock()) continue;  // busy contexts keep theirs
+        cudaStreamSynchronize(o->stream);
+        batch_plans_release(o);  // captured batches are caches: rebuilt when needed
         o->pool.trim();
         o->mu.unlock();
     }
@@ -345,6 +349,7 @@ extern "C" int fhe_ctx_create(const fhe_params *P, const fhe_allocator *alloc, v
     if (alloc) c->pool.alloc = *alloc;
     else memset(&c->pool.alloc, 0, sizeof(fhe_allocator));
     c->pool.stream = c->stream;
+    c->pool.owner = c;
     int e = build_tables(c);
     if (!e) e = fhe_cuda_check(c, cudaDeviceSynchronize(), "ctx_create");
     // choose the NTT factorisation for this ring degree on 32 polynomials

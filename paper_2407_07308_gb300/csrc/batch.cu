@@ -258,7 +258,17 @@ int capture(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups, const std::vector
     return 0;
 }
 
+int replay_in(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups, BatchPlan *P);
+
 int replay(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups, BatchPlan *P)
+{
+    c->bplan_active = P;
+    const int err = replay_in(c, jobs, groups, P);
+    c->bplan_active = nullptr;
+    return err;
+}
+
+int replay_in(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups, BatchPlan *P)
 {
     size_t gi = 0;
     for (auto &kv : groups) {
@@ -351,11 +361,18 @@ int run_context(fhe_ctx *c, const fhe_job *jobs, const std::vector<int> &ids)
 
 }  // namespace
 
-void batch_plans_release(fhe_ctx *c)
+// Frees every captured batch of the context except `keep` (the caller has
+// made sure none of them is running).
+void batch_plans_release(fhe_ctx *c, const BatchPlan *keep)
 {
-    for (BatchPlan *P : c->bplans) plan_free(c, P);
-    c->bplans.clear();
-    c->bseen.clear();
+    std::vector<BatchPlan *> kept;
+    for (BatchPlan *P : c->bplans)
+        if (P == keep)
+            kept.push_back(P);
+        else
+            plan_free(c, P);
+    c->bplans = kept;
+    if (!keep) c->bseen.clear();
 }
 
 extern "C" int fhe_ctx_set_batch_graphs(fhe_ctx *c, int max_plans)

@@ -116,6 +116,7 @@ struct Pool {
     // the plan keeps them afterwards because every replay reuses them.
     std::unordered_map<size_t, std::vector<void *>> *cap_free = nullptr;
     bool in_capture = false;                      // misses use cudaMalloc (never the caller's allocator)
+    fhe_ctx *owner = nullptr;                     // the context (to drop its cached batch graphs)
     void *get(size_t bytes, int *err);
     void put(void *p);
     void trim();
@@ -206,6 +207,7 @@ struct fhe_ctx {
     std::map<std::vector<u64>, int> bseen;
     int bplan_cap = 4;
     u64 bplan_clock = 0;
+    BatchPlan *bplan_active = nullptr;  // the graph being replayed (kept when memory runs out)
     long long launches = 0;       // kernels launched since creation
 };
 
@@ -244,7 +246,7 @@ struct BatchPlan {
     int nodes = 0;
     u64 last = 0;
 };
-void batch_plans_release(fhe_ctx *c);
+void batch_plans_release(fhe_ctx *c, const BatchPlan *keep = nullptr);
 
 struct fhe_plan {
     fhe_ctx *ctx;
