@@ -597,10 +597,10 @@ def run_uneven(args):
     slot_cmps = sum(r["c"]["ns"] for r in reqs)
     cs.sync()
 
-    def batched_step(check=False):
+    def batched_step(check=False, flags=fhe.FHE_BATCH_ALIGN_LEVELS):
         jobs = [fhe.Job(r["c"]["ctx"], r["c"]["evk"], fhe.FHE_JOB_COMPARE, r["xs"], r["ys"]) for r in reqs]
         t = time.perf_counter()
-        bt = fhe.fhe_batch_submit(jobs)
+        bt = fhe.fhe_batch_submit(jobs, flags)
         t_enq = time.perf_counter() - t
         assert fhe.fhe_batch_wait(bt, 600000) == 0
         dt = time.perf_counter() - t
@@ -615,6 +615,11 @@ def run_uneven(args):
                 fhe.fhe_ct_destroy(h)
         return dt, t_enq
 
+    # same-level groups only (no alignment), then the aligned form (the value)
+    batched_step(check=True, flags=0)
+    for _ in range(args.warmup - 1):
+        batched_step(flags=0)
+    unaligned = [batched_step(flags=0)[0] for _ in range(args.steps)]
     batched_step(check=True)
     for _ in range(args.warmup - 1):
         batched_step()
@@ -653,11 +658,15 @@ def run_uneven(args):
                                "level uniform in [lowest decryptable level, 20], 20x50-bit + 4 special primes, one "
                                "ciphertext tuple pair per request", "requests": len(reqs), "by_shape": shapes,
                    "slot_comparisons_per_step": slot_cmps,
-                   "batched_form": "all requests in one fhe_batch_submit (grouped by context, digits, level; "
-                                   "8 streams per context), host wall time of submit + wait",
+                   "batched_form": "all requests in one fhe_batch_submit with FHE_BATCH_ALIGN_LEVELS (requests "
+                                   "of one context and digit count switched down to their lowest start level "
+                                   "and grouped; 8 streams per context; recurring shapes replayed as graphs), "
+                                   "host wall time of submit + wait",
                    "plain_form": "one request at a time through fhe_compare, synchronised",
                    "l2": "inputs and intermediates of every step exceed L2"},
         "plain": plain, "enqueue_ms_p50": round(1e3 * sorted(t for _, t in times)[len(times) // 2], 1),
+        "batched_same_level_groups": {"value": round(slot_cmps * args.steps / sum(unaligned), 2), "unit": UNIT,
+                                      "ms_per_step": round(1e3 * sum(unaligned) / args.steps, 1)},
         "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": None, "roofline": None,
     }
     for r in reqs:

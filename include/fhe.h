@@ -314,6 +314,15 @@ typedef struct fhe_batch fhe_batch;
  * contexts run on their own streams.  Each result equals what the job gives
  * alone.  Enqueues and returns; `*out` tracks completion. */
 int fhe_batch_submit(const fhe_job *jobs, int n, fhe_batch **out);
+/* fhe_batch_submit with options.  FHE_BATCH_ALIGN_LEVELS: within each
+ * (context, keys, kind, digits, wanted outputs), jobs above the lowest level
+ * among them are first switched down to it (copies; the caller's handles are
+ * untouched), so that they share one group and its launches.  Each result
+ * then equals the job run alone from that lower level.  The lowest level must
+ * leave the circuit its depth, as it does when every job of the group could
+ * run alone at its own level. */
+enum { FHE_BATCH_ALIGN_LEVELS = 1 };
+int fhe_batch_submit_ex(const fhe_job *jobs, int n, int flags, fhe_batch **out);
 /* Graph capture of recurring submissions: the second time a context receives
  * the same group shapes (keys, kind, digits, level, ciphertexts per group),
  * its circuit is captured into a CUDA graph with operand and result buffers
@@ -346,7 +355,7 @@ enum { FHE_REQ_QUEUED = 0, FHE_REQ_RUNNING = 1, FHE_REQ_DONE = 2 };
 typedef struct {
     uint64_t hbm_budget; /* bytes; 0 = no limit */
     int max_batch;       /* most requests per submission; 0 = no limit */
-    int reserved;
+    int batch_flags;     /* passed to fhe_batch_submit_ex (e.g. FHE_BATCH_ALIGN_LEVELS) */
 } fhe_server_config;
 
 typedef struct {

@@ -385,12 +385,81 @@ extern "C" int fhe_ctx_set_batch_graphs(fhe_ctx *c, int max_plans)
     return 0;
 }
 
+namespace {
+
+// Level alignment: within each (context, keys, kind, digits, outputs) the
+// jobs above the lowest level get copies of their operands switched down to
+// it (several primes at once), so that they share one group.  The copies are
+// released after the circuit has been enqueued (stream-ordered reuse).
+struct Aligned {
+    std::vector<fhe_job> jobs;
+    std::vector<std::vector<const fhe_ct *>> ops;  // per job: x[0..d), y[0..d)
+    std::vector<fhe_ct *> owned;
+    ~Aligned()
+    {
+        for (fhe_ct *x : owned) fhe_ct_destroy(x);
+    }
+};
+
+int align_levels(const fhe_job *jobs, int n, Aligned &A)
+{
+    std::map<std::tuple<fhe_ctx *, const fhe_evk *, int, int, bool, bool>, int> lowest;
+    for (int i = 0; i < n; i++) {
+        const fhe_job &j = jobs[i];
+        auto key = std::make_tuple(j.ctx, j.evk, j.kind, j.d, j.out0 != nullptr, j.out1 != nullptr);
+        auto it = lowest.find(key);
+        const int lv = j.x[0]->level;
+        if (it == lowest.end() || lv < it->second) lowest[key] = lv;
+    }
+    A.jobs.assign(jobs, jobs + n);
+    A.ops.resize(n);
+    for (int i = 0; i < n; i++) {
+        fhe_job &j = A.jobs[i];
+        const int target =
+            lowest[std::make_tuple(j.ctx, j.evk, j.kind, j.d, j.out0 != nullptr, j.out1 != nullptr)];
+        std::vector<const fhe_ct *> &ops = A.ops[i];
+        ops.assign(2 * j.d, nullptr);
+        for (int k = 0; k < 2 * j.d; k++) {
+            const fhe_ct *src = k < j.d ? j.x[k] : j.y[k - j.d];
+            if (src->level == target) {
+                ops[k] = src;
+                continue;
+            }
+            fhe_ct *r = nullptr;
+            int e;
+            {
+                std::lock_guard<std::mutex> g(j.ctx->mu);
+                e = op_lower(j.ctx, src, target, &r);
+            }
+            if (e) return e;
+            A.owned.push_back(r);
+            ops[k] = r;
+        }
+        j.x = ops.data();
+        j.y = ops.data() + j.d;
+    }
+    return 0;
+}
+
+}  // namespace
+
 extern "C" int fhe_batch_submit(const fhe_job *jobs, int n, fhe_batch **out)
 {
-    if (!jobs || n < 1 || !out) return FHE_EINVAL;
+    return fhe_batch_submit_ex(jobs, n, 0, out);
+}
+
+extern "C" int fhe_batch_submit_ex(const fhe_job *jobs, int n, int flags, fhe_batch **out)
+{
+    if (!jobs || n < 1 || !out || (flags & ~FHE_BATCH_ALIGN_LEVELS)) return FHE_EINVAL;
     for (int i = 0; i < n; i++) {
         int e = batch_check_job(jobs[i]);
         if (e) return e;
+    }
+    Aligned A;
+    if (flags & FHE_BATCH_ALIGN_LEVELS) {
+        const int e = align_levels(jobs, n, A);
+        if (e) return e;
+        jobs = A.jobs.data();
     }
     std::vector<fhe_ctx *> order;
     std::map<fhe_ctx *, std::vector<int>> by_ctx;

@@ -148,7 +148,7 @@ void fhe_server::run()
         }
         lk.unlock();
         fhe_batch *b = nullptr;
-        int err = fhe_batch_submit(jobs.data(), (int)jobs.size(), &b);
+        int err = fhe_batch_submit_ex(jobs.data(), (int)jobs.size(), cfg.batch_flags, &b);
         lk.lock();
         batches++;
         if (err) {

@@ -49,7 +49,7 @@ class fhe_allocator(Structure):
 
 
 class fhe_server_config(Structure):
-    _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_batch", c_int), ("reserved", c_int)]
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_batch", c_int), ("batch_flags", c_int)]
 
 
 class fhe_request_info(Structure):
@@ -142,6 +142,7 @@ def lib() -> ctypes.CDLL:
             "fhe_ctx_autotune": (ci, [vp, ci]),
             "fhe_ctx_ntt_variant": (ci, [vp, ci, vp]),
             "fhe_batch_submit": (ci, [vp, ci, POINTER(vp)]),
+            "fhe_batch_submit_ex": (ci, [vp, ci, ci, POINTER(vp)]),
             "fhe_batch_wait": (ci, [vp, ci]),
             "fhe_batch_destroy": (None, [vp]),
             "fhe_job_footprint": (ctypes.c_uint64, [vp]),
@@ -550,10 +551,13 @@ class Job:
         return None if self._o1 is None else [c_void_p(v) for v in self._o1]
 
 
-def fhe_batch_submit(jobs):
+FHE_BATCH_ALIGN_LEVELS = 1
+
+
+def fhe_batch_submit(jobs, flags: int = 0):
     arr = (fhe_job * len(jobs))(*[j.struct() for j in jobs])
     out = c_void_p()
-    _check(lib().fhe_batch_submit(ctypes.cast(arr, c_void_p), len(jobs), ctypes.byref(out)),
+    _check(lib().fhe_batch_submit_ex(ctypes.cast(arr, c_void_p), len(jobs), int(flags), ctypes.byref(out)),
            jobs[0].ctx if jobs else None)
     return out
 
@@ -597,8 +601,8 @@ def fhe_job_footprint(job: "Job") -> int:
     return int(lib().fhe_job_footprint(ctypes.byref(st)))
 
 
-def fhe_server_start(hbm_budget: int = 0, max_batch: int = 0):
-    cfg = fhe_server_config(int(hbm_budget), int(max_batch), 0)
+def fhe_server_start(hbm_budget: int = 0, max_batch: int = 0, batch_flags: int = 0):
+    cfg = fhe_server_config(int(hbm_budget), int(max_batch), int(batch_flags))
     out = c_void_p()
     _check(lib().fhe_server_start(ctypes.byref(cfg), ctypes.byref(out)))
     return out

@@ -180,3 +180,63 @@ def test_recurring_batches_are_captured_and_match_alone():
         fhe.fhe_pk_destroy(pk)
     finally:
         fhe.fhe_ctx_destroy(ctx)
+
+
+def test_level_aligned_batch_matches_lowered_alone():
+    """FHE_BATCH_ALIGN_LEVELS: jobs of one (context, kind, digits) at
+    different levels share a group at the lowest of them; each result equals
+    the job run alone after switching its operands down to that level."""
+    from paper_2407_07308_gb300 import fhe
+
+    ctx = fhe.fhe_ctx_create(12, 17, 12, 3, CHAIN50["U"], CHAIN50["lo"], CHAIN50["hi"])
+    try:
+        sk, pk = fhe.fhe_keygen(ctx, 3)
+        evk = fhe.fhe_evk_create(ctx, sk, [], 4)
+        ns = fhe.fhe_ctx_info(ctx).slots
+        rnd = np.random.default_rng(8)
+        jobs, meta, hs = [], [], []
+        for i, (level, d, kind) in enumerate([(12, 2, fhe.FHE_JOB_COMPARE), (10, 2, fhe.FHE_JOB_COMPARE),
+                                              (11, 2, fhe.FHE_JOB_COMPARE), (9, 1, fhe.FHE_JOB_MAXMIN),
+                                              (12, 1, fhe.FHE_JOB_MAXMIN)]):
+            xv = rnd.integers(0, 9 ** d, size=(2, ns))
+            yv = np.where(rnd.random((2, ns)) < 0.3, xv, rnd.integers(0, 9 ** d, size=(2, ns)))
+            xs, ys = [], []
+            for k in range(d):
+                for vals, out, sd in ((xv, xs, 10 * i + k), (yv, ys, 10 * i + 5 + k)):
+                    h = fhe.fhe_encrypt(ctx, pk, (vals // 9 ** k) % 9, sd)
+                    if level < 12:
+                        h2 = fhe.fhe_mod_switch(ctx, h, level)
+                        hs.append(h)
+                        h = h2
+                    out.append(h)
+                    hs.append(h)
+            jobs.append(fhe.Job(ctx, evk, kind, xs, ys))
+            meta.append((kind, xs, ys, xv, yv, d))
+        b = fhe.fhe_batch_submit(jobs, fhe.FHE_BATCH_ALIGN_LEVELS)
+        assert fhe.fhe_batch_wait(b, 120000) == 0
+        fhe.fhe_batch_destroy(b)
+        lowest = {fhe.FHE_JOB_COMPARE: 10, fhe.FHE_JOB_MAXMIN: 9}
+        for job, (kind, xs, ys, xv, yv, d) in zip(jobs, meta):
+            lv = lowest[kind]
+            xl = [fhe.fhe_mod_switch(ctx, h, lv) for h in xs]
+            yl = [fhe.fhe_mod_switch(ctx, h, lv) for h in ys]
+            hs += xl + yl
+            if kind == fhe.FHE_JOB_COMPARE:
+                alone = list(fhe.fhe_compare(ctx, evk, xl, yl))
+                assert (fhe.fhe_decrypt(ctx, sk, job.out0[0]) == (xv < yv)).all()
+            else:
+                mx, mn = fhe.fhe_max_min(ctx, evk, xl, yl)
+                alone = mx + mn
+                got = sum(fhe.fhe_decrypt(ctx, sk, job.out0[k]).astype(np.int64) * 9 ** k for k in range(d))
+                assert (got == np.maximum(xv, yv)).all()
+            got_h = job.out0 + job.out1
+            for a, g in zip(alone, got_h):
+                assert np.array_equal(fhe.fhe_ct_export_coeff(ctx, a), fhe.fhe_ct_export_coeff(ctx, g))
+            hs += alone + got_h
+        for h in hs:
+            fhe.fhe_ct_destroy(h)
+        fhe.fhe_evk_destroy(evk)
+        fhe.fhe_sk_destroy(sk)
+        fhe.fhe_pk_destroy(pk)
+    finally:
+        fhe.fhe_ctx_destroy(ctx)
