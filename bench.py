@@ -718,7 +718,7 @@ def run_serve(args):
     cs.sync()
     rate = args.serve_rate
     due = np.cumsum(g.exponential(1.0 / rate, size=len(reqs)))
-    srv = fhe.fhe_server_start(hbm_budget=int(S["budget"]))
+    srv = fhe.fhe_server_start(hbm_budget=int(S["budget"]), batch_flags=fhe.FHE_BATCH_ALIGN_LEVELS)
     l0 = cs.launches()
     errors = []
 
@@ -804,7 +804,7 @@ def run_serve(args):
                                f"[{S['nmin']}, {S['nmax']}] values, N in {{2^13,2^14,2^15}}, p in {{17,131,257}}, "
                                f"d=2, 3/4 LT+EQ and 1/4 max/min, 20x50-bit + 4 special primes, start level = "
                                f"lowest decryptable level, client chunks of <= {S['chunk']} ciphertexts, operands "
-                               f"encrypted on arrival", "hbm_budget_gb": S["budget"] / 1e9, "arrival_rate_per_s": rate},
+                               f"encrypted on arrival, batches level-aligned", "hbm_budget_gb": S["budget"] / 1e9, "arrival_rate_per_s": rate},
         "latency_ms_p50": round(lat[len(lat) // 2], 1),
         "latency_ms_p99": round(lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))], 1),
         "server": {"batches": st.batches, "admitted_peak_gb": round(st.admitted_peak_bytes / 1e9, 2),
