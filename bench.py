@@ -48,6 +48,27 @@ CONFIG = {
 }
 
 
+# C1 of the survey's configurations: the small ring (N = 2^12, p = 17, one
+# digit, 4 x 36-bit data primes + 1 special prime), one ciphertext pair.
+U36 = 8192 * 17
+SMALL = dict(logN=12, p=17, d=1, L=4, K=1, U=U36, lo=2 ** 35, hi=2 ** 36, pairs=1, seed=1)
+
+
+FLUSH_L2 = False
+
+
+def use_small_workload():
+    global METRIC, FLUSH_L2
+    FLUSH_L2 = True
+    W.update(SMALL)
+    METRIC = "encrypted slot-comparisons/sec at N=2^12,p=17,d=1; batched vs plain; p99 ms"
+    CONFIG.clear()
+    CONFIG.update({"workload": "BGV N=2^12 p=17 d=1 LT+EQ, 1 ciphertext pair, 4x36-bit + 1 special prime",
+                   "N": 2 ** 12, "p": 17, "d": 1, "slots_per_ct": 8, "pairs_per_step": 1, "data_primes": 4,
+                   "special_primes": 1, "l2": "data fits in L2: a 256 MB buffer is written between timed steps "
+                                                 "(outside the timed events)"})
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -95,8 +116,11 @@ def make_values(pairs, ns, seed):
 _STATE = {}
 
 
-def _oracle_init():
-    """Worker set-up (untimed): oracle context, keys, the batch's values."""
+def _oracle_init(w=None):
+    """Worker set-up (untimed): oracle context, keys, the batch's values.
+    A spawned worker re-imports this module, so the workload comes in `w`."""
+    if w:
+        W.update(w)
     sys.path.insert(0, ROOT)
     from oracle.bgv import Oracle
     from oracle.encoding import SlotStructure
@@ -145,7 +169,7 @@ class OraclePool:
 
         oracle.build()
         self.workers = workers
-        self.pool = mp.get_context("spawn").Pool(workers, initializer=_oracle_init)
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_oracle_init, initargs=(dict(W),))
 
     def sample(self, npairs):
         res = self.pool.map(_oracle_pair, list(range(npairs)), chunksize=1)
@@ -262,7 +286,8 @@ def run_gpu(args):
         per = op.sample(npairs)
         op.close()
         cpu = {"value": round(npairs * 2 / max(per), 4), "unit": UNIT, "cores": workers, "kind": "oracle",
-               "sample": f"{npairs} of the 16 pairs (LT+EQ, d=2, N=2^14) run concurrently, one spawned process "
+               "sample": f"{npairs} of the {W['pairs']} pairs (LT+EQ, d={W['d']}, N=2^{W['logN']}) run concurrently, "
+                         f"one spawned process "
                          f"per pair; {statistics.mean(per):.1f} s per pair on average"}
 
     stream = torch.cuda.Stream()
@@ -273,7 +298,9 @@ def run_gpu(args):
     info = fhe.fhe_ctx_info(ctx)
     ns, N, pairs = info.slots, info.N, W["pairs"]
     variant, _ = fhe.fhe_ctx_ntt_variant(ctx)
-    split = {0: "2^7 x 2^7, two kernels", 1: "2^8 x 2^6, two kernels", 2: "2^7 x 2^7, one cluster kernel"}[variant]
+    n = W["logN"]
+    n1 = {0: (n + 1) // 2, 1: {11: 5, 12: 7, 13: 6, 14: 8, 15: 7}.get(n), 2: n // 2}[variant]
+    split = f"2^{n1} x 2^{n - n1}, " + ("one cluster kernel" if variant == 2 else "two kernels")
     primes = fhe.fhe_ctx_primes(ctx)
     km = synth.KeyMaterial(W["seed"], primes, W["L"], W["K"], N)
     sk, pk = fhe.fhe_keygen_explicit(ctx, km.s, km.a_pk, km.e_pk)
@@ -309,21 +336,28 @@ def run_gpu(args):
         step()
     fhe.fhe_ctx_sync(ctx)
 
-    evs = [ev() for _ in range(args.steps + 1)]
+    # a workload whose data fits in L2 gets the cache flushed (a 256 MB write)
+    # between timed steps, outside the events that time each step
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if FLUSH_L2 else None
+    evs = [(ev(), ev()) for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
     l0 = fhe.fhe_ctx_launches(ctx)
     with Clocks(local) as clk:
-        evs[0].record(stream)
+        t_wall = time.perf_counter()
         for i in range(args.steps):
+            if flush is not None:
+                with torch.cuda.stream(stream):
+                    flush.fill_(i & 0xFF)
+            evs[i][0].record(stream)
             step()
-            evs[i + 1].record(stream)
+            evs[i][1].record(stream)
         stream.synchronize()
     torch.cuda.synchronize()
     barrier()
     launches = fhe.fhe_ctx_launches(ctx) - l0
-    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    total_ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), world)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = max_over_ranks(sum(step_ms) if flush is not None else evs[0][0].elapsed_time(evs[-1][1]), world)
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(pairs * ns, world, args.steps, total_ms)
 
@@ -355,6 +389,14 @@ def run_gpu(args):
             "share_of_step": round(ms_k / sum(v[0] for v in prof.values()), 3)}
     if bf_k:
         roof["butterflies_per_s"] = bf_k / (ms_k / 1e3)
+    # the integer-pipe view: one 64-bit high product per butterfly, against
+    # the probe's measured rate
+    imad32, mulhi64 = fhe.fhe_probe_int_peak()
+    int_pipe = {"probe_imad32_per_s": imad32, "probe_mulhi64_per_s": mulhi64}
+    if bf_k:
+        int_pipe["dominant_kernel_mulhi64_frac"] = round(bf_k / (ms_k / 1e3) / mulhi64, 4)
+    int_pipe["ntt_classes_mulhi64_frac"] = {
+        k: round(v[3] / (v[0] / 1e3) / mulhi64, 4) for k, v in prof.items() if v[3] and v[0]}
     kernels = {k: {"ms_per_step": round(v[0], 3), "launches_per_step": v[1],
                    "GBps": round(v[2] / (v[0] / 1e3) / 1e9, 1) if v[0] else 0.0}
                for k, v in prof.items() if v[1]}
@@ -388,7 +430,8 @@ def run_gpu(args):
         "batched_step_ms_p50": round(pct(sorted(step_ms), 0.5), 3),
         "batched_step_ms_p99": round(pct(sorted(step_ms), 0.99), 3),
         "p99_ms": round(pct(sorted(step_ms), 0.99), 3),
-        "roofline": roof, "kernels": kernels, "profiled_ms_per_step": round(prof_ms_per_step, 3),
+        "roofline": roof, "int_pipe": int_pipe, "kernels": kernels,
+        "profiled_ms_per_step": round(prof_ms_per_step, 3),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         "memory_gb": {"pool_reserved": round(res / 1e9, 2)},
     }
@@ -478,7 +521,7 @@ def run_reference(args):
     if rank != 0:
         return
     workers = max(1, min(W["pairs"], os.cpu_count() or 1, args.cpu_workers))
-    npairs = workers  # one pair per core per step: a bounded sample of the 16-pair batch
+    npairs = workers  # one pair per core per step: a bounded sample of the batch
     op = OraclePool(workers)
     for _ in range(args.warmup):
         op.sample(npairs)
@@ -494,7 +537,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded BGV keys, noise and values)", "config": dict(CONFIG, parallelism="host cores"),
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": workers, "kind": "oracle",
-                         "sample": f"{npairs} of the 16 pairs per step, one spawned process per pair"},
+                         "sample": f"{npairs} of the {W['pairs']} pairs per step, one spawned process per pair"},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -897,17 +940,22 @@ def main():
     ap.add_argument("--pairs", type=int, default=16, help="ciphertext pairs per batch (16 = the workload)")
     ap.add_argument("--no-plain", action="store_true", help="skip the one-request-at-a-time form")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
-    ap.add_argument("--workload", default="compare", choices=["compare", "uneven", "serve", "tournament"],
-                    help="compare: the 16-pair batch (default); uneven: 256 mixed requests; serve: serving "
-                         "loop; tournament: max/min of 4096 values")
+    ap.add_argument("--workload", default="compare", choices=["compare", "small", "uneven", "serve", "tournament"],
+                    help="compare: the 16-pair batch (default); small: one pair on the small ring; uneven: "
+                         "256 mixed requests; serve: serving loop; tournament: max/min of 4096 values")
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate (requests/s) for serve")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    W["pairs"] = args.pairs
-    CONFIG["pairs_per_step"] = args.pairs
+    if args.workload == "small":
+        use_small_workload()
+    else:
+        W["pairs"] = args.pairs
+        CONFIG["pairs_per_step"] = args.pairs
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in ("compare", "small"):
+        run_gpu(args)
     elif args.workload == "uneven":
         run_uneven(args)
     elif args.workload == "serve":

@@ -416,6 +416,15 @@ int fhe_ntt_inverse(fhe_ctx *ctx, uint64_t *data, const int32_t *prime_idx, int 
 int fhe_ntt_forward_batch(fhe_ctx *ctx, uint64_t *data, int count, int nprimes);
 int fhe_ntt_inverse_batch(fhe_ctx *ctx, uint64_t *data, int count, int nprimes);
 
+/* ---- integer-pipe peaks --------------------------------------------------------- */
+
+/* Measures this GPU's throughput of 32-bit multiply-adds and of 64-bit high
+ * products (__umul64hi), in operations per second over all SMs, with fixed
+ * trip count kernels on the current device.  The NTT's Shoup butterfly does
+ * one 64-bit high product, so butterflies/s over mulhi64 is its integer-pipe
+ * fraction.  Synchronises the device. */
+int fhe_probe_int_peak(double *imad32, double *mulhi64);
+
 /* ---- modulus switching without allocation -------------------------------------- */
 
 /* No counterpart in the paper.  For callers that cannot allocate device

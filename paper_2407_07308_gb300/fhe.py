@@ -148,6 +148,7 @@ def lib() -> ctypes.CDLL:
             "fhe_job_footprint": (ctypes.c_uint64, [vp]),
             "fhe_ctx_inject_alloc_failure": (ci, [vp, ctypes.c_int64]),
             "fhe_ctx_trim": (ci, [vp]),
+            "fhe_probe_int_peak": (ci, [POINTER(ctypes.c_double), POINTER(ctypes.c_double)]),
             "fhe_ctx_fused_modswitch": (ci, [vp, ci]),
             "fhe_ctx_set_batch_graphs": (ci, [vp, ci]),
             "fhe_ctx_memory_peak": (ci, [vp, POINTER(ctypes.c_uint64), ci]),
@@ -580,6 +581,13 @@ def fhe_ctx_set_batch_graphs(ctx, max_plans: int):
 
 def fhe_ctx_fused_modswitch(ctx, on: bool):
     _check(lib().fhe_ctx_fused_modswitch(ctx, int(bool(on))), ctx)
+
+
+def fhe_probe_int_peak():
+    """(32-bit multiply-adds/s, 64-bit high products/s) measured on the current device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().fhe_probe_int_peak(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def fhe_ctx_trim(ctx):
