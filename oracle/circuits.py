@@ -41,6 +41,13 @@ them) are:
     (ceil(log2(p-1)) + ceil(log2 d) + 1) would leave less than one level,
     every ciphertext is refreshed (a stand-in for bootstrapping).
 
+  * bivariate digits (full range [0, p)): powers x^n, y^n by the same rule,
+    computed when first needed; for a = 0 .. p-1 in order, rows with a
+    non-zero c[a][b] give h_a = sum_b c[a][b] y^b (b >= 1; the coefficients
+    have no constant terms) at the level of the lowest power used, and the
+    term x^a h_a (for a = 0 the term is h_a), accumulated in order of a;
+    EQ_k = 1 - (x - y)^(p-1);
+
 Every operation appends (name, level) to ``trace``; the CUDA path emits the
 same trace, and a test compares them.  The multiplication count is pinned
 against the Paterson-Stockmeyer count (8 / 23 / 30 for p = 17 / 131 / 257) and
@@ -49,7 +56,7 @@ the depth against ceil(log2(p-1)).
 from __future__ import annotations
 
 from .bgv import Ct, Oracle
-from .ltpoly import lt_coefficients
+from .ltpoly import lt_bivariate_coefficients, lt_coefficients
 
 
 def centred(c: int, p: int) -> int:
@@ -190,12 +197,54 @@ class Evaluator:
             eq = self.add_const(self.neg(power(p - 1)), 1)
         return lt, eq
 
+    def digit_bivariate(self, x: Ct, y: Ct, want_lt: bool, want_eq: bool):
+        """(LT_k, EQ_k) of one pair of full digits in [0, p)."""
+        p = self.p
+
+        def power(pw: dict, n: int) -> Ct:
+            if n in pw:
+                return pw[n]
+            if n & (n - 1) == 0:
+                h = power(pw, n // 2)
+                r = self.mul(h, h)
+            else:
+                a = 1 << (n.bit_length() - 1)
+                r = self.mul(power(pw, a), power(pw, n - a))
+            pw[n] = r
+            return r
+
+        lt = None
+        if want_lt:
+            c = lt_bivariate_coefficients(p)
+            # no constant terms: L_y(0) = [y = 0] and no x lies below 0
+            assert all(c[a][0] == 0 for a in range(p))
+            px, py = {1: x}, {1: y}
+            for a in range(p):
+                ys = [(b, c[a][b]) for b in range(1, p) if c[a][b]]
+                if not ys:
+                    continue
+                cts = [power(py, b) for b, _ in ys]
+                lv = min(t.level for t in cts)
+                h = None
+                for (b, cb), t in zip(ys, cts):
+                    term = self.mul_const(self.lower(t, lv), cb)
+                    h = term if h is None else self.add(h, term)
+                term = h if a == 0 else self.mul(power(px, a), h)
+                lt = term if lt is None else self.add(lt, term)
+        eq = None
+        if want_eq:
+            pz = {1: self.sub(x, y)}
+            eq = self.add_const(self.neg(power(pz, p - 1)), 1)
+        return lt, eq
+
     # ---- merge of digits -----------------------------------------------------
-    def compare(self, xs, ys, want_lt=True, want_eq=False):
-        """LT(x, y) and/or EQ(x, y) for digit lists (least significant first)."""
+    def compare(self, xs, ys, want_lt=True, want_eq=False, bivariate=False):
+        """LT(x, y) and/or EQ(x, y) for digit lists (least significant first);
+        bivariate: full digits in [0, p) (else digits in [0, (p+1)/2))."""
+        digit = self.digit_bivariate if bivariate else self.digit
         nodes = []
         for x, y in zip(xs, ys):
-            nodes.append(self.digit(x, y, want_lt, True if len(xs) > 1 or want_eq else False))
+            nodes.append(digit(x, y, want_lt, True if len(xs) > 1 or want_eq else False))
         while len(nodes) > 1:
             root = len(nodes) == 2
             nxt = []

@@ -258,3 +258,29 @@ def test_small_config_full_size_lt():
     assert st.decrypt_slots(lt) == [int(a < c) for a, c in zip(xv, yv)]
     nb = st.o.noise_bits(lt, st.s)
     assert nb < np.log2(st.o.primes[0]) - 1, nb
+
+
+def test_compare_bivariate_full_digits_small_ring():
+    """Full digits in [0, p): the bivariate circuit's LT and EQ decrypt to
+    the plaintext comparison of values in [0, p^d), with noise below q0/2;
+    the product count follows the schedule (x and y powers 2..p-1, one
+    product per row a >= 1 with y terms, the EQ power, the merge)."""
+    from oracle.ltpoly import lt_bivariate_coefficients
+
+    p, d = 17, 2
+    st = OracleSetup(logN=8, p=p, L=8, K=2, seed=23, **CHAIN50)
+    rnd = random.Random(17)
+    ns = st.ss.ns
+    xs_v = [rnd.randrange(p ** d) for _ in range(ns)]
+    ys_v = [rnd.randrange(p ** d) if rnd.random() < 0.7 else xs_v[s] for s in range(ns)]
+    x = st.encrypt_slots(_digits(xs_v, p, d), seed=50)
+    y = st.encrypt_slots(_digits(ys_v, p, d), seed=51)
+    ev = st.evaluator()
+    lt, eq = ev.compare(x, y, True, True, bivariate=True)
+    assert st.decrypt_slots(lt) == [int(a < c) for a, c in zip(xs_v, ys_v)]
+    assert st.decrypt_slots(eq) == [int(a == c) for a, c in zip(xs_v, ys_v)]
+    assert st.o.noise_bits(lt, st.s) < np.log2(st.o.primes[0]) - 1
+    c = lt_bivariate_coefficients(p)
+    rows = sum(1 for a in range(1, p) if any(c[a][1:]))
+    per_digit = 2 * (p - 2) + rows + 4  # powers of x and y, row products, z^16 by four squarings
+    assert ev.mul_count() == d * per_digit + 2 * (d - 1)

@@ -70,3 +70,58 @@ def test_table3_digit_bases():
         else:
             assert p ** (d * l) >= 2 ** 64, name
             assert b ** (d * l) < 2 ** 64, name
+
+
+@pytest.mark.parametrize("p", [3, 5, 7, 17])
+def test_lt_bivariate_brute_force(p):
+    """sum c[a][b] x^a y^b = [x < y] at every pair of Z_p (as 0..p-1)."""
+    from oracle.ltpoly import evaluate_bivariate, lt_bivariate_coefficients
+
+    c = lt_bivariate_coefficients(p)
+    for x in range(p):
+        for y in range(p):
+            assert evaluate_bivariate(c, x, y, p) == int(x < y)
+
+
+def test_lt_bivariate_sampled_large_p():
+    import random
+
+    from oracle.ltpoly import evaluate_bivariate, lt_bivariate_coefficients
+
+    p = 131
+    c = lt_bivariate_coefficients(p)
+    rnd = random.Random(5)
+    for _ in range(400):
+        x, y = rnd.randrange(p), rnd.randrange(p)
+        assert evaluate_bivariate(c, x, y, p) == int(x < y)
+    for v in (0, 1, 64, 65, 129, 130):  # the edges of the order
+        assert evaluate_bivariate(c, v, v, p) == 0
+        assert evaluate_bivariate(c, v, (v + 1) % p, p) == int(v + 1 < p)
+
+
+def test_lt_bivariate_by_indicator_expansion():
+    """An independent construction: the point indicator at i is
+    1 - (Z - i)^(p-1) (Fermat), expanded by the binomial theorem, and
+    LT = sum_{i<j} 1_i(X) 1_j(Y).  Both constructions agree, the constant
+    terms vanish and the a = 0 row is Y^(p-1)."""
+    from math import comb
+
+    from oracle.ltpoly import lt_bivariate_coefficients
+
+    p = 17
+    ind = []
+    for i in range(p):
+        # (Z - i)^(p-1) = sum_a C(p-1, a) Z^a (-i)^(p-1-a)
+        row = [-(comb(p - 1, a) * pow(-i, p - 1 - a, p)) % p for a in range(p)]
+        row[0] = (row[0] + 1) % p
+        ind.append(row)
+    want = [[0] * p for _ in range(p)]
+    for i in range(p):
+        for j in range(i + 1, p):
+            for a in range(p):
+                for b in range(p):
+                    want[a][b] = (want[a][b] + ind[i][a] * ind[j][b]) % p
+    c = lt_bivariate_coefficients(p)
+    assert c == want
+    assert all(c[a][0] == 0 for a in range(p))
+    assert c[0] == [0] * (p - 1) + [1]
