@@ -55,6 +55,18 @@ SMALL = dict(logN=12, p=17, d=1, L=4, K=1, U=U36, lo=2 ** 35, hi=2 ** 36, pairs=
 
 
 FLUSH_L2 = False
+BIVARIATE = False
+
+
+def use_bivariate_workload():
+    """The C2 ring (N = 2^14, p = 131, 10 + 3 primes, 16 pairs, d = 2) with
+    full digits: values in [0, 131^2), the bivariate circuit."""
+    global METRIC, BIVARIATE
+    BIVARIATE = True
+    W["bivariate"] = True
+    METRIC = "encrypted slot-comparisons/sec at N=2^14,p=131,d=2, full digits (bivariate); batched vs plain"
+    CONFIG["workload"] = ("BGV N=2^14 p=131 d=2 LT+EQ on full digits (values in [0, 131^2), bivariate circuit), "
+                          "16 ciphertext pairs per batch, 10x50-bit + 3 special primes")
 
 
 def use_small_workload():
@@ -100,7 +112,7 @@ def make_values(pairs, ns, seed):
     from paper_2407_07308_gb300 import synth
 
     g = synth.rng(seed + 1000)
-    b = (W["p"] + 1) // 2
+    b = W["p"] if W.get("bivariate") else (W["p"] + 1) // 2
     hi = b ** W["d"]
     xv = synth.values(g, pairs * ns, hi).reshape(pairs, ns)
     yv = synth.values(g, pairs * ns, hi).reshape(pairs, ns)
@@ -152,7 +164,7 @@ def _oracle_pair(i):
     cts = st["cts"][i]
     ev = Evaluator(o, st["rlk"])
     t = time.perf_counter()
-    lt, eq = ev.compare(cts[0::2], cts[1::2], True, True)
+    lt, eq = ev.compare(cts[0::2], cts[1::2], True, True, bivariate=bool(W.get("bivariate")))
     dt = time.perf_counter() - t
     ok = (ss.decode(o.decrypt_coeffs(lt, km.s)) == [int(a < c) for a, c in zip(xv[i], yv[i])]
           and ss.decode(o.decrypt_coeffs(eq, km.s)) == [int(a == c) for a, c in zip(xv[i], yv[i])])
@@ -323,7 +335,8 @@ def run_gpu(args):
         return torch.cuda.Event(enable_timing=True)
 
     # ---- batched form: the whole 16-pair comparison as one captured graph ----
-    plan = fhe.fhe_compare_plan(ctx, evk, xs, ys)
+    plan_flags = fhe.FHE_PLAN_BIVARIATE if BIVARIATE else 0
+    plan = fhe.fhe_compare_plan(ctx, evk, xs, ys, flags=plan_flags)
     outs = [fhe.fhe_plan_result(plan, 0), fhe.fhe_plan_result(plan, 1)]
     fhe.fhe_plan_run(plan, ctx)
     ltd, eqd = fhe.fhe_decrypt(ctx, sk, outs[0]), fhe.fhe_decrypt(ctx, sk, outs[1])
@@ -366,7 +379,7 @@ def run_gpu(args):
     # events hold the last replay's times.  Recorded serially (no parallel
     # branches) so that each event pair brackets one kernel alone. -----------
     fhe.fhe_ctx_profile(ctx, True)
-    pplan = fhe.fhe_compare_plan(ctx, evk, xs, ys, flags=fhe.FHE_PLAN_SERIAL)
+    pplan = fhe.fhe_compare_plan(ctx, evk, xs, ys, flags=fhe.FHE_PLAN_SERIAL | plan_flags)
     fhe.fhe_ctx_profile(ctx, False)
     pe0, pe1 = ev(), ev()
     pe0.record(stream)
@@ -455,8 +468,10 @@ def run_plain(fhe, ctx, evk, xd, yd, enc_each, pairs, ns, stream, ev):
     xs1 = [enc_each(xd[k], 100 + k) for k in range(W["d"])]
     ys1 = [enc_each(yd[k], 200 + k) for k in range(W["d"])]
 
+    compare = fhe.fhe_compare_bivariate if BIVARIATE else fhe.fhe_compare
+
     def plain_one(i):
-        lt, eq = fhe.fhe_compare(ctx, evk, [x[i] for x in xs1], [y[i] for y in ys1])
+        lt, eq = compare(ctx, evk, [x[i] for x in xs1], [y[i] for y in ys1])
         fhe.fhe_ct_destroy(lt)
         fhe.fhe_ct_destroy(eq)
 
@@ -940,8 +955,9 @@ def main():
     ap.add_argument("--pairs", type=int, default=16, help="ciphertext pairs per batch (16 = the workload)")
     ap.add_argument("--no-plain", action="store_true", help="skip the one-request-at-a-time form")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
-    ap.add_argument("--workload", default="compare", choices=["compare", "small", "uneven", "serve", "tournament"],
-                    help="compare: the 16-pair batch (default); small: one pair on the small ring; uneven: "
+    ap.add_argument("--workload", default="compare", choices=["compare", "small", "bivariate", "uneven", "serve", "tournament"],
+                    help="compare: the 16-pair batch (default); small: one pair on the small ring; bivariate: "
+                         "the 16-pair batch on full digits; uneven: "
                          "256 mixed requests; serve: serving loop; tournament: max/min of 4096 values")
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate (requests/s) for serve")
     args = ap.parse_args()
@@ -949,12 +965,16 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.workload == "small":
         use_small_workload()
+    elif args.workload == "bivariate":
+        use_bivariate_workload()
+        W["pairs"] = args.pairs
+        CONFIG["pairs_per_step"] = args.pairs
     else:
         W["pairs"] = args.pairs
         CONFIG["pairs_per_step"] = args.pairs
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload in ("compare", "small"):
+    elif args.workload in ("compare", "small", "bivariate"):
         run_gpu(args)
     elif args.workload == "uneven":
         run_uneven(args)

@@ -233,6 +233,15 @@ int fhe_compare_eq(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, con
 /* Both at once (they share z^(p-1)). */
 int fhe_compare(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
                 fhe_ct **lt, fhe_ct **eq);
+/* The bivariate circuit (Sec. 2.1) on full digits in [0, p), so values of d
+ * digits span [0, p^d): per digit LT_k = sum_a x^a h_a(y), the unique
+ * polynomial of degree <= p-1 in each variable equal to [x < y] on Z_p x Z_p
+ * (h_a = sum_{b>=1} c[a][b] y^b; powers of x and y by squaring and products;
+ * 2(p-2) power products plus one product per row a >= 1), EQ_k =
+ * 1 - (x - y)^(p-1), the same digit merge.  Depth ceil(log2(p-1)) + 1 per
+ * digit.  lt and/or eq as for fhe_compare. */
+int fhe_compare_bivariate(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                          fhe_ct **lt, fhe_ct **eq);
 /* max / min digit-wise: L = LT(x, y); t_k = L (y_k - x_k);
  * max_k = x_k + t_k, min_k = y_k - t_k.  out_max / out_min: d handles each
  * (either may be NULL). */
@@ -248,7 +257,8 @@ int fhe_min(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, const fhe_
 typedef struct fhe_plan fhe_plan;
 
 /* Plan flags. */
-enum { FHE_PLAN_SERIAL = 1 /* record every kernel on one stream (no parallel branches) */ };
+enum { FHE_PLAN_SERIAL = 1,    /* record every kernel on one stream (no parallel branches) */
+       FHE_PLAN_BIVARIATE = 2 /* the bivariate circuit on full digits (fhe_compare_bivariate) */ };
 
 /* Records fhe_compare(x, y) (the LT and/or EQ outputs selected by want_lt /
  * want_eq) as one CUDA graph: one warm run, then a capture.  Independent

@@ -1087,6 +1087,18 @@ extern "C" int fhe_compare(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *
     return e ? e : launch_status(c, "compare");
 }
 
+extern "C" int fhe_compare_bivariate(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x,
+                                     const fhe_ct *const *y, int d, fhe_ct **lt, fhe_ct **eq)
+{
+    CHECK_CTX(c);
+    int e = check_digits(c, evk, x, y, d);
+    if (e) return e;
+    if (!lt && !eq) return FHE_EINVAL;
+    LOCK(c);
+    e = circuit_compare_bv(c, evk, x, y, d, lt, eq);
+    return e ? e : launch_status(c, "compare_bivariate");
+}
+
 extern "C" int fhe_compare_lt(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
                               fhe_ct **out)
 {
@@ -1272,7 +1284,9 @@ extern "C" int fhe_compare_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *co
     c->tracing = false;
     {
         fhe_ct *lt = nullptr, *eq = nullptr;
-        e = circuit_compare(c, evk, x, y, d, want_lt ? &lt : nullptr, want_eq ? &eq : nullptr);
+        e = (flags & FHE_PLAN_BIVARIATE)
+                ? circuit_compare_bv(c, evk, x, y, d, want_lt ? &lt : nullptr, want_eq ? &eq : nullptr)
+                : circuit_compare(c, evk, x, y, d, want_lt ? &lt : nullptr, want_eq ? &eq : nullptr);
         fhe_ct_destroy(lt);
         fhe_ct_destroy(eq);
         if (!e) e = sync_check(c, "plan warm-up");
@@ -1299,7 +1313,9 @@ extern "C" int fhe_compare_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *co
         e = fhe_cuda_check(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed), "begin capture");
         if (!e) {
             c->capturing = !(flags & FHE_PLAN_SERIAL);
-            e = circuit_compare(c, evk, x, y, d, want_lt ? &P->out[0] : nullptr, want_eq ? &P->out[1] : nullptr);
+            e = (flags & FHE_PLAN_BIVARIATE)
+                    ? circuit_compare_bv(c, evk, x, y, d, want_lt ? &P->out[0] : nullptr, want_eq ? &P->out[1] : nullptr)
+                    : circuit_compare(c, evk, x, y, d, want_lt ? &P->out[0] : nullptr, want_eq ? &P->out[1] : nullptr);
             c->capturing = false;
             cudaGraph_t g = nullptr;
             const int e2 = fhe_cuda_check(c, cudaStreamEndCapture(cap, &g), "end capture");

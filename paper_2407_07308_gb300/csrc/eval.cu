@@ -657,16 +657,15 @@ struct Circuit {
     // sum_i c_i lower(x_i, lv): one fused kernel for the scalar products and
     // additions; the trace records them as the individual operations
     // (cmul, cmul, add, cmul, add, ...).
+    // sum_i c_i x_i at level lv (the scalar products and additions of the
+    // schedule, traced as such): chunks of up to 8 terms with one reduction
+    // each, the chunks added in order
     fhe_ct *lincomb(const std::vector<fhe_ct *> &xs, const std::vector<std::pair<int, int>> &terms, int lv)
     {
         if (err) return nullptr;
-        const fhe_ct *low[8];
-        int64_t k[8];
         const int n = (int)xs.size();
-        if (n > 8) {
-            err = fhe_fail(c, FHE_EUNSUPPORTED, "leaf with more than 8 terms");
-            return nullptr;
-        }
+        std::vector<const fhe_ct *> low(n);
+        std::vector<int64_t> k(n);
         for (int i = 0; i < n; i++) {
             low[i] = lower(xs[i], lv);
             if (!low[i]) return nullptr;
@@ -677,7 +676,20 @@ struct Circuit {
         for (int i = 0; i < n && !dag.err; i++)  // inputs of any arity
             if (low[i]->ready && low[i]->on != c->stream)
                 dag.err = fhe_cuda_check(c, cudaStreamWaitEvent(c->stream, low[i]->ready, 0), "dag wait");
-        if ((err = op_lincomb(c, low, k, n, &r))) return nullptr;
+        for (int i0 = 0; i0 < n && !err; i0 += 8) {
+            fhe_ct *part = nullptr;
+            if ((err = op_lincomb(c, low.data() + i0, k.data() + i0, std::min(8, n - i0), &part))) return nullptr;
+            if (!r) {
+                r = part;
+                continue;
+            }
+            fhe_ct *sum = nullptr;
+            err = op_addsub(c, r, part, 0, &sum);
+            fhe_ct_destroy(r);
+            fhe_ct_destroy(part);
+            if (err) return nullptr;
+            r = sum;
+        }
         dag.end(r);
         for (int i = 0; i < n; i++) {
             trace(c, FHE_OP_CMUL, lv);
@@ -751,12 +763,77 @@ struct Circuit {
         if (want_eq) *eq_out = cadd(neg(power(p - 1)), 1);
     }
 
+    // (LT_k, EQ_k) of one pair of full digits in [0, p): the bivariate LT
+    // polynomial sum_a x^a h_a(y), h_a = sum_{b>=1} c[a][b] y^b (no constant
+    // terms), rows in order of a, powers computed when first needed; EQ_k =
+    // 1 - (x - y)^(p-1).  The schedule of the oracle's bivariate circuit.
+    void digit_bv(const fhe_ct *x, const fhe_ct *y, bool want_lt, bool want_eq, fhe_ct **lt_out, fhe_ct **eq_out)
+    {
+        const int p = (int)c->p;
+        *lt_out = *eq_out = nullptr;
+        using Powers = std::map<int, const fhe_ct *>;
+        std::function<const fhe_ct *(Powers &, int)> power = [&](Powers &pw, int n) -> const fhe_ct * {
+            auto it = pw.find(n);
+            if (it != pw.end()) return it->second;
+            const fhe_ct *r;
+            if ((n & (n - 1)) == 0) {
+                const fhe_ct *h = power(pw, n / 2);
+                r = mul(h, h);
+            } else {
+                int a = 1;
+                while (a * 2 < n) a *= 2;
+                const fhe_ct *A = power(pw, a);
+                const fhe_ct *Bp = power(pw, n - a);
+                r = mul(A, Bp);
+            }
+            pw[n] = r;
+            return r;
+        };
+        if (want_lt) {
+            if (c->ltbv.empty()) lt_bivariate_coefficients(p, c->ltbv);
+            const std::vector<int> &cf = c->ltbv;
+            Powers px, py;
+            px[1] = x;
+            py[1] = y;
+            fhe_ct *acc = nullptr;
+            for (int a = 0; a < p && !err; a++) {
+                std::vector<std::pair<int, int>> terms;
+                for (int b = 1; b < p; b++)
+                    if (cf[(size_t)a * p + b]) terms.push_back({b, cf[(size_t)a * p + b]});
+                if (terms.empty()) continue;
+                std::vector<fhe_ct *> cts;
+                for (auto &t : terms) cts.push_back(const_cast<fhe_ct *>(power(py, t.first)));
+                if (err) return;
+                int lv = 1 << 30;
+                for (auto *t : cts) lv = std::min(lv, t->level);
+                fhe_ct *h = lincomb(cts, terms, lv);
+                fhe_ct *term = h;
+                if (a > 0) {
+                    const fhe_ct *xa = power(px, a);
+                    term = mul(xa, h);
+                }
+                acc = acc ? add(acc, term) : term;
+            }
+            *lt_out = acc;
+        }
+        if (want_eq) {
+            Powers pz;
+            pz[1] = sub(x, y);
+            if (!pz[1]) return;
+            *eq_out = cadd(neg(power(pz, p - 1)), 1);
+        }
+    }
+
     void compare(const fhe_ct *const *xs, const fhe_ct *const *ys, int d, bool want_lt, bool want_eq,
-                 fhe_ct **lt, fhe_ct **eq)
+                 fhe_ct **lt, fhe_ct **eq, bool bivariate = false)
     {
         std::vector<std::pair<fhe_ct *, fhe_ct *>> nodes(d, {nullptr, nullptr});
-        for (int k = 0; k < d && !err; k++)
-            digit(xs[k], ys[k], want_lt, d > 1 || want_eq, &nodes[k].first, &nodes[k].second);
+        for (int k = 0; k < d && !err; k++) {
+            if (bivariate)
+                digit_bv(xs[k], ys[k], want_lt, d > 1 || want_eq, &nodes[k].first, &nodes[k].second);
+            else
+                digit(xs[k], ys[k], want_lt, d > 1 || want_eq, &nodes[k].first, &nodes[k].second);
+        }
         while (nodes.size() > 1 && !err) {
             const bool root = nodes.size() == 2;
             std::vector<std::pair<fhe_ct *, fhe_ct *>> nxt;
@@ -813,6 +890,15 @@ int circuit_multi(fhe_ctx *c, const fhe_evk *evk, const std::vector<MultiItem> &
         else
             C.compare(it.x, it.y, it.d, it.out0 != nullptr, it.out1 != nullptr, it.out0, it.out1);
     }
+    C.finish();
+    return C.err;
+}
+
+int circuit_compare_bv(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                       fhe_ct **lt, fhe_ct **eq)
+{
+    Circuit C(c, evk);
+    C.compare(x, y, d, lt != nullptr, eq != nullptr, lt, eq, true);
     C.finish();
     return C.err;
 }

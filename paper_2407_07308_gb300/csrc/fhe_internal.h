@@ -171,6 +171,7 @@ struct fhe_ctx {
     u64 zeta = 0, gamma = 0;       // primitive 2M-th root / sqrt(-2) mod p
     std::vector<int> slot_exp;     // slot s <-> zeta^slot_exp[s] (linear case)
     std::vector<int> lt;           // LT polynomial coefficients c_0..c_{p-1}
+    std::vector<int> ltbv;         // bivariate LT coefficients c[a p + b] (built on first use)
 
     int ntt_variant = 0;        // NTT factorisation chosen by the autotuner
     float ntt_ms[3] = {0, 0, 0};  // timings of each variant (forward + inverse, per batch; 0 = n/a)
@@ -288,6 +289,7 @@ u64 host_invmod(u64 a, u64 q);
 u64 host_mulmod(u64 a, u64 b, u64 q);
 int build_tables(fhe_ctx *ctx);
 void lt_poly_coefficients(int p, std::vector<int> &out);
+void lt_bivariate_coefficients(int p, std::vector<int> &out);
 
 // kernel launchers (ntt.cu, kernels.cu)
 void launch_ntt_fwd_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs);
@@ -356,6 +358,8 @@ int op_relin(fhe_ctx *c, const KeySwitchKey &k, const fhe_ct *d, fhe_ct **out);
 int op_rotate(fhe_ctx *c, const KeySwitchKey &k, const fhe_ct *a, fhe_ct **out);
 int op_mul_relin(fhe_ctx *c, const KeySwitchKey &rlk, const fhe_ct *a, const fhe_ct *b, fhe_ct **out);
 int galois_perm(fhe_ctx *c, int64_t g, const int **perm);
+int circuit_compare_bv(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
+                       fhe_ct **lt, fhe_ct **eq);
 int circuit_compare(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
                     fhe_ct **lt, fhe_ct **eq);
 int circuit_max_min(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,

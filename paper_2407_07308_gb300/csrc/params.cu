@@ -97,6 +97,38 @@ void lt_poly_coefficients(int p, std::vector<int> &out)
     }
 }
 
+// Bivariate LT on full digits: c[a p + b] with sum c x^a y^b = [x < y] on
+// Z_p x Z_p.  The indicator of the point i is 1 - (Z - i)^(p-1) (Fermat),
+// expanded by the binomial theorem; LT = sum_{i<j} 1_i(X) 1_j(Y), summed as
+// sum_i 1_i(X) S_{i+1}(Y) with S_k the suffix sums of the indicators.
+void lt_bivariate_coefficients(int p, std::vector<int> &out)
+{
+    const u64 P = (u64)p;
+    std::vector<u64> binom(p);  // C(p-1, a) mod p
+    binom[0] = 1;
+    for (int a = 1; a < p; a++)
+        binom[a] = host_mulmod(host_mulmod(binom[a - 1], (P - 1 - (a - 1)) % P, P), host_invmod((u64)a, P), P);
+    std::vector<std::vector<u64>> ind(p, std::vector<u64>(p, 0));
+    for (int i = 0; i < p; i++) {
+        const u64 mi = (P - (u64)i) % P;  // -i
+        for (int a = 0; a < p; a++) {
+            const u64 t = host_mulmod(binom[a], host_powmod(mi, (u64)(p - 1 - a), P), P);
+            ind[i][a] = (P - t) % P;
+        }
+        ind[i][0] = (ind[i][0] + 1) % P;
+    }
+    out.assign((size_t)p * p, 0);
+    std::vector<u64> suffix(p, 0);
+    for (int i = p - 1; i >= 0; i--) {
+        for (int a = 0; a < p; a++) {
+            if (!ind[i][a]) continue;
+            for (int b = 0; b < p; b++)
+                if (suffix[b]) out[(size_t)a * p + b] = (int)((out[(size_t)a * p + b] + ind[i][a] * suffix[b]) % P);
+        }
+        for (int b = 0; b < p; b++) suffix[b] = (suffix[b] + ind[i][b]) % P;
+    }
+}
+
 static int two_adic(u64 x)
 {
     int v = 0;

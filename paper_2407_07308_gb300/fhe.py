@@ -148,6 +148,7 @@ def lib() -> ctypes.CDLL:
             "fhe_job_footprint": (ctypes.c_uint64, [vp]),
             "fhe_ctx_inject_alloc_failure": (ci, [vp, ctypes.c_int64]),
             "fhe_ctx_trim": (ci, [vp]),
+            "fhe_compare_bivariate": (ci, [vp, vp, vp, vp, ci, POINTER(vp), POINTER(vp)]),
             "fhe_probe_int_peak": (ci, [POINTER(ctypes.c_double), POINTER(ctypes.c_double)]),
             "fhe_ctx_fused_modswitch": (ci, [vp, ci]),
             "fhe_ctx_set_batch_graphs": (ci, [vp, ci]),
@@ -475,6 +476,15 @@ def fhe_compare_eq(ctx, evk, xs, ys):
     return out
 
 
+def fhe_compare_bivariate(ctx, evk, xs, ys, want_lt=True, want_eq=True):
+    """LT / EQ of full digits in [0, p) by the bivariate circuit."""
+    lt, eq = c_void_p(), c_void_p()
+    _check(lib().fhe_compare_bivariate(ctx, evk, _handles(xs), _handles(ys), len(xs),
+                                       ctypes.byref(lt) if want_lt else None, ctypes.byref(eq) if want_eq else None),
+           ctx)
+    return (lt if want_lt else None), (eq if want_eq else None)
+
+
 def fhe_max_min(ctx, evk, xs, ys):
     d = len(xs)
     mx, mn = (c_void_p * d)(), (c_void_p * d)()
@@ -483,6 +493,7 @@ def fhe_max_min(ctx, evk, xs, ys):
 
 
 FHE_PLAN_SERIAL = 1
+FHE_PLAN_BIVARIATE = 2
 
 
 def fhe_compare_plan(ctx, evk, xs, ys, want_lt=True, want_eq=True, flags=0):

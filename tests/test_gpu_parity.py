@@ -460,3 +460,39 @@ def test_multi_level_switch_equals_single_steps(logN, p, L, K):
         assert np.array_equal(g.decrypt(direct), np.array(rows, dtype=np.uint64))
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("logN,p,L,K,d,count", [(10, 17, 8, 2, 2, 3), (10, 131, 10, 3, 1, 2)])
+def test_compare_bivariate_full_digits_bitexact(logN, p, L, K, d, count):
+    """The bivariate circuit on full digits in [0, p): LT and EQ of values
+    in [0, p^d) decrypt to the plaintext comparison for every ciphertext of
+    the batch; ciphertext 0 is bit-exact with the oracle and the op traces
+    are equal."""
+    fhe = _fhe()
+    params = dict(logN=logN, p=p, L=L, K=K, **CHAIN50)
+    o, g = _pair(params, seed=19)
+    try:
+        rnd = random.Random(p + d)
+        xv, yv = zip(*[_values(rnd, g.ns, p ** d) for _ in range(count)])
+        xd = [[_digits(xv[c], p, d)[k] for c in range(count)] for k in range(d)]
+        yd = [[_digits(yv[c], p, d)[k] for c in range(count)] for k in range(d)]
+        xg = [g.encrypt_slots(xd[k], seed=300 + k) for k in range(d)]
+        yg = [g.encrypt_slots(yd[k], seed=400 + k) for k in range(d)]
+        fhe.fhe_trace_enable(g.ctx, True)
+        lt_g, eq_g = fhe.fhe_compare_bivariate(g.ctx, g.evk, xg, yg)
+        g.own(lt_g)
+        g.own(eq_g)
+        trace_g = fhe.fhe_trace_get(g.ctx)
+        lt_dec, eq_dec = g.decrypt(lt_g), g.decrypt(eq_g)
+        for c in range(count):
+            assert lt_dec[c].tolist() == [int(a < e) for a, e in zip(xv[c], yv[c])]
+            assert eq_dec[c].tolist() == [int(a == e) for a, e in zip(xv[c], yv[c])]
+        xo = [o.encrypt_slots(xd[k], seed=300 + k)[0] for k in range(d)]
+        yo = [o.encrypt_slots(yd[k], seed=400 + k)[0] for k in range(d)]
+        ev = o.evaluator()
+        lt_o, eq_o = ev.compare(xo, yo, True, True, bivariate=True)
+        assert trace_g == ev.trace
+        _same(lt_o, g.export(lt_g), 0)
+        _same(eq_o, g.export(eq_g), 0)
+    finally:
+        g.close()
