@@ -224,6 +224,33 @@ class Oracle:
         self.L_.orc_add_const(self.h, _p(a.data), int(k), a.level, _p(out))
         return Ct(out, a.level)
 
+    # ---- plaintext operands (slot vectors encoded as polynomials) ---------------
+    def _plain_limbs(self, m, level: int):
+        """The plaintext coefficients (integers), centred into (-p/2, p/2],
+        reduced mod every q_i of the level."""
+        mc = [int(v) % self.p for v in m]
+        mc = [v - self.p if v > self.p // 2 else v for v in mc]
+        return [np.array([v % q for v in mc], dtype=np.uint64) for q in self.primes[:level]]
+
+    def add_plain(self, a: Ct, m, sign: int = 1) -> Ct:
+        """c0 +- m (m the plaintext coefficients)."""
+        assert a.npoly == 2
+        out = a.data.copy()
+        for i, mi in enumerate(self._plain_limbs(m, a.level)):
+            q = int(self.primes[i])
+            c0 = out[0, i].astype(object)
+            out[0, i] = np.array([(int(x) + sign * int(y)) % q for x, y in zip(c0, mi)], dtype=np.uint64)
+        return Ct(out, a.level)
+
+    def mul_plain(self, a: Ct, m) -> Ct:
+        """Every polynomial times m in R_q (negacyclic product per limb)."""
+        out = self._new(a.npoly, a.level)
+        limbs = self._plain_limbs(m, a.level)
+        for j in range(a.npoly):
+            for i in range(a.level):
+                out[j, i] = self.polymul(i, a.data[j, i], limbs[i])
+        return Ct(out, a.level)
+
     def tensor(self, a: Ct, b: Ct) -> Ct:
         assert a.level == b.level and a.npoly == 2 and b.npoly == 2
         out = self._new(3, a.level)

@@ -48,6 +48,16 @@ them) are:
     term x^a h_a (for a = 0 the term is h_a), accumulated in order of a;
     EQ_k = 1 - (x - y)^(p-1);
 
+  * plaintext operands (slot vectors) are encoded and their coefficients
+    lifted to (-p/2, p/2] before reduction mod q_i; ct + pt and ct - pt touch
+    c0 only, ct * pt multiplies both polynomials; no level is consumed;
+  * sorting (p = 1 mod 4, the rows of cols = n_s / 2 columns sorted
+    independently): rank_i = sum_{s=1}^{cols-1} (LT(x_{i+s}, x_i) +
+    w_s[i] EQ(x_{i+s}, x_i)) with x_{i+s} = sigma_{5^s}(x) and the tie-break
+    mask w_s[i] = [i + s >= cols] (equal values keep their order); then
+    out = sum_{s=0}^{cols-1} EQ(sigma_{5^s}(rank) - idx) sigma_{5^s}(x) per
+    digit (idx[i] = i, EQ(u) = 1 - u^(p-1)), shifts in increasing order;
+
 Every operation appends (name, level) to ``trace``; the CUDA path emits the
 same trace, and a test compares them.  The multiplication count is pinned
 against the Paterson-Stockmeyer count (8 / 23 / 30 for p = 17 / 131 / 257) and
@@ -56,6 +66,7 @@ the depth against ceil(log2(p-1)).
 from __future__ import annotations
 
 from .bgv import Ct, Oracle
+from .encoding import SlotStructure
 from .ltpoly import lt_bivariate_coefficients, lt_coefficients
 
 
@@ -131,6 +142,23 @@ class Evaluator:
     def rotate(self, a: Ct, g: int) -> Ct:
         self.trace.append(("rot", a.level))
         return self.o.rotate(a, g, self.gk[g])
+
+    def _slots(self) -> SlotStructure:
+        if not hasattr(self, "_ss"):
+            self._ss = SlotStructure(self.p, self.o.N)
+        return self._ss
+
+    def add_plain(self, a: Ct, slots) -> Ct:
+        self.trace.append(("padd", a.level))
+        return self.o.add_plain(a, self._slots().encode(slots), 1)
+
+    def sub_plain(self, a: Ct, slots) -> Ct:
+        self.trace.append(("psub", a.level))
+        return self.o.add_plain(a, self._slots().encode(slots), -1)
+
+    def mul_plain(self, a: Ct, slots) -> Ct:
+        self.trace.append(("pmul", a.level))
+        return self.o.mul_plain(a, self._slots().encode(slots))
 
     def mul_count(self) -> int:
         return sum(1 for t in self.trace if t[0] == "mul")
@@ -274,6 +302,55 @@ class Evaluator:
             mx.append(self.add(x, t))
             mn.append(self.sub(y, t))
         return mx, mn
+
+
+def sort_galois(p: int, N: int) -> list:
+    """Galois elements the sort needs: sigma_{5^s}, s = 1 .. cols-1."""
+    ss = SlotStructure(p, N)
+    cols = ss.ns // 2
+    return [pow(5, s, 2 * N) for s in range(1, cols)]
+
+
+def sort_rows(ev: "Evaluator", xs):
+    """Digits (least significant first) of every row's values in increasing
+    order; xs: the d digit ciphertexts (univariate digits)."""
+    ss = ev._slots()
+    assert ss.kind == "linear" and ss.ns >= 4, "sorting needs p = 1 mod 4 and two columns or more"
+    p, cols, twoN = ev.p, ss.ns // 2, 2 * ev.o.N
+    rank = None
+    for s in range(1, cols):
+        g = pow(5, s, twoN)
+        xr = [ev.rotate(x, g) for x in xs]
+        lt, eq = ev.compare(xr, xs, True, True)
+        w = [1 if c + s >= cols else 0 for _ in range(2) for c in range(cols)]
+        t = ev.add(lt, ev.mul_plain(eq, w))
+        rank = t if rank is None else ev.add(rank, t)
+    idx = [c for _ in range(2) for c in range(cols)]
+    outs = [None] * len(xs)
+    for s in range(cols):
+        g = pow(5, s, twoN)
+        rr = ev.rotate(rank, g) if s else rank
+        xr = [ev.rotate(x, g) for x in xs] if s else list(xs)
+        u = ev.sub_plain(rr, idx)
+        pw = {1: u}
+
+        def power(n: int) -> Ct:
+            if n in pw:
+                return pw[n]
+            if n & (n - 1) == 0:
+                h = power(n // 2)
+                r = ev.mul(h, h)
+            else:
+                a = 1 << (n.bit_length() - 1)
+                r = ev.mul(power(a), power(n - a))
+            pw[n] = r
+            return r
+
+        e = ev.add_const(ev.neg(power(p - 1)), 1)
+        for k in range(len(xs)):
+            t = ev.mul(e, xr[k])
+            outs[k] = t if outs[k] is None else ev.add(outs[k], t)
+    return outs
 
 
 def round_depth(p: int, d: int) -> int:

@@ -284,3 +284,42 @@ def test_compare_bivariate_full_digits_small_ring():
     rows = sum(1 for a in range(1, p) if any(c[a][1:]))
     per_digit = 2 * (p - 2) + rows + 4  # powers of x and y, row products, z^16 by four squarings
     assert ev.mul_count() == d * per_digit + 2 * (d - 1)
+
+
+def test_plaintext_operands():
+    """ct + pt, ct - pt and ct * pt decrypt to the slot-wise sum, difference
+    and product mod p."""
+    p = 17
+    st = OracleSetup(logN=8, p=p, L=3, K=2, seed=24, **CHAIN50)
+    ns = st.ss.ns
+    rnd = random.Random(2)
+    a = [rnd.randrange(p) for _ in range(ns)]
+    v = [rnd.randrange(p) for _ in range(ns)]
+    x = st.encrypt_slots([a], seed=60)[0]
+    ev = st.evaluator()
+    assert st.decrypt_slots(ev.add_plain(x, v)) == [(u + w) % p for u, w in zip(a, v)]
+    assert st.decrypt_slots(ev.sub_plain(x, v)) == [(u - w) % p for u, w in zip(a, v)]
+    assert st.decrypt_slots(ev.mul_plain(x, v)) == [(u * w) % p for u, w in zip(a, v)]
+    assert [t[0] for t in ev.trace] == ["padd", "psub", "pmul"]
+
+
+def test_sort_rows_small_ring():
+    """Every row of cols = 4 values (2 digits of base 9, ties included)
+    comes out in increasing order."""
+    from oracle.circuits import sort_galois, sort_rows
+
+    p, d = 17, 2
+    N = 2 ** 8
+    st = OracleSetup(logN=8, p=p, L=11, K=2, seed=25, galois=sort_galois(p, N), **CHAIN50)
+    ns = st.ss.ns
+    b = (p + 1) // 2
+    rnd = random.Random(4)
+    vals = [rnd.randrange(b ** d) for _ in range(ns)]
+    vals[1] = vals[2]  # a tie in row 0
+    x = [st.encrypt_slots([dg], seed=70 + k)[0] for k, dg in enumerate(_digits(vals, b, d))]
+    ev = st.evaluator()
+    out = sort_rows(ev, x)
+    got = [sum(st.decrypt_slots(out[k])[s] * b ** k for k in range(d)) for s in range(ns)]
+    cols = ns // 2
+    assert got == sorted(vals[:cols]) + sorted(vals[cols:])
+    assert st.o.noise_bits(out[0], st.s) < np.log2(st.o.primes[0]) - 1
