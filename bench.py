@@ -944,6 +944,75 @@ def run_tournament(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sort(args):
+    """Sorting on the C4 ring (N = 2^15, p = 257, 20 x 50-bit + 4 special
+    primes): 16 ciphertexts of 2 rows x 64 values (2 digits of base 129,
+    10% duplicates), every row sorted on its own.  One step sorts the batch."""
+    import numpy as np
+    import torch
+
+    from paper_2407_07308_gb300 import fhe, synth
+
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    ctx = fhe.fhe_ctx_create(15, 257, 20, 4, U50, 2 ** 49, 2 ** 50, allocator=fhe.torch_allocator(local),
+                             stream=stream.cuda_stream)
+    sk, pk = fhe.fhe_keygen(ctx, 6)
+    evk = fhe.fhe_evk_create(ctx, sk, fhe.fhe_sort_galois(ctx), 7)
+    ns = fhe.fhe_ctx_info(ctx).slots
+    count, b, d = 16, 129, 2
+    g = synth.rng(6)
+    vals = synth.values_with_duplicates(g, count * ns, b ** d, 0.10).reshape(count, ns)
+    dig = synth.to_digits(vals.ravel(), b, d)
+    xs = [fhe.fhe_encrypt(ctx, pk, dig[k].reshape(count, ns).astype(np.uint64), 100 + k) for k in range(d)]
+    cols = ns // 2
+
+    def one(check=False):
+        out = fhe.fhe_sort(ctx, evk, xs)
+        if check:
+            got = sum(fhe.fhe_decrypt(ctx, sk, out[k]).astype(np.int64) * b ** k for k in range(d))
+            want = np.concatenate([np.sort(vals[:, :cols], axis=1), np.sort(vals[:, cols:], axis=1)], axis=1)
+            assert (got == want).all(), "sort mismatch"
+        for h in out:
+            fhe.fhe_ct_destroy(h)
+
+    one(check=True)
+    for _ in range(args.warmup - 1):
+        one()
+    fhe.fhe_ctx_sync(ctx)
+    l0 = fhe.fhe_ctx_launches(ctx)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        evs[0].record(stream)
+        for i in range(args.steps):
+            one()
+            evs[i + 1].record(stream)
+        stream.synchronize()
+    launches = fhe.fhe_ctx_launches(ctx) - l0
+    total = evs[0].elapsed_time(evs[-1])
+    line = {
+        "metric": "encrypted values sorted per second (rows of 64 values, N=2^15, p=257)",
+        "value": round(count * ns * args.steps / (total / 1e3), 1), "unit": "values/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded BGV keys, noise and values, 10% duplicates)",
+        "config": {"workload": "16 ciphertexts x 2 rows x 64 values in [0, 129^2), each row sorted: ranks from 63 "
+                               "column-shift comparisons with a tie-break mask, then rank-matching selection; "
+                               "20x50-bit + 4 special primes, 63 rotation keys",
+                   "values_per_step": count * ns, "l2": "ciphertexts 336 MB per digit > L2"},
+        "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": None, "roofline": None, "e2e": None,
+    }
+    for h in xs:
+        fhe.fhe_ct_destroy(h)
+    fhe.fhe_evk_destroy(evk)
+    fhe.fhe_sk_destroy(sk)
+    fhe.fhe_pk_destroy(pk)
+    fhe.fhe_ctx_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -955,10 +1024,11 @@ def main():
     ap.add_argument("--pairs", type=int, default=16, help="ciphertext pairs per batch (16 = the workload)")
     ap.add_argument("--no-plain", action="store_true", help="skip the one-request-at-a-time form")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
-    ap.add_argument("--workload", default="compare", choices=["compare", "small", "bivariate", "uneven", "serve", "tournament"],
+    ap.add_argument("--workload", default="compare", choices=["compare", "small", "bivariate", "uneven", "serve", "tournament", "sort"],
                     help="compare: the 16-pair batch (default); small: one pair on the small ring; bivariate: "
                          "the 16-pair batch on full digits; uneven: "
-                         "256 mixed requests; serve: serving loop; tournament: max/min of 4096 values")
+                         "256 mixed requests; serve: serving loop; tournament: max/min of 4096 values; sort: rows of 64 "
+                         "values sorted")
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate (requests/s) for serve")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -982,6 +1052,8 @@ def main():
         run_serve(args)
     elif args.workload == "tournament":
         run_tournament(args)
+    elif args.workload == "sort":
+        run_sort(args)
     else:
         run_gpu(args)
 

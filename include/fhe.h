@@ -296,6 +296,29 @@ int fhe_tournament_galois(const fhe_ctx *ctx, int64_t *galois, int cap);
 int fhe_tournament(fhe_ctx *ctx, const fhe_evk *evk, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct *const *x,
                    int d, uint64_t seed, fhe_ct **out_max, fhe_ct **out_min);
 
+/* ---- plaintext operands and sorting --------------------------------------------- */
+
+/* ct + pt, ct - pt, ct * pt for one plaintext slot vector `slots` (n_s
+ * values, host array, reduced mod p) applied to every ciphertext of the
+ * batch.  The encoding's coefficients are lifted to (-p/2, p/2] before
+ * reduction mod q_i; + and - change c0 only; no level is consumed. */
+int fhe_add_plain(fhe_ctx *ctx, const fhe_ct *a, const uint64_t *slots, fhe_ct **out);
+int fhe_sub_plain(fhe_ctx *ctx, const fhe_ct *a, const uint64_t *slots, fhe_ct **out);
+int fhe_mul_plain(fhe_ctx *ctx, const fhe_ct *a, const uint64_t *slots, fhe_ct **out);
+
+/* Sorting (the paper's sort application, Sec. 6): every row of cols = n_s / 2
+ * slots of every ciphertext is sorted on its own, in increasing order, its
+ * values given as d univariate digit handles x[0..d-1] (least significant
+ * first).  rank_i counts the row's values below x_i, and equal values
+ * earlier in the row: the sum over column shifts s of LT(x_{i+s}, x_i) plus
+ * the plaintext tie-break mask [i + s >= cols] times EQ(x_{i+s}, x_i); the
+ * sorted row is the sum over shifts of EQ(rank_{i+s} - i) x_{i+s}, EQ(u) =
+ * 1 - u^(p-1) (exact because ranks are below cols <= p).  Needs p = 1 mod 4,
+ * cols >= 2 and the column rotations of fhe_sort_galois in evk; consumes
+ * the comparison's depth + ceil(log2(p-1)) + 1 levels.  out: d new handles. */
+int fhe_sort_galois(const fhe_ctx *ctx, int64_t *galois, int cap);
+int fhe_sort(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, int d, fhe_ct **out);
+
 /* ---- batches of uneven requests ------------------------------------------------- */
 
 enum { FHE_JOB_COMPARE = 1, /* out0 -> &LT handle, out1 -> &EQ handle (either NULL) */
@@ -406,7 +429,7 @@ int fhe_server_stop(fhe_server *server);
 
 /* Op codes recorded while tracing is on. */
 enum { FHE_OP_MUL = 1, FHE_OP_ADD = 2, FHE_OP_SUB = 3, FHE_OP_CMUL = 4, FHE_OP_CADD = 5, FHE_OP_NEG = 6,
-       FHE_OP_ROT = 7 };
+       FHE_OP_ROT = 7, FHE_OP_PADD = 8, FHE_OP_PSUB = 9, FHE_OP_PMUL = 10 };
 /* on != 0 clears and starts recording circuit-level operations. */
 int fhe_trace_enable(fhe_ctx *ctx, int on);
 /* Copies up to cap entries (op code, level of the operands); returns the

@@ -310,6 +310,8 @@ int sync_check(fhe_ctx *c, const char *where)
 
 }  // namespace
 
+void encode_slot_vector(const fhe_ctx *c, const uint64_t *v, int64_t *m) { encode_slots(c, v, m); }
+
 // Stream tags of the seeded samplers (see sample.cu).
 enum { TAG_S = 1, TAG_E_PK = 2, TAG_A_PK = 3, TAG_U = 16, TAG_E0 = 17, TAG_E1 = 18, TAG_KSK = 1024 };
 
@@ -1097,6 +1099,51 @@ extern "C" int fhe_compare_bivariate(fhe_ctx *c, const fhe_evk *evk, const fhe_c
     LOCK(c);
     e = circuit_compare_bv(c, evk, x, y, d, lt, eq);
     return e ? e : launch_status(c, "compare_bivariate");
+}
+
+static int plain_api(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, int kind, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!same_ctx(c, a) || !slots || !out) return FHE_EINVAL;
+    for (int i = 0; i < c->ns; i++)
+        if (slots[i] >= c->p) return fhe_fail(c, FHE_EINVAL, "plaintext slot value not below p");
+    LOCK(c);
+    const int e = op_plain(c, a, slots, kind, out);
+    return e ? e : launch_status(c, "plaintext operation");
+}
+
+extern "C" int fhe_add_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, fhe_ct **out)
+{
+    return plain_api(c, a, slots, 0, out);
+}
+
+extern "C" int fhe_sub_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, fhe_ct **out)
+{
+    return plain_api(c, a, slots, 1, out);
+}
+
+extern "C" int fhe_mul_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, fhe_ct **out)
+{
+    return plain_api(c, a, slots, 2, out);
+}
+
+extern "C" int fhe_sort_galois(const fhe_ctx *c, int64_t *galois, int cap)
+{
+    if (!c || cap < 0) return FHE_EINVAL;
+    const std::vector<int64_t> g = sort_galois(c);
+    for (int i = 0; i < (int)g.size() && i < cap; i++) galois[i] = g[i];
+    return (int)g.size();
+}
+
+extern "C" int fhe_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int d, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!out) return FHE_EINVAL;
+    int e = check_digits(c, evk, x, x, d);
+    if (e) return e;
+    LOCK(c);
+    e = circuit_sort(c, evk, x, d, out);
+    return e ? e : launch_status(c, "sort");
 }
 
 extern "C" int fhe_compare_lt(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,

@@ -415,6 +415,61 @@ int op_mul_relin(fhe_ctx *c, const KeySwitchKey &rlk, const fhe_ct *a, const fhe
     return 0;
 }
 
+// Plaintext operand: the slot vector v (n_s values) encoded, its coefficients
+// lifted to (-p/2, p/2], reduced mod q_0 .. q_{level-1} and transformed:
+// [level][N] in the NTT domain, in the ciphertext `out` (count 1, one poly).
+static int plain_ntt(fhe_ctx *c, const uint64_t *v, int level, fhe_ct **out)
+{
+    const int N = c->N;
+    std::vector<int64_t> m(N);
+    encode_slot_vector(c, v, m.data());
+    const int64_t p = (int64_t)c->p;
+    for (int64_t &x : m) {
+        x %= p;
+        if (x < 0) x += p;
+        if (x > p / 2) x -= p;
+    }
+    int err = 0;
+    fhe_ct *r = ct_new(c, 1, 1, level, &err);
+    if (!r) return err;
+    Tmp t(c, (size_t)N, &err);
+    if (err) {
+        fhe_ct_destroy(r);
+        return err;
+    }
+    // pageable source: the copy is staged before the call returns
+    cudaMemcpyAsync(t.p, m.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, c->stream);
+    std::vector<int> primes(level);
+    for (int i = 0; i < level; i++) primes[i] = i;
+    launch_rns_from_i64(c, (const int64_t *)t.p, nullptr, 1, r->d, 1, level, primes.data());
+    LimbMap lm = identity_map(level, (long long)level * N, (long long)level * N, 0, 0, 0);
+    launch_ntt_fwd_plain(c, r->d, r->d, lm, level);
+    *out = r;
+    return 0;
+}
+
+// ct (+ | - | *) plaintext slot vector (kind 0 / 1 / 2); no level is consumed.
+int op_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, int kind, fhe_ct **out)
+{
+    if (kind < 0 || kind > 2 || (kind < 2 && a->npoly != 2)) return fhe_fail(c, FHE_EINVAL, "plaintext operation");
+    fhe_ct *m = nullptr;
+    int err = plain_ntt(c, slots, a->level, &m);
+    if (err) return err;
+    fhe_ct *r = ct_new(c, a->count, a->npoly, a->level, &err);
+    if (r) {
+        if (kind == 2) {
+            launch_mul_poly(c, a->d, m->d, r->d, a->count * a->npoly, a->level, 0);
+        } else {
+            cudaMemcpyAsync(r->d, a->d, a->bytes, cudaMemcpyDeviceToDevice, c->stream);
+            launch_add_plain(c, a->d, m->d, r->d, a->count, a->npoly, a->level, kind);
+        }
+    }
+    fhe_ct_destroy(m);
+    if (!r) return err;
+    *out = r;
+    return 0;
+}
+
 // ---------------------------------------------------------------------------
 // comparison circuits
 // ---------------------------------------------------------------------------
@@ -651,6 +706,32 @@ struct Circuit {
         if ((err = op_neg(c, a, &r))) return nullptr;
         dag.end(r);
         trace(c, FHE_OP_NEG, a->level);
+        return keep(r);
+    }
+
+    fhe_ct *rot(const fhe_ct *a, int64_t g)
+    {
+        if (err || !a) return nullptr;
+        const KeySwitchKey *key = evk->find(g);
+        if (!key) {
+            err = fhe_fail(c, FHE_ENOKEY, "no rotation key for this Galois element");
+            return nullptr;
+        }
+        fhe_ct *r = nullptr;
+        dag.begin({a});
+        if ((err = op_rotate(c, *key, a, &r))) return nullptr;
+        dag.end(r);
+        trace(c, FHE_OP_ROT, a->level);
+        return keep(r);
+    }
+    fhe_ct *plain(const fhe_ct *a, const std::vector<uint64_t> &slots, int kind)
+    {
+        if (err || !a) return nullptr;
+        fhe_ct *r = nullptr;
+        dag.begin({a});
+        if ((err = op_plain(c, a, slots.data(), kind, &r))) return nullptr;
+        dag.end(r);
+        trace(c, kind == 0 ? FHE_OP_PADD : kind == 1 ? FHE_OP_PSUB : FHE_OP_PMUL, a->level);
         return keep(r);
     }
 
@@ -1063,6 +1144,109 @@ struct Tourney {
 };
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// sorting (rows of cols = n_s / 2 columns, each row on its own)
+// ---------------------------------------------------------------------------
+//
+// The oracle's schedule: for shifts s = 1 .. cols-1, x_s = sigma_{5^s}(x)
+// (column i holds x_{i+s}), (LT, EQ) = compare(x_s, x), rank += LT + w_s EQ
+// with the plaintext tie-break mask w_s[i] = [i + s >= cols]; then for shifts
+// s = 0 .. cols-1, e = 1 - (sigma_{5^s}(rank) - idx)^(p-1) (idx[i] = i) and
+// out_k += e sigma_{5^s}(x_k) for every digit k.
+
+std::vector<int64_t> sort_galois(const fhe_ctx *c)
+{
+    std::vector<int64_t> g;
+    if (!c->slots_linear || c->ns < 4) return g;
+    const int64_t twoN = 2 * (int64_t)c->N;
+    for (int s = 1; s < c->ns / 2; s++) g.push_back((int64_t)host_powmod(5, (u64)s, (u64)twoN));
+    return g;
+}
+
+// Each shift runs in a circuit of its own, so that its temporaries are
+// freed before the next one; only the running rank and outputs are carried.
+int circuit_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int d, fhe_ct **out)
+{
+    if (!c->slots_linear || c->ns < 4)
+        return fhe_fail(c, FHE_EUNSUPPORTED, "sorting needs p = 1 mod 4 (two columns or more)");
+    const int cols = c->ns / 2, p = (int)c->p;
+    const std::vector<int64_t> gs = sort_galois(c);
+    std::vector<const fhe_ct *> xs(x, x + d);
+    fhe_ct *rank = nullptr;
+    std::vector<fhe_ct *> outs(d, nullptr);
+    int err = 0;
+    auto carry = [](fhe_ct *&held, fhe_ct *next) {
+        if (held) fhe_ct_destroy(held);
+        held = next;
+    };
+    for (int s = 1; s < cols && !err; s++) {
+        Circuit S(c, evk);
+        std::vector<const fhe_ct *> xr(d);
+        for (int k = 0; k < d; k++) xr[k] = S.rot(xs[k], gs[s - 1]);
+        fhe_ct *lt = nullptr, *eq = nullptr;
+        if (!S.err) S.compare(xr.data(), xs.data(), d, true, true, &lt, &eq);
+        if (!S.err) {
+            S.keep(lt);
+            S.keep(eq);
+            std::vector<uint64_t> w(c->ns);
+            for (int r = 0; r < 2; r++)
+                for (int i = 0; i < cols; i++) w[(size_t)r * cols + i] = (i + s >= cols) ? 1 : 0;
+            fhe_ct *t = S.add(lt, S.plain(eq, w, 2));
+            fhe_ct *nr = rank ? S.add(rank, t) : t;
+            S.finish();
+            if (!S.err) carry(rank, S.release(nr));
+        }
+        S.finish();
+        err = S.err;
+    }
+    std::vector<uint64_t> idx(c->ns);
+    for (int r = 0; r < 2; r++)
+        for (int i = 0; i < cols; i++) idx[(size_t)r * cols + i] = (uint64_t)i;
+    for (int s = 0; s < cols && !err; s++) {
+        Circuit S(c, evk);
+        const fhe_ct *rr = s ? S.rot(rank, gs[s - 1]) : rank;
+        std::vector<const fhe_ct *> xr(d);
+        for (int k = 0; k < d; k++) xr[k] = s ? S.rot(xs[k], gs[s - 1]) : xs[k];
+        std::map<int, const fhe_ct *> pw;
+        pw[1] = S.plain(rr, idx, 1);
+        std::function<const fhe_ct *(int)> power = [&](int n) -> const fhe_ct * {
+            auto it = pw.find(n);
+            if (it != pw.end()) return it->second;
+            const fhe_ct *r;
+            if ((n & (n - 1)) == 0) {
+                const fhe_ct *h = power(n / 2);
+                r = S.mul(h, h);
+            } else {
+                int a = 1;
+                while (a * 2 < n) a *= 2;
+                const fhe_ct *A = power(a);
+                const fhe_ct *Bp = power(n - a);
+                r = S.mul(A, Bp);
+            }
+            pw[n] = r;
+            return r;
+        };
+        fhe_ct *e = S.cadd(S.neg(power(p - 1)), 1);
+        std::vector<fhe_ct *> nxt(d, nullptr);
+        for (int k = 0; k < d && !S.err; k++) {
+            fhe_ct *t = S.mul(e, xr[k]);
+            nxt[k] = outs[k] ? S.add(outs[k], t) : t;
+        }
+        S.finish();
+        if (!S.err)
+            for (int k = 0; k < d; k++) carry(outs[k], S.release(nxt[k]));
+        err = S.err;
+    }
+    if (rank) fhe_ct_destroy(rank);
+    if (err) {
+        for (fhe_ct *o : outs)
+            if (o) fhe_ct_destroy(o);
+        return err;
+    }
+    for (int k = 0; k < d; k++) out[k] = outs[k];
+    return 0;
+}
 
 std::vector<int64_t> tournament_galois(const fhe_ctx *c)
 {

@@ -293,6 +293,11 @@ void lt_bivariate_coefficients(int p, std::vector<int> &out);
 
 // kernel launchers (ntt.cu, kernels.cu)
 void launch_ntt_fwd_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs);
+void launch_add_plain(fhe_ctx *c, const u64 *a, const u64 *m, u64 *out, int count, int npoly, int level, int sub);
+void encode_slot_vector(const fhe_ctx *c, const uint64_t *v, int64_t *m);  // n_s slots -> N coefficients in [0, p)
+int op_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, int kind, fhe_ct **out);
+int circuit_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int d, fhe_ct **out);
+std::vector<int64_t> sort_galois(const fhe_ctx *c);
 void launch_ntt_inv_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs);
 // inverse NTT whose output limb l (of the map) is also multiplied by scale[l]/N^-1:
 // scale[l] = (N^-1 c_l mod q, Shoup word)

@@ -188,6 +188,23 @@ __global__ void k_ms_fold(u64 *__restrict__ src, long long total, int logN, int 
     }
 }
 
+// c0 of every ciphertext of a batch plus / minus one plaintext m[level][N]
+// (NTT domain); c1 and further polynomials are left as they are (the caller
+// copied them).  out may equal a.
+__global__ void k_add_plain(const u64 *__restrict__ a, const u64 *__restrict__ m, u64 *__restrict__ out,
+                            long long total, int logN, int level, long long ct_stride, int sub,
+                            const ModQ *__restrict__ mq)
+{
+    const long long LN = (long long)level << logN;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long c = idx / LN, r = idx % LN;
+        const u64 q = mq[(int)(r >> logN)].q;
+        const u64 x = a[c * ct_stride + r], y = m[r];
+        out[c * ct_stride + r] = sub ? submod(x, y, q) : addmod(x, y, q);
+    }
+}
+
 // out[o][i][k] = in[o][i][perm[k]]: sigma_g in the NTT domain.
 __global__ void k_automorphism(const u64 *__restrict__ in, u64 *__restrict__ out, long long total, int logN,
                                const int *__restrict__ perm)
@@ -391,6 +408,13 @@ void launch_rms_fold(fhe_ctx *c, u64 *src, int count, int level)
     const long long total = (long long)count * 2 * c->N;
     LAUNCH_CLS_W(FHE_K_ELEMWISE, c->K + 2.0, k_rms_fold, total, src, total, c->logN, level, c->K, c->d_rms + level,
                  c->d_mq);
+}
+
+void launch_add_plain(fhe_ctx *c, const u64 *a, const u64 *m, u64 *out, int count, int npoly, int level, int sub)
+{
+    const long long total = (long long)count * level * c->N;
+    LAUNCH_CLS_W(FHE_K_ELEMWISE, 3, k_add_plain, total, a, m, out, total, c->logN, level,
+                 (long long)npoly * level * c->N, sub, c->d_mq);
 }
 
 void launch_mul_poly(fhe_ctx *c, const u64 *a, const u64 *b, u64 *out, int outer, int level, long long b_outer)

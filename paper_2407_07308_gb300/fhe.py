@@ -26,7 +26,7 @@ ERRORS = {
     -1: "FHE_EINVAL", -2: "FHE_EMISMATCH", -3: "FHE_ELEVEL", -4: "FHE_ENOMEM", -5: "FHE_EBUDGET",
     -6: "FHE_ETIMEOUT", -7: "FHE_ECUDA", -8: "FHE_ENOKEY", -9: "FHE_EUNSUPPORTED",
 }
-OPS = {1: "mul", 2: "add", 3: "sub", 4: "cmul", 5: "cadd", 6: "neg", 7: "rot"}
+OPS = {1: "mul", 2: "add", 3: "sub", 4: "cmul", 5: "cadd", 6: "neg", 7: "rot", 8: "padd", 9: "psub", 10: "pmul"}
 
 
 class FheError(RuntimeError):
@@ -148,6 +148,11 @@ def lib() -> ctypes.CDLL:
             "fhe_job_footprint": (ctypes.c_uint64, [vp]),
             "fhe_ctx_inject_alloc_failure": (ci, [vp, ctypes.c_int64]),
             "fhe_ctx_trim": (ci, [vp]),
+            "fhe_add_plain": (ci, [vp, vp, vp, POINTER(vp)]),
+            "fhe_sub_plain": (ci, [vp, vp, vp, POINTER(vp)]),
+            "fhe_mul_plain": (ci, [vp, vp, vp, POINTER(vp)]),
+            "fhe_sort_galois": (ci, [vp, vp, ci]),
+            "fhe_sort": (ci, [vp, vp, vp, ci, vp]),
             "fhe_compare_bivariate": (ci, [vp, vp, vp, vp, ci, POINTER(vp), POINTER(vp)]),
             "fhe_probe_int_peak": (ci, [POINTER(ctypes.c_double), POINTER(ctypes.c_double)]),
             "fhe_ctx_fused_modswitch": (ci, [vp, ci]),
@@ -483,6 +488,37 @@ def fhe_compare_bivariate(ctx, evk, xs, ys, want_lt=True, want_eq=True):
                                        ctypes.byref(lt) if want_lt else None, ctypes.byref(eq) if want_eq else None),
            ctx)
     return (lt if want_lt else None), (eq if want_eq else None)
+
+
+def _plain_op(name):
+    def f(ctx, a, slots):
+        v = np.ascontiguousarray(slots, dtype=np.uint64)
+        out = c_void_p()
+        _check(getattr(lib(), name)(ctx, a, _ptr(v), ctypes.byref(out)), ctx)
+        return out
+
+    f.__name__ = name
+    return f
+
+
+fhe_add_plain = _plain_op("fhe_add_plain")
+fhe_sub_plain = _plain_op("fhe_sub_plain")
+fhe_mul_plain = _plain_op("fhe_mul_plain")
+
+
+def fhe_sort_galois(ctx):
+    n = _check(lib().fhe_sort_galois(ctx, None, 0), ctx)
+    g = np.zeros(max(n, 1), dtype=np.int64)
+    lib().fhe_sort_galois(ctx, _ptr(g), n)
+    return [int(v) for v in g[:n]]
+
+
+def fhe_sort(ctx, evk, xs):
+    """Every row of every ciphertext sorted; xs: the d digit handles."""
+    d = len(xs)
+    out = (c_void_p * d)()
+    _check(lib().fhe_sort(ctx, evk, _handles(xs), d, out), ctx)
+    return [c_void_p(v) for v in out]
 
 
 def fhe_max_min(ctx, evk, xs, ys):

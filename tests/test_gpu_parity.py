@@ -496,3 +496,69 @@ def test_compare_bivariate_full_digits_bitexact(logN, p, L, K, d, count):
         _same(eq_o, g.export(eq_g), 0)
     finally:
         g.close()
+
+
+def test_plaintext_operands_bitexact():
+    """ct + pt, ct - pt, ct * pt with one slot vector for the whole batch:
+    ciphertext 0 bit-exact with the oracle, every ciphertext decrypts to the
+    slot-wise result."""
+    fhe = _fhe()
+    params = dict(logN=10, p=17, L=3, K=2, **CHAIN50)
+    o, g = _pair(params, seed=27)
+    try:
+        rnd = random.Random(6)
+        rows = [[rnd.randrange(17) for _ in range(g.ns)] for _ in range(2)]
+        v = [rnd.randrange(17) for _ in range(g.ns)]
+        x = g.encrypt_slots(rows, seed=7)
+        xo = o.encrypt_slots(rows, seed=7)[0]
+        ev = o.evaluator()
+        for name, ref, f in (("add", ev.add_plain, lambda a, b: (a + b) % 17),
+                             ("sub", ev.sub_plain, lambda a, b: (a - b) % 17),
+                             ("mul", ev.mul_plain, lambda a, b: a * b % 17)):
+            r = g.own(getattr(fhe, f"fhe_{name}_plain")(g.ctx, x, v))
+            _same(ref(xo, v), g.export(r), 0)
+            dec = g.decrypt(r)
+            for c in range(2):
+                assert dec[c].tolist() == [f(a, b) for a, b in zip(rows[c], v)]
+    finally:
+        g.close()
+
+
+def test_sort_rows_bitexact():
+    """Every row (cols = 4 values of 2 digits, ties included) of every
+    ciphertext sorted; ciphertext 0 bit-exact with the oracle's sort and the
+    op traces equal."""
+    from oracle.circuits import sort_galois, sort_rows
+
+    fhe = _fhe()
+    p, d, logN = 17, 2, 10
+    gal = sort_galois(p, 2 ** logN)
+    params = dict(logN=logN, p=p, L=11, K=2, **CHAIN50)
+    o, g = _pair(params, seed=29, galois=gal)
+    try:
+        assert fhe.fhe_sort_galois(g.ctx) == gal
+        b = (p + 1) // 2
+        rnd = random.Random(8)
+        vals = [[rnd.randrange(b ** d) for _ in range(g.ns)] for _ in range(2)]
+        vals[0][1] = vals[0][3]  # ties
+        vals[1][4] = vals[1][5]
+        dg = [[_digits(vals[c], b, d)[k] for c in range(2)] for k in range(d)]
+        xg = [g.encrypt_slots(dg[k], seed=500 + k) for k in range(d)]
+        fhe.fhe_trace_enable(g.ctx, True)
+        out = fhe.fhe_sort(g.ctx, g.evk, xg)
+        for h in out:
+            g.own(h)
+        trace_g = fhe.fhe_trace_get(g.ctx)
+        cols = g.ns // 2
+        dec = [g.decrypt(h) for h in out]
+        for c in range(2):
+            got = [sum(int(dec[k][c][s]) * b ** k for k in range(d)) for s in range(g.ns)]
+            assert got == sorted(vals[c][:cols]) + sorted(vals[c][cols:])
+        xo = [o.encrypt_slots(dg[k], seed=500 + k)[0] for k in range(d)]
+        ev = o.evaluator()
+        out_o = sort_rows(ev, xo)
+        assert trace_g == ev.trace
+        for k in range(d):
+            _same(out_o[k], g.export(out[k]), 0)
+    finally:
+        g.close()
