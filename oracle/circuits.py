@@ -58,6 +58,14 @@ them) are:
     out = sum_{s=0}^{cols-1} EQ(sigma_{5^s}(rank) - idx) sigma_{5^s}(x) per
     digit (idx[i] = i, EQ(u) = 1 - u^(p-1)), shifts in increasing order;
 
+  * slot compaction (p = 1 mod 4 with cols = n_s / 2 columns per row, or the
+    two single-slot rows of p = 3 mod 8): k = n_s / used inputs whose
+    values sit in slot indices [0, used) (index r cols + c; used divides
+    cols, or used = cols) are packed into one: input j is masked to those
+    slots, shifted right by o_j = (j used) mod cols columns (sigma_{5^(cols
+    - o_j)}) and moved to row r_j = (j used) div cols (sigma_{2N-1} when
+    r_j = 1); the results are added in order of j;
+
 Every operation appends (name, level) to ``trace``; the CUDA path emits the
 same trace, and a test compares them.  The multiplication count is pinned
 against the Paterson-Stockmeyer count (8 / 23 / 30 for p = 17 / 131 / 257) and
@@ -351,6 +359,49 @@ def sort_rows(ev: "Evaluator", xs):
             t = ev.mul(e, xr[k])
             outs[k] = t if outs[k] is None else ev.add(outs[k], t)
     return outs
+
+
+def pack_plan(ss: SlotStructure, N: int, used: int):
+    """(inputs, [(column shift element or None, row swap)] per input)."""
+    ns = ss.ns
+    cols = ns // 2 if ns >= 2 else 1
+    assert used >= 1 and ns % used == 0 and (used > cols or cols % used == 0 or used == cols), "bad slot count"
+    k = ns // used
+    plan = []
+    for j in range(k):
+        start = j * used
+        r, o = divmod(start, cols) if used <= cols else (start // ns, 0)
+        g = pow(5, (cols - o) % cols, 2 * N) if o else None
+        plan.append((g, r == 1))
+    return k, plan
+
+
+def pack_galois(p: int, N: int, used: int) -> list:
+    ss = SlotStructure(p, N)
+    _, plan = pack_plan(ss, N, used)
+    gs = sorted({g for g, _ in plan if g})
+    if any(sw for _, sw in plan):
+        gs.append(2 * N - 1)
+    return gs
+
+
+def pack(ev: "Evaluator", cts, used: int) -> Ct:
+    """The k = n_s / used inputs (values in slots [0, used)) in one ciphertext:
+    input j's slot t at slot j used + t."""
+    ss = ev._slots()
+    N = ev.o.N
+    k, plan = pack_plan(ss, N, used)
+    assert len(cts) == k
+    mask = [1 if i < used else 0 for i in range(ss.ns)]
+    out = None
+    for j, (ct, (g, swap)) in enumerate(zip(cts, plan)):
+        t = ev.mul_plain(ct, mask)
+        if g:
+            t = ev.rotate(t, g)
+        if swap:
+            t = ev.rotate(t, 2 * N - 1)
+        out = t if out is None else ev.add(out, t)
+    return out
 
 
 def round_depth(p: int, d: int) -> int:

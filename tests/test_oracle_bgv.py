@@ -323,3 +323,23 @@ def test_sort_rows_small_ring():
     cols = ns // 2
     assert got == sorted(vals[:cols]) + sorted(vals[cols:])
     assert st.o.noise_bits(out[0], st.s) < np.log2(st.o.primes[0]) - 1
+
+
+@pytest.mark.parametrize("p,used", [(17, 1), (17, 2), (17, 4), (131, 1)])
+def test_pack_slots(p, used):
+    """Slot compaction: k = n_s / used inputs (values in the first `used`
+    slots, garbage elsewhere) packed into one ciphertext, input j's values at
+    slots [j used, (j + 1) used)."""
+    from oracle.circuits import pack, pack_galois
+
+    N = 2 ** 8
+    st = OracleSetup(logN=8, p=p, L=3, K=2, seed=26, galois=pack_galois(p, N, used), **CHAIN50)
+    ns = st.ss.ns
+    k = ns // used
+    rnd = random.Random(p + used)
+    rows = [[rnd.randrange(p) for _ in range(ns)] for _ in range(k)]  # garbage beyond `used`
+    cts = [st.encrypt_slots([r], seed=80 + j)[0] for j, r in enumerate(rows)]
+    ev = st.evaluator()
+    out = pack(ev, cts, used)
+    want = [rows[j][t] for j in range(k) for t in range(used)]
+    assert st.decrypt_slots(out) == want
