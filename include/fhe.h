@@ -317,6 +317,17 @@ int fhe_mul_plain(fhe_ctx *ctx, const fhe_ct *a, const uint64_t *slots, fhe_ct *
  * cols >= 2 and the column rotations of fhe_sort_galois in evk; consumes
  * the comparison's depth + ceil(log2(p-1)) + 1 levels.  out: d new handles. */
 int fhe_sort_galois(const fhe_ctx *ctx, int64_t *galois, int cap);
+
+/* Slot compaction (the paper's slot manager, Sec. 5): n = n_s / used input
+ * batches whose values sit in slot indices [0, used) (index r cols + c; the
+ * other slots may hold anything) become one batch, input j's slot t at slot
+ * j used + t: masked by a plaintext, shifted right by (j used) mod cols
+ * columns (sigma_{5^(cols - shift)}) and moved to row (j used) div cols
+ * (sigma_{2N-1}).  used must divide n_s and, when below cols, cols.  The
+ * rotation keys are those of fhe_pack_galois.  Inputs: equal count (any
+ * levels; the sum is taken at the lowest).  No level is consumed. */
+int fhe_pack_galois(const fhe_ctx *ctx, int used, int64_t *galois, int cap);
+int fhe_pack(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *in, int n, int used, fhe_ct **out);
 int fhe_sort(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, int d, fhe_ct **out);
 
 /* ---- batches of uneven requests ------------------------------------------------- */

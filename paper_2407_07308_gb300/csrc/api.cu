@@ -1127,6 +1127,28 @@ extern "C" int fhe_mul_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots,
     return plain_api(c, a, slots, 2, out);
 }
 
+extern "C" int fhe_pack_galois(const fhe_ctx *c, int used, int64_t *galois, int cap)
+{
+    if (!c || cap < 0 || used < 1 || c->ns % used) return FHE_EINVAL;
+    const std::vector<int64_t> g = pack_galois(c, used);
+    for (int i = 0; i < (int)g.size() && i < cap; i++) galois[i] = g[i];
+    return (int)g.size();
+}
+
+extern "C" int fhe_pack(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *in, int n, int used, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!evk || evk->ctx != c || !in || n < 1 || !out) return FHE_EINVAL;
+    for (int j = 0; j < n; j++) {
+        if (!same_ctx(c, in[j])) return FHE_EINVAL;
+        if (in[j]->npoly != 2 || in[j]->count != in[0]->count)
+            return fhe_fail(c, FHE_EMISMATCH, "pack: inputs differ in shape");
+    }
+    LOCK(c);
+    const int e = circuit_pack(c, evk, in, n, used, out);
+    return e ? e : launch_status(c, "pack");
+}
+
 extern "C" int fhe_sort_galois(const fhe_ctx *c, int64_t *galois, int cap)
 {
     if (!c || cap < 0) return FHE_EINVAL;

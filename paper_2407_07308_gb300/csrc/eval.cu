@@ -16,6 +16,7 @@
 // Modulus switching l -> l-1: INTT of the last limb, then one fused kernel
 // that forms delta = p [x_last p^-1]_{q_last}, transforms it and applies
 // (x - delta) q_last^-1.
+#include <algorithm>
 #include <functional>
 #include <map>
 
@@ -1246,6 +1247,66 @@ int circuit_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int d, 
     }
     for (int k = 0; k < d; k++) out[k] = outs[k];
     return 0;
+}
+
+// ---------------------------------------------------------------------------
+// slot compaction
+// ---------------------------------------------------------------------------
+//
+// k = n_s / used inputs whose values sit in slot indices [0, used) (index
+// r cols + c) go into one ciphertext: input j masked to those slots, shifted
+// right by o_j = (j used) mod cols columns (sigma_{5^(cols - o_j)}), moved to
+// row (j used) div cols (sigma_{2N-1}), added in order of j.
+
+static int pack_plan(const fhe_ctx *c, int used, std::vector<std::pair<int64_t, bool>> &plan)
+{
+    const int ns = c->ns, cols = ns >= 2 ? ns / 2 : 1;
+    if (used < 1 || ns % used || (used < cols && cols % used)) return FHE_EINVAL;
+    const int64_t twoN = 2 * (int64_t)c->N;
+    plan.clear();
+    for (int j = 0; j < ns / used; j++) {
+        const int start = j * used;
+        const int r = used <= cols ? start / cols : start / ns, o = used <= cols ? start % cols : 0;
+        const int64_t g = o ? (int64_t)host_powmod(5, (u64)((cols - o) % cols), (u64)twoN) : 0;
+        plan.push_back({g, r == 1});
+    }
+    return 0;
+}
+
+std::vector<int64_t> pack_galois(const fhe_ctx *c, int used)
+{
+    std::vector<std::pair<int64_t, bool>> plan;
+    std::vector<int64_t> g;
+    if (pack_plan(c, used, plan)) return g;
+    bool swap = false;
+    for (auto &e : plan) {
+        if (e.first && std::find(g.begin(), g.end(), e.first) == g.end()) g.push_back(e.first);
+        swap = swap || e.second;
+    }
+    std::sort(g.begin(), g.end());
+    if (swap) g.push_back(2 * (int64_t)c->N - 1);
+    return g;
+}
+
+int circuit_pack(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *in, int k, int used, fhe_ct **out)
+{
+    std::vector<std::pair<int64_t, bool>> plan;
+    if (pack_plan(c, used, plan) || k != (int)plan.size())
+        return fhe_fail(c, FHE_EINVAL, "pack: n_s must be the number of inputs times the used slots");
+    std::vector<uint64_t> mask(c->ns);
+    for (int i = 0; i < c->ns; i++) mask[i] = i < used ? 1 : 0;
+    Circuit C(c, evk);
+    fhe_ct *acc = nullptr;
+    const int64_t swap = 2 * (int64_t)c->N - 1;
+    for (int j = 0; j < k && !C.err; j++) {
+        fhe_ct *t = C.plain(in[j], mask, 2);
+        if (plan[j].first) t = C.rot(t, plan[j].first);
+        if (plan[j].second) t = C.rot(t, swap);
+        acc = acc ? C.add(acc, t) : t;
+    }
+    if (!C.err) *out = C.release(acc);
+    C.finish();
+    return C.err;
 }
 
 std::vector<int64_t> tournament_galois(const fhe_ctx *c)

@@ -298,6 +298,8 @@ void encode_slot_vector(const fhe_ctx *c, const uint64_t *v, int64_t *m);  // n_
 int op_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, int kind, fhe_ct **out);
 int circuit_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int d, fhe_ct **out);
 std::vector<int64_t> sort_galois(const fhe_ctx *c);
+std::vector<int64_t> pack_galois(const fhe_ctx *c, int used);
+int circuit_pack(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *in, int k, int used, fhe_ct **out);
 void launch_ntt_inv_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs);
 // inverse NTT whose output limb l (of the map) is also multiplied by scale[l]/N^-1:
 // scale[l] = (N^-1 c_l mod q, Shoup word)

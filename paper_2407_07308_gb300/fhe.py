@@ -152,6 +152,8 @@ def lib() -> ctypes.CDLL:
             "fhe_sub_plain": (ci, [vp, vp, vp, POINTER(vp)]),
             "fhe_mul_plain": (ci, [vp, vp, vp, POINTER(vp)]),
             "fhe_sort_galois": (ci, [vp, vp, ci]),
+            "fhe_pack_galois": (ci, [vp, ci, vp, ci]),
+            "fhe_pack": (ci, [vp, vp, vp, ci, ci, POINTER(vp)]),
             "fhe_sort": (ci, [vp, vp, vp, ci, vp]),
             "fhe_compare_bivariate": (ci, [vp, vp, vp, vp, ci, POINTER(vp), POINTER(vp)]),
             "fhe_probe_int_peak": (ci, [POINTER(ctypes.c_double), POINTER(ctypes.c_double)]),
@@ -511,6 +513,20 @@ def fhe_sort_galois(ctx):
     g = np.zeros(max(n, 1), dtype=np.int64)
     lib().fhe_sort_galois(ctx, _ptr(g), n)
     return [int(v) for v in g[:n]]
+
+
+def fhe_pack_galois(ctx, used: int):
+    n = _check(lib().fhe_pack_galois(ctx, int(used), None, 0), ctx)
+    g = np.zeros(max(n, 1), dtype=np.int64)
+    lib().fhe_pack_galois(ctx, int(used), _ptr(g), n)
+    return [int(v) for v in g[:n]]
+
+
+def fhe_pack(ctx, evk, cts, used: int):
+    """n_s / used batches with values in the first `used` slots, packed into one."""
+    out = c_void_p()
+    _check(lib().fhe_pack(ctx, evk, _handles(cts), len(cts), int(used), ctypes.byref(out)), ctx)
+    return out
 
 
 def fhe_sort(ctx, evk, xs):

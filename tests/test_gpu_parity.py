@@ -562,3 +562,38 @@ def test_sort_rows_bitexact():
             _same(out_o[k], g.export(out[k]), 0)
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("p,used", [(17, 1), (17, 2), (17, 4), (17, 8), (131, 1)])
+def test_pack_slots_bitexact(p, used):
+    """n_s / used batches (values in the first `used` slots, the rest garbage)
+    packed into one: decrypts to the concatenation, bit-exact with the
+    oracle's packing, op traces equal."""
+    from oracle.circuits import pack, pack_galois
+
+    fhe = _fhe()
+    logN = 10
+    gal = pack_galois(p, 2 ** logN, used)
+    params = dict(logN=logN, p=p, L=6, K=2, **CHAIN50)
+    o, g = _pair(params, seed=31 + used, galois=gal)
+    try:
+        assert fhe.fhe_pack_galois(g.ctx, used) == gal
+        k = g.ns // used
+        rnd = random.Random(used)
+        vals = [[[rnd.randrange(p) for _ in range(g.ns)] for _ in range(2)] for _ in range(k)]
+        xg = [g.encrypt_slots(vals[j], seed=600 + j) for j in range(k)]
+        fhe.fhe_trace_enable(g.ctx, True)
+        out = fhe.fhe_pack(g.ctx, g.evk, xg, used)
+        g.own(out)
+        trace_g = fhe.fhe_trace_get(g.ctx)
+        dec = g.decrypt(out)
+        for c in range(2):
+            want = [vals[j][c][t] for j in range(k) for t in range(used)]
+            assert [int(v) for v in dec[c]] == want
+        xo = [o.encrypt_slots(vals[j], seed=600 + j)[0] for j in range(k)]
+        ev = o.evaluator()
+        out_o = pack(ev, xo, used)
+        assert trace_g == ev.trace
+        _same(out_o, g.export(out), 0)
+    finally:
+        g.close()
