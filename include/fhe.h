@@ -318,16 +318,33 @@ int fhe_mul_plain(fhe_ctx *ctx, const fhe_ct *a, const uint64_t *slots, fhe_ct *
  * the comparison's depth + ceil(log2(p-1)) + 1 levels.  out: d new handles. */
 int fhe_sort_galois(const fhe_ctx *ctx, int64_t *galois, int cap);
 
-/* Slot compaction (the paper's slot manager, Sec. 5): n = n_s / used input
- * batches whose values sit in slot indices [0, used) (index r cols + c; the
- * other slots may hold anything) become one batch, input j's slot t at slot
- * j used + t: masked by a plaintext, shifted right by (j used) mod cols
- * columns (sigma_{5^(cols - shift)}) and moved to row (j used) div cols
- * (sigma_{2N-1}).  used must divide n_s and, when below cols, cols.  The
- * rotation keys are those of fhe_pack_galois.  Inputs: equal count (any
- * levels; the sum is taken at the lowest).  No level is consumed. */
-int fhe_pack_galois(const fhe_ctx *ctx, int used, int64_t *galois, int cap);
-int fhe_pack(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *in, int n, int used, fhe_ct **out);
+/* Slot manager and slot compaction (Sec. 5, "Slot Compaction"): inputs whose
+ * useful values fill only some slots are compacted into as few ciphertexts as
+ * the slot rotations allow, before comparison.
+ *
+ * useful: n x n_s bytes, row j for input j, nonzero where slot u (index
+ * r cols + c, cols = n_s / 2, or 1 for n_s = 2) holds a useful value; the
+ * other slots may hold anything and are masked off.  Placement, in order of
+ * input: the slots of input j still to place go, under one slot rotation
+ * (columns shifted right by s, rows swapped when b), into the open output
+ * that takes the most of them (first output, then b, then s, wins a tie); an
+ * output opens only when every open one is full.  Each such piece costs a
+ * plaintext mask, sigma_{5^(cols - s)} when s > 0, sigma_{2N-1} when b, and
+ * an addition.
+ *
+ * fhe_slot_plan (host only: slots = n_s and ring_n = N of the context, as
+ * fhe_ctx_info reports them) returns the number of outputs and, when non-NULL,
+ * fills dest (n x n_s int32: output * n_s + slot, or -1 for slots that are
+ * not useful) and galois (up to galois_cap rotation elements the plan needs:
+ * column shifts ascending, then 2N - 1) with their count in *n_galois.
+ * fhe_slot_pack evaluates the plan on inputs of equal count (any levels; sums
+ * are taken at the lower level) and returns the number of outputs written to
+ * out[0 .. out_cap); FHE_EINVAL when out_cap is smaller, FHE_ENOKEY when evk
+ * lacks a rotation the plan needs.  No level is consumed. */
+int fhe_slot_plan(int slots, int64_t ring_n, int n, const uint8_t *useful, int32_t *dest, int64_t *galois,
+                  int galois_cap, int *n_galois);
+int fhe_slot_pack(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *in, int n, const uint8_t *useful,
+                  fhe_ct **out, int out_cap);
 int fhe_sort(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, int d, fhe_ct **out);
 
 /* ---- batches of uneven requests ------------------------------------------------- */

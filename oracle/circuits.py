@@ -58,13 +58,16 @@ them) are:
     out = sum_{s=0}^{cols-1} EQ(sigma_{5^s}(rank) - idx) sigma_{5^s}(x) per
     digit (idx[i] = i, EQ(u) = 1 - u^(p-1)), shifts in increasing order;
 
-  * slot compaction (p = 1 mod 4 with cols = n_s / 2 columns per row, or the
-    two single-slot rows of p = 3 mod 8): k = n_s / used inputs whose
-    values sit in slot indices [0, used) (index r cols + c; used divides
-    cols, or used = cols) are packed into one: input j is masked to those
-    slots, shifted right by o_j = (j used) mod cols columns (sigma_{5^(cols
-    - o_j)}) and moved to row r_j = (j used) div cols (sigma_{2N-1} when
-    r_j = 1); the results are added in order of j;
+  * slot compaction (the slot manager): each input comes with the list of
+    its useful slots (index r cols + c, cols = n_s / 2 columns per row; the
+    two single-slot rows of p = 3 mod 8 have cols = 1).  Inputs are placed in
+    order; the slots still to place go, under the slot rotation (column
+    shift right by s, rows swapped when b) and into the output that takes
+    the most of them, the first such (output, b, s) in that order winning a
+    tie; a new output opens when none has room.  A piece is evaluated as
+    mask (a plaintext product), sigma_{5^(cols - s)} when s > 0,
+    sigma_{2N-1} when b, and an addition into its output, pieces in plan
+    order;
 
 Every operation appends (name, level) to ``trace``; the CUDA path emits the
 same trace, and a test compares them.  The multiplication count is pinned
@@ -361,47 +364,73 @@ def sort_rows(ev: "Evaluator", xs):
     return outs
 
 
-def pack_plan(ss: SlotStructure, N: int, used: int):
-    """(inputs, [(column shift element or None, row swap)] per input)."""
-    ns = ss.ns
+def slot_plan(ns: int, useful):
+    """The slot manager's placement of useful slots into as few outputs as
+    possible (Sec. 5, slot compaction).  useful[j] lists input j's useful slot
+    indices.  Returns (outputs, pieces, dest): each piece (j, o, src, s, b)
+    moves input j's slots src to output o by shifting columns right by s and
+    swapping rows when b; dest[j][u] = o n_s + slot, or -1 for a slot left
+    behind."""
+    cols, rows = (ns // 2, 2) if ns >= 2 else (1, 1)
+
+    def image(u, s, b):
+        r, c = divmod(u, cols)
+        return (r ^ b) * cols + (c + s) % cols
+
+    occ = []
+    pieces = []
+    dest = [[-1] * ns for _ in useful]
+    for j, u_j in enumerate(useful):
+        rest = sorted(set(u_j))
+        while rest:
+            best, where = 0, None
+            for o in range(len(occ)):
+                for b in range(rows):
+                    for s in range(cols):
+                        n = sum(1 for u in rest if image(u, s, b) not in occ[o])
+                        if n > best:
+                            best, where = n, (o, s, b)
+            if where is None:
+                occ.append(set())
+                continue
+            o, s, b = where
+            src = [u for u in rest if image(u, s, b) not in occ[o]]
+            for u in src:
+                occ[o].add(image(u, s, b))
+                dest[j][u] = o * ns + image(u, s, b)
+            pieces.append((j, o, tuple(src), s, b))
+            rest = [u for u in rest if u not in src]
+    return len(occ), pieces, dest
+
+
+def slot_galois(ns: int, N: int, pieces) -> list:
+    """Rotation keys the pieces need: column shifts (ascending), then the row
+    swap."""
     cols = ns // 2 if ns >= 2 else 1
-    assert used >= 1 and ns % used == 0 and (used > cols or cols % used == 0 or used == cols), "bad slot count"
-    k = ns // used
-    plan = []
-    for j in range(k):
-        start = j * used
-        r, o = divmod(start, cols) if used <= cols else (start // ns, 0)
-        g = pow(5, (cols - o) % cols, 2 * N) if o else None
-        plan.append((g, r == 1))
-    return k, plan
-
-
-def pack_galois(p: int, N: int, used: int) -> list:
-    ss = SlotStructure(p, N)
-    _, plan = pack_plan(ss, N, used)
-    gs = sorted({g for g, _ in plan if g})
-    if any(sw for _, sw in plan):
+    gs = sorted({pow(5, (cols - s) % cols, 2 * N) for _, _, _, s, _ in pieces if s})
+    if any(b for *_, b in pieces):
         gs.append(2 * N - 1)
     return gs
 
 
-def pack(ev: "Evaluator", cts, used: int) -> Ct:
-    """The k = n_s / used inputs (values in slots [0, used)) in one ciphertext:
-    input j's slot t at slot j used + t."""
+def slot_pack(ev: "Evaluator", cts, useful):
+    """Compacts the inputs' useful slots: per piece, in plan order, mask the
+    input to the piece's slots, shift the columns (sigma_{5^(cols - s)}), swap
+    the rows (sigma_{2N-1}) and add into the piece's output."""
     ss = ev._slots()
     N = ev.o.N
-    k, plan = pack_plan(ss, N, used)
-    assert len(cts) == k
-    mask = [1 if i < used else 0 for i in range(ss.ns)]
-    out = None
-    for j, (ct, (g, swap)) in enumerate(zip(cts, plan)):
-        t = ev.mul_plain(ct, mask)
-        if g:
-            t = ev.rotate(t, g)
-        if swap:
+    cols = ss.ns // 2 if ss.ns >= 2 else 1
+    n_out, pieces, _ = slot_plan(ss.ns, useful)
+    outs = [None] * n_out
+    for j, o, src, s, b in pieces:
+        keep = set(src)
+        t = ev.mul_plain(cts[j], [1 if i in keep else 0 for i in range(ss.ns)])
+        if s:
+            t = ev.rotate(t, pow(5, (cols - s) % cols, 2 * N))
+        if b:
             t = ev.rotate(t, 2 * N - 1)
-        out = t if out is None else ev.add(out, t)
-    return out
+        outs[o] = t if outs[o] is None else ev.add(outs[o], t)
+    return outs
 
 
 def round_depth(p: int, d: int) -> int:

@@ -1127,26 +1127,43 @@ extern "C" int fhe_mul_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots,
     return plain_api(c, a, slots, 2, out);
 }
 
-extern "C" int fhe_pack_galois(const fhe_ctx *c, int used, int64_t *galois, int cap)
+extern "C" int fhe_slot_plan(int slots, int64_t ring_n, int n, const uint8_t *useful, int32_t *dest,
+                             int64_t *galois, int galois_cap, int *n_galois)
 {
-    if (!c || cap < 0 || used < 1 || c->ns % used) return FHE_EINVAL;
-    const std::vector<int64_t> g = pack_galois(c, used);
-    for (int i = 0; i < (int)g.size() && i < cap; i++) galois[i] = g[i];
-    return (int)g.size();
+    if (slots < 1 || (slots > 1 && slots % 2) || ring_n < slots || ring_n > (1 << 20) || (ring_n & (ring_n - 1)))
+        return FHE_EINVAL;
+    if (n < 0 || (n && !useful) || galois_cap < 0 || (galois_cap && !galois)) return FHE_EINVAL;
+    std::vector<SlotPiece> pieces;
+    std::vector<int32_t> d;
+    const int n_out = slot_plan(slots, n, useful, pieces, dest ? &d : nullptr);
+    if (dest) std::copy(d.begin(), d.end(), dest);
+    const std::vector<int64_t> g = slot_galois(slots, ring_n, pieces);
+    for (int i = 0; i < (int)g.size() && i < galois_cap; i++) galois[i] = g[i];
+    if (n_galois) *n_galois = (int)g.size();
+    return n_out;
 }
 
-extern "C" int fhe_pack(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *in, int n, int used, fhe_ct **out)
+extern "C" int fhe_slot_pack(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *in, int n, const uint8_t *useful,
+                             fhe_ct **out, int out_cap)
 {
     CHECK_CTX(c);
-    if (!evk || evk->ctx != c || !in || n < 1 || !out) return FHE_EINVAL;
+    if (!evk || evk->ctx != c || !in || n < 1 || !useful || !out || out_cap < 0) return FHE_EINVAL;
     for (int j = 0; j < n; j++) {
         if (!same_ctx(c, in[j])) return FHE_EINVAL;
         if (in[j]->npoly != 2 || in[j]->count != in[0]->count)
-            return fhe_fail(c, FHE_EMISMATCH, "pack: inputs differ in shape");
+            return fhe_fail(c, FHE_EMISMATCH, "slot_pack: inputs differ in shape");
     }
+    std::vector<SlotPiece> pieces;
+    const int n_out = slot_plan(c->ns, n, useful, pieces, nullptr);
+    if (n_out > out_cap) return fhe_fail(c, FHE_EINVAL, "slot_pack: more outputs than out_cap");
+    if (n_out == 0) return 0;
+    for (int64_t g : slot_galois(c->ns, c->N, pieces))
+        if (!evk->find(g)) return fhe_fail(c, FHE_ENOKEY, "slot_pack: missing rotation key");
     LOCK(c);
-    const int e = circuit_pack(c, evk, in, n, used, out);
-    return e ? e : launch_status(c, "pack");
+    const int e = circuit_slot_pack(c, evk, in, n, useful, out, n_out);
+    if (e) return e;
+    const int st = launch_status(c, "slot_pack");
+    return st ? st : n_out;
 }
 
 extern "C" int fhe_sort_galois(const fhe_ctx *c, int64_t *galois, int cap)

@@ -1250,61 +1250,91 @@ int circuit_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int d, 
 }
 
 // ---------------------------------------------------------------------------
-// slot compaction
+// slot compaction (the slot manager)
 // ---------------------------------------------------------------------------
 //
-// k = n_s / used inputs whose values sit in slot indices [0, used) (index
-// r cols + c) go into one ciphertext: input j masked to those slots, shifted
-// right by o_j = (j used) mod cols columns (sigma_{5^(cols - o_j)}), moved to
-// row (j used) div cols (sigma_{2N-1}), added in order of j.
+// Inputs are placed in order.  The useful slots of an input still to place go,
+// under one slot rotation (columns shifted right by s, rows swapped when b),
+// into the output that takes the most of them; the first (output, b, s) wins a
+// tie, and an output opens only when every open one is full.  A piece is a
+// plaintext mask, sigma_{5^(cols - s)} when s > 0, sigma_{2N-1} when b, and a
+// sum into its output, in plan order.
 
-static int pack_plan(const fhe_ctx *c, int used, std::vector<std::pair<int64_t, bool>> &plan)
+int slot_plan(int ns, int n, const uint8_t *useful, std::vector<SlotPiece> &pieces, std::vector<int32_t> *dest)
 {
-    const int ns = c->ns, cols = ns >= 2 ? ns / 2 : 1;
-    if (used < 1 || ns % used || (used < cols && cols % used)) return FHE_EINVAL;
-    const int64_t twoN = 2 * (int64_t)c->N;
-    plan.clear();
-    for (int j = 0; j < ns / used; j++) {
-        const int start = j * used;
-        const int r = used <= cols ? start / cols : start / ns, o = used <= cols ? start % cols : 0;
-        const int64_t g = o ? (int64_t)host_powmod(5, (u64)((cols - o) % cols), (u64)twoN) : 0;
-        plan.push_back({g, r == 1});
+    const int cols = ns >= 2 ? ns / 2 : 1, rows = ns >= 2 ? 2 : 1;
+    auto image = [&](int u, int s, int b) { return ((u / cols) ^ b) * cols + (u % cols + s) % cols; };
+    std::vector<std::vector<char>> occ;
+    pieces.clear();
+    if (dest) dest->assign((size_t)n * ns, -1);
+    for (int j = 0; j < n; j++) {
+        std::vector<int> rest;
+        for (int u = 0; u < ns; u++)
+            if (useful[(size_t)j * ns + u]) rest.push_back(u);
+        while (!rest.empty()) {
+            int best = 0, bo = -1, bs = 0, bb = 0;
+            for (int o = 0; o < (int)occ.size(); o++)
+                for (int b = 0; b < rows; b++)
+                    for (int s2 = 0; s2 < cols; s2++) {
+                        int cnt = 0;
+                        for (int u : rest) cnt += !occ[o][image(u, s2, b)];
+                        if (cnt > best) { best = cnt; bo = o; bs = s2; bb = b; }
+                    }
+            if (bo < 0) { occ.emplace_back(ns, 0); continue; }
+            SlotPiece pc{j, bo, bs, bb, {}};
+            std::vector<int> left;
+            for (int u : rest) {
+                const int t = image(u, bs, bb);
+                if (occ[bo][t]) { left.push_back(u); continue; }
+                occ[bo][t] = 1;
+                pc.src.push_back(u);
+                if (dest) (*dest)[(size_t)j * ns + u] = bo * ns + t;
+            }
+            pieces.push_back(std::move(pc));
+            rest.swap(left);
+        }
     }
-    return 0;
+    return (int)occ.size();
 }
 
-std::vector<int64_t> pack_galois(const fhe_ctx *c, int used)
+std::vector<int64_t> slot_galois(int ns, int64_t N, const std::vector<SlotPiece> &pieces)
 {
-    std::vector<std::pair<int64_t, bool>> plan;
+    const int cols = ns >= 2 ? ns / 2 : 1;
+    const u64 twoN = 2 * (u64)N;
     std::vector<int64_t> g;
-    if (pack_plan(c, used, plan)) return g;
     bool swap = false;
-    for (auto &e : plan) {
-        if (e.first && std::find(g.begin(), g.end(), e.first) == g.end()) g.push_back(e.first);
-        swap = swap || e.second;
+    for (const SlotPiece &pc : pieces) {
+        if (pc.s) {
+            const int64_t e = (int64_t)host_powmod(5, (u64)((cols - pc.s) % cols), twoN);
+            if (std::find(g.begin(), g.end(), e) == g.end()) g.push_back(e);
+        }
+        swap = swap || pc.b;
     }
     std::sort(g.begin(), g.end());
-    if (swap) g.push_back(2 * (int64_t)c->N - 1);
+    if (swap) g.push_back((int64_t)twoN - 1);
     return g;
 }
 
-int circuit_pack(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *in, int k, int used, fhe_ct **out)
+int circuit_slot_pack(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *in, int n, const uint8_t *useful,
+                      fhe_ct **out, int n_out)
 {
-    std::vector<std::pair<int64_t, bool>> plan;
-    if (pack_plan(c, used, plan) || k != (int)plan.size())
-        return fhe_fail(c, FHE_EINVAL, "pack: n_s must be the number of inputs times the used slots");
-    std::vector<uint64_t> mask(c->ns);
-    for (int i = 0; i < c->ns; i++) mask[i] = i < used ? 1 : 0;
-    Circuit C(c, evk);
-    fhe_ct *acc = nullptr;
+    std::vector<SlotPiece> pieces;
+    if (slot_plan(c->ns, n, useful, pieces, nullptr) != n_out) return FHE_EINVAL;
+    const int ns = c->ns, cols = ns >= 2 ? ns / 2 : 1;
     const int64_t swap = 2 * (int64_t)c->N - 1;
-    for (int j = 0; j < k && !C.err; j++) {
-        fhe_ct *t = C.plain(in[j], mask, 2);
-        if (plan[j].first) t = C.rot(t, plan[j].first);
-        if (plan[j].second) t = C.rot(t, swap);
-        acc = acc ? C.add(acc, t) : t;
+    Circuit C(c, evk);
+    std::vector<fhe_ct *> acc(n_out, nullptr);
+    for (const SlotPiece &pc : pieces) {
+        if (C.err) break;
+        std::vector<uint64_t> mask(ns, 0);
+        for (int u : pc.src) mask[u] = 1;
+        fhe_ct *t = C.plain(in[pc.j], mask, 2);
+        if (pc.s) t = C.rot(t, (int64_t)host_powmod(5, (u64)((cols - pc.s) % cols), 2 * (u64)c->N));
+        if (pc.b) t = C.rot(t, swap);
+        acc[pc.o] = acc[pc.o] ? C.add(acc[pc.o], t) : t;
     }
-    if (!C.err) *out = C.release(acc);
+    if (!C.err)
+        for (int o = 0; o < n_out; o++) out[o] = C.release(acc[o]);
     C.finish();
     return C.err;
 }

@@ -298,8 +298,14 @@ void encode_slot_vector(const fhe_ctx *c, const uint64_t *v, int64_t *m);  // n_
 int op_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, int kind, fhe_ct **out);
 int circuit_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int d, fhe_ct **out);
 std::vector<int64_t> sort_galois(const fhe_ctx *c);
-std::vector<int64_t> pack_galois(const fhe_ctx *c, int used);
-int circuit_pack(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *in, int k, int used, fhe_ct **out);
+struct SlotPiece {
+    int j, o, s, b;        // input, output, column shift right, row swap
+    std::vector<int> src;  // input slots the piece moves
+};
+int slot_plan(int ns, int n, const uint8_t *useful, std::vector<SlotPiece> &pieces, std::vector<int32_t> *dest);
+std::vector<int64_t> slot_galois(int ns, int64_t N, const std::vector<SlotPiece> &pieces);
+int circuit_slot_pack(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *in, int n, const uint8_t *useful,
+                      fhe_ct **out, int n_out);
 void launch_ntt_inv_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs);
 // inverse NTT whose output limb l (of the map) is also multiplied by scale[l]/N^-1:
 // scale[l] = (N^-1 c_l mod q, Shoup word)

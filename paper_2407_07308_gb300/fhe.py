@@ -152,8 +152,8 @@ def lib() -> ctypes.CDLL:
             "fhe_sub_plain": (ci, [vp, vp, vp, POINTER(vp)]),
             "fhe_mul_plain": (ci, [vp, vp, vp, POINTER(vp)]),
             "fhe_sort_galois": (ci, [vp, vp, ci]),
-            "fhe_pack_galois": (ci, [vp, ci, vp, ci]),
-            "fhe_pack": (ci, [vp, vp, vp, ci, ci, POINTER(vp)]),
+            "fhe_slot_plan": (ci, [ci, i64, ci, vp, vp, vp, ci, vp]),
+            "fhe_slot_pack": (ci, [vp, vp, vp, ci, vp, POINTER(vp), ci]),
             "fhe_sort": (ci, [vp, vp, vp, ci, vp]),
             "fhe_compare_bivariate": (ci, [vp, vp, vp, vp, ci, POINTER(vp), POINTER(vp)]),
             "fhe_probe_int_peak": (ci, [POINTER(ctypes.c_double), POINTER(ctypes.c_double)]),
@@ -515,18 +515,35 @@ def fhe_sort_galois(ctx):
     return [int(v) for v in g[:n]]
 
 
-def fhe_pack_galois(ctx, used: int):
-    n = _check(lib().fhe_pack_galois(ctx, int(used), None, 0), ctx)
-    g = np.zeros(max(n, 1), dtype=np.int64)
-    lib().fhe_pack_galois(ctx, int(used), _ptr(g), n)
-    return [int(v) for v in g[:n]]
+def _useful(ns, useful):
+    u = np.ascontiguousarray(np.asarray(useful, dtype=bool).astype(np.uint8))
+    if u.ndim != 2 or u.shape[1] != ns:
+        raise ValueError(f"useful must be (inputs, {ns})")
+    return u
 
 
-def fhe_pack(ctx, evk, cts, used: int):
-    """n_s / used batches with values in the first `used` slots, packed into one."""
-    out = c_void_p()
-    _check(lib().fhe_pack(ctx, evk, _handles(cts), len(cts), int(used), ctypes.byref(out)), ctx)
-    return out
+def fhe_slot_plan(slots: int, ring_n: int, useful):
+    """Host-only placement: (number of outputs, dest (inputs x n_s: output *
+    n_s + slot or -1), rotation elements the plan needs)."""
+    u = _useful(slots, useful)
+    n = u.shape[0]
+    dest = np.zeros(u.shape, dtype=np.int32)
+    ng = ctypes.c_int(0)
+    _check(lib().fhe_slot_plan(int(slots), int(ring_n), n, _ptr(u), _ptr(dest), None, 0, ctypes.byref(ng)))
+    g = np.zeros(max(ng.value, 1), dtype=np.int64)
+    n_out = _check(lib().fhe_slot_plan(int(slots), int(ring_n), n, _ptr(u), None, _ptr(g), ng.value, None))
+    return n_out, dest, [int(v) for v in g[:ng.value]]
+
+
+def fhe_slot_pack(ctx, evk, cts, useful):
+    """The inputs' useful slots compacted into as few ciphertexts as the plan
+    needs (handles, caller-owned)."""
+    u = _useful(fhe_ctx_info(ctx).slots, useful)
+    if u.shape[0] != len(cts):
+        raise ValueError("one row of useful per input")
+    out = (c_void_p * max(len(cts), 1))()
+    n = _check(lib().fhe_slot_pack(ctx, evk, _handles(cts), len(cts), _ptr(u), out, len(cts)), ctx)
+    return [c_void_p(out[i]) for i in range(n)]
 
 
 def fhe_sort(ctx, evk, xs):

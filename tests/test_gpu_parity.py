@@ -564,36 +564,54 @@ def test_sort_rows_bitexact():
         g.close()
 
 
-@pytest.mark.parametrize("p,used", [(17, 1), (17, 2), (17, 4), (17, 8), (131, 1)])
-def test_pack_slots_bitexact(p, used):
-    """n_s / used batches (values in the first `used` slots, the rest garbage)
-    packed into one: decrypts to the concatenation, bit-exact with the
-    oracle's packing, op traces equal."""
-    from oracle.circuits import pack, pack_galois
+@pytest.mark.parametrize("p,kind", [(17, "lead1"), (17, "lead2"), (17, "lead4"), (17, "stride4"),
+                                    (17, "random"), (131, "lead1")])
+def test_slot_pack_bitexact(p, kind):
+    """Slot compaction (values in some slots, garbage elsewhere): every useful
+    value decrypts where the plan puts it, each output bit-exact with the
+    oracle's compaction, op traces equal."""
+    from oracle.circuits import slot_galois, slot_pack, slot_plan
+    from oracle.encoding import SlotStructure
 
     fhe = _fhe()
     logN = 10
-    gal = pack_galois(p, 2 ** logN, used)
+    N = 2 ** logN
+    ns = SlotStructure(p, N).ns
+    rnd = random.Random(p + len(kind))
+    if kind.startswith("lead"):
+        used = int(kind[4:])
+        useful = [list(range(used))] * (ns // used)
+    elif kind == "stride4":
+        useful = [[i for i in range(ns) if i % 4 == 3]] * 4
+    else:
+        useful = [sorted(rnd.sample(range(ns), rnd.randrange(1, ns))) for _ in range(5)]
+    n_out, pieces, dest = slot_plan(ns, useful)
+    gal = slot_galois(ns, N, pieces)
     params = dict(logN=logN, p=p, L=6, K=2, **CHAIN50)
-    o, g = _pair(params, seed=31 + used, galois=gal)
+    o, g = _pair(params, seed=31 + len(kind), galois=gal)
     try:
-        assert fhe.fhe_pack_galois(g.ctx, used) == gal
-        k = g.ns // used
-        rnd = random.Random(used)
-        vals = [[[rnd.randrange(p) for _ in range(g.ns)] for _ in range(2)] for _ in range(k)]
-        xg = [g.encrypt_slots(vals[j], seed=600 + j) for j in range(k)]
+        mask = np.zeros((len(useful), ns), dtype=bool)
+        for j, u_j in enumerate(useful):
+            mask[j, u_j] = True
+        assert fhe.fhe_slot_plan(g.ns, N, mask)[2] == gal
+        vals = [[[rnd.randrange(p) for _ in range(ns)] for _ in range(2)] for _ in useful]
+        xg = [g.encrypt_slots(vals[j], seed=600 + j) for j in range(len(useful))]
         fhe.fhe_trace_enable(g.ctx, True)
-        out = fhe.fhe_pack(g.ctx, g.evk, xg, used)
-        g.own(out)
+        outs = fhe.fhe_slot_pack(g.ctx, g.evk, xg, mask)
+        for h in outs:
+            g.own(h)
         trace_g = fhe.fhe_trace_get(g.ctx)
-        dec = g.decrypt(out)
-        for c in range(2):
-            want = [vals[j][c][t] for j in range(k) for t in range(used)]
-            assert [int(v) for v in dec[c]] == want
-        xo = [o.encrypt_slots(vals[j], seed=600 + j)[0] for j in range(k)]
+        assert len(outs) == n_out
+        dec = [g.decrypt(h) for h in outs]
+        for j, u_j in enumerate(useful):
+            for u in u_j:
+                q, t = divmod(dest[j][u], ns)
+                assert [int(dec[q][c][t]) for c in range(2)] == [vals[j][c][u] for c in range(2)]
+        xo = [o.encrypt_slots(vals[j], seed=600 + j)[0] for j in range(len(useful))]
         ev = o.evaluator()
-        out_o = pack(ev, xo, used)
+        outs_o = slot_pack(ev, xo, useful)
         assert trace_g == ev.trace
-        _same(out_o, g.export(out), 0)
+        for q in range(n_out):
+            _same(outs_o[q], g.export(outs[q]), 0)
     finally:
         g.close()

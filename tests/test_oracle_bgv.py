@@ -325,21 +325,88 @@ def test_sort_rows_small_ring():
     assert st.o.noise_bits(out[0], st.s) < np.log2(st.o.primes[0]) - 1
 
 
-@pytest.mark.parametrize("p,used", [(17, 1), (17, 2), (17, 4), (131, 1)])
-def test_pack_slots(p, used):
-    """Slot compaction: k = n_s / used inputs (values in the first `used`
-    slots, garbage elsewhere) packed into one ciphertext, input j's values at
-    slots [j used, (j + 1) used)."""
-    from oracle.circuits import pack, pack_galois
+def _check_plan(ns, useful, n_out, pieces, dest):
+    """The plan is a valid compaction: every useful slot lands exactly once,
+    no two land on one output slot, and each piece moves its slots by one
+    slot rotation (a column shift and an optional row swap)."""
+    cols = ns // 2 if ns >= 2 else 1
+    landed = [d for j, u_j in enumerate(useful) for d in (dest[j][u] for u in u_j)]
+    assert -1 not in landed and len(set(landed)) == len(landed) and all(d < n_out * ns for d in landed)
+    for j, o, src, s, b in pieces:
+        for u in src:
+            r, c = divmod(u, cols)
+            assert dest[j][u] == o * ns + (r ^ b) * cols + (c + s) % cols
+
+
+@pytest.mark.parametrize("ns", [2, 8, 128])
+def test_slot_plan_structured_cases(ns):
+    """Brute-force facts about the slot manager's placement: leading blocks
+    concatenate in input order (one rotation each), strided inputs interleave
+    (the convolution example, results in every fourth slot), full inputs
+    stay where they are, and the output count is the fewest possible."""
+    from oracle.circuits import slot_plan
+
+    cols = ns // 2
+    for used in [u for u in (1, 2, 4, cols, ns) if u <= ns and ns % u == 0]:
+        k = ns // used
+        useful = [list(range(used))] * k
+        n_out, pieces, dest = slot_plan(ns, useful)
+        _check_plan(ns, useful, n_out, pieces, dest)
+        assert n_out == 1 and len(pieces) == k
+        assert [dest[j][t] for j in range(k) for t in range(used)] == list(range(ns))
+    if ns >= 8:
+        useful = [[i for i in range(ns) if i % 4 == 3]] * 4
+        n_out, pieces, dest = slot_plan(ns, useful)
+        _check_plan(ns, useful, n_out, pieces, dest)
+        assert n_out == 1 and len(pieces) == 4 and [pc[3] for pc in pieces] == [0, 1, 2, 3]
+    useful = [list(range(ns))] * 3
+    n_out, pieces, dest = slot_plan(ns, useful)
+    assert n_out == 3 and all(pc[3] == 0 and pc[4] == 0 for pc in pieces)
+
+
+def test_slot_plan_random_masks():
+    """Random useful sets: the plan is valid and no output beyond the first
+    opens while an earlier one could take a slot under some rotation."""
+    from oracle.circuits import slot_plan
+
+    rnd = random.Random(3)
+    for ns in (2, 8, 16):
+        for _ in range(30):
+            useful = [sorted(rnd.sample(range(ns), rnd.randrange(0, ns + 1))) for _ in range(rnd.randrange(1, 6))]
+            n_out, pieces, dest = slot_plan(ns, useful)
+            _check_plan(ns, useful, n_out, pieces, dest)
+            total = sum(len(u) for u in useful)
+            assert (total + ns - 1) // ns <= n_out <= max(1, total) or total == 0
+            for o in range(n_out - 1):  # every output but the last is full
+                assert sum(1 for j, u_j in enumerate(useful) for u in u_j if dest[j][u] // ns == o) == ns
+
+
+@pytest.mark.parametrize("p,kind", [(17, "lead1"), (17, "lead2"), (17, "stride4"), (17, "random"), (131, "lead1")])
+def test_slot_pack_decrypts(p, kind):
+    """Slot compaction on ciphertexts: the useful values (garbage elsewhere)
+    decrypt at the slots the plan assigns them."""
+    from oracle.circuits import slot_galois, slot_pack, slot_plan
+    from oracle.encoding import SlotStructure
 
     N = 2 ** 8
-    st = OracleSetup(logN=8, p=p, L=3, K=2, seed=26, galois=pack_galois(p, N, used), **CHAIN50)
-    ns = st.ss.ns
-    k = ns // used
-    rnd = random.Random(p + used)
-    rows = [[rnd.randrange(p) for _ in range(ns)] for _ in range(k)]  # garbage beyond `used`
+    ns = SlotStructure(p, N).ns
+    rnd = random.Random(p + len(kind))
+    if kind.startswith("lead"):
+        used = int(kind[4:])
+        useful = [list(range(used))] * (ns // used)
+    elif kind == "stride4":
+        useful = [[i for i in range(ns) if i % 4 == 3]] * 4
+    else:
+        useful = [sorted(rnd.sample(range(ns), rnd.randrange(1, ns))) for _ in range(4)]
+    n_out, pieces, dest = slot_plan(ns, useful)
+    st = OracleSetup(logN=8, p=p, L=3, K=2, seed=26, galois=slot_galois(ns, N, pieces), **CHAIN50)
+    rows = [[rnd.randrange(p) for _ in range(ns)] for _ in useful]
     cts = [st.encrypt_slots([r], seed=80 + j)[0] for j, r in enumerate(rows)]
     ev = st.evaluator()
-    out = pack(ev, cts, used)
-    want = [rows[j][t] for j in range(k) for t in range(used)]
-    assert st.decrypt_slots(out) == want
+    outs = slot_pack(ev, cts, useful)
+    assert len(outs) == n_out
+    got = [st.decrypt_slots(c) for c in outs]
+    for j, u_j in enumerate(useful):
+        for u in u_j:
+            o, t = divmod(dest[j][u], ns)
+            assert got[o][t] == rows[j][u]
