@@ -318,7 +318,7 @@ int fhe_mul_plain(fhe_ctx *ctx, const fhe_ct *a, const uint64_t *slots, fhe_ct *
  * the comparison's depth + ceil(log2(p-1)) + 1 levels.  out: d new handles. */
 int fhe_sort_galois(const fhe_ctx *ctx, int64_t *galois, int cap);
 
-/* Slot manager and slot compaction (Sec. 5, "Slot Compaction"): inputs whose
+/* Slot manager and slot compaction (Sec. 5.3, "Slot Compaction"): inputs whose
  * useful values fill only some slots are compacted into as few ciphertexts as
  * the slot rotations allow, before comparison.
  *

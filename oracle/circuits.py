@@ -366,7 +366,7 @@ def sort_rows(ev: "Evaluator", xs):
 
 def slot_plan(ns: int, useful):
     """The slot manager's placement of useful slots into as few outputs as
-    possible (Sec. 5, slot compaction).  useful[j] lists input j's useful slot
+    possible (Sec. 5.3, slot compaction).  useful[j] lists input j's useful slot
     indices.  Returns (outputs, pieces, dest): each piece (j, o, src, s, b)
     moves input j's slots src to output o by shifting columns right by s and
     swapping rows when b; dest[j][u] = o n_s + slot, or -1 for a slot left

@@ -1250,7 +1250,7 @@ int circuit_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int d, 
 }
 
 // ---------------------------------------------------------------------------
-// slot compaction (the slot manager)
+// slot compaction and the slot manager (Sec. 5.3)
 // ---------------------------------------------------------------------------
 //
 // Inputs are placed in order.  The useful slots of an input still to place go,
