@@ -69,6 +69,11 @@ them) are:
     sigma_{2N-1} when b, and an addition into its output, pieces in plan
     order;
 
+  * digit extraction from F_{p^d} slots: extension.py states the reading;
+    the ciphertext's Frobenius images sigma_{p^t}(ct), t = 1 .. d-1, are
+    taken first, in order of t; digit k is then the sum over t (ascending)
+    of their products with the plaintexts lambda_k^(p^t);
+
 Every operation appends (name, level) to ``trace``; the CUDA path emits the
 same trace, and a test compares them.  The multiplication count is pinned
 against the Paterson-Stockmeyer count (8 / 23 / 30 for p = 17 / 131 / 257) and
@@ -170,6 +175,11 @@ class Evaluator:
     def mul_plain(self, a: Ct, slots) -> Ct:
         self.trace.append(("pmul", a.level))
         return self.o.mul_plain(a, self._slots().encode(slots))
+
+    def mul_plain_coeffs(self, a: Ct, coeffs) -> Ct:
+        """a times a plaintext given by its coefficients (any slot field)."""
+        self.trace.append(("pmul", a.level))
+        return self.o.mul_plain(a, coeffs)
 
     def mul_count(self) -> int:
         return sum(1 for t in self.trace if t[0] == "mul")
@@ -431,6 +441,25 @@ def slot_pack(ev: "Evaluator", cts, useful):
             t = ev.rotate(t, 2 * N - 1)
         outs[o] = t if outs[o] is None else ev.add(outs[o], t)
     return outs
+
+
+def extract_digits(ev: "Evaluator", ct: Ct, d: int, xs=None):
+    """Mod extract: the d digits of every F_{p^d} slot of ct, digit k in a
+    ciphertext of its own (F_p constants).  B_t = sigma_{p^t}(ct) for t =
+    1 .. d-1; D_k = sum_t B_t * L[k][t], t ascending (extension.ExtSlots)."""
+    from .extension import ExtSlots
+
+    xs = xs or ExtSlots(ev.p, ev.o.N, d)
+    L = xs.extraction_plaintexts()
+    B = [ct] + [ev.rotate(ct, g) for g in xs.galois()]
+    out = []
+    for k in range(d):
+        acc = None
+        for t in range(d):
+            term = ev.mul_plain_coeffs(B[t], L[k][t])
+            acc = term if acc is None else ev.add(acc, term)
+        out.append(acc)
+    return out
 
 
 def round_depth(p: int, d: int) -> int:

@@ -34,3 +34,10 @@ class OracleSetup:
 
     def decrypt_slots(self, ct):
         return self.ss.decode(self.o.decrypt_coeffs(ct, self.s))
+
+    def encrypt_coeffs(self, coeff_rows, seed):
+        """Encrypt each row of plaintext coefficients (len N) into one
+        ciphertext, with the same randomness stream as encrypt_slots."""
+        rows = np.asarray(coeff_rows, dtype=np.int64).reshape(-1, self.N)
+        r = synth.EncRandomness(seed, rows.shape[0], self.N)
+        return [self.o.encrypt(self.pk, row, r.u[i], r.e0[i], r.e1[i]) for i, row in enumerate(rows)]
