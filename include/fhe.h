@@ -318,6 +318,38 @@ int fhe_mul_plain(fhe_ctx *ctx, const fhe_ct *a, const uint64_t *slots, fhe_ct *
  * the comparison's depth + ceil(log2(p-1)) + 1 levels.  out: d new handles. */
 int fhe_sort_galois(const fhe_ctx *ctx, int64_t *galois, int cap);
 
+/* F_{p^d} slots and digit extraction ("mod extract", Sec. 2.1): a d-digit
+ * operand is held in ONE ciphertext whose every slot is an element of F_{p^d};
+ * the server splits it into d ciphertexts of F_p digits, the form the
+ * comparison calls take.
+ *
+ * Slot fields: slot s of the F_p-slot structure has the factor g_s of Y^M + 1
+ * (Y - zeta^e_s for p = 1 mod 4, Y^2 +- gamma Y - 1 for p = 3 mod 8).  For
+ * d = e deg(g_s), e a power of two with M e <= N, the subring generated by
+ * Y' = X^(N/(M e)) has one factor f_s(Y') = g_s(Y'^e) per slot: slot s is the
+ * field F_p[Y']/(f_s), and digit k of a slot element is its coefficient of
+ * Y'^k (d = 1, 2, 4 .. for p = 17 and 257; 2, 4, .. for p = 131).
+ * FHE_EUNSUPPORTED for a d the ring has no slots of.
+ *
+ * digits: count x n_s x d u64 in [0, p) (ciphertext, slot, digit; least
+ * significant first).  fhe_encrypt_ext / _explicit encode and encrypt like
+ * fhe_encrypt / _explicit.  fhe_decrypt_ext decrypts to that layout
+ * (FHE_EINVAL if the plaintext is not such an encoding).
+ *
+ * fhe_extract_digits: out[0 .. d) receive new handles, digit k of every slot
+ * as an F_p constant in out[k], at the input's level (none consumed):
+ * digit k = Tr(lambda_k x) = sum_{t<d} lambda_k^(p^t) sigma_{p^t}(x), lambda
+ * the trace-dual basis of 1, Y', .., Y'^(d-1).  Costs d - 1 rotations (keys:
+ * fhe_ext_galois, p^t mod 2N for t = 1 .. d-1) and d^2 plaintext products.
+ * fhe_ext_galois returns the count and writes up to cap elements. */
+int fhe_ext_galois(fhe_ctx *ctx, int d, int64_t *galois, int cap);
+int fhe_encrypt_ext(fhe_ctx *ctx, const fhe_pk *pk, const uint64_t *digits, int count, int d, uint64_t seed,
+                    fhe_ct **out);
+int fhe_encrypt_ext_explicit(fhe_ctx *ctx, const fhe_pk *pk, const uint64_t *digits, int count, int d,
+                             const int64_t *u, const int64_t *e0, const int64_t *e1, fhe_ct **out);
+int fhe_decrypt_ext(fhe_ctx *ctx, const fhe_sk *sk, const fhe_ct *ct, int d, uint64_t *digits);
+int fhe_extract_digits(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *ct, int d, fhe_ct **out);
+
 /* Slot manager and slot compaction (Sec. 5.3, "Slot Compaction"): inputs whose
  * useful values fill only some slots are compacted into as few ciphertexts as
  * the slot rotations allow, before comparison.

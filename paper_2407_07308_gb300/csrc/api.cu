@@ -704,6 +704,20 @@ static int encode_batch(fhe_ctx *c, const uint64_t *slots, int count, std::vecto
     return 0;
 }
 
+// F_{p^d} slot elements of a batch: digits [count][n_s][d] -> coefficients
+static int encode_batch_ext(fhe_ctx *c, const uint64_t *digits, int count, int d, std::vector<int64_t> &m)
+{
+    int err = 0;
+    const ExtTables *T = ext_tables(c, d, &err);
+    if (!T) return err;
+    const long long per = (long long)c->ns * d;
+    for (long long i = 0; i < count * per; i++)
+        if (digits[i] >= c->p) return fhe_fail(c, FHE_EINVAL, "digit out of [0, p)");
+    m.assign((size_t)count * c->N, 0);
+    for (int i = 0; i < count; i++) ext_encode(c, T, digits + i * per, m.data() + (size_t)i * c->N);
+    return 0;
+}
+
 extern "C" int fhe_encrypt_explicit(fhe_ctx *c, const fhe_pk *pk, const uint64_t *slots, int count,
                                     const int64_t *u, const int64_t *e0, const int64_t *e1, fhe_ct **out)
 {
@@ -797,6 +811,92 @@ extern "C" int fhe_decrypt(fhe_ctx *c, const fhe_sk *sk, const fhe_ct *ct, uint6
     for (int i = 0; i < count; i++)
         if (!decode_slots(c, m.data() + (size_t)i * N, slots + (size_t)i * c->ns))
             return fhe_fail(c, FHE_EINVAL, "decrypt: plaintext is not a slot encoding");
+    return 0;
+}
+
+extern "C" int fhe_ext_galois(fhe_ctx *c, int d, int64_t *galois, int cap)
+{
+    CHECK_CTX(c);
+    if (d < 1 || cap < 0 || (cap && !galois)) return FHE_EINVAL;
+    LOCK(c);
+    int err = 0;
+    const ExtTables *T = ext_tables(c, d, &err);
+    if (!T) return err;
+    for (int i = 0; i < (int)T->galois.size() && i < cap; i++) galois[i] = T->galois[i];
+    return (int)T->galois.size();
+}
+
+extern "C" int fhe_encrypt_ext(fhe_ctx *c, const fhe_pk *pk, const uint64_t *digits, int count, int d, uint64_t seed,
+                               fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!pk || !digits || !out || count < 1 || d < 1) return FHE_EINVAL;
+    LOCK(c);
+    std::vector<int64_t> m;
+    int err = encode_batch_ext(c, digits, count, d, m);
+    if (err) return err;
+    const long long n = (long long)count * c->N;
+    DevBuf du(c, sizeof(int64_t) * n, &err), d0(c, sizeof(int64_t) * n, &err), d1(c, sizeof(int64_t) * n, &err),
+        dm(c, sizeof(int64_t) * n, &err);
+    if (err) return fhe_fail(c, err, "encrypt: out of memory");
+    cudaMemcpyAsync(dm.p, m.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->stream);
+    sample_ternary(c, du.i(), n, seed, TAG_U);
+    sample_gaussian(c, d0.i(), n, seed, TAG_E0);
+    sample_gaussian(c, d1.i(), n, seed, TAG_E1);
+    fhe_ct *ct = nullptr;
+    if ((err = encrypt_dev(c, pk, dm.i(), du.i(), d0.i(), d1.i(), count, &ct))) return err;
+    if ((err = sync_check(c, "encrypt"))) {
+        fhe_ct_destroy(ct);
+        return err;
+    }
+    *out = ct;
+    return 0;
+}
+
+extern "C" int fhe_encrypt_ext_explicit(fhe_ctx *c, const fhe_pk *pk, const uint64_t *digits, int count, int d,
+                                        const int64_t *u, const int64_t *e0, const int64_t *e1, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!pk || !digits || !u || !e0 || !e1 || !out || count < 1 || d < 1) return FHE_EINVAL;
+    LOCK(c);
+    std::vector<int64_t> m;
+    int err = encode_batch_ext(c, digits, count, d, m);
+    if (err) return err;
+    const size_t vb = sizeof(int64_t) * count * c->N;
+    DevBuf du(c, vb, &err), d0(c, vb, &err), d1(c, vb, &err), dm(c, vb, &err);
+    if (err) return fhe_fail(c, err, "encrypt: out of memory");
+    cudaMemcpyAsync(du.p, u, vb, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(d0.p, e0, vb, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(d1.p, e1, vb, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(dm.p, m.data(), vb, cudaMemcpyHostToDevice, c->stream);
+    fhe_ct *ct = nullptr;
+    if ((err = encrypt_dev(c, pk, dm.i(), du.i(), d0.i(), d1.i(), count, &ct))) return err;
+    if ((err = sync_check(c, "encrypt"))) {
+        fhe_ct_destroy(ct);
+        return err;
+    }
+    *out = ct;
+    return 0;
+}
+
+extern "C" int fhe_decrypt_ext(fhe_ctx *c, const fhe_sk *sk, const fhe_ct *ct, int d, uint64_t *digits)
+{
+    CHECK_CTX(c);
+    if (!sk || !ct || !digits || ct->npoly != 2 || d < 1) return FHE_EINVAL;
+    LOCK(c);
+    int err = 0;
+    const ExtTables *T = ext_tables(c, d, &err);
+    if (!T) return err;
+    const int N = c->N, count = ct->count;
+    DevBuf dm(c, sizeof(int64_t) * count * N, &err);
+    if (err) return fhe_fail(c, err, "decrypt: out of memory");
+    if ((err = decrypt_coeffs_dev(c, sk, ct, dm.i()))) return err;
+    std::vector<int64_t> m((size_t)count * N);
+    cudaMemcpyAsync(m.data(), dm.p, sizeof(int64_t) * m.size(), cudaMemcpyDeviceToHost, c->stream);
+    if ((err = sync_check(c, "decrypt"))) return err;
+    for (int i = 0; i < count; i++)
+        if (!ext_decode(c, T, m.data() + (size_t)i * N, digits + (size_t)i * c->ns * d))
+            return fhe_fail(c, FHE_EINVAL, "decrypt: plaintext is not an F_(p^d) slot encoding");
     return 0;
 }
 
@@ -1125,6 +1225,20 @@ extern "C" int fhe_sub_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots,
 extern "C" int fhe_mul_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, fhe_ct **out)
 {
     return plain_api(c, a, slots, 2, out);
+}
+
+extern "C" int fhe_extract_digits(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *a, int d, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!evk || evk->ctx != c || !same_ctx(c, a) || a->npoly != 2 || !out || d < 1) return FHE_EINVAL;
+    LOCK(c);
+    int err = 0;
+    const ExtTables *T = ext_tables(c, d, &err);
+    if (!T) return err;
+    for (int64_t g : T->galois)
+        if (!evk->find(g)) return fhe_fail(c, FHE_ENOKEY, "extract: missing Frobenius key");
+    if ((err = circuit_extract(c, evk, a, T, out))) return err;
+    return launch_status(c, "extract");
 }
 
 extern "C" int fhe_slot_plan(int slots, int64_t ring_n, int n, const uint8_t *useful, int32_t *dest,

@@ -416,14 +416,13 @@ int op_mul_relin(fhe_ctx *c, const KeySwitchKey &rlk, const fhe_ct *a, const fhe
     return 0;
 }
 
-// Plaintext operand: the slot vector v (n_s values) encoded, its coefficients
-// lifted to (-p/2, p/2], reduced mod q_0 .. q_{level-1} and transformed:
-// [level][N] in the NTT domain, in the ciphertext `out` (count 1, one poly).
-static int plain_ntt(fhe_ctx *c, const uint64_t *v, int level, fhe_ct **out)
+// Plaintext operand: coefficients m[N] (any residues mod p) lifted to
+// (-p/2, p/2], reduced mod q_0 .. q_{level-1} and transformed: [level][N] in
+// the NTT domain, in the ciphertext `out` (count 1, one poly).
+static int plain_ntt(fhe_ctx *c, const int64_t *m_in, int level, fhe_ct **out)
 {
     const int N = c->N;
-    std::vector<int64_t> m(N);
-    encode_slot_vector(c, v, m.data());
+    std::vector<int64_t> m(m_in, m_in + N);
     const int64_t p = (int64_t)c->p;
     for (int64_t &x : m) {
         x %= p;
@@ -449,12 +448,13 @@ static int plain_ntt(fhe_ctx *c, const uint64_t *v, int level, fhe_ct **out)
     return 0;
 }
 
-// ct (+ | - | *) plaintext slot vector (kind 0 / 1 / 2); no level is consumed.
-int op_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, int kind, fhe_ct **out)
+// ct (+ | - | *) plaintext given by its coefficients (kind 0 / 1 / 2); no
+// level is consumed.
+int op_plain_coeffs(fhe_ctx *c, const fhe_ct *a, const int64_t *coeffs, int kind, fhe_ct **out)
 {
     if (kind < 0 || kind > 2 || (kind < 2 && a->npoly != 2)) return fhe_fail(c, FHE_EINVAL, "plaintext operation");
     fhe_ct *m = nullptr;
-    int err = plain_ntt(c, slots, a->level, &m);
+    int err = plain_ntt(c, coeffs, a->level, &m);
     if (err) return err;
     fhe_ct *r = ct_new(c, a->count, a->npoly, a->level, &err);
     if (r) {
@@ -469,6 +469,14 @@ int op_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, int kind, fhe_c
     if (!r) return err;
     *out = r;
     return 0;
+}
+
+// ct (+ | - | *) plaintext slot vector (n_s values in F_p; kind 0 / 1 / 2)
+int op_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, int kind, fhe_ct **out)
+{
+    std::vector<int64_t> m(c->N);
+    encode_slot_vector(c, slots, m.data());
+    return op_plain_coeffs(c, a, m.data(), kind, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -723,6 +731,16 @@ struct Circuit {
         if ((err = op_rotate(c, *key, a, &r))) return nullptr;
         dag.end(r);
         trace(c, FHE_OP_ROT, a->level);
+        return keep(r);
+    }
+    fhe_ct *plain_coeffs(const fhe_ct *a, const std::vector<int64_t> &m)
+    {
+        if (err || !a) return nullptr;
+        fhe_ct *r = nullptr;
+        dag.begin({a});
+        if ((err = op_plain_coeffs(c, a, m.data(), 2, &r))) return nullptr;
+        dag.end(r);
+        trace(c, FHE_OP_PMUL, a->level);
         return keep(r);
     }
     fhe_ct *plain(const fhe_ct *a, const std::vector<uint64_t> &slots, int kind)
@@ -1335,6 +1353,31 @@ int circuit_slot_pack(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *in, i
     }
     if (!C.err)
         for (int o = 0; o < n_out; o++) out[o] = C.release(acc[o]);
+    C.finish();
+    return C.err;
+}
+
+// ---------------------------------------------------------------------------
+// digit extraction from F_{p^d} slots (mod extract, Sec. 2.1)
+// ---------------------------------------------------------------------------
+//
+// B_t = sigma_{p^t}(a), t = 1 .. d-1, in order of t; digit k = sum_t B_t *
+// L[k][t], t ascending (extract.cu builds L).
+
+int circuit_extract(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *a, const ExtTables *T, fhe_ct **out)
+{
+    const int d = T->d;
+    Circuit C(c, evk);
+    std::vector<const fhe_ct *> B{a};
+    for (int t = 1; t < d && !C.err; t++) B.push_back(C.rot(a, T->galois[t - 1]));
+    std::vector<fhe_ct *> D(d, nullptr);
+    for (int k = 0; k < d && !C.err; k++)
+        for (int t = 0; t < d && !C.err; t++) {
+            fhe_ct *term = C.plain_coeffs(B[t], T->L[(size_t)k * d + t]);
+            D[k] = D[k] ? C.add(D[k], term) : term;
+        }
+    if (!C.err)
+        for (int k = 0; k < d; k++) out[k] = C.release(D[k]);
     C.finish();
     return C.err;
 }

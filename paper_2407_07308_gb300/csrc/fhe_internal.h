@@ -6,6 +6,7 @@
 #include <mutex>
 #include <string>
 #include <map>
+#include <memory>
 #include <unordered_map>
 #include <vector>
 
@@ -131,6 +132,14 @@ void trim_other_pools(Pool *self);
 
 struct BatchPlan;
 
+// F_{p^d} slots of one digit count (extract.cu)
+struct ExtTables {
+    int d = 0, Me = 0, stride = 0;                // slot degree, subring size, N / Me
+    std::vector<std::vector<u64>> factors, idem;  // f_s and CRT idempotents, lowest degree first
+    std::vector<std::vector<int64_t>> L;          // [k * d + t]: plaintext, slot s = lambda_{k,s}^(p^t)
+    std::vector<int64_t> galois;                  // p^t mod 2N, t = 1 .. d-1
+};
+
 struct fhe_ctx {
     // parameters
     int logN = 0, N = 0, L = 0, K = 0, np = 0;
@@ -172,6 +181,7 @@ struct fhe_ctx {
     std::vector<int> slot_exp;     // slot s <-> zeta^slot_exp[s] (linear case)
     std::vector<int> lt;           // LT polynomial coefficients c_0..c_{p-1}
     std::vector<int> ltbv;         // bivariate LT coefficients c[a p + b] (built on first use)
+    std::map<int, std::shared_ptr<ExtTables>> ext;  // F_{p^d} slot tables by d (built on first use)
 
     int ntt_variant = 0;        // NTT factorisation chosen by the autotuner
     float ntt_ms[3] = {0, 0, 0};  // timings of each variant (forward + inverse, per batch; 0 = n/a)
@@ -304,6 +314,11 @@ struct SlotPiece {
 };
 int slot_plan(int ns, int n, const uint8_t *useful, std::vector<SlotPiece> &pieces, std::vector<int32_t> *dest);
 std::vector<int64_t> slot_galois(int ns, int64_t N, const std::vector<SlotPiece> &pieces);
+const ExtTables *ext_tables(fhe_ctx *c, int d, int *err);
+void ext_encode(const fhe_ctx *c, const ExtTables *T, const uint64_t *digits, int64_t *m);
+bool ext_decode(const fhe_ctx *c, const ExtTables *T, const int64_t *m, uint64_t *digits);
+int op_plain_coeffs(fhe_ctx *c, const fhe_ct *a, const int64_t *m, int kind, fhe_ct **out);
+int circuit_extract(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *a, const ExtTables *T, fhe_ct **out);
 int circuit_slot_pack(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *in, int n, const uint8_t *useful,
                       fhe_ct **out, int n_out);
 void launch_ntt_inv_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs);

@@ -152,6 +152,11 @@ def lib() -> ctypes.CDLL:
             "fhe_sub_plain": (ci, [vp, vp, vp, POINTER(vp)]),
             "fhe_mul_plain": (ci, [vp, vp, vp, POINTER(vp)]),
             "fhe_sort_galois": (ci, [vp, vp, ci]),
+            "fhe_ext_galois": (ci, [vp, ci, vp, ci]),
+            "fhe_encrypt_ext": (ci, [vp, vp, vp, ci, ci, u64, POINTER(vp)]),
+            "fhe_encrypt_ext_explicit": (ci, [vp, vp, vp, ci, ci, vp, vp, vp, POINTER(vp)]),
+            "fhe_decrypt_ext": (ci, [vp, vp, vp, ci, vp]),
+            "fhe_extract_digits": (ci, [vp, vp, vp, ci, POINTER(vp)]),
             "fhe_slot_plan": (ci, [ci, i64, ci, vp, vp, vp, ci, vp]),
             "fhe_slot_pack": (ci, [vp, vp, vp, ci, vp, POINTER(vp), ci]),
             "fhe_sort": (ci, [vp, vp, vp, ci, vp]),
@@ -513,6 +518,56 @@ def fhe_sort_galois(ctx):
     g = np.zeros(max(n, 1), dtype=np.int64)
     lib().fhe_sort_galois(ctx, _ptr(g), n)
     return [int(v) for v in g[:n]]
+
+
+def fhe_ext_galois(ctx, d: int):
+    n = _check(lib().fhe_ext_galois(ctx, int(d), None, 0), ctx)
+    g = np.zeros(max(n, 1), dtype=np.int64)
+    lib().fhe_ext_galois(ctx, int(d), _ptr(g), n)
+    return [int(v) for v in g[:n]]
+
+
+def _ext_digits(ctx, digits, d):
+    ns = fhe_ctx_info(ctx).slots
+    a = np.ascontiguousarray(np.asarray(digits, dtype=np.uint64))
+    if a.ndim == 2:
+        a = a[None]
+    if a.ndim != 3 or a.shape[1:] != (ns, d):
+        raise ValueError(f"digits must be (count, {ns}, {d})")
+    return a
+
+
+def fhe_encrypt_ext(ctx, pk, digits, d: int, seed: int):
+    """digits (count, n_s, d) in [0, p): each slot the F_{p^d} element
+    sum_k digits[.., k] Y'^k."""
+    a = _ext_digits(ctx, digits, d)
+    out = c_void_p()
+    _check(lib().fhe_encrypt_ext(ctx, pk, _ptr(a), a.shape[0], int(d), seed, ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_encrypt_ext_explicit(ctx, pk, digits, d: int, u, e0, e1):
+    a = _ext_digits(ctx, digits, d)
+    u, e0, e1 = (np.ascontiguousarray(x, dtype=np.int64) for x in (u, e0, e1))
+    out = c_void_p()
+    _check(lib().fhe_encrypt_ext_explicit(ctx, pk, _ptr(a), a.shape[0], int(d), _ptr(u), _ptr(e0), _ptr(e1),
+                                          ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_decrypt_ext(ctx, sk, ct, d: int):
+    count = fhe_ct_shape(ct)[0]
+    ns = fhe_ctx_info(ctx).slots
+    out = np.zeros((count, ns, d), dtype=np.uint64)
+    _check(lib().fhe_decrypt_ext(ctx, sk, ct, int(d), _ptr(out)), ctx)
+    return out
+
+
+def fhe_extract_digits(ctx, evk, ct, d: int):
+    """The d digit ciphertexts (F_p constants) of an F_{p^d}-slot ciphertext."""
+    out = (c_void_p * d)()
+    _check(lib().fhe_extract_digits(ctx, evk, ct, int(d), out), ctx)
+    return [c_void_p(out[k]) for k in range(d)]
 
 
 def _useful(ns, useful):

@@ -32,6 +32,13 @@ class GpuSetup:
         r = synth.EncRandomness(seed, rows.shape[0], self.N)
         return self.own(fhe.fhe_encrypt_explicit(self.ctx, self.pk, rows, r.u, r.e0, r.e1))
 
+    def encrypt_ext(self, digits, d, seed):
+        """One batch handle of F_{p^d}-slot ciphertexts, digits (count, n_s,
+        d) (same randomness order as OracleSetup.encrypt_coeffs)."""
+        a = np.asarray(digits, dtype=np.uint64).reshape(-1, self.ns, d)
+        r = synth.EncRandomness(seed, a.shape[0], self.N)
+        return self.own(fhe.fhe_encrypt_ext_explicit(self.ctx, self.pk, a, d, r.u, r.e0, r.e1))
+
     def encrypt_each(self, slot_rows, seed):
         """One single-ciphertext handle per row."""
         rows = np.asarray(slot_rows, dtype=np.uint64).reshape(-1, self.ns)

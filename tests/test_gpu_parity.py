@@ -615,3 +615,72 @@ def test_slot_pack_bitexact(p, kind):
             _same(outs_o[q], g.export(outs[q]), 0)
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("p,d,logN", [(17, 2, 10), (131, 2, 10), (131, 4, 10), (257, 2, 10)])
+def test_extract_digits_bitexact(p, d, logN):
+    """F_{p^d}-slot encryption bit-exact with the oracle's encoding; digit
+    extraction bit-exact digit by digit, op traces equal; the digits decrypt
+    to the inputs and fhe_decrypt_ext inverts the encoding."""
+    from oracle.circuits import extract_digits
+    from oracle.extension import ExtSlots
+
+    fhe = _fhe()
+    N = 2 ** logN
+    xs = ExtSlots(p, N, d)
+    params = dict(logN=logN, p=p, L=6, K=2, **CHAIN50)
+    o, g = _pair(params, seed=43 + d, galois=xs.galois())
+    try:
+        assert fhe.fhe_ext_galois(g.ctx, d) == xs.galois()
+        rnd = np.random.default_rng(p * d)
+        digits = rnd.integers(0, p, size=(2, xs.ns, d))
+        ct = g.encrypt_ext(digits, d, seed=700)
+        assert (fhe.fhe_decrypt_ext(g.ctx, g.sk, ct, d) == digits).all()
+        co = o.encrypt_coeffs([xs.encode(digits[0].tolist())], seed=700)[0]
+        _same(co, g.export(ct), 0)
+        fhe.fhe_trace_enable(g.ctx, True)
+        out = fhe.fhe_extract_digits(g.ctx, g.evk, ct, d)
+        for h in out:
+            g.own(h)
+        trace_g = fhe.fhe_trace_get(g.ctx)
+        for k in range(d):
+            assert (g.decrypt(out[k]) == digits[:, :, k]).all()
+        ev = o.evaluator()
+        out_o = extract_digits(ev, co, d, xs)
+        assert trace_g == ev.trace
+        for k in range(d):
+            _same(out_o[k], g.export(out[k]), 0)
+    finally:
+        g.close()
+
+
+def test_extract_then_compare():
+    """Operands sent as one F_{131^2}-slot ciphertext each (values below
+    66^2): extraction on the device, then LT / EQ; decrypts to the integer
+    comparison."""
+    fhe = _fhe()
+    from oracle.extension import ExtSlots
+
+    p, d, logN = 131, 2, 11
+    xs = ExtSlots(p, 2 ** logN, d)
+    params = dict(logN=logN, p=p, L=11, K=3, **CHAIN50)
+    from tests.gpu_setup import GpuSetup
+
+    g = GpuSetup(seed=47, galois=xs.galois(), **params)
+    try:
+        b = (p + 1) // 2
+        rnd = np.random.default_rng(5)
+        xv = rnd.integers(0, b ** d, size=(3, g.ns))
+        yv = rnd.integers(0, b ** d, size=(3, g.ns))
+        yv[0] = xv[0]
+        dig = lambda v: np.stack([(v // b ** k) % b for k in range(d)], axis=-1)  # noqa: E731
+        cx = g.own(fhe.fhe_encrypt_ext(g.ctx, g.pk, dig(xv), d, 11))
+        cy = g.own(fhe.fhe_encrypt_ext(g.ctx, g.pk, dig(yv), d, 12))
+        dx = [g.own(h) for h in fhe.fhe_extract_digits(g.ctx, g.evk, cx, d)]
+        dy = [g.own(h) for h in fhe.fhe_extract_digits(g.ctx, g.evk, cy, d)]
+        lt, eq = fhe.fhe_compare(g.ctx, g.evk, dx, dy)
+        g.own(lt)
+        g.own(eq)
+        assert (g.decrypt(lt) == (xv < yv)).all() and (g.decrypt(eq) == (xv == yv)).all()
+    finally:
+        g.close()
