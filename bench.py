@@ -1131,6 +1131,102 @@ def run_compact(args):
     print(json.dumps(line), flush=True)
 
 
+def run_extract(args):
+    """Server-side digit extraction on the C2 ring (N = 2^14, p = 131, 10 x
+    50-bit + 3 special primes; slots F_{131^2}): 16 operand pairs, each
+    operand ONE ciphertext whose slots hold 2-digit values (base 66) as
+    F_{131^2} elements.  One step extracts the digits of both operands (one
+    Frobenius rotation and 4 plaintext products each) and runs LT + EQ.  The
+    comparison alone, on digits the client encrypted one ciphertext per digit,
+    is timed beside it (both op by op)."""
+    import numpy as np
+    import torch
+
+    from paper_2407_07308_gb300 import fhe, synth
+
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    ctx = fhe.fhe_ctx_create(14, 131, 10, 3, U50, 2 ** 49, 2 ** 50, allocator=fhe.torch_allocator(local),
+                             stream=stream.cuda_stream)
+    ns = fhe.fhe_ctx_info(ctx).slots
+    count, b, d = args.pairs, 66, 2
+    gal = fhe.fhe_ext_galois(ctx, d)
+    sk, pk = fhe.fhe_keygen(ctx, 10)
+    evk = fhe.fhe_evk_create(ctx, sk, gal, 11)
+    g = synth.rng(2)
+    xv = g.integers(0, b ** d, size=(count, ns))
+    yv = g.integers(0, b ** d, size=(count, ns))
+    dig = lambda v: np.stack([(v // b ** k) % b for k in range(d)], axis=-1).astype(np.uint64)  # noqa: E731
+    cx = fhe.fhe_encrypt_ext(ctx, pk, dig(xv), d, 21)
+    cy = fhe.fhe_encrypt_ext(ctx, pk, dig(yv), d, 22)
+    px = [fhe.fhe_encrypt(ctx, pk, np.ascontiguousarray(dig(xv)[:, :, k]), 23 + k) for k in range(d)]
+    py = [fhe.fhe_encrypt(ctx, pk, np.ascontiguousarray(dig(yv)[:, :, k]), 25 + k) for k in range(d)]
+
+    def with_extract(check=False):
+        dx = fhe.fhe_extract_digits(ctx, evk, cx, d)
+        dy = fhe.fhe_extract_digits(ctx, evk, cy, d)
+        lt, eq = fhe.fhe_compare(ctx, evk, dx, dy)
+        if check:
+            assert (fhe.fhe_decrypt(ctx, sk, lt) == (xv < yv)).all(), "LT mismatch"
+            assert (fhe.fhe_decrypt(ctx, sk, eq) == (xv == yv)).all(), "EQ mismatch"
+        for h in dx + dy + [lt, eq]:
+            fhe.fhe_ct_destroy(h)
+
+    def client_digits(check=False):
+        lt, eq = fhe.fhe_compare(ctx, evk, px, py)
+        if check:
+            assert (fhe.fhe_decrypt(ctx, sk, lt) == (xv < yv)).all(), "LT mismatch"
+        for h in (lt, eq):
+            fhe.fhe_ct_destroy(h)
+
+    def timed(fn):
+        fn(check=True)
+        for _ in range(args.warmup - 1):
+            fn()
+        fhe.fhe_ctx_sync(ctx)
+        l0 = fhe.fhe_ctx_launches(ctx)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        torch.cuda.synchronize()
+        with Clocks(local) as clk:
+            evs[0].record(stream)
+            for i in range(args.steps):
+                fn()
+                evs[i + 1].record(stream)
+            stream.synchronize()
+        return evs[0].elapsed_time(evs[-1]), fhe.fhe_ctx_launches(ctx) - l0, clk.summary()
+
+    t_p, _, _ = timed(client_digits)
+    t_e, launches, clk = timed(with_extract)
+    cmp_per_step = count * ns
+    ct_bytes = 2 * 10 * 2 ** 14 * 8 * count  # one operand's ciphertexts at the top level
+    line = {
+        "metric": "encrypted slot-comparisons/sec at N=2^14,p=131,d=2 with server-side digit extraction from "
+                  "F_{131^2} slots",
+        "value": round(cmp_per_step * args.steps / (t_e / 1e3), 1), "unit": "slot-comparisons/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_e / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded BGV keys, noise and values in [0, 66^2))",
+        "config": {"workload": f"{count} operand pairs, one F_(131^2)-slot ciphertext per operand; per step: digit "
+                               "extraction of both operands (1 Frobenius rotation + 4 plaintext products each), "
+                               "then LT+EQ; op by op; 10x50-bit + 3 special primes",
+                   "operand_bytes_per_step": {"extracted_on_server": 2 * ct_bytes,
+                                              "digits_from_client": 2 * d * ct_bytes},
+                   "l2": "ciphertexts 42 MB per operand, 336 MB of working set per step > L2"},
+        "digits_from_client": {"value": round(cmp_per_step * args.steps / (t_p / 1e3), 1),
+                               "unit": "slot-comparisons/s", "ms_per_step": round(t_p / args.steps, 2)},
+        "extract_ms_per_step": round((t_e - t_p) / args.steps, 2),
+        "gpu_launches": launches, "clocks": clk, "cpu_baseline": None, "roofline": None, "e2e": None,
+    }
+    for h in [cx, cy] + px + py:
+        fhe.fhe_ct_destroy(h)
+    fhe.fhe_evk_destroy(evk)
+    fhe.fhe_sk_destroy(sk)
+    fhe.fhe_pk_destroy(pk)
+    fhe.fhe_ctx_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1143,11 +1239,12 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the one-request-at-a-time form")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--workload", default="compare", choices=["compare", "small", "bivariate", "uneven", "serve", "tournament", "sort",
-                                                          "compact"],
+                                                          "compact", "extract"],
                     help="compare: the 16-pair batch (default); small: one pair on the small ring; bivariate: "
                          "the 16-pair batch on full digits; uneven: "
                          "256 mixed requests; serve: serving loop; tournament: max/min of 4096 values; sort: rows of 64 "
-                         "values sorted; compact: slot compaction before comparison")
+                         "values sorted; compact: slot compaction before comparison; extract: server-side digit extraction from "
+                         "F_(p^d) slots, then comparison")
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate (requests/s) for serve")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -1175,6 +1272,8 @@ def main():
         run_sort(args)
     elif args.workload == "compact":
         run_compact(args)
+    elif args.workload == "extract":
+        run_extract(args)
     else:
         run_gpu(args)
 
