@@ -74,6 +74,12 @@ them) are:
     taken first, in order of t; digit k is then the sum over t (ascending)
     of their products with the plaintexts lambda_k^(p^t);
 
+  * private query (non-blocking comparison application): EQ(q, k) for a
+    public code k is 1 - (q - k)^(p-1) with z = q + (-k) (a constant
+    addition) and the power rule above; the three EQs come first, in code
+    order, then data + op1, data * op1, data^op2 (power rule), then
+    ((r1 c1 + r2 c2) + r3 c3);
+
 Every operation appends (name, level) to ``trace``; the CUDA path emits the
 same trace, and a test compares them.  The multiplication count is pinned
 against the Paterson-Stockmeyer count (8 / 23 / 30 for p = 17 / 131 / 257) and
@@ -441,6 +447,49 @@ def slot_pack(ev: "Evaluator", cts, useful):
             t = ev.rotate(t, 2 * N - 1)
         outs[o] = t if outs[o] is None else ev.add(outs[o], t)
     return outs
+
+
+def _powers(ev: "Evaluator", x: Ct):
+    """z^n by the fixed power rule (n = 1: z; n a power of two: square of
+    z^(n/2); else z^(2^a) z^(n - 2^a), 2^a the largest power of two below n),
+    results cached."""
+    pw = {1: x}
+
+    def power(n: int) -> Ct:
+        if n in pw:
+            return pw[n]
+        if n & (n - 1) == 0:
+            h = power(n // 2)
+            r = ev.mul(h, h)
+        else:
+            a = 1 << (n.bit_length() - 1)
+            r = ev.mul(power(a), power(n - a))
+        pw[n] = r
+        return r
+
+    return power
+
+
+def eq_const(ev: "Evaluator", x: Ct, k: int) -> Ct:
+    """EQ(x, k) for a public constant k: 1 - (x - k)^(p-1)."""
+    z = ev.add_const(x, -k)
+    return ev.add_const(ev.neg(_powers(ev, z)(ev.p - 1)), 1)
+
+
+def private_query(ev: "Evaluator", q: Ct, data: Ct, op1: Ct, op2: int, codes) -> Ct:
+    """The private query of Sec. 5.3 with its branches straight-lined: the
+    query type q is compared with the three public codes (add, multiply,
+    power); the three candidate results data + op1, data * op1 and
+    data^op2 are computed; the answer is sum_i result_i * EQ(q, code_i).
+    Issue order: the branch evaluation (the three EQs, in code order), then
+    the three results, then the selection."""
+    c = [eq_const(ev, q, k) for k in codes]
+    r1 = ev.add(data, op1)
+    r2 = ev.mul(data, op1)
+    r3 = _powers(ev, data)(op2)
+    out = ev.mul(r1, c[0])
+    out = ev.add(out, ev.mul(r2, c[1]))
+    return ev.add(out, ev.mul(r3, c[2]))
 
 
 def extract_digits(ev: "Evaluator", ct: Ct, d: int, xs=None):

@@ -410,3 +410,25 @@ def test_slot_pack_decrypts(p, kind):
         for u in u_j:
             o, t = divmod(dest[j][u], ns)
             assert got[o][t] == rows[j][u]
+
+def test_private_query_decrypts():
+    """Straight-lined private query (Sec. 5.3): per slot, the answer is
+    data + op1, data * op1 or data^3 as the encrypted query type selects
+    (codes 1, 2, 3), and 0 for any other type."""
+    from oracle.circuits import eq_const, private_query
+
+    p = 17
+    st = OracleSetup(logN=8, p=p, L=8, K=2, seed=51, **CHAIN50)
+    ns = st.ss.ns
+    rnd = random.Random(4)
+    qv = [rnd.randrange(5) for _ in range(ns)]
+    qv[:4] = [0, 1, 2, 3]
+    dv = [rnd.randrange(p) for _ in range(ns)]
+    ov = [rnd.randrange(p) for _ in range(ns)]
+    q, data, op1 = (st.encrypt_slots([v], seed=60 + i)[0] for i, v in enumerate((qv, dv, ov)))
+    ev = st.evaluator()
+    assert st.decrypt_slots(eq_const(ev, q, 2)) == [int(v == 2) for v in qv]
+    out = private_query(ev, q, data, op1, 3, (1, 2, 3))
+    want = [((d + o) if t == 1 else (d * o) if t == 2 else d ** 3 if t == 3 else 0) % p
+            for t, d, o in zip(qv, dv, ov)]
+    assert st.decrypt_slots(out) == want
