@@ -1227,6 +1227,90 @@ def run_extract(args):
     print(json.dumps(line), flush=True)
 
 
+def run_query(args):
+    """Private query with non-blocking comparison on the C2 ring (N = 2^14,
+    p = 131, 10 x 50-bit + 3 special primes): one ciphertext each of query
+    type, data and operand (2 slots); answer = sum over {data + op1, data *
+    op1, data^4} of candidate * EQ(type, code).  One step = one query.  The
+    latency with the comparison branch overlapping the arithmetic (dependency
+    scheduler, several streams) is timed beside the in-order form."""
+    import numpy as np
+    import torch
+
+    from paper_2407_07308_gb300 import fhe
+
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    p = 131
+    ctx = fhe.fhe_ctx_create(14, p, 10, 3, U50, 2 ** 49, 2 ** 50, allocator=fhe.torch_allocator(local),
+                             stream=stream.cuda_stream)
+    ns = fhe.fhe_ctx_info(ctx).slots
+    sk, pk = fhe.fhe_keygen(ctx, 12)
+    evk = fhe.fhe_evk_create(ctx, sk, [], 13)
+    g = np.random.default_rng(7)
+    qv = np.array([[1, 3]], dtype=np.uint64)[:, :ns]
+    dv = g.integers(0, p, size=(1, ns)).astype(np.uint64)
+    ov = g.integers(0, p, size=(1, ns)).astype(np.uint64)
+    q, data, op1 = (fhe.fhe_encrypt(ctx, pk, v, 30 + i) for i, v in enumerate((qv, dv, ov)))
+    want = np.where(qv == 1, (dv + ov) % p, np.where(qv == 2, dv * ov % p, np.where(qv == 3, dv ** 4 % p, 0)))
+
+    def one(overlap, check=False):
+        out = fhe.fhe_private_query(ctx, evk, q, data, op1, 4, (1, 2, 3), overlap=overlap)
+        if check:
+            assert (fhe.fhe_decrypt(ctx, sk, out) == want).all(), "query mismatch"
+        fhe.fhe_ct_destroy(out)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(overlap):
+        one(overlap, check=True)
+        for _ in range(args.warmup - 1):
+            one(overlap)
+        fhe.fhe_ctx_sync(ctx)
+        l0 = fhe.fhe_ctx_launches(ctx)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+        with Clocks(local) as clk:
+            for i in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(i & 0xFF)
+                torch.cuda.synchronize()
+                evs[2 * i].record(stream)
+                one(overlap)
+                evs[2 * i + 1].record(stream)
+                stream.synchronize()
+            torch.cuda.synchronize()
+        ms = sorted(evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(args.steps))
+        return ms, fhe.fhe_ctx_launches(ctx) - l0, clk.summary()
+
+    ms_in, _, _ = timed(False)
+    ms_ov, launches, clk = timed(True)
+    med = lambda v: v[len(v) // 2]  # noqa: E731
+    total = sum(ms_ov)
+    line = {
+        "metric": "private queries per second with non-blocking comparison (N=2^14, p=131, one ciphertext per "
+                  "operand; latency-bound)",
+        "value": round(args.steps / (total / 1e3), 2), "unit": "queries/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded BGV keys, noise and values)",
+        "config": {"workload": "one private query: EQ of the encrypted query type with codes 1, 2, 3 (p-1 = 130: "
+                               "8 squarings + 1 product each), candidates data+op1, data*op1, data^4, selection; "
+                               "10x50-bit + 3 special primes",
+                   "l2": "a 256 MB buffer is written before every timed query (outside the events)"},
+        "latency_ms": {"overlap_p50": round(med(ms_ov), 2), "in_order_p50": round(med(ms_in), 2),
+                       "overlap_max": round(ms_ov[-1], 2), "in_order_max": round(ms_in[-1], 2)},
+        "gpu_launches": launches, "clocks": clk, "cpu_baseline": None, "roofline": None, "e2e": None,
+    }
+    for h in (q, data, op1):
+        fhe.fhe_ct_destroy(h)
+    fhe.fhe_evk_destroy(evk)
+    fhe.fhe_sk_destroy(sk)
+    fhe.fhe_pk_destroy(pk)
+    fhe.fhe_ctx_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1239,12 +1323,12 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the one-request-at-a-time form")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--workload", default="compare", choices=["compare", "small", "bivariate", "uneven", "serve", "tournament", "sort",
-                                                          "compact", "extract"],
+                                                          "compact", "extract", "query"],
                     help="compare: the 16-pair batch (default); small: one pair on the small ring; bivariate: "
                          "the 16-pair batch on full digits; uneven: "
                          "256 mixed requests; serve: serving loop; tournament: max/min of 4096 values; sort: rows of 64 "
                          "values sorted; compact: slot compaction before comparison; extract: server-side digit extraction from "
-                         "F_(p^d) slots, then comparison")
+                         "F_(p^d) slots, then comparison; query: private query with non-blocking comparison")
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate (requests/s) for serve")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -1274,6 +1358,8 @@ def main():
         run_compact(args)
     elif args.workload == "extract":
         run_extract(args)
+    elif args.workload == "query":
+        run_query(args)
     else:
         run_gpu(args)
 

@@ -318,6 +318,23 @@ int fhe_mul_plain(fhe_ctx *ctx, const fhe_ct *a, const uint64_t *slots, fhe_ct *
  * the comparison's depth + ceil(log2(p-1)) + 1 levels.  out: d new handles. */
 int fhe_sort_galois(const fhe_ctx *ctx, int64_t *galois, int cap);
 
+/* Private query with straight-lined branches and non-blocking comparison
+ * (Sec. 5.3): q holds the encrypted query type, compared for equality with
+ * the three public codes codes[0..2] (add, multiply, power); the answer is
+ *   (data + op1) EQ(q, codes[0]) + (data * op1) EQ(q, codes[1])
+ *     + data^op2 EQ(q, codes[2]),
+ * with EQ(q, k) = 1 - (q - k)^(p-1) (so 0 where q matches no code).  q, data
+ * and op1: equal count, any levels (products align levels by switching
+ * down).  Consumes ceil(log2(p-1)) + 1 levels beyond the lowest input, or
+ * more when op2 needs a longer power chain.  flags FHE_QUERY_OVERLAP: the
+ * comparison branch and the arithmetic are issued to the dependency
+ * scheduler's streams and run concurrently on the device (the paper's helper
+ * thread), joining at the selection; 0 issues everything on the context's
+ * stream in order.  Same residues either way. */
+enum { FHE_QUERY_OVERLAP = 1 };
+int fhe_private_query(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *q, const fhe_ct *data, const fhe_ct *op1,
+                      int op2, const int64_t *codes, int flags, fhe_ct **out);
+
 /* F_{p^d} slots and digit extraction ("mod extract", Sec. 2.1): a d-digit
  * operand is held in ONE ciphertext whose every slot is an element of F_{p^d};
  * the server splits it into d ciphertexts of F_p digits, the form the

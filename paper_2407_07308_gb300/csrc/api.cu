@@ -1241,6 +1241,20 @@ extern "C" int fhe_extract_digits(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *
     return launch_status(c, "extract");
 }
 
+extern "C" int fhe_private_query(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *q, const fhe_ct *data,
+                                 const fhe_ct *op1, int op2, const int64_t *codes, int flags, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!evk || evk->ctx != c || !same_ctx(c, q) || !same_ctx(c, data) || !same_ctx(c, op1) || !codes || !out ||
+        op2 < 1 || op2 >= (1 << 20) || (flags & ~FHE_QUERY_OVERLAP))
+        return FHE_EINVAL;
+    if (q->npoly != 2 || data->npoly != 2 || op1->npoly != 2 || q->count != data->count || op1->count != data->count)
+        return fhe_fail(c, FHE_EMISMATCH, "private query: operands differ in shape");
+    LOCK(c);
+    const int e = circuit_private_query(c, evk, q, data, op1, op2, codes, (flags & FHE_QUERY_OVERLAP) != 0, out);
+    return e ? e : launch_status(c, "private_query");
+}
+
 extern "C" int fhe_slot_plan(int slots, int64_t ring_n, int n, const uint8_t *useful, int32_t *dest,
                              int64_t *galois, int galois_cap, int *n_galois)
 {

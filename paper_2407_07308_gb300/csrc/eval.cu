@@ -1382,6 +1382,68 @@ int circuit_extract(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *a, const ExtTa
     return C.err;
 }
 
+// ---------------------------------------------------------------------------
+// private query with straight-lined branches (Sec. 5.3, non-blocking comparison)
+// ---------------------------------------------------------------------------
+//
+// EQ(q, code_i) = 1 - (q - code_i)^(p-1) for the three public codes, then the
+// candidates data + op1, data * op1, data^op2, then
+// ((r1 EQ_1 + r2 EQ_2) + r3 EQ_3).  With overlap the circuit runs under the
+// dependency scheduler: every operation is issued on one of its streams after
+// its inputs, so the comparison branch and the arithmetic run concurrently on
+// the device and join only at the selection.  The results are the same
+// residues either way.
+
+int circuit_private_query(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *q, const fhe_ct *data, const fhe_ct *op1,
+                          int op2, const int64_t *codes, bool overlap, fhe_ct **out)
+{
+    const bool was = c->multistream;
+    c->multistream = overlap;
+    int e = 0;
+    {
+        Circuit C(c, evk);
+        auto power_of = [&C](const fhe_ct *x, int n) -> fhe_ct * {
+            std::map<int, const fhe_ct *> pw;
+            pw[1] = x;
+            std::function<const fhe_ct *(int)> power = [&](int m) -> const fhe_ct * {
+                auto it = pw.find(m);
+                if (it != pw.end()) return it->second;
+                const fhe_ct *r;
+                if ((m & (m - 1)) == 0) {
+                    const fhe_ct *h = power(m / 2);
+                    r = C.mul(h, h);
+                } else {
+                    int a = 1;
+                    while (a * 2 < m) a *= 2;
+                    const fhe_ct *A = power(a);
+                    const fhe_ct *Bp = power(m - a);
+                    r = C.mul(A, Bp);
+                }
+                pw[m] = r;
+                return r;
+            };
+            return const_cast<fhe_ct *>(power(n));
+        };
+        const int p = (int)c->p;
+        fhe_ct *eq[3];
+        for (int i = 0; i < 3; i++) {
+            fhe_ct *z = C.cadd(q, -codes[i]);
+            eq[i] = C.cadd(C.neg(power_of(z, p - 1)), 1);
+        }
+        fhe_ct *r1 = C.add(data, op1);
+        fhe_ct *r2 = C.mul(data, op1);
+        fhe_ct *r3 = power_of(data, op2);
+        fhe_ct *o = C.mul(r1, eq[0]);
+        o = C.add(o, C.mul(r2, eq[1]));
+        o = C.add(o, C.mul(r3, eq[2]));
+        if (!C.err) *out = C.release(o);
+        C.finish();
+        e = C.err;
+    }
+    c->multistream = was;
+    return e;
+}
+
 std::vector<int64_t> tournament_galois(const fhe_ctx *c)
 {
     std::vector<int64_t> g;

@@ -318,6 +318,8 @@ const ExtTables *ext_tables(fhe_ctx *c, int d, int *err);
 void ext_encode(const fhe_ctx *c, const ExtTables *T, const uint64_t *digits, int64_t *m);
 bool ext_decode(const fhe_ctx *c, const ExtTables *T, const int64_t *m, uint64_t *digits);
 int op_plain_coeffs(fhe_ctx *c, const fhe_ct *a, const int64_t *m, int kind, fhe_ct **out);
+int circuit_private_query(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *q, const fhe_ct *data, const fhe_ct *op1,
+                          int op2, const int64_t *codes, bool overlap, fhe_ct **out);
 int circuit_extract(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *a, const ExtTables *T, fhe_ct **out);
 int circuit_slot_pack(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *in, int n, const uint8_t *useful,
                       fhe_ct **out, int n_out);

@@ -152,6 +152,7 @@ def lib() -> ctypes.CDLL:
             "fhe_sub_plain": (ci, [vp, vp, vp, POINTER(vp)]),
             "fhe_mul_plain": (ci, [vp, vp, vp, POINTER(vp)]),
             "fhe_sort_galois": (ci, [vp, vp, ci]),
+            "fhe_private_query": (ci, [vp, vp, vp, vp, vp, ci, vp, ci, POINTER(vp)]),
             "fhe_ext_galois": (ci, [vp, ci, vp, ci]),
             "fhe_encrypt_ext": (ci, [vp, vp, vp, ci, ci, u64, POINTER(vp)]),
             "fhe_encrypt_ext_explicit": (ci, [vp, vp, vp, ci, ci, vp, vp, vp, POINTER(vp)]),
@@ -518,6 +519,21 @@ def fhe_sort_galois(ctx):
     g = np.zeros(max(n, 1), dtype=np.int64)
     lib().fhe_sort_galois(ctx, _ptr(g), n)
     return [int(v) for v in g[:n]]
+
+
+FHE_QUERY_OVERLAP = 1
+
+
+def fhe_private_query(ctx, evk, q, data, op1, op2: int, codes, overlap: bool = True):
+    """sum over the three candidates (data + op1, data * op1, data^op2) of
+    candidate * EQ(q, code); overlap runs the comparison branch concurrently
+    with the arithmetic."""
+    cd = np.ascontiguousarray(np.asarray(codes, dtype=np.int64))
+    assert cd.shape == (3,)
+    out = c_void_p()
+    _check(lib().fhe_private_query(ctx, evk, q, data, op1, int(op2), _ptr(cd),
+                                   FHE_QUERY_OVERLAP if overlap else 0, ctypes.byref(out)), ctx)
+    return out
 
 
 def fhe_ext_galois(ctx, d: int):

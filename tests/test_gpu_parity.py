@@ -636,7 +636,7 @@ def test_extract_digits_bitexact(p, d, logN):
         digits = rnd.integers(0, p, size=(2, xs.ns, d))
         ct = g.encrypt_ext(digits, d, seed=700)
         assert (fhe.fhe_decrypt_ext(g.ctx, g.sk, ct, d) == digits).all()
-        co = o.encrypt_coeffs([xs.encode(digits[0].tolist())], seed=700)[0]
+        co = o.encrypt_coeffs([xs.encode(digits[c].tolist()) for c in range(2)], seed=700)[0]
         _same(co, g.export(ct), 0)
         fhe.fhe_trace_enable(g.ctx, True)
         out = fhe.fhe_extract_digits(g.ctx, g.evk, ct, d)
@@ -682,5 +682,39 @@ def test_extract_then_compare():
         g.own(lt)
         g.own(eq)
         assert (g.decrypt(lt) == (xv < yv)).all() and (g.decrypt(eq) == (xv == yv)).all()
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("overlap", [False, True])
+def test_private_query_bitexact(overlap):
+    """Private query (branches straight-lined): bit-exact with the oracle,
+    op traces equal, whether the comparison branch overlaps the arithmetic
+    on the scheduler's streams or not; decrypts to the selected candidate."""
+    from oracle.circuits import private_query
+
+    fhe = _fhe()
+    p, logN = 17, 10
+    params = dict(logN=logN, p=p, L=8, K=2, **CHAIN50)
+    o, g = _pair(params, seed=53)
+    try:
+        rnd = random.Random(6)
+        rows = lambda hi: [[rnd.randrange(hi) for _ in range(g.ns)] for _ in range(2)]  # noqa: E731
+        qv, dv, ov = rows(5), rows(p), rows(p)
+        qv[0][:4] = [0, 1, 2, 3]
+        qg, dg, og = (g.encrypt_slots(v, seed=800 + i) for i, v in enumerate((qv, dv, ov)))
+        fhe.fhe_trace_enable(g.ctx, True)
+        out = g.own(fhe.fhe_private_query(g.ctx, g.evk, qg, dg, og, 3, (1, 2, 3), overlap=overlap))
+        trace_g = fhe.fhe_trace_get(g.ctx)
+        dec = g.decrypt(out)
+        for c in range(2):
+            want = [((d + x) if t == 1 else (d * x) if t == 2 else d ** 3 if t == 3 else 0) % p
+                    for t, d, x in zip(qv[c], dv[c], ov[c])]
+            assert [int(v) for v in dec[c]] == want
+        qo, do, oo = (o.encrypt_slots(v, seed=800 + i)[0] for i, v in enumerate((qv, dv, ov)))
+        ev = o.evaluator()
+        out_o = private_query(ev, qo, do, oo, 3, (1, 2, 3))
+        assert trace_g == ev.trace
+        _same(out_o, g.export(out), 0)
     finally:
         g.close()
