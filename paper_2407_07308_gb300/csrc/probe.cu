@@ -41,7 +41,71 @@ __global__ void k_probe_mulhi64(u64 *out, u64 seed)
     out[blockIdx.x * blockDim.x + threadIdx.x] = r;
 }
 
+// The NTT's butterfly (Harvey's lazy forward butterfly with a Shoup twiddle:
+// t = Y w - floor(Y w' / 2^64) q, X <- X + t, Y <- X - t + 2q) on 8
+// register-resident values per thread, three butterfly layers per iteration
+// (strides 4, 2, 1) so that every value depends on every other: the roof of
+// the NTT's arithmetic with no memory traffic at all.
+constexpr int BFLY_ITERS = 512;
+
+__global__ void k_probe_bfly(u64 *out, u64 seed, u64 q, u64 w, u64 ws)
+{
+    u64 x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = seed + threadIdx.x * 8 + k;
+    const u64 q2 = 2 * q;
+    for (int i = 0; i < BFLY_ITERS; i++) {
+#pragma unroll
+        for (int h = 4; h >= 1; h >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                if (k & h) continue;
+                const u64 t = shoup_lazy(x[k + h], w, ws, q);
+                const u64 a = x[k];
+                x[k] = a + t;
+                x[k + h] = a - t + q2;
+            }
+        }
+    }
+    u64 r = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) r ^= x[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
 }  // namespace
+
+// Butterflies per second over all SMs (k_probe_bfly with a 50-bit prime and
+// twiddle).  Synchronises; allocates a small buffer.
+extern "C" int fhe_probe_bfly_peak(double *bfly)
+{
+    if (!bfly) return FHE_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return FHE_ECUDA;
+    const int threads = 256, blocks = sms * 8;
+    void *buf = nullptr;
+    if (cudaMalloc(&buf, sizeof(u64) * threads * blocks) != cudaSuccess) return FHE_ENOMEM;
+    const u64 q = 564395044569089ull, w = 123456789012345ull % q;
+    const u64 ws = (u64)(((unsigned __int128)w << 64) / q);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int r = 0; r < 2; r++) k_probe_bfly<<<blocks, threads>>>((u64 *)buf, 1ull, q, w, ws);
+    cudaEventRecord(e0);
+    for (int r = 0; r < 10; r++) k_probe_bfly<<<blocks, threads>>>((u64 *)buf, (u64)r, q, w, ws);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    *bfly = 10.0 * threads * blocks * BFLY_ITERS * 12 / (ms / 1e3);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const cudaError_t e = cudaGetLastError();
+    cudaFree(buf);
+    return e == cudaSuccess ? 0 : FHE_ECUDA;
+}
 
 // Writes the measured rates (operations per second, all SMs) to
 // imad32[0] and mulhi64[0].  Synchronises; allocates a small buffer.

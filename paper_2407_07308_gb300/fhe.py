@@ -152,6 +152,7 @@ def lib() -> ctypes.CDLL:
             "fhe_sub_plain": (ci, [vp, vp, vp, POINTER(vp)]),
             "fhe_mul_plain": (ci, [vp, vp, vp, POINTER(vp)]),
             "fhe_sort_galois": (ci, [vp, vp, ci]),
+            "fhe_probe_bfly_peak": (ci, [vp]),
             "fhe_private_query": (ci, [vp, vp, vp, vp, vp, ci, vp, ci, POINTER(vp)]),
             "fhe_ext_galois": (ci, [vp, ci, vp, ci]),
             "fhe_encrypt_ext": (ci, [vp, vp, vp, ci, ci, u64, POINTER(vp)]),
@@ -732,6 +733,12 @@ def fhe_ctx_set_batch_graphs(ctx, max_plans: int):
 
 def fhe_ctx_fused_modswitch(ctx, on: bool):
     _check(lib().fhe_ctx_fused_modswitch(ctx, int(bool(on))), ctx)
+
+
+def fhe_probe_bfly_peak():
+    v = ctypes.c_double()
+    _check(lib().fhe_probe_bfly_peak(ctypes.byref(v)))
+    return v.value
 
 
 def fhe_probe_int_peak():
