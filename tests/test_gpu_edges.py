@@ -154,3 +154,97 @@ def test_malformed_calls_are_refused():
     finally:
         fhe.fhe_ctx_destroy(ctx)
         fhe.fhe_ctx_destroy(other)
+
+
+def test_slot_pack_mixed_levels_bitexact_and_refusals():
+    """Compaction of inputs at different levels (sums are taken at the lower
+    level): bit-exact with the oracle; an output array that is too small, a
+    missing rotation key and a mask of the wrong shape are refused."""
+    from oracle.circuits import slot_galois, slot_pack, slot_plan
+    from paper_2407_07308_gb300 import fhe
+    from tests.gpu_setup import GpuSetup
+    from tests.oracle_setup import OracleSetup
+
+    p, logN, L = 17, 10, 6
+    ns = 8
+    useful = [[0, 1]] * 4
+    n_out, pieces, dest = slot_plan(ns, useful)
+    gal = slot_galois(ns, 2 ** logN, pieces)
+    params = dict(logN=logN, p=p, L=L, K=2, **CHAIN50)
+    g = GpuSetup(seed=61, galois=gal, **params)
+    o = OracleSetup(seed=61, galois=gal, **params)
+    try:
+        rnd = np.random.default_rng(9)
+        vals = rnd.integers(0, p, size=(4, 1, ns))
+        xg = [g.encrypt_slots(vals[j], seed=900 + j) for j in range(4)]
+        xo = [o.encrypt_slots(vals[j], seed=900 + j)[0] for j in range(4)]
+        drops = {1: L - 2, 3: L - 1}
+        for j, lv in drops.items():
+            xg[j] = g.own(fhe.fhe_mod_switch(g.ctx, xg[j], lv))
+            for _ in range(L - lv):
+                xo[j] = o.o.modswitch(xo[j])
+        mask = np.zeros((4, ns), dtype=bool)
+        mask[:, :2] = True
+        fhe.fhe_trace_enable(g.ctx, True)
+        out = fhe.fhe_slot_pack(g.ctx, g.evk, xg, mask)
+        for h in out:
+            g.own(h)
+        trace_g = fhe.fhe_trace_get(g.ctx)
+        ev = o.evaluator()
+        out_o = slot_pack(ev, xo, useful)
+        assert trace_g == ev.trace
+        assert np.array_equal(g.export(out[0])[0], out_o[0].data)
+        assert fhe.fhe_ct_shape(out[0])[2] == L - 2
+        dec = g.decrypt(out[0])[0]
+        assert [int(dec[dest[j][u]]) for j in range(4) for u in (0, 1)] == [int(vals[j, 0, u]) for j in range(4)
+                                                                           for u in (0, 1)]
+        # refusals
+        arr = (fhe.c_void_p * 1)()
+        handles = fhe._handles(xg)
+        u8 = np.ascontiguousarray(mask.astype(np.uint8))
+        spread = np.zeros((4, ns), dtype=bool)
+        spread[:, 0] = True
+        spread[0, :] = True  # input 0 full: 2 outputs
+        assert fhe.lib().fhe_slot_pack(g.ctx, g.evk, handles, 4, fhe._ptr(np.ascontiguousarray(spread.astype(np.uint8))),
+                                       arr, 1) == -1
+        bare = fhe.fhe_evk_create(g.ctx, g.sk, [], 7)
+        try:
+            assert fhe.lib().fhe_slot_pack(g.ctx, bare, handles, 4, fhe._ptr(u8), arr, 1) == -8
+        finally:
+            fhe.fhe_evk_destroy(bare)
+        with pytest.raises(ValueError):
+            fhe.fhe_slot_pack(g.ctx, g.evk, xg, mask[:, :4])
+    finally:
+        g.close()
+
+
+def test_extract_and_query_refusals_and_degenerate_cases():
+    """Digit extraction: a digit count the ring has no slots of and a missing
+    Frobenius key are refused.  Private query: op2 = 1 (the data itself is a
+    candidate) and query types matching no code (answer 0)."""
+    from paper_2407_07308_gb300 import fhe
+    from tests.gpu_setup import GpuSetup
+
+    p, logN = 17, 10
+    g = GpuSetup(seed=63, logN=logN, p=p, L=8, K=2, **CHAIN50)
+    try:
+        ns = g.ns
+        with pytest.raises(fhe.FheError) as e:
+            fhe.fhe_ext_galois(g.ctx, 3)
+        assert e.value.code == -9
+        ct = g.own(fhe.fhe_encrypt_ext(g.ctx, g.pk, np.zeros((1, ns, 2), dtype=np.uint64), 2, 5))
+        with pytest.raises(fhe.FheError) as e:
+            fhe.fhe_extract_digits(g.ctx, g.evk, ct, 2)  # no sigma_17 key in this evk
+        assert e.value.code == -8
+        rnd = np.random.default_rng(3)
+        qv = np.array([[1, 0, 4, 5, 1, 6, 7, 1]], dtype=np.uint64)[:, :ns]
+        dv = rnd.integers(0, p, size=(1, ns)).astype(np.uint64)
+        ov = rnd.integers(0, p, size=(1, ns)).astype(np.uint64)
+        q, data, op1 = (g.own(fhe.fhe_encrypt(g.ctx, g.pk, v, 40 + i)) for i, v in enumerate((qv, dv, ov)))
+        out = g.own(fhe.fhe_private_query(g.ctx, g.evk, q, data, op1, 1, (2, 3, 1)))
+        want = np.where(qv == 2, (dv + ov) % p, np.where(qv == 3, dv * ov % p, np.where(qv == 1, dv, 0)))
+        assert (g.decrypt(out) == want).all()
+        with pytest.raises(fhe.FheError):
+            fhe.fhe_private_query(g.ctx, g.evk, q, data, op1, 0, (1, 2, 3))
+    finally:
+        g.close()
