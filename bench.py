@@ -600,14 +600,15 @@ class Contexts:
     """One context (own stream, keys resident) per (ring degree, prime) on
     the universal 50-bit chain."""
 
-    def __init__(self, fhe, torch, local, specs, L, K, seed):
+    def __init__(self, fhe, torch, local, specs, L, K, seed, sort_keys=False):
         self.fhe, self.items = fhe, {}
         for logN, p in specs:
             stream = torch.cuda.Stream()
             ctx = fhe.fhe_ctx_create(logN, p, L, K, U50, 2 ** 49, 2 ** 50, allocator=fhe.torch_allocator(local),
                                      stream=stream.cuda_stream)
             sk, pk = fhe.fhe_keygen(ctx, seed * 1000 + logN * 300 + p)
-            evk = fhe.fhe_evk_create(ctx, sk, [], seed * 1000 + logN * 300 + p + 1)
+            gal = fhe.fhe_sort_galois(ctx) if sort_keys and p % 4 == 1 else []
+            evk = fhe.fhe_evk_create(ctx, sk, gal, seed * 1000 + logN * 300 + p + 1)
             self.items[(logN, p)] = dict(ctx=ctx, sk=sk, pk=pk, evk=evk, stream=stream,
                                          ns=fhe.fhe_ctx_info(ctx).slots)
 
@@ -748,8 +749,8 @@ def run_uneven(args):
 def run_serve(args):
     """The serving loop: requests of n values (log-uniform in [16, 4096];
     ceil(n / n_s) ciphertexts, split by the client into jobs of at most 16
-    ciphertexts) arrive as a Poisson process; 3 of 4 are LT+EQ compares, 1 of
-    4 max/min selections.  The client encrypts a request's operands when it
+    ciphertexts) arrive as a Poisson process; 1 of 2 are LT+EQ compares, 1 of
+    4 max/min selections, 1 of 4 row sorts (on p = 17 and 257 rings).  The client encrypts a request's operands when it
     arrives (device-seeded encryption) and frees them when the request is
     done; the server admits requests under a 150 GB footprint budget and
     batches continuously.  Latency is the server's submission-to-completion
@@ -766,24 +767,33 @@ def run_serve(args):
     torch.cuda.set_device(local)
     S = SERVE
     g = synth.rng(S["seed"])
-    cs = Contexts(fhe, torch, local, [(n, p) for n in S["logNs"] for p in S["ps"]], S["L"], S["K"], S["seed"])
+    cs = Contexts(fhe, torch, local, [(n, p) for n in S["logNs"] for p in S["ps"]], S["L"], S["K"], S["seed"],
+                  sort_keys=True)
     d = S["d"]
     reqs = []
     for i in range(S["requests"]):
-        logN, p = int(g.choice(S["logNs"])), int(g.choice(S["ps"]))
+        u = g.random()
+        kind = fhe.FHE_JOB_SORT if u < 0.25 else fhe.FHE_JOB_MAXMIN if u < 0.5 else fhe.FHE_JOB_COMPARE
+        logN = int(g.choice(S["logNs"]))
+        p = int(g.choice([q for q in S["ps"] if q % 4 == 1] if kind == fhe.FHE_JOB_SORT else S["ps"]))
         c = cs.items[(logN, p)]
         ns, b = c["ns"], (p + 1) // 2
         n = int(round(math.exp(g.uniform(math.log(S["nmin"]), math.log(S["nmax"])))))
         count = -(-n // ns)
-        kind = fhe.FHE_JOB_MAXMIN if g.random() < 0.25 else fhe.FHE_JOB_COMPARE
-        level = max(lowest_level(logN, p, d, kind == fhe.FHE_JOB_MAXMIN), circuit_depth(p, d) + 1)
+        if kind == fhe.FHE_JOB_SORT:
+            # ranks (the comparison) + the selection EQ (p - 1 power) + its product, one level spare
+            level = min(S["L"], circuit_depth(p, d) + (p - 2).bit_length() + 3)
+            per_ct = ns * (ns // 2 - 1)  # every value compared with the other cols - 1 of its row
+        else:
+            level = max(lowest_level(logN, p, d, kind == fhe.FHE_JOB_MAXMIN), circuit_depth(p, d) + 1)
+            per_ct = ns
         parts = []
         for lo in range(0, count, S["chunk"]):
             cnt = min(S["chunk"], count - lo)
             xv = synth.values(g, cnt * ns, b ** d).reshape(cnt, ns)
             yv = np.where(g.random((cnt, ns)) < 0.3, xv, synth.values(g, cnt * ns, b ** d).reshape(cnt, ns))
             parts.append(dict(xv=xv, yv=yv, seed=20000 + 1000 * i + lo))
-        reqs.append(dict(c=c, p=p, logN=logN, n=n, slots=count * ns, kind=kind, parts=parts, b=b, level=level))
+        reqs.append(dict(c=c, p=p, logN=logN, n=n, slots=count * per_ct, kind=kind, parts=parts, b=b, level=level))
     cs.sync()
     rate = args.serve_rate
     due = np.cumsum(g.exponential(1.0 / rate, size=len(reqs)))
@@ -794,7 +804,12 @@ def run_serve(args):
     def arrive(r):
         for pt in r["parts"]:
             pt["xs"], pt["ys"] = _encrypt_request(fhe, r["c"], pt["xv"], pt["yv"], r["b"], d, r["level"], pt["seed"])
-        r["jobs"] = [fhe.Job(r["c"]["ctx"], r["c"]["evk"], r["kind"], pt["xs"], pt["ys"]) for pt in r["parts"]]
+            if r["kind"] == fhe.FHE_JOB_SORT:  # one operand
+                for h in pt["ys"]:
+                    fhe.fhe_ct_destroy(h)
+                pt["ys"] = []
+        r["jobs"] = [fhe.Job(r["c"]["ctx"], r["c"]["evk"], r["kind"], pt["xs"],
+                             None if r["kind"] == fhe.FHE_JOB_SORT else pt["ys"]) for pt in r["parts"]]
         r["tickets"] = [fhe.fhe_server_submit(srv, j) for j in r["jobs"]]
         r["t_sub"], r["t_fin"], r["open"] = float("inf"), 0.0, len(r["tickets"])
 
@@ -857,6 +872,11 @@ def run_serve(args):
         for j, pt in zip(r["jobs"], r["parts"]):
             if r["kind"] == fhe.FHE_JOB_COMPARE:
                 assert (fhe.fhe_decrypt(ctx, sk, j.out0[0]) == (pt["xv"] < pt["yv"])).all(), "serve LT mismatch"
+            elif r["kind"] == fhe.FHE_JOB_SORT:
+                got = sum(fhe.fhe_decrypt(ctx, sk, j.out0[k]).astype(np.int64) * r["b"] ** k for k in range(d))
+                h = pt["xv"].shape[1] // 2
+                want = np.concatenate([np.sort(pt["xv"][:, :h], 1), np.sort(pt["xv"][:, h:], 1)], 1)
+                assert (got == want).all(), "serve sort mismatch"
             else:
                 got = sum(fhe.fhe_decrypt(ctx, sk, j.out0[k]).astype(np.int64) * r["b"] ** k for k in range(d))
                 assert (got == np.maximum(pt["xv"], pt["yv"])).all(), "serve max mismatch"
@@ -871,9 +891,15 @@ def run_serve(args):
         "dtype": "u64", "data": "synthetic (seeded BGV keys, noise and values)",
         "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {rate} req/s, n log-uniform in "
                                f"[{S['nmin']}, {S['nmax']}] values, N in {{2^13,2^14,2^15}}, p in {{17,131,257}}, "
-                               f"d=2, 3/4 LT+EQ and 1/4 max/min, 20x50-bit + 4 special primes, start level = "
-                               f"lowest decryptable level, client chunks of <= {S['chunk']} ciphertexts, operands "
-                               f"encrypted on arrival, batches level-aligned", "hbm_budget_gb": S["budget"] / 1e9, "arrival_rate_per_s": rate},
+                               f"d=2, 1/2 LT+EQ, 1/4 max/min, 1/4 row sorts (p in {{17,257}}; a sorted ciphertext "
+                               f"counts n_s (n_s/2 - 1) slot-comparisons), 20x50-bit + 4 special primes, start level "
+                               f"= lowest decryptable level, client chunks of <= {S['chunk']} ciphertexts, operands "
+                               f"encrypted on arrival, batches level-aligned", "hbm_budget_gb": S["budget"] / 1e9,
+                   "arrival_rate_per_s": rate, "requests_by_kind": {
+                       k: sum(1 for r in reqs if r["kind"] == v) for k, v in
+                       (("compare", fhe.FHE_JOB_COMPARE), ("maxmin", fhe.FHE_JOB_MAXMIN),
+                        ("sort", fhe.FHE_JOB_SORT))}},
+        "requests_per_s": round(len(reqs) / wall, 3),
         "latency_ms_p50": round(lat[len(lat) // 2], 1),
         "latency_ms_p99": round(lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))], 1),
         "server": {"batches": st.batches, "admitted_peak_gb": round(st.admitted_peak_bytes / 1e9, 2),

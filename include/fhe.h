@@ -399,7 +399,10 @@ int fhe_sort(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, int d, fh
 /* ---- batches of uneven requests ------------------------------------------------- */
 
 enum { FHE_JOB_COMPARE = 1, /* out0 -> &LT handle, out1 -> &EQ handle (either NULL) */
-       FHE_JOB_MAXMIN = 2   /* out0 -> d max digit handles, out1 -> d min digit handles */ };
+       FHE_JOB_MAXMIN = 2,  /* out0 -> d max digit handles, out1 -> d min digit handles */
+       FHE_JOB_SORT = 3     /* rows of x sorted as fhe_sort does: y ignored (may be NULL),
+                               out0 -> d sorted digit handles, out1 NULL; evk must hold
+                               fhe_sort_galois; p = 1 mod 4 rings only */ };
 
 /* One request: the d digit handles x[], y[] (equal count and level) of one
  * context.  Output handles are written at submission and hold the results

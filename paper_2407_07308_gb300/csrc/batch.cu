@@ -41,13 +41,17 @@ struct Group {
 
 int batch_check_job(const fhe_job &j)
 {
-    if (!j.ctx || !j.evk || j.evk->ctx != j.ctx || !j.x || !j.y || j.d < 1) return FHE_EINVAL;
-    if (j.kind != FHE_JOB_COMPARE && j.kind != FHE_JOB_MAXMIN) return FHE_EINVAL;
+    const bool sort = j.kind == FHE_JOB_SORT;
+    if (!j.ctx || !j.evk || j.evk->ctx != j.ctx || !j.x || (!sort && !j.y) || j.d < 1) return FHE_EINVAL;
+    if (j.kind != FHE_JOB_COMPARE && j.kind != FHE_JOB_MAXMIN && !sort) return FHE_EINVAL;
     if (!j.out0 && !j.out1) return FHE_EINVAL;
+    if (sort && (!j.out0 || j.out1)) return FHE_EINVAL;
+    if (sort && (!j.ctx->slots_linear || j.ctx->ns < 4))
+        return fhe_fail(j.ctx, FHE_EUNSUPPORTED, "batch job: sorting needs p = 1 mod 4");
     const fhe_ct *a = j.x[0];
     if (!a) return FHE_EINVAL;
     for (int k = 0; k < j.d; k++) {
-        const fhe_ct *u = j.x[k], *v = j.y[k];
+        const fhe_ct *u = j.x[k], *v = sort ? a : j.y[k];
         if (!u || !v || u->ctx != j.ctx || v->ctx != j.ctx) return FHE_EINVAL;
         if (u->npoly != 2 || v->npoly != 2 || u->count != a->count || v->count != a->count ||
             u->level != a->level || v->level != a->level)
@@ -303,7 +307,7 @@ int run_direct(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups)
         for (int k = 0; k < g.d && !err; k++) {
             bool o1 = false, o2 = false;
             err = gather(c, jobs, g.jobs, k, false, &g.X[k], &o1);
-            if (!err) err = gather(c, jobs, g.jobs, k, true, &g.Y[k], &o2);
+            if (!err && g.kind != FHE_JOB_SORT) err = gather(c, jobs, g.jobs, k, true, &g.Y[k], &o2);
             g.own_x[k] = o1;
             g.own_x[g.d + k] = o2;
         }
@@ -314,6 +318,7 @@ int run_direct(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups)
     if (!err)
         for (auto &kv : groups) {
             Group &g = kv.second;
+            if (g.kind == FHE_JOB_SORT) continue;
             auto it = items_for(g, jobs[g.jobs[0]], g.X, g.Y, g.out0, g.out1);
             by_evk[g.evk].push_back(it[0]);
         }
@@ -321,6 +326,15 @@ int run_direct(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups)
     for (auto &kv : by_evk) {
         if (err) break;
         err = circuit_multi(c, kv.first, kv.second);
+    }
+    // sorting groups: one sort circuit each (rows are independent, so the
+    // concatenated group sorts every job's rows)
+    for (auto &kv : groups) {
+        Group &g = kv.second;
+        if (err || g.kind != FHE_JOB_SORT) continue;
+        g.out0.assign(g.d, nullptr);
+        std::vector<const fhe_ct *> X(g.X.begin(), g.X.end());
+        err = circuit_sort(c, g.evk, X.data(), g.d, g.out0.data());
     }
     c->multistream = false;
     for (auto &kv : groups) {
@@ -339,7 +353,9 @@ int run_direct(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups)
 int run_context(fhe_ctx *c, const fhe_job *jobs, const std::vector<int> &ids)
 {
     GroupMap groups = make_groups(jobs, ids);
-    if (c->bplan_cap <= 0) return run_direct(c, jobs, groups);
+    bool sort = false;
+    for (auto &kv : groups) sort = sort || kv.second.kind == FHE_JOB_SORT;
+    if (c->bplan_cap <= 0 || sort) return run_direct(c, jobs, groups);  // sorting is not captured
     const std::vector<u64> sig = signature(jobs, groups);
     for (BatchPlan *P : c->bplans)
         if (P->sig == sig) return replay(c, jobs, groups, P);
@@ -419,7 +435,8 @@ int align_levels(const fhe_job *jobs, int n, Aligned &A)
             lowest[std::make_tuple(j.ctx, j.evk, j.kind, j.d, j.out0 != nullptr, j.out1 != nullptr)];
         std::vector<const fhe_ct *> &ops = A.ops[i];
         ops.assign(2 * j.d, nullptr);
-        for (int k = 0; k < 2 * j.d; k++) {
+        const int nops = j.kind == FHE_JOB_SORT ? j.d : 2 * j.d;
+        for (int k = 0; k < nops; k++) {
             const fhe_ct *src = k < j.d ? j.x[k] : j.y[k - j.d];
             if (src->level == target) {
                 ops[k] = src;

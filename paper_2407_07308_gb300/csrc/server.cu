@@ -91,6 +91,9 @@ extern "C" uint64_t fhe_job_footprint(const fhe_job *j)
     u64 est = mults * per_mult;
     est += d * (B / 2 + ceil_log2(c->p) + 4) * ct;
     est += (j->kind == FHE_JOB_MAXMIN ? 2 * d : 2) * ct;
+    if (j->kind == FHE_JOB_SORT)  // one shift's comparison at a time, plus the rotated
+        // operands, the rank, the selection powers and the d accumulated outputs
+        est += (ceil_log2(c->p) + 3 * d + 4) * ct + 2 * per_mult;
     return est;
 }
 

@@ -71,7 +71,7 @@ class fhe_job(Structure):
                 ("y", c_void_p), ("out0", c_void_p), ("out1", c_void_p)]
 
 
-FHE_JOB_COMPARE, FHE_JOB_MAXMIN = 1, 2
+FHE_JOB_COMPARE, FHE_JOB_MAXMIN, FHE_JOB_SORT = 1, 2, 3
 
 
 class fhe_info(Structure):
@@ -683,15 +683,17 @@ class Job:
 
     def __init__(self, ctx, evk, kind, xs, ys, want0=True, want1=True):
         self.ctx, self.evk, self.kind, self.d = ctx, evk, kind, len(xs)
-        self._x, self._y = _handles(xs), _handles(ys)
-        n = self.d if kind == FHE_JOB_MAXMIN else 1
+        self._x = _handles(xs)
+        self._y = _handles(ys) if ys is not None else None
+        n = self.d if kind in (FHE_JOB_MAXMIN, FHE_JOB_SORT) else 1
         self._o0 = (c_void_p * n)() if want0 else None
-        self._o1 = (c_void_p * n)() if want1 else None
+        self._o1 = (c_void_p * n)() if want1 and kind != FHE_JOB_SORT else None
 
     def struct(self):
         return fhe_job(self.ctx.value if isinstance(self.ctx, c_void_p) else self.ctx,
                        self.evk.value if isinstance(self.evk, c_void_p) else self.evk, self.kind, self.d,
-                       ctypes.cast(self._x, c_void_p), ctypes.cast(self._y, c_void_p),
+                       ctypes.cast(self._x, c_void_p),
+                       ctypes.cast(self._y, c_void_p) if self._y is not None else None,
                        ctypes.cast(self._o0, c_void_p) if self._o0 is not None else None,
                        ctypes.cast(self._o1, c_void_p) if self._o1 is not None else None)
 

@@ -240,3 +240,92 @@ def test_level_aligned_batch_matches_lowered_alone():
         fhe.fhe_pk_destroy(pk)
     finally:
         fhe.fhe_ctx_destroy(ctx)
+
+
+def test_sort_jobs_in_batches_and_served():
+    """Sort jobs beside compare jobs: in one batch submission (two sort jobs
+    of one group, concatenated) and through the serving loop, each sort
+    result has the bits of fhe_sort on the job alone; a sort job on a
+    p = 3 mod 8 ring is refused."""
+    from paper_2407_07308_gb300 import fhe
+
+    p, logN, d = 17, 11, 2
+    b = (p + 1) // 2
+    ctx = fhe.fhe_ctx_create(logN, p, 12, 4, CHAIN50["U"], CHAIN50["lo"], CHAIN50["hi"])
+    bad = fhe.fhe_ctx_create(logN, 131, 6, 2, CHAIN50["U"], CHAIN50["lo"], CHAIN50["hi"])
+    handles = []
+    try:
+        sk, pk = fhe.fhe_keygen(ctx, 3)
+        evk = fhe.fhe_evk_create(ctx, sk, fhe.fhe_sort_galois(ctx), 4)
+        ns = fhe.fhe_ctx_info(ctx).slots
+        rnd = np.random.default_rng(8)
+
+        def operand(count, seed):
+            v = rnd.integers(0, b ** d, size=(count, ns))
+            hs = [fhe.fhe_encrypt(ctx, pk, (v // b ** k) % b, seed + k) for k in range(d)]
+            handles.extend(hs)
+            return v, hs
+
+        (v1, s1), (v2, s2) = operand(2, 10), operand(1, 20)
+        (xv, xs), (yv, ys) = operand(2, 30), operand(2, 40)
+        alone, peaks = [], []
+        for hs in (s1, s2):
+            fhe.fhe_ctx_sync(ctx)
+            fhe.fhe_ctx_memory_peak(ctx, reset=True)
+            base = fhe.fhe_ctx_memory(ctx)[1]
+            out = fhe.fhe_sort(ctx, evk, hs)
+            fhe.fhe_ctx_sync(ctx)
+            peaks.append(fhe.fhe_ctx_memory_peak(ctx) - base)
+            alone.append([fhe.fhe_ct_export_coeff(ctx, h) for h in out])
+            for h in out:
+                fhe.fhe_ct_destroy(h)
+        jobs = [fhe.Job(ctx, evk, fhe.FHE_JOB_SORT, s1, None), fhe.Job(ctx, evk, fhe.FHE_JOB_COMPARE, xs, ys),
+                fhe.Job(ctx, evk, fhe.FHE_JOB_SORT, s2, None)]
+        for jb, pk_ in zip((jobs[0], jobs[2]), peaks):  # the admission estimate covers the measured peak
+            assert fhe.fhe_job_footprint(jb) >= pk_, (fhe.fhe_job_footprint(jb), pk_)
+        bt = fhe.fhe_batch_submit(jobs)
+        assert fhe.fhe_batch_wait(bt, 120000) == 0
+        fhe.fhe_batch_destroy(bt)
+        for jb, want in zip((jobs[0], jobs[2]), alone):
+            got = [fhe.fhe_ct_export_coeff(ctx, h) for h in jb.out0]
+            assert all(np.array_equal(g_, w_) for g_, w_ in zip(got, want))
+        cols = ns // 2
+        dec = sum(fhe.fhe_decrypt(ctx, sk, jobs[0].out0[k]).astype(np.int64) * b ** k for k in range(d))
+        assert (dec == np.concatenate([np.sort(v1[:, :cols], 1), np.sort(v1[:, cols:], 1)], 1)).all()
+        assert (fhe.fhe_decrypt(ctx, sk, jobs[1].out0[0]) == (xv < yv)).all()
+        for jb in jobs:
+            for h in (jb.out0 or []) + (jb.out1 or []):
+                fhe.fhe_ct_destroy(h)
+        # served
+        srv = fhe.fhe_server_start(hbm_budget=0)
+        try:
+            js = fhe.Job(ctx, evk, fhe.FHE_JOB_SORT, s2, None)
+            t = fhe.fhe_server_submit(srv, js)
+            done, info = fhe.fhe_server_poll(srv, t, 120000)
+            assert done and info.error == 0
+            got = [fhe.fhe_ct_export_coeff(ctx, h) for h in js.out0]
+            assert all(np.array_equal(g_, w_) for g_, w_ in zip(got, alone[1]))
+            for h in js.out0:
+                fhe.fhe_ct_destroy(h)
+            assert fhe.fhe_job_footprint(js) > 0
+        finally:
+            fhe.fhe_server_stop(srv)
+        # refused on a ring without sortable rows
+        bsk, bpk = fhe.fhe_keygen(bad, 5)
+        bevk = fhe.fhe_evk_create(bad, bsk, [], 6)
+        bx = fhe.fhe_encrypt(bad, bpk, np.zeros((1, 2), dtype=np.uint64), 7)
+        with pytest.raises(fhe.FheError) as e:
+            fhe.fhe_batch_submit([fhe.Job(bad, bevk, fhe.FHE_JOB_SORT, [bx], None)])
+        assert e.value.code == -9
+        fhe.fhe_ct_destroy(bx)
+        fhe.fhe_evk_destroy(bevk)
+        fhe.fhe_sk_destroy(bsk)
+        fhe.fhe_pk_destroy(bpk)
+        fhe.fhe_evk_destroy(evk)
+        fhe.fhe_sk_destroy(sk)
+        fhe.fhe_pk_destroy(pk)
+    finally:
+        for h in handles:
+            fhe.fhe_ct_destroy(h)
+        fhe.fhe_ctx_destroy(ctx)
+        fhe.fhe_ctx_destroy(bad)
