@@ -197,7 +197,10 @@ extern "C" int fhe_server_submit(fhe_server *s, const fhe_job *job, uint64_t *ti
     auto q = std::make_unique<Request>();
     q->job = *job;
     q->x.assign(job->x, job->x + job->d);
-    q->y.assign(job->y, job->y + job->d);
+    if (job->y)
+        q->y.assign(job->y, job->y + job->d);
+    else
+        q->y.assign(job->d, nullptr);  // sort jobs take one operand
     q->job.x = q->x.data();
     q->job.y = q->y.data();
     q->est = fhe_job_footprint(job);
