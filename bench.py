@@ -455,6 +455,13 @@ def run_gpu(args):
         "batched_step_ms_p99": round(pct(sorted(step_ms), 0.99), 3),
         "p99_ms": round(pct(sorted(step_ms), 0.99), 3),
         "roofline": roof, "int_pipe": int_pipe, "kernels": kernels,
+        # the survey's secondary rates: digit comparisons (one LT+EQ of one
+        # ciphertext's digit) and limb NTTs ((N/2) log2 N butterflies each;
+        # fused ModUp / ModDown / switch transforms included), per second of
+        # the batched step
+        "ciphertext_digit_comparisons_per_s": round(pairs * W["d"] * world / (ms_per_step / 1e3), 1),
+        "limb_ntts_per_s": round(sum(v[3] for v in prof.values()) / ((N // 2) * (N.bit_length() - 1))
+                                 / (ms_per_step / 1e3), 1),
         "profiled_ms_per_step": round(prof_ms_per_step, 3),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         "memory_gb": {"pool_reserved": round(res / 1e9, 2)},
@@ -1323,6 +1330,31 @@ def run_query(args):
     ms_in, _, _ = timed(False)
     ms_ov, launches, clk = timed(True)
     med = lambda v: v[len(v) // 2]  # noqa: E731
+    # the application's shape: 100 ciphertexts of records per query batch
+    nb = 100
+    qb = np.tile(np.array([[1, 2]], dtype=np.uint64)[:, :ns], (nb, 1))
+    qb[::3] = 3
+    db = g.integers(0, p, size=(nb, ns)).astype(np.uint64)
+    ob = g.integers(0, p, size=(nb, ns)).astype(np.uint64)
+    Qb, Db, Ob = (fhe.fhe_encrypt(ctx, pk, v, 60 + i) for i, v in enumerate((qb, db, ob)))
+    want_b = np.where(qb == 1, (db + ob) % p, np.where(qb == 2, db * ob % p, np.where(qb == 3, db ** 4 % p, 0)))
+    batch = {}
+    for overlap in (False, True):
+        out = fhe.fhe_private_query(ctx, evk, Qb, Db, Ob, 4, (1, 2, 3), overlap=overlap)
+        assert (fhe.fhe_decrypt(ctx, sk, out) == want_b).all(), "batched query mismatch"
+        fhe.fhe_ct_destroy(out)
+        fhe.fhe_ctx_sync(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fhe.fhe_ct_destroy(fhe.fhe_private_query(ctx, evk, Qb, Db, Ob, 4, (1, 2, 3), overlap=overlap))
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        batch["overlap" if overlap else "in_order"] = {"ms_per_batch": round(ms, 2),
+                                                       "record_queries_per_s": round(nb * ns / (ms / 1e3), 1)}
+    for h in (Qb, Db, Ob):
+        fhe.fhe_ct_destroy(h)
     total = sum(ms_ov)
     line = {
         "metric": "private queries per second with non-blocking comparison (N=2^14, p=131, one ciphertext per "
@@ -1337,6 +1369,7 @@ def run_query(args):
                    "l2": "a 256 MB buffer is written before every timed query (outside the events)"},
         "latency_ms": {"overlap_p50": round(med(ms_ov), 2), "in_order_p50": round(med(ms_in), 2),
                        "overlap_max": round(ms_ov[-1], 2), "in_order_max": round(ms_in[-1], 2)},
+        "batch_of_100_ciphertexts": batch,
         "gpu_launches": launches, "clocks": clk, "cpu_baseline": None, "roofline": None, "e2e": None,
     }
     for h in (q, data, op1):
