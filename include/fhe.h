@@ -334,6 +334,13 @@ int fhe_sort_galois(const fhe_ctx *ctx, int64_t *galois, int cap);
 enum { FHE_QUERY_OVERLAP = 1 };
 int fhe_private_query(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *q, const fhe_ct *data, const fhe_ct *op1,
                       int op2, const int64_t *codes, int flags, fhe_ct **out);
+/* The private query recorded as a CUDA graph (see fhe_compare_plan: the
+ * plan binds the three input handles, whose contents the caller may
+ * overwrite between runs; fhe_plan_run replays it; fhe_plan_result(plan, 0)
+ * is the answer).  flags: 0 records the branches on parallel streams (the
+ * overlap of FHE_QUERY_OVERLAP), FHE_PLAN_SERIAL records one stream. */
+int fhe_private_query_plan(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *q, const fhe_ct *data,
+                           const fhe_ct *op1, int op2, const int64_t *codes, int flags, fhe_plan **out);
 
 /* F_{p^d} slots and digit extraction ("mod extract", Sec. 2.1): a d-digit
  * operand is held in ONE ciphertext whose every slot is an element of F_{p^d};

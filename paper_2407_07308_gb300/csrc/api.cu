@@ -6,6 +6,8 @@
 
 #include <algorithm>
 
+#include <functional>
+
 #include "fhe_internal.h"
 
 // ---------------------------------------------------------------------------
@@ -1483,26 +1485,22 @@ extern "C" int fhe_selftest_modarith(uint64_t prime_mod, uint64_t prime_lo, uint
 // captured comparison plans (CUDA graphs)
 // ---------------------------------------------------------------------------
 
-extern "C" int fhe_compare_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y,
-                                int d, int want_lt, int want_eq, int flags, fhe_plan **out)
+// Records a circuit into a CUDA graph.  run(o0, o1) enqueues the circuit and
+// writes its result handles; it is called once uncaptured (the warm run fills
+// the pool with every block size the circuit needs and builds any lazily
+// created table, so the captured run allocates nothing) and once under
+// capture, whose results become the plan's outputs.
+static int capture_plan(fhe_ctx *c, int flags, const std::function<int(fhe_ct **, fhe_ct **)> &run, fhe_plan **out)
 {
-    CHECK_CTX(c);
-    if (!out || (!want_lt && !want_eq)) return FHE_EINVAL;
-    int e = check_digits(c, evk, x, y, d);
-    if (e) return e;
-    LOCK(c);
-    // warm run: fills the pool with every block size the circuit needs and
-    // builds any lazily created table, so the captured run allocates nothing
     const bool prof = c->prof_on, tr = c->tracing;
     c->prof_on = false;
     c->tracing = false;
+    int e;
     {
-        fhe_ct *lt = nullptr, *eq = nullptr;
-        e = (flags & FHE_PLAN_BIVARIATE)
-                ? circuit_compare_bv(c, evk, x, y, d, want_lt ? &lt : nullptr, want_eq ? &eq : nullptr)
-                : circuit_compare(c, evk, x, y, d, want_lt ? &lt : nullptr, want_eq ? &eq : nullptr);
-        fhe_ct_destroy(lt);
-        fhe_ct_destroy(eq);
+        fhe_ct *o0 = nullptr, *o1 = nullptr;
+        e = run(&o0, &o1);
+        fhe_ct_destroy(o0);
+        fhe_ct_destroy(o1);
         if (!e) e = sync_check(c, "plan warm-up");
         if (e) {
             c->prof_on = prof;
@@ -1527,9 +1525,7 @@ extern "C" int fhe_compare_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *co
         e = fhe_cuda_check(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed), "begin capture");
         if (!e) {
             c->capturing = !(flags & FHE_PLAN_SERIAL);
-            e = (flags & FHE_PLAN_BIVARIATE)
-                    ? circuit_compare_bv(c, evk, x, y, d, want_lt ? &P->out[0] : nullptr, want_eq ? &P->out[1] : nullptr)
-                    : circuit_compare(c, evk, x, y, d, want_lt ? &P->out[0] : nullptr, want_eq ? &P->out[1] : nullptr);
+            e = run(&P->out[0], &P->out[1]);
             c->capturing = false;
             cudaGraph_t g = nullptr;
             const int e2 = fhe_cuda_check(c, cudaStreamEndCapture(cap, &g), "end capture");
@@ -1556,6 +1552,43 @@ extern "C" int fhe_compare_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *co
     }
     *out = P;
     return 0;
+}
+
+extern "C" int fhe_compare_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y,
+                                int d, int want_lt, int want_eq, int flags, fhe_plan **out)
+{
+    CHECK_CTX(c);
+    if (!out || (!want_lt && !want_eq) || (flags & ~(FHE_PLAN_SERIAL | FHE_PLAN_BIVARIATE))) return FHE_EINVAL;
+    int e = check_digits(c, evk, x, y, d);
+    if (e) return e;
+    LOCK(c);
+    return capture_plan(
+        c, flags,
+        [&](fhe_ct **lt, fhe_ct **eq) {
+            return (flags & FHE_PLAN_BIVARIATE)
+                       ? circuit_compare_bv(c, evk, x, y, d, want_lt ? lt : nullptr, want_eq ? eq : nullptr)
+                       : circuit_compare(c, evk, x, y, d, want_lt ? lt : nullptr, want_eq ? eq : nullptr);
+        },
+        out);
+}
+
+extern "C" int fhe_private_query_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *q, const fhe_ct *data,
+                                      const fhe_ct *op1, int op2, const int64_t *codes, int flags, fhe_plan **out)
+{
+    CHECK_CTX(c);
+    if (!evk || evk->ctx != c || !same_ctx(c, q) || !same_ctx(c, data) || !same_ctx(c, op1) || !codes || !out ||
+        op2 < 1 || op2 >= (1 << 20) || (flags & ~FHE_PLAN_SERIAL))
+        return FHE_EINVAL;
+    if (q->npoly != 2 || data->npoly != 2 || op1->npoly != 2 || q->count != data->count || op1->count != data->count)
+        return fhe_fail(c, FHE_EMISMATCH, "private query: operands differ in shape");
+    const int64_t k[3] = {codes[0], codes[1], codes[2]};
+    LOCK(c);
+    return capture_plan(
+        c, flags,
+        [&](fhe_ct **answer, fhe_ct **) {
+            return circuit_private_query(c, evk, q, data, op1, op2, k, !(flags & FHE_PLAN_SERIAL), answer);
+        },
+        out);
 }
 
 extern "C" int fhe_plan_run(fhe_plan *P)

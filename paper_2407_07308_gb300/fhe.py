@@ -154,6 +154,7 @@ def lib() -> ctypes.CDLL:
             "fhe_sort_galois": (ci, [vp, vp, ci]),
             "fhe_probe_bfly_peak": (ci, [vp]),
             "fhe_private_query": (ci, [vp, vp, vp, vp, vp, ci, vp, ci, POINTER(vp)]),
+            "fhe_private_query_plan": (ci, [vp, vp, vp, vp, vp, ci, vp, ci, POINTER(vp)]),
             "fhe_ext_galois": (ci, [vp, ci, vp, ci]),
             "fhe_encrypt_ext": (ci, [vp, vp, vp, ci, ci, u64, POINTER(vp)]),
             "fhe_encrypt_ext_explicit": (ci, [vp, vp, vp, ci, ci, vp, vp, vp, POINTER(vp)]),
@@ -534,6 +535,17 @@ def fhe_private_query(ctx, evk, q, data, op1, op2: int, codes, overlap: bool = T
     out = c_void_p()
     _check(lib().fhe_private_query(ctx, evk, q, data, op1, int(op2), _ptr(cd),
                                    FHE_QUERY_OVERLAP if overlap else 0, ctypes.byref(out)), ctx)
+    return out
+
+
+def fhe_private_query_plan(ctx, evk, q, data, op1, op2: int, codes, serial: bool = False):
+    """The private query captured as a graph; fhe_plan_run replays it and
+    fhe_plan_result(plan, 0) is the answer."""
+    cd = np.ascontiguousarray(np.asarray(codes, dtype=np.int64))
+    assert cd.shape == (3,)
+    out = c_void_p()
+    _check(lib().fhe_private_query_plan(ctx, evk, q, data, op1, int(op2), _ptr(cd),
+                                        FHE_PLAN_SERIAL if serial else 0, ctypes.byref(out)), ctx)
     return out
 
 

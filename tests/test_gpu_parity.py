@@ -716,5 +716,14 @@ def test_private_query_bitexact(overlap):
         out_o = private_query(ev, qo, do, oo, 3, (1, 2, 3))
         assert trace_g == ev.trace
         _same(out_o, g.export(out), 0)
+        fhe.fhe_trace_enable(g.ctx, False)
+        # captured as a graph: every replay gives the same bits
+        plan = fhe.fhe_private_query_plan(g.ctx, g.evk, qg, dg, og, 3, (1, 2, 3), serial=not overlap)
+        try:
+            for _ in range(2):
+                fhe.fhe_plan_run(plan, g.ctx)
+                assert np.array_equal(g.export(fhe.fhe_plan_result(plan, 0)), g.export(out))
+        finally:
+            fhe.fhe_plan_destroy(plan)
     finally:
         g.close()
