@@ -341,44 +341,53 @@ def sort_galois(p: int, N: int) -> list:
 def sort_rows(ev: "Evaluator", xs):
     """Digits (least significant first) of every row's values in increasing
     order; xs: the d digit ciphertexts (univariate digits)."""
+    return sort_joint(ev, [xs])[0]
+
+
+def sort_joint(ev: "Evaluator", cts):
+    """Row r of the K ciphertexts cts[0..K) (each a list of d digit
+    ciphertexts) is one sequence of K cols values, global index a cols + c
+    for column c of ciphertext a.  Returns K digit lists whose row r holds
+    that sequence in increasing order (ciphertext t: positions t cols ..
+    t cols + cols - 1); needs K cols <= p.
+
+    rank^a = sum over (b, s) != (a, 0), b and then s ascending, of
+    LT(sigma_{5^s} x^b, x^a) + w * EQ(sigma_{5^s} x^b, x^a), with the
+    tie-break mask w[c] = [b cols + (c + s) mod cols < a cols + c]; then for
+    a and s ascending (sigma_{5^s} of rank^a and of x^a taken once) and t
+    ascending: out^t += EQ(sigma_{5^s} rank^a - (t cols + c)) sigma_{5^s} x^a
+    per digit."""
     ss = ev._slots()
     assert ss.kind == "linear" and ss.ns >= 4, "sorting needs p = 1 mod 4 and two columns or more"
     p, cols, twoN = ev.p, ss.ns // 2, 2 * ev.o.N
-    rank = None
-    for s in range(1, cols):
-        g = pow(5, s, twoN)
-        xr = [ev.rotate(x, g) for x in xs]
-        lt, eq = ev.compare(xr, xs, True, True)
-        w = [1 if c + s >= cols else 0 for _ in range(2) for c in range(cols)]
-        t = ev.add(lt, ev.mul_plain(eq, w))
-        rank = t if rank is None else ev.add(rank, t)
-    idx = [c for _ in range(2) for c in range(cols)]
-    outs = [None] * len(xs)
-    for s in range(cols):
-        g = pow(5, s, twoN)
-        rr = ev.rotate(rank, g) if s else rank
-        xr = [ev.rotate(x, g) for x in xs] if s else list(xs)
-        u = ev.sub_plain(rr, idx)
-        pw = {1: u}
-
-        def power(n: int) -> Ct:
-            if n in pw:
-                return pw[n]
-            if n & (n - 1) == 0:
-                h = power(n // 2)
-                r = ev.mul(h, h)
-            else:
-                a = 1 << (n.bit_length() - 1)
-                r = ev.mul(power(a), power(n - a))
-            pw[n] = r
-            return r
-
-        e = ev.add_const(ev.neg(power(p - 1)), 1)
-        for k in range(len(xs)):
-            t = ev.mul(e, xr[k])
-            outs[k] = t if outs[k] is None else ev.add(outs[k], t)
+    K, d = len(cts), len(cts[0])
+    assert K * cols <= p, "ranks must stay below p"
+    ranks = []
+    for a in range(K):
+        rank = None
+        for b in range(K):
+            for s in range(cols):
+                if b == a and s == 0:
+                    continue
+                xr = [ev.rotate(x, pow(5, s, twoN)) for x in cts[b]] if s else list(cts[b])
+                lt, eq = ev.compare(xr, cts[a], True, True)
+                w = [1 if b * cols + (c + s) % cols < a * cols + c else 0 for _ in range(2) for c in range(cols)]
+                t = ev.add(lt, ev.mul_plain(eq, w))
+                rank = t if rank is None else ev.add(rank, t)
+        ranks.append(rank)
+    outs = [[None] * d for _ in range(K)]
+    for a in range(K):
+        for s in range(cols):
+            g = pow(5, s, twoN)
+            rr = ev.rotate(ranks[a], g) if s else ranks[a]
+            xr = [ev.rotate(x, g) for x in cts[a]] if s else list(cts[a])
+            for t in range(K):
+                u = ev.sub_plain(rr, [t * cols + c for _ in range(2) for c in range(cols)])
+                e = ev.add_const(ev.neg(_powers(ev, u)(p - 1)), 1)
+                for k in range(d):
+                    term = ev.mul(e, xr[k])
+                    outs[t][k] = term if outs[t][k] is None else ev.add(outs[t][k], term)
     return outs
-
 
 def slot_plan(ns: int, useful):
     """The slot manager's placement of useful slots into as few outputs as

@@ -325,6 +325,37 @@ def test_sort_rows_small_ring():
     assert st.o.noise_bits(out[0], st.s) < np.log2(st.o.primes[0]) - 1
 
 
+def test_sort_joint_sixteen_values():
+    """Sixteen values (the paper's sort size) in row 0 of four ciphertexts of
+    the p = 17 ring (4 columns each), ties across ciphertexts included: row r
+    of the outputs, read in ciphertext order, is the sorted sequence of row r
+    of the inputs; and one ciphertext reduces to the row sort."""
+    from oracle.circuits import sort_galois, sort_joint, sort_rows
+
+    p, d = 17, 2
+    N = 2 ** 8
+    st = OracleSetup(logN=8, p=p, L=11, K=2, seed=27, galois=sort_galois(p, N), **CHAIN50)
+    ns = st.ss.ns
+    cols = ns // 2
+    b = (p + 1) // 2
+    rnd = random.Random(6)
+    K = 4
+    vals = [[rnd.randrange(b ** d) for _ in range(ns)] for _ in range(K)]
+    vals[3][0] = vals[0][2]  # ties across ciphertexts, in both rows
+    vals[2][5] = vals[1][4] = vals[0][7]
+    cts = [[st.encrypt_slots([dg], seed=90 + 10 * a + k)[0] for k, dg in enumerate(_digits(vals[a], b, d))]
+           for a in range(K)]
+    ev = st.evaluator()
+    out = sort_joint(ev, cts)
+    dec = [[sum(st.decrypt_slots(out[t][k])[s] * b ** k for k in range(d)) for s in range(ns)] for t in range(K)]
+    for r in range(2):
+        seq = [vals[a][r * cols + c] for a in range(K) for c in range(cols)]
+        got = [dec[t][r * cols + c] for t in range(K) for c in range(cols)]
+        assert got == sorted(seq)
+    one = sort_rows(st.evaluator(), cts[0])
+    assert [st.decrypt_slots(x) for x in one] == [st.decrypt_slots(x) for x in sort_joint(st.evaluator(), [cts[0]])[0]]
+
+
 def _check_plan(ns, useful, n_out, pieces, dest):
     """The plan is a valid compaction: every useful slot lands exactly once,
     no two land on one output slot, and each piece moves its slots by one
