@@ -1399,6 +1399,82 @@ def run_query(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sort16(args):
+    """The paper's sort size: sequences of 16 values (2 digits of base 9) on
+    the p = 17 ring (N = 2^13, 12 x 50-bit + 2 special primes; rows of 4
+    columns), each sequence spread over row r of 4 ciphertexts and sorted
+    jointly.  A step sorts 16 problems x 2 rows = 32 sequences."""
+    import numpy as np
+    import torch
+
+    from paper_2407_07308_gb300 import fhe, synth
+
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    p, K, d, b, count = 17, 4, 2, 9, 16
+    ctx = fhe.fhe_ctx_create(13, p, 12, 2, U50, 2 ** 49, 2 ** 50, allocator=fhe.torch_allocator(local),
+                             stream=stream.cuda_stream)
+    ns = fhe.fhe_ctx_info(ctx).slots
+    cols = ns // 2
+    sk, pk = fhe.fhe_keygen(ctx, 14)
+    evk = fhe.fhe_evk_create(ctx, sk, fhe.fhe_sort_galois(ctx), 15)
+    g = synth.rng(9)
+    vals = synth.values_with_duplicates(g, K * count * ns, b ** d, 0.10).reshape(K, count, ns)
+    xs = [[fhe.fhe_encrypt(ctx, pk, ((vals[a] // b ** k) % b).astype(np.uint64), 200 + 10 * a + k)
+           for k in range(d)] for a in range(K)]
+
+    def one(check=False):
+        out = fhe.fhe_sort_joint(ctx, evk, xs)
+        if check:
+            got = [sum(fhe.fhe_decrypt(ctx, sk, out[t][k]).astype(np.int64) * b ** k for k in range(d))
+                   for t in range(K)]
+            for r in range(2):
+                seq = np.concatenate([vals[a][:, r * cols:(r + 1) * cols] for a in range(K)], axis=1)
+                res = np.concatenate([got[t][:, r * cols:(r + 1) * cols] for t in range(K)], axis=1)
+                assert (res == np.sort(seq, axis=1)).all(), "joint sort mismatch"
+        for hs in out:
+            for h in hs:
+                fhe.fhe_ct_destroy(h)
+
+    one(check=True)
+    for _ in range(args.warmup - 1):
+        one()
+    fhe.fhe_ctx_sync(ctx)
+    l0 = fhe.fhe_ctx_launches(ctx)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        evs[0].record(stream)
+        for i in range(args.steps):
+            one()
+            evs[i + 1].record(stream)
+        stream.synchronize()
+    launches = fhe.fhe_ctx_launches(ctx) - l0
+    total = evs[0].elapsed_time(evs[-1])
+    seqs = count * 2
+    line = {
+        "metric": "sequences of 16 encrypted values sorted per second (p=17, N=2^13, one row of 4 ciphertexts each)",
+        "value": round(seqs * args.steps / (total / 1e3), 2), "unit": "sequences/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded BGV keys, noise and values in [0, 81), 10% duplicates)",
+        "config": {"workload": "32 sequences of 16 values per step (16 ciphertexts per batch x 2 rows; each sequence "
+                               "in row r of 4 batches), joint sort: 60 comparisons + 64 selection powers per "
+                               "sequence set, 12x50-bit + 2 special primes, 3 rotation keys",
+                   "l2": "ciphertexts 25 MB per batch and digit; working set > L2 within a step"},
+        "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": None, "roofline": None, "e2e": None,
+    }
+    for hs in xs:
+        for h in hs:
+            fhe.fhe_ct_destroy(h)
+    fhe.fhe_evk_destroy(evk)
+    fhe.fhe_sk_destroy(sk)
+    fhe.fhe_pk_destroy(pk)
+    fhe.fhe_ctx_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1411,12 +1487,13 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the one-request-at-a-time form")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--workload", default="compare", choices=["compare", "small", "bivariate", "uneven", "serve", "tournament", "sort",
-                                                          "compact", "extract", "query"],
+                                                          "compact", "extract", "query", "sort16"],
                     help="compare: the 16-pair batch (default); small: one pair on the small ring; bivariate: "
                          "the 16-pair batch on full digits; uneven: "
                          "256 mixed requests; serve: serving loop; tournament: max/min of 4096 values; sort: rows of 64 "
                          "values sorted; compact: slot compaction before comparison; extract: server-side digit extraction from "
-                         "F_(p^d) slots, then comparison; query: private query with non-blocking comparison")
+                         "F_(p^d) slots, then comparison; query: private query with non-blocking comparison; sort16: joint sort of 16-value "
+                         "sequences across 4 ciphertexts")
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate (requests/s) for serve")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -1448,6 +1525,8 @@ def main():
         run_extract(args)
     elif args.workload == "query":
         run_query(args)
+    elif args.workload == "sort16":
+        run_sort16(args)
     else:
         run_gpu(args)
 

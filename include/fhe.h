@@ -402,6 +402,17 @@ int fhe_slot_plan(int slots, int64_t ring_n, int n, const uint8_t *useful, int32
 int fhe_slot_pack(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *in, int n, const uint8_t *useful,
                   fhe_ct **out, int out_cap);
 int fhe_sort(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, int d, fhe_ct **out);
+/* Joint sort of sequences longer than a row: row r of the K batches
+ * x[a * d + k] (batch a, digit k; equal count and level) is one sequence of
+ * K cols values, value (a, c) at global index a cols + c.  rank^a sums, over
+ * every (b, s) != (a, 0), LT(sigma_{5^s} x^b, x^a) plus the tie-break mask
+ * [b cols + (c + s) mod cols < a cols + c] times EQ; the output batch t holds
+ * positions t cols .. t cols + cols - 1 of the sorted sequence: the sum over
+ * (a, s) of EQ(sigma_{5^s} rank^a - (t cols + c)) sigma_{5^s} x^a.  Needs
+ * K cols <= p (FHE_EINVAL otherwise) and the keys of fhe_sort_galois; K = 1
+ * is fhe_sort.  Costs K^2 cols - K comparisons and K^2 cols selection
+ * powers.  out: K * d new handles, out[t * d + k]. */
+int fhe_sort_joint(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, int K, int d, fhe_ct **out);
 
 /* ---- batches of uneven requests ------------------------------------------------- */
 

@@ -1315,6 +1315,22 @@ extern "C" int fhe_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, 
     return e ? e : launch_status(c, "sort");
 }
 
+extern "C" int fhe_sort_joint(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int K, int d, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!out || !x || K < 1 || d < 1) return FHE_EINVAL;
+    int e = check_digits(c, evk, x, x, d);
+    if (e) return e;
+    for (int i = 0; i < K * d; i++) {
+        if (!same_ctx(c, x[i])) return FHE_EINVAL;
+        if (x[i]->npoly != 2 || x[i]->count != x[0]->count || x[i]->level != x[0]->level)
+            return fhe_fail(c, FHE_EMISMATCH, "joint sort: inputs differ in shape or level");
+    }
+    LOCK(c);
+    e = circuit_sort_joint(c, evk, x, K, d, out);
+    return e ? e : launch_status(c, "sort");
+}
+
 extern "C" int fhe_compare_lt(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
                               fhe_ct **out)
 {

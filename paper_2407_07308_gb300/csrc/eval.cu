@@ -1185,86 +1185,114 @@ std::vector<int64_t> sort_galois(const fhe_ctx *c)
 
 // Each shift runs in a circuit of its own, so that its temporaries are
 // freed before the next one; only the running rank and outputs are carried.
-int circuit_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int d, fhe_ct **out)
+// Joint sort: row r of the K inputs x[a * d + k] (ciphertext a, digit k) is
+// one sequence of K cols values, global index a cols + c.  rank^a sums, over
+// (b, s) != (a, 0) with b and then s ascending, LT(sigma_{5^s} x^b, x^a) +
+// w EQ(sigma_{5^s} x^b, x^a), w[c] = [b cols + (c + s) mod cols < a cols + c];
+// then for a and s ascending (the rotations of rank^a and x^a taken once) and
+// each target t: out^t += EQ(sigma_{5^s} rank^a - (t cols + c)) sigma_{5^s} x^a.
+// Each comparison, and each (a, s) of the selection, is a sub-circuit of its
+// own, so only the running sums outlive it.  K = 1 is the row sort.
+int circuit_sort_joint(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int K, int d, fhe_ct **out)
 {
     if (!c->slots_linear || c->ns < 4)
         return fhe_fail(c, FHE_EUNSUPPORTED, "sorting needs p = 1 mod 4 (two columns or more)");
     const int cols = c->ns / 2, p = (int)c->p;
+    if (K < 1 || (long long)K * cols > p) return fhe_fail(c, FHE_EINVAL, "joint sort: K cols must not exceed p");
     const std::vector<int64_t> gs = sort_galois(c);
-    std::vector<const fhe_ct *> xs(x, x + d);
-    fhe_ct *rank = nullptr;
-    std::vector<fhe_ct *> outs(d, nullptr);
+    auto X = [&](int a) { return std::vector<const fhe_ct *>(x + (size_t)a * d, x + (size_t)(a + 1) * d); };
+    std::vector<fhe_ct *> rank(K, nullptr), outs((size_t)K * d, nullptr);
     int err = 0;
     auto carry = [](fhe_ct *&held, fhe_ct *next) {
         if (held) fhe_ct_destroy(held);
         held = next;
     };
-    for (int s = 1; s < cols && !err; s++) {
-        Circuit S(c, evk);
-        std::vector<const fhe_ct *> xr(d);
-        for (int k = 0; k < d; k++) xr[k] = S.rot(xs[k], gs[s - 1]);
-        fhe_ct *lt = nullptr, *eq = nullptr;
-        if (!S.err) S.compare(xr.data(), xs.data(), d, true, true, &lt, &eq);
-        if (!S.err) {
-            S.keep(lt);
-            S.keep(eq);
-            std::vector<uint64_t> w(c->ns);
-            for (int r = 0; r < 2; r++)
-                for (int i = 0; i < cols; i++) w[(size_t)r * cols + i] = (i + s >= cols) ? 1 : 0;
-            fhe_ct *t = S.add(lt, S.plain(eq, w, 2));
-            fhe_ct *nr = rank ? S.add(rank, t) : t;
-            S.finish();
-            if (!S.err) carry(rank, S.release(nr));
-        }
-        S.finish();
-        err = S.err;
-    }
-    std::vector<uint64_t> idx(c->ns);
-    for (int r = 0; r < 2; r++)
-        for (int i = 0; i < cols; i++) idx[(size_t)r * cols + i] = (uint64_t)i;
-    for (int s = 0; s < cols && !err; s++) {
-        Circuit S(c, evk);
-        const fhe_ct *rr = s ? S.rot(rank, gs[s - 1]) : rank;
-        std::vector<const fhe_ct *> xr(d);
-        for (int k = 0; k < d; k++) xr[k] = s ? S.rot(xs[k], gs[s - 1]) : xs[k];
-        std::map<int, const fhe_ct *> pw;
-        pw[1] = S.plain(rr, idx, 1);
-        std::function<const fhe_ct *(int)> power = [&](int n) -> const fhe_ct * {
-            auto it = pw.find(n);
-            if (it != pw.end()) return it->second;
-            const fhe_ct *r;
-            if ((n & (n - 1)) == 0) {
-                const fhe_ct *h = power(n / 2);
-                r = S.mul(h, h);
-            } else {
-                int a = 1;
-                while (a * 2 < n) a *= 2;
-                const fhe_ct *A = power(a);
-                const fhe_ct *Bp = power(n - a);
-                r = S.mul(A, Bp);
+    for (int a = 0; a < K && !err; a++) {
+        const std::vector<const fhe_ct *> xa = X(a);
+        for (int b = 0; b < K && !err; b++) {
+            const std::vector<const fhe_ct *> xb = X(b);
+            for (int s = 0; s < cols && !err; s++) {
+                if (b == a && s == 0) continue;
+                Circuit S(c, evk);
+                std::vector<const fhe_ct *> xr(d);
+                for (int k = 0; k < d; k++) xr[k] = s ? S.rot(xb[k], gs[s - 1]) : xb[k];
+                fhe_ct *lt = nullptr, *eq = nullptr;
+                if (!S.err) S.compare(xr.data(), xa.data(), d, true, true, &lt, &eq);
+                if (!S.err) {
+                    S.keep(lt);
+                    S.keep(eq);
+                    std::vector<uint64_t> w(c->ns);
+                    for (int r = 0; r < 2; r++)
+                        for (int i = 0; i < cols; i++)
+                            w[(size_t)r * cols + i] = (b * cols + (i + s) % cols < a * cols + i) ? 1 : 0;
+                    fhe_ct *t = S.add(lt, S.plain(eq, w, 2));
+                    fhe_ct *nr = rank[a] ? S.add(rank[a], t) : t;
+                    S.finish();
+                    if (!S.err) carry(rank[a], S.release(nr));
+                }
+                S.finish();
+                err = S.err;
             }
-            pw[n] = r;
-            return r;
-        };
-        fhe_ct *e = S.cadd(S.neg(power(p - 1)), 1);
-        std::vector<fhe_ct *> nxt(d, nullptr);
-        for (int k = 0; k < d && !S.err; k++) {
-            fhe_ct *t = S.mul(e, xr[k]);
-            nxt[k] = outs[k] ? S.add(outs[k], t) : t;
         }
-        S.finish();
-        if (!S.err)
-            for (int k = 0; k < d; k++) carry(outs[k], S.release(nxt[k]));
-        err = S.err;
     }
-    if (rank) fhe_ct_destroy(rank);
+    for (int a = 0; a < K && !err; a++) {
+        const std::vector<const fhe_ct *> xa = X(a);
+        for (int s = 0; s < cols && !err; s++) {
+            Circuit S(c, evk);
+            const fhe_ct *rr = s ? S.rot(rank[a], gs[s - 1]) : rank[a];
+            std::vector<const fhe_ct *> xr(d);
+            for (int k = 0; k < d; k++) xr[k] = s ? S.rot(xa[k], gs[s - 1]) : xa[k];
+            std::vector<fhe_ct *> nxt((size_t)K * d, nullptr);
+            for (int t = 0; t < K && !S.err; t++) {
+                std::vector<uint64_t> idx(c->ns);
+                for (int r = 0; r < 2; r++)
+                    for (int i = 0; i < cols; i++) idx[(size_t)r * cols + i] = (uint64_t)(t * cols + i);
+                std::map<int, const fhe_ct *> pw;
+                pw[1] = S.plain(rr, idx, 1);
+                std::function<const fhe_ct *(int)> power = [&](int n) -> const fhe_ct * {
+                    auto it = pw.find(n);
+                    if (it != pw.end()) return it->second;
+                    const fhe_ct *r;
+                    if ((n & (n - 1)) == 0) {
+                        const fhe_ct *h = power(n / 2);
+                        r = S.mul(h, h);
+                    } else {
+                        int m = 1;
+                        while (m * 2 < n) m *= 2;
+                        const fhe_ct *A = power(m);
+                        const fhe_ct *Bp = power(n - m);
+                        r = S.mul(A, Bp);
+                    }
+                    pw[n] = r;
+                    return r;
+                };
+                fhe_ct *e = S.cadd(S.neg(power(p - 1)), 1);
+                for (int k = 0; k < d && !S.err; k++) {
+                    fhe_ct *term = S.mul(e, xr[k]);
+                    fhe_ct *&o = outs[(size_t)t * d + k];
+                    nxt[(size_t)t * d + k] = o ? S.add(o, term) : term;
+                }
+            }
+            S.finish();
+            if (!S.err)
+                for (size_t i = 0; i < nxt.size(); i++) carry(outs[i], S.release(nxt[i]));
+            err = S.err;
+        }
+    }
+    for (fhe_ct *r : rank)
+        if (r) fhe_ct_destroy(r);
     if (err) {
         for (fhe_ct *o : outs)
             if (o) fhe_ct_destroy(o);
         return err;
     }
-    for (int k = 0; k < d; k++) out[k] = outs[k];
+    for (size_t i = 0; i < outs.size(); i++) out[i] = outs[i];
     return 0;
+}
+
+int circuit_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int d, fhe_ct **out)
+{
+    return circuit_sort_joint(c, evk, x, 1, d, out);
 }
 
 // ---------------------------------------------------------------------------

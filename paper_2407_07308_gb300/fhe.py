@@ -153,6 +153,7 @@ def lib() -> ctypes.CDLL:
             "fhe_mul_plain": (ci, [vp, vp, vp, POINTER(vp)]),
             "fhe_sort_galois": (ci, [vp, vp, ci]),
             "fhe_probe_bfly_peak": (ci, [vp]),
+            "fhe_sort_joint": (ci, [vp, vp, vp, ci, ci, POINTER(vp)]),
             "fhe_private_query": (ci, [vp, vp, vp, vp, vp, ci, vp, ci, POINTER(vp)]),
             "fhe_private_query_plan": (ci, [vp, vp, vp, vp, vp, ci, vp, ci, POINTER(vp)]),
             "fhe_ext_galois": (ci, [vp, ci, vp, ci]),
@@ -636,6 +637,15 @@ def fhe_sort(ctx, evk, xs):
     out = (c_void_p * d)()
     _check(lib().fhe_sort(ctx, evk, _handles(xs), d, out), ctx)
     return [c_void_p(v) for v in out]
+
+
+def fhe_sort_joint(ctx, evk, cts):
+    """Row r of the K batches cts[a] (each a list of d digit handles) sorted as
+    one sequence; returns K lists of d handles (batch t: positions t cols ..)."""
+    K, d = len(cts), len(cts[0])
+    out = (c_void_p * (K * d))()
+    _check(lib().fhe_sort_joint(ctx, evk, _handles([h for xs in cts for h in xs]), K, d, out), ctx)
+    return [[c_void_p(out[t * d + k]) for k in range(d)] for t in range(K)]
 
 
 def fhe_max_min(ctx, evk, xs, ys):

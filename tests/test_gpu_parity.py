@@ -727,3 +727,48 @@ def test_private_query_bitexact(overlap):
             fhe.fhe_plan_destroy(plan)
     finally:
         g.close()
+
+
+def test_sort_joint_bitexact():
+    """Sixteen values per row across four ciphertexts (p = 17, 4 columns),
+    ties across ciphertexts: bit-exact with the oracle's joint sort, traces
+    equal, decrypts to the sorted sequence; K cols > p is refused."""
+    from oracle.circuits import sort_galois, sort_joint
+
+    fhe = _fhe()
+    p, d, logN, K = 17, 2, 10, 4
+    gal = sort_galois(p, 2 ** logN)
+    params = dict(logN=logN, p=p, L=11, K=2, **CHAIN50)
+    o, g = _pair(params, seed=37, galois=gal)
+    try:
+        b = (p + 1) // 2
+        cols = g.ns // 2
+        rnd = random.Random(12)
+        vals = [[rnd.randrange(b ** d) for _ in range(g.ns)] for _ in range(K)]
+        vals[3][1] = vals[0][0]
+        vals[2][6] = vals[1][5]
+        dig = lambda v: [[(x // b ** k) % b for x in v] for k in range(d)]  # noqa: E731
+        xg = [[g.encrypt_slots([dig(vals[a])[k]], seed=1000 + 10 * a + k) for k in range(d)] for a in range(K)]
+        fhe.fhe_trace_enable(g.ctx, True)
+        out = fhe.fhe_sort_joint(g.ctx, g.evk, xg)
+        for hs in out:
+            for h in hs:
+                g.own(h)
+        trace_g = fhe.fhe_trace_get(g.ctx)
+        fhe.fhe_trace_enable(g.ctx, False)
+        dec = [[sum(int(g.decrypt(out[t][k])[0][s]) * b ** k for k in range(d)) for s in range(g.ns)] for t in range(K)]
+        for r in range(2):
+            seq = [vals[a][r * cols + c] for a in range(K) for c in range(cols)]
+            assert [dec[t][r * cols + c] for t in range(K) for c in range(cols)] == sorted(seq)
+        xo = [[o.encrypt_slots([dig(vals[a])[k]], seed=1000 + 10 * a + k)[0] for k in range(d)] for a in range(K)]
+        ev = o.evaluator()
+        out_o = sort_joint(ev, xo)
+        assert trace_g == ev.trace
+        for t in range(K):
+            for k in range(d):
+                _same(out_o[t][k], g.export(out[t][k]), 0)
+        with pytest.raises(fhe.FheError) as e:
+            fhe.fhe_sort_joint(g.ctx, g.evk, xg + [xg[0]])  # 5 x 4 columns > 17
+        assert e.value.code == -1
+    finally:
+        g.close()
