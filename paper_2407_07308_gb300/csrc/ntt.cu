@@ -290,10 +290,14 @@ __global__ void __launch_bounds__(Sub<N1>::T, FHE_MINB(Sub<N1>::T))
     const int job = blockIdx.x / BLK, lo0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
     const typename IO::St st = io.begin(job, NN);
     const u64 q = mq[st.prime].q, q2 = 2 * q;
-    for (int r = tid; r < (1 << N1); r += C::T) W[twp(r)] = tw[(size_t)st.prime * NN + r];
+    // one twiddle per thread (T = 2^N1), loaded before the tile and stored
+    // after it, so that its latency overlaps the tile's loads
+    static_assert(C::T == (1 << N1), "one twiddle per thread");
+    const ulonglong2 wv = __ldg(tw + (size_t)st.prime * NN + tid);
     tile_in<N1, IO::LDCH>(
         tid, [&](int r) { return io.load(st, ((r >> 4) << N2) + lo0 + (r & 15)); },
         [&](int r, u64 v) { sm[C::at(r & 15, r >> 4)] = v; });
+    W[twp(tid)] = wv;
     __syncthreads();
     sub16<N1, true>(sm, tid, PrefixTw{W}, 0, 0, 0, q, q2);
     __syncthreads();
@@ -370,13 +374,19 @@ __global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
     const ModQ mqp = mq[prime];
     const u64 q = mqp.q, q2 = 2 * q;
     const ulonglong2 *W = tw + (size_t)prime * NN;
-    for (int k = tid; k < (1 << N2) - 1; k += C::T) {
-        const int u = 31 - __clz(k + 1);  // stage of entry k
-        tws[twp(k)] = __ldg(W + (1 << (N1 + u)) + (hi << u) + (k + 1 - (1 << u)));
+    // at most one twiddle per thread (T = 2^N2), loaded before the tile and
+    // stored after it, so that its latency overlaps the tile's loads
+    static_assert(C::T >= (1 << N2) - 1, "one twiddle per thread");
+    const bool has_w = tid < (1 << N2) - 1;
+    ulonglong2 wv = make_ulonglong2(0, 0);
+    if (has_w) {
+        const int u = 31 - __clz(tid + 1);  // stage of entry tid
+        wv = __ldg(W + (1 << (N1 + u)) + (hi << u) + (tid + 1 - (1 << u)));
     }
     tile_in<N2>(
         tid, [&](int r) { return io.inter(sts[r >> N2])[(hi << N2) + (r & (C::SZ - 1))]; },
         [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
+    if (has_w) tws[twp(tid)] = wv;
     __syncthreads();
     sub16<N2, true>(sm, tid, RowTw{tws, N1, hi}, N1, hi, 0, q, q2);
     __syncthreads();
@@ -402,13 +412,17 @@ __global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
     const int prime = sts[0].prime;
     const u64 q = mq[prime].q, q2 = 2 * q;
     const ulonglong2 *W = tw + (size_t)prime * NN;
-    for (int k = tid; k < (1 << N2) - 1; k += C::T) {
-        const int u = 31 - __clz(k + 1);
-        tws[twp(k)] = __ldg(W + (1 << (N1 + u)) + (hi << u) + (k + 1 - (1 << u)));
+    static_assert(C::T >= (1 << N2) - 1, "one twiddle per thread");
+    const bool has_w = tid < (1 << N2) - 1;
+    ulonglong2 wv = make_ulonglong2(0, 0);
+    if (has_w) {  // stored after the tile (latency overlap)
+        const int u = 31 - __clz(tid + 1);
+        wv = __ldg(W + (1 << (N1 + u)) + (hi << u) + (tid + 1 - (1 << u)));
     }
     tile_in<N2>(
         tid, [&](int r) { return io.load(sts[r >> N2], (hi << N2) + (r & (C::SZ - 1))); },
         [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
+    if (has_w) tws[twp(tid)] = wv;
     __syncthreads();
     sub16<N2, false>(sm, tid, RowTw{tws, N1, hi}, N1, hi, 0, q, q2);
     __syncthreads();
@@ -431,12 +445,14 @@ __global__ void __launch_bounds__(Sub<N1>::T, FHE_MINB(Sub<N1>::T))
     const int job = blockIdx.x / BLK, lo0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
     const typename IO::St st = io.begin(job, NN);
     const u64 q = mq[st.prime].q, q2 = 2 * q;
-    for (int r = tid; r < (1 << N1); r += C::T) W[twp(r)] = tw[(size_t)st.prime * NN + r];
+    static_assert(C::T == (1 << N1), "one twiddle per thread");
+    const ulonglong2 wv = __ldg(tw + (size_t)st.prime * NN + tid);  // stored after the tile (latency overlap)
     const ulonglong2 ni = io.final_scale(st, ninv);
     const u64 *mid = io.inter(st);
     tile_in<N1>(
         tid, [&](int r) { return mid[((r >> 4) << N2) + lo0 + (r & 15)]; },
         [&](int r, u64 v) { sm[C::at(r & 15, r >> 4)] = v; });
+    W[twp(tid)] = wv;
     __syncthreads();
     sub16<N1, false>(sm, tid, PrefixTw{W}, 0, 0, 0, q, q2);
     __syncthreads();
