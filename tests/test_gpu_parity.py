@@ -2,6 +2,7 @@
 identical seeded inputs.  Every comparison of ciphertext limbs is exact
 (tolerance 0: integer arithmetic), decryptions are compared with plaintext
 results, and the circuit-level operation traces must be identical."""
+import os
 import random
 
 import numpy as np
@@ -304,9 +305,10 @@ def test_ntt_variants_and_autotuner(logN, variants):
     g = GpuSetup(seed=13, logN=logN, p=17, L=6, K=2, **CHAIN50)
     try:
         v, ms = fhe.fhe_ctx_ntt_variant(g.ctx)
-        assert v in variants and all(ms[u] > 0 for u in variants)
-        assert v == 0 or ms[v] < 0.97 * ms[0]
-        assert fhe.fhe_ctx_autotune(g.ctx, 64) in variants
+        if not os.environ.get("FHE_NTT_VARIANT"):  # a pinned variant skips the timings
+            assert v in variants and all(ms[u] > 0 for u in variants)
+            assert v == 0 or ms[v] < 0.97 * ms[0]
+            assert fhe.fhe_ctx_autotune(g.ctx, 64) in variants
         rnd = random.Random(4)
         xs = [[rnd.randrange(9) for _ in range(g.ns)] for _ in range(16)]
         ys = [[x if rnd.random() < 0.3 else rnd.randrange(9) for x in row] for row in xs]
