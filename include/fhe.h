@@ -53,7 +53,9 @@ enum {
     FHE_ETIMEOUT = -6,    /* a bounded wait ran out */
     FHE_ECUDA = -7,       /* a CUDA runtime call failed */
     FHE_ENOKEY = -8,      /* no switching key for the requested Galois element */
-    FHE_EUNSUPPORTED = -9 /* parameter combination not provided */
+    FHE_EUNSUPPORTED = -9, /* parameter combination not provided */
+    FHE_ECANCELED = -10,   /* a served request was canceled before it ran */
+    FHE_EBUSY = -11        /* the request already runs or is done */
 };
 
 /* BGV parameters.  The prime chain is the L+K smallest primes q with
@@ -191,6 +193,20 @@ int fhe_ct_import_coeff(fhe_ctx *ctx, const uint64_t *host, int count, int npoly
  * the context's stream (host must stay valid until the stream reaches it).
  * This is how new inputs reach a captured plan (fhe_compare_plan). */
 int fhe_ct_load_coeff(fhe_ctx *ctx, fhe_ct *ct, const uint64_t *host);
+
+/* Checkpoint / resume of a ciphertext batch.  The image is a 32-byte header
+ * ("FHEC", version 1, log2 N, polynomials, count, level as u32; p as u64),
+ * the level's primes q_0 .. q_{level-1} (u64), then the coefficient-domain
+ * limbs [count][npoly][level][N] (u64, as fhe_ct_export_coeff writes them);
+ * host byte order.  fhe_ct_serialize stores the image size in *size and, when
+ * buf is non-NULL, writes the image (FHE_EINVAL if cap is smaller); it
+ * synchronises.  fhe_ct_deserialize creates a new handle in ctx from an image,
+ * refusing one of another ring degree, plaintext modulus or prime chain
+ * (FHE_EMISMATCH), a truncated or oversized buffer or a residue not below its
+ * prime (FHE_EINVAL).  Keys are not imaged: the seeded key generators
+ * recreate them. */
+int fhe_ct_serialize(fhe_ctx *ctx, const fhe_ct *ct, void *buf, uint64_t cap, uint64_t *size);
+int fhe_ct_deserialize(fhe_ctx *ctx, const void *buf, uint64_t size, fhe_ct **out);
 
 /* ---- arithmetic (Sec. 2.1: add, mult, rotate; Sec. 2.2: RNS, NTT) -------- */
 
@@ -518,6 +534,10 @@ int fhe_server_submit(fhe_server *server, const fhe_job *job, uint64_t *ticket);
  * it is done (the ticket is then retired), 0 when not yet, FHE_EINVAL for an
  * unknown ticket.  info may be NULL. */
 int fhe_server_poll(fhe_server *server, uint64_t ticket, int timeout_ms, fhe_request_info *info);
+/* Cancels a request that is still queued: it reports done with error
+ * FHE_ECANCELED and writes no outputs.  FHE_EBUSY if it was already admitted
+ * (its batch runs to completion), FHE_EINVAL for an unknown ticket. */
+int fhe_server_cancel(fhe_server *server, uint64_t ticket);
 int fhe_server_stats(fhe_server *server, fhe_server_status *status);
 /* Serves every request already submitted, joins the worker and frees the
  * server; tickets not yet polled are retired with it. */

@@ -723,6 +723,7 @@ static int encode_batch_ext(fhe_ctx *c, const uint64_t *digits, int count, int d
 extern "C" int fhe_encrypt_explicit(fhe_ctx *c, const fhe_pk *pk, const uint64_t *slots, int count,
                                     const int64_t *u, const int64_t *e0, const int64_t *e1, fhe_ct **out)
 {
+    FHE_RANGE("fhe_encrypt_explicit");
     CHECK_CTX(c);
     if (!pk || !slots || !u || !e0 || !e1 || !out || count < 1) return FHE_EINVAL;
     LOCK(c);
@@ -749,6 +750,7 @@ extern "C" int fhe_encrypt_explicit(fhe_ctx *c, const fhe_pk *pk, const uint64_t
 
 extern "C" int fhe_encrypt(fhe_ctx *c, const fhe_pk *pk, const uint64_t *slots, int count, uint64_t seed, fhe_ct **out)
 {
+    FHE_RANGE("fhe_encrypt");
     CHECK_CTX(c);
     if (!pk || !slots || !out || count < 1) return FHE_EINVAL;
     LOCK(c);
@@ -799,6 +801,7 @@ static int decrypt_coeffs_dev(fhe_ctx *c, const fhe_sk *sk, const fhe_ct *ct, in
 
 extern "C" int fhe_decrypt(fhe_ctx *c, const fhe_sk *sk, const fhe_ct *ct, uint64_t *slots)
 {
+    FHE_RANGE("fhe_decrypt");
     CHECK_CTX(c);
     if (!sk || !ct || !slots || ct->npoly != 2) return FHE_EINVAL;
     LOCK(c);
@@ -831,6 +834,7 @@ extern "C" int fhe_ext_galois(fhe_ctx *c, int d, int64_t *galois, int cap)
 extern "C" int fhe_encrypt_ext(fhe_ctx *c, const fhe_pk *pk, const uint64_t *digits, int count, int d, uint64_t seed,
                                fhe_ct **out)
 {
+    FHE_RANGE("fhe_encrypt_ext");
     CHECK_CTX(c);
     if (!pk || !digits || !out || count < 1 || d < 1) return FHE_EINVAL;
     LOCK(c);
@@ -883,6 +887,7 @@ extern "C" int fhe_encrypt_ext_explicit(fhe_ctx *c, const fhe_pk *pk, const uint
 
 extern "C" int fhe_decrypt_ext(fhe_ctx *c, const fhe_sk *sk, const fhe_ct *ct, int d, uint64_t *digits)
 {
+    FHE_RANGE("fhe_decrypt_ext");
     CHECK_CTX(c);
     if (!sk || !ct || !digits || ct->npoly != 2 || d < 1) return FHE_EINVAL;
     LOCK(c);
@@ -947,6 +952,7 @@ int refresh_seeded(fhe_ctx *c, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct 
 extern "C" int fhe_refresh(fhe_ctx *c, const fhe_sk *sk, const fhe_pk *pk, const fhe_ct *ct, uint64_t seed,
                            fhe_ct **out)
 {
+    FHE_RANGE("fhe_refresh");
     CHECK_CTX(c);
     if (!sk || !pk || !ct || ct->npoly != 2 || !out) return FHE_EINVAL;
     LOCK(c);
@@ -1010,6 +1016,65 @@ extern "C" int fhe_ct_import_coeff(fhe_ctx *c, const uint64_t *host, int count, 
     }
     *out = ct;
     return 0;
+}
+
+// Checkpoint image of a ciphertext batch: a fixed header, the level's primes,
+// then the coefficient-domain limbs [count][npoly][level][N] (u64 residues).
+namespace {
+struct CtImage {
+    char magic[4];  // "FHEC"
+    uint32_t version, log_n, npoly, count, level;
+    uint64_t p;
+};
+static_assert(sizeof(CtImage) == 32, "image header layout");
+}  // namespace
+
+extern "C" int fhe_ct_serialize(fhe_ctx *c, const fhe_ct *ct, void *buf, uint64_t cap, uint64_t *size)
+{
+    CHECK_CTX(c);
+    if (!ct || ct->ctx != c || !size) return FHE_EINVAL;
+    const uint64_t need = sizeof(CtImage) + 8ull * ct->level + (uint64_t)ct->bytes;
+    *size = need;
+    if (!buf) return 0;
+    if (cap < need) return fhe_fail(c, FHE_EINVAL, "serialize: buffer smaller than the image");
+    CtImage h;
+    memcpy(h.magic, "FHEC", 4);
+    h.version = 1;
+    h.log_n = (uint32_t)c->logN;
+    h.npoly = (uint32_t)ct->npoly;
+    h.count = (uint32_t)ct->count;
+    h.level = (uint32_t)ct->level;
+    h.p = c->p;
+    char *o = (char *)buf;
+    memcpy(o, &h, sizeof h);
+    for (int i = 0; i < ct->level; i++) memcpy(o + sizeof h + 8 * i, &c->q[i], 8);
+    return fhe_ct_export_coeff(c, ct, (uint64_t *)(o + sizeof h + 8ull * ct->level));
+}
+
+extern "C" int fhe_ct_deserialize(fhe_ctx *c, const void *buf, uint64_t size, fhe_ct **out)
+{
+    CHECK_CTX(c);
+    if (!buf || !out || size < sizeof(CtImage)) return FHE_EINVAL;
+    CtImage h;
+    memcpy(&h, buf, sizeof h);
+    if (memcmp(h.magic, "FHEC", 4) || h.version != 1) return fhe_fail(c, FHE_EINVAL, "deserialize: not an image");
+    if ((int)h.log_n != c->logN || h.p != c->p || h.npoly < 2 || h.npoly > 3 || h.count < 1 || h.level < 1 ||
+        (int)h.level > c->L)
+        return fhe_fail(c, FHE_EMISMATCH, "deserialize: image of another ring, plaintext modulus or level");
+    const uint64_t words = (uint64_t)h.count * h.npoly * h.level * (uint64_t)c->N;
+    if (size != sizeof h + 8ull * h.level + 8 * words) return fhe_fail(c, FHE_EINVAL, "deserialize: size mismatch");
+    const char *in = (const char *)buf;
+    for (uint32_t i = 0; i < h.level; i++) {
+        uint64_t q;
+        memcpy(&q, in + sizeof h + 8 * i, 8);
+        if (q != c->q[i]) return fhe_fail(c, FHE_EMISMATCH, "deserialize: image of another prime chain");
+    }
+    std::vector<uint64_t> limbs(words);
+    memcpy(limbs.data(), in + sizeof h + 8ull * h.level, 8 * words);
+    const uint64_t N = (uint64_t)c->N;
+    for (uint64_t w = 0; w < words; w++)
+        if (limbs[w] >= c->q[(w / N) % h.level]) return fhe_fail(c, FHE_EINVAL, "deserialize: residue out of range");
+    return fhe_ct_import_coeff(c, limbs.data(), (int)h.count, (int)h.npoly, (int)h.level, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -1100,6 +1165,7 @@ extern "C" int fhe_add_const(fhe_ctx *c, const fhe_ct *a, int64_t k, fhe_ct **ou
 
 extern "C" int fhe_mul(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **out)
 {
+    FHE_RANGE("fhe_mul");
     CHECK_CTX(c);
     if (!same_ctx(c, a) || !same_ctx(c, b) || !out) return FHE_EINVAL;
     LOCK(c);
@@ -1114,6 +1180,7 @@ extern "C" int fhe_mul(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **ou
 
 extern "C" int fhe_relinearize(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *a, fhe_ct **out)
 {
+    FHE_RANGE("fhe_relinearize");
     CHECK_CTX(c);
     if (!evk || evk->ctx != c || !same_ctx(c, a) || !out) return FHE_EINVAL;
     LOCK(c);
@@ -1123,6 +1190,7 @@ extern "C" int fhe_relinearize(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *a, 
 
 extern "C" int fhe_mod_switch(fhe_ctx *c, const fhe_ct *a, int target_level, fhe_ct **out)
 {
+    FHE_RANGE("fhe_mod_switch");
     CHECK_CTX(c);
     if (!same_ctx(c, a) || !out) return FHE_EINVAL;
     LOCK(c);
@@ -1132,6 +1200,7 @@ extern "C" int fhe_mod_switch(fhe_ctx *c, const fhe_ct *a, int target_level, fhe
 
 extern "C" int fhe_rotate(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *a, int64_t galois, fhe_ct **out)
 {
+    FHE_RANGE("fhe_rotate");
     CHECK_CTX(c);
     if (!evk || evk->ctx != c || !same_ctx(c, a) || !out) return FHE_EINVAL;
     LOCK(c);
@@ -1147,6 +1216,7 @@ extern "C" int fhe_rotate(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *a, int64
 
 extern "C" int fhe_mul_relin(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *a, const fhe_ct *b, fhe_ct **out)
 {
+    FHE_RANGE("fhe_mul_relin");
     CHECK_CTX(c);
     if (!evk || evk->ctx != c || !same_ctx(c, a) || !same_ctx(c, b) || !out) return FHE_EINVAL;
     LOCK(c);
@@ -1182,6 +1252,7 @@ int check_digits(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const f
 extern "C" int fhe_compare(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
                            fhe_ct **lt, fhe_ct **eq)
 {
+    FHE_RANGE("fhe_compare");
     CHECK_CTX(c);
     int e = check_digits(c, evk, x, y, d);
     if (e) return e;
@@ -1194,6 +1265,7 @@ extern "C" int fhe_compare(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *
 extern "C" int fhe_compare_bivariate(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x,
                                      const fhe_ct *const *y, int d, fhe_ct **lt, fhe_ct **eq)
 {
+    FHE_RANGE("fhe_compare_bivariate");
     CHECK_CTX(c);
     int e = check_digits(c, evk, x, y, d);
     if (e) return e;
@@ -1216,21 +1288,25 @@ static int plain_api(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, int kin
 
 extern "C" int fhe_add_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, fhe_ct **out)
 {
+    FHE_RANGE("fhe_add_plain");
     return plain_api(c, a, slots, 0, out);
 }
 
 extern "C" int fhe_sub_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, fhe_ct **out)
 {
+    FHE_RANGE("fhe_sub_plain");
     return plain_api(c, a, slots, 1, out);
 }
 
 extern "C" int fhe_mul_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, fhe_ct **out)
 {
+    FHE_RANGE("fhe_mul_plain");
     return plain_api(c, a, slots, 2, out);
 }
 
 extern "C" int fhe_extract_digits(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *a, int d, fhe_ct **out)
 {
+    FHE_RANGE("fhe_extract_digits");
     CHECK_CTX(c);
     if (!evk || evk->ctx != c || !same_ctx(c, a) || a->npoly != 2 || !out || d < 1) return FHE_EINVAL;
     LOCK(c);
@@ -1246,6 +1322,7 @@ extern "C" int fhe_extract_digits(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *
 extern "C" int fhe_private_query(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *q, const fhe_ct *data,
                                  const fhe_ct *op1, int op2, const int64_t *codes, int flags, fhe_ct **out)
 {
+    FHE_RANGE("fhe_private_query");
     CHECK_CTX(c);
     if (!evk || evk->ctx != c || !same_ctx(c, q) || !same_ctx(c, data) || !same_ctx(c, op1) || !codes || !out ||
         op2 < 1 || op2 >= (1 << 20) || (flags & ~FHE_QUERY_OVERLAP))
@@ -1276,6 +1353,7 @@ extern "C" int fhe_slot_plan(int slots, int64_t ring_n, int n, const uint8_t *us
 extern "C" int fhe_slot_pack(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *in, int n, const uint8_t *useful,
                              fhe_ct **out, int out_cap)
 {
+    FHE_RANGE("fhe_slot_pack");
     CHECK_CTX(c);
     if (!evk || evk->ctx != c || !in || n < 1 || !useful || !out || out_cap < 0) return FHE_EINVAL;
     for (int j = 0; j < n; j++) {
@@ -1306,6 +1384,7 @@ extern "C" int fhe_sort_galois(const fhe_ctx *c, int64_t *galois, int cap)
 
 extern "C" int fhe_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int d, fhe_ct **out)
 {
+    FHE_RANGE("fhe_sort");
     CHECK_CTX(c);
     if (!out) return FHE_EINVAL;
     int e = check_digits(c, evk, x, x, d);
@@ -1317,6 +1396,7 @@ extern "C" int fhe_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, 
 
 extern "C" int fhe_sort_joint(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int K, int d, fhe_ct **out)
 {
+    FHE_RANGE("fhe_sort_joint");
     CHECK_CTX(c);
     if (!out || !x || K < 1 || d < 1) return FHE_EINVAL;
     int e = check_digits(c, evk, x, x, d);
@@ -1348,6 +1428,7 @@ extern "C" int fhe_compare_eq(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *cons
 extern "C" int fhe_max_min(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
                            fhe_ct **out_max, fhe_ct **out_min)
 {
+    FHE_RANGE("fhe_max_min");
     CHECK_CTX(c);
     int e = check_digits(c, evk, x, y, d);
     if (e) return e;
@@ -1437,11 +1518,13 @@ static int raw_ntt_batch(fhe_ctx *c, uint64_t *data, int count, int nprimes, boo
 
 extern "C" int fhe_ntt_forward_batch(fhe_ctx *c, uint64_t *data, int count, int nprimes)
 {
+    FHE_RANGE("fhe_ntt_forward_batch");
     return raw_ntt_batch(c, data, count, nprimes, false);
 }
 
 extern "C" int fhe_ntt_inverse_batch(fhe_ctx *c, uint64_t *data, int count, int nprimes)
 {
+    FHE_RANGE("fhe_ntt_inverse_batch");
     return raw_ntt_batch(c, data, count, nprimes, true);
 }
 
@@ -1573,6 +1656,7 @@ static int capture_plan(fhe_ctx *c, int flags, const std::function<int(fhe_ct **
 extern "C" int fhe_compare_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y,
                                 int d, int want_lt, int want_eq, int flags, fhe_plan **out)
 {
+    FHE_RANGE("fhe_compare_plan");
     CHECK_CTX(c);
     if (!out || (!want_lt && !want_eq) || (flags & ~(FHE_PLAN_SERIAL | FHE_PLAN_BIVARIATE))) return FHE_EINVAL;
     int e = check_digits(c, evk, x, y, d);
@@ -1591,6 +1675,7 @@ extern "C" int fhe_compare_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *co
 extern "C" int fhe_private_query_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *q, const fhe_ct *data,
                                       const fhe_ct *op1, int op2, const int64_t *codes, int flags, fhe_plan **out)
 {
+    FHE_RANGE("fhe_private_query_plan");
     CHECK_CTX(c);
     if (!evk || evk->ctx != c || !same_ctx(c, q) || !same_ctx(c, data) || !same_ctx(c, op1) || !codes || !out ||
         op2 < 1 || op2 >= (1 << 20) || (flags & ~FHE_PLAN_SERIAL))
@@ -1609,6 +1694,7 @@ extern "C" int fhe_private_query_plan(fhe_ctx *c, const fhe_evk *evk, const fhe_
 
 extern "C" int fhe_plan_run(fhe_plan *P)
 {
+    FHE_RANGE("fhe_plan_run");
     if (!P || !P->exec) return FHE_EINVAL;
     fhe_ctx *c = P->ctx;
     LOCK(c);
@@ -1653,6 +1739,7 @@ extern "C" int fhe_tournament_galois(const fhe_ctx *c, int64_t *galois, int cap)
 extern "C" int fhe_tournament(fhe_ctx *c, const fhe_evk *evk, const fhe_sk *sk, const fhe_pk *pk,
                               const fhe_ct *const *x, int d, uint64_t seed, fhe_ct **out_max, fhe_ct **out_min)
 {
+    FHE_RANGE("fhe_tournament");
     CHECK_CTX(c);
     if (!evk || evk->ctx != c || !x || d < 1 || (!out_max && !out_min)) return FHE_EINVAL;
     for (int k = 0; k < d; k++)

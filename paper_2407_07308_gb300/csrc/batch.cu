@@ -467,6 +467,7 @@ extern "C" int fhe_batch_submit(const fhe_job *jobs, int n, fhe_batch **out)
 
 extern "C" int fhe_batch_submit_ex(const fhe_job *jobs, int n, int flags, fhe_batch **out)
 {
+    FHE_RANGE("fhe_batch_submit_ex");
     if (!jobs || n < 1 || !out || (flags & ~FHE_BATCH_ALIGN_LEVELS)) return FHE_EINVAL;
     for (int i = 0; i < n; i++) {
         int e = batch_check_job(jobs[i]);

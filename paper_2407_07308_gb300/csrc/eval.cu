@@ -661,6 +661,7 @@ struct Circuit {
     }
     fhe_ct *mul(const fhe_ct *a, const fhe_ct *b)
     {
+        FHE_RANGE("circuit mul");
         if (err || !a || !b) return nullptr;
         const int lv = std::min(a->level, b->level);
         const fhe_ct *a2 = lower(a, lv), *b2 = lower(b, lv);
@@ -720,6 +721,7 @@ struct Circuit {
 
     fhe_ct *rot(const fhe_ct *a, int64_t g)
     {
+        FHE_RANGE("circuit rot");
         if (err || !a) return nullptr;
         const KeySwitchKey *key = evk->find(g);
         if (!key) {

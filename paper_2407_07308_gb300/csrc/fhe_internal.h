@@ -13,6 +13,19 @@
 #include "../../include/fhe.h"
 #include "modarith.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
+// NVTX range over a scope: every public evaluation call and every circuit
+// product and rotation shows up by name on a profiler's timeline (the calls
+// cost nothing measurable when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define FHE_RANGE(name) NvtxRange fhe_nvtx_range_(name)
+
 #define FHE_MAXP 32  // max data + special primes
 #define FHE_MAXK 8   // max special primes (alpha)
 #define FHE_MAXD 8   // max key-switching digits

@@ -216,6 +216,26 @@ extern "C" int fhe_server_submit(fhe_server *s, const fhe_job *job, uint64_t *ti
     return 0;
 }
 
+extern "C" int fhe_server_cancel(fhe_server *s, uint64_t ticket)
+{
+    if (!s) return FHE_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return FHE_EINVAL;
+    Request *q = it->second.get();
+    if (q->state != FHE_REQ_QUEUED) return FHE_EBUSY;
+    auto pos = std::find(s->queue.begin(), s->queue.end(), q);
+    if (pos == s->queue.end()) return FHE_EBUSY;
+    s->queue.erase(pos);
+    q->state = FHE_REQ_DONE;
+    q->error = FHE_ECANCELED;
+    q->t_done = s->now();
+    s->completed++;
+    s->failed++;
+    s->cv_done.notify_all();
+    return 0;
+}
+
 extern "C" int fhe_server_poll(fhe_server *s, uint64_t ticket, int timeout_ms, fhe_request_info *info)
 {
     if (!s) return FHE_EINVAL;

@@ -153,6 +153,9 @@ def lib() -> ctypes.CDLL:
             "fhe_mul_plain": (ci, [vp, vp, vp, POINTER(vp)]),
             "fhe_sort_galois": (ci, [vp, vp, ci]),
             "fhe_probe_bfly_peak": (ci, [vp]),
+            "fhe_ct_serialize": (ci, [vp, vp, vp, u64, POINTER(c_uint64)]),
+            "fhe_ct_deserialize": (ci, [vp, vp, u64, POINTER(vp)]),
+            "fhe_server_cancel": (ci, [vp, c_uint64]),
             "fhe_sort_joint": (ci, [vp, vp, vp, ci, ci, POINTER(vp)]),
             "fhe_private_query": (ci, [vp, vp, vp, vp, vp, ci, vp, ci, POINTER(vp)]),
             "fhe_private_query_plan": (ci, [vp, vp, vp, vp, vp, ci, vp, ci, POINTER(vp)]),
@@ -388,6 +391,21 @@ def fhe_philox_blocks(seed: int, tag: int, n: int):
 
 def fhe_ct_destroy(ct):
     lib().fhe_ct_destroy(ct)
+
+
+def fhe_ct_serialize(ctx, ct) -> bytes:
+    """The ciphertext batch as a checkpoint image (header, primes, limbs)."""
+    n = c_uint64()
+    _check(lib().fhe_ct_serialize(ctx, ct, None, 0, ctypes.byref(n)), ctx)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().fhe_ct_serialize(ctx, ct, buf, n.value, ctypes.byref(n)), ctx)
+    return buf.raw
+
+
+def fhe_ct_deserialize(ctx, image: bytes):
+    out = c_void_p()
+    _check(lib().fhe_ct_deserialize(ctx, image, len(image), ctypes.byref(out)), ctx)
+    return out
 
 
 def fhe_ct_export_coeff(ctx, ct):
@@ -812,6 +830,15 @@ def fhe_server_poll(server, ticket: int, timeout_ms: int = 0):
     info = fhe_request_info()
     rc = _check(lib().fhe_server_poll(server, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(info)))
     return rc == 1, info
+
+
+def fhe_server_cancel(server, ticket: int) -> int:
+    """0 if the queued request was canceled; FHE_EBUSY (-11) if it already
+    runs or is done."""
+    rc = lib().fhe_server_cancel(server, ctypes.c_uint64(ticket))
+    if rc < 0 and rc != -11:
+        _check(rc)
+    return rc
 
 
 def fhe_server_stats(server) -> fhe_server_status:

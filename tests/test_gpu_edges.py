@@ -248,3 +248,63 @@ def test_extract_and_query_refusals_and_degenerate_cases():
             fhe.fhe_private_query(g.ctx, g.evk, q, data, op1, 0, (1, 2, 3))
     finally:
         g.close()
+
+
+def test_checkpoint_resume_of_ciphertexts():
+    """A batch imaged with fhe_ct_serialize and restored into a new context
+    built from the same seeds gives, through a comparison, the bits of the
+    original; images of another ring, a truncated image and an out-of-range
+    residue are refused."""
+    from paper_2407_07308_gb300 import fhe
+
+    def make(p=17):
+        ctx = fhe.fhe_ctx_create(11, p, 8, 2, CHAIN50["U"], CHAIN50["lo"], CHAIN50["hi"])
+        sk, pk = fhe.fhe_keygen(ctx, 5)
+        evk = fhe.fhe_evk_create(ctx, sk, [], 6)
+        return ctx, sk, pk, evk
+
+    def free(ctx, sk, pk, evk):
+        fhe.fhe_evk_destroy(evk)
+        fhe.fhe_sk_destroy(sk)
+        fhe.fhe_pk_destroy(pk)
+        fhe.fhe_ctx_destroy(ctx)
+
+    a = make()
+    ctx, sk, pk, evk = a
+    ns = fhe.fhe_ctx_info(ctx).slots
+    rnd = np.random.default_rng(2)
+    xv, yv = rnd.integers(0, 9, size=(2, 3, ns))
+    x, y = fhe.fhe_encrypt(ctx, pk, xv, 1), fhe.fhe_encrypt(ctx, pk, yv, 2)
+    x3 = fhe.fhe_mod_switch(ctx, x, 5)
+    images = [fhe.fhe_ct_serialize(ctx, h) for h in (x, y, x3)]
+    lt = fhe.fhe_compare_lt(ctx, evk, [x], [y])
+    want = fhe.fhe_ct_export_coeff(ctx, lt)
+    for h in (x, y, x3, lt):
+        fhe.fhe_ct_destroy(h)
+    free(*a)
+    b = make()  # resume: same seeds, new context
+    ctx, sk, pk, evk = b
+    other = make(131)
+    try:
+        x, y, x3 = (fhe.fhe_ct_deserialize(ctx, im) for im in images)
+        assert fhe.fhe_ct_shape(x3)[2] == 5
+        lt = fhe.fhe_compare_lt(ctx, evk, [x], [y])
+        assert np.array_equal(fhe.fhe_ct_export_coeff(ctx, lt), want)
+        assert (fhe.fhe_decrypt(ctx, sk, lt) == (xv < yv)).all()
+        assert fhe.fhe_ct_serialize(ctx, x) == images[0]
+        with pytest.raises(fhe.FheError) as e:
+            fhe.fhe_ct_deserialize(other[0], images[0])
+        assert e.value.code == -2
+        with pytest.raises(fhe.FheError) as e:
+            fhe.fhe_ct_deserialize(ctx, images[0][:-8])
+        assert e.value.code == -1
+        bad = bytearray(images[0])
+        bad[-8:] = (2 ** 64 - 1).to_bytes(8, "little")
+        with pytest.raises(fhe.FheError) as e:
+            fhe.fhe_ct_deserialize(ctx, bytes(bad))
+        assert e.value.code == -1
+        for h in (x, y, x3, lt):
+            fhe.fhe_ct_destroy(h)
+    finally:
+        free(*b)
+        free(*other)

@@ -266,3 +266,51 @@ def test_errors_are_reported_and_context_recovers():
             if h:
                 fhe.fhe_ct_destroy(h)
         _close(fhe, ctxs)
+
+
+def test_queued_request_is_canceled():
+    """A request held back by the memory budget is canceled while the one
+    before it runs: it reports done with FHE_ECANCELED and no outputs; the
+    running one completes; canceling a finished request answers FHE_EBUSY."""
+    from paper_2407_07308_gb300 import fhe
+
+    ctx = fhe.fhe_ctx_create(14, 131, 10, 3, CHAIN50["U"], CHAIN50["lo"], CHAIN50["hi"])
+    handles = []
+    try:
+        sk, pk = fhe.fhe_keygen(ctx, 1)
+        evk = fhe.fhe_evk_create(ctx, sk, [], 2)
+        ns = fhe.fhe_ctx_info(ctx).slots
+        rnd = np.random.default_rng(3)
+        xv, yv = rnd.integers(0, 66 ** 2, size=(2, 16, ns))
+        ops = []
+        for vals, sd in ((xv, 10), (yv, 20)):
+            hs = [fhe.fhe_encrypt(ctx, pk, (vals // 66 ** k) % 66, sd + k) for k in range(2)]
+            handles += hs
+            ops.append(hs)
+        j1 = fhe.Job(ctx, evk, fhe.FHE_JOB_COMPARE, ops[0], ops[1])
+        j2 = fhe.Job(ctx, evk, fhe.FHE_JOB_COMPARE, ops[0], ops[1])
+        srv = fhe.fhe_server_start(hbm_budget=fhe.fhe_job_footprint(j1))  # one request at a time
+        try:
+            t1 = fhe.fhe_server_submit(srv, j1)
+            t2 = fhe.fhe_server_submit(srv, j2)
+            assert fhe.fhe_server_cancel(srv, t2) == 0
+            done, info = fhe.fhe_server_poll(srv, t2, 0)
+            assert done and info.error == -10
+            done, info = fhe.fhe_server_poll(srv, t1, 120000)
+            assert done and info.error == 0
+            assert (fhe.fhe_decrypt(ctx, sk, j1.out0[0]) == (xv < yv)).all()
+            assert j2.out0[0].value is None  # nothing written
+            assert fhe.fhe_server_cancel(srv, t1) == -11
+            with pytest.raises(fhe.FheError):
+                fhe.fhe_server_cancel(srv, 987654321)
+        finally:
+            fhe.fhe_server_stop(srv)
+        for h in j1.out0 + j1.out1:
+            fhe.fhe_ct_destroy(h)
+        fhe.fhe_evk_destroy(evk)
+        fhe.fhe_sk_destroy(sk)
+        fhe.fhe_pk_destroy(pk)
+    finally:
+        for h in handles:
+            fhe.fhe_ct_destroy(h)
+        fhe.fhe_ctx_destroy(ctx)
