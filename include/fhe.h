@@ -536,7 +536,8 @@ int fhe_server_submit(fhe_server *server, const fhe_job *job, uint64_t *ticket);
 int fhe_server_poll(fhe_server *server, uint64_t ticket, int timeout_ms, fhe_request_info *info);
 /* Cancels a request that is still queued: it reports done with error
  * FHE_ECANCELED and writes no outputs.  FHE_EBUSY if it was already admitted
- * (its batch runs to completion), FHE_EINVAL for an unknown ticket. */
+ * (its batch runs to completion), FHE_EINVAL for an unknown ticket (including
+ * one retired by fhe_server_poll reporting it done). */
 int fhe_server_cancel(fhe_server *server, uint64_t ticket);
 int fhe_server_stats(fhe_server *server, fhe_server_status *status);
 /* Serves every request already submitted, joins the worker and frees the

@@ -293,16 +293,19 @@ def test_queued_request_is_canceled():
         try:
             t1 = fhe.fhe_server_submit(srv, j1)
             t2 = fhe.fhe_server_submit(srv, j2)
-            assert fhe.fhe_server_cancel(srv, t2) == 0
+            t0 = time.time()
+            while fhe.fhe_server_poll(srv, t1, 0)[1].state == fhe.FHE_REQ_QUEUED and time.time() - t0 < 10:
+                time.sleep(0.0005)
+            assert fhe.fhe_server_cancel(srv, t2) == 0  # j2 waits for j1's memory
+            assert fhe.fhe_server_cancel(srv, t1) == -11  # admitted: runs to completion
             done, info = fhe.fhe_server_poll(srv, t2, 0)
             assert done and info.error == -10
             done, info = fhe.fhe_server_poll(srv, t1, 120000)
             assert done and info.error == 0
             assert (fhe.fhe_decrypt(ctx, sk, j1.out0[0]) == (xv < yv)).all()
             assert j2.out0[0].value is None  # nothing written
-            assert fhe.fhe_server_cancel(srv, t1) == -11
-            with pytest.raises(fhe.FheError):
-                fhe.fhe_server_cancel(srv, 987654321)
+            with pytest.raises(fhe.FheError):  # retired once reported done
+                fhe.fhe_server_cancel(srv, t1)
         finally:
             fhe.fhe_server_stop(srv)
         for h in j1.out0 + j1.out1:
