@@ -48,8 +48,8 @@ CONFIG = {
 }
 
 
-# C1 of the survey's configurations: the small ring (N = 2^12, p = 17, one
-# digit, 4 x 36-bit data primes + 1 special prime), one ciphertext pair.
+# The small ring (N = 2^12, p = 17, one digit, 4 x 36-bit data primes + 1
+# special prime), one ciphertext pair.
 U36 = 8192 * 17
 SMALL = dict(logN=12, p=17, d=1, L=4, K=1, U=U36, lo=2 ** 35, hi=2 ** 36, pairs=1, seed=1)
 
@@ -59,7 +59,7 @@ BIVARIATE = False
 
 
 def use_bivariate_workload():
-    """The C2 ring (N = 2^14, p = 131, 10 + 3 primes, 16 pairs, d = 2) with
+    """The N = 2^14, p = 131 ring (10 + 3 primes, 16 pairs, d = 2) with
     full digits: values in [0, 131^2), the bivariate circuit."""
     global METRIC, BIVARIATE
     BIVARIATE = True
@@ -455,8 +455,8 @@ def run_gpu(args):
         "batched_step_ms_p99": round(pct(sorted(step_ms), 0.99), 3),
         "p99_ms": round(pct(sorted(step_ms), 0.99), 3),
         "roofline": roof, "int_pipe": int_pipe, "kernels": kernels,
-        # the survey's secondary rates: digit comparisons (one LT+EQ of one
-        # ciphertext's digit) and limb NTTs ((N/2) log2 N butterflies each;
+        # secondary rates: digit comparisons (one LT+EQ of one ciphertext's
+        # digit) and limb NTTs ((N/2) log2 N butterflies each;
         # fused ModUp / ModDown / switch transforms included), per second of
         # the batched step
         "ciphertext_digit_comparisons_per_s": round(pairs * W["d"] * world / (ms_per_step / 1e3), 1),
@@ -989,7 +989,7 @@ def run_tournament(args):
 
 
 def run_sort(args):
-    """Sorting on the C4 ring (N = 2^15, p = 257, 20 x 50-bit + 4 special
+    """Sorting on the N = 2^15, p = 257 ring (20 x 50-bit + 4 special
     primes): 16 ciphertexts of 2 rows x 64 values (2 digits of base 129,
     10% duplicates), every row sorted on its own.  One step sorts the batch."""
     import numpy as np
@@ -1176,7 +1176,7 @@ def run_compact(args):
 
 
 def run_extract(args):
-    """Server-side digit extraction on the C2 ring (N = 2^14, p = 131, 10 x
+    """Server-side digit extraction on the N = 2^14, p = 131 ring (10 x
     50-bit + 3 special primes; slots F_{131^2}): 16 operand pairs, each
     operand ONE ciphertext whose slots hold 2-digit values (base 66) as
     F_{131^2} elements.  One step extracts the digits of both operands (one
@@ -1272,8 +1272,8 @@ def run_extract(args):
 
 
 def run_query(args):
-    """Private query with non-blocking comparison on the C2 ring (N = 2^14,
-    p = 131, 10 x 50-bit + 3 special primes): one ciphertext each of query
+    """Private query with non-blocking comparison on the N = 2^14, p = 131
+    ring (10 x 50-bit + 3 special primes): one ciphertext each of query
     type, data and operand (2 slots); answer = sum over {data + op1, data *
     op1, data^4} of candidate * EQ(type, code).  One step = one query.  The
     latency with the comparison branch overlapping the arithmetic (dependency
