@@ -1242,6 +1242,53 @@ def run_extract(args):
 
     t_p, _, _ = timed(client_digits)
     t_e, launches, clk = timed(with_extract)
+
+    # end to end: the operands arrive from pinned host memory every step (one
+    # F_(131^2) ciphertext per operand, or d digit ciphertexts), LT goes back
+    def pinned_images(handles):
+        out = []
+        for h in handles:
+            a = fhe.fhe_ct_export_coeff(ctx, h)
+            pin = torch.empty(a.shape, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+            pin[...] = a
+            out.append(pin)
+        return out
+
+    lt_host = {}
+
+    def e2e(handles, compute):
+        imgs = pinned_images(handles)
+
+        def step():
+            for h, a in zip(handles, imgs):
+                fhe._check(fhe.lib().fhe_ct_load_coeff(ctx, h, fhe._ptr(a)), ctx)
+            lt = compute()
+            shape = fhe.fhe_ct_shape(lt) + (2 ** 14,)
+            if lt_host.get("shape") != shape:  # sized from the result, once
+                lt_host["shape"] = shape
+                lt_host["buf"] = torch.empty(shape, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+            fhe._check(fhe.lib().fhe_ct_export_coeff(ctx, lt, fhe._ptr(lt_host["buf"])), ctx)
+            fhe.fhe_ct_destroy(lt)
+
+        step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        return {"value": round(count * ns * args.steps / dt, 1), "unit": "slot-comparisons/s",
+                "h2d_bytes_per_step": sum(a.nbytes for a in imgs), "d2h_bytes_per_step": lt_host["buf"].nbytes}
+
+    def lt_extracted():
+        dx, dy = fhe.fhe_extract_digits(ctx, evk, cx, d), fhe.fhe_extract_digits(ctx, evk, cy, d)
+        lt = fhe.fhe_compare_lt(ctx, evk, dx, dy)
+        for h in dx + dy:
+            fhe.fhe_ct_destroy(h)
+        return lt
+
+    e2e_ext = e2e([cx, cy], lt_extracted)
+    e2e_cli = e2e(px + py, lambda: fhe.fhe_compare_lt(ctx, evk, px, py))
     cmp_per_step = count * ns
     ct_bytes = 2 * 10 * 2 ** 14 * 8 * count  # one operand's ciphertexts at the top level
     line = {
@@ -1260,7 +1307,9 @@ def run_extract(args):
         "digits_from_client": {"value": round(cmp_per_step * args.steps / (t_p / 1e3), 1),
                                "unit": "slot-comparisons/s", "ms_per_step": round(t_p / args.steps, 2)},
         "extract_ms_per_step": round((t_e - t_p) / args.steps, 2),
-        "gpu_launches": launches, "clocks": clk, "cpu_baseline": None, "roofline": None, "e2e": None,
+        "gpu_launches": launches, "clocks": clk, "cpu_baseline": None, "roofline": None,
+        "e2e": dict(e2e_ext, note="LT only; operands uploaded from pinned host memory every step"),
+        "e2e_digits_from_client": e2e_cli,
     }
     for h in [cx, cy] + px + py:
         fhe.fhe_ct_destroy(h)
