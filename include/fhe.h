@@ -607,12 +607,14 @@ int fhe_mod_switch_noalloc(fhe_ctx *ctx, const uint64_t *in, uint64_t *out, int 
  * 0 runs them as two kernels with n1 = ceil(n/2), variant 1 as two kernels
  * with the other split (n = 11..15), variant 2 as one kernel in which a
  * thread-block cluster holds each limb and exchanges the half-transformed
- * limb through distributed shared memory (square splits: n = 10, 12, 14).
+ * limb through distributed shared memory (square splits: n = 10, 12, 14),
+ * variant 3 as variant 0 with 8 elements per thread instead of 16 (twice the
+ * threads, for launches too small to fill the SMs; n = 12..15).
  * fhe_ctx_create times the variants on a representative batch and keeps
  * variant 0 unless another is at least 3% faster; fhe_ctx_autotune(ctx,
  * njobs) re-times them on njobs limbs.  Both return the chosen variant.
  * fhe_ctx_ntt_variant(ctx, set, ms): set >= 0 forces a variant (FHE_EINVAL if
- * it does not exist for this N; set < 0 only reads); ms[3] (may be NULL)
+ * it does not exist for this N; set < 0 only reads); ms[4] (may be NULL)
  * receives the last timings in milliseconds (0 for variants that do not
  * exist).  All variants give identical results.
  * The environment variable FHE_NTT_VARIANT (a digit) pins the variant for

@@ -197,7 +197,7 @@ struct fhe_ctx {
     std::map<int, std::shared_ptr<ExtTables>> ext;  // F_{p^d} slot tables by d (built on first use)
 
     int ntt_variant = 0;        // NTT factorisation chosen by the autotuner
-    float ntt_ms[3] = {0, 0, 0};  // timings of each variant (forward + inverse, per batch; 0 = n/a)
+    float ntt_ms[4] = {0, 0, 0, 0};  // timings of each variant (forward + inverse, per batch; 0 = n/a)
 
     cudaStream_t stream = 0;
     Pool pool;
@@ -374,7 +374,7 @@ void launch_muladd(fhe_ctx *c, const u64 *a, const u64 *b, const u64 *cc, u64 *o
 void launch_ksk_digit(fhe_ctx *c, const u64 *a, const u64 *e, const u64 *s, const u64 *sp, u64 *k0, u64 *k1, int dlo,
                       int dhi, const u64 *Pw, const u64 *Pws);
 bool ntt_supported_logn(int logN);
-#define FHE_NTT_VARIANTS 3
+#define FHE_NTT_VARIANTS 4
 bool ntt_variant_ok(int logN, int v);
 int ntt_autotune(fhe_ctx *c, int njobs, float *ms_out);
 // out = sum_{t<n} w[t] x[t], n <= 8, every x[t] an [outer][level][N] batch

@@ -114,6 +114,12 @@ __device__ __forceinline__ void inv_round(u64 (&x)[1 << R], int s0, int hi, TW W
 #define FHE_NTT_THREADS_PER_SM 768
 #endif
 #define FHE_MINB(T) (FHE_NTT_THREADS_PER_SM / (T) > 0 ? FHE_NTT_THREADS_PER_SM / (T) : 1)
+// The 8-elements-per-thread kernels exist to put more warps on each SM, so
+// they are capped for 1024 resident threads (64 registers a thread).
+#ifndef FHE_NTT8_THREADS_PER_SM
+#define FHE_NTT8_THREADS_PER_SM 1024
+#endif
+#define FHE_MINB_V(T, V) ((V) == 8 ? (FHE_NTT8_THREADS_PER_SM / (T) > 0 ? FHE_NTT8_THREADS_PER_SM / (T) : 1) : FHE_MINB(T))
 
 // Shared-memory twiddle tables: entry k at k + k / 8 (one 16-byte pad per 8
 // entries), so that the second round's strided twiddle reads (stride up to 8
@@ -203,16 +209,124 @@ __device__ __forceinline__ void sub16(u64 *sm, int tid, TW W, int S, int hi0, in
     }
 }
 
+// The same 16 sub-transforms with 8 elements per thread (twice the threads,
+// for launches too small to fill the SMs): round A holds e = k G + g (k < 8,
+// G = 2^M / 8) for local stages 0..2; round B holds, of block b (G
+// contiguous elements, 8 per sub-transform), the elements b G + h + j PT
+// (j < 8, PT = G / 8 threads per block, h < PT) for local stages 3..5 in
+// registers and the remaining M - 6 stages across the PT lanes of a block
+// (lanes h and h ^ delta, one 64-bit shuffle per element).  Same butterflies,
+// same order per element: the results are identical to sub16's.
+template <int M>
+struct Sub8 {
+    static constexpr int SZ = 1 << M;       // elements per sub-transform
+    static constexpr int G = SZ / 8;        // threads per sub-transform
+    static constexpr int T = 16 * G;        // threads per CTA
+    static constexpr int R2 = M - 3;        // stages of round B
+    static constexpr int PT = G / 8;        // lanes per block in round B
+    static constexpr int P = Sub<M>::P;     // padded stride (same layout as Sub)
+    static constexpr int WORDS = Sub<M>::WORDS;
+    static_assert(M >= 6 && M <= 8, "8-element sub-transforms need 64 <= 2^M <= 256");
+    __device__ static int at(int c, int e) { return Sub<M>::at(c, e); }
+};
+
+template <int M, int V>
+struct SubSel {
+    using type = Sub<M>;
+};
+template <int M>
+struct SubSel<M, 8> {
+    using type = Sub8<M>;
+};
+
+// Block-local stage R >= 3 of round B across lanes h and h ^ delta.
+template <int M, bool FWD, int R, class TW>
+__device__ __forceinline__ void sub8_cross(u64 (&x)[8], int h, int hb, TW W, int S, u64 q, u64 q2)
+{
+    constexpr int PT = Sub8<M>::PT, DELTA = PT >> (R - 2);
+    const bool lower = (h & DELTA) == 0;
+    const int tg0 = (h << (R - 3)) / PT;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const ulonglong2 w = W.get(S + 3 + R, (hb << R) + j * (1 << (R - 3)) + tg0);
+        const u64 other = __shfl_xor_sync(0xffffffffu, x[j], DELTA);
+        const u64 a = lower ? x[j] : other, b = lower ? other : x[j];
+        if (FWD) {
+            const u64 t = shoup_lazy(b, w.x, w.y, q);
+            x[j] = lower ? a + t : a - t + q2;
+        } else {
+            u64 s2 = a + b;
+            s2 = s2 >= q2 ? s2 - q2 : s2;
+            x[j] = lower ? s2 : shoup_lazy(a - b + q2, w.x, w.y, q);
+        }
+    }
+}
+
+template <int M, bool FWD, class TW>
+__device__ __forceinline__ void sub8(u64 *sm, int tid, TW W, int S, int hi0, int hstep, u64 q, u64 q2)
+{
+    using C = Sub8<M>;
+    constexpr int G = C::G, R2 = C::R2, PT = C::PT;
+    auto roundA = [&]() {
+        const int c = tid & 15, g = tid >> 4;
+        const int hi = hi0 + c * hstep;
+        u64 x[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[k] = sm[C::at(c, k * G + g)];
+        if (FWD)
+            fwd_round<3>(x, S, hi, W, q, q2);
+        else
+            inv_round<3>(x, S, hi, W, q, q2);
+#pragma unroll
+        for (int k = 0; k < 8; k++) sm[C::at(c, k * G + g)] = x[k];
+    };
+    auto roundB = [&]() {
+        const int c = tid / G, gp = tid % G, b = gp / PT, h = gp % PT;
+        const int hb = (hi0 + c * hstep) * 8 + b;
+        u64 x[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) x[j] = sm[C::at(c, b * G + h + j * PT)];
+        if (FWD) {
+            fwd_round<3>(x, S + 3, hb, W, q, q2);
+            if constexpr (R2 > 3) sub8_cross<M, true, 3>(x, h, hb, W, S, q, q2);
+            if constexpr (R2 > 4) sub8_cross<M, true, 4>(x, h, hb, W, S, q, q2);
+        } else {
+            if constexpr (R2 > 4) sub8_cross<M, false, 4>(x, h, hb, W, S, q, q2);
+            if constexpr (R2 > 3) sub8_cross<M, false, 3>(x, h, hb, W, S, q, q2);
+            inv_round<3>(x, S + 3, hb, W, q, q2);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++) sm[C::at(c, b * G + h + j * PT)] = x[j];
+    };
+    if (FWD) {
+        roundA();
+        __syncthreads();
+        roundB();
+    } else {
+        roundB();
+        __syncthreads();
+        roundA();
+    }
+}
+
+template <int M, int V, bool FWD, class TW>
+__device__ __forceinline__ void subtx(u64 *sm, int tid, TW W, int S, int hi0, int hstep, u64 q, u64 q2)
+{
+    if constexpr (V == 16)
+        sub16<M, FWD>(sm, tid, W, S, hi0, hstep, q, q2);
+    else
+        sub8<M, FWD>(sm, tid, W, S, hi0, hstep, q, q2);
+}
+
 // Moves a CTA's 16 x 2^M words into shared memory: word r (r = tid + k T)
 // is read by src(r) and written by dst(r, v).  Staged in chunks of CH: the
 // chunk's reads are all issued before its first write (the compiler does not
 // reorder a global read past a shared-memory write on its own), so they
 // overlap; CH = 0 keeps read/write pairs (better for loads that already hold
 // several reads each, like ModUp's basis conversion).
-template <int M, int CH = 16, class Src, class Dst>
+template <class C, int CH = 16, class Src, class Dst>
 __device__ __forceinline__ void tile_in(int tid, Src src, Dst dst)
 {
-    using C = Sub<M>;
     constexpr int IT = 16 * C::SZ / C::T;
     if constexpr (CH > 0) {
         constexpr int K = CH < IT ? CH : IT;
@@ -234,10 +348,9 @@ __device__ __forceinline__ void tile_in(int tid, Src src, Dst dst)
 // store reads (IO::NPRE per word) are loaded for a chunk of words before
 // any of the chunk's writes, so those loads overlap (otherwise every write
 // to global memory would order the next word's reads behind it).
-template <int M, class IO, class StF, class Idx, class Val>
+template <class C, class IO, class StF, class Idx, class Val>
 __device__ __forceinline__ void tile_out(const IO &io, int tid, StF st, Idx idx, Val val)
 {
-    using C = Sub<M>;
     constexpr int IT = 16 * C::SZ / C::T;
     if constexpr (IO::NPRE > 0) {
         constexpr int CH = IO::NPRE == 1 ? IT : IT / 2;
@@ -279,27 +392,28 @@ struct RowTw {
 // ---------------------------------------------------------------------------
 
 // Forward, columns: global stages 0..N1-1 on columns lo0..lo0+15.
-template <int N1, int N2, class IO>
-__global__ void __launch_bounds__(Sub<N1>::T, FHE_MINB(Sub<N1>::T))
+template <int N1, int N2, class IO, int V = 16>
+__global__ void __launch_bounds__(SubSel<N1, V>::type::T, FHE_MINB_V((SubSel<N1, V>::type::T), V))
     k_fwd_cols(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
 {
-    using C = Sub<N1>;
+    using C = typename SubSel<N1, V>::type;
     constexpr int NN = 1 << (N1 + N2), BLK = (1 << N2) / 16;
     __shared__ u64 sm[C::WORDS];
     __shared__ ulonglong2 W[twp_size(1 << N1)];  // stages 0..N1-1 use only the table's prefix
     const int job = blockIdx.x / BLK, lo0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
     const typename IO::St st = io.begin(job, NN);
     const u64 q = mq[st.prime].q, q2 = 2 * q;
-    // one twiddle per thread (T = 2^N1), loaded before the tile and stored
-    // after it, so that its latency overlaps the tile's loads
-    static_assert(C::T == (1 << N1), "one twiddle per thread");
-    const ulonglong2 wv = __ldg(tw + (size_t)st.prime * NN + tid);
-    tile_in<N1, IO::LDCH>(
+    // at most one twiddle per thread (T >= 2^N1), loaded before the tile and
+    // stored after it, so that its latency overlaps the tile's loads
+    static_assert(C::T >= (1 << N1), "one twiddle per thread");
+    const bool has_w = tid < (1 << N1);
+    const ulonglong2 wv = has_w ? __ldg(tw + (size_t)st.prime * NN + tid) : make_ulonglong2(0, 0);
+    tile_in<C, IO::LDCH>(
         tid, [&](int r) { return io.load(st, ((r >> 4) << N2) + lo0 + (r & 15)); },
         [&](int r, u64 v) { sm[C::at(r & 15, r >> 4)] = v; });
-    W[twp(tid)] = wv;
+    if (has_w) W[twp(tid)] = wv;
     __syncthreads();
-    sub16<N1, true>(sm, tid, PrefixTw{W}, 0, 0, 0, q, q2);
+    subtx<N1, V, true>(sm, tid, PrefixTw{W}, 0, 0, 0, q, q2);
     __syncthreads();
     u64 *mid = io.inter(st);
     for (int r = tid; r < 16 * C::SZ; r += C::T) {
@@ -309,11 +423,11 @@ __global__ void __launch_bounds__(Sub<N1>::T, FHE_MINB(Sub<N1>::T))
 }
 
 // Forward, rows: global stages N1..N1+N2-1 on rows hi0..hi0+15.
-template <int N1, int N2, class IO>
-__global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
+template <int N1, int N2, class IO, int V = 16>
+__global__ void __launch_bounds__(SubSel<N2, V>::type::T, FHE_MINB_V((SubSel<N2, V>::type::T), V))
     k_fwd_rows(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
 {
-    using C = Sub<N2>;
+    using C = typename SubSel<N2, V>::type;
     constexpr int NN = 1 << (N1 + N2), BLK = (1 << N1) / 16;
     __shared__ u64 sm[C::WORDS];
     const int job = blockIdx.x / BLK, hi0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
@@ -321,33 +435,33 @@ __global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
     const u64 q = mq[st.prime].q, q2 = 2 * q;
     const GTw W{tw + (size_t)st.prime * NN};
     const u64 *mid = io.inter(st) + ((size_t)hi0 << N2);
-    tile_in<N2>(tid, [&](int r) { return mid[r]; }, [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
+    tile_in<C>(tid, [&](int r) { return mid[r]; }, [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
     __syncthreads();
-    sub16<N2, true>(sm, tid, W, N1, hi0, 1, q, q2);
+    subtx<N2, V, true>(sm, tid, W, N1, hi0, 1, q, q2);
     __syncthreads();
     const ModQ mqp = mq[st.prime];
-    tile_out<N2>(
+    tile_out<C>(
         io, tid, [&](int) -> const typename IO::St & { return st; }, [&](int r) { return (hi0 << N2) + r; },
         [&](int r) { return reduce64(sm[C::at(r >> N2, r & (C::SZ - 1))], mqp); });
 }
 
 // Inverse, rows first: undoes global stages N1+N2-1..N1.
-template <int N1, int N2, class IO>
-__global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
+template <int N1, int N2, class IO, int V = 16>
+__global__ void __launch_bounds__(SubSel<N2, V>::type::T, FHE_MINB_V((SubSel<N2, V>::type::T), V))
     k_inv_rows(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
 {
-    using C = Sub<N2>;
+    using C = typename SubSel<N2, V>::type;
     constexpr int NN = 1 << (N1 + N2), BLK = (1 << N1) / 16;
     __shared__ u64 sm[C::WORDS];
     const int job = blockIdx.x / BLK, hi0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
     const typename IO::St st = io.begin(job, NN);
     const u64 q = mq[st.prime].q, q2 = 2 * q;
     const GTw W{tw + (size_t)st.prime * NN};
-    tile_in<N2>(
+    tile_in<C>(
         tid, [&](int r) { return io.load(st, (hi0 << N2) + r); },
         [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
     __syncthreads();
-    sub16<N2, false>(sm, tid, W, N1, hi0, 1, q, q2);
+    subtx<N2, V, false>(sm, tid, W, N1, hi0, 1, q, q2);
     __syncthreads();
     u64 *mid = io.inter(st) + ((size_t)hi0 << N2);
     for (int r = tid; r < 16 * C::SZ; r += C::T) mid[r] = sm[C::at(r >> N2, r & (C::SZ - 1))];
@@ -357,11 +471,11 @@ __global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
 // `groups` x 16 such jobs per residue class of j mod stride.  CTA
 // (group g, row hi): sub-transform c is row hi of job base + (16 kb + c) stride
 // with base = g % stride, kb = g / stride.
-template <int N1, int N2, class IO>
-__global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
+template <int N1, int N2, class IO, int V = 16>
+__global__ void __launch_bounds__(SubSel<N2, V>::type::T, FHE_MINB_V((SubSel<N2, V>::type::T), V))
     k_fwd_rows_grp(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw, int stride)
 {
-    using C = Sub<N2>;
+    using C = typename SubSel<N2, V>::type;
     constexpr int NN = 1 << (N1 + N2), ROWS = 1 << N1;
     __shared__ u64 sm[C::WORDS];
     __shared__ ulonglong2 tws[twp_size((1 << N2) - 1)];
@@ -383,24 +497,24 @@ __global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
         const int u = 31 - __clz(tid + 1);  // stage of entry tid
         wv = __ldg(W + (1 << (N1 + u)) + (hi << u) + (tid + 1 - (1 << u)));
     }
-    tile_in<N2>(
+    tile_in<C>(
         tid, [&](int r) { return io.inter(sts[r >> N2])[(hi << N2) + (r & (C::SZ - 1))]; },
         [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
     if (has_w) tws[twp(tid)] = wv;
     __syncthreads();
-    sub16<N2, true>(sm, tid, RowTw{tws, N1, hi}, N1, hi, 0, q, q2);
+    subtx<N2, V, true>(sm, tid, RowTw{tws, N1, hi}, N1, hi, 0, q, q2);
     __syncthreads();
-    tile_out<N2>(
+    tile_out<C>(
         io, tid, [&](int r) -> const typename IO::St & { return sts[r >> N2]; },
         [&](int r) { return (hi << N2) + (r & (C::SZ - 1)); },
         [&](int r) { return reduce64(sm[C::at(r >> N2, r & (C::SZ - 1))], mqp); });
 }
 
-template <int N1, int N2, class IO>
-__global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
+template <int N1, int N2, class IO, int V = 16>
+__global__ void __launch_bounds__(SubSel<N2, V>::type::T, FHE_MINB_V((SubSel<N2, V>::type::T), V))
     k_inv_rows_grp(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw, int stride)
 {
-    using C = Sub<N2>;
+    using C = typename SubSel<N2, V>::type;
     constexpr int NN = 1 << (N1 + N2), ROWS = 1 << N1;
     __shared__ u64 sm[C::WORDS];
     __shared__ ulonglong2 tws[twp_size((1 << N2) - 1)];
@@ -419,12 +533,12 @@ __global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
         const int u = 31 - __clz(tid + 1);
         wv = __ldg(W + (1 << (N1 + u)) + (hi << u) + (tid + 1 - (1 << u)));
     }
-    tile_in<N2>(
+    tile_in<C>(
         tid, [&](int r) { return io.load(sts[r >> N2], (hi << N2) + (r & (C::SZ - 1))); },
         [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
     if (has_w) tws[twp(tid)] = wv;
     __syncthreads();
-    sub16<N2, false>(sm, tid, RowTw{tws, N1, hi}, N1, hi, 0, q, q2);
+    subtx<N2, V, false>(sm, tid, RowTw{tws, N1, hi}, N1, hi, 0, q, q2);
     __syncthreads();
     for (int r = tid; r < 16 * C::SZ; r += C::T) {
         const int c = r >> N2, f = r & (C::SZ - 1);
@@ -433,28 +547,29 @@ __global__ void __launch_bounds__(Sub<N2>::T, FHE_MINB(Sub<N2>::T))
 }
 
 // Inverse, columns: undoes global stages N1-1..0, then scales by N^-1.
-template <int N1, int N2, class IO>
-__global__ void __launch_bounds__(Sub<N1>::T, FHE_MINB(Sub<N1>::T))
+template <int N1, int N2, class IO, int V = 16>
+__global__ void __launch_bounds__(SubSel<N1, V>::type::T, FHE_MINB_V((SubSel<N1, V>::type::T), V))
     k_inv_cols(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw,
                const ulonglong2 *__restrict__ ninv)
 {
-    using C = Sub<N1>;
+    using C = typename SubSel<N1, V>::type;
     constexpr int NN = 1 << (N1 + N2), BLK = (1 << N2) / 16;
     __shared__ u64 sm[C::WORDS];
     __shared__ ulonglong2 W[twp_size(1 << N1)];
     const int job = blockIdx.x / BLK, lo0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
     const typename IO::St st = io.begin(job, NN);
     const u64 q = mq[st.prime].q, q2 = 2 * q;
-    static_assert(C::T == (1 << N1), "one twiddle per thread");
-    const ulonglong2 wv = __ldg(tw + (size_t)st.prime * NN + tid);  // stored after the tile (latency overlap)
+    static_assert(C::T >= (1 << N1), "one twiddle per thread");
+    const bool has_w = tid < (1 << N1);  // stored after the tile (latency overlap)
+    const ulonglong2 wv = has_w ? __ldg(tw + (size_t)st.prime * NN + tid) : make_ulonglong2(0, 0);
     const ulonglong2 ni = io.final_scale(st, ninv);
     const u64 *mid = io.inter(st);
-    tile_in<N1>(
+    tile_in<C>(
         tid, [&](int r) { return mid[((r >> 4) << N2) + lo0 + (r & 15)]; },
         [&](int r, u64 v) { sm[C::at(r & 15, r >> 4)] = v; });
-    W[twp(tid)] = wv;
+    if (has_w) W[twp(tid)] = wv;
     __syncthreads();
-    sub16<N1, false>(sm, tid, PrefixTw{W}, 0, 0, 0, q, q2);
+    subtx<N1, V, false>(sm, tid, PrefixTw{W}, 0, 0, 0, q, q2);
     __syncthreads();
     for (int r = tid; r < 16 * C::SZ; r += C::T) {
         const int c = r & 15, e = r >> 4;
@@ -887,7 +1002,7 @@ __global__ void __cluster_dims__((1 << M) / 16, 1, 1) __launch_bounds__(Sub<M>::
     const typename IO::St st = io.begin(job, NN);
     const u64 q = mq[st.prime].q, q2 = 2 * q;
     for (int r = tid; r < (1 << M); r += C::T) W[twp(r)] = tw[(size_t)st.prime * NN + r];
-    tile_in<M, IO::LDCH>(
+    tile_in<C, IO::LDCH>(
         tid, [&](int r) { return io.load(st, ((r >> 4) << M) + lo0 + (r & 15)); },
         [&](int r, u64 v) { sm[C::at(r & 15, r >> 4)] = v; });
     __syncthreads();
@@ -903,7 +1018,7 @@ __global__ void __cluster_dims__((1 << M) / 16, 1, 1) __launch_bounds__(Sub<M>::
     sub16<M, true>(sm2, tid, GTw{tw + (size_t)st.prime * NN}, M, hi0, 1, q, q2);
     __syncthreads();
     const ModQ mqp = mq[st.prime];
-    tile_out<M>(
+    tile_out<C>(
         io, tid, [&](int) -> const typename IO::St & { return st; }, [&](int r) { return (hi0 << M) + r; },
         [&](int r) { return reduce64(sm2[C::at(r >> M, r & (C::SZ - 1))], mqp); });
 }
@@ -926,7 +1041,7 @@ __global__ void __cluster_dims__((1 << M) / 16, 1, 1) __launch_bounds__(Sub<M>::
     const u64 q = mq[st.prime].q, q2 = 2 * q;
     for (int r = tid; r < (1 << M); r += C::T) W[twp(r)] = tw[(size_t)st.prime * NN + r];
     const ulonglong2 ni = io.final_scale(st, ninv);
-    tile_in<M>(
+    tile_in<C>(
         tid, [&](int r) { return io.load(st, (hi0 << M) + r); },
         [&](int r, u64 v) { sm[C::at(r >> M, r & (C::SZ - 1))] = v; });
     __syncthreads();
@@ -969,32 +1084,34 @@ bool groupable(const IO &io, int njobs)
     return st > 0 && njobs % st == 0 && (njobs / st) % 16 == 0;
 }
 
-template <int N1, int N2, class IO>
+template <int N1, int N2, class IO, int V = 16>
 void fwd_pair(fhe_ctx *c, const IO &io, int njobs)
 {
-    k_fwd_cols<N1, N2, IO><<<njobs * ((1 << N2) / 16), Sub<N1>::T, 0, c->stream>>>(io, c->d_mq, c->d_fwd);
+    constexpr int T1 = SubSel<N1, V>::type::T, T2 = SubSel<N2, V>::type::T;
+    k_fwd_cols<N1, N2, IO, V><<<njobs * ((1 << N2) / 16), T1, 0, c->stream>>>(io, c->d_mq, c->d_fwd);
     if (groupable(io, njobs))
-        k_fwd_rows_grp<N1, N2, IO><<<(njobs / 16) * (1 << N1), Sub<N2>::T, 0, c->stream>>>(io, c->d_mq, c->d_fwd,
-                                                                                             io.prime_stride());
+        k_fwd_rows_grp<N1, N2, IO, V><<<(njobs / 16) * (1 << N1), T2, 0, c->stream>>>(io, c->d_mq, c->d_fwd,
+                                                                                      io.prime_stride());
     else
-        k_fwd_rows<N1, N2, IO><<<njobs * ((1 << N1) / 16), Sub<N2>::T, 0, c->stream>>>(io, c->d_mq, c->d_fwd);
+        k_fwd_rows<N1, N2, IO, V><<<njobs * ((1 << N1) / 16), T2, 0, c->stream>>>(io, c->d_mq, c->d_fwd);
 }
 
-template <int N1, int N2, class IO>
+template <int N1, int N2, class IO, int V = 16>
 void inv_pair(fhe_ctx *c, const IO &io, int njobs)
 {
+    constexpr int T1 = SubSel<N1, V>::type::T, T2 = SubSel<N2, V>::type::T;
     if (groupable(io, njobs))
-        k_inv_rows_grp<N1, N2, IO><<<(njobs / 16) * (1 << N1), Sub<N2>::T, 0, c->stream>>>(io, c->d_mq, c->d_inv,
-                                                                                             io.prime_stride());
+        k_inv_rows_grp<N1, N2, IO, V><<<(njobs / 16) * (1 << N1), T2, 0, c->stream>>>(io, c->d_mq, c->d_inv,
+                                                                                      io.prime_stride());
     else
-        k_inv_rows<N1, N2, IO><<<njobs * ((1 << N1) / 16), Sub<N2>::T, 0, c->stream>>>(io, c->d_mq, c->d_inv);
-    k_inv_cols<N1, N2, IO><<<njobs * ((1 << N2) / 16), Sub<N1>::T, 0, c->stream>>>(io, c->d_mq, c->d_inv,
-                                                                                    c->d_ninv);
+        k_inv_rows<N1, N2, IO, V><<<njobs * ((1 << N1) / 16), T2, 0, c->stream>>>(io, c->d_mq, c->d_inv);
+    k_inv_cols<N1, N2, IO, V><<<njobs * ((1 << N2) / 16), T1, 0, c->stream>>>(io, c->d_mq, c->d_inv, c->d_ninv);
 }
 
 // Factorisations N = 2^n1 x 2^n2 per ring degree (the autotuner picks one
 // per context; all compute the same transform): variant 0 and 1 are the two
-// two-kernel splits, variant 2 the one-launch cluster form of a square split.
+// two-kernel splits, variant 2 the one-launch cluster form of a square split,
+// variant 3 variant 0's split with 8 elements per thread (twice the warps).
 // Returns the number of kernels launched.
 template <class IO>
 int fwd_dispatch(fhe_ctx *c, const IO &io, int njobs)
@@ -1005,11 +1122,15 @@ int fwd_dispatch(fhe_ctx *c, const IO &io, int njobs)
         fwd_pair<5, 5>(c, io, njobs); return 2;
     case 11: v ? fwd_pair<5, 6>(c, io, njobs) : fwd_pair<6, 5>(c, io, njobs); return 2;
     case 12: if (v == 2) return fwd_fused<6>(c, io, njobs), 1;
+        if (v == 3) return fwd_pair<6, 6, IO, 8>(c, io, njobs), 2;
         v ? fwd_pair<7, 5>(c, io, njobs) : fwd_pair<6, 6>(c, io, njobs); return 2;
-    case 13: v ? fwd_pair<6, 7>(c, io, njobs) : fwd_pair<7, 6>(c, io, njobs); return 2;
+    case 13: if (v == 3) return fwd_pair<7, 6, IO, 8>(c, io, njobs), 2;
+        v ? fwd_pair<6, 7>(c, io, njobs) : fwd_pair<7, 6>(c, io, njobs); return 2;
     case 14: if (v == 2) return fwd_fused<7>(c, io, njobs), 1;
+        if (v == 3) return fwd_pair<7, 7, IO, 8>(c, io, njobs), 2;
         v ? fwd_pair<8, 6>(c, io, njobs) : fwd_pair<7, 7>(c, io, njobs); return 2;
-    case 15: v ? fwd_pair<7, 8>(c, io, njobs) : fwd_pair<8, 7>(c, io, njobs); return 2;
+    case 15: if (v == 3) return fwd_pair<8, 7, IO, 8>(c, io, njobs), 2;
+        v ? fwd_pair<7, 8>(c, io, njobs) : fwd_pair<8, 7>(c, io, njobs); return 2;
     default: return 0;
     }
 }
@@ -1023,11 +1144,15 @@ int inv_dispatch(fhe_ctx *c, const IO &io, int njobs)
         inv_pair<5, 5>(c, io, njobs); return 2;
     case 11: v ? inv_pair<5, 6>(c, io, njobs) : inv_pair<6, 5>(c, io, njobs); return 2;
     case 12: if (v == 2) return inv_fused<6>(c, io, njobs), 1;
+        if (v == 3) return inv_pair<6, 6, IO, 8>(c, io, njobs), 2;
         v ? inv_pair<7, 5>(c, io, njobs) : inv_pair<6, 6>(c, io, njobs); return 2;
-    case 13: v ? inv_pair<6, 7>(c, io, njobs) : inv_pair<7, 6>(c, io, njobs); return 2;
+    case 13: if (v == 3) return inv_pair<7, 6, IO, 8>(c, io, njobs), 2;
+        v ? inv_pair<6, 7>(c, io, njobs) : inv_pair<7, 6>(c, io, njobs); return 2;
     case 14: if (v == 2) return inv_fused<7>(c, io, njobs), 1;
+        if (v == 3) return inv_pair<7, 7, IO, 8>(c, io, njobs), 2;
         v ? inv_pair<8, 6>(c, io, njobs) : inv_pair<7, 7>(c, io, njobs); return 2;
-    case 15: v ? inv_pair<7, 8>(c, io, njobs) : inv_pair<8, 7>(c, io, njobs); return 2;
+    case 15: if (v == 3) return inv_pair<8, 7, IO, 8>(c, io, njobs), 2;
+        v ? inv_pair<7, 8>(c, io, njobs) : inv_pair<8, 7>(c, io, njobs); return 2;
     default: return 0;
     }
 }
@@ -1198,6 +1323,7 @@ bool ntt_variant_ok(int logN, int v)
     if (v == 0) return true;
     if (v == 1) return logN >= 11 && logN <= 15;
     if (v == 2) return logN == 10 || logN == 12 || logN == 14;
+    if (v == 3) return logN >= 12 && logN <= 15;
     return false;
 }
 

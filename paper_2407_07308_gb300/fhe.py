@@ -856,8 +856,8 @@ def fhe_ctx_autotune(ctx, njobs: int) -> int:
 
 
 def fhe_ctx_ntt_variant(ctx, set_variant: int = -1):
-    """(chosen variant, [ms of variants 0, 1, 2]; 0 where a variant does not exist)."""
-    ms = np.zeros(3, dtype=np.float32)
+    """(chosen variant, [ms of variants 0, 1, 2, 3]; 0 where a variant does not exist)."""
+    ms = np.zeros(4, dtype=np.float32)
     v = _check(lib().fhe_ctx_ntt_variant(ctx, set_variant, _ptr(ms)), ctx)
     return v, [float(x) for x in ms]
 
