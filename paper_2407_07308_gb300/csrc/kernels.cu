@@ -92,7 +92,7 @@ __global__ void k_tensor(const u64 *__restrict__ a, const u64 *__restrict__ b, u
 // key words once and reuses them for its CB ciphertexts, whose input words
 // are all loaded before the first product so that the loads overlap.
 template <int CB>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
     k_ks_inner(const u64 *__restrict__ ext, const u64 *__restrict__ xbase, long long x_outer,
                const u64 *__restrict__ ksk, u64 *__restrict__ acc, int count, int l, int K, int L, int dnum,
                int logN, const ModQ *__restrict__ mq)
