@@ -248,7 +248,7 @@ class Clocks:
 # headline command (profiles/ntt_inverse_c2_dram.md) for the NTT source whose
 # SHA-256 starts with the given prefix; for any other source the traffic is
 # reported as null.
-DRAM_PER_ALGORITHMIC = {"ntt_inv": (1.04, "b016f63aa0547a5c")}
+DRAM_PER_ALGORITHMIC = {"ntt_inv": (1.04, "635767c87a38cfd9")}
 
 
 def traffic_for(kernel_class: str, algorithmic_bytes: float):
