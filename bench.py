@@ -42,7 +42,8 @@ UNIT = "slot-comparisons/s"
 U50 = 2 ** 16 * 17 * 131 * 257
 W = dict(logN=14, p=131, d=2, L=10, K=3, U=U50, lo=2 ** 49, hi=2 ** 50, pairs=16, seed=2)
 CONFIG = {
-    "workload": "BGV N=2^14 p=131 d=2 LT+EQ, 16 ciphertext pairs per batch, 10x50-bit + 3 special primes",
+    "workload": "BGV N=2^14 p=131 d=2 LT+EQ, univariate circuit on base-66 digits (values in [0, 4356)), "
+                "16 ciphertext pairs per batch, 10x50-bit + 3 special primes",
     "N": 2 ** 14, "p": 131, "d": 2, "slots_per_ct": 2, "pairs_per_step": 16, "data_primes": 10, "special_primes": 3,
     "l2": "inputs 168 MB > L2 (129 MB); intermediates ~10 GB per step",
 }
@@ -75,7 +76,8 @@ def use_small_workload():
     W.update(SMALL)
     METRIC = "encrypted slot-comparisons/sec at N=2^12,p=17,d=1; batched vs plain; p99 ms"
     CONFIG.clear()
-    CONFIG.update({"workload": "BGV N=2^12 p=17 d=1 LT+EQ, 1 ciphertext pair, 4x36-bit + 1 special prime",
+    CONFIG.update({"workload": "BGV N=2^12 p=17 d=1 LT+EQ, univariate circuit on base-9 digits (values in [0, 9)), "
+                               "1 ciphertext pair, 4x36-bit + 1 special prime",
                    "N": 2 ** 12, "p": 17, "d": 1, "slots_per_ct": 8, "pairs_per_step": 1, "data_primes": 4,
                    "special_primes": 1, "l2": "data fits in L2: a 256 MB buffer is written between timed steps "
                                                  "(outside the timed events)"})
@@ -182,6 +184,13 @@ class OraclePool:
         oracle.build()
         self.workers = workers
         self.pool = mp.get_context("spawn").Pool(workers, initializer=_oracle_init, initargs=(dict(W),))
+
+    @staticmethod
+    def slots():
+        """n_s of the workload's ring (slot-comparisons per ciphertext pair)."""
+        from oracle.encoding import SlotStructure
+
+        return SlotStructure(W["p"], 1 << W["logN"]).ns
 
     def sample(self, npairs):
         res = self.pool.map(_oracle_pair, list(range(npairs)), chunksize=1)
@@ -297,7 +306,8 @@ def run_gpu(args):
         op = OraclePool(workers)
         per = op.sample(npairs)
         op.close()
-        cpu = {"value": round(npairs * 2 / max(per), 4), "unit": UNIT, "cores": workers, "kind": "oracle",
+        cpu = {"value": round(npairs * OraclePool.slots() / max(per), 4), "unit": UNIT, "cores": workers,
+               "kind": "oracle",
                "sample": f"{npairs} of the {W['pairs']} pairs (LT+EQ, d={W['d']}, N=2^{W['logN']}) run concurrently, "
                          f"one spawned process "
                          f"per pair; {statistics.mean(per):.1f} s per pair on average"}
@@ -564,7 +574,7 @@ def run_reference(args):
         walls.append(max(op.sample(npairs)))
     op.close()
     total = sum(walls)
-    value = npairs * 2 * args.steps / total
+    value = npairs * OraclePool.slots() * args.steps / total
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 1),

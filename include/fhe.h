@@ -594,11 +594,14 @@ int fhe_probe_bfly_peak(double *bfly_per_s);
  * with npoly 2 or 3 and 2 <= level <= L.  Its only temporary is a fixed
  * device array of 2^20 words (8 MiB) inside the library, held on every device
  * that loads the library until the process exits; count*npoly*N above 2^20
- * fails with FHE_EINVAL.  It calls no allocator.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) and should come
- * before any stream capture.  All calls share the array, so calls whose GPU
- * work overlaps (other streams or contexts on the same device) race and must
- * be serialised by the caller.  The result equals fhe_mod_switch(.., level-1). */
+ * fails with FHE_EINVAL.  It calls no allocator.  The device current at the
+ * call must be the one the context was created on (else FHE_EINVAL, before
+ * any GPU work).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and must come before any stream capture: a
+ * first call while the context's stream is capturing fails with FHE_EINVAL.
+ * All calls share the array, so calls whose GPU work overlaps (other streams
+ * or contexts on the same device) race and must be serialised by the caller.
+ * The result equals fhe_mod_switch(.., level-1). */
 int fhe_mod_switch_noalloc(fhe_ctx *ctx, const uint64_t *in, uint64_t *out, int count, int npoly, int level);
 
 /* ---- NTT autotuning ------------------------------------------------------------ */

@@ -5,7 +5,7 @@ published definition.
 TEST INFRASTRUCTURE ONLY (see the package docstring).  Used to check the
 library's device generator word for word; the known-answer vectors of the
 generator's reference distribution pin this implementation
-(tests/test_oracle_philox.py).
+(tests/test_oracle_tournament.py, test_philox_known_answers).
 
 One round maps (c0, c1, c2, c3) with key (k0, k1) to
   (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),

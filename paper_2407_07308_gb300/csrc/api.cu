@@ -339,6 +339,7 @@ extern "C" int fhe_ctx_create(const fhe_params *P, const fhe_allocator *alloc, v
     c->np = P->L + P->K;
     c->p = P->p;
     c->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess) c->device = -1;
     c->q.resize(c->np);
     if (host_find_primes(P->prime_mod, P->prime_lo, P->prime_hi, c->np, c->q.data()) != c->np) {
         delete c;

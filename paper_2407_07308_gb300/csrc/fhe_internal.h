@@ -200,6 +200,7 @@ struct fhe_ctx {
     float ntt_ms[4] = {0, 0, 0, 0};  // timings of each variant (forward + inverse, per batch; 0 = n/a)
 
     cudaStream_t stream = 0;
+    int device = -1;  // the device current when the context was created
     Pool pool;
     std::string err;
     std::mutex mu;

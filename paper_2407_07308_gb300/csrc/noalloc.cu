@@ -23,14 +23,17 @@
 static __device__ __align__(256) uint64_t g_noalloc_scratch[FHE_NOALLOC_SCRATCH_WORDS];
 
 // Device address of the scratch array, looked up once per device with that
-// device current (the host-side symbol is only a stand-in for it).
-static int scratch_address(int dev, u64 **out)
+// device current (the host-side symbol is only a stand-in for it).  The
+// lookup may load the library's module on that device, which a stream under
+// capture does not allow: a first call while `capturing` is refused.
+static int scratch_address(int dev, bool capturing, u64 **out)
 {
     static std::mutex mu;
     static u64 *addr[64] = {nullptr};
     if (dev < 0 || dev >= 64) return FHE_EINVAL;
     std::lock_guard<std::mutex> g(mu);
     if (!addr[dev]) {
+        if (capturing) return FHE_EINVAL;
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FHE_ECUDA;
         addr[dev] = (u64 *)p;
@@ -50,8 +53,17 @@ extern "C" int fhe_mod_switch_noalloc(fhe_ctx *c, const uint64_t *in, uint64_t *
     std::lock_guard<std::mutex> lock(c->mu);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return fhe_fail(c, FHE_ECUDA, "mod_switch_noalloc: no current device");
+    // the kernels run on the context's stream, i.e. on the context's device:
+    // the scratch address must be that device's
+    if (dev != c->device)
+        return fhe_fail(c, FHE_EINVAL, "mod_switch_noalloc: the current device is not the context's device");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cap) != cudaSuccess)
+        return fhe_fail(c, FHE_ECUDA, "mod_switch_noalloc: stream query failed");
     u64 *scratch = nullptr;
-    int e = scratch_address(dev, &scratch);
+    int e = scratch_address(dev, cap != cudaStreamCaptureStatusNone, &scratch);
+    if (e == FHE_EINVAL)
+        return fhe_fail(c, e, "mod_switch_noalloc: the first call on a device must not be made during stream capture");
     if (e) return fhe_fail(c, e, "mod_switch_noalloc: cudaGetSymbolAddress failed");
     // per-launch event timing would create events; this path creates nothing
     const bool prof = c->prof_on;

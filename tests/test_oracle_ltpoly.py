@@ -125,3 +125,21 @@ def test_lt_bivariate_by_indicator_expansion():
     assert c == want
     assert all(c[a][0] == 0 for a in range(p))
     assert c[0] == [0] * (p - 1) + [1]
+
+
+def _golden(name):
+    with open(os.path.join(HERE, "golden", name)) as f:
+        return [int(s) for s in (line.split("#")[0].strip() for line in f) if s]
+
+
+def test_lt_p17_worked_example():
+    """The hand-worked p = 17 coefficients: first checked on their own (at
+    every z in Z_17, and the structure the leading term fixes), then the
+    oracle must reproduce them exactly."""
+    want = _golden("ltpoly_p17.txt")
+    p = 17
+    assert len(want) == p
+    for z in range(p):
+        assert evaluate(want, z, p) == (1 if z >= (p + 1) // 2 else 0)
+    assert want[p - 1] == (p + 1) // 2
+    assert lt_coefficients(p) == want
