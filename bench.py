@@ -321,9 +321,10 @@ def run_gpu(args):
     ns, N, pairs = info.slots, info.N, W["pairs"]
     variant, _ = fhe.fhe_ctx_ntt_variant(ctx)
     n = W["logN"]
-    n1 = {0: (n + 1) // 2, 1: {11: 5, 12: 7, 13: 6, 14: 8, 15: 7}.get(n), 2: n // 2, 3: (n + 1) // 2}[variant]
-    split = f"2^{n1} x 2^{n - n1}, " + {2: "one cluster kernel", 3: "two kernels, 8 elements per thread"}.get(
-        variant, "two kernels, 16 elements per thread")
+    n1 = (n + 1) // 2
+    split = (f"2^{n1} x 2^{n - n1}, column and row kernels, 128-thread CTAs on 2048-residue units, "
+             + {0: "one CTA per unit", 1: "6 persistent CTAs per SM", 2: "4 persistent CTAs per SM",
+                3: "2 persistent CTAs per SM"}[variant])
     primes = fhe.fhe_ctx_primes(ctx)
     km = synth.KeyMaterial(W["seed"], primes, W["L"], W["K"], N)
     sk, pk = fhe.fhe_keygen_explicit(ctx, km.s, km.a_pk, km.e_pk)

@@ -606,20 +606,18 @@ int fhe_mod_switch_noalloc(fhe_ctx *ctx, const uint64_t *in, uint64_t *out, int 
 
 /* ---- NTT autotuning ------------------------------------------------------------ */
 
-/* The NTT splits N = 2^n1 x 2^n2 into a column pass and a row pass.  Variant
- * 0 runs them as two kernels with n1 = ceil(n/2), variant 1 as two kernels
- * with the other split (n = 11..15), variant 2 as one kernel in which a
- * thread-block cluster holds each limb and exchanges the half-transformed
- * limb through distributed shared memory (square splits: n = 10, 12, 14),
- * variant 3 as variant 0 with 8 elements per thread instead of 16 (twice the
- * threads, for launches too small to fill the SMs; n = 12..15).
- * fhe_ctx_create times the variants on a representative batch and keeps
- * variant 0 unless another is at least 3% faster; fhe_ctx_autotune(ctx,
- * njobs) re-times them on njobs limbs.  Both return the chosen variant.
+/* The NTT splits N = 2^n1 x 2^n2 (n1 = ceil(n/2)) into a column pass and a
+ * row pass, each one kernel whose CTAs (128 threads) work on units of 2048
+ * residues; one launch serves batches of any ring degree 2^10..2^15 and
+ * level.  The variant is the grid policy: variant 0 launches one CTA per
+ * unit; variants 1, 2 and 3 launch 6, 4 and 2 resident CTAs per SM that walk
+ * all units (persistent CTAs).  fhe_ctx_create times the variants on a
+ * representative batch and keeps variant 0 unless another is at least 3%
+ * faster; fhe_ctx_autotune(ctx, njobs) re-times them on njobs limbs.  Both
+ * return the chosen variant.
  * fhe_ctx_ntt_variant(ctx, set, ms): set >= 0 forces a variant (FHE_EINVAL if
- * it does not exist for this N; set < 0 only reads); ms[4] (may be NULL)
- * receives the last timings in milliseconds (0 for variants that do not
- * exist).  All variants give identical results.
+ * it does not exist; set < 0 only reads); ms[4] (may be NULL) receives the
+ * last timings in milliseconds.  All variants give identical results.
  * The environment variable FHE_NTT_VARIANT (a digit) pins the variant for
  * contexts created afterwards, skipping the timing (for profiling runs,
  * whose timings would mislead the choice).

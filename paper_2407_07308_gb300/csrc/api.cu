@@ -340,6 +340,8 @@ extern "C" int fhe_ctx_create(const fhe_params *P, const fhe_allocator *alloc, v
     c->p = P->p;
     c->stream = (cudaStream_t)stream;
     if (cudaGetDevice(&c->device) != cudaSuccess) c->device = -1;
+    if (c->device < 0 || cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        c->sms = 0;
     c->q.resize(c->np);
     if (host_find_primes(P->prime_mod, P->prime_lo, P->prime_hi, c->np, c->q.data()) != c->np) {
         delete c;
@@ -391,6 +393,11 @@ extern "C" void fhe_ctx_destroy(fhe_ctx *c)
     cudaFree(c->d_modswitch);
     cudaFree(c->d_rms);
     cudaFree(c->d_mss);
+    cudaFree(c->d_ks_xscale);
+    cudaFree(c->d_ms4scale);
+    cudaFree(c->d_ks_pscale);
+    cudaFree(c->d_ms_lastscale);
+    cudaFree(c->d_mss_scale);
     for (auto &kv : c->d_perm) cudaFree(kv.second);
     for (cudaStream_t s : c->branch_streams) cudaStreamDestroy(s);
     for (cudaEvent_t ev : c->branch_events) cudaEventDestroy(ev);

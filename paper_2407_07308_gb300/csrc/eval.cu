@@ -86,7 +86,7 @@ int op_modswitch1(fhe_ctx *c, const fhe_ct *a, fhe_ct **out)
     const int outer = a->count * a->npoly;
     // last = [x_{l-1} p^-1]_{q_{l-1}} in the coefficient domain
     LimbMap m = identity_map(1, (long long)l * N, N, l - 1, 0, l - 1);
-    launch_ntt_inv_scaled(c, a->d, last.p, m, &c->ms_lastscale[l], outer);
+    launch_ntt_inv_scaled(c, a->d, last.p, m, c->d_ms_lastscale + l, outer);
     launch_ntt_modswitch(c, last.p, a->d, r->d, l, a->npoly, a->count);
     *out = r;
     return 0;
@@ -114,7 +114,7 @@ int op_modswitch_k(fhe_ctx *c, const fhe_ct *a, int k, fhe_ct **out)
     m.in_outer = (long long)l * N;
     m.out_outer = (long long)k * N;
     for (int j = 0; j < k; j++) m.in_limb[j] = l - 1 - j, m.out_limb[j] = j, m.prime[j] = l - 1 - j;
-    launch_ntt_inv_scaled(c, a->d, src.p, m, &c->mss_scale[((size_t)l * (FHE_MAXK + 1) + k) * FHE_MAXK],
+    launch_ntt_inv_scaled(c, a->d, src.p, m, c->d_mss_scale + ((size_t)l * (FHE_MAXK + 1) + k) * FHE_MAXK,
                           outer * k);
     launch_ms_fold(c, src.p, outer, l, k);
     launch_ntt_multiswitch(c, src.p, a->d, r->d, l, k, a->npoly, a->count);
@@ -255,14 +255,14 @@ static int keyswitch(fhe_ctx *c, const u64 *xbase, long long x_outer, const u64 
     // 1. INTT of X, each limb i of digit j times (Q_j/q_i)^-1 (the first step of
     //    the basis conversion)
     LimbMap m1 = identity_map(l, x_outer, (long long)l * N, 0, 0, 0);
-    launch_ntt_inv_scaled(c, xbase, xc.p, m1, c->ks_xscale[l].data(), count * l);
+    launch_ntt_inv_scaled(c, xbase, xc.p, m1, c->d_ks_xscale + (size_t)l * FHE_MAXP, count * l);
     // 2. ModUp (basis conversion fused with NTT)
     launch_ntt_modup(c, xc.p, ext.p, l, count);
     // 3. inner product with the key
     launch_ks_inner(c, ext.p, xbase, x_outer, k.d, acc.p, count, l);
     // 4. INTT of the special limbs of both accumulators, times p^-1 (P/p_k)^-1
     LimbMap m4 = identity_map(K, (long long)(l + K) * N, (long long)K * N, l, 0, c->L);
-    launch_ntt_inv_scaled(c, acc.p, accP.p, m4, c->ks_pscale.data(), count * 2 * K);
+    launch_ntt_inv_scaled(c, acc.p, accP.p, m4, c->d_ks_pscale, count * 2 * K);
     // 5. ModDown fused with NTT, plus the addend
     launch_ntt_moddown(c, accP.p, acc.p, abase, a_outer, a_poly, amask, out, l, count);
     return 0;
@@ -283,7 +283,7 @@ static int keyswitch_ms(fhe_ctx *c, const u64 *xbase, long long x_outer, const u
     Tmp src(c, (size_t)count * 2 * (K + 1) * N, &err);
     if (err) return fhe_fail(c, err, "key switching: out of device memory");
     LimbMap m1 = identity_map(l, x_outer, (long long)l * N, 0, 0, 0);
-    launch_ntt_inv_scaled(c, xbase, xc.p, m1, c->ks_xscale[l].data(), count * l);
+    launch_ntt_inv_scaled(c, xbase, xc.p, m1, c->d_ks_xscale + (size_t)l * FHE_MAXP, count * l);
     launch_ntt_modup(c, xc.p, ext.p, l, count);
     launch_ks_inner(c, ext.p, xbase, x_outer, k.d, acc.p, count, l);
     // t_k = INTT(acc_P,k) p^-1 (P/p_k)^-1 and Y' = INTT(y) (p P)^-1 with
@@ -293,19 +293,17 @@ static int keyswitch_ms(fhe_ctx *c, const u64 *xbase, long long x_outer, const u
     m4.nl = K + 1;
     m4.in_outer = (long long)(l + K) * N;
     m4.out_outer = (long long)(K + 1) * N;
-    std::vector<ulonglong2> scale(K + 1);
     for (int j = 0; j < K; j++) {
         m4.in_limb[j] = l + j;
         m4.out_limb[j] = j;
         m4.prime[j] = c->L + j;
-        scale[j] = c->ks_pscale[j];
     }
     m4.in_limb[K] = l - 1;
     m4.out_limb[K] = K;
     m4.prime[K] = l - 1;
-    scale[K] = c->rms_yscale[l];
-    launch_ntt_inv_scaled_y(c, acc.p, src.p, m4, scale.data(), count * 2 * (K + 1), abase, a_outer, a_poly, amask,
-                            l);
+    // scales (ks_pscale[0..K-1], rms_yscale[l])
+    launch_ntt_inv_scaled_y(c, acc.p, src.p, m4, c->d_ms4scale + (size_t)l * (FHE_MAXK + 1), count * 2 * (K + 1),
+                            abase, a_outer, a_poly, amask, l);
     launch_rms_fold(c, src.p, count, l);
     launch_ntt_relin_ms(c, src.p, acc.p, abase, a_outer, a_poly, amask, out, l, count);
     return 0;

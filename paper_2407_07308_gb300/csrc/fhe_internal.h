@@ -186,6 +186,11 @@ struct fhe_ctx {
     std::vector<std::vector<ulonglong2>> ks_xscale;  // [level][i]: N^-1 (Q_j/q_i)^-1 mod q_i, i in digit j
     std::vector<ulonglong2> ks_pscale;               // [k]: N^-1 p^-1 (P/p_k)^-1 mod p_k
     std::vector<ulonglong2> ms_lastscale;            // [level]: N^-1 p^-1 mod q_{level-1}
+    // device copies: ks_xscale as [level][FHE_MAXP]; ms4scale [level][FHE_MAXK + 1]
+    // = (ks_pscale[0..K-1], rms_yscale[level]); ks_pscale [K]; ms_lastscale
+    // [level]; mss_scale in its host layout
+    ulonglong2 *d_ks_xscale = nullptr, *d_ms4scale = nullptr, *d_ks_pscale = nullptr;
+    ulonglong2 *d_ms_lastscale = nullptr, *d_mss_scale = nullptr;
 
     // plaintext side
     int ns = 0, M = 0;             // slots and subring size
@@ -196,7 +201,8 @@ struct fhe_ctx {
     std::vector<int> ltbv;         // bivariate LT coefficients c[a p + b] (built on first use)
     std::map<int, std::shared_ptr<ExtTables>> ext;  // F_{p^d} slot tables by d (built on first use)
 
-    int ntt_variant = 0;        // NTT factorisation chosen by the autotuner
+    int sms = 0;                // SMs of the device (persistent NTT grids)
+    int ntt_variant = 0;        // NTT grid policy chosen by the autotuner
     float ntt_ms[4] = {0, 0, 0, 0};  // timings of each variant (forward + inverse, per batch; 0 = n/a)
 
     cudaStream_t stream = 0;
@@ -315,7 +321,53 @@ int build_tables(fhe_ctx *ctx);
 void lt_poly_coefficients(int p, std::vector<int> &out);
 void lt_bivariate_coefficients(int p, std::vector<int> &out);
 
-// kernel launchers (ntt.cu, kernels.cu)
+// NTT engine (ntt.cu).  A multi-segment launch takes one argument record per
+// segment (up to FHE_SEGS per kernel launch; more are split over launches);
+// segments may belong to different contexts on one device (the launch runs
+// on the first segment's context's stream) and differ in level and size.
+#define FHE_SEGS 24
+struct NttMapArgs {  // transform through a limb map; scale: device (N^-1 c_l, Shoup) per entry, or null
+    fhe_ctx *c;
+    const u64 *in;
+    u64 *out;
+    LimbMap m;
+    const ulonglong2 *scale;
+    int njobs;
+};
+struct NttYArgs : NttMapArgs {  // scaled inverse whose last entry loads y = acc + P add
+    const u64 *abase;
+    long long a_outer, a_poly;
+    int amask, level;
+};
+struct NttModUpArgs {
+    fhe_ctx *c;
+    const u64 *d2c;
+    u64 *ext;
+    int level, count;
+};
+struct NttDownArgs {  // ModDown (src = special limbs) or relinearise + switch (src = t_k and w)
+    fhe_ctx *c;
+    const u64 *src, *acc, *abase;
+    long long a_outer, a_poly;
+    int amask;
+    u64 *out;
+    int level, count;
+};
+struct NttSwitchArgs {  // k = 1: src = the switched limb's w; k > 1: the k values w_t
+    fhe_ctx *c;
+    const u64 *src, *in;
+    u64 *out;
+    int level, k, npoly, count;
+};
+void launch_ntt_map_many(const std::vector<NttMapArgs> &a, bool fwd, int cls);
+void launch_ntt_inv_scaled_y_many(const std::vector<NttYArgs> &a);
+void launch_ntt_modup_many(const std::vector<NttModUpArgs> &a);
+void launch_ntt_moddown_many(const std::vector<NttDownArgs> &a);
+void launch_ntt_relin_ms_many(const std::vector<NttDownArgs> &a);
+void launch_ntt_modswitch_many(const std::vector<NttSwitchArgs> &a);
+void launch_ntt_multiswitch_many(const std::vector<NttSwitchArgs> &a);
+
+// kernel launchers (ntt.cu, kernels.cu); scale arrays are device pointers
 void launch_ntt_fwd_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs);
 void launch_add_plain(fhe_ctx *c, const u64 *a, const u64 *m, u64 *out, int count, int npoly, int level, int sub);
 void encode_slot_vector(const fhe_ctx *c, const uint64_t *v, int64_t *m);  // n_s slots -> N coefficients in [0, p)

@@ -79,7 +79,7 @@ extern "C" int fhe_mod_switch_noalloc(fhe_ctx *c, const uint64_t *in, uint64_t *
     m.prime[0] = level - 1;
     // every scratch word read below is written by this inverse NTT first,
     // so nothing needs clearing between calls
-    launch_ntt_inv_scaled(c, in, scratch, m, &c->ms_lastscale[level], count * npoly);
+    launch_ntt_inv_scaled(c, in, scratch, m, c->d_ms_lastscale + level, count * npoly);
     launch_ntt_modswitch(c, scratch, in, out, level, npoly, count);
     c->prof_on = prof;
     return fhe_cuda_check(c, cudaGetLastError(), "mod_switch_noalloc");

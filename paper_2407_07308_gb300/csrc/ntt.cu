@@ -1,5 +1,6 @@
-// ntt.cu -- negacyclic NTT / inverse NTT over batches of RNS limbs, and the
-// key-switching / modulus-switching steps fused into them.
+// ntt.cu -- the NTT engine: negacyclic NTT / inverse NTT over batches of RNS
+// limbs, with the key-switching and modulus-switching steps fused into their
+// loads and stores.
 //
 // Transform (BoostCom Sec. 2.2: radix-2 NTT, Cooley-Tukey forward and
 // Gentleman-Sande inverse, for power-of-two N):
@@ -8,35 +9,43 @@
 //            twiddle psi^brv(2^s + (j >> (logN - s)));
 //   inverse  the stages undone in reverse order with psi^-brv(.), then N^-1.
 //
-// GB300 mapping: N = 2^n is split as 2^n1 x 2^n2 (n1 = ceil(n/2)).  The
-// forward transform is two kernels: "columns" runs global stages 0..n1-1,
+// GB300 mapping.  N = 2^n is split as 2^n1 x 2^n2 (n1 = ceil(n/2)).  The
+// forward transform is two passes: "columns" runs global stages 0..n1-1,
 // which only combine residues j = e 2^n2 + lo of one column lo, and "rows"
-// runs stages n1..n-1 inside contiguous rows of 2^n2 residues.  Each is a
-// sub-transform of size 2^M (M = n1 or n2) whose twiddles are entries of the
-// full table: at local stage u, element e of a sub-transform with block index
-// hi uses psi^brv(2^(S+u) + hi 2^u + (e >> (M-u))), S its first global stage.
-// A CTA holds 16 sub-transforms in shared memory ([16][2^M], padded), every
-// thread 16 residues in registers; a sub-transform runs as one radix-16 round
-// (4 stages, strided residues) and one round of the remaining M-4 stages
-// (contiguous blocks), with shared-memory exchanges in between.  Global
-// memory is always read and written in coalesced runs of 16 residues or more
-// (128 B).  The inverse runs the same kernels in reverse order (rows first),
-// undoing stages n-1..0.  ~17 KB of shared memory and 128 threads per CTA
-// (n = 14) leave room for many CTAs per SM; N up to 2^16 needs no cluster.
-// Butterflies are Harvey's lazy ones (values in [0,4q) forward, [0,2q)
-// inverse) with Shoup twiddles.
+// runs stages n1..n-1 inside contiguous rows of 2^n2 residues.  Each pass is
+// made of sub-transforms of size 2^M (M = n1 or n2) whose twiddles are
+// entries of the full table: at local stage u, element e of a sub-transform
+// with block index hi uses psi^brv(2^(S+u) + hi 2^u + (e >> (M-u))), S its
+// first global stage.  The inverse runs rows first, then columns.  The
+// half-transformed limb between the passes lives in the job's output limb.
+//
+// Units.  Every CTA has 128 threads holding 16 residues each, so a unit of
+// work is 2048 residues in shared memory: NS = 2^(11-M) sub-transforms of 2^M
+// points.  A sub-transform runs as one radix-16 round (4 stages on strided
+// residues) and one round of the remaining M-4 stages (contiguous blocks),
+// with shared-memory exchanges in between.  A column unit is NC adjacent
+// columns of each of NS/NC jobs (one job except at n = 10); a row unit is
+// either one row of each of 16 jobs that share a prime times NS/16 adjacent
+// rows (the batched case: the CTA stages those rows' twiddles once), or NS
+// adjacent rows of one job (small batches; twiddles read through the cache).
+// Global memory is read and written in coalesced runs of at least 64 bytes.
+//
+// Segments and persistence.  A launch carries a table of up to FHE_SEGS
+// segments; a segment is one batch of limb jobs with its own context (ring
+// degree, twiddle and constant tables), pointers and level.  One launch can
+// therefore serve ciphertexts of different ring degree, level and origin:
+// the units of all segments are numbered in order and every CTA walks them
+// with a grid stride, dispatching each unit on its segment's ring degree.
+// The grid is either one CTA per unit or a fixed number of resident CTAs per
+// SM (the autotuner's choice per context).
 //
 // Load/store functors let one kernel body serve the plain transform and the
 // fused variants: ModUp (basis conversion of a key-switching digit computed
 // while loading, then NTT), ModDown and modulus switching (correction
-// computed while loading, subtract-and-scale applied while storing).  The
-// half-transformed limb between the two kernels lives in the job's output
-// limb.
-#include <cooperative_groups.h>
-
+// computed while loading, subtract-and-scale applied while storing).
+// Butterflies are Harvey's lazy ones (values below (2s+1)q after s forward
+// stages, in [0, 2q) inverse) with Shoup twiddles.
 #include "fhe_internal.h"
-
-namespace cg = cooperative_groups;
 
 namespace {
 
@@ -64,7 +73,7 @@ __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 
 // Stages s0 .. s0+R-1 of the forward transform on one group x[0..2^R) whose
 // block index is hi.
 template <int R, class TW>
-__device__ __forceinline__ void fwd_round(u64 (&x)[1 << R], int s0, int hi, TW W, u64 q, u64 q2)
+__device__ __forceinline__ void fwd_round(u64 (&x)[1 << R], int s0, int hi, const TW &W, u64 q, u64 q2)
 {
 #pragma unroll
     for (int u = 0; u < R; u++) {
@@ -85,7 +94,7 @@ __device__ __forceinline__ void fwd_round(u64 (&x)[1 << R], int s0, int hi, TW W
 // half-distance 2^(R-1-U).  A template per stage keeps every index a
 // compile-time constant, so x stays in registers.
 template <int R, int U, class TW>
-__device__ __forceinline__ void inv_stage(u64 (&x)[1 << R], int s0, int hi, TW W, u64 q, u64 q2)
+__device__ __forceinline__ void inv_stage(u64 (&x)[1 << R], int s0, int hi, const TW &W, u64 q, u64 q2)
 {
     constexpr int half = 1 << (R - 1 - U);
 #pragma unroll
@@ -98,34 +107,47 @@ __device__ __forceinline__ void inv_stage(u64 (&x)[1 << R], int s0, int hi, TW W
 }
 
 template <int R, class TW>
-__device__ __forceinline__ void inv_round(u64 (&x)[1 << R], int s0, int hi, TW W, u64 q, u64 q2)
+__device__ __forceinline__ void inv_round(u64 (&x)[1 << R], int s0, int hi, const TW &W, u64 q, u64 q2)
 {
     inv_stage<R, R - 1>(x, s0, hi, W, q, q2);
 }
 
 // ---------------------------------------------------------------------------
-// 16 sub-transforms of size 2^M in shared memory
+// unit geometry
 // ---------------------------------------------------------------------------
 
-// Register cap of every NTT kernel: enough for 768 resident threads per SM
-// (85 registers a thread), measured faster than both the uncapped kernels
-// and a 64-register cap.
-#ifndef FHE_NTT_THREADS_PER_SM
-#define FHE_NTT_THREADS_PER_SM 768
+constexpr int T = 128;  // threads per CTA, 16 residues each
+
+// Register cap: 6 resident CTAs (768 threads) per SM, 85 registers a thread.
+#ifndef FHE_NTT_MINB
+#define FHE_NTT_MINB 6
 #endif
-#define FHE_MINB(T) (FHE_NTT_THREADS_PER_SM / (T) > 0 ? FHE_NTT_THREADS_PER_SM / (T) : 1)
-// The 8-elements-per-thread kernels exist to put more warps on each SM, so
-// they are capped for 1024 resident threads (64 registers a thread).
-#ifndef FHE_NTT8_THREADS_PER_SM
-#define FHE_NTT8_THREADS_PER_SM 1024
-#endif
-#define FHE_MINB_V(T, V) ((V) == 8 ? (FHE_NTT8_THREADS_PER_SM / (T) > 0 ? FHE_NTT8_THREADS_PER_SM / (T) : 1) : FHE_MINB(T))
 
 // Shared-memory twiddle tables: entry k at k + k / 8 (one 16-byte pad per 8
 // entries), so that the second round's strided twiddle reads (stride up to 8
 // entries across threads) hit distinct banks.
 __host__ __device__ constexpr int twp(int k) { return k + (k >> 3); }
 __host__ __device__ constexpr int twp_size(int n) { return n + n / 8 + 1; }
+
+// smem layout: sub-transform c at c*P(M), element e at e + (e >> 4); P is odd
+// mod 16 in u64 units, so the strided, blocked and row-wise access patterns
+// spread over the banks.
+template <int M>
+struct Sub {
+    static constexpr int SZ = 1 << M;           // elements per sub-transform
+    static constexpr int G = SZ / 16;           // threads per sub-transform
+    static constexpr int NS = T / G;            // sub-transforms per unit
+    static constexpr int R2 = M - 4;            // stages of the second round
+    static constexpr int P = SZ + SZ / 16 + 1;  // padded stride
+    static constexpr int WORDS = NS * P;        // shared memory words
+    static_assert(M >= 5 && M <= 8, "sub-transform size");
+    static_assert(NS * SZ == 16 * T, "16 residues a thread");
+    __device__ static int at(int c, int e) { return c * P + e + (e >> 4); }
+};
+
+constexpr int SM_WORDS = Sub<5>::WORDS > Sub<8>::WORDS ? Sub<5>::WORDS : Sub<8>::WORDS;
+constexpr int TW_WORDS = twp_size(256);  // largest staged twiddle table (ulonglong2)
+constexpr int ROW_J = 16;                    // jobs per grouped row unit
 
 // Twiddle accessors: get(s, j) = psi^brv(2^s + j), the twiddle of global
 // stage s with in-stage index j < 2^s.
@@ -139,51 +161,52 @@ struct PrefixTw {  // the first entries of the table, copied to shared memory
     __device__ ulonglong2 get(int s, int j) const { return sm[twp((1 << s) + j)]; }
 };
 
-// smem layout: sub-transform c at c*P(M), element e at e + (e >> 4); P is odd
-// mod 16 in u64 units, so the strided, blocked and row-wise access patterns
-// below all spread over the banks.
-template <int M>
-struct Sub {
-    static constexpr int SZ = 1 << M;                 // elements per sub-transform
-    static constexpr int G = SZ / 16;                 // threads per sub-transform
-    static constexpr int T = 16 * G;                  // threads per CTA
-    static constexpr int R2 = M - 4;                  // stages of the second round
-    static constexpr int P = SZ + SZ / 16 + 1;        // padded stride
-    static constexpr int WORDS = 16 * P;              // shared memory words
-    static_assert(M >= 5 && M <= 8, "sub-transform size");
-    __device__ static int at(int c, int e) { return c * P + e + (e >> 4); }
+// Row twiddles of one row hi (stages N1.., in-stage index hi 2^u + t) staged
+// at offset 2^u - 1 + t.
+struct RowTw {
+    const ulonglong2 *sm;
+    int N1, hi;
+    __device__ ulonglong2 get(int s, int j) const
+    {
+        const int u = s - N1;
+        return sm[twp((1 << u) - 1 + j - (hi << u))];
+    }
 };
 
-// Round 1: thread t = (g, c) with c = t % 16, g = t / 16 holds elements
+// Round 1: thread t = (g, c) with c = t % NS, g = t / NS holds elements
 // e = k G + g (k < 16) of sub-transform c: local stages 0..3.
 // Round 2: thread t = (c, g') with c = t / G, g' = t % G holds the 16/G
 // blocks b = g' (16/G) + i of G contiguous elements: local stages 4..M-1.
-// hi of sub-transform c is hi0 + c * hstep.
-template <int M, bool FWD, class TW>
-__device__ __forceinline__ void sub16(u64 *sm, int tid, TW W, int S, int hi0, int hstep, u64 q, u64 q2)
+// geo gives each sub-transform's twiddle accessor, block index and prime.
+template <int M, bool FWD, class Geo>
+__device__ __forceinline__ void subtx(u64 *sm, int tid, const Geo &geo)
 {
     using C = Sub<M>;
-    constexpr int G = C::G, R2 = C::R2, NB = 16 / G;
+    constexpr int G = C::G, R2 = C::R2, NB = 16 / G, NS = C::NS;
     // Addresses as a per-thread base plus compile-time offsets: for e = kG + g
     // (g < G <= 16, kG a multiple of G) e >> 4 = (kG) >> 4, and for
     // e = 16 g' + iG + f (iG + f < 16) e >> 4 = g'.
     auto round1 = [&]() {
-        const int c = tid & 15, g = tid >> 4;
-        const int hi = hi0 + c * hstep;
+        const int c = tid % NS, g = tid / NS;
+        const auto W = geo.tw(c);
+        const int hi = geo.hi(c);
+        const u64 q = geo.q(c), q2 = 2 * q;
         u64 *b1 = sm + c * C::P + g;
         u64 x[16];
 #pragma unroll
         for (int k = 0; k < 16; k++) x[k] = b1[k * G + ((k * G) >> 4)];
         if (FWD)
-            fwd_round<4>(x, S, hi, W, q, q2);
+            fwd_round<4>(x, geo.S, hi, W, q, q2);
         else
-            inv_round<4>(x, S, hi, W, q, q2);
+            inv_round<4>(x, geo.S, hi, W, q, q2);
 #pragma unroll
         for (int k = 0; k < 16; k++) b1[k * G + ((k * G) >> 4)] = x[k];
     };
     auto round2 = [&]() {
         const int c = tid / G, gp = tid % G;
-        const int hi = hi0 + c * hstep;
+        const auto W = geo.tw(c);
+        const int hi = geo.hi(c);
+        const u64 q = geo.q(c), q2 = 2 * q;
         u64 *b2 = sm + c * C::P + gp * 17;
 #pragma unroll
         for (int i = 0; i < NB; i++) {
@@ -191,9 +214,9 @@ __device__ __forceinline__ void sub16(u64 *sm, int tid, TW W, int S, int hi0, in
 #pragma unroll
             for (int f = 0; f < (1 << R2); f++) x[f] = b2[i * G + f];
             if (FWD)
-                fwd_round<R2>(x, S + 4, hi * 16 + gp * NB + i, W, q, q2);
+                fwd_round<R2>(x, geo.S + 4, hi * 16 + gp * NB + i, W, q, q2);
             else
-                inv_round<R2>(x, S + 4, hi * 16 + gp * NB + i, W, q, q2);
+                inv_round<R2>(x, geo.S + 4, hi * 16 + gp * NB + i, W, q, q2);
 #pragma unroll
             for (int f = 0; f < (1 << R2); f++) b2[i * G + f] = x[f];
         }
@@ -209,149 +232,140 @@ __device__ __forceinline__ void sub16(u64 *sm, int tid, TW W, int S, int hi0, in
     }
 }
 
-// The same 16 sub-transforms with 8 elements per thread (twice the threads,
-// for launches too small to fill the SMs): round A holds e = k G + g (k < 8,
-// G = 2^M / 8) for local stages 0..2; round B holds, of block b (G
-// contiguous elements, 8 per sub-transform), the elements b G + h + j PT
-// (j < 8, PT = G / 8 threads per block, h < PT) for local stages 3..5 in
-// registers and the remaining M - 6 stages across the PT lanes of a block
-// (lanes h and h ^ delta, one 64-bit shuffle per element).  Same butterflies,
-// same order per element: the results are identical to sub16's.
-template <int M>
-struct Sub8 {
-    static constexpr int SZ = 1 << M;       // elements per sub-transform
-    static constexpr int G = SZ / 8;        // threads per sub-transform
-    static constexpr int T = 16 * G;        // threads per CTA
-    static constexpr int R2 = M - 3;        // stages of round B
-    static constexpr int PT = G / 8;        // lanes per block in round B
-    static constexpr int P = Sub<M>::P;     // padded stride (same layout as Sub)
-    static constexpr int WORDS = Sub<M>::WORDS;
-    static_assert(M >= 6 && M <= 8, "8-element sub-transforms need 64 <= 2^M <= 256");
-    __device__ static int at(int c, int e) { return Sub<M>::at(c, e); }
+// Column pass of ring degree 2^(N1+N2): NC adjacent columns of NJ jobs.
+template <int N1, int N2>
+struct ColGeo {
+    using C = Sub<N1>;
+    static constexpr int NS = C::NS, SZ = C::SZ, NN = 1 << (N1 + N2);
+    static constexpr int NC = NS < (1 << N2) ? NS : (1 << N2);  // columns per job
+    static constexpr int NJ = NS / NC;                          // jobs per unit
+    static constexpr int BLK = (1 << N2) / NC;                  // column blocks per job
+    static constexpr int TWC = twp_size(1 << N1);               // staged twiddles per job
+    static_assert(NJ * TWC <= TW_WORDS, "twiddle staging");
+    static_assert(NJ <= 2, "jobs per column unit");
+    // word r of the unit: job slot, column in job, element
+    __device__ static int jslot(int r) { return NJ == 1 ? 0 : r / (NC * SZ); }
+    __device__ static int col(int r) { return r % NC; }
+    __device__ static int elem(int r) { return (r % (NC * SZ)) / NC; }
 };
 
-template <int M, int V>
-struct SubSel {
-    using type = Sub<M>;
-};
-template <int M>
-struct SubSel<M, 8> {
-    using type = Sub8<M>;
+template <int N1, int N2>
+struct ColTw {
+    const ulonglong2 *W;
+    u64 q0, q1;
+    static constexpr int S = 0;
+    __device__ PrefixTw tw(int c) const { return PrefixTw{W + (c / ColGeo<N1, N2>::NC) * ColGeo<N1, N2>::TWC}; }
+    __device__ int hi(int) const { return 0; }
+    __device__ u64 q(int c) const { return c / ColGeo<N1, N2>::NC == 0 ? q0 : q1; }
 };
 
-// Block-local stage R >= 3 of round B across lanes h and h ^ delta.
-template <int M, bool FWD, int R, class TW>
-__device__ __forceinline__ void sub8_cross(u64 (&x)[8], int h, int hb, TW W, int S, u64 q, u64 q2)
-{
-    constexpr int PT = Sub8<M>::PT, DELTA = PT >> (R - 2);
-    const bool lower = (h & DELTA) == 0;
-    const int tg0 = (h << (R - 3)) / PT;
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-        const ulonglong2 w = W.get(S + 3 + R, (hb << R) + j * (1 << (R - 3)) + tg0);
-        const u64 other = __shfl_xor_sync(0xffffffffu, x[j], DELTA);
-        const u64 a = lower ? x[j] : other, b = lower ? other : x[j];
-        if (FWD) {
-            const u64 t = shoup_lazy(b, w.x, w.y, q);
-            x[j] = lower ? a + t : a - t + q2;
-        } else {
-            u64 s2 = a + b;
-            s2 = s2 >= q2 ? s2 - q2 : s2;
-            x[j] = lower ? s2 : shoup_lazy(a - b + q2, w.x, w.y, q);
-        }
+// Row pass: grouped (16 jobs of one prime x R adjacent rows) or single (NS
+// adjacent rows of one job).
+template <int N1, int N2>
+struct RowGeo {
+    using C = Sub<N2>;
+    static constexpr int NS = C::NS, SZ = C::SZ, NN = 1 << (N1 + N2);
+    static constexpr int R = NS / ROW_J;         // rows per grouped unit
+    static constexpr int CH = (1 << N1) / R;     // row chunks per limb (grouped)
+    // row chunks per limb (single; a limb with fewer than NS rows, n = 10,
+    // always takes the grouped form)
+    static constexpr int CHS = (1 << N1) >= NS ? (1 << N1) / NS : 1;
+    static constexpr int TWR = twp_size(SZ - 1); // staged twiddles per row
+    static_assert(NS >= ROW_J && NS % ROW_J == 0, "row units");
+    static_assert(R * TWR <= TW_WORDS, "twiddle staging");
+};
+
+template <int N1, int N2>
+struct RowGrpTw {
+    const ulonglong2 *W;
+    int hi0;
+    u64 qq;
+    int S;
+    __device__ RowTw tw(int c) const
+    {
+        constexpr int R = RowGeo<N1, N2>::R;
+        return RowTw{W + (c % R) * RowGeo<N1, N2>::TWR, N1, hi0 + c % R};
     }
-}
+    __device__ int hi(int c) const { return hi0 + c % RowGeo<N1, N2>::R; }
+    __device__ u64 q(int) const { return qq; }
+};
 
-template <int M, bool FWD, class TW>
-__device__ __forceinline__ void sub8(u64 *sm, int tid, TW W, int S, int hi0, int hstep, u64 q, u64 q2)
+struct RowOneTw {
+    GTw g;
+    int hi0;
+    u64 qq;
+    int S;
+    __device__ GTw tw(int) const { return g; }
+    __device__ int hi(int c) const { return hi0 + c; }
+    __device__ u64 q(int) const { return qq; }
+};
+
+// ---------------------------------------------------------------------------
+// segment tables
+// ---------------------------------------------------------------------------
+
+// Per segment: jobs = outer * nl, job = o * nl + l, and the prime of a job
+// depends on l only (so the jobs l, nl + l, 2 nl + l ... can share a CTA).
+struct SegHdr {
+    int logN, outer, nl, grouped;  // grouped: row units of 16 jobs
+    int u_cols, u_rows, pad0, pad1;
+    const ModQ *mq;
+    const ulonglong2 *tw;    // forward or inverse table of the segment's context
+    const ulonglong2 *ninv;  // N^-1 per prime (Shoup pairs)
+};
+
+template <class S>
+struct SegIO {
+    int nseg, ucols, urows, pad;
+    SegHdr h[FHE_SEGS];
+    S s[FHE_SEGS];
+};
+
+template <class IO>
+__device__ __forceinline__ int seg_of(const IO &io, int u, bool rows)
 {
-    using C = Sub8<M>;
-    constexpr int G = C::G, R2 = C::R2, PT = C::PT;
-    auto roundA = [&]() {
-        const int c = tid & 15, g = tid >> 4;
-        const int hi = hi0 + c * hstep;
-        u64 x[8];
-#pragma unroll
-        for (int k = 0; k < 8; k++) x[k] = sm[C::at(c, k * G + g)];
-        if (FWD)
-            fwd_round<3>(x, S, hi, W, q, q2);
-        else
-            inv_round<3>(x, S, hi, W, q, q2);
-#pragma unroll
-        for (int k = 0; k < 8; k++) sm[C::at(c, k * G + g)] = x[k];
-    };
-    auto roundB = [&]() {
-        const int c = tid / G, gp = tid % G, b = gp / PT, h = gp % PT;
-        const int hb = (hi0 + c * hstep) * 8 + b;
-        u64 x[8];
-#pragma unroll
-        for (int j = 0; j < 8; j++) x[j] = sm[C::at(c, b * G + h + j * PT)];
-        if (FWD) {
-            fwd_round<3>(x, S + 3, hb, W, q, q2);
-            if constexpr (R2 > 3) sub8_cross<M, true, 3>(x, h, hb, W, S, q, q2);
-            if constexpr (R2 > 4) sub8_cross<M, true, 4>(x, h, hb, W, S, q, q2);
-        } else {
-            if constexpr (R2 > 4) sub8_cross<M, false, 4>(x, h, hb, W, S, q, q2);
-            if constexpr (R2 > 3) sub8_cross<M, false, 3>(x, h, hb, W, S, q, q2);
-            inv_round<3>(x, S + 3, hb, W, q, q2);
-        }
-#pragma unroll
-        for (int j = 0; j < 8; j++) sm[C::at(c, b * G + h + j * PT)] = x[j];
-    };
-    if (FWD) {
-        roundA();
-        __syncthreads();
-        roundB();
-    } else {
-        roundB();
-        __syncthreads();
-        roundA();
-    }
+    int sg = 0;
+    while (sg + 1 < io.nseg && (rows ? io.h[sg + 1].u_rows : io.h[sg + 1].u_cols) <= u) sg++;
+    return sg;
 }
 
-template <int M, int V, bool FWD, class TW>
-__device__ __forceinline__ void subtx(u64 *sm, int tid, TW W, int S, int hi0, int hstep, u64 q, u64 q2)
-{
-    if constexpr (V == 16)
-        sub16<M, FWD>(sm, tid, W, S, hi0, hstep, q, q2);
-    else
-        sub8<M, FWD>(sm, tid, W, S, hi0, hstep, q, q2);
-}
+// ---------------------------------------------------------------------------
+// the unit bodies
+// ---------------------------------------------------------------------------
 
-// Moves a CTA's 16 x 2^M words into shared memory: word r (r = tid + k T)
-// is read by src(r) and written by dst(r, v).  Staged in chunks of CH: the
-// chunk's reads are all issued before its first write (the compiler does not
-// reorder a global read past a shared-memory write on its own), so they
-// overlap; CH = 0 keeps read/write pairs (better for loads that already hold
-// several reads each, like ModUp's basis conversion).
-template <class C, int CH = 16, class Src, class Dst>
+// Moves words r = tid + k T (k < 16) through src(r) -> dst(r, v), staged in
+// chunks of CH: the chunk's reads are all issued before its first write (the
+// compiler does not reorder a global read past a shared-memory write on its
+// own), so they overlap; CH = 0 keeps read/write pairs (better for loads
+// that already hold several reads each, like ModUp's basis conversion).
+template <int CH, class Src, class Dst>
 __device__ __forceinline__ void tile_in(int tid, Src src, Dst dst)
 {
-    constexpr int IT = 16 * C::SZ / C::T;
+    constexpr int IT = 16;
     if constexpr (CH > 0) {
         constexpr int K = CH < IT ? CH : IT;
 #pragma unroll
         for (int k0 = 0; k0 < IT; k0 += K) {
             u64 v[K];
 #pragma unroll
-            for (int k = 0; k < K; k++) v[k] = src(tid + (k0 + k) * C::T);
+            for (int k = 0; k < K; k++) v[k] = src(tid + (k0 + k) * T);
 #pragma unroll
-            for (int k = 0; k < K; k++) dst(tid + (k0 + k) * C::T, v[k]);
+            for (int k = 0; k < K; k++) dst(tid + (k0 + k) * T, v[k]);
         }
     } else {
-        for (int r = tid; r < 16 * C::SZ; r += C::T) dst(r, src(r));
+#pragma unroll 4
+        for (int k = 0; k < IT; k++) dst(tid + k * T, src(tid + k * T));
     }
 }
 
-// Stores a CTA's 16 x 2^M results of a forward row pass: word r goes to
-// index idx(r) of state st(r) with value val(r).  Staged: the operands the
-// store reads (IO::NPRE per word) are loaded for a chunk of words before
-// any of the chunk's writes, so those loads overlap (otherwise every write
-// to global memory would order the next word's reads behind it).
-template <class C, class IO, class StF, class Idx, class Val>
-__device__ __forceinline__ void tile_out(const IO &io, int tid, StF st, Idx idx, Val val)
+// Stores of a forward row pass: word r goes to index idx(r) of state st(r)
+// with value val(r) when ok(r).  Staged: the operands the store reads
+// (IO::NPRE per word) are loaded for a chunk of words before any of the
+// chunk's writes, so those loads overlap.
+template <class IO, class StF, class Ok, class Idx, class Val>
+__device__ __forceinline__ void tile_out(const IO &io, int tid, StF st, Ok ok, Idx idx, Val val)
 {
-    constexpr int IT = 16 * C::SZ / C::T;
+    constexpr int IT = 16;
     if constexpr (IO::NPRE > 0) {
         constexpr int CH = IO::NPRE == 1 ? IT : IT / 2;
 #pragma unroll
@@ -359,480 +373,642 @@ __device__ __forceinline__ void tile_out(const IO &io, int tid, StF st, Idx idx,
             u64 a[CH][IO::NPRE];
 #pragma unroll
             for (int k = 0; k < CH; k++) {
-                const int r = tid + (k0 + k) * C::T;
+                const int r = tid + (k0 + k) * T;
 #pragma unroll
-                for (int w = 0; w < IO::NPRE; w++) a[k][w] = io.pre(st(r), idx(r), w);
+                for (int w = 0; w < IO::NPRE; w++) a[k][w] = ok(r) ? io.pre(st(r), idx(r), w) : 0;
             }
 #pragma unroll
             for (int k = 0; k < CH; k++) {
-                const int r = tid + (k0 + k) * C::T;
-                io.store_pre(st(r), idx(r), val(r), a[k]);
+                const int r = tid + (k0 + k) * T;
+                if (ok(r)) io.store_pre(st(r), idx(r), val(r), a[k]);
             }
         }
     } else {
-        for (int r = tid; r < 16 * C::SZ; r += C::T) io.store(st(r), idx(r), val(r));
+#pragma unroll 4
+        for (int k = 0; k < IT; k++) {
+            const int r = tid + k * T;
+            if (ok(r)) io.store(st(r), idx(r), val(r));
+        }
     }
 }
 
-// Grouped row kernels: all 16 sub-transforms of the CTA are row hi of 16
-// limbs with one prime, so the CTA needs only the 2^N2 - 1 twiddles of that
-// row: stage N1+u, in-stage index hi 2^u + t, at offset 2^u - 1 + t.
-struct RowTw {
-    const ulonglong2 *sm;
-    int N1, hi;
-    __device__ ulonglong2 get(int s, int j) const
+// The jobs of a column unit: slot j (j < NJ) holds job0 + j.
+template <int N1, int N2, class IO>
+__device__ __forceinline__ int col_jobs(const IO &io, int sg, int lu, typename IO::St *sts, int *lo0)
+{
+    using Gm = ColGeo<N1, N2>;
+    const SegHdr &H = io.h[sg];
+    const int njobs = H.outer * H.nl;
+    const int job0 = (lu / Gm::BLK) * Gm::NJ;
+    *lo0 = (lu % Gm::BLK) * Gm::NC;
+    if (threadIdx.x < Gm::NJ && job0 + (int)threadIdx.x < njobs) sts[threadIdx.x] = io.begin(sg, job0 + threadIdx.x);
+    __syncthreads();
+    return njobs - job0;  // valid job slots (>= 1)
+}
+
+// Stages the first 2^N1 twiddles of each job's prime (the column stages):
+// loaded into registers first, stored after the tile loads (latency overlap).
+template <int N1, int N2>
+struct ColTwStage {
+    using Gm = ColGeo<N1, N2>;
+    static constexpr int NW = Gm::NJ << N1;
+    static constexpr int PER = (NW + T - 1) / T;
+    ulonglong2 v[PER];
+    template <class St>
+    __device__ void load(const SegHdr &H, const St *sts, int nvalid)
     {
-        const int u = s - N1;
-        return sm[twp((1 << u) - 1 + j - (hi << u))];
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            const int i = threadIdx.x + k * T, j = i >> N1;
+            v[k] = (i < NW && j < nvalid) ? __ldg(H.tw + (size_t)sts[j].prime * Gm::NN + (i & ((1 << N1) - 1)))
+                                          : make_ulonglong2(0, 0);
+        }
+    }
+    __device__ void store(ulonglong2 *W) const
+    {
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            const int i = threadIdx.x + k * T;
+            if (i < NW) W[(i >> N1) * Gm::TWC + twp(i & ((1 << N1) - 1))] = v[k];
+        }
     }
 };
 
-// ---------------------------------------------------------------------------
-// kernels.  Grid: one CTA per (job, block of 16 columns / rows).
-// ---------------------------------------------------------------------------
-
-// Forward, columns: global stages 0..N1-1 on columns lo0..lo0+15.
-template <int N1, int N2, class IO, int V = 16>
-__global__ void __launch_bounds__(SubSel<N1, V>::type::T, FHE_MINB_V((SubSel<N1, V>::type::T), V))
-    k_fwd_cols(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
+// Forward, columns: global stages 0..N1-1.
+template <int N1, int N2, class IO>
+__device__ __noinline__ void fwd_cols_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
+                                              typename IO::St *sts)
 {
-    using C = typename SubSel<N1, V>::type;
-    constexpr int NN = 1 << (N1 + N2), BLK = (1 << N2) / 16;
-    __shared__ u64 sm[C::WORDS];
-    __shared__ ulonglong2 W[twp_size(1 << N1)];  // stages 0..N1-1 use only the table's prefix
-    const int job = blockIdx.x / BLK, lo0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
-    const typename IO::St st = io.begin(job, NN);
-    const u64 q = mq[st.prime].q, q2 = 2 * q;
-    // at most one twiddle per thread (T >= 2^N1), loaded before the tile and
-    // stored after it, so that its latency overlaps the tile's loads
-    static_assert(C::T >= (1 << N1), "one twiddle per thread");
-    const bool has_w = tid < (1 << N1);
-    const ulonglong2 wv = has_w ? __ldg(tw + (size_t)st.prime * NN + tid) : make_ulonglong2(0, 0);
-    tile_in<C, IO::LDCH>(
-        tid, [&](int r) { return io.load(st, ((r >> 4) << N2) + lo0 + (r & 15)); },
-        [&](int r, u64 v) { sm[C::at(r & 15, r >> 4)] = v; });
-    if (has_w) W[twp(tid)] = wv;
+    using Gm = ColGeo<N1, N2>;
+    using C = typename Gm::C;
+    const int tid = threadIdx.x;
+    int lo0;
+    const int nvalid = col_jobs<N1, N2>(io, sg, lu, sts, &lo0);
+    const SegHdr &H = io.h[sg];
+    ColTwStage<N1, N2> tws;
+    tws.load(H, sts, nvalid);
+    const u64 q0 = H.mq[sts[0].prime].q, q1 = nvalid > 1 ? H.mq[sts[Gm::NJ - 1].prime].q : q0;
+    tile_in<IO::LDCH>(
+        tid,
+        [&](int r) {
+            const int j = Gm::jslot(r);
+            return j < nvalid ? io.load(sts[j], (Gm::elem(r) << N2) + lo0 + Gm::col(r)) : 0;
+        },
+        [&](int r, u64 v) { sm[C::at(Gm::jslot(r) * Gm::NC + Gm::col(r), Gm::elem(r))] = v; });
+    tws.store(W);
     __syncthreads();
-    subtx<N1, V, true>(sm, tid, PrefixTw{W}, 0, 0, 0, q, q2);
+    subtx<N1, true>(sm, tid, ColTw<N1, N2>{W, q0, q1});
     __syncthreads();
-    u64 *mid = io.inter(st);
-    for (int r = tid; r < 16 * C::SZ; r += C::T) {
-        const int c = r & 15, e = r >> 4;
-        mid[(e << N2) + lo0 + c] = sm[C::at(c, e)];
+#pragma unroll 4
+    for (int k = 0; k < 16; k++) {
+        const int r = tid + k * T, j = Gm::jslot(r);
+        if (j < nvalid)
+            io.inter(sts[j])[(Gm::elem(r) << N2) + lo0 + Gm::col(r)] =
+                sm[C::at(j * Gm::NC + Gm::col(r), Gm::elem(r))];
     }
 }
 
-// Forward, rows: global stages N1..N1+N2-1 on rows hi0..hi0+15.
-template <int N1, int N2, class IO, int V = 16>
-__global__ void __launch_bounds__(SubSel<N2, V>::type::T, FHE_MINB_V((SubSel<N2, V>::type::T), V))
-    k_fwd_rows(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
+// Inverse, columns: undoes global stages N1-1..0, then scales (N^-1 times the
+// job's constant) and stores.
+template <int N1, int N2, class IO>
+__device__ __noinline__ void inv_cols_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
+                                              typename IO::St *sts)
 {
-    using C = typename SubSel<N2, V>::type;
-    constexpr int NN = 1 << (N1 + N2), BLK = (1 << N1) / 16;
-    __shared__ u64 sm[C::WORDS];
-    const int job = blockIdx.x / BLK, hi0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
-    const typename IO::St st = io.begin(job, NN);
-    const u64 q = mq[st.prime].q, q2 = 2 * q;
-    const GTw W{tw + (size_t)st.prime * NN};
-    const u64 *mid = io.inter(st) + ((size_t)hi0 << N2);
-    tile_in<C>(tid, [&](int r) { return mid[r]; }, [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
+    using Gm = ColGeo<N1, N2>;
+    using C = typename Gm::C;
+    const int tid = threadIdx.x;
+    int lo0;
+    const int nvalid = col_jobs<N1, N2>(io, sg, lu, sts, &lo0);
+    const SegHdr &H = io.h[sg];
+    ColTwStage<N1, N2> tws;
+    tws.load(H, sts, nvalid);
+    const u64 q0 = H.mq[sts[0].prime].q, q1 = nvalid > 1 ? H.mq[sts[Gm::NJ - 1].prime].q : q0;
+    tile_in<16>(
+        tid,
+        [&](int r) {
+            const int j = Gm::jslot(r);
+            return j < nvalid ? io.inter(sts[j])[(Gm::elem(r) << N2) + lo0 + Gm::col(r)] : 0;
+        },
+        [&](int r, u64 v) { sm[C::at(Gm::jslot(r) * Gm::NC + Gm::col(r), Gm::elem(r))] = v; });
+    tws.store(W);
     __syncthreads();
-    subtx<N2, V, true>(sm, tid, W, N1, hi0, 1, q, q2);
+    subtx<N1, false>(sm, tid, ColTw<N1, N2>{W, q0, q1});
     __syncthreads();
-    const ModQ mqp = mq[st.prime];
-    tile_out<C>(
-        io, tid, [&](int) -> const typename IO::St & { return st; }, [&](int r) { return (hi0 << N2) + r; },
-        [&](int r) { return reduce64(sm[C::at(r >> N2, r & (C::SZ - 1))], mqp); });
+#pragma unroll 4
+    for (int k = 0; k < 16; k++) {
+        const int r = tid + k * T, j = Gm::jslot(r);
+        if (j < nvalid) {
+            const ulonglong2 ni = io.final_scale(sts[j]);
+            const u64 q = j == 0 ? q0 : q1;
+            io.store(sts[j], (Gm::elem(r) << N2) + lo0 + Gm::col(r),
+                     reduce2q(shoup_lazy(sm[C::at(j * Gm::NC + Gm::col(r), Gm::elem(r))], ni.x, ni.y, q), q));
+        }
+    }
+}
+
+// The jobs of a row unit.  Grouped: slots jj < 16 hold jobs (oc 16 + jj) nl
+// + l, rows hi0 .. hi0+R-1; single: slot 0 holds the job, rows hi0 ..
+// hi0+NS-1.  Returns the number of valid slots.
+template <int N1, int N2, bool GRP, class IO>
+__device__ __forceinline__ int row_jobs(const IO &io, int sg, int lu, typename IO::St *sts, int *hi0)
+{
+    using Gm = RowGeo<N1, N2>;
+    const SegHdr &H = io.h[sg];
+    int nvalid;
+    if (GRP) {
+        const int OC = (H.outer + ROW_J - 1) / ROW_J;
+        const int hc = lu % Gm::CH, t = lu / Gm::CH;
+        const int oc = t % OC, l = t / OC;
+        *hi0 = hc * Gm::R;
+        nvalid = min(ROW_J, H.outer - oc * ROW_J);
+        if ((int)threadIdx.x < nvalid) sts[threadIdx.x] = io.begin(sg, (oc * ROW_J + threadIdx.x) * H.nl + l);
+    } else {
+        *hi0 = (lu % Gm::CHS) * Gm::NS;
+        nvalid = 1;
+        if (threadIdx.x == 0) sts[0] = io.begin(sg, lu / Gm::CHS);
+    }
+    __syncthreads();
+    return nvalid;
+}
+
+// Grouped rows stage the R rows' twiddles: entry k of row r is the stage
+// u = floor(log2(k+1)) twiddle with in-stage index (hi0 + r) 2^u + k+1-2^u.
+template <int N1, int N2>
+struct RowTwStage {
+    using Gm = RowGeo<N1, N2>;
+    static constexpr int NW = Gm::R * (Gm::SZ - 1);
+    static constexpr int PER = (NW + T - 1) / T;
+    ulonglong2 v[PER];
+    __device__ void load(const ulonglong2 *tw, int hi0)
+    {
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            const int i = threadIdx.x + k * T;
+            v[k] = make_ulonglong2(0, 0);
+            if (i < NW) {
+                const int r = i / (Gm::SZ - 1), e = i % (Gm::SZ - 1);
+                const int u = 31 - __clz(e + 1);
+                v[k] = __ldg(tw + (1 << (N1 + u)) + ((hi0 + r) << u) + (e + 1 - (1 << u)));
+            }
+        }
+    }
+    __device__ void store(ulonglong2 *W) const
+    {
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            const int i = threadIdx.x + k * T;
+            if (i < NW) W[(i / (Gm::SZ - 1)) * Gm::TWR + twp(i % (Gm::SZ - 1))] = v[k];
+        }
+    }
+};
+
+// word r of a row unit -> (sub-transform c = r >> N2, element f); the job
+// slot and row of c
+template <int N1, int N2, bool GRP>
+struct RowMap {
+    using Gm = RowGeo<N1, N2>;
+    int hi0;
+    __device__ int c(int r) const { return r >> N2; }
+    __device__ int f(int r) const { return r & (Gm::SZ - 1); }
+    __device__ int slot(int r) const { return GRP ? c(r) / Gm::R : 0; }
+    __device__ int row(int r) const { return hi0 + (GRP ? c(r) % Gm::R : c(r)); }
+};
+
+// Forward, rows: global stages N1..N1+N2-1, reduction to [0, q), store.
+template <int N1, int N2, bool GRP, class IO>
+__device__ __noinline__ void fwd_rows_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
+                                          typename IO::St *sts)
+{
+    using Gm = RowGeo<N1, N2>;
+    using C = typename Gm::C;
+    const int tid = threadIdx.x;
+    const SegHdr &H = io.h[sg];
+    int hi0;
+    const int nvalid = row_jobs<N1, N2, GRP>(io, sg, lu, sts, &hi0);
+    const RowMap<N1, N2, GRP> mp{hi0};
+    const int prime = sts[0].prime;
+    const ModQ mqp = H.mq[prime];
+    const ulonglong2 *tw = H.tw + (size_t)prime * Gm::NN;
+    RowTwStage<N1, N2> tws;
+    if (GRP) tws.load(tw, hi0);
+    tile_in<16>(
+        tid,
+        [&](int r) {
+            const int j = mp.slot(r);
+            return j < nvalid ? io.inter(sts[j])[(mp.row(r) << N2) + mp.f(r)] : 0;
+        },
+        [&](int r, u64 v) { sm[C::at(mp.c(r), mp.f(r))] = v; });
+    if (GRP) tws.store(W);
+    __syncthreads();
+    if (GRP)
+        subtx<N2, true>(sm, tid, RowGrpTw<N1, N2>{W, hi0, mqp.q, N1});
+    else
+        subtx<N2, true>(sm, tid, RowOneTw{GTw{tw}, hi0, mqp.q, N1});
+    __syncthreads();
+    tile_out(
+        io, tid, [&](int r) -> const typename IO::St & { return sts[mp.slot(r)]; },
+        [&](int r) { return mp.slot(r) < nvalid; }, [&](int r) { return (mp.row(r) << N2) + mp.f(r); },
+        [&](int r) { return reduce64(sm[C::at(mp.c(r), mp.f(r))], mqp); });
 }
 
 // Inverse, rows first: undoes global stages N1+N2-1..N1.
-template <int N1, int N2, class IO, int V = 16>
-__global__ void __launch_bounds__(SubSel<N2, V>::type::T, FHE_MINB_V((SubSel<N2, V>::type::T), V))
-    k_inv_rows(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
+template <int N1, int N2, bool GRP, class IO>
+__device__ __noinline__ void inv_rows_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
+                                          typename IO::St *sts)
 {
-    using C = typename SubSel<N2, V>::type;
-    constexpr int NN = 1 << (N1 + N2), BLK = (1 << N1) / 16;
-    __shared__ u64 sm[C::WORDS];
-    const int job = blockIdx.x / BLK, hi0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
-    const typename IO::St st = io.begin(job, NN);
-    const u64 q = mq[st.prime].q, q2 = 2 * q;
-    const GTw W{tw + (size_t)st.prime * NN};
-    tile_in<C>(
-        tid, [&](int r) { return io.load(st, (hi0 << N2) + r); },
-        [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
-    __syncthreads();
-    subtx<N2, V, false>(sm, tid, W, N1, hi0, 1, q, q2);
-    __syncthreads();
-    u64 *mid = io.inter(st) + ((size_t)hi0 << N2);
-    for (int r = tid; r < 16 * C::SZ; r += C::T) mid[r] = sm[C::at(r >> N2, r & (C::SZ - 1))];
-}
-
-// Grouped rows.  Jobs j and j + stride share a prime; the launch holds
-// `groups` x 16 such jobs per residue class of j mod stride.  CTA
-// (group g, row hi): sub-transform c is row hi of job base + (16 kb + c) stride
-// with base = g % stride, kb = g / stride.
-template <int N1, int N2, class IO, int V = 16>
-__global__ void __launch_bounds__(SubSel<N2, V>::type::T, FHE_MINB_V((SubSel<N2, V>::type::T), V))
-    k_fwd_rows_grp(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw, int stride)
-{
-    using C = typename SubSel<N2, V>::type;
-    constexpr int NN = 1 << (N1 + N2), ROWS = 1 << N1;
-    __shared__ u64 sm[C::WORDS];
-    __shared__ ulonglong2 tws[twp_size((1 << N2) - 1)];
-    __shared__ typename IO::St sts[16];
-    const int tid = threadIdx.x, hi = blockIdx.x % ROWS, g = blockIdx.x / ROWS;
-    const int base = g % stride, kb = g / stride;
-    if (tid < 16) sts[tid] = io.begin(base + (16 * kb + tid) * stride, NN);
-    __syncthreads();
+    using Gm = RowGeo<N1, N2>;
+    using C = typename Gm::C;
+    const int tid = threadIdx.x;
+    const SegHdr &H = io.h[sg];
+    int hi0;
+    const int nvalid = row_jobs<N1, N2, GRP>(io, sg, lu, sts, &hi0);
+    const RowMap<N1, N2, GRP> mp{hi0};
     const int prime = sts[0].prime;
-    const ModQ mqp = mq[prime];
-    const u64 q = mqp.q, q2 = 2 * q;
-    const ulonglong2 *W = tw + (size_t)prime * NN;
-    // at most one twiddle per thread (T = 2^N2), loaded before the tile and
-    // stored after it, so that its latency overlaps the tile's loads
-    static_assert(C::T >= (1 << N2) - 1, "one twiddle per thread");
-    const bool has_w = tid < (1 << N2) - 1;
-    ulonglong2 wv = make_ulonglong2(0, 0);
-    if (has_w) {
-        const int u = 31 - __clz(tid + 1);  // stage of entry tid
-        wv = __ldg(W + (1 << (N1 + u)) + (hi << u) + (tid + 1 - (1 << u)));
-    }
-    tile_in<C>(
-        tid, [&](int r) { return io.inter(sts[r >> N2])[(hi << N2) + (r & (C::SZ - 1))]; },
-        [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
-    if (has_w) tws[twp(tid)] = wv;
+    const u64 q = H.mq[prime].q;
+    const ulonglong2 *tw = H.tw + (size_t)prime * Gm::NN;
+    RowTwStage<N1, N2> tws;
+    if (GRP) tws.load(tw, hi0);
+    tile_in<IO::LDCH>(
+        tid,
+        [&](int r) {
+            const int j = mp.slot(r);
+            return j < nvalid ? io.load(sts[j], (mp.row(r) << N2) + mp.f(r)) : 0;
+        },
+        [&](int r, u64 v) { sm[C::at(mp.c(r), mp.f(r))] = v; });
+    if (GRP) tws.store(W);
     __syncthreads();
-    subtx<N2, V, true>(sm, tid, RowTw{tws, N1, hi}, N1, hi, 0, q, q2);
+    if (GRP)
+        subtx<N2, false>(sm, tid, RowGrpTw<N1, N2>{W, hi0, q, N1});
+    else
+        subtx<N2, false>(sm, tid, RowOneTw{GTw{tw}, hi0, q, N1});
     __syncthreads();
-    tile_out<C>(
-        io, tid, [&](int r) -> const typename IO::St & { return sts[r >> N2]; },
-        [&](int r) { return (hi << N2) + (r & (C::SZ - 1)); },
-        [&](int r) { return reduce64(sm[C::at(r >> N2, r & (C::SZ - 1))], mqp); });
-}
-
-template <int N1, int N2, class IO, int V = 16>
-__global__ void __launch_bounds__(SubSel<N2, V>::type::T, FHE_MINB_V((SubSel<N2, V>::type::T), V))
-    k_inv_rows_grp(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw, int stride)
-{
-    using C = typename SubSel<N2, V>::type;
-    constexpr int NN = 1 << (N1 + N2), ROWS = 1 << N1;
-    __shared__ u64 sm[C::WORDS];
-    __shared__ ulonglong2 tws[twp_size((1 << N2) - 1)];
-    __shared__ typename IO::St sts[16];
-    const int tid = threadIdx.x, hi = blockIdx.x % ROWS, g = blockIdx.x / ROWS;
-    const int base = g % stride, kb = g / stride;
-    if (tid < 16) sts[tid] = io.begin(base + (16 * kb + tid) * stride, NN);
-    __syncthreads();
-    const int prime = sts[0].prime;
-    const u64 q = mq[prime].q, q2 = 2 * q;
-    const ulonglong2 *W = tw + (size_t)prime * NN;
-    static_assert(C::T >= (1 << N2) - 1, "one twiddle per thread");
-    const bool has_w = tid < (1 << N2) - 1;
-    ulonglong2 wv = make_ulonglong2(0, 0);
-    if (has_w) {  // stored after the tile (latency overlap)
-        const int u = 31 - __clz(tid + 1);
-        wv = __ldg(W + (1 << (N1 + u)) + (hi << u) + (tid + 1 - (1 << u)));
-    }
-    tile_in<C>(
-        tid, [&](int r) { return io.load(sts[r >> N2], (hi << N2) + (r & (C::SZ - 1))); },
-        [&](int r, u64 v) { sm[C::at(r >> N2, r & (C::SZ - 1))] = v; });
-    if (has_w) tws[twp(tid)] = wv;
-    __syncthreads();
-    subtx<N2, V, false>(sm, tid, RowTw{tws, N1, hi}, N1, hi, 0, q, q2);
-    __syncthreads();
-    for (int r = tid; r < 16 * C::SZ; r += C::T) {
-        const int c = r >> N2, f = r & (C::SZ - 1);
-        io.inter(sts[c])[(hi << N2) + f] = sm[C::at(c, f)];
-    }
-}
-
-// Inverse, columns: undoes global stages N1-1..0, then scales by N^-1.
-template <int N1, int N2, class IO, int V = 16>
-__global__ void __launch_bounds__(SubSel<N1, V>::type::T, FHE_MINB_V((SubSel<N1, V>::type::T), V))
-    k_inv_cols(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw,
-               const ulonglong2 *__restrict__ ninv)
-{
-    using C = typename SubSel<N1, V>::type;
-    constexpr int NN = 1 << (N1 + N2), BLK = (1 << N2) / 16;
-    __shared__ u64 sm[C::WORDS];
-    __shared__ ulonglong2 W[twp_size(1 << N1)];
-    const int job = blockIdx.x / BLK, lo0 = (blockIdx.x % BLK) * 16, tid = threadIdx.x;
-    const typename IO::St st = io.begin(job, NN);
-    const u64 q = mq[st.prime].q, q2 = 2 * q;
-    static_assert(C::T >= (1 << N1), "one twiddle per thread");
-    const bool has_w = tid < (1 << N1);  // stored after the tile (latency overlap)
-    const ulonglong2 wv = has_w ? __ldg(tw + (size_t)st.prime * NN + tid) : make_ulonglong2(0, 0);
-    const ulonglong2 ni = io.final_scale(st, ninv);
-    const u64 *mid = io.inter(st);
-    tile_in<C>(
-        tid, [&](int r) { return mid[((r >> 4) << N2) + lo0 + (r & 15)]; },
-        [&](int r, u64 v) { sm[C::at(r & 15, r >> 4)] = v; });
-    if (has_w) W[twp(tid)] = wv;
-    __syncthreads();
-    subtx<N1, V, false>(sm, tid, PrefixTw{W}, 0, 0, 0, q, q2);
-    __syncthreads();
-    for (int r = tid; r < 16 * C::SZ; r += C::T) {
-        const int c = r & 15, e = r >> 4;
-        io.store(st, (e << N2) + lo0 + c, reduce2q(shoup_lazy(sm[C::at(c, e)], ni.x, ni.y, q), q));
+#pragma unroll 4
+    for (int k = 0; k < 16; k++) {
+        const int r = tid + k * T, j = mp.slot(r);
+        if (j < nvalid) io.inter(sts[j])[(mp.row(r) << N2) + mp.f(r)] = sm[C::at(mp.c(r), mp.f(r))];
     }
 }
 
 // ---------------------------------------------------------------------------
-// load/store functors
+// kernels: one per (functor, direction, pass); every ring degree 2^10..2^15
 // ---------------------------------------------------------------------------
 
-struct IOPlain {
+#define FHE_NTT_DISPATCH(UNIT, LOGN, ...)                          \
+    switch (LOGN) {                                                \
+    case 10: UNIT<5, 5>(__VA_ARGS__); break;                       \
+    case 11: UNIT<6, 5>(__VA_ARGS__); break;                       \
+    case 12: UNIT<6, 6>(__VA_ARGS__); break;                       \
+    case 13: UNIT<7, 6>(__VA_ARGS__); break;                       \
+    case 14: UNIT<7, 7>(__VA_ARGS__); break;                       \
+    case 15: UNIT<8, 7>(__VA_ARGS__); break;                       \
+    default: break;                                                \
+    }
+
+// rows: n = 10 has fewer rows per limb than a single-job unit needs and
+// always takes the grouped form
+#define FHE_NTT_DISPATCH_G(UNIT, G, LOGN, ...)                     \
+    switch (LOGN) {                                                \
+    case 10: if (G) UNIT<5, 5, true>(__VA_ARGS__); break;          \
+    case 11: UNIT<6, 5, G>(__VA_ARGS__); break;                    \
+    case 12: UNIT<6, 6, G>(__VA_ARGS__); break;                    \
+    case 13: UNIT<7, 6, G>(__VA_ARGS__); break;                    \
+    case 14: UNIT<7, 7, G>(__VA_ARGS__); break;                    \
+    case 15: UNIT<8, 7, G>(__VA_ARGS__); break;                    \
+    default: break;                                                \
+    }
+
+template <class IO>
+__global__ void __launch_bounds__(T, FHE_NTT_MINB) k_fwd_cols(const __grid_constant__ IO io)
+{
+    __shared__ u64 sm[SM_WORDS];
+    __shared__ ulonglong2 W[TW_WORDS];
+    __shared__ typename IO::St sts[ROW_J];
+    for (int u = blockIdx.x; u < io.ucols; u += gridDim.x) {
+        const int sg = seg_of(io, u, false);
+        FHE_NTT_DISPATCH(fwd_cols_unit, io.h[sg].logN, io, sg, u - io.h[sg].u_cols, sm, W, sts);
+        __syncthreads();
+    }
+}
+
+template <class IO>
+__global__ void __launch_bounds__(T, FHE_NTT_MINB) k_fwd_rows(const __grid_constant__ IO io)
+{
+    __shared__ u64 sm[SM_WORDS];
+    __shared__ ulonglong2 W[TW_WORDS];
+    __shared__ typename IO::St sts[ROW_J];
+    for (int u = blockIdx.x; u < io.urows; u += gridDim.x) {
+        const int sg = seg_of(io, u, true);
+        if (io.h[sg].grouped) {
+            FHE_NTT_DISPATCH_G(fwd_rows_unit, true, io.h[sg].logN, io, sg, u - io.h[sg].u_rows, sm, W, sts);
+        } else {
+            FHE_NTT_DISPATCH_G(fwd_rows_unit, false, io.h[sg].logN, io, sg, u - io.h[sg].u_rows, sm, W, sts);
+        }
+        __syncthreads();
+    }
+}
+
+template <class IO>
+__global__ void __launch_bounds__(T, FHE_NTT_MINB) k_inv_rows(const __grid_constant__ IO io)
+{
+    __shared__ u64 sm[SM_WORDS];
+    __shared__ ulonglong2 W[TW_WORDS];
+    __shared__ typename IO::St sts[ROW_J];
+    for (int u = blockIdx.x; u < io.urows; u += gridDim.x) {
+        const int sg = seg_of(io, u, true);
+        if (io.h[sg].grouped) {
+            FHE_NTT_DISPATCH_G(inv_rows_unit, true, io.h[sg].logN, io, sg, u - io.h[sg].u_rows, sm, W, sts);
+        } else {
+            FHE_NTT_DISPATCH_G(inv_rows_unit, false, io.h[sg].logN, io, sg, u - io.h[sg].u_rows, sm, W, sts);
+        }
+        __syncthreads();
+    }
+}
+
+template <class IO>
+__global__ void __launch_bounds__(T, FHE_NTT_MINB) k_inv_cols(const __grid_constant__ IO io)
+{
+    __shared__ u64 sm[SM_WORDS];
+    __shared__ ulonglong2 W[TW_WORDS];
+    __shared__ typename IO::St sts[ROW_J];
+    for (int u = blockIdx.x; u < io.ucols; u += gridDim.x) {
+        const int sg = seg_of(io, u, false);
+        FHE_NTT_DISPATCH(inv_cols_unit, io.h[sg].logN, io, sg, u - io.h[sg].u_cols, sm, W, sts);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// load/store functors (one payload per segment)
+// ---------------------------------------------------------------------------
+
+// A limb map: job (o, l) reads limb in_limb[l] of outer item o and writes
+// limb out_limb[l]; prime[l]; the inverse's final scale is N^-1 times the
+// map entry's constant (scale[l], device) or plain N^-1.
+struct MapSeg {
     const u64 *in;
     u64 *out;
-    LimbMap m;
+    long long in_outer, out_outer;  // u64 elements
+    const ulonglong2 *scale;
+    uint8_t in_limb[FHE_MAXP], out_limb[FHE_MAXP], prime[FHE_MAXP];
+};
+
+struct IOMap : SegIO<MapSeg> {
     struct St {
         const u64 *in;
         u64 *out;
+        ulonglong2 fs;
         int prime;
     };
-    __device__ St begin(int job, int N) const
+    __device__ St begin(int sg, int job) const
     {
-        const int o = job / m.nl, l = job % m.nl;
-        St s;
-        s.in = in + o * m.in_outer + (long long)m.in_limb[l] * N;
-        s.out = out + o * m.out_outer + (long long)m.out_limb[l] * N;
-        s.prime = m.prime[l];
-        return s;
+        const SegHdr &H = h[sg];
+        const MapSeg &S = s[sg];
+        const int N = 1 << H.logN, o = job / H.nl, l = job % H.nl;
+        St t;
+        t.in = S.in + o * S.in_outer + (long long)S.in_limb[l] * N;
+        t.out = S.out + o * S.out_outer + (long long)S.out_limb[l] * N;
+        t.prime = S.prime[l];
+        t.fs = S.scale ? S.scale[l] : H.ninv[t.prime];
+        return t;
     }
-    __device__ u64 load(const St &s, int i) const { return s.in[i]; }
-    __device__ void store(const St &s, int i, u64 v) const { s.out[i] = v; }
-    static constexpr int NPRE = 0;  // operands the store reads
+    __device__ u64 load(const St &t, int i) const { return t.in[i]; }
+    __device__ void store(const St &t, int i, u64 v) const { t.out[i] = v; }
+    static constexpr int NPRE = 0;   // operands the store reads
     static constexpr int LDCH = 16;  // loads staged per chunk (0: not staged)
     __device__ u64 pre(const St &, int, int) const { return 0; }
-    __device__ void store_pre(const St &s, int i, u64 v, const u64 *) const { s.out[i] = v; }
-    __device__ u64 *inter(const St &s) const { return s.out; }
-    __device__ ulonglong2 final_scale(const St &s, const ulonglong2 *ninv) const { return ninv[s.prime]; }
-    int prime_stride() const { return m.nl; }  // jobs j and j + nl use one prime
+    __device__ void store_pre(const St &t, int i, u64 v, const u64 *) const { t.out[i] = v; }
+    __device__ u64 *inter(const St &t) const { return t.out; }
+    __device__ ulonglong2 final_scale(const St &t) const { return t.fs; }
 };
 
-// Inverse transform whose output limb l is also multiplied by a constant:
-// the final scaling uses N^-1 c_l (and its Shoup word) from scale[l].
-struct IOScaled {
-    const u64 *in;
-    u64 *out;
-    LimbMap m;
-    ulonglong2 scale[FHE_MAXP];
-    struct St {
-        const u64 *in;
-        u64 *out;
-        int prime, limb;
-    };
-    __device__ St begin(int job, int N) const
-    {
-        const int o = job / m.nl, l = job % m.nl;
-        St s;
-        s.in = in + o * m.in_outer + (long long)m.in_limb[l] * N;
-        s.out = out + o * m.out_outer + (long long)m.out_limb[l] * N;
-        s.prime = m.prime[l];
-        s.limb = l;
-        return s;
-    }
-    __device__ u64 load(const St &s, int i) const { return s.in[i]; }
-    __device__ void store(const St &s, int i, u64 v) const { s.out[i] = v; }
-    __device__ u64 *inter(const St &s) const { return s.out; }
-    __device__ ulonglong2 final_scale(const St &s, const ulonglong2 *) const { return scale[s.limb]; }
-    int prime_stride() const { return m.nl; }
-};
-
-// IOScaled whose last map entry (limb l-1 of the relinearisation
+// A scaled inverse whose last map entry (limb l-1 of the relinearisation
 // accumulators) loads y = acc + (P mod q) addend: the first step of the
 // relinearisation fused with the modulus switch.  Job = (ct, poly) * nl + entry.
-struct IOScaledY : IOScaled {
+struct YSeg : MapSeg {
     const u64 *abase;
     long long a_outer, a_poly;
     int amask, alimb;
     u64 Pm, Pm_s, qm;
-    struct St : IOScaled::St {
-        const u64 *add;
+};
+
+struct IOScaledY : SegIO<YSeg> {
+    struct St {
+        const u64 *in, *add;
+        u64 *out;
+        ulonglong2 fs;
+        u64 Pm, Pm_s, qm;
+        int prime;
     };
-    __device__ St begin(int job, int N) const
+    __device__ St begin(int sg, int job) const
     {
-        St s;
-        static_cast<IOScaled::St &>(s) = IOScaled::begin(job, N);
-        const int o = job / m.nl, e = job % m.nl, pi = o & 1;
+        const SegHdr &H = h[sg];
+        const YSeg &S = s[sg];
+        const int N = 1 << H.logN, o = job / H.nl, e = job % H.nl, pi = o & 1;
         const long long c = o >> 1;
-        s.add = (e == m.nl - 1 && ((amask >> pi) & 1)) ? abase + c * a_outer + pi * a_poly + (long long)alimb * N
-                                                      : nullptr;
-        return s;
+        St t;
+        t.in = S.in + o * S.in_outer + (long long)S.in_limb[e] * N;
+        t.out = S.out + o * S.out_outer + (long long)S.out_limb[e] * N;
+        t.prime = S.prime[e];
+        t.fs = S.scale[e];
+        t.add = (e == H.nl - 1 && ((S.amask >> pi) & 1)) ? S.abase + c * S.a_outer + pi * S.a_poly + (long long)S.alimb * N
+                                                          : nullptr;
+        t.Pm = S.Pm;
+        t.Pm_s = S.Pm_s;
+        t.qm = S.qm;
+        return t;
     }
-    __device__ u64 load(const St &s, int i) const
+    __device__ u64 load(const St &t, int i) const
     {
-        return s.add ? addmod(s.in[i], shoup(s.add[i], Pm, Pm_s, qm), qm) : s.in[i];
+        return t.add ? addmod(t.in[i], shoup(t.add[i], t.Pm, t.Pm_s, t.qm), t.qm) : t.in[i];
     }
+    __device__ void store(const St &t, int i, u64 v) const { t.out[i] = v; }
+    static constexpr int NPRE = 0;
+    static constexpr int LDCH = 16;
+    __device__ u64 pre(const St &, int, int) const { return 0; }
+    __device__ void store_pre(const St &t, int i, u64 v, const u64 *) const { t.out[i] = v; }
+    __device__ u64 *inter(const St &t) const { return t.out; }
+    __device__ ulonglong2 final_scale(const St &t) const { return t.fs; }
 };
 
 // ModUp: extended limb t of digit j of ct c:  y = sum_a t_a (Q_j/q_a) mod r,
 // where the source limbs already hold t_a = [x_a (Q_j/q_a)^-1]_{q_a} (the
-// inverse NTT that produced them applied that factor).
-struct IOModUp {
+// inverse NTT that produced them applied that factor).  Job = c * njobs + e
+// (entry e: digit, target limb, prime).
+struct ModUpSeg {
     const u64 *d2c;  // [count][l][N] coefficient domain
     u64 *ext;        // [count][dnum][l+K][N]
     const ModUpParams *P;
-    const ModQ *mq;
-    int l, K, dnum, njobs;
+    int l, K, dnum, pad;
+};
+
+struct IOModUp : SegIO<ModUpSeg> {
     struct St {
         const u64 *src;
         u64 *dst;
-        int nsrc, prime;
+        int nsrc, prime, N, pad;
         ModQ mt;
         u64 hat[FHE_MAXK];
     };
-    __device__ St begin(int job, int N) const
+    __device__ St begin(int sg, int job) const
     {
-        const int c = job / njobs, e = job % njobs;
-        const int j = P->job_digit[e], t = P->job_tgt[e];
-        St s;
+        const SegHdr &H = h[sg];
+        const ModUpSeg &S = s[sg];
+        const int N = 1 << H.logN, c = job / H.nl, e = job % H.nl;
+        const ModUpParams *P = S.P;
+        const int j = P->job_digit[e], tg = P->job_tgt[e];
+        St t;
         const int lo = P->digit_lo[j];
-        s.nsrc = P->digit_n[j];
-        s.src = d2c + ((long long)c * l + lo) * N;
-        s.dst = ext + (((long long)c * dnum + j) * (l + K) + t) * N;
-        s.prime = P->job_prime[e];
-        s.mt = mq[s.prime];
+        t.nsrc = P->digit_n[j];
+        t.N = N;
+        t.src = S.d2c + ((long long)c * S.l + lo) * N;
+        t.dst = S.ext + (((long long)c * S.dnum + j) * (S.l + S.K) + tg) * N;
+        t.prime = P->job_prime[e];
+        t.mt = H.mq[t.prime];
 #pragma unroll
         for (int a = 0; a < FHE_MAXK; a++)
-            if (a < s.nsrc) s.hat[a] = P->hat[j][a][t];
-        return s;
+            if (a < t.nsrc) t.hat[a] = P->hat[j][a][tg];
+        return t;
     }
-    __device__ u64 load(const St &s, int n) const
+    __device__ u64 load(const St &t, int n) const
     {
         u128 acc = 0;
 #pragma unroll
         for (int a = 0; a < FHE_MAXK; a++)
-            if (a < s.nsrc) acc += (u128)s.src[(long long)a * stride + n] * s.hat[a];
-        return barrett128(acc, s.mt);
+            if (a < t.nsrc) acc += (u128)t.src[(long long)a * t.N + n] * t.hat[a];
+        return barrett128(acc, t.mt);
     }
-    __device__ void store(const St &s, int k, u64 v) const { s.dst[k] = v; }
+    __device__ void store(const St &t, int k, u64 v) const { t.dst[k] = v; }
     static constexpr int NPRE = 0;
     static constexpr int LDCH = 0;  // each load already sums several limbs
     __device__ u64 pre(const St &, int, int) const { return 0; }
-    __device__ void store_pre(const St &s, int k, u64 v, const u64 *) const { s.dst[k] = v; }
-    __device__ u64 *inter(const St &s) const { return s.dst; }
-    int prime_stride() const { return njobs; }  // one entry per (digit, target) and ct
-    int stride;  // N
+    __device__ void store_pre(const St &t, int k, u64 v, const u64 *) const { t.dst[k] = v; }
+    __device__ u64 *inter(const St &t) const { return t.dst; }
+    __device__ ulonglong2 final_scale(const St &) const { return make_ulonglong2(0, 0); }
 };
 
 // ModDown of poly pi of ct c, data limb i:
 //   delta_i = sum_k t_k * (p P/p_k mod q_i),  out_i = (acc_i - delta_i) P^-1 + addend_i,
 // where the special limbs already hold t_k = [acc_{P,k} p^-1 (P/p_k)^-1]_{p_k}
-// (applied by the inverse NTT that produced them).
-struct IOModDown {
+// (applied by the inverse NTT that produced them).  Job = (c, pi) * l + i.
+struct ModDownSeg {
     const u64 *accP;  // [count][2][K][N] coefficient domain
     const u64 *acc;   // [count][2][l+K][N] NTT domain
     const u64 *abase;
     long long a_outer, a_poly;
-    int amask;
     u64 *out;         // [count][2][l][N]
     const ModDownParams *P;
-    const ModQ *mq;
-    int l, K, stride;
+    int l, K, amask, pad;
+};
+
+struct IOModDown : SegIO<ModDownSeg> {
     struct St {
         const u64 *w, *acc, *add;
         u64 *out;
-        int prime;
+        int prime, K, N, pad;
         ModQ mi;
         u64 pinv, pinv_s;
         u64 phat[FHE_MAXK];
     };
-    __device__ St begin(int job, int N) const
+    __device__ St begin(int sg, int job) const
     {
+        const SegHdr &H = h[sg];
+        const ModDownSeg &S = s[sg];
+        const int N = 1 << H.logN, l = S.l, K = S.K;
         const int c = job / (2 * l), pi = (job / l) % 2, i = job % l;
-        St s;
-        s.w = accP + ((long long)c * 2 + pi) * K * N;
-        s.acc = acc + (((long long)c * 2 + pi) * (l + K) + i) * N;
-        s.add = ((amask >> pi) & 1) ? abase + c * a_outer + pi * a_poly + (long long)i * N : nullptr;
-        s.out = out + (((long long)c * 2 + pi) * l + i) * N;
-        s.prime = i;
-        s.mi = mq[i];
-        s.pinv = P->pinv[i];
-        s.pinv_s = P->pinv_s[i];
+        St t;
+        t.w = S.accP + ((long long)c * 2 + pi) * K * N;
+        t.acc = S.acc + (((long long)c * 2 + pi) * (l + K) + i) * N;
+        t.add = ((S.amask >> pi) & 1) ? S.abase + c * S.a_outer + pi * S.a_poly + (long long)i * N : nullptr;
+        t.out = S.out + (((long long)c * 2 + pi) * l + i) * N;
+        t.prime = i;
+        t.K = K;
+        t.N = N;
+        t.mi = H.mq[i];
+        t.pinv = S.P->pinv[i];
+        t.pinv_s = S.P->pinv_s[i];
 #pragma unroll
         for (int k = 0; k < FHE_MAXK; k++)
-            if (k < K) s.phat[k] = P->phat[k][i];
-        return s;
+            if (k < K) t.phat[k] = S.P->phat[k][i];
+        return t;
     }
-    __device__ u64 load(const St &s, int n) const
+    __device__ u64 load(const St &t, int n) const
     {
         u128 a = 0;
 #pragma unroll
         for (int k = 0; k < FHE_MAXK; k++)
-            if (k < K) a += (u128)s.w[(long long)k * stride + n] * s.phat[k];
-        return barrett128(a, s.mi);
+            if (k < t.K) a += (u128)t.w[(long long)k * t.N + n] * t.phat[k];
+        return barrett128(a, t.mi);
     }
-    __device__ void store(const St &s, int k, u64 v) const
+    __device__ void store(const St &t, int k, u64 v) const
     {
-        const u64 q = s.mi.q;
-        u64 r = shoup(submod(s.acc[k], v, q), s.pinv, s.pinv_s, q);
-        if (s.add) r = addmod(r, s.add[k], q);
-        s.out[k] = r;
+        const u64 q = t.mi.q;
+        u64 r = shoup(submod(t.acc[k], v, q), t.pinv, t.pinv_s, q);
+        if (t.add) r = addmod(r, t.add[k], q);
+        t.out[k] = r;
     }
     static constexpr int NPRE = 2;  // accumulator, addend
     static constexpr int LDCH = 16;
-    __device__ u64 pre(const St &s, int k, int w) const { return w == 0 ? s.acc[k] : (s.add ? s.add[k] : 0); }
-    __device__ void store_pre(const St &s, int k, u64 v, const u64 *pv) const
+    __device__ u64 pre(const St &t, int k, int w) const { return w == 0 ? t.acc[k] : (t.add ? t.add[k] : 0); }
+    __device__ void store_pre(const St &t, int k, u64 v, const u64 *pv) const
     {
-        const u64 q = s.mi.q;
-        u64 r = shoup(submod(pv[0], v, q), s.pinv, s.pinv_s, q);
-        if (s.add) r = addmod(r, pv[1], q);
-        s.out[k] = r;
+        const u64 q = t.mi.q;
+        u64 r = shoup(submod(pv[0], v, q), t.pinv, t.pinv_s, q);
+        if (t.add) r = addmod(r, pv[1], q);
+        t.out[k] = r;
     }
-    __device__ u64 *inter(const St &s) const { return s.out; }
-    int prime_stride() const { return l; }  // job = (ct, poly) * l + limb
+    __device__ u64 *inter(const St &t) const { return t.out; }
+    __device__ ulonglong2 final_scale(const St &) const { return make_ulonglong2(0, 0); }
 };
 
 // Modulus switch l -> l-1 of poly pi of ct c, limb i < l-1:
 //   delta_i = p w mod q_i,  out_i = (x_i - delta_i) q_{l-1}^-1,
 // where `last` already holds w = [x_{l-1} p^-1]_{q_{l-1}} in the coefficient
 // domain (applied by the inverse NTT that produced it).
-struct IOModSwitch {
+// Job = (c, pi) * (l-1) + i.
+struct SwitchSeg {
     const u64 *last;  // [count][npoly][N] coefficient domain
     const u64 *in;    // [count][npoly][l][N]
     u64 *out;         // [count][npoly][l-1][N]
     const ModSwitchParams *P;
-    const ModQ *mq;
     int l, npoly;
+};
+
+struct IOModSwitch : SegIO<SwitchSeg> {
     struct St {
         const u64 *last, *in;
         u64 *out;
-        int prime;
-        u64 q, ql, pl, pls, pi, pis, qi, qis;
+        int prime, pad;
+        u64 q, pi, pis, qi, qis;
     };
-    __device__ St begin(int job, int N) const
+    __device__ St begin(int sg, int job) const
     {
-        const int c = job / (npoly * (l - 1)), pi = (job / (l - 1)) % npoly, i = job % (l - 1);
-        St s;
-        s.last = last + ((long long)c * npoly + pi) * N;
-        s.in = in + (((long long)c * npoly + pi) * l + i) * N;
-        s.out = out + (((long long)c * npoly + pi) * (l - 1) + i) * N;
-        s.prime = i;
-        s.q = mq[i].q;
-        s.ql = mq[l - 1].q;
-        s.pl = P->pinv_last;
-        s.pls = P->pinv_last_s;
-        s.pi = P->p_i[i];
-        s.pis = P->p_i_s[i];
-        s.qi = P->qinv[i];
-        s.qis = P->qinv_s[i];
-        return s;
+        const SegHdr &H = h[sg];
+        const SwitchSeg &S = s[sg];
+        const int N = 1 << H.logN, l = S.l, np = S.npoly;
+        const int c = job / (np * (l - 1)), pi = (job / (l - 1)) % np, i = job % (l - 1);
+        St t;
+        t.last = S.last + ((long long)c * np + pi) * N;
+        t.in = S.in + (((long long)c * np + pi) * l + i) * N;
+        t.out = S.out + (((long long)c * np + pi) * (l - 1) + i) * N;
+        t.prime = i;
+        t.q = H.mq[i].q;
+        t.pi = S.P->p_i[i];
+        t.pis = S.P->p_i_s[i];
+        t.qi = S.P->qinv[i];
+        t.qis = S.P->qinv_s[i];
+        return t;
     }
-    __device__ u64 load(const St &s, int n) const { return shoup(s.last[n], s.pi, s.pis, s.q); }
-    __device__ void store(const St &s, int k, u64 v) const
-    {
-        s.out[k] = shoup(submod(s.in[k], v, s.q), s.qi, s.qis, s.q);
-    }
+    __device__ u64 load(const St &t, int n) const { return shoup(t.last[n], t.pi, t.pis, t.q); }
+    __device__ void store(const St &t, int k, u64 v) const { t.out[k] = shoup(submod(t.in[k], v, t.q), t.qi, t.qis, t.q); }
     static constexpr int NPRE = 1;  // the limb being switched
     static constexpr int LDCH = 16;
-    __device__ u64 pre(const St &s, int k, int) const { return s.in[k]; }
-    __device__ void store_pre(const St &s, int k, u64 v, const u64 *pv) const
+    __device__ u64 pre(const St &t, int k, int) const { return t.in[k]; }
+    __device__ void store_pre(const St &t, int k, u64 v, const u64 *pv) const
     {
-        s.out[k] = shoup(submod(pv[0], v, s.q), s.qi, s.qis, s.q);
+        t.out[k] = shoup(submod(pv[0], v, t.q), t.qi, t.qis, t.q);
     }
-    __device__ u64 *inter(const St &s) const { return s.out; }
-    int prime_stride() const { return l - 1; }  // job = (ct, poly) * (l-1) + limb
+    __device__ u64 *inter(const St &t) const { return t.out; }
+    __device__ ulonglong2 final_scale(const St &) const { return make_ulonglong2(0, 0); }
 };
 
 // Relinearisation fused with the modulus switch that follows it (l -> l-1)
@@ -840,495 +1016,490 @@ struct IOModSwitch {
 //   correction_i = sum_{k<K} t_k h[k][i] + w h[K][i] (coefficient domain),
 //   out_i = (acc_i P^-1 + add_i - NTT(correction)_i) q_{l-1}^-1,
 // where src holds t_0..t_{K-1} (the special limbs, already scaled) and w.
-struct IORelinMS {
+// Job = (c, pi) * (l-1) + i.
+struct RelinMSSeg {
     const u64 *src;  // [count][2][K+1][N] coefficient domain
     const u64 *acc;  // [count][2][l+K][N] NTT domain
     const u64 *abase;
     long long a_outer, a_poly;
-    int amask;
     u64 *out;        // [count][2][l-1][N]
     const RelinMSParams *P;
-    const ModQ *mq;
-    int l, K, stride;
+    int l, K, amask, pad;
+};
+
+struct IORelinMS : SegIO<RelinMSSeg> {
     struct St {
         const u64 *w, *acc, *add;
         u64 *out;
-        int prime;
+        int prime, K, N, pad;
         ModQ mi;
         u64 pinv, pinv_s, qminv, qminv_s;
         u64 h[FHE_MAXK];
     };
-    __device__ St begin(int job, int N) const
+    __device__ St begin(int sg, int job) const
     {
-        const int m = l - 1;
+        const SegHdr &H = h[sg];
+        const RelinMSSeg &S = s[sg];
+        const int N = 1 << H.logN, l = S.l, K = S.K, m = l - 1;
         const int c = job / (2 * m), pi = (job / m) % 2, i = job % m;
-        St s;
-        s.w = src + ((long long)c * 2 + pi) * (K + 1) * N;
-        s.acc = acc + (((long long)c * 2 + pi) * (l + K) + i) * N;
-        s.add = ((amask >> pi) & 1) ? abase + c * a_outer + pi * a_poly + (long long)i * N : nullptr;
-        s.out = out + (((long long)c * 2 + pi) * m + i) * N;
-        s.prime = i;
-        s.mi = mq[i];
-        s.pinv = P->pinv[i];
-        s.pinv_s = P->pinv_s[i];
-        s.qminv = P->qminv[i];
-        s.qminv_s = P->qminv_s[i];
+        St t;
+        t.w = S.src + ((long long)c * 2 + pi) * (K + 1) * N;
+        t.acc = S.acc + (((long long)c * 2 + pi) * (l + K) + i) * N;
+        t.add = ((S.amask >> pi) & 1) ? S.abase + c * S.a_outer + pi * S.a_poly + (long long)i * N : nullptr;
+        t.out = S.out + (((long long)c * 2 + pi) * m + i) * N;
+        t.prime = i;
+        t.K = K;
+        t.N = N;
+        t.mi = H.mq[i];
+        t.pinv = S.P->pinv[i];
+        t.pinv_s = S.P->pinv_s[i];
+        t.qminv = S.P->qminv[i];
+        t.qminv_s = S.P->qminv_s[i];
 #pragma unroll
         for (int k = 0; k < FHE_MAXK; k++)
-            if (k <= K) s.h[k] = P->h[k][i];
-        return s;
+            if (k <= K) t.h[k] = S.P->h[k][i];
+        return t;
     }
     // K + 1 <= FHE_MAXK products of canonical residues: below 2^(2b+3)
-    __device__ u64 load(const St &s, int n) const
+    __device__ u64 load(const St &t, int n) const
     {
         u128 a = 0;
 #pragma unroll
         for (int k = 0; k < FHE_MAXK; k++)
-            if (k <= K) a += (u128)s.w[(long long)k * stride + n] * s.h[k];
-        return barrett128(a, s.mi);
+            if (k <= t.K) a += (u128)t.w[(long long)k * t.N + n] * t.h[k];
+        return barrett128(a, t.mi);
     }
-    __device__ u64 combine(const St &s, u64 accv, u64 addv, u64 v) const
+    __device__ u64 combine(const St &t, u64 accv, u64 addv, u64 v) const
     {
-        const u64 q = s.mi.q;
-        u64 t = shoup(accv, s.pinv, s.pinv_s, q);
-        if (s.add) t = addmod(t, addv, q);
-        return shoup(submod(t, v, q), s.qminv, s.qminv_s, q);
+        const u64 q = t.mi.q;
+        u64 r = shoup(accv, t.pinv, t.pinv_s, q);
+        if (t.add) r = addmod(r, addv, q);
+        return shoup(submod(r, v, q), t.qminv, t.qminv_s, q);
     }
-    __device__ void store(const St &s, int k, u64 v) const
-    {
-        s.out[k] = combine(s, s.acc[k], s.add ? s.add[k] : 0, v);
-    }
+    __device__ void store(const St &t, int k, u64 v) const { t.out[k] = combine(t, t.acc[k], t.add ? t.add[k] : 0, v); }
     static constexpr int NPRE = 2;  // accumulator, addend
     static constexpr int LDCH = 0;  // each load sums K + 1 limbs
-    __device__ u64 pre(const St &s, int k, int w) const { return w == 0 ? s.acc[k] : (s.add ? s.add[k] : 0); }
-    __device__ void store_pre(const St &s, int k, u64 v, const u64 *pv) const
-    {
-        s.out[k] = combine(s, pv[0], pv[1], v);
-    }
-    __device__ u64 *inter(const St &s) const { return s.out; }
-    int prime_stride() const { return l - 1; }  // job = (ct, poly) * (l-1) + limb
+    __device__ u64 pre(const St &t, int k, int w) const { return w == 0 ? t.acc[k] : (t.add ? t.add[k] : 0); }
+    __device__ void store_pre(const St &t, int k, u64 v, const u64 *pv) const { t.out[k] = combine(t, pv[0], pv[1], v); }
+    __device__ u64 *inter(const St &t) const { return t.out; }
+    __device__ ulonglong2 final_scale(const St &) const { return make_ulonglong2(0, 0); }
 };
 
 // k modulus switches at once (l -> l-k), poly pi of ct c, kept limb i < l-k:
 //   correction_i = sum_{t<k} w_t G[t][i],  out_i = (x_i - NTT(correction)_i) D_k^-1.
-struct IOMultiSwitch {
+// Job = (c, pi) * (l-k) + i.
+struct MultiSeg {
     const u64 *src;  // [count][npoly][k][N] coefficient domain: w_0 .. w_{k-1}
     const u64 *in;   // [count][npoly][l][N]
     u64 *out;        // [count][npoly][l-k][N]
     const MultiSwitchParams *P;
-    const ModQ *mq;
-    int l, k, npoly, stride;
+    int l, k, npoly, pad;
+};
+
+struct IOMultiSwitch : SegIO<MultiSeg> {
     struct St {
         const u64 *w, *in;
         u64 *out;
-        int prime;
+        int prime, k, N, pad;
         ModQ mi;
         u64 dinv, dinv_s;
         u64 g[FHE_MAXK];
     };
-    __device__ St begin(int job, int N) const
+    __device__ St begin(int sg, int job) const
     {
-        const int kept = l - k;
-        const int c = job / (npoly * kept), pi = (job / kept) % npoly, i = job % kept;
-        St s;
-        s.w = src + ((long long)c * npoly + pi) * k * N;
-        s.in = in + (((long long)c * npoly + pi) * l + i) * N;
-        s.out = out + (((long long)c * npoly + pi) * kept + i) * N;
-        s.prime = i;
-        s.mi = mq[i];
-        s.dinv = P->Dinv[i];
-        s.dinv_s = P->Dinv_s[i];
+        const SegHdr &H = h[sg];
+        const MultiSeg &S = s[sg];
+        const int N = 1 << H.logN, kept = S.l - S.k, np = S.npoly;
+        const int c = job / (np * kept), pi = (job / kept) % np, i = job % kept;
+        St t;
+        t.w = S.src + ((long long)c * np + pi) * S.k * N;
+        t.in = S.in + (((long long)c * np + pi) * S.l + i) * N;
+        t.out = S.out + (((long long)c * np + pi) * kept + i) * N;
+        t.prime = i;
+        t.k = S.k;
+        t.N = N;
+        t.mi = H.mq[i];
+        t.dinv = S.P->Dinv[i];
+        t.dinv_s = S.P->Dinv_s[i];
 #pragma unroll
-        for (int t = 0; t < FHE_MAXK; t++)
-            if (t < k) s.g[t] = P->G[t][i];
-        return s;
+        for (int j = 0; j < FHE_MAXK; j++)
+            if (j < S.k) t.g[j] = S.P->G[j][i];
+        return t;
     }
-    __device__ u64 load(const St &s, int n) const
+    __device__ u64 load(const St &t, int n) const
     {
         u128 a = 0;
 #pragma unroll
-        for (int t = 0; t < FHE_MAXK; t++)
-            if (t < k) a += (u128)s.w[(long long)t * stride + n] * s.g[t];
-        return barrett128(a, s.mi);
+        for (int j = 0; j < FHE_MAXK; j++)
+            if (j < t.k) a += (u128)t.w[(long long)j * t.N + n] * t.g[j];
+        return barrett128(a, t.mi);
     }
-    __device__ void store(const St &s, int j, u64 v) const
+    __device__ void store(const St &t, int j, u64 v) const
     {
-        s.out[j] = shoup(submod(s.in[j], v, s.mi.q), s.dinv, s.dinv_s, s.mi.q);
+        t.out[j] = shoup(submod(t.in[j], v, t.mi.q), t.dinv, t.dinv_s, t.mi.q);
     }
     static constexpr int NPRE = 1;
     static constexpr int LDCH = 0;
-    __device__ u64 pre(const St &s, int j, int) const { return s.in[j]; }
-    __device__ void store_pre(const St &s, int j, u64 v, const u64 *pv) const
+    __device__ u64 pre(const St &t, int j, int) const { return t.in[j]; }
+    __device__ void store_pre(const St &t, int j, u64 v, const u64 *pv) const
     {
-        s.out[j] = shoup(submod(pv[0], v, s.mi.q), s.dinv, s.dinv_s, s.mi.q);
+        t.out[j] = shoup(submod(pv[0], v, t.mi.q), t.dinv, t.dinv_s, t.mi.q);
     }
-    __device__ u64 *inter(const St &s) const { return s.out; }
-    int prime_stride() const { return l - k; }
+    __device__ u64 *inter(const St &t) const { return t.out; }
+    __device__ ulonglong2 final_scale(const St &) const { return make_ulonglong2(0, 0); }
 };
 
 // ---------------------------------------------------------------------------
-// one-launch NTT for square splits N = 2^M x 2^M (M = 5, 6, 7)
+// host side: unit counts, grids, launches
 // ---------------------------------------------------------------------------
-//
-// A cluster of CL = 2^M / 16 CTAs holds one limb.  Forward: CTA k transforms
-// columns 16k .. 16k+15 (global stages 0..M-1), writes each element (row e,
-// column 16k + c) into the shared memory of CTA e / 16 (distributed shared
-// memory), and after one cluster barrier transforms rows 16k .. 16k+15
-// (stages M..2M-1).  Inverse: rows first, then columns.  The half-transformed
-// limb never leaves the cluster, and the transform is one launch.  Every CTA
-// runs the same two barriers (no early exit), and no CTA touches another's
-// shared memory after the second one.
 
-__device__ __forceinline__ void cluster_arrive_relaxed()
+struct Split {
+    int n1, n2, ns1, ns2;
+};
+
+Split split_of(int logN)
 {
-    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+    Split s;
+    s.n1 = (logN + 1) / 2;
+    s.n2 = logN / 2;
+    s.ns1 = 2048 >> s.n1;
+    s.ns2 = 2048 >> s.n2;
+    return s;
 }
 
-__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
+// Row units are grouped (16 jobs of one prime) once a segment has at least
+// this many outer items; below it a unit holds adjacent rows of one job.
+constexpr int GROUP_MIN_OUTER = 12;
 
-template <int M, class IO>
-__global__ void __cluster_dims__((1 << M) / 16, 1, 1) __launch_bounds__(Sub<M>::T, FHE_MINB(Sub<M>::T))
-    k_fwd_fused(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw)
+// Fills the header of segment `sg` (jobs = outer * nl) and its unit counts.
+void seg_header(SegHdr &H, const fhe_ctx *c, bool fwd, int outer, int nl)
 {
-    using C = Sub<M>;
-    constexpr int CL = (1 << M) / 16, NN = 1 << (2 * M);
-    __shared__ u64 sm[C::WORDS];   // columns 16k .. 16k+15, all rows
-    __shared__ u64 sm2[C::WORDS];  // rows 16k .. 16k+15, all columns (written by the cluster)
-    __shared__ ulonglong2 W[twp_size(1 << M)];
-    cg::cluster_group cluster = cg::this_cluster();
-    cluster_arrive_relaxed();  // matched by cluster_wait before the first remote write
-    const int k = (int)cluster.block_rank();
-    const int job = blockIdx.x / CL, lo0 = 16 * k, hi0 = 16 * k, tid = threadIdx.x;
-    const typename IO::St st = io.begin(job, NN);
-    const u64 q = mq[st.prime].q, q2 = 2 * q;
-    for (int r = tid; r < (1 << M); r += C::T) W[twp(r)] = tw[(size_t)st.prime * NN + r];
-    tile_in<C, IO::LDCH>(
-        tid, [&](int r) { return io.load(st, ((r >> 4) << M) + lo0 + (r & 15)); },
-        [&](int r, u64 v) { sm[C::at(r & 15, r >> 4)] = v; });
-    __syncthreads();
-    sub16<M, true>(sm, tid, PrefixTw{W}, 0, 0, 0, q, q2);
-    __syncthreads();
-    cluster_wait();
-    for (int r = tid; r < 16 * C::SZ; r += C::T) {
-        const int c = r & 15, e = r >> 4;
-        u64 *dst = cluster.map_shared_rank(sm2, e >> 4);
-        dst[C::at(e & 15, lo0 + c)] = sm[C::at(c, e)];
-    }
-    cluster.sync();
-    sub16<M, true>(sm2, tid, GTw{tw + (size_t)st.prime * NN}, M, hi0, 1, q, q2);
-    __syncthreads();
-    const ModQ mqp = mq[st.prime];
-    tile_out<C>(
-        io, tid, [&](int) -> const typename IO::St & { return st; }, [&](int r) { return (hi0 << M) + r; },
-        [&](int r) { return reduce64(sm2[C::at(r >> M, r & (C::SZ - 1))], mqp); });
-}
-
-template <int M, class IO>
-__global__ void __cluster_dims__((1 << M) / 16, 1, 1) __launch_bounds__(Sub<M>::T, FHE_MINB(Sub<M>::T))
-    k_inv_fused(const __grid_constant__ IO io, const ModQ *__restrict__ mq, const ulonglong2 *__restrict__ tw,
-                const ulonglong2 *__restrict__ ninv)
-{
-    using C = Sub<M>;
-    constexpr int CL = (1 << M) / 16, NN = 1 << (2 * M);
-    __shared__ u64 sm[C::WORDS];   // rows 16k .. 16k+15
-    __shared__ u64 sm2[C::WORDS];  // columns 16k .. 16k+15 (written by the cluster)
-    __shared__ ulonglong2 W[twp_size(1 << M)];
-    cg::cluster_group cluster = cg::this_cluster();
-    cluster_arrive_relaxed();
-    const int k = (int)cluster.block_rank();
-    const int job = blockIdx.x / CL, lo0 = 16 * k, hi0 = 16 * k, tid = threadIdx.x;
-    const typename IO::St st = io.begin(job, NN);
-    const u64 q = mq[st.prime].q, q2 = 2 * q;
-    for (int r = tid; r < (1 << M); r += C::T) W[twp(r)] = tw[(size_t)st.prime * NN + r];
-    const ulonglong2 ni = io.final_scale(st, ninv);
-    tile_in<C>(
-        tid, [&](int r) { return io.load(st, (hi0 << M) + r); },
-        [&](int r, u64 v) { sm[C::at(r >> M, r & (C::SZ - 1))] = v; });
-    __syncthreads();
-    sub16<M, false>(sm, tid, GTw{tw + (size_t)st.prime * NN}, M, hi0, 1, q, q2);
-    __syncthreads();
-    cluster_wait();
-    // element (row hi0 + rl, column f) goes to CTA f / 16 as its column f % 16
-    for (int r = tid; r < 16 * C::SZ; r += C::T) {
-        const int rl = r & 15, f = r >> 4;
-        u64 *dst = cluster.map_shared_rank(sm2, f >> 4);
-        dst[C::at(f & 15, hi0 + rl)] = sm[C::at(rl, f)];
-    }
-    cluster.sync();
-    sub16<M, false>(sm2, tid, PrefixTw{W}, 0, 0, 0, q, q2);
-    __syncthreads();
-    for (int r = tid; r < 16 * C::SZ; r += C::T) {
-        const int c = r & 15, e = r >> 4;
-        io.store(st, (e << M) + lo0 + c, reduce2q(shoup_lazy(sm2[C::at(c, e)], ni.x, ni.y, q), q));
-    }
-}
-
-template <int M, class IO>
-void fwd_fused(fhe_ctx *c, const IO &io, int njobs)
-{
-    k_fwd_fused<M, IO><<<njobs * ((1 << M) / 16), Sub<M>::T, 0, c->stream>>>(io, c->d_mq, c->d_fwd);
-}
-
-template <int M, class IO>
-void inv_fused(fhe_ctx *c, const IO &io, int njobs)
-{
-    k_inv_fused<M, IO><<<njobs * ((1 << M) / 16), Sub<M>::T, 0, c->stream>>>(io, c->d_mq, c->d_inv, c->d_ninv);
-}
-
-// Row kernels take the grouped form when every prime of the launch has a
-// multiple of 16 jobs (the batched case); otherwise 16 rows of one limb.
-template <class IO>
-bool groupable(const IO &io, int njobs)
-{
-    const int st = io.prime_stride();
-    return st > 0 && njobs % st == 0 && (njobs / st) % 16 == 0;
-}
-
-template <int N1, int N2, class IO, int V = 16>
-void fwd_pair(fhe_ctx *c, const IO &io, int njobs)
-{
-    constexpr int T1 = SubSel<N1, V>::type::T, T2 = SubSel<N2, V>::type::T;
-    k_fwd_cols<N1, N2, IO, V><<<njobs * ((1 << N2) / 16), T1, 0, c->stream>>>(io, c->d_mq, c->d_fwd);
-    if (groupable(io, njobs))
-        k_fwd_rows_grp<N1, N2, IO, V><<<(njobs / 16) * (1 << N1), T2, 0, c->stream>>>(io, c->d_mq, c->d_fwd,
-                                                                                      io.prime_stride());
+    memset(&H, 0, sizeof(H));
+    const Split sp = split_of(c->logN);
+    H.logN = c->logN;
+    H.outer = outer;
+    H.nl = nl;
+    H.mq = c->d_mq;
+    H.tw = fwd ? c->d_fwd : c->d_inv;
+    H.ninv = c->d_ninv;
+    const int njobs = outer * nl;
+    const int nc = std::min(sp.ns1, 1 << sp.n2), nj = sp.ns1 / nc, blk = (1 << sp.n2) / nc;
+    H.u_cols = ((njobs + nj - 1) / nj) * blk;  // counts; turned into prefixes by finish()
+    H.grouped = outer >= GROUP_MIN_OUTER || (1 << sp.n1) < sp.ns2;
+    if (H.grouped)
+        H.u_rows = nl * ((outer + ROW_J - 1) / ROW_J) * ((1 << sp.n1) / (sp.ns2 / ROW_J));
     else
-        k_fwd_rows<N1, N2, IO, V><<<njobs * ((1 << N1) / 16), T2, 0, c->stream>>>(io, c->d_mq, c->d_fwd);
+        H.u_rows = njobs * ((1 << sp.n1) / sp.ns2);
 }
 
-template <int N1, int N2, class IO, int V = 16>
-void inv_pair(fhe_ctx *c, const IO &io, int njobs)
+// Grid of a pass: one CTA per unit (variant 0) or a fixed number of resident
+// CTAs per SM that walk the units (variants 1..3: 6, 4 and 2 per SM).
+int grid_of(const fhe_ctx *c, int units)
 {
-    constexpr int T1 = SubSel<N1, V>::type::T, T2 = SubSel<N2, V>::type::T;
-    if (groupable(io, njobs))
-        k_inv_rows_grp<N1, N2, IO, V><<<(njobs / 16) * (1 << N1), T2, 0, c->stream>>>(io, c->d_mq, c->d_inv,
-                                                                                      io.prime_stride());
-    else
-        k_inv_rows<N1, N2, IO, V><<<njobs * ((1 << N1) / 16), T2, 0, c->stream>>>(io, c->d_mq, c->d_inv);
-    k_inv_cols<N1, N2, IO, V><<<njobs * ((1 << N2) / 16), T1, 0, c->stream>>>(io, c->d_mq, c->d_inv, c->d_ninv);
-}
-
-// Factorisations N = 2^n1 x 2^n2 per ring degree (the autotuner picks one
-// per context; all compute the same transform): variant 0 and 1 are the two
-// two-kernel splits, variant 2 the one-launch cluster form of a square split,
-// variant 3 variant 0's split with 8 elements per thread (twice the warps).
-// Returns the number of kernels launched.
-template <class IO>
-int fwd_dispatch(fhe_ctx *c, const IO &io, int njobs)
-{
+    static const int per_sm[FHE_NTT_VARIANTS] = {0, 6, 4, 2};
     const int v = c->ntt_variant;
-    switch (c->logN) {
-    case 10: if (v == 2) return fwd_fused<5>(c, io, njobs), 1;
-        fwd_pair<5, 5>(c, io, njobs); return 2;
-    case 11: v ? fwd_pair<5, 6>(c, io, njobs) : fwd_pair<6, 5>(c, io, njobs); return 2;
-    case 12: if (v == 2) return fwd_fused<6>(c, io, njobs), 1;
-        if (v == 3) return fwd_pair<6, 6, IO, 8>(c, io, njobs), 2;
-        v ? fwd_pair<7, 5>(c, io, njobs) : fwd_pair<6, 6>(c, io, njobs); return 2;
-    case 13: if (v == 3) return fwd_pair<7, 6, IO, 8>(c, io, njobs), 2;
-        v ? fwd_pair<6, 7>(c, io, njobs) : fwd_pair<7, 6>(c, io, njobs); return 2;
-    case 14: if (v == 2) return fwd_fused<7>(c, io, njobs), 1;
-        if (v == 3) return fwd_pair<7, 7, IO, 8>(c, io, njobs), 2;
-        v ? fwd_pair<8, 6>(c, io, njobs) : fwd_pair<7, 7>(c, io, njobs); return 2;
-    case 15: if (v == 3) return fwd_pair<8, 7, IO, 8>(c, io, njobs), 2;
-        v ? fwd_pair<7, 8>(c, io, njobs) : fwd_pair<8, 7>(c, io, njobs); return 2;
-    default: return 0;
-    }
+    if (v <= 0 || v >= FHE_NTT_VARIANTS || c->sms <= 0) return units;
+    return std::min(units, per_sm[v] * c->sms);
 }
 
 template <class IO>
-int inv_dispatch(fhe_ctx *c, const IO &io, int njobs)
+void finish(IO &io)
 {
-    const int v = c->ntt_variant;
-    switch (c->logN) {
-    case 10: if (v == 2) return inv_fused<5>(c, io, njobs), 1;
-        inv_pair<5, 5>(c, io, njobs); return 2;
-    case 11: v ? inv_pair<5, 6>(c, io, njobs) : inv_pair<6, 5>(c, io, njobs); return 2;
-    case 12: if (v == 2) return inv_fused<6>(c, io, njobs), 1;
-        if (v == 3) return inv_pair<6, 6, IO, 8>(c, io, njobs), 2;
-        v ? inv_pair<7, 5>(c, io, njobs) : inv_pair<6, 6>(c, io, njobs); return 2;
-    case 13: if (v == 3) return inv_pair<7, 6, IO, 8>(c, io, njobs), 2;
-        v ? inv_pair<6, 7>(c, io, njobs) : inv_pair<7, 6>(c, io, njobs); return 2;
-    case 14: if (v == 2) return inv_fused<7>(c, io, njobs), 1;
-        if (v == 3) return inv_pair<7, 7, IO, 8>(c, io, njobs), 2;
-        v ? inv_pair<8, 6>(c, io, njobs) : inv_pair<7, 7>(c, io, njobs); return 2;
-    case 15: if (v == 3) return inv_pair<8, 7, IO, 8>(c, io, njobs), 2;
-        v ? inv_pair<7, 8>(c, io, njobs) : inv_pair<8, 7>(c, io, njobs); return 2;
-    default: return 0;
+    int uc = 0, ur = 0;
+    for (int s = 0; s < io.nseg; s++) {
+        const int nc = io.h[s].u_cols, nr = io.h[s].u_rows;
+        io.h[s].u_cols = uc;
+        io.h[s].u_rows = ur;
+        uc += nc;
+        ur += nr;
     }
+    io.ucols = uc;
+    io.urows = ur;
 }
 
-// words_per_job: u64 words of global traffic per limb job (algorithmic: the
-// transform reads and writes each limb once; fused variants add their operands)
+// Launches both passes of the segments in io on the stream of `c` (the
+// first segment's context).  bytes / bfly: algorithmic traffic and butterflies
+// of the whole launch, for the per-class timing.
 template <class IO>
-void run_fwd(fhe_ctx *c, const IO &io, int njobs, int cls, double words_per_job = 2.0)
+void run(fhe_ctx *c, IO &io, bool fwd, int cls, double bytes, double bfly)
 {
-    if (njobs <= 0) return;
-    prof_begin(c, cls, 8.0 * words_per_job * c->N * njobs, (double)njobs * (c->N / 2) * c->logN);
-    c->launches += fwd_dispatch(c, io, njobs);
+    if (io.nseg == 0) return;
+    finish(io);
+    if (io.ucols == 0) return;
+    prof_begin(c, cls, bytes, bfly);
+    if (fwd) {
+        k_fwd_cols<IO><<<grid_of(c, io.ucols), T, 0, c->stream>>>(io);
+        k_fwd_rows<IO><<<grid_of(c, io.urows), T, 0, c->stream>>>(io);
+    } else {
+        k_inv_rows<IO><<<grid_of(c, io.urows), T, 0, c->stream>>>(io);
+        k_inv_cols<IO><<<grid_of(c, io.ucols), T, 0, c->stream>>>(io);
+    }
+    c->launches += 2;
     prof_end(c);
 }
 
-template <class IO>
-void run_inv(fhe_ctx *c, const IO &io, int njobs, int cls, double words_per_job = 2.0)
+double bfly_of(const fhe_ctx *c, double njobs) { return njobs * (c->N / 2) * c->logN; }
+
+void map_seg(MapSeg &S, const u64 *in, u64 *out, const LimbMap &m, const ulonglong2 *scale)
 {
-    if (njobs <= 0) return;
-    prof_begin(c, cls, 8.0 * words_per_job * c->N * njobs, (double)njobs * (c->N / 2) * c->logN);
-    c->launches += inv_dispatch(c, io, njobs);
-    prof_end(c);
+    memset(&S, 0, sizeof(S));
+    S.in = in;
+    S.out = out;
+    S.in_outer = m.in_outer;
+    S.out_outer = m.out_outer;
+    S.scale = scale;
+    for (int i = 0; i < m.nl; i++) {
+        S.in_limb[i] = (uint8_t)m.in_limb[i];
+        S.out_limb[i] = (uint8_t)m.out_limb[i];
+        S.prime[i] = (uint8_t)m.prime[i];
+    }
+}
+
+// Runs `fill(io, item)` over items in launches of at most FHE_SEGS segments.
+template <class IO, class Item, class Fill>
+void run_many(const std::vector<Item> &items, bool fwd, int cls, Fill fill)
+{
+    size_t i = 0;
+    while (i < items.size()) {
+        IO io;
+        memset(&io, 0, sizeof(io));
+        fhe_ctx *c0 = items[i].c;
+        double bytes = 0, bfly = 0;
+        for (; i < items.size() && io.nseg < FHE_SEGS; i++) {
+            double b = 0, f = 0;
+            if (fill(io, io.nseg, items[i], &b, &f)) io.nseg++;
+            bytes += b;
+            bfly += f;
+        }
+        run(c0, io, fwd, cls, bytes, bfly);
+    }
 }
 
 }  // namespace
 
 bool ntt_supported_logn(int logN) { return logN >= 10 && logN <= 15; }
 
+// ---------------------------------------------------------------------------
+// multi-segment launchers
+// ---------------------------------------------------------------------------
+
+void launch_ntt_map_many(const std::vector<NttMapArgs> &a, bool fwd, int cls)
+{
+    run_many<IOMap>(a, fwd, cls, [fwd](IOMap &io, int sg, const NttMapArgs &x, double *b, double *f) {
+        if (x.njobs <= 0) return false;
+        seg_header(io.h[sg], x.c, fwd, x.njobs / x.m.nl, x.m.nl);
+        map_seg(io.s[sg], x.in, x.out, x.m, x.scale);
+        *b = 16.0 * x.c->N * x.njobs;
+        *f = bfly_of(x.c, x.njobs);
+        return true;
+    });
+}
+
+void launch_ntt_inv_scaled_y_many(const std::vector<NttYArgs> &a)
+{
+    run_many<IOScaledY>(a, false, FHE_K_NTT_INV, [](IOScaledY &io, int sg, const NttYArgs &x, double *b, double *f) {
+        if (x.njobs <= 0) return false;
+        seg_header(io.h[sg], x.c, false, x.njobs / x.m.nl, x.m.nl);
+        YSeg &S = io.s[sg];
+        map_seg(S, x.in, x.out, x.m, x.scale);
+        S.abase = x.abase;
+        S.a_outer = x.a_outer;
+        S.a_poly = x.a_poly;
+        S.amask = x.amask;
+        S.alimb = x.level - 1;
+        S.qm = x.c->q[x.level - 1];
+        S.Pm = x.c->rms[x.level].Pm;
+        S.Pm_s = x.c->rms[x.level].Pm_s;
+        // the y entry (one of nl) also reads the addend limb
+        *b = 8.0 * x.c->N * x.njobs * (2.0 + 1.0 / x.m.nl);
+        *f = bfly_of(x.c, x.njobs);
+        return true;
+    });
+}
+
+void launch_ntt_modup_many(const std::vector<NttModUpArgs> &a)
+{
+    run_many<IOModUp>(a, true, FHE_K_NTT_MODUP, [](IOModUp &io, int sg, const NttModUpArgs &x, double *b, double *f) {
+        const ModUpParams &P = x.c->modup[x.level];
+        if (x.count <= 0 || P.njobs <= 0) return false;
+        seg_header(io.h[sg], x.c, true, x.count, P.njobs);
+        ModUpSeg &S = io.s[sg];
+        S.d2c = x.d2c;
+        S.ext = x.ext;
+        S.P = x.c->d_modup + x.level;
+        S.l = x.level;
+        S.K = x.c->K;
+        S.dnum = P.dnum;
+        double words = 0;
+        for (int e = 0; e < P.njobs; e++) words += P.digit_n[P.job_digit[e]] + 1.0;
+        *b = 8.0 * x.c->N * words * x.count;
+        *f = bfly_of(x.c, (double)P.njobs * x.count);
+        return true;
+    });
+}
+
+void launch_ntt_moddown_many(const std::vector<NttDownArgs> &a)
+{
+    run_many<IOModDown>(a, true, FHE_K_NTT_MODDOWN, [](IOModDown &io, int sg, const NttDownArgs &x, double *b, double *f) {
+        if (x.count <= 0) return false;
+        seg_header(io.h[sg], x.c, true, 2 * x.count, x.level);
+        ModDownSeg &S = io.s[sg];
+        S.accP = x.src;
+        S.acc = x.acc;
+        S.abase = x.abase;
+        S.a_outer = x.a_outer;
+        S.a_poly = x.a_poly;
+        S.amask = x.amask;
+        S.out = x.out;
+        S.P = x.c->d_moddown + x.level;
+        S.l = x.level;
+        S.K = x.c->K;
+        // reads K special limbs, acc_i and (for masked polys) the addend; writes out_i
+        const double add_frac = ((x.amask & 1) + ((x.amask >> 1) & 1)) / 2.0;
+        const double njobs = 2.0 * x.level * x.count;
+        *b = 8.0 * x.c->N * njobs * (x.c->K + 2.0 + add_frac);
+        *f = bfly_of(x.c, njobs);
+        return true;
+    });
+}
+
+void launch_ntt_relin_ms_many(const std::vector<NttDownArgs> &a)
+{
+    run_many<IORelinMS>(a, true, FHE_K_NTT_MODDOWN, [](IORelinMS &io, int sg, const NttDownArgs &x, double *b, double *f) {
+        if (x.count <= 0 || x.level < 2) return false;
+        seg_header(io.h[sg], x.c, true, 2 * x.count, x.level - 1);
+        RelinMSSeg &S = io.s[sg];
+        S.src = x.src;
+        S.acc = x.acc;
+        S.abase = x.abase;
+        S.a_outer = x.a_outer;
+        S.a_poly = x.a_poly;
+        S.amask = x.amask;
+        S.out = x.out;
+        S.P = x.c->d_rms + x.level;
+        S.l = x.level;
+        S.K = x.c->K;
+        // reads K + 1 correction sources, acc_i and (for masked polys) the addend; writes out_i
+        const double add_frac = ((x.amask & 1) + ((x.amask >> 1) & 1)) / 2.0;
+        const double njobs = 2.0 * (x.level - 1) * x.count;
+        *b = 8.0 * x.c->N * njobs * (x.c->K + 3.0 + add_frac);
+        *f = bfly_of(x.c, njobs);
+        return true;
+    });
+}
+
+void launch_ntt_modswitch_many(const std::vector<NttSwitchArgs> &a)
+{
+    run_many<IOModSwitch>(a, true, FHE_K_NTT_MODSWITCH, [](IOModSwitch &io, int sg, const NttSwitchArgs &x, double *b,
+                                                           double *f) {
+        if (x.count <= 0 || x.level < 2) return false;
+        seg_header(io.h[sg], x.c, true, x.npoly * x.count, x.level - 1);
+        SwitchSeg &S = io.s[sg];
+        S.last = x.src;
+        S.in = x.in;
+        S.out = x.out;
+        S.P = x.c->d_modswitch + x.level;
+        S.l = x.level;
+        S.npoly = x.npoly;
+        const double njobs = (double)x.npoly * (x.level - 1) * x.count;
+        *b = 8.0 * x.c->N * njobs * 3.0;
+        *f = bfly_of(x.c, njobs);
+        return true;
+    });
+}
+
+void launch_ntt_multiswitch_many(const std::vector<NttSwitchArgs> &a)
+{
+    run_many<IOMultiSwitch>(a, true, FHE_K_NTT_MODSWITCH, [](IOMultiSwitch &io, int sg, const NttSwitchArgs &x,
+                                                             double *b, double *f) {
+        if (x.count <= 0 || x.k < 2 || x.k >= x.level) return false;
+        seg_header(io.h[sg], x.c, true, x.npoly * x.count, x.level - x.k);
+        MultiSeg &S = io.s[sg];
+        S.src = x.src;
+        S.in = x.in;
+        S.out = x.out;
+        S.P = x.c->d_mss + (size_t)x.level * (FHE_MAXK + 1) + x.k;
+        S.l = x.level;
+        S.k = x.k;
+        S.npoly = x.npoly;
+        // reads the k switch values and x_i, writes out_i
+        const double njobs = (double)x.npoly * (x.level - x.k) * x.count;
+        *b = 8.0 * x.c->N * njobs * (x.k + 2.0);
+        *f = bfly_of(x.c, njobs);
+        return true;
+    });
+}
+
+// ---------------------------------------------------------------------------
+// single-segment launchers
+// ---------------------------------------------------------------------------
+
 void launch_ntt_fwd_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs)
 {
-    IOPlain io{in, out, m};
-    run_fwd(c, io, njobs, FHE_K_NTT_FWD);
+    launch_ntt_map_many({NttMapArgs{c, in, out, m, nullptr, njobs}}, true, FHE_K_NTT_FWD);
 }
 
 void launch_ntt_inv_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs)
 {
-    IOPlain io{in, out, m};
-    run_inv(c, io, njobs, FHE_K_NTT_INV);
+    launch_ntt_map_many({NttMapArgs{c, in, out, m, nullptr, njobs}}, false, FHE_K_NTT_INV);
 }
 
 void launch_ntt_inv_scaled(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, const ulonglong2 *scale,
                            int njobs)
 {
-    IOScaled io;
-    io.in = in;
-    io.out = out;
-    io.m = m;
-    for (int i = 0; i < m.nl; i++) io.scale[i] = scale[i];
-    run_inv(c, io, njobs, FHE_K_NTT_INV);
+    launch_ntt_map_many({NttMapArgs{c, in, out, m, scale, njobs}}, false, FHE_K_NTT_INV);
 }
 
 void launch_ntt_inv_scaled_y(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, const ulonglong2 *scale,
                              int njobs, const u64 *abase, long long a_outer, long long a_poly, int amask, int level)
 {
-    IOScaledY io;
-    io.in = in;
-    io.out = out;
-    io.m = m;
-    for (int i = 0; i < m.nl; i++) io.scale[i] = scale[i];
-    io.abase = abase;
-    io.a_outer = a_outer;
-    io.a_poly = a_poly;
-    io.amask = amask;
-    io.alimb = level - 1;
-    io.qm = c->q[level - 1];
-    io.Pm = c->rms[level].Pm;
-    io.Pm_s = c->rms[level].Pm_s;
-    // the y entry (one of nl) also reads the addend limb
-    run_inv(c, io, njobs, FHE_K_NTT_INV, 2.0 + 1.0 / m.nl);
+    NttYArgs y;
+    static_cast<NttMapArgs &>(y) = NttMapArgs{c, in, out, m, scale, njobs};
+    y.abase = abase;
+    y.a_outer = a_outer;
+    y.a_poly = a_poly;
+    y.amask = amask;
+    y.level = level;
+    launch_ntt_inv_scaled_y_many({y});
 }
 
 void launch_ntt_modup(fhe_ctx *c, const u64 *d2c, u64 *ext, int level, int count)
 {
-    const ModUpParams &P = c->modup[level];
-    IOModUp io;
-    io.d2c = d2c;
-    io.ext = ext;
-    io.P = c->d_modup + level;
-    io.mq = c->d_mq;
-    io.l = level;
-    io.K = c->K;
-    io.dnum = P.dnum;
-    io.njobs = P.njobs;
-    io.stride = c->N;
-    double words = 0;
-    for (int e = 0; e < P.njobs; e++) words += P.digit_n[P.job_digit[e]] + 1.0;
-    run_fwd(c, io, P.njobs * count, FHE_K_NTT_MODUP, words / P.njobs);
+    launch_ntt_modup_many({NttModUpArgs{c, d2c, ext, level, count}});
 }
 
 void launch_ntt_moddown(fhe_ctx *c, const u64 *accP, const u64 *acc, const u64 *abase, long long a_outer,
                         long long a_poly, int amask, u64 *out, int level, int count)
 {
-    IOModDown io;
-    io.accP = accP;
-    io.acc = acc;
-    io.abase = abase;
-    io.a_outer = a_outer;
-    io.a_poly = a_poly;
-    io.amask = amask;
-    io.out = out;
-    io.P = c->d_moddown + level;
-    io.mq = c->d_mq;
-    io.l = level;
-    io.K = c->K;
-    io.stride = c->N;
-    // reads K special limbs, acc_i and (for masked polys) the addend; writes out_i
-    const double add_frac = ((amask & 1) + ((amask >> 1) & 1)) / 2.0;
-    run_fwd(c, io, 2 * level * count, FHE_K_NTT_MODDOWN, c->K + 2.0 + add_frac);
+    launch_ntt_moddown_many({NttDownArgs{c, accP, acc, abase, a_outer, a_poly, amask, out, level, count}});
 }
 
 void launch_ntt_relin_ms(fhe_ctx *c, const u64 *src, const u64 *acc, const u64 *abase, long long a_outer,
                          long long a_poly, int amask, u64 *out, int level, int count)
 {
-    IORelinMS io;
-    io.src = src;
-    io.acc = acc;
-    io.abase = abase;
-    io.a_outer = a_outer;
-    io.a_poly = a_poly;
-    io.amask = amask;
-    io.out = out;
-    io.P = c->d_rms + level;
-    io.mq = c->d_mq;
-    io.l = level;
-    io.K = c->K;
-    io.stride = c->N;
-    // reads K + 1 correction sources, acc_i and (for masked polys) the addend; writes out_i
-    const double add_frac = ((amask & 1) + ((amask >> 1) & 1)) / 2.0;
-    run_fwd(c, io, 2 * (level - 1) * count, FHE_K_NTT_MODDOWN, c->K + 3.0 + add_frac);
+    launch_ntt_relin_ms_many({NttDownArgs{c, src, acc, abase, a_outer, a_poly, amask, out, level, count}});
 }
 
 void launch_ntt_multiswitch(fhe_ctx *c, const u64 *src, const u64 *in, u64 *out, int level, int k, int npoly,
                             int count)
 {
-    IOMultiSwitch io;
-    io.src = src;
-    io.in = in;
-    io.out = out;
-    io.P = c->d_mss + (size_t)level * (FHE_MAXK + 1) + k;
-    io.mq = c->d_mq;
-    io.l = level;
-    io.k = k;
-    io.npoly = npoly;
-    io.stride = c->N;
-    // reads the k switch values and x_i, writes out_i
-    run_fwd(c, io, npoly * (level - k) * count, FHE_K_NTT_MODSWITCH, k + 2.0);
+    launch_ntt_multiswitch_many({NttSwitchArgs{c, src, in, out, level, k, npoly, count}});
 }
 
 void launch_ntt_modswitch(fhe_ctx *c, const u64 *last, const u64 *in, u64 *out, int level, int npoly, int count)
 {
-    IOModSwitch io;
-    io.last = last;
-    io.in = in;
-    io.out = out;
-    io.P = c->d_modswitch + level;
-    io.mq = c->d_mq;
-    io.l = level;
-    io.npoly = npoly;
-    run_fwd(c, io, npoly * (level - 1) * count, FHE_K_NTT_MODSWITCH, 3.0);
+    launch_ntt_modswitch_many({NttSwitchArgs{c, last, in, out, level, 1, npoly, count}});
 }
 
 // ---------------------------------------------------------------------------
-// autotuner: times both factorisations on a representative batch
+// autotuner: the grid policy (one CTA per unit, or 6 / 4 / 2 resident CTAs
+// per SM walking the units), timed on a representative batch
 // ---------------------------------------------------------------------------
 
-bool ntt_variant_ok(int logN, int v)
-{
-    if (v == 0) return true;
-    if (v == 1) return logN >= 11 && logN <= 15;
-    if (v == 2) return logN == 10 || logN == 12 || logN == 14;
-    if (v == 3) return logN >= 12 && logN <= 15;
-    return false;
-}
+bool ntt_variant_ok(int logN, int v) { return ntt_supported_logn(logN) && v >= 0 && v < FHE_NTT_VARIANTS; }
 
 // Times forward + inverse of `outer` x nl limbs (nl = min(primes, 10)),
-// `outer` rounded to a multiple of 16 when >= 16 so that the row kernels take
+// `outer` rounded to a multiple of 16 when >= 16 so that the row units take
 // their grouped form as in batched use; keeps the faster variant.
 int ntt_autotune(fhe_ctx *c, int njobs, float *ms_out)
 {
@@ -1356,15 +1527,14 @@ int ntt_autotune(fhe_ctx *c, int njobs, float *ms_out)
         if (ms_out) ms_out[v] = 0;
         if (!ntt_variant_ok(c->logN, v)) continue;
         c->ntt_variant = v;
-        IOPlain io{buf, buf, m};
         for (int w = 0; w < 2; w++) {
-            fwd_dispatch(c, io, jobs);
-            inv_dispatch(c, io, jobs);
+            launch_ntt_fwd_plain(c, buf, buf, m, jobs);
+            launch_ntt_inv_plain(c, buf, buf, m, jobs);
         }
         cudaEventRecord(e0, c->stream);
         for (int r = 0; r < 5; r++) {
-            fwd_dispatch(c, io, jobs);
-            inv_dispatch(c, io, jobs);
+            launch_ntt_fwd_plain(c, buf, buf, m, jobs);
+            launch_ntt_inv_plain(c, buf, buf, m, jobs);
         }
         cudaEventRecord(e1, c->stream);
         cudaEventSynchronize(e1);
@@ -1372,8 +1542,8 @@ int ntt_autotune(fhe_ctx *c, int njobs, float *ms_out)
         cudaEventElapsedTime(&ms, e0, e1);
         ms /= 5;
         if (ms_out) ms_out[v] = ms;
-        // the first factorisation stays unless another is clearly faster
-        // (3%), so that near-ties do not flip from one context to the next
+        // the first policy stays unless another is clearly faster (3%), so
+        // that near-ties do not flip from one context to the next
         if (v == 0 || ms < 0.97f * best) best = ms, best_v = v;
     }
     c->ntt_variant = best_v;

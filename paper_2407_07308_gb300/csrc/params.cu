@@ -376,6 +376,25 @@ int build_tables(fhe_ctx *c)
         c->ks_pscale[k] = sc(host_mulmod(ninv[L + k].x, c->moddown[L].cinv[k], pk), pk);
     }
 
+    // the same constants on the device, so that a launch serving several
+    // contexts or levels reads each segment's own (ntt.cu takes pointers)
+    {
+        std::vector<ulonglong2> xs((size_t)(L + 1) * FHE_MAXP, make_ulonglong2(0, 0));
+        std::vector<ulonglong2> m4((size_t)(L + 1) * (FHE_MAXK + 1), make_ulonglong2(0, 0));
+        for (int l = 1; l <= L; l++) {
+            for (int i = 0; i < l; i++) xs[(size_t)l * FHE_MAXP + i] = c->ks_xscale[l][i];
+            for (int k = 0; k < K; k++) m4[(size_t)l * (FHE_MAXK + 1) + k] = c->ks_pscale[k];
+            m4[(size_t)l * (FHE_MAXK + 1) + K] = c->rms_yscale[l];
+        }
+        if ((e = upload(c, (void **)&c->d_ks_xscale, xs.data(), sizeof(ulonglong2) * xs.size()))) return e;
+        if ((e = upload(c, (void **)&c->d_ms4scale, m4.data(), sizeof(ulonglong2) * m4.size()))) return e;
+        if ((e = upload(c, (void **)&c->d_ks_pscale, c->ks_pscale.data(), sizeof(ulonglong2) * K))) return e;
+        if ((e = upload(c, (void **)&c->d_ms_lastscale, c->ms_lastscale.data(), sizeof(ulonglong2) * (L + 1))))
+            return e;
+        if ((e = upload(c, (void **)&c->d_mss_scale, c->mss_scale.data(), sizeof(ulonglong2) * c->mss_scale.size())))
+            return e;
+    }
+
     lt_poly_coefficients((int)c->p, c->lt);
     if (slot_structure(c)) return FHE_EUNSUPPORTED;
     if (c->N % c->M) return FHE_EUNSUPPORTED;

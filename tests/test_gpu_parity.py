@@ -53,7 +53,7 @@ def _same(oracle_ct, gpu_export, idx=0):
 
 @pytest.mark.parametrize("logN,variant", [(10, 0), (10, 2), (11, 0), (11, 1), (12, 0), (12, 1), (12, 2), (12, 3),
                                            (13, 0), (13, 1), (13, 3), (14, 0), (14, 1), (14, 2), (14, 3), (15, 0),
-                                           (15, 1), (15, 3)])
+                                           (15, 1), (15, 3), (15, 2)])
 def test_ntt_forward_inverse_match_oracle(logN, variant):
     from oracle.bgv import Oracle
 
@@ -288,7 +288,7 @@ def test_batch_equals_singles():
         g.close()
 
 
-@pytest.mark.parametrize("logN,variants", [(13, (0, 1, 3)), (12, (0, 1, 2, 3)), (14, (0, 2, 3))])
+@pytest.mark.parametrize("logN,variants", [(13, (0, 1, 2, 3)), (12, (0, 1, 2, 3)), (14, (0, 1, 2, 3))])
 def test_ntt_variants_and_autotuner(logN, variants):
     """Every NTT variant gives the same bits through the whole compare path
     (16 ciphertexts, so the grouped row kernels run), and the autotuner
@@ -322,9 +322,6 @@ def test_ntt_variants_and_autotuner(logN, variants):
             assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1], o[1])
         with pytest.raises(fhe.FheError):
             fhe.fhe_ctx_ntt_variant(g.ctx, 4)
-        if 2 not in variants:
-            with pytest.raises(fhe.FheError):
-                fhe.fhe_ctx_ntt_variant(g.ctx, 2)
     finally:
         g.close()
 
