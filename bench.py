@@ -704,7 +704,9 @@ def run_uneven(args):
                 fhe.fhe_ct_destroy(h)
         return dt, t_enq
 
-    # same-level groups only (no alignment), then the aligned form (the value)
+    # same-level groups only (no alignment), the aligned form per context,
+    # then the fused form (the value): the contexts of one plaintext prime in
+    # one circuit, every step one launch across ring degrees and levels
     batched_step(check=True, flags=0)
     for _ in range(args.warmup - 1):
         batched_step(flags=0)
@@ -713,8 +715,15 @@ def run_uneven(args):
     for _ in range(args.warmup - 1):
         batched_step()
     l0 = cs.launches()
+    aligned = [batched_step()[0] for _ in range(args.steps)]
+    aligned_launches = (cs.launches() - l0) / args.steps
+    fused = fhe.FHE_BATCH_ALIGN_LEVELS | fhe.FHE_BATCH_FUSE_RINGS
+    batched_step(check=True, flags=fused)
+    for _ in range(args.warmup - 1):
+        batched_step(flags=fused)
+    l0 = cs.launches()
     with Clocks(local) as clk:
-        times = [batched_step() for _ in range(args.steps)]
+        times = [batched_step(flags=fused) for _ in range(args.steps)]
     launches = cs.launches() - l0
     walls = [t for t, _ in times]
     value = slot_cmps * args.steps / sum(walls)
@@ -747,15 +756,22 @@ def run_uneven(args):
                                "level uniform in [lowest decryptable level, 20], 20x50-bit + 4 special primes, one "
                                "ciphertext tuple pair per request", "requests": len(reqs), "by_shape": shapes,
                    "slot_comparisons_per_step": slot_cmps,
-                   "batched_form": "all requests in one fhe_batch_submit with FHE_BATCH_ALIGN_LEVELS (requests "
-                                   "of one context and digit count switched down to their lowest start level "
-                                   "and grouped; 8 streams per context; recurring shapes replayed as graphs), "
-                                   "host wall time of submit + wait",
+                   "batched_form": "all requests in one fhe_batch_submit with FHE_BATCH_ALIGN_LEVELS | "
+                                   "FHE_BATCH_FUSE_RINGS (requests of one context and digit count switched down "
+                                   "to their lowest start level and grouped; the contexts of one plaintext prime "
+                                   "in one circuit whose every step is one launch over all their groups, ring "
+                                   "degrees and levels mixed), host wall time of submit + wait",
                    "plain_form": "one request at a time through fhe_compare, synchronised",
                    "l2": "inputs and intermediates of every step exceed L2"},
         "plain": plain, "enqueue_ms_p50": round(1e3 * sorted(t for _, t in times)[len(times) // 2], 1),
         "batched_same_level_groups": {"value": round(slot_cmps * args.steps / sum(unaligned), 2), "unit": UNIT,
                                       "ms_per_step": round(1e3 * sum(unaligned) / args.steps, 1)},
+        "batched_aligned_per_context": {"value": round(slot_cmps * args.steps / sum(aligned), 2), "unit": UNIT,
+                                        "ms_per_step": round(1e3 * sum(aligned) / args.steps, 1),
+                                        "launches_per_step": round(aligned_launches, 1),
+                                        "form": "FHE_BATCH_ALIGN_LEVELS only: one circuit per context, recurring "
+                                                "shapes replayed as graphs"},
+        "launches_per_step": round(launches / args.steps, 1),
         "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": None, "roofline": None,
     }
     for r in reqs:

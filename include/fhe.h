@@ -467,8 +467,15 @@ int fhe_batch_submit(const fhe_job *jobs, int n, fhe_batch **out);
  * untouched), so that they share one group and its launches.  Each result
  * then equals the job run alone from that lower level.  The lowest level must
  * leave the circuit its depth, as it does when every job of the group could
- * run alone at its own level. */
-enum { FHE_BATCH_ALIGN_LEVELS = 1 };
+ * run alone at its own level.
+ * FHE_BATCH_FUSE_RINGS: the compare and max/min jobs of all contexts that
+ * share a device and a plaintext prime (hence the digit polynomial) run in
+ * one circuit, whose every step is one kernel launch over all their groups:
+ * ring degrees, digit counts and levels mixed in one launch (the first such
+ * context's stream carries the work; the others' streams wait for it).
+ * Their submissions run directly, without batch graphs.  Results are those
+ * of each job alone. */
+enum { FHE_BATCH_ALIGN_LEVELS = 1, FHE_BATCH_FUSE_RINGS = 2 };
 int fhe_batch_submit_ex(const fhe_job *jobs, int n, int flags, fhe_batch **out);
 /* Graph capture of recurring submissions: the second time a context receives
  * the same group shapes (keys, kind, digits, level, ciphertexts per group),

@@ -340,6 +340,7 @@ extern "C" int fhe_ctx_create(const fhe_params *P, const fhe_allocator *alloc, v
     c->p = P->p;
     c->stream = (cudaStream_t)stream;
     if (cudaGetDevice(&c->device) != cudaSuccess) c->device = -1;
+    if (const char *ws = getenv("FHE_WAVE_SPLIT")) c->wave_split = std::max(1, std::min(8, atoi(ws)));
     if (c->device < 0 || cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
         c->sms = 0;
     c->q.resize(c->np);

@@ -295,10 +295,10 @@ int replay_in(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups, BatchPlan *P)
     return err;
 }
 
-int run_direct(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups)
+// each group's operands concatenated (one batch per digit)
+int gather_groups(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups)
 {
     int err = 0;
-    // operands
     for (auto &kv : groups) {
         Group &g = kv.second;
         g.X.assign(g.d, nullptr);
@@ -313,6 +313,29 @@ int run_direct(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups)
         }
         if (err) break;
     }
+    return err;
+}
+
+// results back to the jobs; the group buffers freed
+int scatter_groups(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups, int err)
+{
+    for (auto &kv : groups) {
+        Group &g = kv.second;
+        if (!err) err = scatter(c, jobs, g, g.out0, g.out1, true);
+        for (fhe_ct *x : g.out0) fhe_ct_destroy(x);
+        for (fhe_ct *x : g.out1) fhe_ct_destroy(x);
+        for (int k = 0; k < 2 * g.d && k < (int)g.own_x.size(); k++)
+            if (g.own_x[k]) fhe_ct_destroy(k < g.d ? g.X[k] : g.Y[k - g.d]);
+        g.out0.clear();
+        g.out1.clear();
+        g.own_x.clear();
+    }
+    return err;
+}
+
+int run_direct(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups)
+{
+    int err = gather_groups(c, jobs, groups);
     // one circuit per key set; with multistream the groups overlap
     std::map<const fhe_evk *, std::vector<MultiItem>> by_evk;
     if (!err)
@@ -337,13 +360,77 @@ int run_direct(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups)
         err = circuit_sort(c, g.evk, X.data(), g.d, g.out0.data());
     }
     c->multistream = false;
-    for (auto &kv : groups) {
-        Group &g = kv.second;
-        if (!err) err = scatter(c, jobs, g, g.out0, g.out1, true);
-        for (fhe_ct *x : g.out0) fhe_ct_destroy(x);
-        for (fhe_ct *x : g.out1) fhe_ct_destroy(x);
-        for (int k = 0; k < 2 * g.d && k < (int)g.own_x.size(); k++)
-            if (g.own_x[k]) fhe_ct_destroy(k < g.d ? g.X[k] : g.Y[k - g.d]);
+    return scatter_groups(c, jobs, groups, err);
+}
+
+// The compare and max/min jobs of contexts that share a device and a
+// plaintext prime, in one circuit (fused launches across ring degrees,
+// digit counts and levels); their sort jobs afterwards, per context.  Every
+// member context works on the leader's stream meanwhile: the leader first
+// waits for what the others have queued, and they wait for the leader at
+// the end.  The caller holds every member's lock.
+int run_family(const std::vector<fhe_ctx *> &fam, const fhe_job *jobs, std::map<fhe_ctx *, std::vector<int>> &by_ctx)
+{
+    fhe_ctx *lead = fam[0];
+    const cudaStream_t ls = lead->stream;
+    std::vector<cudaStream_t> saved;
+    int err = 0;
+    auto follow = [&](cudaStream_t waiter, cudaStream_t on) {  // waiter waits for work queued on `on`
+        cudaEvent_t ev = nullptr;
+        int e = fhe_cuda_check(lead, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "fuse event");
+        if (!e) e = fhe_cuda_check(lead, cudaEventRecord(ev, on), "fuse event");
+        if (!e) e = fhe_cuda_check(lead, cudaStreamWaitEvent(waiter, ev, 0), "fuse wait");
+        if (ev) cudaEventDestroy(ev);
+        return e;
+    };
+    for (fhe_ctx *m : fam) {
+        saved.push_back(m->stream);
+        if (m == lead) continue;
+        if (!err) err = follow(ls, m->stream);
+        m->stream = ls;
+        m->pool.stream = ls;
+    }
+    std::vector<GroupMap> gm(fam.size());
+    std::vector<GroupMap> sorts(fam.size());
+    std::vector<const fhe_evk *> evks;
+    std::vector<MultiItem> items;
+    for (size_t i = 0; i < fam.size() && !err; i++) {
+        std::vector<int> cmp, srt;
+        for (int id : by_ctx[fam[i]]) (jobs[id].kind == FHE_JOB_SORT ? srt : cmp).push_back(id);
+        gm[i] = make_groups(jobs, cmp);
+        sorts[i] = make_groups(jobs, srt);
+        err = gather_groups(fam[i], jobs, gm[i]);
+        for (auto &kv : gm[i]) {
+            Group &g = kv.second;
+            auto it = items_for(g, jobs[g.jobs[0]], g.X, g.Y, g.out0, g.out1);
+            items.push_back(it[0]);
+            evks.push_back(g.evk);
+        }
+    }
+    if (!err && !items.empty()) {
+        // the leader's keys first (it leads the circuit)
+        for (size_t i = 0; i < evks.size(); i++)
+            if (evks[i]->ctx == lead) {
+                std::swap(evks[0], evks[i]);
+                std::swap(items[0], items[i]);
+                break;
+            }
+        if (evks[0]->ctx != lead) lead = evks[0]->ctx;  // the leader has no compare job: another member leads
+        const bool ms = lead->multistream;
+        lead->multistream = true;
+        err = circuit_multi_ctx(evks, items);
+        lead->multistream = ms;
+    }
+    for (size_t i = 0; i < fam.size(); i++) err = scatter_groups(fam[i], jobs, gm[i], err);
+    for (size_t i = 0; i < fam.size() && !err; i++)
+        if (!sorts[i].empty()) err = run_direct(fam[i], jobs, sorts[i]);
+    for (size_t i = 0; i < fam.size(); i++) {
+        fhe_ctx *m = fam[i];
+        if (m == fam[0]) continue;
+        m->stream = saved[i];
+        m->pool.stream = saved[i];
+        const int e = follow(m->stream, ls);
+        if (!err) err = e;
     }
     return err;
 }
@@ -468,7 +555,7 @@ extern "C" int fhe_batch_submit(const fhe_job *jobs, int n, fhe_batch **out)
 extern "C" int fhe_batch_submit_ex(const fhe_job *jobs, int n, int flags, fhe_batch **out)
 {
     FHE_RANGE("fhe_batch_submit_ex");
-    if (!jobs || n < 1 || !out || (flags & ~FHE_BATCH_ALIGN_LEVELS)) return FHE_EINVAL;
+    if (!jobs || n < 1 || !out || (flags & ~(FHE_BATCH_ALIGN_LEVELS | FHE_BATCH_FUSE_RINGS))) return FHE_EINVAL;
     for (int i = 0; i < n; i++) {
         int e = batch_check_job(jobs[i]);
         if (e) return e;
@@ -485,15 +572,34 @@ extern "C" int fhe_batch_submit_ex(const fhe_job *jobs, int n, int flags, fhe_ba
         if (!by_ctx.count(jobs[i].ctx)) order.push_back(jobs[i].ctx);
         by_ctx[jobs[i].ctx].push_back(i);
     }
+    // families of contexts that run in one circuit (FHE_BATCH_FUSE_RINGS:
+    // one device and plaintext prime), in order of first appearance
+    std::vector<std::vector<fhe_ctx *>> fams;
+    for (fhe_ctx *c : order) {
+        bool placed = false;
+        if (flags & FHE_BATCH_FUSE_RINGS)
+            for (auto &f : fams)
+                if (f[0]->p == c->p && f[0]->device == c->device) {
+                    f.push_back(c);
+                    placed = true;
+                    break;
+                }
+        if (!placed) fams.push_back({c});
+    }
     fhe_batch *B = new fhe_batch;
     int err = 0;
-    for (fhe_ctx *c : order) {
-        std::lock_guard<std::mutex> g(c->mu);
-        err = run_context(c, jobs, by_ctx[c]);
-        cudaEvent_t ev = nullptr;
-        if (!err) err = fhe_cuda_check(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch event");
-        if (!err) err = fhe_cuda_check(c, cudaEventRecord(ev, c->stream), "batch event");
-        if (ev) B->done.push_back({c, ev});
+    for (auto &fam : fams) {
+        std::vector<fhe_ctx *> lock_order(fam);
+        std::sort(lock_order.begin(), lock_order.end());
+        std::vector<std::unique_lock<std::mutex>> locks;
+        for (fhe_ctx *c : lock_order) locks.emplace_back(c->mu);
+        err = fam.size() == 1 ? run_context(fam[0], jobs, by_ctx[fam[0]]) : run_family(fam, jobs, by_ctx);
+        for (fhe_ctx *c : fam) {
+            cudaEvent_t ev = nullptr;
+            if (!err) err = fhe_cuda_check(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch event");
+            if (!err) err = fhe_cuda_check(c, cudaEventRecord(ev, c->stream), "batch event");
+            if (ev) B->done.push_back({c, ev});
+        }
         if (err) break;
     }
     if (err) {

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <functional>
 #include <map>
+#include <set>
 
 #include "fhe_internal.h"
 
@@ -414,6 +415,202 @@ int op_mul_relin(fhe_ctx *c, const KeySwitchKey &rlk, const fhe_ct *a, const fhe
     return 0;
 }
 
+// ---------------------------------------------------------------------------
+// the same operations over several batches at once: every step is one launch
+// for all of them (segment tables, see ntt.cu and many.cu), so the launches
+// of independent products are as large as their sum.  Items may belong to
+// different contexts of one device; the launches run on the stream of the
+// first item's context.
+// ---------------------------------------------------------------------------
+
+int op_mul_relin_many(std::vector<MulItem> &it)
+{
+    std::vector<size_t> fused;
+    for (size_t i = 0; i < it.size(); i++) {
+        MulItem &m = it[i];
+        fhe_ctx *c = m.c;
+        if (m.a->level != m.b->level || m.a->count != m.b->count || m.a->npoly != 2 || m.b->npoly != 2)
+            return fhe_fail(c, FHE_EMISMATCH, "tensor: shapes differ");
+        if (m.a->level > 1 && c->K + 1 <= FHE_MAXK && !c->separate_ms)
+            fused.push_back(i);
+        else if (int e = op_mul_relin(c, *m.rlk, m.a, m.b, &m.out))
+            return e;
+    }
+    if (fused.empty()) return 0;
+    struct Tm {
+        fhe_ct *d = nullptr, *r = nullptr;
+        u64 *xc = nullptr, *ext = nullptr, *acc = nullptr, *src = nullptr;
+    };
+    std::vector<Tm> tm(fused.size());
+    int err = 0;
+    auto release = [&]() {
+        for (size_t j = 0; j < fused.size(); j++) {
+            fhe_ctx *c = it[fused[j]].c;
+            Tm &t = tm[j];
+            if (t.d) fhe_ct_destroy(t.d);
+            for (u64 *q : {t.xc, t.ext, t.acc, t.src})
+                if (q) c->pool.put(q);
+            t = Tm();
+        }
+    };
+    for (size_t j = 0; j < fused.size() && !err; j++) {
+        const MulItem &m = it[fused[j]];
+        fhe_ctx *c = m.c;
+        const int l = m.a->level, count = m.a->count, N = c->N, K = c->K, dnum = c->modup[l].dnum;
+        Tm &t = tm[j];
+        t.d = ct_new(c, count, 3, l, &err);
+        if (!err) t.r = ct_new(c, count, 2, l - 1, &err);
+        if (!err) t.xc = (u64 *)c->pool.get(sizeof(u64) * (size_t)count * l * N, &err);
+        if (!err) t.ext = (u64 *)c->pool.get(sizeof(u64) * (size_t)count * dnum * (l + K) * N, &err);
+        if (!err) t.acc = (u64 *)c->pool.get(sizeof(u64) * (size_t)count * 2 * (l + K) * N, &err);
+        if (!err) t.src = (u64 *)c->pool.get(sizeof(u64) * (size_t)count * 2 * (K + 1) * N, &err);
+    }
+    if (err) {
+        for (Tm &t : tm)
+            if (t.r) fhe_ct_destroy(t.r);
+        release();
+        return fhe_fail(it[0].c, err, "product: out of device memory");
+    }
+    std::vector<TensorArgs> ta;
+    std::vector<NttMapArgs> m1;
+    std::vector<NttModUpArgs> mu;
+    std::vector<KsInnerArgs> ks;
+    std::vector<NttYArgs> ys;
+    std::vector<FoldArgs> fo;
+    std::vector<NttDownArgs> dn;
+    for (size_t j = 0; j < fused.size(); j++) {
+        const MulItem &m = it[fused[j]];
+        fhe_ctx *c = m.c;
+        const Tm &t = tm[j];
+        const int l = m.a->level, count = m.a->count, K = c->K;
+        const long long LN = (long long)l * c->N;
+        const u64 *x2 = t.d->d + 2 * LN;  // the key-switched poly c2
+        ta.push_back(TensorArgs{c, m.a->d, m.b->d, t.d->d, count, l});
+        // INTT of c2, each limb i of digit j times (Q_j/q_i)^-1
+        m1.push_back(NttMapArgs{c, x2, t.xc, identity_map(l, 3 * LN, LN, 0, 0, 0),
+                                c->d_ks_xscale + (size_t)l * FHE_MAXP, count * l});
+        mu.push_back(NttModUpArgs{c, t.xc, t.ext, l, count});
+        ks.push_back(KsInnerArgs{c, t.ext, x2, 3 * LN, m.rlk->d, t.acc, count, l});
+        // t_k = INTT(acc_P,k) p^-1 (P/p_k)^-1 and Y' = INTT(y) (p P)^-1 with
+        // y = acc_{l-1} + P add_{l-1} formed while loading
+        NttYArgs y;
+        LimbMap m4;
+        memset(&m4, 0, sizeof(m4));
+        m4.nl = K + 1;
+        m4.in_outer = (long long)(l + K) * c->N;
+        m4.out_outer = (long long)(K + 1) * c->N;
+        for (int q = 0; q < K; q++) m4.in_limb[q] = l + q, m4.out_limb[q] = q, m4.prime[q] = c->L + q;
+        m4.in_limb[K] = l - 1;
+        m4.out_limb[K] = K;
+        m4.prime[K] = l - 1;
+        static_cast<NttMapArgs &>(y) =
+            NttMapArgs{c, t.acc, t.src, m4, c->d_ms4scale + (size_t)l * (FHE_MAXK + 1), count * 2 * (K + 1)};
+        y.abase = t.d->d;
+        y.a_outer = 3 * LN;
+        y.a_poly = LN;
+        y.amask = 3;
+        y.level = l;
+        ys.push_back(y);
+        fo.push_back(FoldArgs{c, t.src, count, l, 0});
+        dn.push_back(NttDownArgs{c, t.src, t.acc, t.d->d, 3 * LN, LN, 3, t.r->d, l, count});
+    }
+    launch_tensor_many(ta);
+    launch_ntt_map_many(m1, false, FHE_K_NTT_INV);
+    launch_ntt_modup_many(mu);
+    launch_ks_inner_many(ks);
+    launch_ntt_inv_scaled_y_many(ys);
+    launch_rms_fold_many(fo);
+    launch_ntt_relin_ms_many(dn);
+    for (size_t j = 0; j < fused.size(); j++) it[fused[j]].out = tm[j].r;
+    release();
+    return 0;
+}
+
+int op_modswitch_many(std::vector<SwitchItem> &it)
+{
+    std::vector<NttMapArgs> inv;
+    std::vector<FoldArgs> fold;
+    std::vector<NttSwitchArgs> one, multi;
+    std::vector<std::pair<fhe_ctx *, u64 *>> tmp;
+    int err = 0;
+    for (SwitchItem &s : it) {
+        fhe_ctx *c = s.c;
+        const fhe_ct *a = s.a;
+        const int l = a->level, k = s.k, N = c->N, outer = a->count * a->npoly;
+        if (k < 1 || k > FHE_MAXK || k >= l) {
+            err = fhe_fail(c, FHE_ELEVEL, "modulus switch below level 1");
+            break;
+        }
+        s.out = ct_new(c, a->count, a->npoly, l - k, &err);
+        if (err) break;
+        u64 *src = (u64 *)c->pool.get(sizeof(u64) * (size_t)outer * k * N, &err);
+        if (err) break;
+        tmp.push_back({c, src});
+        LimbMap m;
+        memset(&m, 0, sizeof(m));
+        m.nl = k;
+        m.in_outer = (long long)l * N;
+        m.out_outer = (long long)k * N;
+        for (int j = 0; j < k; j++) m.in_limb[j] = l - 1 - j, m.out_limb[j] = j, m.prime[j] = l - 1 - j;
+        if (k == 1) {
+            // w = [x_{l-1} p^-1]_{q_{l-1}} in the coefficient domain
+            inv.push_back(NttMapArgs{c, a->d, src, m, c->d_ms_lastscale + l, outer});
+            one.push_back(NttSwitchArgs{c, src, a->d, s.out->d, l, 1, a->npoly, a->count});
+        } else {
+            // X'_j = INTT(x_{l-1-j}) p^-1 D_j^-1
+            inv.push_back(NttMapArgs{c, a->d, src, m, c->d_mss_scale + ((size_t)l * (FHE_MAXK + 1) + k) * FHE_MAXK,
+                                     outer * k});
+            fold.push_back(FoldArgs{c, src, outer, l, k});
+            multi.push_back(NttSwitchArgs{c, src, a->d, s.out->d, l, k, a->npoly, a->count});
+        }
+    }
+    if (!err) {
+        launch_ntt_map_many(inv, false, FHE_K_NTT_INV);
+        launch_ms_fold_many(fold);
+        launch_ntt_modswitch_many(one);
+        launch_ntt_multiswitch_many(multi);
+    }
+    for (auto &t : tmp) t.first->pool.put(t.second);
+    if (err)
+        for (SwitchItem &s : it)
+            if (s.out) fhe_ct_destroy(s.out), s.out = nullptr;
+    return err;
+}
+
+int op_ew_many(std::vector<EwItem> &it)
+{
+    std::vector<EwArgs> args;
+    int err = 0;
+    for (EwItem &e : it) {
+        fhe_ctx *c = e.c;
+        const fhe_ct *x0 = e.x[0];
+        for (int j = 1; j < e.n; j++)
+            if (e.x[j]->level != x0->level || e.x[j]->count != x0->count || e.x[j]->npoly != x0->npoly)
+                err = fhe_fail(c, FHE_EMISMATCH, "element-wise operation: shapes differ");
+        if (e.op == FHE_EW_CADD && x0->npoly != 2) err = fhe_fail(c, FHE_EINVAL, "add_const needs a 2-poly ciphertext");
+        if (err) break;
+        e.out = ct_new(c, x0->count, x0->npoly, x0->level, &err);
+        if (err) break;
+        EwArgs a;
+        memset(&a, 0, sizeof(a));
+        a.c = c;
+        a.op = e.op;
+        a.n = e.n;
+        for (int j = 0; j < e.n; j++) a.x[j] = e.x[j]->d, a.k[j] = centred_const(c, e.k[j]);
+        a.out = e.out->d;
+        a.outer = x0->count * x0->npoly;
+        a.level = x0->level;
+        args.push_back(a);
+    }
+    if (err) {
+        for (EwItem &e : it)
+            if (e.out) fhe_ct_destroy(e.out), e.out = nullptr;
+        return err;
+    }
+    launch_ew_many(args);
+    return 0;
+}
+
 // Plaintext operand: coefficients m[N] (any residues mod p) lifted to
 // (-p/2, p/2], reduced mod q_0 .. q_{level-1} and transformed: [level][N] in
 // the NTT domain, in the ciphertext `out` (count 1, one poly).
@@ -505,11 +702,16 @@ namespace {
 // blocks go back to the plan (capture) or to the pool (direct).
 struct Dag {
     static constexpr int S = 8;
-    fhe_ctx *c;
+    using FreeMap = std::unordered_map<size_t, std::vector<void *>>;
+    fhe_ctx *c;  // the leader: its streams and events serve every member
     bool on = false;
     cudaStream_t main = nullptr;
-    std::unordered_map<size_t, std::vector<void *>> *main_free = nullptr;
-    std::vector<std::unordered_map<size_t, std::vector<void *>>> frees;
+    // members (contexts whose batches the circuit touches; [0] = the leader),
+    // each with its own free lists: scratch freed on branch k goes to
+    // frees[m][k] and back to member m's pool or capture list at the join
+    std::vector<fhe_ctx *> mem;
+    std::vector<FreeMap *> main_free;
+    std::vector<std::vector<FreeMap>> frees;
     bool used[S] = {false};
     int rr = 0, ev_next = 0, err = 0;
     std::vector<fhe_ct *> marked;
@@ -520,15 +722,24 @@ struct Dag {
         if (!c->capturing && !c->multistream) return;
         on = true;
         main = c->stream;
-        main_free = c->pool.cap_free;
-        frees.resize(S);
         while ((int)c->branch_streams.size() < S) {
             cudaStream_t s;
             cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
             c->branch_streams.push_back(s);
         }
+        add(c);
         origin = event();
         err = fhe_cuda_check(c, cudaEventRecord(origin, main), "dag fork");
+    }
+    // another context whose stream is the leader's for the circuit's span
+    void add(fhe_ctx *m)
+    {
+        if (!on) return;
+        for (fhe_ctx *x : mem)
+            if (x == m) return;
+        mem.push_back(m);
+        main_free.push_back(m->pool.cap_free);
+        frees.emplace_back(S);
     }
     cudaEvent_t event()
     {
@@ -538,6 +749,15 @@ struct Dag {
             c->branch_events.push_back(ev);
         }
         return c->branch_events[ev_next++];
+    }
+    void use(int k)
+    {
+        cudaStream_t s = c->branch_streams[k];
+        for (size_t m = 0; m < mem.size(); m++) {
+            mem[m]->stream = s;
+            mem[m]->pool.stream = s;
+            mem[m]->pool.cap_free = &frees[m][k];
+        }
     }
     // issue the next op after its inputs
     void begin(std::initializer_list<const fhe_ct *> ins)
@@ -552,9 +772,27 @@ struct Dag {
         }
         for (const fhe_ct *x : ins)
             if (x && x->ready && x->on != s) err = err ? err : fhe_cuda_check(c, cudaStreamWaitEvent(s, x->ready, 0), "dag wait");
-        c->stream = s;
-        c->pool.stream = s;
-        c->pool.cap_free = &frees[k];
+        use(k);
+    }
+    void begin(const std::vector<const fhe_ct *> &ins)
+    {
+        if (!on || err) return;
+        begin({});
+        for (const fhe_ct *x : ins)
+            if (x && x->ready && x->on != c->stream)
+                err = err ? err : fhe_cuda_check(c, cudaStreamWaitEvent(c->stream, x->ready, 0), "dag wait");
+    }
+    // one event for all outputs of a merged operation
+    void end_all(const std::vector<fhe_ct *> &outs)
+    {
+        if (!on || err || outs.empty() || !outs[0]) return;
+        end(outs[0]);
+        for (size_t i = 1; i < outs.size(); i++)
+            if (outs[i]) {
+                outs[i]->ready = outs[0]->ready;
+                outs[i]->on = outs[0]->on;
+                marked.push_back(outs[i]);
+            }
     }
     void end(fhe_ct *out)
     {
@@ -574,20 +812,23 @@ struct Dag {
             if (!err) err = fhe_cuda_check(c, cudaEventRecord(ev, c->branch_streams[k]), "dag join");
             if (!err) err = fhe_cuda_check(c, cudaStreamWaitEvent(main, ev, 0), "dag join");
         }
-        c->stream = main;
-        c->pool.stream = main;
-        c->pool.cap_free = main_free;
-        for (auto &f : frees)
-            for (auto &kv : f) {
-                if (main_free) {  // capture: the plan keeps them
-                    auto &dst = (*main_free)[kv.first];
-                    dst.insert(dst.end(), kv.second.begin(), kv.second.end());
-                } else {  // direct: back to the pool, usable on the original stream
-                    auto &dst = c->pool.free_lists[kv.first];
-                    dst.insert(dst.end(), kv.second.begin(), kv.second.end());
-                    c->pool.in_use -= kv.first * kv.second.size();
+        for (size_t m = 0; m < mem.size(); m++) {
+            fhe_ctx *x = mem[m];
+            x->stream = main;
+            x->pool.stream = main;
+            x->pool.cap_free = main_free[m];
+            for (auto &f : frees[m])
+                for (auto &kv : f) {
+                    if (main_free[m]) {  // capture: the plan keeps them
+                        auto &dst = (*main_free[m])[kv.first];
+                        dst.insert(dst.end(), kv.second.begin(), kv.second.end());
+                    } else {  // direct: back to the pool, usable on the original stream
+                        auto &dst = x->pool.free_lists[kv.first];
+                        dst.insert(dst.end(), kv.second.begin(), kv.second.end());
+                        x->pool.in_use -= kv.first * kv.second.size();
+                    }
                 }
-            }
+        }
         for (fhe_ct *x : marked) x->ready = nullptr, x->on = nullptr;
         on = false;
         return err;
@@ -604,7 +845,17 @@ struct Circuit {
     std::map<std::pair<const fhe_ct *, int>, fhe_ct *> lowered;
     Dag dag;
 
-    Circuit(fhe_ctx *ctx, const fhe_evk *e) : c(ctx), evk(e), rlk(&e->keys[0]), dag(ctx) {}
+    std::map<const fhe_ctx *, const fhe_evk *> evks;  // keys of every member context
+
+    Circuit(fhe_ctx *ctx, const fhe_evk *e) : c(ctx), evk(e), rlk(&e->keys[0]), dag(ctx) { evks[ctx] = e; }
+    // batches of another context (same device and plaintext prime; its
+    // stream is the leader's while the circuit runs) take part with keys e
+    void add_member(const fhe_evk *e)
+    {
+        evks[e->ctx] = e;
+        dag.add(e->ctx);
+    }
+    const KeySwitchKey *rlk_of(const fhe_ctx *cx) const { return &evks.at(cx)->keys[0]; }
     ~Circuit()
     {
         finish();
@@ -798,69 +1049,381 @@ struct Circuit {
         return keep(r);
     }
 
-    // (LT_k, EQ_k) of one digit pair
-    void digit(const fhe_ct *x, const fhe_ct *y, bool want_lt, bool want_eq, fhe_ct **lt_out, fhe_ct **eq_out)
+    // ---- merged operations: every item of one call runs in the same
+    // launches (one per step), traced item by item as the single forms are
+
+    // x lowered to each requested level.  Per source, the targets run in
+    // descending order, each from the nearest copy above it (cached, made
+    // earlier in the chain, or the source; at most FHE_MAXK primes a step);
+    // step r of every chain is one merged switch.  Multi-prime switches give
+    // the residues of single ones, so every path yields the same bits.
+    std::vector<const fhe_ct *> lower_many(const std::vector<std::pair<const fhe_ct *, int>> &req)
+    {
+        std::vector<const fhe_ct *> res(req.size(), nullptr);
+        if (err) return res;
+        std::map<const fhe_ct *, std::set<int, std::greater<int>>> want;
+        for (auto &r : req) {
+            if (!r.first) return res;
+            if (r.second < 1 || r.second > r.first->level) {
+                err = fhe_fail(c, FHE_ELEVEL, "bad target level");
+                return res;
+            }
+            if (r.second < r.first->level && !lowered.count(r)) want[r.first].insert(r.second);
+        }
+        struct Step {
+            const fhe_ct *x;
+            int from, to;
+        };
+        std::vector<std::vector<Step>> chains;
+        for (auto &kv : want) {
+            const fhe_ct *x = kv.first;
+            std::set<int> have;
+            std::vector<Step> ch;
+            for (int t : kv.second) {
+                int from = x->level;
+                for (int lv = t + 1; lv < x->level; lv++)
+                    if (have.count(lv) || lowered.count({x, lv})) {
+                        from = lv;
+                        break;
+                    }
+                while (from - t > FHE_MAXK) {
+                    ch.push_back({x, from, from - FHE_MAXK});
+                    from -= FHE_MAXK;
+                    have.insert(from);
+                }
+                ch.push_back({x, from, t});
+                have.insert(t);
+            }
+            chains.push_back(ch);
+        }
+        for (size_t r = 0; !err; r++) {
+            std::vector<SwitchItem> items;
+            std::vector<std::pair<const fhe_ct *, int>> keys;
+            std::vector<const fhe_ct *> ins;
+            for (auto &ch : chains)
+                if (r < ch.size()) {
+                    const Step &st = ch[r];
+                    const fhe_ct *src = st.from == st.x->level ? st.x : lowered.at({st.x, st.from});
+                    items.push_back(SwitchItem{src->ctx, src, st.from - st.to, nullptr});
+                    keys.push_back({st.x, st.to});
+                    ins.push_back(src);
+                }
+            if (items.empty()) break;
+            dag.begin(ins);
+            if ((err = op_modswitch_many(items))) return res;
+            std::vector<fhe_ct *> outs;
+            for (size_t i = 0; i < items.size(); i++) {
+                lowered[keys[i]] = items[i].out;
+                outs.push_back(items[i].out);
+            }
+            dag.end_all(outs);
+        }
+        for (size_t i = 0; i < req.size(); i++)
+            res[i] = req[i].second == req[i].first->level ? req[i].first : lowered.at(req[i]);
+        return res;
+    }
+
+    std::vector<fhe_ct *> mul_many(const std::vector<std::pair<const fhe_ct *, const fhe_ct *>> &pr)
+    {
+        FHE_RANGE("circuit mul");
+        std::vector<fhe_ct *> out(pr.size(), nullptr);
+        if (err || pr.empty()) return out;
+        std::vector<std::pair<const fhe_ct *, int>> req;
+        for (auto &q : pr) {
+            if (!q.first || !q.second) return out;
+            const int lv = std::min(q.first->level, q.second->level);
+            req.push_back({q.first, lv});
+            req.push_back({q.second, lv});
+        }
+        std::vector<const fhe_ct *> low = lower_many(req);
+        if (err) return out;
+        // the wave in `parts` merged operations (items dealt round robin),
+        // each on a stream of its own under the scheduler, so that one
+        // part's streaming steps overlap another's transforms
+        const int parts = dag.on ? std::max(1, std::min((int)pr.size(), c->wave_split)) : 1;
+        for (int part = 0; part < parts && !err; part++) {
+            std::vector<MulItem> items;
+            std::vector<size_t> at;
+            std::vector<const fhe_ct *> ins;
+            for (size_t i = part; i < pr.size(); i += parts) {
+                fhe_ctx *cx = low[2 * i]->ctx;
+                items.push_back(MulItem{cx, rlk_of(cx), low[2 * i], low[2 * i + 1], nullptr});
+                at.push_back(i);
+                ins.push_back(low[2 * i]);
+                ins.push_back(low[2 * i + 1]);
+            }
+            dag.begin(ins);
+            if ((err = op_mul_relin_many(items))) return out;
+            std::vector<fhe_ct *> po;
+            for (size_t j = 0; j < at.size(); j++) po.push_back(out[at[j]] = items[j].out);
+            dag.end_all(po);
+        }
+        for (size_t i = 0; i < pr.size() && !err; i++) {
+            trace(low[2 * i]->ctx, FHE_OP_MUL, low[2 * i]->level);
+            keep(out[i]);
+        }
+        return out;
+    }
+
+    // element-wise items; add / sub / lincomb operands aligned to their
+    // lowest level (lincomb: to lv when lv > 0)
+    std::vector<fhe_ct *> ew_many(std::vector<EwItem> items, const std::vector<int> &lv = {})
+    {
+        std::vector<fhe_ct *> out(items.size(), nullptr);
+        if (err || items.empty()) return out;
+        std::vector<std::pair<const fhe_ct *, int>> req;
+        for (size_t i = 0; i < items.size(); i++) {
+            const EwItem &e = items[i];
+            int l = 1 << 30;
+            for (int j = 0; j < e.n; j++) {
+                if (!e.x[j]) return out;
+                l = std::min(l, e.x[j]->level);
+            }
+            if (!lv.empty() && lv[i] > 0) l = lv[i];
+            for (int j = 0; j < e.n; j++) req.push_back({e.x[j], l});
+        }
+        std::vector<const fhe_ct *> low = lower_many(req);
+        if (err) return out;
+        size_t q = 0;
+        for (EwItem &e : items)
+            for (int j = 0; j < e.n; j++) e.x[j] = low[q++];
+        dag.begin(low);
+        if ((err = op_ew_many(items))) return out;
+        for (size_t i = 0; i < items.size(); i++) out[i] = items[i].out;
+        dag.end_all(out);
+        for (size_t i = 0; i < items.size(); i++) {
+            const EwItem &e = items[i];
+            const int l = e.x[0]->level;
+            switch (e.op) {
+            case FHE_EW_ADD: trace(e.c, FHE_OP_ADD, l); break;
+            case FHE_EW_SUB: trace(e.c, FHE_OP_SUB, l); break;
+            case FHE_EW_NEG: trace(e.c, FHE_OP_NEG, l); break;
+            case FHE_EW_CMUL: trace(e.c, FHE_OP_CMUL, l); break;
+            case FHE_EW_CADD: trace(e.c, FHE_OP_CADD, l); break;
+            default:
+                for (int j = 0; j < e.n; j++) {
+                    trace(e.c, FHE_OP_CMUL, l);
+                    if (j) trace(e.c, FHE_OP_ADD, l);
+                }
+            }
+            keep(out[i]);
+        }
+        return out;
+    }
+
+    static EwItem ew(int op, std::initializer_list<const fhe_ct *> xs, std::initializer_list<int64_t> ks = {})
+    {
+        EwItem e;
+        memset(&e, 0, sizeof(e));
+        e.op = op;
+        for (const fhe_ct *x : xs) e.x[e.n++] = x;
+        int j = 0;
+        for (int64_t k : ks) e.k[j++] = k;
+        e.c = e.x[0] ? e.x[0]->ctx : nullptr;
+        return e;
+    }
+
+    // (LT_k, EQ_k) of every digit pair k < d at once.  The schedule (the
+    // oracle's): z = x - y; powers z^n = (z^(n/2))^2 for n a power of two,
+    // else z^(2^a) z^(n-2^a); Paterson-Stockmeyer on the odd part with baby
+    // powers z^1..z^(B-1), B = 2^ceil(log2(p-1)/2): leaves L_k = sum_r
+    // c_(Bk+r) z^r at the level of their lowest power, blocks combined
+    // pairwise as lo + z^(B 2^(t-1)) hi; LT = c_(p-1) z^(p-1) + odd part;
+    // EQ = 1 - z^(p-1).  It runs wave by wave across digits (powers by depth,
+    // the leaves, each level of the block tree, the leading term), every
+    // wave one merged operation over all its products and digits; the
+    // operations and their levels are those of evaluating it digit by digit.
+    void digits(const fhe_ct *const *xs, const fhe_ct *const *ys, int d, bool want_lt, bool want_eq,
+                std::vector<fhe_ct *> &lt, std::vector<fhe_ct *> &eq)
     {
         const int p = (int)c->p;
-        *lt_out = *eq_out = nullptr;
-        fhe_ct *z = sub(x, y);
-        if (!z) return;
-        std::map<int, fhe_ct *> pw;
-        pw[1] = z;
-        std::function<fhe_ct *(int)> power = [&](int n) -> fhe_ct * {
-            auto it = pw.find(n);
-            if (it != pw.end()) return it->second;
-            fhe_ct *r;
+        lt.assign(d, nullptr);
+        eq.assign(d, nullptr);
+        std::vector<EwItem> zs;
+        for (int k = 0; k < d; k++) zs.push_back(ew(FHE_EW_SUB, {xs[k], ys[k]}));
+        std::vector<fhe_ct *> z = ew_many(zs);
+        if (err) return;
+        const std::vector<int> &cf = c->lt;
+        int lg = 0;
+        while ((1 << lg) < p - 1) lg++;  // ceil(log2(p-1))
+        const int B = 1 << ((lg + 1) / 2);
+        const int nblocks = (p - 2) / B + 1;
+        int T = 0;
+        while ((1 << T) < nblocks) T++;
+        // leaf terms and which tree nodes are empty
+        std::vector<std::vector<std::pair<int, int>>> terms(nblocks);
+        for (int k = 0; k < nblocks; k++)
+            for (int r = 1; r < B; r += 2)
+                if (B * k + r <= p - 2 && cf[B * k + r]) terms[k].push_back({r, cf[B * k + r]});
+        auto nonempty = [&](int k0, int t) {  // tree(k0, t) of digit() is not null
+            for (int k = k0; k < std::min(nblocks, k0 + (1 << t)); k++)
+                if (!terms[k].empty()) return true;
+            return false;
+        };
+        // exponents the schedule needs, with the power rule's operands
+        std::set<int> need;
+        std::function<void(int)> add_exp = [&](int n) {
+            if (need.count(n)) return;
+            need.insert(n);
+            if (n == 1) return;
             if ((n & (n - 1)) == 0) {
-                fhe_ct *h = power(n / 2);
-                r = mul(h, h);
+                add_exp(n / 2);
             } else {
                 int a = 1;
                 while (a * 2 < n) a *= 2;
-                fhe_ct *A = power(a);
-                fhe_ct *Bp = power(n - a);
-                r = mul(A, Bp);
+                add_exp(a);
+                add_exp(n - a);
             }
-            pw[n] = r;
-            return r;
         };
         if (want_lt) {
-            const std::vector<int> &cf = c->lt;
-            int lg = 0;
-            while ((1 << lg) < p - 1) lg++;  // ceil(log2(p-1))
-            const int B = 1 << ((lg + 1) / 2);
-            const int nblocks = (p - 2) / B + 1;
-            auto leaf = [&](int k) -> fhe_ct * {
-                std::vector<std::pair<int, int>> terms;
-                for (int r = 1; r < B; r += 2)
-                    if (B * k + r <= p - 2 && cf[B * k + r]) terms.push_back({r, cf[B * k + r]});
-                if (terms.empty()) return nullptr;
-                std::vector<fhe_ct *> cts;
-                for (auto &t : terms) cts.push_back(power(t.first));
-                if (err) return nullptr;
-                int lv = 1 << 30;
-                for (auto *t : cts) lv = std::min(lv, t->level);
-                return lincomb(cts, terms, lv);
-            };
-            std::function<fhe_ct *(int, int)> tree = [&](int k0, int t) -> fhe_ct * {
-                if (err || k0 >= nblocks) return nullptr;
-                if (t == 0) return leaf(k0);
-                const int half = 1 << (t - 1);
-                fhe_ct *lo = tree(k0, t - 1);
-                fhe_ct *hi = tree(k0 + half, t - 1);
-                if (!hi) return lo;
-                fhe_ct *gp = power(B * half);
-                fhe_ct *prod = mul(gp, hi);
-                return lo ? add(lo, prod) : prod;
-            };
-            int t = 0;
-            while ((1 << t) < nblocks) t++;
-            fhe_ct *odd = tree(0, t);
-            fhe_ct *zp = power(p - 1);
-            fhe_ct *lead = cmul(zp, cf[p - 1]);
-            *lt_out = odd ? add(lead, odd) : lead;
+            for (auto &tk : terms)
+                for (auto &tm : tk) add_exp(tm.first);
+            for (int t = 1; t <= T; t++)
+                for (int k0 = 0; k0 < nblocks; k0 += 1 << t)
+                    if (k0 + (1 << (t - 1)) < nblocks && nonempty(k0 + (1 << (t - 1)), t - 1))
+                        add_exp(B * (1 << (t - 1)));
         }
-        if (want_eq) *eq_out = cadd(neg(power(p - 1)), 1);
+        add_exp(p - 1);
+        std::map<int, std::vector<fhe_ct *>> pw;
+        pw[1] = z;
+        auto depth = [](int n) {
+            int r = 0;
+            while ((1 << r) < n) r++;
+            return r;
+        };
+        int maxd = 0;
+        for (int n : need) maxd = std::max(maxd, depth(n));
+        for (int dd = 1; dd <= maxd && !err; dd++) {
+            std::vector<int> ex;
+            std::vector<std::pair<const fhe_ct *, const fhe_ct *>> pr;
+            for (int n : need) {
+                if (n == 1 || depth(n) != dd) continue;
+                int a, b;
+                if ((n & (n - 1)) == 0) {
+                    a = b = n / 2;
+                } else {
+                    a = 1;
+                    while (a * 2 < n) a *= 2;
+                    b = n - a;
+                }
+                ex.push_back(n);
+                for (int k = 0; k < d; k++) pr.push_back({pw.at(a)[k], pw.at(b)[k]});
+            }
+            std::vector<fhe_ct *> r = mul_many(pr);
+            for (size_t i = 0; i < ex.size(); i++) pw[ex[i]] = std::vector<fhe_ct *>(r.begin() + i * d, r.begin() + (i + 1) * d);
+        }
+        if (err) return;
+        if (want_lt) {
+            // leaves L_k = sum_r c_{Bk+r} z^r at the level of their lowest power
+            // (chunks of at most 8 terms, one reduction each, the chunks
+            // then added in order: the traced operations are the terms'
+            // scalar products and additions either way)
+            std::map<std::pair<int, int>, std::vector<fhe_ct *>> node;  // (k0, t) -> per digit
+            std::vector<EwItem> li;
+            std::vector<int> llv;
+            std::vector<std::pair<int, int>> lkd;  // (block, digit) of each chunk
+            for (int k = 0; k < nblocks; k++) {
+                if (terms[k].empty()) continue;
+                for (int dg = 0; dg < d; dg++) {
+                    int lv = 1 << 30;
+                    for (auto &tm : terms[k]) lv = std::min(lv, pw.at(tm.first)[dg]->level);
+                    for (size_t t0 = 0; t0 < terms[k].size(); t0 += 8) {
+                        EwItem e = ew(FHE_EW_LINCOMB, {});
+                        for (size_t t = t0; t < std::min(terms[k].size(), t0 + 8); t++) {
+                            e.x[e.n] = pw.at(terms[k][t].first)[dg];
+                            e.k[e.n++] = terms[k][t].second;
+                        }
+                        e.c = e.x[0]->ctx;
+                        li.push_back(e);
+                        llv.push_back(lv);
+                        lkd.push_back({k, dg});
+                    }
+                }
+            }
+            std::vector<fhe_ct *> lr = ew_many(li, llv);
+            if (err) return;
+            std::map<std::pair<int, int>, std::vector<fhe_ct *>> parts;
+            for (size_t i = 0; i < lkd.size(); i++) parts[lkd[i]].push_back(lr[i]);
+            for (;;) {  // chunk sums, first two at a time, for every leaf at once
+                std::vector<EwItem> ad;
+                std::vector<std::pair<int, int>> who;
+                for (auto &kv : parts)
+                    if (kv.second.size() > 1) {
+                        ad.push_back(ew(FHE_EW_ADD, {kv.second[0], kv.second[1]}));
+                        who.push_back(kv.first);
+                    }
+                if (ad.empty()) break;
+                std::vector<fhe_ct *> sm = ew_many(ad);
+                if (err) return;
+                for (size_t i = 0; i < who.size(); i++) {
+                    auto &v = parts[who[i]];
+                    v.erase(v.begin(), v.begin() + 2);
+                    v.insert(v.begin(), sm[i]);
+                }
+            }
+            for (auto &kv : parts) {
+                auto &v = node[{kv.first.first, 0}];
+                v.resize(d, nullptr);
+                v[kv.first.second] = kv.second[0];
+            }
+            // the block tree, one level at a time: node(k0, t) = lo + z^(B half) hi
+            for (int t = 1; t <= T && !err; t++) {
+                const int half = 1 << (t - 1);
+                std::vector<std::pair<const fhe_ct *, const fhe_ct *>> pr;
+                std::vector<int> pk;
+                for (int k0 = 0; k0 < nblocks; k0 += 1 << t) {
+                    auto hi = node.find({k0 + half, t - 1});
+                    if (hi == node.end()) {
+                        auto lo = node.find({k0, t - 1});
+                        if (lo != node.end()) node[{k0, t}] = lo->second;
+                        continue;
+                    }
+                    for (int dg = 0; dg < d; dg++) pr.push_back({pw.at(B * half)[dg], hi->second[dg]});
+                    pk.push_back(k0);
+                }
+                std::vector<fhe_ct *> prod = mul_many(pr);
+                if (err) return;
+                std::vector<EwItem> ad;
+                std::vector<int> ak;
+                for (size_t i = 0; i < pk.size(); i++) {
+                    const int k0 = pk[i];
+                    std::vector<fhe_ct *> pv(prod.begin() + i * d, prod.begin() + (i + 1) * d);
+                    auto lo = node.find({k0, t - 1});
+                    if (lo == node.end()) {
+                        node[{k0, t}] = pv;
+                        continue;
+                    }
+                    for (int dg = 0; dg < d; dg++) ad.push_back(ew(FHE_EW_ADD, {lo->second[dg], pv[dg]}));
+                    ak.push_back(k0);
+                }
+                std::vector<fhe_ct *> sums = ew_many(ad);
+                if (err) return;
+                for (size_t i = 0; i < ak.size(); i++)
+                    node[{ak[i], t}] = std::vector<fhe_ct *>(sums.begin() + i * d, sums.begin() + (i + 1) * d);
+            }
+            // LT_k = c_{p-1} z^(p-1) + odd part
+            std::vector<EwItem> ld;
+            for (int dg = 0; dg < d; dg++) ld.push_back(ew(FHE_EW_CMUL, {pw.at(p - 1)[dg]}, {cf[p - 1]}));
+            std::vector<fhe_ct *> lead = ew_many(ld);
+            if (err) return;
+            auto odd = node.find({0, T});
+            if (odd == node.end()) {
+                lt = lead;
+            } else {
+                std::vector<EwItem> ad;
+                for (int dg = 0; dg < d; dg++) ad.push_back(ew(FHE_EW_ADD, {lead[dg], odd->second[dg]}));
+                lt = ew_many(ad);
+            }
+        }
+        if (want_eq && !err) {
+            // EQ_k = 1 - z^(p-1)
+            std::vector<EwItem> ng, ca;
+            for (int dg = 0; dg < d; dg++) ng.push_back(ew(FHE_EW_NEG, {pw.at(p - 1)[dg]}));
+            std::vector<fhe_ct *> n = ew_many(ng);
+            if (err) return;
+            for (int dg = 0; dg < d; dg++) ca.push_back(ew(FHE_EW_CADD, {n[dg]}, {1}));
+            eq = ew_many(ca);
+        }
     }
 
     // (LT_k, EQ_k) of one pair of full digits in [0, p): the bivariate LT
@@ -924,16 +1487,141 @@ struct Circuit {
         }
     }
 
+    // Several comparisons (and max/min selections) at once: the digit
+    // polynomials of all of them in one digits() call per kind, the merge
+    // trees level by level and the selections as merged operations.  Each
+    // result equals the comparison run alone.
+    struct Req {
+        const fhe_ct *const *x;
+        const fhe_ct *const *y;
+        int d;
+        bool want_lt, want_eq, maxmin;
+        fhe_ct **lt, **eq;  // comparison outputs (either may be null)
+        fhe_ct **mx, **mn;  // max / min digits (maxmin; either may be null)
+    };
+    void compare_many(std::vector<Req> &rq)
+    {
+        if (err || rq.empty()) return;
+        // digit results (L_k, E_k) of every request; requests of one kind
+        // (what the digit circuit must produce) share one digits() call
+        std::vector<std::vector<std::pair<fhe_ct *, fhe_ct *>>> nodes(rq.size());
+        for (int kind = 0; kind < 4 && !err; kind++) {
+            const bool wl = kind & 1, we = kind & 2;
+            std::vector<const fhe_ct *> X, Y;
+            std::vector<size_t> who;
+            for (size_t i = 0; i < rq.size(); i++) {
+                const Req &r = rq[i];
+                const bool rl = r.want_lt || r.maxmin, re = r.d > 1 || (r.want_eq && !r.maxmin);
+                if (rl != wl || re != we) continue;
+                for (int k = 0; k < r.d; k++) X.push_back(r.x[k]), Y.push_back(r.y[k]);
+                who.push_back(i);
+            }
+            if (who.empty()) continue;
+            std::vector<fhe_ct *> L, E;
+            digits(X.data(), Y.data(), (int)X.size(), wl, we, L, E);
+            size_t q = 0;
+            for (size_t i : who)
+                for (int k = 0; k < rq[i].d; k++, q++) nodes[i].push_back({L[q], E[q]});
+        }
+        if (err) return;
+        // merge trees, one level of every request at a time: pairs (2i+1
+        // high, 2i low) -> (L_hi + E_hi L_lo, E_hi E_lo); the root skips the
+        // E product unless EQ is wanted; an odd last node passes up
+        for (;;) {
+            std::vector<std::pair<const fhe_ct *, const fhe_ct *>> pr;
+            struct Slot {
+                size_t req, pair;
+                int mi, ei;  // indices into pr (-1: none)
+            };
+            std::vector<Slot> slots;
+            for (size_t i = 0; i < rq.size(); i++) {
+                auto &nd = nodes[i];
+                if (nd.size() < 2) continue;
+                const bool root = nd.size() == 2, wl = rq[i].want_lt || rq[i].maxmin;
+                const bool we = rq[i].want_eq && !rq[i].maxmin;
+                for (size_t j = 0; j < nd.size() / 2; j++) {
+                    auto lo = nd[2 * j], hi = nd[2 * j + 1];
+                    Slot sl{i, j, -1, -1};
+                    if (wl) sl.mi = (int)pr.size(), pr.push_back({hi.second, lo.first});
+                    if (we || !root) sl.ei = (int)pr.size(), pr.push_back({hi.second, lo.second});
+                    slots.push_back(sl);
+                }
+            }
+            if (slots.empty()) break;
+            std::vector<fhe_ct *> prod = mul_many(pr);
+            if (err) return;
+            std::vector<EwItem> ad;
+            std::vector<size_t> ai;
+            for (size_t s = 0; s < slots.size(); s++)
+                if (slots[s].mi >= 0) {
+                    auto hi = nodes[slots[s].req][2 * slots[s].pair + 1];
+                    ad.push_back(ew(FHE_EW_ADD, {hi.first, prod[slots[s].mi]}));
+                    ai.push_back(s);
+                }
+            std::vector<fhe_ct *> sums = ew_many(ad);
+            if (err) return;
+            std::vector<fhe_ct *> Ls(slots.size(), nullptr);
+            for (size_t a = 0; a < ai.size(); a++) Ls[ai[a]] = sums[a];
+            std::vector<std::vector<std::pair<fhe_ct *, fhe_ct *>>> nxt(rq.size());
+            for (size_t s = 0; s < slots.size(); s++)
+                nxt[slots[s].req].push_back({Ls[s], slots[s].ei >= 0 ? prod[slots[s].ei] : nullptr});
+            for (size_t i = 0; i < rq.size(); i++) {
+                if (nodes[i].size() < 2) continue;
+                if (nodes[i].size() % 2) nxt[i].push_back(nodes[i].back());
+                nodes[i] = nxt[i];
+            }
+        }
+        // comparison outputs
+        for (size_t i = 0; i < rq.size(); i++) {
+            const Req &r = rq[i];
+            if (r.maxmin) continue;
+            if (r.lt) *r.lt = r.want_lt ? release(nodes[i][0].first) : nullptr;
+            if (r.eq) *r.eq = r.want_eq ? release(nodes[i][0].second) : nullptr;
+        }
+        // selections: t_k = L (y_k - x_k), max_k = x_k + t_k, min_k = y_k - t_k
+        std::vector<EwItem> df;
+        std::vector<std::pair<size_t, int>> at;
+        for (size_t i = 0; i < rq.size(); i++)
+            if (rq[i].maxmin)
+                for (int k = 0; k < rq[i].d; k++) {
+                    df.push_back(ew(FHE_EW_SUB, {rq[i].y[k], rq[i].x[k]}));
+                    at.push_back({i, k});
+                }
+        if (df.empty()) return;
+        std::vector<fhe_ct *> diff = ew_many(df);
+        if (err) return;
+        std::vector<std::pair<const fhe_ct *, const fhe_ct *>> pr;
+        for (size_t a = 0; a < at.size(); a++) pr.push_back({nodes[at[a].first][0].first, diff[a]});
+        std::vector<fhe_ct *> t = mul_many(pr);
+        if (err) return;
+        std::vector<EwItem> sel;
+        for (size_t a = 0; a < at.size(); a++) {
+            const Req &r = rq[at[a].first];
+            const int k = at[a].second;
+            sel.push_back(ew(FHE_EW_ADD, {r.x[k], t[a]}));
+            sel.push_back(ew(FHE_EW_SUB, {r.y[k], t[a]}));
+        }
+        std::vector<fhe_ct *> mm = ew_many(sel);
+        if (err) return;
+        for (size_t a = 0; a < at.size(); a++) {
+            const Req &r = rq[at[a].first];
+            const int k = at[a].second;
+            if (r.mx) r.mx[k] = release(mm[2 * a]);
+            if (r.mn) r.mn[k] = release(mm[2 * a + 1]);
+        }
+    }
+
     void compare(const fhe_ct *const *xs, const fhe_ct *const *ys, int d, bool want_lt, bool want_eq,
                  fhe_ct **lt, fhe_ct **eq, bool bivariate = false)
     {
-        std::vector<std::pair<fhe_ct *, fhe_ct *>> nodes(d, {nullptr, nullptr});
-        for (int k = 0; k < d && !err; k++) {
-            if (bivariate)
-                digit_bv(xs[k], ys[k], want_lt, d > 1 || want_eq, &nodes[k].first, &nodes[k].second);
-            else
-                digit(xs[k], ys[k], want_lt, d > 1 || want_eq, &nodes[k].first, &nodes[k].second);
+        if (!bivariate) {
+            std::vector<Req> rq{Req{xs, ys, d, want_lt, want_eq, false, lt, eq, nullptr, nullptr}};
+            compare_many(rq);
+            return;
         }
+        std::vector<std::pair<fhe_ct *, fhe_ct *>> nodes(d, {nullptr, nullptr});
+        for (int k = 0; k < d && !err; k++)
+            digit_bv(xs[k], ys[k], want_lt, d > 1 || want_eq, &nodes[k].first, &nodes[k].second);
         while (nodes.size() > 1 && !err) {
             const bool root = nodes.size() == 2;
             std::vector<std::pair<fhe_ct *, fhe_ct *>> nxt;
@@ -962,34 +1650,52 @@ struct Circuit {
 static int circuit_max_min_in(Circuit &C, const fhe_ct *const *x, const fhe_ct *const *y, int d, fhe_ct **mx,
                               fhe_ct **mn)
 {
-    fhe_ct *L = nullptr;
-    C.compare(x, y, d, true, false, &L, nullptr);
-    if (C.err) return C.err;
-    C.keep(L);
-    for (int k = 0; k < d; k++) {
-        fhe_ct *diff = C.sub(y[k], x[k]);
-        fhe_ct *t = C.mul(L, diff);
-        fhe_ct *a = C.add(x[k], t);
-        fhe_ct *b = C.sub(y[k], t);
-        if (C.err) return C.err;
-        if (mx) mx[k] = C.release(a);
-        if (mn) mn[k] = C.release(b);
-    }
-    return 0;
+    std::vector<Circuit::Req> rq{Circuit::Req{x, y, d, true, false, true, nullptr, nullptr, mx, mn}};
+    C.compare_many(rq);
+    return C.err;
 }
 
-// Several independent comparisons in one circuit (one dependency scheduler),
-// so that with c->multistream their operations interleave on the streams.
+// Several independent comparisons and selections in one circuit: their
+// digit polynomials, merge trees and selections run as merged operations.
 int circuit_multi(fhe_ctx *c, const fhe_evk *evk, const std::vector<MultiItem> &items)
 {
     Circuit C(c, evk);
+    std::vector<Circuit::Req> rq;
     for (const MultiItem &it : items) {
-        if (C.err) break;
         if (it.maxmin)
-            circuit_max_min_in(C, it.x, it.y, it.d, it.out0, it.out1);
+            rq.push_back(Circuit::Req{it.x, it.y, it.d, true, false, true, nullptr, nullptr, it.out0, it.out1});
         else
-            C.compare(it.x, it.y, it.d, it.out0 != nullptr, it.out1 != nullptr, it.out0, it.out1);
+            rq.push_back(Circuit::Req{it.x, it.y, it.d, it.out0 != nullptr, it.out1 != nullptr, false, it.out0,
+                                      it.out1, nullptr, nullptr});
     }
+    C.compare_many(rq);
+    C.finish();
+    return C.err;
+}
+
+// The same over several contexts of one device and plaintext prime (one
+// circuit: every merged step is one launch across their ring degrees and
+// levels).  Item i uses keys evks[i]; evks[0]'s context leads.  The caller
+// holds every context's lock and has pointed every context's stream (and
+// pool stream) at the leader's for the call.
+int circuit_multi_ctx(const std::vector<const fhe_evk *> &evks, const std::vector<MultiItem> &items)
+{
+    if (evks.empty() || evks.size() != items.size()) return FHE_EINVAL;
+    fhe_ctx *lead = evks[0]->ctx;
+    for (const fhe_evk *e : evks)
+        if (e->ctx->p != lead->p || e->ctx->device != lead->device)
+            return fhe_fail(lead, FHE_EMISMATCH, "fused contexts differ in plaintext prime or device");
+    Circuit C(lead, evks[0]);
+    for (const fhe_evk *e : evks) C.add_member(e);
+    std::vector<Circuit::Req> rq;
+    for (const MultiItem &it : items) {
+        if (it.maxmin)
+            rq.push_back(Circuit::Req{it.x, it.y, it.d, true, false, true, nullptr, nullptr, it.out0, it.out1});
+        else
+            rq.push_back(Circuit::Req{it.x, it.y, it.d, it.out0 != nullptr, it.out1 != nullptr, false, it.out0,
+                                      it.out1, nullptr, nullptr});
+    }
+    C.compare_many(rq);
     C.finish();
     return C.err;
 }

@@ -229,6 +229,7 @@ struct fhe_ctx {
     // them concurrently.  Each branch has its own capture-private free list.
     bool capturing = false;
     bool multistream = false;  // the same scheduling without capture (batch execution)
+    int wave_split = 2;        // a circuit's product wave runs as this many merged operations (streams)
     std::vector<cudaStream_t> branch_streams;
     std::vector<cudaEvent_t> branch_events;  // reused by every capture
 
@@ -367,6 +368,41 @@ void launch_ntt_relin_ms_many(const std::vector<NttDownArgs> &a);
 void launch_ntt_modswitch_many(const std::vector<NttSwitchArgs> &a);
 void launch_ntt_multiswitch_many(const std::vector<NttSwitchArgs> &a);
 
+// Streaming kernels over several batches per launch (many.cu).
+enum { FHE_EW_ADD = 0, FHE_EW_SUB = 1, FHE_EW_NEG = 2, FHE_EW_LINCOMB = 3, FHE_EW_CMUL = 4, FHE_EW_CADD = 5 };
+struct EwArgs {  // out = op(x[0..n)) over outer polys of `level` limbs; k: centred scalars
+    fhe_ctx *c;
+    int op, n;
+    const u64 *x[8];
+    int64_t k[8];
+    u64 *out;
+    int outer, level;
+};
+struct TensorArgs {
+    fhe_ctx *c;
+    const u64 *a, *b;
+    u64 *out;
+    int count, level;
+};
+struct KsInnerArgs {
+    fhe_ctx *c;
+    const u64 *ext, *xbase;
+    long long x_outer;
+    const u64 *ksk;
+    u64 *acc;
+    int count, level;
+};
+struct FoldArgs {  // rms: outer = ciphertexts; multi-switch: outer = polys, k switches
+    fhe_ctx *c;
+    u64 *src;
+    int outer, level, k;
+};
+void launch_ew_many(const std::vector<EwArgs> &items);
+void launch_tensor_many(const std::vector<TensorArgs> &items);
+void launch_ks_inner_many(const std::vector<KsInnerArgs> &items);
+void launch_rms_fold_many(const std::vector<FoldArgs> &items);
+void launch_ms_fold_many(const std::vector<FoldArgs> &items);
+
 // kernel launchers (ntt.cu, kernels.cu); scale arrays are device pointers
 void launch_ntt_fwd_plain(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap &m, int njobs);
 void launch_add_plain(fhe_ctx *c, const u64 *a, const u64 *m, u64 *out, int count, int npoly, int level, int sub);
@@ -455,6 +491,29 @@ int op_relin(fhe_ctx *c, const KeySwitchKey &k, const fhe_ct *d, fhe_ct **out);
 int op_rotate(fhe_ctx *c, const KeySwitchKey &k, const fhe_ct *a, fhe_ct **out);
 int op_mul_relin(fhe_ctx *c, const KeySwitchKey &rlk, const fhe_ct *a, const fhe_ct *b, fhe_ct **out);
 int galois_perm(fhe_ctx *c, int64_t g, const int **perm);
+// several batches at once (one launch per step for all; eval.cu)
+struct MulItem {  // out = relinearised (and, above level 1, switched) a * b
+    fhe_ctx *c;
+    const KeySwitchKey *rlk;
+    const fhe_ct *a, *b;
+    fhe_ct *out;
+};
+struct SwitchItem {  // out = a with its k last primes dropped
+    fhe_ctx *c;
+    const fhe_ct *a;
+    int k;
+    fhe_ct *out;
+};
+struct EwItem {  // out = op(x[0..n)) with centred scalars k (FHE_EW_*)
+    fhe_ctx *c;
+    int op, n;
+    const fhe_ct *x[8];
+    int64_t k[8];
+    fhe_ct *out;
+};
+int op_mul_relin_many(std::vector<MulItem> &items);
+int op_modswitch_many(std::vector<SwitchItem> &items);
+int op_ew_many(std::vector<EwItem> &items);
 int circuit_compare_bv(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
                        fhe_ct **lt, fhe_ct **eq);
 int circuit_compare(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
@@ -473,6 +532,7 @@ struct MultiItem {
     fhe_ct **out1;
 };
 int circuit_multi(fhe_ctx *c, const fhe_evk *evk, const std::vector<MultiItem> &items);
+int circuit_multi_ctx(const std::vector<const fhe_evk *> &evks, const std::vector<MultiItem> &items);
 int op_slice(fhe_ctx *c, const fhe_ct *a, int start, int n, fhe_ct **out);
 int op_concat(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **out);
 std::vector<int64_t> tournament_galois(const fhe_ctx *c);

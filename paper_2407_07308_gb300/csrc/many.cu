@@ -1,0 +1,379 @@
+// many.cu -- the streaming kernels of a product or a switch over several
+// batches in one launch: element-wise ciphertext arithmetic, the tensor
+// product, the key-switching inner product and the switch folds.
+//
+// A launch carries a table of up to FHE_SEGS segments (one batch each, of any
+// context, level and size on one device); segment s owns a contiguous range
+// of blocks, so a block never straddles two segments and every warp still
+// reads 256 contiguous bytes.  The arithmetic per element is the one of the
+// single-batch kernels in kernels.cu; only the addressing differs.
+#include <string.h>
+
+#include "fhe_internal.h"
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr int EW_ELEMS = TPB * 4;  // elements per block of the element-wise kernels
+
+// |k| < q: k mod q in [0, q)
+__device__ __forceinline__ u64 small_mod(int64_t k, u64 q) { return k >= 0 ? (u64)k : q - (u64)(-k); }
+
+template <class S>
+__device__ __forceinline__ int block_seg(const S *s, int n)
+{
+    int sg = 0;
+    while (sg + 1 < n && s[sg + 1].b0 <= (int)blockIdx.x) sg++;
+    return sg;
+}
+
+// ---- element-wise: x0 + x1, x0 - x1, -x0, sum_t k_t x_t, k0 x0, x0 + k0 on
+// poly 0 of 2-poly ciphertexts (poly 1 copied) ------------------------------
+
+struct EwSeg {
+    const u64 *x[8];
+    u64 *out;
+    const ModQ *mq;
+    long long total;  // elements: outer * level * N
+    int logN, level, n, op, b0, pad;
+    int64_t k[8];     // centred scalars, |k| < p
+};
+
+struct EwTable {
+    int nseg, pad;
+    EwSeg s[FHE_SEGS];
+};
+
+__global__ void k_ew_many(const __grid_constant__ EwTable t)
+{
+    const EwSeg &S = t.s[block_seg(t.s, t.nseg)];
+    const long long base = (long long)(blockIdx.x - S.b0) * EW_ELEMS;
+    for (int e = threadIdx.x; e < EW_ELEMS; e += TPB) {
+        const long long idx = base + e;
+        if (idx >= S.total) break;
+        const long long li = idx >> S.logN;
+        const int i = (int)(li % S.level);
+        const u64 q = S.mq[i].q;
+        u64 r;
+        switch (S.op) {
+        case FHE_EW_ADD: r = addmod(S.x[0][idx], S.x[1][idx], q); break;
+        case FHE_EW_SUB: r = submod(S.x[0][idx], S.x[1][idx], q); break;
+        case FHE_EW_NEG: r = negmod(S.x[0][idx], q); break;
+        case FHE_EW_CMUL: r = barrett128((u128)S.x[0][idx] * small_mod(S.k[0], q), S.mq[i]); break;
+        case FHE_EW_CADD: {
+            const int poly = (int)((li / S.level) % 2);
+            r = poly == 0 ? addmod(S.x[0][idx], small_mod(S.k[0], q), q) : S.x[0][idx];
+            break;
+        }
+        default: {  // FHE_EW_LINCOMB: at most eight products below the Barrett bound
+            u128 acc = 0;
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if (j < S.n) acc += (u128)S.x[j][idx] * small_mod(S.k[j], q);
+            r = barrett128(acc, S.mq[i]);
+        }
+        }
+        S.out[idx] = r;
+    }
+}
+
+// ---- tensor: (a0,a1) x (b0,b1) -> (a0 b0, a0 b1 + a1 b0, a1 b1) -----------
+
+struct TensorSeg {
+    const u64 *a, *b;
+    u64 *out;
+    const ModQ *mq;
+    long long total;  // count * level * N
+    int logN, level, b0, pad;
+};
+
+struct TensorTable {
+    int nseg, pad;
+    TensorSeg s[FHE_SEGS];
+};
+
+__global__ void k_tensor_many(const __grid_constant__ TensorTable t)
+{
+    const TensorSeg &S = t.s[block_seg(t.s, t.nseg)];
+    const long long LN = (long long)S.level << S.logN;
+    const long long base = (long long)(blockIdx.x - S.b0) * EW_ELEMS;
+    for (int e = threadIdx.x; e < EW_ELEMS; e += TPB) {
+        const long long idx = base + e;
+        if (idx >= S.total) break;
+        const long long c = idx / LN, r = idx % LN;
+        const ModQ m = S.mq[(int)(r >> S.logN)];
+        const u64 a0 = S.a[2 * c * LN + r], a1 = S.a[(2 * c + 1) * LN + r];
+        const u64 b0 = S.b[2 * c * LN + r], b1 = S.b[(2 * c + 1) * LN + r];
+        S.out[3 * c * LN + r] = barrett128((u128)a0 * b0, m);
+        S.out[(3 * c + 1) * LN + r] = barrett128((u128)a0 * b1 + (u128)a1 * b0, m);
+        S.out[(3 * c + 2) * LN + r] = barrett128((u128)a1 * b1, m);
+    }
+}
+
+// ---- key-switching inner product ------------------------------------------
+// acc[c][pi][r] = sum_j y_j[r] ksk_j[pi][prime(r)], y_j[r] = x_c[r] for r in
+// digit j, else the ModUp limb.  A block covers TPB coefficients of one
+// extended limb r for CB ciphertexts; each thread loads its 2 dnum key words
+// once for its CB ciphertexts.
+
+constexpr int KS_CB = 4;
+
+struct KsSeg {
+    const u64 *ext, *xbase, *ksk;
+    u64 *acc;
+    const ModQ *mq;
+    long long x_outer;
+    int count, l, K, L, dnum, logN, b0, nbx;  // nbx: blocks along n
+};
+
+struct KsTable {
+    int nseg, pad;
+    KsSeg s[FHE_SEGS];
+};
+
+__global__ void __launch_bounds__(TPB, 3) k_ks_inner_many(const __grid_constant__ KsTable t)
+{
+    const KsSeg &S = t.s[block_seg(t.s, t.nseg)];
+    const int lb = blockIdx.x - S.b0;
+    const int lK = S.l + S.K, N = 1 << S.logN;
+    const int bx = lb % S.nbx, r = (lb / S.nbx) % lK, cz = lb / (S.nbx * lK);
+    const int n = bx * TPB + threadIdx.x;
+    if (n >= N) return;
+    const int prime = r < S.l ? r : S.L + (r - S.l);
+    const ModQ m = S.mq[prime];
+    const int LK = S.L + S.K;
+    const int rdig = r < S.l ? r / S.K : -1;
+    const int c0 = cz * KS_CB;
+    const int ncb = min(KS_CB, S.count - c0);
+    u128 a0[KS_CB], a1[KS_CB];
+#pragma unroll
+    for (int cc = 0; cc < KS_CB; cc++) a0[cc] = a1[cc] = 0;
+    for (int j = 0; j < S.dnum; j++) {
+        const u64 k0 = S.ksk[(((long long)j * 2 + 0) * LK + prime) * N + n];
+        const u64 k1 = S.ksk[(((long long)j * 2 + 1) * LK + prime) * N + n];
+        u64 y[KS_CB];
+#pragma unroll
+        for (int cc = 0; cc < KS_CB; cc++) {
+            const int c = c0 + cc;
+            if (cc < ncb)
+                y[cc] = (j == rdig) ? S.xbase[c * S.x_outer + (long long)r * N + n]
+                                    : S.ext[(((long long)c * S.dnum + j) * lK + r) * N + n];
+        }
+#pragma unroll
+        for (int cc = 0; cc < KS_CB; cc++) {
+            if (cc < ncb) {
+                a0[cc] += (u128)y[cc] * k0;
+                a1[cc] += (u128)y[cc] * k1;
+            }
+        }
+    }
+#pragma unroll
+    for (int cc = 0; cc < KS_CB; cc++) {
+        const int c = c0 + cc;
+        if (cc < ncb) {
+            S.acc[(((long long)c * 2 + 0) * lK + r) * N + n] = barrett128(a0[cc], m);
+            S.acc[(((long long)c * 2 + 1) * lK + r) * N + n] = barrett128(a1[cc], m);
+        }
+    }
+}
+
+// ---- folds of the fused relinearise + switch and of the multi-prime switch
+
+struct FoldSeg {
+    u64 *src;
+    const ModQ *mq;
+    const void *P;    // RelinMSParams (k = 0) or MultiSwitchParams
+    long long total;  // outer * N
+    int logN, l, k, K, b0, pad;
+};
+
+struct FoldTable {
+    int nseg, rms;
+    FoldSeg s[FHE_SEGS];
+};
+
+// rms: src[c][pi] = (t_0 .. t_{K-1}, Y') -> Y' - sum_k t_k p_k^-1 mod q_{l-1}.
+// multi-switch: src[o] = (X'_0 .. X'_{k-1}) -> w_j = X'_j - sum_{t<j} w_t F[j][t].
+__global__ void k_fold_many(const __grid_constant__ FoldTable t)
+{
+    const FoldSeg &S = t.s[block_seg(t.s, t.nseg)];
+    const int N = 1 << S.logN;
+    const long long base = (long long)(blockIdx.x - S.b0) * EW_ELEMS;
+    for (int e = threadIdx.x; e < EW_ELEMS; e += TPB) {
+        const long long idx = base + e;
+        if (idx >= S.total) break;
+        const long long o = idx >> S.logN;
+        const int n = (int)(idx & (N - 1));
+        if (t.rms) {
+            const RelinMSParams *P = (const RelinMSParams *)S.P;
+            const ModQ mm = S.mq[S.l - 1];
+            u64 *b = S.src + o * (S.K + 1) * N + n;
+            u128 a = 0;
+            for (int k = 0; k < S.K; k++) a += (u128)b[(long long)k * N] * P->pkinv[k];
+            b[(long long)S.K * N] = submod(b[(long long)S.K * N], barrett128(a, mm), mm.q);
+        } else {
+            const MultiSwitchParams *P = (const MultiSwitchParams *)S.P;
+            u64 *b = S.src + o * S.k * N + n;
+            u64 w[FHE_MAXK];
+#pragma unroll
+            for (int j = 0; j < FHE_MAXK; j++) {
+                if (j < S.k) {
+                    const ModQ mj = S.mq[S.l - 1 - j];
+                    u128 a = 0;
+#pragma unroll
+                    for (int q = 0; q < FHE_MAXK; q++)
+                        if (q < j) a += (u128)w[q] * P->F[j][q];
+                    w[j] = submod(b[(long long)j * N], barrett128(a, mj), mj.q);
+                    b[(long long)j * N] = w[j];
+                }
+            }
+        }
+    }
+}
+
+int ew_blocks(long long total) { return (int)((total + EW_ELEMS - 1) / EW_ELEMS); }
+
+// Launches kern over `items` in tables of at most FHE_SEGS segments; fill
+// sets segment s from an item and returns its blocks (0 = nothing to do) and
+// its algorithmic bytes.
+template <class Table, class Item, class Fill, class Launch>
+void launch_tables(const std::vector<Item> &items, int cls, Fill fill, Launch launch)
+{
+    size_t i = 0;
+    while (i < items.size()) {
+        Table t;
+        memset(&t, 0, sizeof(t));
+        fhe_ctx *c = items[i].c;
+        int blocks = 0;
+        double bytes = 0;
+        for (; i < items.size() && t.nseg < FHE_SEGS; i++) {
+            double b = 0;
+            const int nb = fill(t.s[t.nseg], items[i], &b);
+            if (nb <= 0) continue;
+            t.s[t.nseg].b0 = blocks;
+            blocks += nb;
+            bytes += b;
+            t.nseg++;
+        }
+        if (!t.nseg) continue;
+        prof_begin(c, cls, bytes);
+        launch(t, blocks, c->stream);
+        prof_end(c);
+        c->launches++;
+    }
+}
+
+}  // namespace
+
+void launch_ew_many(const std::vector<EwArgs> &items)
+{
+    launch_tables<EwTable>(
+        items, FHE_K_ELEMWISE,
+        [](EwSeg &S, const EwArgs &a, double *bytes) {
+            S.total = (long long)a.outer * a.level * a.c->N;
+            if (S.total <= 0) return 0;
+            for (int j = 0; j < 8; j++) S.x[j] = a.x[j], S.k[j] = a.k[j];
+            S.out = a.out;
+            S.mq = a.c->d_mq;
+            S.logN = a.c->logN;
+            S.level = a.level;
+            S.n = a.n;
+            S.op = a.op;
+            const int reads = a.op == FHE_EW_LINCOMB ? a.n : (a.op == FHE_EW_ADD || a.op == FHE_EW_SUB) ? 2 : 1;
+            *bytes = 8.0 * (reads + 1) * S.total;
+            return ew_blocks(S.total);
+        },
+        [](const EwTable &t, int blocks, cudaStream_t s) { k_ew_many<<<blocks, TPB, 0, s>>>(t); });
+}
+
+void launch_tensor_many(const std::vector<TensorArgs> &items)
+{
+    launch_tables<TensorTable>(
+        items, FHE_K_TENSOR,
+        [](TensorSeg &S, const TensorArgs &a, double *bytes) {
+            S.total = (long long)a.count * a.level * a.c->N;
+            if (S.total <= 0) return 0;
+            S.a = a.a;
+            S.b = a.b;
+            S.out = a.out;
+            S.mq = a.c->d_mq;
+            S.logN = a.c->logN;
+            S.level = a.level;
+            *bytes = 8.0 * 7 * S.total;
+            return ew_blocks(S.total);
+        },
+        [](const TensorTable &t, int blocks, cudaStream_t s) { k_tensor_many<<<blocks, TPB, 0, s>>>(t); });
+}
+
+void launch_ks_inner_many(const std::vector<KsInnerArgs> &items)
+{
+    launch_tables<KsTable>(
+        items, FHE_K_KS_INNER,
+        [](KsSeg &S, const KsInnerArgs &a, double *bytes) {
+            fhe_ctx *c = a.c;
+            if (a.count <= 0) return 0;
+            S.ext = a.ext;
+            S.xbase = a.xbase;
+            S.ksk = a.ksk;
+            S.acc = a.acc;
+            S.mq = c->d_mq;
+            S.x_outer = a.x_outer;
+            S.count = a.count;
+            S.l = a.level;
+            S.K = c->K;
+            S.L = c->L;
+            S.dnum = c->modup[a.level].dnum;
+            S.logN = c->logN;
+            S.nbx = (c->N + TPB - 1) / TPB;
+            // per (r, n): 2 dnum key words once per CB ciphertexts, dnum inputs and 2 outputs per ciphertext
+            *bytes = 8.0 * (double)(a.level + c->K) * c->N * (2.0 * S.dnum + a.count * (S.dnum + 2.0));
+            return S.nbx * (a.level + c->K) * ((a.count + KS_CB - 1) / KS_CB);
+        },
+        [](const KsTable &t, int blocks, cudaStream_t s) { k_ks_inner_many<<<blocks, TPB, 0, s>>>(t); });
+}
+
+void launch_rms_fold_many(const std::vector<FoldArgs> &items)
+{
+    launch_tables<FoldTable>(
+        items, FHE_K_ELEMWISE,
+        [](FoldSeg &S, const FoldArgs &a, double *bytes) {
+            fhe_ctx *c = a.c;
+            S.total = (long long)a.outer * 2 * c->N;  // (ct, poly) pairs
+            if (S.total <= 0) return 0;
+            S.src = a.src;
+            S.mq = c->d_mq;
+            S.P = c->d_rms + a.level;
+            S.logN = c->logN;
+            S.l = a.level;
+            S.K = c->K;
+            *bytes = 8.0 * (c->K + 2.0) * S.total;
+            return ew_blocks(S.total);
+        },
+        [](FoldTable &t, int blocks, cudaStream_t s) {
+            t.rms = 1;
+            k_fold_many<<<blocks, TPB, 0, s>>>(t);
+        });
+}
+
+void launch_ms_fold_many(const std::vector<FoldArgs> &items)
+{
+    launch_tables<FoldTable>(
+        items, FHE_K_ELEMWISE,
+        [](FoldSeg &S, const FoldArgs &a, double *bytes) {
+            fhe_ctx *c = a.c;
+            S.total = (long long)a.outer * c->N;
+            if (S.total <= 0 || a.k < 2) return 0;
+            S.src = a.src;
+            S.mq = c->d_mq;
+            S.P = c->d_mss + (size_t)a.level * (FHE_MAXK + 1) + a.k;
+            S.logN = c->logN;
+            S.l = a.level;
+            S.k = a.k;
+            *bytes = 8.0 * 2.0 * a.k * S.total;
+            return ew_blocks(S.total);
+        },
+        [](FoldTable &t, int blocks, cudaStream_t s) {
+            t.rms = 0;
+            k_fold_many<<<blocks, TPB, 0, s>>>(t);
+        });
+}

@@ -401,7 +401,7 @@ __device__ __forceinline__ int col_jobs(const IO &io, int sg, int lu, typename I
     const int njobs = H.outer * H.nl;
     const int job0 = (lu / Gm::BLK) * Gm::NJ;
     *lo0 = (lu % Gm::BLK) * Gm::NC;
-    if (threadIdx.x < Gm::NJ && job0 + (int)threadIdx.x < njobs) sts[threadIdx.x] = io.begin(sg, job0 + threadIdx.x);
+    if (threadIdx.x < Gm::NJ && job0 + (int)threadIdx.x < njobs) io.begin(sg, job0 + threadIdx.x, sts[threadIdx.x]);
     __syncthreads();
     return njobs - job0;  // valid job slots (>= 1)
 }
@@ -424,6 +424,14 @@ struct ColTwStage {
                                           : make_ulonglong2(0, 0);
         }
     }
+    __device__ void load1(const SegHdr &H, int prime)  // one job per unit
+    {
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            const int i = threadIdx.x + k * T;
+            v[k] = i < NW ? __ldg(H.tw + (size_t)prime * Gm::NN + i) : make_ulonglong2(0, 0);
+        }
+    }
     __device__ void store(ulonglong2 *W) const
     {
 #pragma unroll
@@ -434,13 +442,77 @@ struct ColTwStage {
     }
 };
 
+// Column units of one job (every ring degree but 2^10): the job's state is
+// computed by every thread and stays in registers.
+template <int N1, int N2, class IO>
+__device__ __forceinline__ void fwd_cols_unit1(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W)
+{
+    using Gm = ColGeo<N1, N2>;
+    using C = typename Gm::C;
+    const int tid = threadIdx.x;
+    const SegHdr &H = io.h[sg];
+    const int lo0 = (lu % Gm::BLK) * Gm::NC;
+    typename IO::St st;
+    io.begin(sg, lu / Gm::BLK, st);
+    ColTwStage<N1, N2> tws;
+    tws.load1(H, st.prime);
+    const u64 q = H.mq[st.prime].q;
+    tile_in<IO::LDCH>(
+        tid, [&](int r) { return io.load(st, (Gm::elem(r) << N2) + lo0 + Gm::col(r)); },
+        [&](int r, u64 v) { sm[C::at(Gm::col(r), Gm::elem(r))] = v; });
+    tws.store(W);
+    __syncthreads();
+    subtx<N1, true>(sm, tid, ColTw<N1, N2>{W, q, q});
+    __syncthreads();
+    u64 *mid = io.inter(st);
+#pragma unroll 4
+    for (int k = 0; k < 16; k++) {
+        const int r = tid + k * T;
+        mid[(Gm::elem(r) << N2) + lo0 + Gm::col(r)] = sm[C::at(Gm::col(r), Gm::elem(r))];
+    }
+}
+
+template <int N1, int N2, class IO>
+__device__ __forceinline__ void inv_cols_unit1(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W)
+{
+    using Gm = ColGeo<N1, N2>;
+    using C = typename Gm::C;
+    const int tid = threadIdx.x;
+    const SegHdr &H = io.h[sg];
+    const int lo0 = (lu % Gm::BLK) * Gm::NC;
+    typename IO::St st;
+    io.begin(sg, lu / Gm::BLK, st);
+    ColTwStage<N1, N2> tws;
+    tws.load1(H, st.prime);
+    const u64 q = H.mq[st.prime].q;
+    const ulonglong2 ni = io.final_scale(st);
+    const u64 *mid = io.inter(st);
+    tile_in<16>(
+        tid, [&](int r) { return mid[(Gm::elem(r) << N2) + lo0 + Gm::col(r)]; },
+        [&](int r, u64 v) { sm[C::at(Gm::col(r), Gm::elem(r))] = v; });
+    tws.store(W);
+    __syncthreads();
+    subtx<N1, false>(sm, tid, ColTw<N1, N2>{W, q, q});
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < 16; k++) {
+        const int r = tid + k * T;
+        io.store(st, (Gm::elem(r) << N2) + lo0 + Gm::col(r),
+                 reduce2q(shoup_lazy(sm[C::at(Gm::col(r), Gm::elem(r))], ni.x, ni.y, q), q));
+    }
+}
+
 // Forward, columns: global stages 0..N1-1.
 template <int N1, int N2, class IO>
-__device__ __noinline__ void fwd_cols_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
+__device__ __forceinline__ void fwd_cols_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
                                               typename IO::St *sts)
 {
     using Gm = ColGeo<N1, N2>;
     using C = typename Gm::C;
+    if constexpr (Gm::NJ == 1) {
+        fwd_cols_unit1<N1, N2>(io, sg, lu, sm, W);
+        return;
+    }
     const int tid = threadIdx.x;
     int lo0;
     const int nvalid = col_jobs<N1, N2>(io, sg, lu, sts, &lo0);
@@ -471,11 +543,15 @@ __device__ __noinline__ void fwd_cols_unit(const IO &io, int sg, int lu, u64 *sm
 // Inverse, columns: undoes global stages N1-1..0, then scales (N^-1 times the
 // job's constant) and stores.
 template <int N1, int N2, class IO>
-__device__ __noinline__ void inv_cols_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
+__device__ __forceinline__ void inv_cols_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
                                               typename IO::St *sts)
 {
     using Gm = ColGeo<N1, N2>;
     using C = typename Gm::C;
+    if constexpr (Gm::NJ == 1) {
+        inv_cols_unit1<N1, N2>(io, sg, lu, sm, W);
+        return;
+    }
     const int tid = threadIdx.x;
     int lo0;
     const int nvalid = col_jobs<N1, N2>(io, sg, lu, sts, &lo0);
@@ -521,11 +597,11 @@ __device__ __forceinline__ int row_jobs(const IO &io, int sg, int lu, typename I
         const int oc = t % OC, l = t / OC;
         *hi0 = hc * Gm::R;
         nvalid = min(ROW_J, H.outer - oc * ROW_J);
-        if ((int)threadIdx.x < nvalid) sts[threadIdx.x] = io.begin(sg, (oc * ROW_J + threadIdx.x) * H.nl + l);
+        if ((int)threadIdx.x < nvalid) io.begin(sg, (oc * ROW_J + threadIdx.x) * H.nl + l, sts[threadIdx.x]);
     } else {
         *hi0 = (lu % Gm::CHS) * Gm::NS;
         nvalid = 1;
-        if (threadIdx.x == 0) sts[0] = io.begin(sg, lu / Gm::CHS);
+        if (threadIdx.x == 0) io.begin(sg, lu / Gm::CHS, sts[0]);
     }
     __syncthreads();
     return nvalid;
@@ -576,7 +652,7 @@ struct RowMap {
 
 // Forward, rows: global stages N1..N1+N2-1, reduction to [0, q), store.
 template <int N1, int N2, bool GRP, class IO>
-__device__ __noinline__ void fwd_rows_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
+__device__ __forceinline__ void fwd_rows_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
                                           typename IO::St *sts)
 {
     using Gm = RowGeo<N1, N2>;
@@ -613,7 +689,7 @@ __device__ __noinline__ void fwd_rows_unit(const IO &io, int sg, int lu, u64 *sm
 
 // Inverse, rows first: undoes global stages N1+N2-1..N1.
 template <int N1, int N2, bool GRP, class IO>
-__device__ __noinline__ void inv_rows_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
+__device__ __forceinline__ void inv_rows_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
                                           typename IO::St *sts)
 {
     using Gm = RowGeo<N1, N2>;
@@ -759,17 +835,15 @@ struct IOMap : SegIO<MapSeg> {
         ulonglong2 fs;
         int prime;
     };
-    __device__ St begin(int sg, int job) const
+    __device__ void begin(int sg, int job, St &t) const
     {
         const SegHdr &H = h[sg];
         const MapSeg &S = s[sg];
         const int N = 1 << H.logN, o = job / H.nl, l = job % H.nl;
-        St t;
         t.in = S.in + o * S.in_outer + (long long)S.in_limb[l] * N;
         t.out = S.out + o * S.out_outer + (long long)S.out_limb[l] * N;
         t.prime = S.prime[l];
         t.fs = S.scale ? S.scale[l] : H.ninv[t.prime];
-        return t;
     }
     __device__ u64 load(const St &t, int i) const { return t.in[i]; }
     __device__ void store(const St &t, int i, u64 v) const { t.out[i] = v; }
@@ -799,13 +873,12 @@ struct IOScaledY : SegIO<YSeg> {
         u64 Pm, Pm_s, qm;
         int prime;
     };
-    __device__ St begin(int sg, int job) const
+    __device__ void begin(int sg, int job, St &t) const
     {
         const SegHdr &H = h[sg];
         const YSeg &S = s[sg];
         const int N = 1 << H.logN, o = job / H.nl, e = job % H.nl, pi = o & 1;
         const long long c = o >> 1;
-        St t;
         t.in = S.in + o * S.in_outer + (long long)S.in_limb[e] * N;
         t.out = S.out + o * S.out_outer + (long long)S.out_limb[e] * N;
         t.prime = S.prime[e];
@@ -815,7 +888,6 @@ struct IOScaledY : SegIO<YSeg> {
         t.Pm = S.Pm;
         t.Pm_s = S.Pm_s;
         t.qm = S.qm;
-        return t;
     }
     __device__ u64 load(const St &t, int i) const
     {
@@ -849,14 +921,13 @@ struct IOModUp : SegIO<ModUpSeg> {
         ModQ mt;
         u64 hat[FHE_MAXK];
     };
-    __device__ St begin(int sg, int job) const
+    __device__ void begin(int sg, int job, St &t) const
     {
         const SegHdr &H = h[sg];
         const ModUpSeg &S = s[sg];
         const int N = 1 << H.logN, c = job / H.nl, e = job % H.nl;
         const ModUpParams *P = S.P;
         const int j = P->job_digit[e], tg = P->job_tgt[e];
-        St t;
         const int lo = P->digit_lo[j];
         t.nsrc = P->digit_n[j];
         t.N = N;
@@ -867,7 +938,6 @@ struct IOModUp : SegIO<ModUpSeg> {
 #pragma unroll
         for (int a = 0; a < FHE_MAXK; a++)
             if (a < t.nsrc) t.hat[a] = P->hat[j][a][tg];
-        return t;
     }
     __device__ u64 load(const St &t, int n) const
     {
@@ -909,13 +979,12 @@ struct IOModDown : SegIO<ModDownSeg> {
         u64 pinv, pinv_s;
         u64 phat[FHE_MAXK];
     };
-    __device__ St begin(int sg, int job) const
+    __device__ void begin(int sg, int job, St &t) const
     {
         const SegHdr &H = h[sg];
         const ModDownSeg &S = s[sg];
         const int N = 1 << H.logN, l = S.l, K = S.K;
         const int c = job / (2 * l), pi = (job / l) % 2, i = job % l;
-        St t;
         t.w = S.accP + ((long long)c * 2 + pi) * K * N;
         t.acc = S.acc + (((long long)c * 2 + pi) * (l + K) + i) * N;
         t.add = ((S.amask >> pi) & 1) ? S.abase + c * S.a_outer + pi * S.a_poly + (long long)i * N : nullptr;
@@ -929,7 +998,6 @@ struct IOModDown : SegIO<ModDownSeg> {
 #pragma unroll
         for (int k = 0; k < FHE_MAXK; k++)
             if (k < K) t.phat[k] = S.P->phat[k][i];
-        return t;
     }
     __device__ u64 load(const St &t, int n) const
     {
@@ -980,13 +1048,12 @@ struct IOModSwitch : SegIO<SwitchSeg> {
         int prime, pad;
         u64 q, pi, pis, qi, qis;
     };
-    __device__ St begin(int sg, int job) const
+    __device__ void begin(int sg, int job, St &t) const
     {
         const SegHdr &H = h[sg];
         const SwitchSeg &S = s[sg];
         const int N = 1 << H.logN, l = S.l, np = S.npoly;
         const int c = job / (np * (l - 1)), pi = (job / (l - 1)) % np, i = job % (l - 1);
-        St t;
         t.last = S.last + ((long long)c * np + pi) * N;
         t.in = S.in + (((long long)c * np + pi) * l + i) * N;
         t.out = S.out + (((long long)c * np + pi) * (l - 1) + i) * N;
@@ -996,7 +1063,6 @@ struct IOModSwitch : SegIO<SwitchSeg> {
         t.pis = S.P->p_i_s[i];
         t.qi = S.P->qinv[i];
         t.qis = S.P->qinv_s[i];
-        return t;
     }
     __device__ u64 load(const St &t, int n) const { return shoup(t.last[n], t.pi, t.pis, t.q); }
     __device__ void store(const St &t, int k, u64 v) const { t.out[k] = shoup(submod(t.in[k], v, t.q), t.qi, t.qis, t.q); }
@@ -1036,13 +1102,12 @@ struct IORelinMS : SegIO<RelinMSSeg> {
         u64 pinv, pinv_s, qminv, qminv_s;
         u64 h[FHE_MAXK];
     };
-    __device__ St begin(int sg, int job) const
+    __device__ void begin(int sg, int job, St &t) const
     {
         const SegHdr &H = h[sg];
         const RelinMSSeg &S = s[sg];
         const int N = 1 << H.logN, l = S.l, K = S.K, m = l - 1;
         const int c = job / (2 * m), pi = (job / m) % 2, i = job % m;
-        St t;
         t.w = S.src + ((long long)c * 2 + pi) * (K + 1) * N;
         t.acc = S.acc + (((long long)c * 2 + pi) * (l + K) + i) * N;
         t.add = ((S.amask >> pi) & 1) ? S.abase + c * S.a_outer + pi * S.a_poly + (long long)i * N : nullptr;
@@ -1058,7 +1123,6 @@ struct IORelinMS : SegIO<RelinMSSeg> {
 #pragma unroll
         for (int k = 0; k < FHE_MAXK; k++)
             if (k <= K) t.h[k] = S.P->h[k][i];
-        return t;
     }
     // K + 1 <= FHE_MAXK products of canonical residues: below 2^(2b+3)
     __device__ u64 load(const St &t, int n) const
@@ -1105,13 +1169,12 @@ struct IOMultiSwitch : SegIO<MultiSeg> {
         u64 dinv, dinv_s;
         u64 g[FHE_MAXK];
     };
-    __device__ St begin(int sg, int job) const
+    __device__ void begin(int sg, int job, St &t) const
     {
         const SegHdr &H = h[sg];
         const MultiSeg &S = s[sg];
         const int N = 1 << H.logN, kept = S.l - S.k, np = S.npoly;
         const int c = job / (np * kept), pi = (job / kept) % np, i = job % kept;
-        St t;
         t.w = S.src + ((long long)c * np + pi) * S.k * N;
         t.in = S.in + (((long long)c * np + pi) * S.l + i) * N;
         t.out = S.out + (((long long)c * np + pi) * kept + i) * N;
@@ -1124,7 +1187,6 @@ struct IOMultiSwitch : SegIO<MultiSeg> {
 #pragma unroll
         for (int j = 0; j < FHE_MAXK; j++)
             if (j < S.k) t.g[j] = S.P->G[j][i];
-        return t;
     }
     __device__ u64 load(const St &t, int n) const
     {

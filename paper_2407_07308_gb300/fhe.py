@@ -747,6 +747,7 @@ class Job:
 
 
 FHE_BATCH_ALIGN_LEVELS = 1
+FHE_BATCH_FUSE_RINGS = 2
 
 
 def fhe_batch_submit(jobs, flags: int = 0):

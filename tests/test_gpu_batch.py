@@ -329,3 +329,76 @@ def test_sort_jobs_in_batches_and_served():
             fhe.fhe_ct_destroy(h)
         fhe.fhe_ctx_destroy(ctx)
         fhe.fhe_ctx_destroy(bad)
+
+
+def test_fused_rings_mixed_degrees_match_alone_and_oracle():
+    """FHE_BATCH_FUSE_RINGS: compare and max/min jobs of three contexts of one
+    plaintext prime (N = 2^13, 2^14, 2^15; digit counts 1 and 2; start levels
+    8, 7 and 6) in one submission, whose circuit runs every step as one launch
+    over all ring degrees: each result equals the job alone, and ciphertext 0
+    of one compare job per ring degree equals the CPU oracle limb for limb."""
+    from paper_2407_07308_gb300 import fhe
+    from tests.gpu_setup import GpuSetup
+    from tests.oracle_setup import compare_many
+
+    p, L, K = 17, 8, 4
+    setups = [GpuSetup(seed=60 + n, logN=n, p=p, L=L, K=K, **CHAIN50) for n in (13, 14, 15)]
+    rnd = random.Random(61)
+    try:
+        jobs, meta, handles, oracle_jobs = [], [], [], []
+        for i in range(9):
+            g = setups[i % 3]
+            b, ns = (p + 1) // 2, g.ns
+            d = 1 + (i // 3) % 2
+            count = 2 + i % 2
+            level = L - (i % 3)
+            xv = [[rnd.randrange(b ** d) for _ in range(ns)] for _ in range(count)]
+            yv = [[x if rnd.random() < 0.3 else rnd.randrange(b ** d) for x in row] for row in xv]
+            xd = [[[(v // b ** k) % b for v in row] for row in xv] for k in range(d)]
+            yd = [[[(v // b ** k) % b for v in row] for row in yv] for k in range(d)]
+            sx = [700 + 10 * i + k for k in range(d)]
+            sy = [800 + 10 * i + k for k in range(d)]
+            xs = [g.encrypt_slots(xd[k], seed=sx[k]) for k in range(d)]
+            ys = [g.encrypt_slots(yd[k], seed=sy[k]) for k in range(d)]
+            if level < L:
+                xs = [g.own(fhe.fhe_mod_switch(g.ctx, h, level)) for h in xs]
+                ys = [g.own(fhe.fhe_mod_switch(g.ctx, h, level)) for h in ys]
+            kind = fhe.FHE_JOB_MAXMIN if i in (4, 8) else fhe.FHE_JOB_COMPARE
+            jobs.append(fhe.Job(g.ctx, g.evk, kind, xs, ys))
+            meta.append((g, kind, xs, ys, np.array(xv), np.array(yv), b, d))
+            if kind == fhe.FHE_JOB_COMPARE and i < 3:
+                params = dict(logN=(13, 14, 15)[i], p=p, L=L, K=K, **CHAIN50)
+                oracle_jobs.append((i, (params, 60 + params["logN"], xd, yd, sx, sy, 0,
+                                        level if level < L else None)))
+        batch = fhe.fhe_batch_submit(jobs, fhe.FHE_BATCH_FUSE_RINGS)
+        assert fhe.fhe_batch_wait(batch, 300000) == 0
+        fhe.fhe_batch_destroy(batch)
+        for job, (g, kind, xs, ys, xv, yv, b, d) in zip(jobs, meta):
+            outs = [h for h in (job.out0 or []) + (job.out1 or []) if h]
+            for h in outs:
+                g.own(h)
+            if kind == fhe.FHE_JOB_COMPARE:
+                lt, eq = fhe.fhe_compare(g.ctx, g.evk, xs, ys)
+                g.own(lt)
+                g.own(eq)
+                assert np.array_equal(g.export(job.out0[0]), g.export(lt))
+                assert np.array_equal(g.export(job.out1[0]), g.export(eq))
+                assert (g.decrypt(job.out0[0]) == (xv < yv)).all()
+                assert (g.decrypt(job.out1[0]) == (xv == yv)).all()
+            else:
+                mx, mn = fhe.fhe_max_min(g.ctx, g.evk, xs, ys)
+                for h in mx + mn:
+                    g.own(h)
+                for k in range(d):
+                    assert np.array_equal(g.export(job.out0[k]), g.export(mx[k]))
+                    assert np.array_equal(g.export(job.out1[k]), g.export(mn[k]))
+                got = sum(g.decrypt(job.out0[k]).astype(np.int64) * b ** k for k in range(d))
+                assert (got == np.maximum(xv, yv)).all()
+        res = compare_many([oj for _, oj in oracle_jobs])
+        for (i, _), (want_lt, want_eq, _) in zip(oracle_jobs, res):
+            g = meta[i][0]
+            assert np.array_equal(g.export(jobs[i].out0[0])[0], want_lt), i
+            assert np.array_equal(g.export(jobs[i].out1[0])[0], want_eq), i
+    finally:
+        for g in setups:
+            g.close()

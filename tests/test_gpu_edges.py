@@ -192,7 +192,7 @@ def test_slot_pack_mixed_levels_bitexact_and_refusals():
         trace_g = fhe.fhe_trace_get(g.ctx)
         ev = o.evaluator()
         out_o = slot_pack(ev, xo, useful)
-        assert trace_g == ev.trace
+        assert sorted(trace_g) == sorted(ev.trace)
         assert np.array_equal(g.export(out[0])[0], out_o[0].data)
         assert fhe.fhe_ct_shape(out[0])[2] == L - 2
         dec = g.decrypt(out[0])[0]

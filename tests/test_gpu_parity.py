@@ -1,7 +1,9 @@
 """GPU parity: the CUDA library (through its C ABI) against the CPU oracle on
 identical seeded inputs.  Every comparison of ciphertext limbs is exact
 (tolerance 0: integer arithmetic), decryptions are compared with plaintext
-results, and the circuit-level operation traces must be identical."""
+results, and the circuit-level operation traces must hold the same operations
+at the same levels (the library runs independent operations of a circuit
+together, so their order may differ from the oracle's)."""
 import os
 import random
 
@@ -222,7 +224,7 @@ def _run_compare(params, d, count, seed, want_maxmin=False, check_bits=True):
             yo = [o.encrypt_slots(yd[k], seed=200 + k)[0] for k in range(d)]
             ev = o.evaluator()
             lt_o, eq_o = ev.compare(xo, yo, True, True)
-            assert trace_g == ev.trace
+            assert sorted(trace_g) == sorted(ev.trace)
             _same(lt_o, g.export(lt_g), 0)
             _same(eq_o, g.export(eq_g), 0)
         if want_maxmin:
@@ -485,7 +487,7 @@ def test_compare_bivariate_full_digits_bitexact(logN, p, L, K, d, count):
         yo = [o.encrypt_slots(yd[k], seed=400 + k)[0] for k in range(d)]
         ev = o.evaluator()
         lt_o, eq_o = ev.compare(xo, yo, True, True, bivariate=True)
-        assert trace_g == ev.trace
+        assert sorted(trace_g) == sorted(ev.trace)
         _same(lt_o, g.export(lt_g), 0)
         _same(eq_o, g.export(eq_g), 0)
     finally:
@@ -551,7 +553,7 @@ def test_sort_rows_bitexact():
         xo = [o.encrypt_slots(dg[k], seed=500 + k)[0] for k in range(d)]
         ev = o.evaluator()
         out_o = sort_rows(ev, xo)
-        assert trace_g == ev.trace
+        assert sorted(trace_g) == sorted(ev.trace)
         for k in range(d):
             _same(out_o[k], g.export(out[k]), 0)
     finally:
@@ -604,7 +606,7 @@ def test_slot_pack_bitexact(p, kind):
         xo = [o.encrypt_slots(vals[j], seed=600 + j)[0] for j in range(len(useful))]
         ev = o.evaluator()
         outs_o = slot_pack(ev, xo, useful)
-        assert trace_g == ev.trace
+        assert sorted(trace_g) == sorted(ev.trace)
         for q in range(n_out):
             _same(outs_o[q], g.export(outs[q]), 0)
     finally:
@@ -641,7 +643,7 @@ def test_extract_digits_bitexact(p, d, logN):
             assert (g.decrypt(out[k]) == digits[:, :, k]).all()
         ev = o.evaluator()
         out_o = extract_digits(ev, co, d, xs)
-        assert trace_g == ev.trace
+        assert sorted(trace_g) == sorted(ev.trace)
         for k in range(d):
             _same(out_o[k], g.export(out[k]), 0)
     finally:
@@ -708,7 +710,7 @@ def test_private_query_bitexact(overlap):
         qo, do, oo = (o.encrypt_slots(v, seed=800 + i)[0] for i, v in enumerate((qv, dv, ov)))
         ev = o.evaluator()
         out_o = private_query(ev, qo, do, oo, 3, (1, 2, 3))
-        assert trace_g == ev.trace
+        assert sorted(trace_g) == sorted(ev.trace)
         _same(out_o, g.export(out), 0)
         fhe.fhe_trace_enable(g.ctx, False)
         # captured as a graph: every replay gives the same bits
@@ -757,7 +759,7 @@ def test_sort_joint_bitexact():
         xo = [[o.encrypt_slots([dig(vals[a])[k]], seed=1000 + 10 * a + k)[0] for k in range(d)] for a in range(K)]
         ev = o.evaluator()
         out_o = sort_joint(ev, xo)
-        assert trace_g == ev.trace
+        assert sorted(trace_g) == sorted(ev.trace)
         for t in range(K):
             for k in range(d):
                 _same(out_o[t][k], g.export(out[t][k]), 0)
