@@ -584,10 +584,11 @@ int fhe_ntt_inverse_batch(fhe_ctx *ctx, uint64_t *data, int count, int nprimes);
  * fraction.  Synchronises the device. */
 int fhe_probe_int_peak(double *imad32, double *mulhi64);
 /* Measured butterflies per second over all SMs: the NTT's lazy forward
- * butterfly with a Shoup twiddle (one 64-bit high product, two 64-bit low
- * products, three additions) on register-resident values, three dependent
- * layers per iteration, no memory traffic: the arithmetic roof the NTT
- * kernels are reported against.  Synchronises the device. */
+ * butterfly with a Shoup twiddle (the quotient from one 32x32->64 and two
+ * 32x32->high products, two 64-bit low products, three additions; result in
+ * [0, 4q)) on register-resident values, three dependent layers per
+ * iteration, no memory traffic: the arithmetic roof the NTT kernels are
+ * reported against.  Synchronises the device. */
 int fhe_probe_bfly_peak(double *bfly_per_s);
 
 /* ---- modulus switching without allocation -------------------------------------- */

@@ -1580,6 +1580,8 @@ extern "C" int fhe_selftest_modarith(uint64_t prime_mod, uint64_t prime_lo, uint
             const u64 w = b[0], ws = shoup_const(w, q), x = edge ? ~0ull - (u64)it : rnd();
             const u64 lz = shoup_lazy(x, w, ws, q);
             if (lz >= 2 * q || lz % q != (u64)(((u128)x * w) % q)) bad++;
+            const u64 l4 = shoup_lazy4(x, w, ws, q);
+            if (l4 >= 4 * q || l4 % q != (u64)(((u128)x * w) % q)) bad++;
             if (shoup(x, w, ws, q) != (u64)(((u128)x * w) % q)) bad++;
             if (reduce4q(4 * q - 1 - (x % (4 * q)), 2 * q, q) != (4 * q - 1 - (x % (4 * q))) % q) bad++;
             const u64 v = edge ? (it < 32 ? ~0ull - (u64)it : 31 * q - 1 - (u64)it) : rnd();

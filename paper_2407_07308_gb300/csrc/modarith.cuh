@@ -47,6 +47,26 @@ struct ModQ {
 // a * w mod q in [0, 2q), w < q, ws = floor(w 2^64 / q), any a < 2^64.
 FHE_HD u64 shoup_lazy(u64 a, u64 w, u64 ws, u64 q) { return a * w - fhe_mulhi(a, ws) * q; }
 
+// Shoup's product with a cheaper quotient (the NTT butterflies' form): with
+// a = ah 2^32 + al and ws = wh 2^32 + wl, floor(a ws / 2^64) = ah wh +
+// floor((ah wl + al wh) / 2^32 + al wl / 2^64), and the estimate
+// ah wh + floor(ah wl / 2^32) + floor(al wh / 2^32) drops three fractions
+// below 1 each, so it is 0, 1 or 2 below the exact quotient.  Shoup's bound
+// a w - floor(a ws / 2^64) q in [0, 2q) then gives a w - qhat q in [0, 4q),
+// for any a < 2^64; the difference fits in 64 bits, so the arithmetic mod
+// 2^64 is exact.  One 32x32->64 and two 32x32->hi products instead of the
+// four 32x32->64 products (and their carries) of the exact high half.
+FHE_HD u64 shoup_lazy4(u64 a, u64 w, u64 ws, u64 q)
+{
+    const uint32_t al = (uint32_t)a, ah = (uint32_t)(a >> 32), wl = (uint32_t)ws, wh = (uint32_t)(ws >> 32);
+#ifdef __CUDA_ARCH__
+    const u64 qhat = (u64)ah * wh + ((u64)__umulhi(ah, wl) + __umulhi(al, wh));
+#else
+    const u64 qhat = (u64)ah * wh + ((((u64)ah * wl) >> 32) + (((u64)al * wh) >> 32));
+#endif
+    return a * w - qhat * q;
+}
+
 FHE_HD u64 shoup(u64 a, u64 w, u64 ws, u64 q)
 {
     u64 r = shoup_lazy(a, w, ws, q);

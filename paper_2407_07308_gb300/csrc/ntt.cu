@@ -49,24 +49,27 @@
 
 namespace {
 
-// Forward butterfly without normalisation: t = [Y w] in [0, 2q) for any
-// 64-bit Y, so if X, Y < B then X + t and X - t + 2q lie in [0, B + 2q).
-// After s stages every value is below (2s + 1) q <= 31 q < 2^63 (primes
-// below 2^58, s <= 15); one reduction at the end brings it to [0, q).
-__device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 q, u64 q2)
+// Forward butterfly without normalisation: t = [Y w] in [0, 4q) for any
+// 64-bit Y (shoup_lazy4), so if X, Y < B then X + t and X - t + 4q lie in
+// [0, B + 4q).  After s stages every value is below (4s + 1) q <= 61 q <
+// 2^63 (primes below 2^57, s <= 15); one reduction at the end brings it to
+// [0, q).  q4 = 4q.
+__device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 q, u64 q4)
 {
-    const u64 t = shoup_lazy(Y, w.x, w.y, q);
+    const u64 t = shoup_lazy4(Y, w.x, w.y, q);
     const u64 x = X;
     X = x + t;
-    Y = x - t + q2;
+    Y = x - t + q4;
 }
 
-__device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 q, u64 q2)
+// Inverse butterfly on values in [0, 4q): X + Y reduced once by 4q, and
+// [(X - Y + 4q) w] in [0, 4q).
+__device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 q, u64 q4)
 {
     u64 s = X + Y;
-    s = s >= q2 ? s - q2 : s;
-    u64 d = X - Y + q2;
-    Y = shoup_lazy(d, w.x, w.y, q);
+    s = s >= q4 ? s - q4 : s;
+    u64 d = X - Y + q4;
+    Y = shoup_lazy4(d, w.x, w.y, q);
     X = s;
 }
 
@@ -190,7 +193,7 @@ __device__ __forceinline__ void subtx(u64 *sm, int tid, const Geo &geo)
         const int c = tid % NS, g = tid / NS;
         const auto W = geo.tw(c);
         const int hi = geo.hi(c);
-        const u64 q = geo.q(c), q2 = 2 * q;
+        const u64 q = geo.q(c), q2 = 4 * q;  // lazy bound of the butterflies
         u64 *b1 = sm + c * C::P + g;
         u64 x[16];
 #pragma unroll
@@ -206,7 +209,7 @@ __device__ __forceinline__ void subtx(u64 *sm, int tid, const Geo &geo)
         const int c = tid / G, gp = tid % G;
         const auto W = geo.tw(c);
         const int hi = geo.hi(c);
-        const u64 q = geo.q(c), q2 = 2 * q;
+        const u64 q = geo.q(c), q2 = 4 * q;  // lazy bound of the butterflies
         u64 *b2 = sm + c * C::P + gp * 17;
 #pragma unroll
         for (int i = 0; i < NB; i++) {
