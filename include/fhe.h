@@ -429,6 +429,18 @@ int fhe_sort(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, int d, fh
  * is fhe_sort.  Costs K^2 cols - K comparisons and K^2 cols selection
  * powers.  out: K * d new handles, out[t * d + k]. */
 int fhe_sort_joint(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, int K, int d, fhe_ct **out);
+/* The sort application (Sec. 6) on sequences of any length, K cols values a
+ * row, including K cols > p, where the selection step of fhe_sort_joint would
+ * no longer be exact: the rank step alone.  ranks[a] (K new handles) holds in
+ * slot (r, c) the rank of value (a, c) of row r -- the number of values of
+ * the row below it plus those equal to it at a lower global index -- mod p.
+ * matrix, when not NULL, receives K * K * cols handles: matrix[(a K + b) cols
+ * + s] = LT(sigma_{5^s} x^b, x^a), whose slot (r, c) is [x_j < x_i] for
+ * i = a cols + c and j = b cols + (c + s) mod cols (NULL at s = 0, b = a).
+ * Inputs as for fhe_sort_joint (keys of fhe_sort_galois); costs K^2 cols - K
+ * comparisons. */
+int fhe_sort_ranks(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *const *x, int K, int d, fhe_ct **ranks,
+                   fhe_ct **matrix);
 
 /* ---- batches of uneven requests ------------------------------------------------- */
 

@@ -344,6 +344,40 @@ def sort_rows(ev: "Evaluator", xs):
     return sort_joint(ev, [xs])[0]
 
 
+def sort_ranks(ev: "Evaluator", cts):
+    """The rank step of sort_joint on sequences of any length n = K cols (the
+    sort application, Sec. 6; for n > p the ranks wrap mod p, so they, and
+    the comparisons they are summed from, are the result): returns the K rank
+    ciphertexts and the comparison matrix, a dict (a, b, s) -> LT(sigma_{5^s}
+    x^b, x^a) over (b, s) != (a, 0), whose slot (r, c) is [x_j < x_i] for the
+    global indices i = a cols + c and j = b cols + (c + s) mod cols of row r.
+
+    rank^a = sum over (b, s) != (a, 0), b and then s ascending, of
+    LT(sigma_{5^s} x^b, x^a) + w * EQ(sigma_{5^s} x^b, x^a), with the
+    tie-break mask w[c] = [b cols + (c + s) mod cols < a cols + c]: slot
+    (r, c) of rank^a is the number of values of row r below x_i, plus those
+    equal to it at a lower index, mod p."""
+    ss = ev._slots()
+    assert ss.kind == "linear" and ss.ns >= 4, "sorting needs p = 1 mod 4 and two columns or more"
+    cols, twoN = ss.ns // 2, 2 * ev.o.N
+    K = len(cts)
+    ranks, matrix = [], {}
+    for a in range(K):
+        rank = None
+        for b in range(K):
+            for s in range(cols):
+                if b == a and s == 0:
+                    continue
+                xr = [ev.rotate(x, pow(5, s, twoN)) for x in cts[b]] if s else list(cts[b])
+                lt, eq = ev.compare(xr, cts[a], True, True)
+                matrix[(a, b, s)] = lt
+                w = [1 if b * cols + (c + s) % cols < a * cols + c else 0 for _ in range(2) for c in range(cols)]
+                t = ev.add(lt, ev.mul_plain(eq, w))
+                rank = t if rank is None else ev.add(rank, t)
+        ranks.append(rank)
+    return ranks, matrix
+
+
 def sort_joint(ev: "Evaluator", cts):
     """Row r of the K ciphertexts cts[0..K) (each a list of d digit
     ciphertexts) is one sequence of K cols values, global index a cols + c
@@ -358,23 +392,10 @@ def sort_joint(ev: "Evaluator", cts):
     ascending: out^t += EQ(sigma_{5^s} rank^a - (t cols + c)) sigma_{5^s} x^a
     per digit."""
     ss = ev._slots()
-    assert ss.kind == "linear" and ss.ns >= 4, "sorting needs p = 1 mod 4 and two columns or more"
     p, cols, twoN = ev.p, ss.ns // 2, 2 * ev.o.N
     K, d = len(cts), len(cts[0])
     assert K * cols <= p, "ranks must stay below p"
-    ranks = []
-    for a in range(K):
-        rank = None
-        for b in range(K):
-            for s in range(cols):
-                if b == a and s == 0:
-                    continue
-                xr = [ev.rotate(x, pow(5, s, twoN)) for x in cts[b]] if s else list(cts[b])
-                lt, eq = ev.compare(xr, cts[a], True, True)
-                w = [1 if b * cols + (c + s) % cols < a * cols + c else 0 for _ in range(2) for c in range(cols)]
-                t = ev.add(lt, ev.mul_plain(eq, w))
-                rank = t if rank is None else ev.add(rank, t)
-        ranks.append(rank)
+    ranks, _ = sort_ranks(ev, cts)
     outs = [[None] * d for _ in range(K)]
     for a in range(K):
         for s in range(cols):

@@ -1420,6 +1420,24 @@ extern "C" int fhe_sort_joint(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *cons
     return e ? e : launch_status(c, "sort");
 }
 
+extern "C" int fhe_sort_ranks(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int K, int d, fhe_ct **ranks,
+                              fhe_ct **matrix)
+{
+    FHE_RANGE("fhe_sort_ranks");
+    CHECK_CTX(c);
+    if (!ranks || !x || K < 1 || d < 1) return FHE_EINVAL;
+    int e = check_digits(c, evk, x, x, d);
+    if (e) return e;
+    for (int i = 0; i < K * d; i++) {
+        if (!same_ctx(c, x[i])) return FHE_EINVAL;
+        if (x[i]->npoly != 2 || x[i]->count != x[0]->count || x[i]->level != x[0]->level)
+            return fhe_fail(c, FHE_EMISMATCH, "sort ranks: inputs differ in shape or level");
+    }
+    LOCK(c);
+    e = circuit_sort_ranks(c, evk, x, K, d, ranks, matrix);
+    return e ? e : launch_status(c, "sort ranks");
+}
+
 extern "C" int fhe_compare_lt(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, const fhe_ct *const *y, int d,
                               fhe_ct **out)
 {

@@ -1899,6 +1899,78 @@ std::vector<int64_t> sort_galois(const fhe_ctx *c)
 // each target t: out^t += EQ(sigma_{5^s} rank^a - (t cols + c)) sigma_{5^s} x^a.
 // Each comparison, and each (a, s) of the selection, is a sub-circuit of its
 // own, so only the running sums outlive it.  K = 1 is the row sort.
+// The rank step: for every ciphertext a and every other (b, s), (LT, EQ) =
+// compare(sigma_{5^s} x^b, x^a) and rank^a += LT + w EQ (the tie-break mask
+// of the schedule above); the comparisons of one (a, b) run in one circuit
+// (merged across shifts), so only the running ranks outlive it.  matrix, when
+// given, receives LT at [(a K + b) cols + s] (null at (a, a, 0)).  No bound on
+// K cols: the ranks are counts mod p.
+int circuit_sort_ranks(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int K, int d, fhe_ct **rank_out,
+                       fhe_ct **matrix)
+{
+    if (!c->slots_linear || c->ns < 4)
+        return fhe_fail(c, FHE_EUNSUPPORTED, "sorting needs p = 1 mod 4 (two columns or more)");
+    if (K < 1 || d < 1) return fhe_fail(c, FHE_EINVAL, "sort ranks: K and d must be positive");
+    const int cols = c->ns / 2;
+    const std::vector<int64_t> gs = sort_galois(c);
+    auto X = [&](int a) { return std::vector<const fhe_ct *>(x + (size_t)a * d, x + (size_t)(a + 1) * d); };
+    std::vector<fhe_ct *> rank(K, nullptr);
+    std::vector<fhe_ct *> mat(matrix ? (size_t)K * K * cols : 0, nullptr);
+    int err = 0;
+    for (int a = 0; a < K && !err; a++) {
+        const std::vector<const fhe_ct *> xa = X(a);
+        for (int b = 0; b < K && !err; b++) {
+            const std::vector<const fhe_ct *> xb = X(b);
+            Circuit S(c, evk);
+            std::vector<int> sh;
+            std::vector<std::vector<const fhe_ct *>> xr;
+            for (int s = 0; s < cols && !S.err; s++) {
+                if (b == a && s == 0) continue;
+                std::vector<const fhe_ct *> r(d);
+                for (int k = 0; k < d; k++) r[k] = s ? S.rot(xb[k], gs[s - 1]) : xb[k];
+                sh.push_back(s);
+                xr.push_back(r);
+            }
+            std::vector<fhe_ct *> lt(sh.size(), nullptr), eq(sh.size(), nullptr);
+            std::vector<Circuit::Req> rq;
+            for (size_t i = 0; i < sh.size(); i++)
+                rq.push_back(Circuit::Req{xr[i].data(), xa.data(), d, true, true, false, &lt[i], &eq[i], nullptr,
+                                          nullptr});
+            if (!S.err) S.compare_many(rq);
+            fhe_ct *nr = nullptr;
+            for (size_t i = 0; i < sh.size() && !S.err; i++) {
+                const int s = sh[i];
+                S.keep(lt[i]);
+                S.keep(eq[i]);
+                std::vector<uint64_t> w(c->ns);
+                for (int r = 0; r < 2; r++)
+                    for (int j = 0; j < cols; j++)
+                        w[(size_t)r * cols + j] = (b * cols + (j + s) % cols < a * cols + j) ? 1 : 0;
+                fhe_ct *t = S.add(lt[i], S.plain(eq[i], w, 2));
+                nr = nr ? S.add(nr, t) : (rank[a] ? S.add(rank[a], t) : t);
+            }
+            S.finish();
+            if (!S.err) {
+                if (rank[a]) fhe_ct_destroy(rank[a]);
+                rank[a] = S.release(nr);
+                if (matrix)
+                    for (size_t i = 0; i < sh.size(); i++) mat[((size_t)a * K + b) * cols + sh[i]] = S.release(lt[i]);
+            }
+            err = S.err;
+        }
+    }
+    if (err) {
+        for (fhe_ct *r : rank)
+            if (r) fhe_ct_destroy(r);
+        for (fhe_ct *m : mat)
+            if (m) fhe_ct_destroy(m);
+        return err;
+    }
+    for (int a = 0; a < K; a++) rank_out[a] = rank[a];
+    for (size_t i = 0; i < mat.size(); i++) matrix[i] = mat[i];
+    return 0;
+}
+
 int circuit_sort_joint(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int K, int d, fhe_ct **out)
 {
     if (!c->slots_linear || c->ns < 4)
@@ -1908,39 +1980,11 @@ int circuit_sort_joint(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, i
     const std::vector<int64_t> gs = sort_galois(c);
     auto X = [&](int a) { return std::vector<const fhe_ct *>(x + (size_t)a * d, x + (size_t)(a + 1) * d); };
     std::vector<fhe_ct *> rank(K, nullptr), outs((size_t)K * d, nullptr);
-    int err = 0;
     auto carry = [](fhe_ct *&held, fhe_ct *next) {
         if (held) fhe_ct_destroy(held);
         held = next;
     };
-    for (int a = 0; a < K && !err; a++) {
-        const std::vector<const fhe_ct *> xa = X(a);
-        for (int b = 0; b < K && !err; b++) {
-            const std::vector<const fhe_ct *> xb = X(b);
-            for (int s = 0; s < cols && !err; s++) {
-                if (b == a && s == 0) continue;
-                Circuit S(c, evk);
-                std::vector<const fhe_ct *> xr(d);
-                for (int k = 0; k < d; k++) xr[k] = s ? S.rot(xb[k], gs[s - 1]) : xb[k];
-                fhe_ct *lt = nullptr, *eq = nullptr;
-                if (!S.err) S.compare(xr.data(), xa.data(), d, true, true, &lt, &eq);
-                if (!S.err) {
-                    S.keep(lt);
-                    S.keep(eq);
-                    std::vector<uint64_t> w(c->ns);
-                    for (int r = 0; r < 2; r++)
-                        for (int i = 0; i < cols; i++)
-                            w[(size_t)r * cols + i] = (b * cols + (i + s) % cols < a * cols + i) ? 1 : 0;
-                    fhe_ct *t = S.add(lt, S.plain(eq, w, 2));
-                    fhe_ct *nr = rank[a] ? S.add(rank[a], t) : t;
-                    S.finish();
-                    if (!S.err) carry(rank[a], S.release(nr));
-                }
-                S.finish();
-                err = S.err;
-            }
-        }
-    }
+    int err = circuit_sort_ranks(c, evk, x, K, d, rank.data(), nullptr);
     for (int a = 0; a < K && !err; a++) {
         const std::vector<const fhe_ct *> xa = X(a);
         for (int s = 0; s < cols && !err; s++) {

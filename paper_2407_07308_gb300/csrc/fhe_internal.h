@@ -410,6 +410,8 @@ void encode_slot_vector(const fhe_ctx *c, const uint64_t *v, int64_t *m);  // n_
 int op_plain(fhe_ctx *c, const fhe_ct *a, const uint64_t *slots, int kind, fhe_ct **out);
 int circuit_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int d, fhe_ct **out);
 int circuit_sort_joint(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int K, int d, fhe_ct **out);
+int circuit_sort_ranks(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int K, int d, fhe_ct **rank,
+                       fhe_ct **matrix);
 std::vector<int64_t> sort_galois(const fhe_ctx *c);
 struct SlotPiece {
     int j, o, s, b;        // input, output, column shift right, row swap

@@ -157,6 +157,7 @@ def lib() -> ctypes.CDLL:
             "fhe_ct_deserialize": (ci, [vp, vp, u64, POINTER(vp)]),
             "fhe_server_cancel": (ci, [vp, c_uint64]),
             "fhe_sort_joint": (ci, [vp, vp, vp, ci, ci, POINTER(vp)]),
+            "fhe_sort_ranks": (ci, [vp, vp, vp, ci, ci, POINTER(vp), vp]),
             "fhe_private_query": (ci, [vp, vp, vp, vp, vp, ci, vp, ci, POINTER(vp)]),
             "fhe_private_query_plan": (ci, [vp, vp, vp, vp, vp, ci, vp, ci, POINTER(vp)]),
             "fhe_ext_galois": (ci, [vp, ci, vp, ci]),
@@ -664,6 +665,23 @@ def fhe_sort_joint(ctx, evk, cts):
     out = (c_void_p * (K * d))()
     _check(lib().fhe_sort_joint(ctx, evk, _handles([h for xs in cts for h in xs]), K, d, out), ctx)
     return [[c_void_p(out[t * d + k]) for k in range(d)] for t in range(K)]
+
+
+def fhe_sort_ranks(ctx, evk, cts, matrix=False):
+    """Ranks (mod p) of every value of row r of the K batches cts[a] (lists of
+    d digit handles), any K cols; with matrix=True also the comparison matrix
+    as a dict (a, b, s) -> handle.  Returns (ranks, matrix or None)."""
+    K, d = len(cts), len(cts[0])
+    cols = fhe_ctx_info(ctx).slots // 2
+    ranks = (c_void_p * K)()
+    mat = (c_void_p * (K * K * cols))() if matrix else None
+    _check(lib().fhe_sort_ranks(ctx, evk, _handles([h for xs in cts for h in xs]), K, d, ranks,
+                                ctypes.cast(mat, c_void_p) if mat is not None else None), ctx)
+    m = None
+    if matrix:
+        m = {(a, b, s): c_void_p(mat[(a * K + b) * cols + s]) for a in range(K) for b in range(K) for s in range(cols)
+             if not (a == b and s == 0)}
+    return [c_void_p(ranks[a]) for a in range(K)], m
 
 
 def fhe_max_min(ctx, evk, xs, ys):

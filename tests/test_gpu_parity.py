@@ -768,3 +768,51 @@ def test_sort_joint_bitexact():
         assert e.value.code == -1
     finally:
         g.close()
+
+
+def test_sort_ranks_longer_than_p_bitexact():
+    """Sequences longer than p (24 values per row at p = 17: six ciphertexts
+    of 4 columns, ties included): the ranks and the comparison matrix
+    bit-exact with the oracle, the ranks decrypting to the plaintext ranks
+    mod p and the matrix to the plaintext comparisons."""
+    from oracle.circuits import sort_galois, sort_ranks
+
+    fhe = _fhe()
+    p, d, logN, K = 17, 1, 10, 6
+    gal = sort_galois(p, 2 ** logN)
+    params = dict(logN=logN, p=p, L=8, K=2, **CHAIN50)
+    o, g = _pair(params, seed=39, galois=gal)
+    try:
+        b = (p + 1) // 2
+        cols = g.ns // 2
+        rnd = random.Random(14)
+        vals = [[rnd.randrange(b) for _ in range(g.ns)] for _ in range(K)]
+        vals[5][1] = vals[0][2]
+        vals[3][6] = vals[2][6]
+        xg = [[g.encrypt_slots([vals[a]], seed=2000 + a)] for a in range(K)]
+        fhe.fhe_trace_enable(g.ctx, True)
+        ranks, mat = fhe.fhe_sort_ranks(g.ctx, g.evk, xg, matrix=True)
+        for h in ranks + list(mat.values()):
+            g.own(h)
+        trace_g = fhe.fhe_trace_get(g.ctx)
+        fhe.fhe_trace_enable(g.ctx, False)
+        for r in range(2):
+            seq = [vals[a][r * cols + c] for a in range(K) for c in range(cols)]
+            assert len(seq) > p
+            for a in range(K):
+                got = g.decrypt(ranks[a])[0]
+                for c in range(cols):
+                    i = a * cols + c
+                    want = sum(1 for j, v in enumerate(seq) if v < seq[i] or (v == seq[i] and j < i)) % p
+                    assert got[r * cols + c] == want
+        xo = [[o.encrypt_slots([vals[a]], seed=2000 + a)[0]] for a in range(K)]
+        ev = o.evaluator()
+        ranks_o, mat_o = sort_ranks(ev, xo)
+        assert sorted(trace_g) == sorted(ev.trace)
+        for a in range(K):
+            _same(ranks_o[a], g.export(ranks[a]), 0)
+        assert set(mat) == set(mat_o)
+        for key in list(mat)[::5]:
+            _same(mat_o[key], g.export(mat[key]), 0)
+    finally:
+        g.close()

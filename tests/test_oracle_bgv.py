@@ -356,6 +356,43 @@ def test_sort_joint_sixteen_values():
     assert [st.decrypt_slots(x) for x in one] == [st.decrypt_slots(x) for x in sort_joint(st.evaluator(), [cts[0]])[0]]
 
 
+def test_sort_ranks_longer_than_p():
+    """Sequences longer than p (24 values per row at p = 17: six ciphertexts
+    of 4 columns, ties included): the rank of every value (the number of
+    values below it plus those equal to it at a lower index) decrypts to its
+    plaintext rank mod p, and every entry of the comparison matrix to the
+    plaintext comparison of its two values."""
+    from oracle.circuits import sort_galois, sort_ranks
+
+    p, d = 17, 1
+    N = 2 ** 8
+    st = OracleSetup(logN=8, p=p, L=8, K=2, seed=29, galois=sort_galois(p, N), **CHAIN50)
+    ns = st.ss.ns
+    cols = ns // 2
+    b = (p + 1) // 2
+    rnd = random.Random(8)
+    K = 6
+    vals = [[rnd.randrange(b) for _ in range(ns)] for _ in range(K)]
+    vals[5][1] = vals[0][2]
+    cts = [[st.encrypt_slots([vals[a]], seed=120 + a)[0]] for a in range(K)]
+    ranks, matrix = sort_ranks(st.evaluator(), cts)
+    assert len(matrix) == K * K * cols - K
+    for r in range(2):
+        seq = [vals[a][r * cols + c] for a in range(K) for c in range(cols)]
+        assert len(seq) > p
+        for a in range(K):
+            got = st.decrypt_slots(ranks[a])
+            for c in range(cols):
+                i = a * cols + c
+                want = sum(1 for j, v in enumerate(seq) if v < seq[i] or (v == seq[i] and j < i)) % p
+                assert got[r * cols + c] == want
+        for (a, bb, sh), lt in list(matrix.items())[:: 7]:
+            got = st.decrypt_slots(lt)
+            for c in range(cols):
+                i, j = a * cols + c, bb * cols + (c + sh) % cols
+                assert got[r * cols + c] == int(seq[j] < seq[i])
+
+
 def _check_plan(ns, useful, n_out, pieces, dest):
     """The plan is a valid compaction: every useful slot lands exactly once,
     no two land on one output slot, and each piece moves its slots by one
