@@ -964,9 +964,19 @@ def run_tournament(args):
     sk, pk = fhe.fhe_keygen(ctx, 4)
     evk = fhe.fhe_evk_create(ctx, sk, fhe.fhe_tournament_galois(ctx), 5)
     g = synth.rng(4)
-    vals = synth.values_with_duplicates(g, 4096, 129 ** 2, 0.10)
-    b, d = 129, 2
+    b, d = 129, args.digits
+    # d = 2: values in [0, 129^2) (about 14 bits); d = 3: the full 16-bit range
+    # [0, 2^16) in three base-129 digits (129^3 >= 2^16)
+    hi = 2 ** 16 if d >= 3 else b ** d
+    vals = synth.values_with_duplicates(g, 4096, hi, 0.10)
     dig = synth.to_digits(vals, b, d)
+    # refreshes per track: before a round that would end below level 1
+    depth = (257 - 2).bit_length() + (d - 1).bit_length() + 1
+    level, refreshes = 20, 0
+    for _ in range(12):
+        if level - depth < 1:
+            level, refreshes = 20, refreshes + 1
+        level -= depth
     xs = [fhe.fhe_encrypt(ctx, pk, dig[k].reshape(32, 128).astype(np.uint64), 100 + k) for k in range(d)]
 
     def one(seed, check=False):
@@ -1000,9 +1010,10 @@ def run_tournament(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded BGV keys, noise and values, 10% duplicates)",
-        "config": {"workload": "max and min of 4096 values in [0, 129^2), N=2^15, p=257, d=2, 32 ciphertexts x "
-                               "128 slots, 20x50-bit + 4 special primes, refresh (device decrypt + re-encrypt) "
-                               "inside the timed region", "rounds": "5 cross-ciphertext + 7 in-slot (rotations)",
+        "config": {"workload": f"max and min of 4096 values in [0, {hi}), N=2^15, p=257, d={d} (base 129), 32 "
+                               "ciphertexts x 128 slots, 20x50-bit + 4 special primes, refresh (device decrypt + "
+                               "re-encrypt) inside the timed region", "rounds": "5 cross-ciphertext + 7 in-slot "
+                               "(rotations)", "levels_per_round": depth, "refreshes_per_track": refreshes,
                    "l2": "ciphertexts 336 MB per digit set > L2"},
         "tournament_ms_p50": round(sorted(ms)[len(ms) // 2], 2), "gpu_launches": launches,
         "clocks": clk.summary(), "cpu_baseline": None, "roofline": None, "e2e": None,
@@ -1572,6 +1583,8 @@ def main():
                          "F_(p^d) slots, then comparison; query: private query with non-blocking comparison; sort16: joint sort of 16-value "
                          "sequences across 4 ciphertexts")
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate (requests/s) for serve")
+    ap.add_argument("--digits", type=int, default=2, choices=[2, 3],
+                    help="tournament digits: 2 (values below 129^2) or 3 (the 16-bit range)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -500,6 +500,12 @@ int fhe_ctx_set_batch_graphs(fhe_ctx *ctx, int max_plans);
 /* 0 once every job of the batch is complete; FHE_ETIMEOUT if that takes
  * longer than timeout_ms (the batch keeps running; wait again later). */
 int fhe_batch_wait(fhe_batch *batch, int timeout_ms);
+/* Per-job completion, without waiting: 1 once job i (its index in the
+ * submission) has its results, 0 if not yet, FHE_EINVAL for a bad index.  A
+ * submission runs its compare and max/min jobs before its sort jobs, with
+ * one completion event per phase and context, so a job need not wait for
+ * the sorts of its batch (or for other contexts' work). */
+int fhe_batch_job_done(fhe_batch *batch, int i);
 /* Waits for the batch and releases its tracking state (not the outputs). */
 void fhe_batch_destroy(fhe_batch *batch);
 

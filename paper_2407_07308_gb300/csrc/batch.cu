@@ -23,8 +23,21 @@
 #include "fhe_internal.h"
 
 struct fhe_batch {
-    std::vector<std::pair<fhe_ctx *, cudaEvent_t>> done;
+    std::vector<std::pair<fhe_ctx *, cudaEvent_t>> done;  // every event of the batch
+    std::vector<int> job_event;                          // per job: its index into done
 };
+
+// Whether job i of the batch has its results (its context's compare phase,
+// or for a sort job its sort phase, has completed): 1 done, 0 not yet, or a
+// negative error.
+int batch_job_done(fhe_batch *B, int i)
+{
+    if (!B || i < 0 || i >= (int)B->job_event.size()) return FHE_EINVAL;
+    const auto &d = B->done[B->job_event[i]];
+    const cudaError_t q = cudaEventQuery(d.second);
+    if (q == cudaErrorNotReady) return 0;
+    return q == cudaSuccess ? 1 : fhe_cuda_check(d.first, q, "batch job");
+}
 
 namespace {
 
@@ -587,18 +600,37 @@ extern "C" int fhe_batch_submit_ex(const fhe_job *jobs, int n, int flags, fhe_ba
         if (!placed) fams.push_back({c});
     }
     fhe_batch *B = new fhe_batch;
+    B->job_event.assign(n, 0);
     int err = 0;
+    // Two phases per family: its compare and max/min jobs, then its sort jobs
+    // (long circuits), each followed by one event per context, so that a
+    // job completes with its own phase rather than with the whole batch.
     for (auto &fam : fams) {
         std::vector<fhe_ctx *> lock_order(fam);
         std::sort(lock_order.begin(), lock_order.end());
         std::vector<std::unique_lock<std::mutex>> locks;
         for (fhe_ctx *c : lock_order) locks.emplace_back(c->mu);
-        err = fam.size() == 1 ? run_context(fam[0], jobs, by_ctx[fam[0]]) : run_family(fam, jobs, by_ctx);
-        for (fhe_ctx *c : fam) {
-            cudaEvent_t ev = nullptr;
-            if (!err) err = fhe_cuda_check(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch event");
-            if (!err) err = fhe_cuda_check(c, cudaEventRecord(ev, c->stream), "batch event");
-            if (ev) B->done.push_back({c, ev});
+        for (int phase = 0; phase < 2 && !err; phase++) {
+            std::map<fhe_ctx *, std::vector<int>> ids;
+            bool any = false;
+            for (fhe_ctx *c : fam)
+                for (int id : by_ctx[c])
+                    if ((jobs[id].kind == FHE_JOB_SORT) == (phase == 1)) ids[c].push_back(id), any = true;
+            if (!any) continue;
+            if (fam.size() == 1)
+                err = run_context(fam[0], jobs, ids[fam[0]]);
+            else
+                err = run_family(fam, jobs, ids);
+            for (fhe_ctx *c : fam) {
+                if (!ids.count(c)) continue;
+                cudaEvent_t ev = nullptr;
+                if (!err) err = fhe_cuda_check(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch event");
+                if (!err) err = fhe_cuda_check(c, cudaEventRecord(ev, c->stream), "batch event");
+                if (ev) {
+                    for (int id : ids[c]) B->job_event[id] = (int)B->done.size();
+                    B->done.push_back({c, ev});
+                }
+            }
         }
         if (err) break;
     }
@@ -609,6 +641,8 @@ extern "C" int fhe_batch_submit_ex(const fhe_job *jobs, int n, int flags, fhe_ba
     *out = B;
     return 0;
 }
+
+extern "C" int fhe_batch_job_done(fhe_batch *B, int i) { return batch_job_done(B, i); }
 
 extern "C" int fhe_batch_wait(fhe_batch *B, int timeout_ms)
 {

@@ -1901,13 +1901,15 @@ std::vector<int64_t> sort_galois(const fhe_ctx *c)
 // own, so only the running sums outlive it.  K = 1 is the row sort.
 // The rank step: for every ciphertext a and every other (b, s), (LT, EQ) =
 // compare(sigma_{5^s} x^b, x^a) and rank^a += LT + w EQ (the tie-break mask
-// of the schedule above); the comparisons of one (a, b) run in one circuit
-// (merged across shifts), so only the running ranks outlive it.  matrix, when
+// of the schedule above); up to SORT_MERGE shifts of one (a, b) run in one
+// circuit (merged operations), so only the running ranks outlive it and the
+// scratch stays that many comparisons' worth.  matrix, when
 // given, receives LT at [(a K + b) cols + s] (null at (a, a, 0)).  No bound on
 // K cols: the ranks are counts mod p.
 int circuit_sort_ranks(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int K, int d, fhe_ct **rank_out,
                        fhe_ct **matrix)
 {
+    constexpr int SORT_MERGE = FHE_SORT_MERGE;
     if (!c->slots_linear || c->ns < 4)
         return fhe_fail(c, FHE_EUNSUPPORTED, "sorting needs p = 1 mod 4 (two columns or more)");
     if (K < 1 || d < 1) return fhe_fail(c, FHE_EINVAL, "sort ranks: K and d must be positive");
@@ -1919,18 +1921,21 @@ int circuit_sort_ranks(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, i
     int err = 0;
     for (int a = 0; a < K && !err; a++) {
         const std::vector<const fhe_ct *> xa = X(a);
-        for (int b = 0; b < K && !err; b++) {
+        for (int bs = 0; bs < K * ((cols + SORT_MERGE - 1) / SORT_MERGE) && !err; bs++) {
+            const int b = bs / ((cols + SORT_MERGE - 1) / SORT_MERGE);
+            const int s0 = (bs % ((cols + SORT_MERGE - 1) / SORT_MERGE)) * SORT_MERGE;
             const std::vector<const fhe_ct *> xb = X(b);
             Circuit S(c, evk);
             std::vector<int> sh;
             std::vector<std::vector<const fhe_ct *>> xr;
-            for (int s = 0; s < cols && !S.err; s++) {
+            for (int s = s0; s < std::min(cols, s0 + SORT_MERGE) && !S.err; s++) {
                 if (b == a && s == 0) continue;
                 std::vector<const fhe_ct *> r(d);
                 for (int k = 0; k < d; k++) r[k] = s ? S.rot(xb[k], gs[s - 1]) : xb[k];
                 sh.push_back(s);
                 xr.push_back(r);
             }
+            if (sh.empty()) continue;
             std::vector<fhe_ct *> lt(sh.size(), nullptr), eq(sh.size(), nullptr);
             std::vector<Circuit::Req> rq;
             for (size_t i = 0; i < sh.size(); i++)

@@ -244,6 +244,7 @@ struct fhe_ctx {
 };
 
 struct fhe_batch;
+int batch_job_done(fhe_batch *B, int job);  // 1 once job `job` of the batch has its results
 
 struct fhe_sk {
     fhe_ctx *ctx;
@@ -412,6 +413,7 @@ int circuit_sort(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int d, 
 int circuit_sort_joint(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int K, int d, fhe_ct **out);
 int circuit_sort_ranks(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *const *x, int K, int d, fhe_ct **rank,
                        fhe_ct **matrix);
+#define FHE_SORT_MERGE 4  // comparisons of a sort's rank step merged into one circuit
 std::vector<int64_t> sort_galois(const fhe_ctx *c);
 struct SlotPiece {
     int j, o, s, b;        // input, output, column shift right, row swap

@@ -3,8 +3,10 @@
 // the device memory they will hold fits a budget, and submits every admitted
 // request as one uneven batch (continuous batching: the next batch is
 // enqueued while the previous one still runs, so the device never waits for
-// the host).  Keys and contexts stay resident; the server owns no
-// ciphertexts.
+// the host).  Each request retires as soon as its own job has its results
+// (per-job completion events of the batch), and its memory estimate leaves
+// the admitted total then.  Keys and contexts stay resident; the server owns
+// no ciphertexts.
 #include <string.h>
 
 #include <algorithm>
@@ -73,8 +75,8 @@ struct fhe_server {
 // limbs: coefficient copy, ModUp digits, the two accumulators, their special
 // part), the relinearised and switched results (4l limbs), all at the input
 // level l; plus the per-digit working set of powers and partial sums and the
-// outputs.  A limb is N words per ciphertext of the batch; B = 4 for p < 64,
-// else 16.
+// outputs; a sort holds FHE_SORT_MERGE comparisons at a time.  A limb is N
+// words per ciphertext of the batch; B = 4 for p < 64, else 16.
 extern "C" uint64_t fhe_job_footprint(const fhe_job *j)
 {
     if (!j || !j->ctx || !j->x || !j->x[0] || j->d < 1) return 0;
@@ -91,32 +93,43 @@ extern "C" uint64_t fhe_job_footprint(const fhe_job *j)
     u64 est = mults * per_mult;
     est += d * (B / 2 + ceil_log2(c->p) + 4) * ct;
     est += (j->kind == FHE_JOB_MAXMIN ? 2 * d : 2) * ct;
-    if (j->kind == FHE_JOB_SORT)  // one shift's comparison at a time, plus the rotated
-        // operands, the rank, the selection powers and the d accumulated outputs
-        est += (ceil_log2(c->p) + 3 * d + 4) * ct + 2 * per_mult;
+    if (j->kind == FHE_JOB_SORT)  // FHE_SORT_MERGE shifts' comparisons at a time, plus the
+        // rotated operands, the rank, the selection powers and the d accumulated outputs
+        est = FHE_SORT_MERGE * est + (ceil_log2(c->p) + 3 * d + 4) * ct + 2 * per_mult;
     return est;
 }
 
+// Each request retires when its own job has its results (not when the whole
+// submission has); a submission is released once all its requests have.
 void fhe_server::reap(std::unique_lock<std::mutex> &)
 {
     for (size_t i = 0; i < inflight.size();) {
-        const int r = fhe_batch_wait(inflight[i].batch, 0);
-        if (r == FHE_ETIMEOUT) {
-            i++;
-            continue;
-        }
+        InFlight &f = inflight[i];
+        bool all = true, any = false;
         const double t = now();
-        for (Request *q : inflight[i].reqs) {
+        for (size_t j = 0; j < f.reqs.size(); j++) {
+            Request *q = f.reqs[j];
+            if (q->state == FHE_REQ_DONE) continue;
+            const int r = batch_job_done(f.batch, (int)j);
+            if (r == 0) {
+                all = false;
+                continue;
+            }
             q->state = FHE_REQ_DONE;
-            q->error = r;
+            q->error = r < 0 ? r : 0;
             q->t_done = t;
             admitted -= q->est;
             completed++;
-            if (r) failed++;
+            if (r < 0) failed++;
+            any = true;
         }
-        fhe_batch_destroy(inflight[i].batch);
+        if (any) cv_done.notify_all();
+        if (!all) {
+            i++;
+            continue;
+        }
+        fhe_batch_destroy(f.batch);
         inflight.erase(inflight.begin() + i);
-        cv_done.notify_all();
     }
 }
 
@@ -264,7 +277,8 @@ extern "C" int fhe_server_stats(fhe_server *s, fhe_server_status *st)
     std::lock_guard<std::mutex> g(s->mu);
     st->queued = (long long)s->queue.size();
     long long running = 0;
-    for (auto &f : s->inflight) running += (long long)f.reqs.size();
+    for (auto &f : s->inflight)
+        for (Request *q : f.reqs) running += q->state == FHE_REQ_RUNNING;
     st->running = running;
     st->completed = s->completed;
     st->failed = s->failed;

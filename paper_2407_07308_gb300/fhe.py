@@ -144,6 +144,7 @@ def lib() -> ctypes.CDLL:
             "fhe_batch_submit": (ci, [vp, ci, POINTER(vp)]),
             "fhe_batch_submit_ex": (ci, [vp, ci, ci, POINTER(vp)]),
             "fhe_batch_wait": (ci, [vp, ci]),
+            "fhe_batch_job_done": (ci, [vp, ci]),
             "fhe_batch_destroy": (None, [vp]),
             "fhe_job_footprint": (ctypes.c_uint64, [vp]),
             "fhe_ctx_inject_alloc_failure": (ci, [vp, ctypes.c_int64]),
@@ -782,6 +783,11 @@ def fhe_batch_wait(batch, timeout_ms: int) -> int:
     if rc < 0 and rc != -6:
         _check(rc)
     return rc
+
+
+def fhe_batch_job_done(batch, i: int) -> bool:
+    """True once job i of the batch has its results (no waiting)."""
+    return _check(lib().fhe_batch_job_done(batch, int(i))) == 1
 
 
 def fhe_batch_destroy(batch):
