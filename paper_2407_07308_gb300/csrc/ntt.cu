@@ -1,1346 +1,8 @@
-// ntt.cu -- the NTT engine: negacyclic NTT / inverse NTT over batches of RNS
-// limbs, with the key-switching and modulus-switching steps fused into their
-// loads and stores.
-//
-// Transform (BoostCom Sec. 2.2: radix-2 NTT, Cooley-Tukey forward and
-// Gentleman-Sande inverse, for power-of-two N):
-//   forward  A[k] = a(psi^(2 brv(k) + 1)), natural-order input, bit-reversed
-//            output; stage s (s = 0..logN-1) pairs j, j + N/2^(s+1) with the
-//            twiddle psi^brv(2^s + (j >> (logN - s)));
-//   inverse  the stages undone in reverse order with psi^-brv(.), then N^-1.
-//
-// GB300 mapping.  N = 2^n is split as 2^n1 x 2^n2 (n1 = ceil(n/2)).  The
-// forward transform is two passes: "columns" runs global stages 0..n1-1,
-// which only combine residues j = e 2^n2 + lo of one column lo, and "rows"
-// runs stages n1..n-1 inside contiguous rows of 2^n2 residues.  Each pass is
-// made of sub-transforms of size 2^M (M = n1 or n2) whose twiddles are
-// entries of the full table: at local stage u, element e of a sub-transform
-// with block index hi uses psi^brv(2^(S+u) + hi 2^u + (e >> (M-u))), S its
-// first global stage.  The inverse runs rows first, then columns.  The
-// half-transformed limb between the passes lives in the job's output limb.
-//
-// Units.  Every CTA has 128 threads holding 16 residues each, so a unit of
-// work is 2048 residues in shared memory: NS = 2^(11-M) sub-transforms of 2^M
-// points.  A sub-transform runs as one radix-16 round (4 stages on strided
-// residues) and one round of the remaining M-4 stages (contiguous blocks),
-// with shared-memory exchanges in between.  A column unit is NC adjacent
-// columns of each of NS/NC jobs (one job except at n = 10); a row unit is
-// either one row of each of 16 jobs that share a prime times NS/16 adjacent
-// rows (the batched case: the CTA stages those rows' twiddles once), or NS
-// adjacent rows of one job (small batches; twiddles read through the cache).
-// Global memory is read and written in coalesced runs of at least 64 bytes.
-//
-// Segments and persistence.  A launch carries a table of up to FHE_SEGS
-// segments; a segment is one batch of limb jobs with its own context (ring
-// degree, twiddle and constant tables), pointers and level.  One launch can
-// therefore serve ciphertexts of different ring degree, level and origin:
-// the units of all segments are numbered in order and every CTA walks them
-// with a grid stride, dispatching each unit on its segment's ring degree.
-// The grid is either one CTA per unit or a fixed number of resident CTAs per
-// SM (the autotuner's choice per context).
-//
-// Load/store functors let one kernel body serve the plain transform and the
-// fused variants: ModUp (basis conversion of a key-switching digit computed
-// while loading, then NTT), ModDown and modulus switching (correction
-// computed while loading, subtract-and-scale applied while storing).
-// Butterflies are Harvey's lazy ones (values below (2s+1)q after s forward
-// stages, in [0, 2q) inverse) with Shoup twiddles.
-#include "fhe_internal.h"
-
-namespace {
-
-// Forward butterfly without normalisation: t = [Y w] in [0, 4q) for any
-// 64-bit Y (shoup_lazy4), so if X, Y < B then X + t and X - t + 4q lie in
-// [0, B + 4q).  After s stages every value is below (4s + 1) q <= 61 q <
-// 2^63 (primes below 2^57, s <= 15); one reduction at the end brings it to
-// [0, q).  q4 = 4q.
-__device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 q, u64 q4)
-{
-    const u64 t = shoup_lazy4(Y, w.x, w.y, q);
-    const u64 x = X;
-    X = x + t;
-    Y = x - t + q4;
-}
-
-// Inverse butterfly on values in [0, 4q): X + Y reduced once by 4q, and
-// [(X - Y + 4q) w] in [0, 4q).
-__device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 q, u64 q4)
-{
-    u64 s = X + Y;
-    s = s >= q4 ? s - q4 : s;
-    u64 d = X - Y + q4;
-    Y = shoup_lazy4(d, w.x, w.y, q);
-    X = s;
-}
-
-// Stages s0 .. s0+R-1 of the forward transform on one group x[0..2^R) whose
-// block index is hi.
-template <int R, class TW>
-__device__ __forceinline__ void fwd_round(u64 (&x)[1 << R], int s0, int hi, const TW &W, u64 q, u64 q2)
-{
-#pragma unroll
-    for (int u = 0; u < R; u++) {
-        const int half = 1 << (R - 1 - u);
-#pragma unroll
-        for (int t = 0; t < (1 << u); t++) {
-            const ulonglong2 w = W.get(s0 + u, (hi << u) + t);
-#pragma unroll
-            for (int k = 0; k < half; k++) {
-                const int e = t * 2 * half + k;
-                ct_bfly(x[e], x[e + half], w, q, q2);
-            }
-        }
-    }
-}
-
-// One stage of the inverse on x[0..2^R): local stage U, butterflies of
-// half-distance 2^(R-1-U).  A template per stage keeps every index a
-// compile-time constant, so x stays in registers.
-template <int R, int U, class TW>
-__device__ __forceinline__ void inv_stage(u64 (&x)[1 << R], int s0, int hi, const TW &W, u64 q, u64 q2)
-{
-    constexpr int half = 1 << (R - 1 - U);
-#pragma unroll
-    for (int t = 0; t < (1 << U); t++) {
-        const ulonglong2 w = W.get(s0 + U, (hi << U) + t);
-#pragma unroll
-        for (int k = 0; k < half; k++) gs_bfly(x[t * 2 * half + k], x[t * 2 * half + k + half], w, q, q2);
-    }
-    if constexpr (U > 0) inv_stage<R, U - 1>(x, s0, hi, W, q, q2);
-}
-
-template <int R, class TW>
-__device__ __forceinline__ void inv_round(u64 (&x)[1 << R], int s0, int hi, const TW &W, u64 q, u64 q2)
-{
-    inv_stage<R, R - 1>(x, s0, hi, W, q, q2);
-}
-
-// ---------------------------------------------------------------------------
-// unit geometry
-// ---------------------------------------------------------------------------
-
-constexpr int T = 128;  // threads per CTA, 16 residues each
-
-// Register cap: 6 resident CTAs (768 threads) per SM, 85 registers a thread.
-#ifndef FHE_NTT_MINB
-#define FHE_NTT_MINB 6
-#endif
-
-// Shared-memory twiddle tables: entry k at k + k / 8 (one 16-byte pad per 8
-// entries), so that the second round's strided twiddle reads (stride up to 8
-// entries across threads) hit distinct banks.
-__host__ __device__ constexpr int twp(int k) { return k + (k >> 3); }
-__host__ __device__ constexpr int twp_size(int n) { return n + n / 8 + 1; }
-
-// smem layout: sub-transform c at c*P(M), element e at e + (e >> 4); P is odd
-// mod 16 in u64 units, so the strided, blocked and row-wise access patterns
-// spread over the banks.
-template <int M>
-struct Sub {
-    static constexpr int SZ = 1 << M;           // elements per sub-transform
-    static constexpr int G = SZ / 16;           // threads per sub-transform
-    static constexpr int NS = T / G;            // sub-transforms per unit
-    static constexpr int R2 = M - 4;            // stages of the second round
-    static constexpr int P = SZ + SZ / 16 + 1;  // padded stride
-    static constexpr int WORDS = NS * P;        // shared memory words
-    static_assert(M >= 5 && M <= 8, "sub-transform size");
-    static_assert(NS * SZ == 16 * T, "16 residues a thread");
-    __device__ static int at(int c, int e) { return c * P + e + (e >> 4); }
-};
-
-constexpr int SM_WORDS = Sub<5>::WORDS > Sub<8>::WORDS ? Sub<5>::WORDS : Sub<8>::WORDS;
-constexpr int TW_WORDS = twp_size(256);  // largest staged twiddle table (ulonglong2)
-constexpr int ROW_J = 16;                    // jobs per grouped row unit
-
-// Twiddle accessors: get(s, j) = psi^brv(2^s + j), the twiddle of global
-// stage s with in-stage index j < 2^s.
-struct GTw {  // the full table in global memory, read-only path
-    const ulonglong2 *__restrict__ p;
-    __device__ ulonglong2 get(int s, int j) const { return __ldg(p + (1 << s) + j); }
-};
-
-struct PrefixTw {  // the first entries of the table, copied to shared memory
-    const ulonglong2 *sm;
-    __device__ ulonglong2 get(int s, int j) const { return sm[twp((1 << s) + j)]; }
-};
-
-// Row twiddles of one row hi (stages N1.., in-stage index hi 2^u + t) staged
-// at offset 2^u - 1 + t.
-struct RowTw {
-    const ulonglong2 *sm;
-    int N1, hi;
-    __device__ ulonglong2 get(int s, int j) const
-    {
-        const int u = s - N1;
-        return sm[twp((1 << u) - 1 + j - (hi << u))];
-    }
-};
-
-// Round 1: thread t = (g, c) with c = t % NS, g = t / NS holds elements
-// e = k G + g (k < 16) of sub-transform c: local stages 0..3.
-// Round 2: thread t = (c, g') with c = t / G, g' = t % G holds the 16/G
-// blocks b = g' (16/G) + i of G contiguous elements: local stages 4..M-1.
-// geo gives each sub-transform's twiddle accessor, block index and prime.
-template <int M, bool FWD, class Geo>
-__device__ __forceinline__ void subtx(u64 *sm, int tid, const Geo &geo)
-{
-    using C = Sub<M>;
-    constexpr int G = C::G, R2 = C::R2, NB = 16 / G, NS = C::NS;
-    // Addresses as a per-thread base plus compile-time offsets: for e = kG + g
-    // (g < G <= 16, kG a multiple of G) e >> 4 = (kG) >> 4, and for
-    // e = 16 g' + iG + f (iG + f < 16) e >> 4 = g'.
-    auto round1 = [&]() {
-        const int c = tid % NS, g = tid / NS;
-        const auto W = geo.tw(c);
-        const int hi = geo.hi(c);
-        const u64 q = geo.q(c), q2 = 4 * q;  // lazy bound of the butterflies
-        u64 *b1 = sm + c * C::P + g;
-        u64 x[16];
-#pragma unroll
-        for (int k = 0; k < 16; k++) x[k] = b1[k * G + ((k * G) >> 4)];
-        if (FWD)
-            fwd_round<4>(x, geo.S, hi, W, q, q2);
-        else
-            inv_round<4>(x, geo.S, hi, W, q, q2);
-#pragma unroll
-        for (int k = 0; k < 16; k++) b1[k * G + ((k * G) >> 4)] = x[k];
-    };
-    auto round2 = [&]() {
-        const int c = tid / G, gp = tid % G;
-        const auto W = geo.tw(c);
-        const int hi = geo.hi(c);
-        const u64 q = geo.q(c), q2 = 4 * q;  // lazy bound of the butterflies
-        u64 *b2 = sm + c * C::P + gp * 17;
-#pragma unroll
-        for (int i = 0; i < NB; i++) {
-            u64 x[1 << R2];
-#pragma unroll
-            for (int f = 0; f < (1 << R2); f++) x[f] = b2[i * G + f];
-            if (FWD)
-                fwd_round<R2>(x, geo.S + 4, hi * 16 + gp * NB + i, W, q, q2);
-            else
-                inv_round<R2>(x, geo.S + 4, hi * 16 + gp * NB + i, W, q, q2);
-#pragma unroll
-            for (int f = 0; f < (1 << R2); f++) b2[i * G + f] = x[f];
-        }
-    };
-    if (FWD) {
-        round1();
-        __syncthreads();
-        round2();
-    } else {
-        round2();
-        __syncthreads();
-        round1();
-    }
-}
-
-// Column pass of ring degree 2^(N1+N2): NC adjacent columns of NJ jobs.
-template <int N1, int N2>
-struct ColGeo {
-    using C = Sub<N1>;
-    static constexpr int NS = C::NS, SZ = C::SZ, NN = 1 << (N1 + N2);
-    static constexpr int NC = NS < (1 << N2) ? NS : (1 << N2);  // columns per job
-    static constexpr int NJ = NS / NC;                          // jobs per unit
-    static constexpr int BLK = (1 << N2) / NC;                  // column blocks per job
-    static constexpr int TWC = twp_size(1 << N1);               // staged twiddles per job
-    static_assert(NJ * TWC <= TW_WORDS, "twiddle staging");
-    static_assert(NJ <= 2, "jobs per column unit");
-    // word r of the unit: job slot, column in job, element
-    __device__ static int jslot(int r) { return NJ == 1 ? 0 : r / (NC * SZ); }
-    __device__ static int col(int r) { return r % NC; }
-    __device__ static int elem(int r) { return (r % (NC * SZ)) / NC; }
-};
-
-template <int N1, int N2>
-struct ColTw {
-    const ulonglong2 *W;
-    u64 q0, q1;
-    static constexpr int S = 0;
-    __device__ PrefixTw tw(int c) const { return PrefixTw{W + (c / ColGeo<N1, N2>::NC) * ColGeo<N1, N2>::TWC}; }
-    __device__ int hi(int) const { return 0; }
-    __device__ u64 q(int c) const { return c / ColGeo<N1, N2>::NC == 0 ? q0 : q1; }
-};
-
-// Row pass: grouped (16 jobs of one prime x R adjacent rows) or single (NS
-// adjacent rows of one job).
-template <int N1, int N2>
-struct RowGeo {
-    using C = Sub<N2>;
-    static constexpr int NS = C::NS, SZ = C::SZ, NN = 1 << (N1 + N2);
-    static constexpr int R = NS / ROW_J;         // rows per grouped unit
-    static constexpr int CH = (1 << N1) / R;     // row chunks per limb (grouped)
-    // row chunks per limb (single; a limb with fewer than NS rows, n = 10,
-    // always takes the grouped form)
-    static constexpr int CHS = (1 << N1) >= NS ? (1 << N1) / NS : 1;
-    static constexpr int TWR = twp_size(SZ - 1); // staged twiddles per row
-    static_assert(NS >= ROW_J && NS % ROW_J == 0, "row units");
-    static_assert(R * TWR <= TW_WORDS, "twiddle staging");
-};
-
-template <int N1, int N2>
-struct RowGrpTw {
-    const ulonglong2 *W;
-    int hi0;
-    u64 qq;
-    int S;
-    __device__ RowTw tw(int c) const
-    {
-        constexpr int R = RowGeo<N1, N2>::R;
-        return RowTw{W + (c % R) * RowGeo<N1, N2>::TWR, N1, hi0 + c % R};
-    }
-    __device__ int hi(int c) const { return hi0 + c % RowGeo<N1, N2>::R; }
-    __device__ u64 q(int) const { return qq; }
-};
-
-struct RowOneTw {
-    GTw g;
-    int hi0;
-    u64 qq;
-    int S;
-    __device__ GTw tw(int) const { return g; }
-    __device__ int hi(int c) const { return hi0 + c; }
-    __device__ u64 q(int) const { return qq; }
-};
-
-// ---------------------------------------------------------------------------
-// segment tables
-// ---------------------------------------------------------------------------
-
-// Per segment: jobs = outer * nl, job = o * nl + l, and the prime of a job
-// depends on l only (so the jobs l, nl + l, 2 nl + l ... can share a CTA).
-struct SegHdr {
-    int logN, outer, nl, grouped;  // grouped: row units of 16 jobs
-    int u_cols, u_rows, pad0, pad1;
-    const ModQ *mq;
-    const ulonglong2 *tw;    // forward or inverse table of the segment's context
-    const ulonglong2 *ninv;  // N^-1 per prime (Shoup pairs)
-};
-
-template <class S>
-struct SegIO {
-    int nseg, ucols, urows, pad;
-    SegHdr h[FHE_SEGS];
-    S s[FHE_SEGS];
-};
-
-template <class IO>
-__device__ __forceinline__ int seg_of(const IO &io, int u, bool rows)
-{
-    int sg = 0;
-    while (sg + 1 < io.nseg && (rows ? io.h[sg + 1].u_rows : io.h[sg + 1].u_cols) <= u) sg++;
-    return sg;
-}
-
-// ---------------------------------------------------------------------------
-// the unit bodies
-// ---------------------------------------------------------------------------
-
-// Moves words r = tid + k T (k < 16) through src(r) -> dst(r, v), staged in
-// chunks of CH: the chunk's reads are all issued before its first write (the
-// compiler does not reorder a global read past a shared-memory write on its
-// own), so they overlap; CH = 0 keeps read/write pairs (better for loads
-// that already hold several reads each, like ModUp's basis conversion).
-template <int CH, class Src, class Dst>
-__device__ __forceinline__ void tile_in(int tid, Src src, Dst dst)
-{
-    constexpr int IT = 16;
-    if constexpr (CH > 0) {
-        constexpr int K = CH < IT ? CH : IT;
-#pragma unroll
-        for (int k0 = 0; k0 < IT; k0 += K) {
-            u64 v[K];
-#pragma unroll
-            for (int k = 0; k < K; k++) v[k] = src(tid + (k0 + k) * T);
-#pragma unroll
-            for (int k = 0; k < K; k++) dst(tid + (k0 + k) * T, v[k]);
-        }
-    } else {
-#pragma unroll 4
-        for (int k = 0; k < IT; k++) dst(tid + k * T, src(tid + k * T));
-    }
-}
-
-// Stores of a forward row pass: word r goes to index idx(r) of state st(r)
-// with value val(r) when ok(r).  Staged: the operands the store reads
-// (IO::NPRE per word) are loaded for a chunk of words before any of the
-// chunk's writes, so those loads overlap.
-template <class IO, class StF, class Ok, class Idx, class Val>
-__device__ __forceinline__ void tile_out(const IO &io, int tid, StF st, Ok ok, Idx idx, Val val)
-{
-    constexpr int IT = 16;
-    if constexpr (IO::NPRE > 0) {
-        constexpr int CH = IO::NPRE == 1 ? IT : IT / 2;
-#pragma unroll
-        for (int k0 = 0; k0 < IT; k0 += CH) {
-            u64 a[CH][IO::NPRE];
-#pragma unroll
-            for (int k = 0; k < CH; k++) {
-                const int r = tid + (k0 + k) * T;
-#pragma unroll
-                for (int w = 0; w < IO::NPRE; w++) a[k][w] = ok(r) ? io.pre(st(r), idx(r), w) : 0;
-            }
-#pragma unroll
-            for (int k = 0; k < CH; k++) {
-                const int r = tid + (k0 + k) * T;
-                if (ok(r)) io.store_pre(st(r), idx(r), val(r), a[k]);
-            }
-        }
-    } else {
-#pragma unroll 4
-        for (int k = 0; k < IT; k++) {
-            const int r = tid + k * T;
-            if (ok(r)) io.store(st(r), idx(r), val(r));
-        }
-    }
-}
-
-// The jobs of a column unit: slot j (j < NJ) holds job0 + j.
-template <int N1, int N2, class IO>
-__device__ __forceinline__ int col_jobs(const IO &io, int sg, int lu, typename IO::St *sts, int *lo0)
-{
-    using Gm = ColGeo<N1, N2>;
-    const SegHdr &H = io.h[sg];
-    const int njobs = H.outer * H.nl;
-    const int job0 = (lu / Gm::BLK) * Gm::NJ;
-    *lo0 = (lu % Gm::BLK) * Gm::NC;
-    if (threadIdx.x < Gm::NJ && job0 + (int)threadIdx.x < njobs) io.begin(sg, job0 + threadIdx.x, sts[threadIdx.x]);
-    __syncthreads();
-    return njobs - job0;  // valid job slots (>= 1)
-}
-
-// Stages the first 2^N1 twiddles of each job's prime (the column stages):
-// loaded into registers first, stored after the tile loads (latency overlap).
-template <int N1, int N2>
-struct ColTwStage {
-    using Gm = ColGeo<N1, N2>;
-    static constexpr int NW = Gm::NJ << N1;
-    static constexpr int PER = (NW + T - 1) / T;
-    ulonglong2 v[PER];
-    template <class St>
-    __device__ void load(const SegHdr &H, const St *sts, int nvalid)
-    {
-#pragma unroll
-        for (int k = 0; k < PER; k++) {
-            const int i = threadIdx.x + k * T, j = i >> N1;
-            v[k] = (i < NW && j < nvalid) ? __ldg(H.tw + (size_t)sts[j].prime * Gm::NN + (i & ((1 << N1) - 1)))
-                                          : make_ulonglong2(0, 0);
-        }
-    }
-    __device__ void load1(const SegHdr &H, int prime)  // one job per unit
-    {
-#pragma unroll
-        for (int k = 0; k < PER; k++) {
-            const int i = threadIdx.x + k * T;
-            v[k] = i < NW ? __ldg(H.tw + (size_t)prime * Gm::NN + i) : make_ulonglong2(0, 0);
-        }
-    }
-    __device__ void store(ulonglong2 *W) const
-    {
-#pragma unroll
-        for (int k = 0; k < PER; k++) {
-            const int i = threadIdx.x + k * T;
-            if (i < NW) W[(i >> N1) * Gm::TWC + twp(i & ((1 << N1) - 1))] = v[k];
-        }
-    }
-};
-
-// Column units of one job (every ring degree but 2^10): the job's state is
-// computed by every thread and stays in registers.
-template <int N1, int N2, class IO>
-__device__ __forceinline__ void fwd_cols_unit1(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W)
-{
-    using Gm = ColGeo<N1, N2>;
-    using C = typename Gm::C;
-    const int tid = threadIdx.x;
-    const SegHdr &H = io.h[sg];
-    const int lo0 = (lu % Gm::BLK) * Gm::NC;
-    typename IO::St st;
-    io.begin(sg, lu / Gm::BLK, st);
-    ColTwStage<N1, N2> tws;
-    tws.load1(H, st.prime);
-    const u64 q = H.mq[st.prime].q;
-    tile_in<IO::LDCH>(
-        tid, [&](int r) { return io.load(st, (Gm::elem(r) << N2) + lo0 + Gm::col(r)); },
-        [&](int r, u64 v) { sm[C::at(Gm::col(r), Gm::elem(r))] = v; });
-    tws.store(W);
-    __syncthreads();
-    subtx<N1, true>(sm, tid, ColTw<N1, N2>{W, q, q});
-    __syncthreads();
-    u64 *mid = io.inter(st);
-#pragma unroll 4
-    for (int k = 0; k < 16; k++) {
-        const int r = tid + k * T;
-        mid[(Gm::elem(r) << N2) + lo0 + Gm::col(r)] = sm[C::at(Gm::col(r), Gm::elem(r))];
-    }
-}
-
-template <int N1, int N2, class IO>
-__device__ __forceinline__ void inv_cols_unit1(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W)
-{
-    using Gm = ColGeo<N1, N2>;
-    using C = typename Gm::C;
-    const int tid = threadIdx.x;
-    const SegHdr &H = io.h[sg];
-    const int lo0 = (lu % Gm::BLK) * Gm::NC;
-    typename IO::St st;
-    io.begin(sg, lu / Gm::BLK, st);
-    ColTwStage<N1, N2> tws;
-    tws.load1(H, st.prime);
-    const u64 q = H.mq[st.prime].q;
-    const ulonglong2 ni = io.final_scale(st);
-    const u64 *mid = io.inter(st);
-    tile_in<16>(
-        tid, [&](int r) { return mid[(Gm::elem(r) << N2) + lo0 + Gm::col(r)]; },
-        [&](int r, u64 v) { sm[C::at(Gm::col(r), Gm::elem(r))] = v; });
-    tws.store(W);
-    __syncthreads();
-    subtx<N1, false>(sm, tid, ColTw<N1, N2>{W, q, q});
-    __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < 16; k++) {
-        const int r = tid + k * T;
-        io.store(st, (Gm::elem(r) << N2) + lo0 + Gm::col(r),
-                 reduce2q(shoup_lazy(sm[C::at(Gm::col(r), Gm::elem(r))], ni.x, ni.y, q), q));
-    }
-}
-
-// Forward, columns: global stages 0..N1-1.
-template <int N1, int N2, class IO>
-__device__ __forceinline__ void fwd_cols_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
-                                              typename IO::St *sts)
-{
-    using Gm = ColGeo<N1, N2>;
-    using C = typename Gm::C;
-    if constexpr (Gm::NJ == 1) {
-        fwd_cols_unit1<N1, N2>(io, sg, lu, sm, W);
-        return;
-    }
-    const int tid = threadIdx.x;
-    int lo0;
-    const int nvalid = col_jobs<N1, N2>(io, sg, lu, sts, &lo0);
-    const SegHdr &H = io.h[sg];
-    ColTwStage<N1, N2> tws;
-    tws.load(H, sts, nvalid);
-    const u64 q0 = H.mq[sts[0].prime].q, q1 = nvalid > 1 ? H.mq[sts[Gm::NJ - 1].prime].q : q0;
-    tile_in<IO::LDCH>(
-        tid,
-        [&](int r) {
-            const int j = Gm::jslot(r);
-            return j < nvalid ? io.load(sts[j], (Gm::elem(r) << N2) + lo0 + Gm::col(r)) : 0;
-        },
-        [&](int r, u64 v) { sm[C::at(Gm::jslot(r) * Gm::NC + Gm::col(r), Gm::elem(r))] = v; });
-    tws.store(W);
-    __syncthreads();
-    subtx<N1, true>(sm, tid, ColTw<N1, N2>{W, q0, q1});
-    __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < 16; k++) {
-        const int r = tid + k * T, j = Gm::jslot(r);
-        if (j < nvalid)
-            io.inter(sts[j])[(Gm::elem(r) << N2) + lo0 + Gm::col(r)] =
-                sm[C::at(j * Gm::NC + Gm::col(r), Gm::elem(r))];
-    }
-}
-
-// Inverse, columns: undoes global stages N1-1..0, then scales (N^-1 times the
-// job's constant) and stores.
-template <int N1, int N2, class IO>
-__device__ __forceinline__ void inv_cols_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
-                                              typename IO::St *sts)
-{
-    using Gm = ColGeo<N1, N2>;
-    using C = typename Gm::C;
-    if constexpr (Gm::NJ == 1) {
-        inv_cols_unit1<N1, N2>(io, sg, lu, sm, W);
-        return;
-    }
-    const int tid = threadIdx.x;
-    int lo0;
-    const int nvalid = col_jobs<N1, N2>(io, sg, lu, sts, &lo0);
-    const SegHdr &H = io.h[sg];
-    ColTwStage<N1, N2> tws;
-    tws.load(H, sts, nvalid);
-    const u64 q0 = H.mq[sts[0].prime].q, q1 = nvalid > 1 ? H.mq[sts[Gm::NJ - 1].prime].q : q0;
-    tile_in<16>(
-        tid,
-        [&](int r) {
-            const int j = Gm::jslot(r);
-            return j < nvalid ? io.inter(sts[j])[(Gm::elem(r) << N2) + lo0 + Gm::col(r)] : 0;
-        },
-        [&](int r, u64 v) { sm[C::at(Gm::jslot(r) * Gm::NC + Gm::col(r), Gm::elem(r))] = v; });
-    tws.store(W);
-    __syncthreads();
-    subtx<N1, false>(sm, tid, ColTw<N1, N2>{W, q0, q1});
-    __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < 16; k++) {
-        const int r = tid + k * T, j = Gm::jslot(r);
-        if (j < nvalid) {
-            const ulonglong2 ni = io.final_scale(sts[j]);
-            const u64 q = j == 0 ? q0 : q1;
-            io.store(sts[j], (Gm::elem(r) << N2) + lo0 + Gm::col(r),
-                     reduce2q(shoup_lazy(sm[C::at(j * Gm::NC + Gm::col(r), Gm::elem(r))], ni.x, ni.y, q), q));
-        }
-    }
-}
-
-// The jobs of a row unit.  Grouped: slots jj < 16 hold jobs (oc 16 + jj) nl
-// + l, rows hi0 .. hi0+R-1; single: slot 0 holds the job, rows hi0 ..
-// hi0+NS-1.  Returns the number of valid slots.
-template <int N1, int N2, bool GRP, class IO>
-__device__ __forceinline__ int row_jobs(const IO &io, int sg, int lu, typename IO::St *sts, int *hi0)
-{
-    using Gm = RowGeo<N1, N2>;
-    const SegHdr &H = io.h[sg];
-    int nvalid;
-    if (GRP) {
-        const int OC = (H.outer + ROW_J - 1) / ROW_J;
-        const int hc = lu % Gm::CH, t = lu / Gm::CH;
-        const int oc = t % OC, l = t / OC;
-        *hi0 = hc * Gm::R;
-        nvalid = min(ROW_J, H.outer - oc * ROW_J);
-        if ((int)threadIdx.x < nvalid) io.begin(sg, (oc * ROW_J + threadIdx.x) * H.nl + l, sts[threadIdx.x]);
-    } else {
-        *hi0 = (lu % Gm::CHS) * Gm::NS;
-        nvalid = 1;
-        if (threadIdx.x == 0) io.begin(sg, lu / Gm::CHS, sts[0]);
-    }
-    __syncthreads();
-    return nvalid;
-}
-
-// Grouped rows stage the R rows' twiddles: entry k of row r is the stage
-// u = floor(log2(k+1)) twiddle with in-stage index (hi0 + r) 2^u + k+1-2^u.
-template <int N1, int N2>
-struct RowTwStage {
-    using Gm = RowGeo<N1, N2>;
-    static constexpr int NW = Gm::R * (Gm::SZ - 1);
-    static constexpr int PER = (NW + T - 1) / T;
-    ulonglong2 v[PER];
-    __device__ void load(const ulonglong2 *tw, int hi0)
-    {
-#pragma unroll
-        for (int k = 0; k < PER; k++) {
-            const int i = threadIdx.x + k * T;
-            v[k] = make_ulonglong2(0, 0);
-            if (i < NW) {
-                const int r = i / (Gm::SZ - 1), e = i % (Gm::SZ - 1);
-                const int u = 31 - __clz(e + 1);
-                v[k] = __ldg(tw + (1 << (N1 + u)) + ((hi0 + r) << u) + (e + 1 - (1 << u)));
-            }
-        }
-    }
-    __device__ void store(ulonglong2 *W) const
-    {
-#pragma unroll
-        for (int k = 0; k < PER; k++) {
-            const int i = threadIdx.x + k * T;
-            if (i < NW) W[(i / (Gm::SZ - 1)) * Gm::TWR + twp(i % (Gm::SZ - 1))] = v[k];
-        }
-    }
-};
-
-// word r of a row unit -> (sub-transform c = r >> N2, element f); the job
-// slot and row of c
-template <int N1, int N2, bool GRP>
-struct RowMap {
-    using Gm = RowGeo<N1, N2>;
-    int hi0;
-    __device__ int c(int r) const { return r >> N2; }
-    __device__ int f(int r) const { return r & (Gm::SZ - 1); }
-    __device__ int slot(int r) const { return GRP ? c(r) / Gm::R : 0; }
-    __device__ int row(int r) const { return hi0 + (GRP ? c(r) % Gm::R : c(r)); }
-};
-
-// Forward, rows: global stages N1..N1+N2-1, reduction to [0, q), store.
-template <int N1, int N2, bool GRP, class IO>
-__device__ __forceinline__ void fwd_rows_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
-                                          typename IO::St *sts)
-{
-    using Gm = RowGeo<N1, N2>;
-    using C = typename Gm::C;
-    const int tid = threadIdx.x;
-    const SegHdr &H = io.h[sg];
-    int hi0;
-    const int nvalid = row_jobs<N1, N2, GRP>(io, sg, lu, sts, &hi0);
-    const RowMap<N1, N2, GRP> mp{hi0};
-    const int prime = sts[0].prime;
-    const ModQ mqp = H.mq[prime];
-    const ulonglong2 *tw = H.tw + (size_t)prime * Gm::NN;
-    RowTwStage<N1, N2> tws;
-    if (GRP) tws.load(tw, hi0);
-    tile_in<16>(
-        tid,
-        [&](int r) {
-            const int j = mp.slot(r);
-            return j < nvalid ? io.inter(sts[j])[(mp.row(r) << N2) + mp.f(r)] : 0;
-        },
-        [&](int r, u64 v) { sm[C::at(mp.c(r), mp.f(r))] = v; });
-    if (GRP) tws.store(W);
-    __syncthreads();
-    if (GRP)
-        subtx<N2, true>(sm, tid, RowGrpTw<N1, N2>{W, hi0, mqp.q, N1});
-    else
-        subtx<N2, true>(sm, tid, RowOneTw{GTw{tw}, hi0, mqp.q, N1});
-    __syncthreads();
-    tile_out(
-        io, tid, [&](int r) -> const typename IO::St & { return sts[mp.slot(r)]; },
-        [&](int r) { return mp.slot(r) < nvalid; }, [&](int r) { return (mp.row(r) << N2) + mp.f(r); },
-        [&](int r) { return reduce64(sm[C::at(mp.c(r), mp.f(r))], mqp); });
-}
-
-// Inverse, rows first: undoes global stages N1+N2-1..N1.
-template <int N1, int N2, bool GRP, class IO>
-__device__ __forceinline__ void inv_rows_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
-                                          typename IO::St *sts)
-{
-    using Gm = RowGeo<N1, N2>;
-    using C = typename Gm::C;
-    const int tid = threadIdx.x;
-    const SegHdr &H = io.h[sg];
-    int hi0;
-    const int nvalid = row_jobs<N1, N2, GRP>(io, sg, lu, sts, &hi0);
-    const RowMap<N1, N2, GRP> mp{hi0};
-    const int prime = sts[0].prime;
-    const u64 q = H.mq[prime].q;
-    const ulonglong2 *tw = H.tw + (size_t)prime * Gm::NN;
-    RowTwStage<N1, N2> tws;
-    if (GRP) tws.load(tw, hi0);
-    tile_in<IO::LDCH>(
-        tid,
-        [&](int r) {
-            const int j = mp.slot(r);
-            return j < nvalid ? io.load(sts[j], (mp.row(r) << N2) + mp.f(r)) : 0;
-        },
-        [&](int r, u64 v) { sm[C::at(mp.c(r), mp.f(r))] = v; });
-    if (GRP) tws.store(W);
-    __syncthreads();
-    if (GRP)
-        subtx<N2, false>(sm, tid, RowGrpTw<N1, N2>{W, hi0, q, N1});
-    else
-        subtx<N2, false>(sm, tid, RowOneTw{GTw{tw}, hi0, q, N1});
-    __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < 16; k++) {
-        const int r = tid + k * T, j = mp.slot(r);
-        if (j < nvalid) io.inter(sts[j])[(mp.row(r) << N2) + mp.f(r)] = sm[C::at(mp.c(r), mp.f(r))];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// kernels: one per (functor, direction, pass); every ring degree 2^10..2^15
-// ---------------------------------------------------------------------------
-
-#define FHE_NTT_DISPATCH(UNIT, LOGN, ...)                          \
-    switch (LOGN) {                                                \
-    case 10: UNIT<5, 5>(__VA_ARGS__); break;                       \
-    case 11: UNIT<6, 5>(__VA_ARGS__); break;                       \
-    case 12: UNIT<6, 6>(__VA_ARGS__); break;                       \
-    case 13: UNIT<7, 6>(__VA_ARGS__); break;                       \
-    case 14: UNIT<7, 7>(__VA_ARGS__); break;                       \
-    case 15: UNIT<8, 7>(__VA_ARGS__); break;                       \
-    default: break;                                                \
-    }
-
-// rows: n = 10 has fewer rows per limb than a single-job unit needs and
-// always takes the grouped form
-#define FHE_NTT_DISPATCH_G(UNIT, G, LOGN, ...)                     \
-    switch (LOGN) {                                                \
-    case 10: if (G) UNIT<5, 5, true>(__VA_ARGS__); break;          \
-    case 11: UNIT<6, 5, G>(__VA_ARGS__); break;                    \
-    case 12: UNIT<6, 6, G>(__VA_ARGS__); break;                    \
-    case 13: UNIT<7, 6, G>(__VA_ARGS__); break;                    \
-    case 14: UNIT<7, 7, G>(__VA_ARGS__); break;                    \
-    case 15: UNIT<8, 7, G>(__VA_ARGS__); break;                    \
-    default: break;                                                \
-    }
-
-template <class IO>
-__global__ void __launch_bounds__(T, FHE_NTT_MINB) k_fwd_cols(const __grid_constant__ IO io)
-{
-    __shared__ u64 sm[SM_WORDS];
-    __shared__ ulonglong2 W[TW_WORDS];
-    __shared__ typename IO::St sts[ROW_J];
-    for (int u = blockIdx.x; u < io.ucols; u += gridDim.x) {
-        const int sg = seg_of(io, u, false);
-        FHE_NTT_DISPATCH(fwd_cols_unit, io.h[sg].logN, io, sg, u - io.h[sg].u_cols, sm, W, sts);
-        __syncthreads();
-    }
-}
-
-template <class IO>
-__global__ void __launch_bounds__(T, FHE_NTT_MINB) k_fwd_rows(const __grid_constant__ IO io)
-{
-    __shared__ u64 sm[SM_WORDS];
-    __shared__ ulonglong2 W[TW_WORDS];
-    __shared__ typename IO::St sts[ROW_J];
-    for (int u = blockIdx.x; u < io.urows; u += gridDim.x) {
-        const int sg = seg_of(io, u, true);
-        if (io.h[sg].grouped) {
-            FHE_NTT_DISPATCH_G(fwd_rows_unit, true, io.h[sg].logN, io, sg, u - io.h[sg].u_rows, sm, W, sts);
-        } else {
-            FHE_NTT_DISPATCH_G(fwd_rows_unit, false, io.h[sg].logN, io, sg, u - io.h[sg].u_rows, sm, W, sts);
-        }
-        __syncthreads();
-    }
-}
-
-template <class IO>
-__global__ void __launch_bounds__(T, FHE_NTT_MINB) k_inv_rows(const __grid_constant__ IO io)
-{
-    __shared__ u64 sm[SM_WORDS];
-    __shared__ ulonglong2 W[TW_WORDS];
-    __shared__ typename IO::St sts[ROW_J];
-    for (int u = blockIdx.x; u < io.urows; u += gridDim.x) {
-        const int sg = seg_of(io, u, true);
-        if (io.h[sg].grouped) {
-            FHE_NTT_DISPATCH_G(inv_rows_unit, true, io.h[sg].logN, io, sg, u - io.h[sg].u_rows, sm, W, sts);
-        } else {
-            FHE_NTT_DISPATCH_G(inv_rows_unit, false, io.h[sg].logN, io, sg, u - io.h[sg].u_rows, sm, W, sts);
-        }
-        __syncthreads();
-    }
-}
-
-template <class IO>
-__global__ void __launch_bounds__(T, FHE_NTT_MINB) k_inv_cols(const __grid_constant__ IO io)
-{
-    __shared__ u64 sm[SM_WORDS];
-    __shared__ ulonglong2 W[TW_WORDS];
-    __shared__ typename IO::St sts[ROW_J];
-    for (int u = blockIdx.x; u < io.ucols; u += gridDim.x) {
-        const int sg = seg_of(io, u, false);
-        FHE_NTT_DISPATCH(inv_cols_unit, io.h[sg].logN, io, sg, u - io.h[sg].u_cols, sm, W, sts);
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// load/store functors (one payload per segment)
-// ---------------------------------------------------------------------------
-
-// A limb map: job (o, l) reads limb in_limb[l] of outer item o and writes
-// limb out_limb[l]; prime[l]; the inverse's final scale is N^-1 times the
-// map entry's constant (scale[l], device) or plain N^-1.
-struct MapSeg {
-    const u64 *in;
-    u64 *out;
-    long long in_outer, out_outer;  // u64 elements
-    const ulonglong2 *scale;
-    uint8_t in_limb[FHE_MAXP], out_limb[FHE_MAXP], prime[FHE_MAXP];
-};
-
-struct IOMap : SegIO<MapSeg> {
-    struct St {
-        const u64 *in;
-        u64 *out;
-        ulonglong2 fs;
-        int prime;
-    };
-    __device__ void begin(int sg, int job, St &t) const
-    {
-        const SegHdr &H = h[sg];
-        const MapSeg &S = s[sg];
-        const int N = 1 << H.logN, o = job / H.nl, l = job % H.nl;
-        t.in = S.in + o * S.in_outer + (long long)S.in_limb[l] * N;
-        t.out = S.out + o * S.out_outer + (long long)S.out_limb[l] * N;
-        t.prime = S.prime[l];
-        t.fs = S.scale ? S.scale[l] : H.ninv[t.prime];
-    }
-    __device__ u64 load(const St &t, int i) const { return t.in[i]; }
-    __device__ void store(const St &t, int i, u64 v) const { t.out[i] = v; }
-    static constexpr int NPRE = 0;   // operands the store reads
-    static constexpr int LDCH = 16;  // loads staged per chunk (0: not staged)
-    __device__ u64 pre(const St &, int, int) const { return 0; }
-    __device__ void store_pre(const St &t, int i, u64 v, const u64 *) const { t.out[i] = v; }
-    __device__ u64 *inter(const St &t) const { return t.out; }
-    __device__ ulonglong2 final_scale(const St &t) const { return t.fs; }
-};
-
-// A scaled inverse whose last map entry (limb l-1 of the relinearisation
-// accumulators) loads y = acc + (P mod q) addend: the first step of the
-// relinearisation fused with the modulus switch.  Job = (ct, poly) * nl + entry.
-struct YSeg : MapSeg {
-    const u64 *abase;
-    long long a_outer, a_poly;
-    int amask, alimb;
-    u64 Pm, Pm_s, qm;
-};
-
-struct IOScaledY : SegIO<YSeg> {
-    struct St {
-        const u64 *in, *add;
-        u64 *out;
-        ulonglong2 fs;
-        u64 Pm, Pm_s, qm;
-        int prime;
-    };
-    __device__ void begin(int sg, int job, St &t) const
-    {
-        const SegHdr &H = h[sg];
-        const YSeg &S = s[sg];
-        const int N = 1 << H.logN, o = job / H.nl, e = job % H.nl, pi = o & 1;
-        const long long c = o >> 1;
-        t.in = S.in + o * S.in_outer + (long long)S.in_limb[e] * N;
-        t.out = S.out + o * S.out_outer + (long long)S.out_limb[e] * N;
-        t.prime = S.prime[e];
-        t.fs = S.scale[e];
-        t.add = (e == H.nl - 1 && ((S.amask >> pi) & 1)) ? S.abase + c * S.a_outer + pi * S.a_poly + (long long)S.alimb * N
-                                                          : nullptr;
-        t.Pm = S.Pm;
-        t.Pm_s = S.Pm_s;
-        t.qm = S.qm;
-    }
-    __device__ u64 load(const St &t, int i) const
-    {
-        return t.add ? addmod(t.in[i], shoup(t.add[i], t.Pm, t.Pm_s, t.qm), t.qm) : t.in[i];
-    }
-    __device__ void store(const St &t, int i, u64 v) const { t.out[i] = v; }
-    static constexpr int NPRE = 0;
-    static constexpr int LDCH = 16;
-    __device__ u64 pre(const St &, int, int) const { return 0; }
-    __device__ void store_pre(const St &t, int i, u64 v, const u64 *) const { t.out[i] = v; }
-    __device__ u64 *inter(const St &t) const { return t.out; }
-    __device__ ulonglong2 final_scale(const St &t) const { return t.fs; }
-};
-
-// ModUp: extended limb t of digit j of ct c:  y = sum_a t_a (Q_j/q_a) mod r,
-// where the source limbs already hold t_a = [x_a (Q_j/q_a)^-1]_{q_a} (the
-// inverse NTT that produced them applied that factor).  Job = c * njobs + e
-// (entry e: digit, target limb, prime).
-struct ModUpSeg {
-    const u64 *d2c;  // [count][l][N] coefficient domain
-    u64 *ext;        // [count][dnum][l+K][N]
-    const ModUpParams *P;
-    int l, K, dnum, pad;
-};
-
-struct IOModUp : SegIO<ModUpSeg> {
-    struct St {
-        const u64 *src;
-        u64 *dst;
-        int nsrc, prime, N, pad;
-        ModQ mt;
-        u64 hat[FHE_MAXK];
-    };
-    __device__ void begin(int sg, int job, St &t) const
-    {
-        const SegHdr &H = h[sg];
-        const ModUpSeg &S = s[sg];
-        const int N = 1 << H.logN, c = job / H.nl, e = job % H.nl;
-        const ModUpParams *P = S.P;
-        const int j = P->job_digit[e], tg = P->job_tgt[e];
-        const int lo = P->digit_lo[j];
-        t.nsrc = P->digit_n[j];
-        t.N = N;
-        t.src = S.d2c + ((long long)c * S.l + lo) * N;
-        t.dst = S.ext + (((long long)c * S.dnum + j) * (S.l + S.K) + tg) * N;
-        t.prime = P->job_prime[e];
-        t.mt = H.mq[t.prime];
-#pragma unroll
-        for (int a = 0; a < FHE_MAXK; a++)
-            if (a < t.nsrc) t.hat[a] = P->hat[j][a][tg];
-    }
-    __device__ u64 load(const St &t, int n) const
-    {
-        u128 acc = 0;
-#pragma unroll
-        for (int a = 0; a < FHE_MAXK; a++)
-            if (a < t.nsrc) acc += (u128)t.src[(long long)a * t.N + n] * t.hat[a];
-        return barrett128(acc, t.mt);
-    }
-    __device__ void store(const St &t, int k, u64 v) const { t.dst[k] = v; }
-    static constexpr int NPRE = 0;
-    static constexpr int LDCH = 0;  // each load already sums several limbs
-    __device__ u64 pre(const St &, int, int) const { return 0; }
-    __device__ void store_pre(const St &t, int k, u64 v, const u64 *) const { t.dst[k] = v; }
-    __device__ u64 *inter(const St &t) const { return t.dst; }
-    __device__ ulonglong2 final_scale(const St &) const { return make_ulonglong2(0, 0); }
-};
-
-// ModDown of poly pi of ct c, data limb i:
-//   delta_i = sum_k t_k * (p P/p_k mod q_i),  out_i = (acc_i - delta_i) P^-1 + addend_i,
-// where the special limbs already hold t_k = [acc_{P,k} p^-1 (P/p_k)^-1]_{p_k}
-// (applied by the inverse NTT that produced them).  Job = (c, pi) * l + i.
-struct ModDownSeg {
-    const u64 *accP;  // [count][2][K][N] coefficient domain
-    const u64 *acc;   // [count][2][l+K][N] NTT domain
-    const u64 *abase;
-    long long a_outer, a_poly;
-    u64 *out;         // [count][2][l][N]
-    const ModDownParams *P;
-    int l, K, amask, pad;
-};
-
-struct IOModDown : SegIO<ModDownSeg> {
-    struct St {
-        const u64 *w, *acc, *add;
-        u64 *out;
-        int prime, K, N, pad;
-        ModQ mi;
-        u64 pinv, pinv_s;
-        u64 phat[FHE_MAXK];
-    };
-    __device__ void begin(int sg, int job, St &t) const
-    {
-        const SegHdr &H = h[sg];
-        const ModDownSeg &S = s[sg];
-        const int N = 1 << H.logN, l = S.l, K = S.K;
-        const int c = job / (2 * l), pi = (job / l) % 2, i = job % l;
-        t.w = S.accP + ((long long)c * 2 + pi) * K * N;
-        t.acc = S.acc + (((long long)c * 2 + pi) * (l + K) + i) * N;
-        t.add = ((S.amask >> pi) & 1) ? S.abase + c * S.a_outer + pi * S.a_poly + (long long)i * N : nullptr;
-        t.out = S.out + (((long long)c * 2 + pi) * l + i) * N;
-        t.prime = i;
-        t.K = K;
-        t.N = N;
-        t.mi = H.mq[i];
-        t.pinv = S.P->pinv[i];
-        t.pinv_s = S.P->pinv_s[i];
-#pragma unroll
-        for (int k = 0; k < FHE_MAXK; k++)
-            if (k < K) t.phat[k] = S.P->phat[k][i];
-    }
-    __device__ u64 load(const St &t, int n) const
-    {
-        u128 a = 0;
-#pragma unroll
-        for (int k = 0; k < FHE_MAXK; k++)
-            if (k < t.K) a += (u128)t.w[(long long)k * t.N + n] * t.phat[k];
-        return barrett128(a, t.mi);
-    }
-    __device__ void store(const St &t, int k, u64 v) const
-    {
-        const u64 q = t.mi.q;
-        u64 r = shoup(submod(t.acc[k], v, q), t.pinv, t.pinv_s, q);
-        if (t.add) r = addmod(r, t.add[k], q);
-        t.out[k] = r;
-    }
-    static constexpr int NPRE = 2;  // accumulator, addend
-    static constexpr int LDCH = 16;
-    __device__ u64 pre(const St &t, int k, int w) const { return w == 0 ? t.acc[k] : (t.add ? t.add[k] : 0); }
-    __device__ void store_pre(const St &t, int k, u64 v, const u64 *pv) const
-    {
-        const u64 q = t.mi.q;
-        u64 r = shoup(submod(pv[0], v, q), t.pinv, t.pinv_s, q);
-        if (t.add) r = addmod(r, pv[1], q);
-        t.out[k] = r;
-    }
-    __device__ u64 *inter(const St &t) const { return t.out; }
-    __device__ ulonglong2 final_scale(const St &) const { return make_ulonglong2(0, 0); }
-};
-
-// Modulus switch l -> l-1 of poly pi of ct c, limb i < l-1:
-//   delta_i = p w mod q_i,  out_i = (x_i - delta_i) q_{l-1}^-1,
-// where `last` already holds w = [x_{l-1} p^-1]_{q_{l-1}} in the coefficient
-// domain (applied by the inverse NTT that produced it).
-// Job = (c, pi) * (l-1) + i.
-struct SwitchSeg {
-    const u64 *last;  // [count][npoly][N] coefficient domain
-    const u64 *in;    // [count][npoly][l][N]
-    u64 *out;         // [count][npoly][l-1][N]
-    const ModSwitchParams *P;
-    int l, npoly;
-};
-
-struct IOModSwitch : SegIO<SwitchSeg> {
-    struct St {
-        const u64 *last, *in;
-        u64 *out;
-        int prime, pad;
-        u64 q, pi, pis, qi, qis;
-    };
-    __device__ void begin(int sg, int job, St &t) const
-    {
-        const SegHdr &H = h[sg];
-        const SwitchSeg &S = s[sg];
-        const int N = 1 << H.logN, l = S.l, np = S.npoly;
-        const int c = job / (np * (l - 1)), pi = (job / (l - 1)) % np, i = job % (l - 1);
-        t.last = S.last + ((long long)c * np + pi) * N;
-        t.in = S.in + (((long long)c * np + pi) * l + i) * N;
-        t.out = S.out + (((long long)c * np + pi) * (l - 1) + i) * N;
-        t.prime = i;
-        t.q = H.mq[i].q;
-        t.pi = S.P->p_i[i];
-        t.pis = S.P->p_i_s[i];
-        t.qi = S.P->qinv[i];
-        t.qis = S.P->qinv_s[i];
-    }
-    __device__ u64 load(const St &t, int n) const { return shoup(t.last[n], t.pi, t.pis, t.q); }
-    __device__ void store(const St &t, int k, u64 v) const { t.out[k] = shoup(submod(t.in[k], v, t.q), t.qi, t.qis, t.q); }
-    static constexpr int NPRE = 1;  // the limb being switched
-    static constexpr int LDCH = 16;
-    __device__ u64 pre(const St &t, int k, int) const { return t.in[k]; }
-    __device__ void store_pre(const St &t, int k, u64 v, const u64 *pv) const
-    {
-        t.out[k] = shoup(submod(pv[0], v, t.q), t.qi, t.qis, t.q);
-    }
-    __device__ u64 *inter(const St &t) const { return t.out; }
-    __device__ ulonglong2 final_scale(const St &) const { return make_ulonglong2(0, 0); }
-};
-
-// Relinearisation fused with the modulus switch that follows it (l -> l-1)
-// for poly pi of ct c, kept limb i < l-1:
-//   correction_i = sum_{k<K} t_k h[k][i] + w h[K][i] (coefficient domain),
-//   out_i = (acc_i P^-1 + add_i - NTT(correction)_i) q_{l-1}^-1,
-// where src holds t_0..t_{K-1} (the special limbs, already scaled) and w.
-// Job = (c, pi) * (l-1) + i.
-struct RelinMSSeg {
-    const u64 *src;  // [count][2][K+1][N] coefficient domain
-    const u64 *acc;  // [count][2][l+K][N] NTT domain
-    const u64 *abase;
-    long long a_outer, a_poly;
-    u64 *out;        // [count][2][l-1][N]
-    const RelinMSParams *P;
-    int l, K, amask, pad;
-};
-
-struct IORelinMS : SegIO<RelinMSSeg> {
-    struct St {
-        const u64 *w, *acc, *add;
-        u64 *out;
-        int prime, K, N, pad;
-        ModQ mi;
-        u64 pinv, pinv_s, qminv, qminv_s;
-        u64 h[FHE_MAXK];
-    };
-    __device__ void begin(int sg, int job, St &t) const
-    {
-        const SegHdr &H = h[sg];
-        const RelinMSSeg &S = s[sg];
-        const int N = 1 << H.logN, l = S.l, K = S.K, m = l - 1;
-        const int c = job / (2 * m), pi = (job / m) % 2, i = job % m;
-        t.w = S.src + ((long long)c * 2 + pi) * (K + 1) * N;
-        t.acc = S.acc + (((long long)c * 2 + pi) * (l + K) + i) * N;
-        t.add = ((S.amask >> pi) & 1) ? S.abase + c * S.a_outer + pi * S.a_poly + (long long)i * N : nullptr;
-        t.out = S.out + (((long long)c * 2 + pi) * m + i) * N;
-        t.prime = i;
-        t.K = K;
-        t.N = N;
-        t.mi = H.mq[i];
-        t.pinv = S.P->pinv[i];
-        t.pinv_s = S.P->pinv_s[i];
-        t.qminv = S.P->qminv[i];
-        t.qminv_s = S.P->qminv_s[i];
-#pragma unroll
-        for (int k = 0; k < FHE_MAXK; k++)
-            if (k <= K) t.h[k] = S.P->h[k][i];
-    }
-    // K + 1 <= FHE_MAXK products of canonical residues: below 2^(2b+3)
-    __device__ u64 load(const St &t, int n) const
-    {
-        u128 a = 0;
-#pragma unroll
-        for (int k = 0; k < FHE_MAXK; k++)
-            if (k <= t.K) a += (u128)t.w[(long long)k * t.N + n] * t.h[k];
-        return barrett128(a, t.mi);
-    }
-    __device__ u64 combine(const St &t, u64 accv, u64 addv, u64 v) const
-    {
-        const u64 q = t.mi.q;
-        u64 r = shoup(accv, t.pinv, t.pinv_s, q);
-        if (t.add) r = addmod(r, addv, q);
-        return shoup(submod(r, v, q), t.qminv, t.qminv_s, q);
-    }
-    __device__ void store(const St &t, int k, u64 v) const { t.out[k] = combine(t, t.acc[k], t.add ? t.add[k] : 0, v); }
-    static constexpr int NPRE = 2;  // accumulator, addend
-    static constexpr int LDCH = 0;  // each load sums K + 1 limbs
-    __device__ u64 pre(const St &t, int k, int w) const { return w == 0 ? t.acc[k] : (t.add ? t.add[k] : 0); }
-    __device__ void store_pre(const St &t, int k, u64 v, const u64 *pv) const { t.out[k] = combine(t, pv[0], pv[1], v); }
-    __device__ u64 *inter(const St &t) const { return t.out; }
-    __device__ ulonglong2 final_scale(const St &) const { return make_ulonglong2(0, 0); }
-};
-
-// k modulus switches at once (l -> l-k), poly pi of ct c, kept limb i < l-k:
-//   correction_i = sum_{t<k} w_t G[t][i],  out_i = (x_i - NTT(correction)_i) D_k^-1.
-// Job = (c, pi) * (l-k) + i.
-struct MultiSeg {
-    const u64 *src;  // [count][npoly][k][N] coefficient domain: w_0 .. w_{k-1}
-    const u64 *in;   // [count][npoly][l][N]
-    u64 *out;        // [count][npoly][l-k][N]
-    const MultiSwitchParams *P;
-    int l, k, npoly, pad;
-};
-
-struct IOMultiSwitch : SegIO<MultiSeg> {
-    struct St {
-        const u64 *w, *in;
-        u64 *out;
-        int prime, k, N, pad;
-        ModQ mi;
-        u64 dinv, dinv_s;
-        u64 g[FHE_MAXK];
-    };
-    __device__ void begin(int sg, int job, St &t) const
-    {
-        const SegHdr &H = h[sg];
-        const MultiSeg &S = s[sg];
-        const int N = 1 << H.logN, kept = S.l - S.k, np = S.npoly;
-        const int c = job / (np * kept), pi = (job / kept) % np, i = job % kept;
-        t.w = S.src + ((long long)c * np + pi) * S.k * N;
-        t.in = S.in + (((long long)c * np + pi) * S.l + i) * N;
-        t.out = S.out + (((long long)c * np + pi) * kept + i) * N;
-        t.prime = i;
-        t.k = S.k;
-        t.N = N;
-        t.mi = H.mq[i];
-        t.dinv = S.P->Dinv[i];
-        t.dinv_s = S.P->Dinv_s[i];
-#pragma unroll
-        for (int j = 0; j < FHE_MAXK; j++)
-            if (j < S.k) t.g[j] = S.P->G[j][i];
-    }
-    __device__ u64 load(const St &t, int n) const
-    {
-        u128 a = 0;
-#pragma unroll
-        for (int j = 0; j < FHE_MAXK; j++)
-            if (j < t.k) a += (u128)t.w[(long long)j * t.N + n] * t.g[j];
-        return barrett128(a, t.mi);
-    }
-    __device__ void store(const St &t, int j, u64 v) const
-    {
-        t.out[j] = shoup(submod(t.in[j], v, t.mi.q), t.dinv, t.dinv_s, t.mi.q);
-    }
-    static constexpr int NPRE = 1;
-    static constexpr int LDCH = 0;
-    __device__ u64 pre(const St &t, int j, int) const { return t.in[j]; }
-    __device__ void store_pre(const St &t, int j, u64 v, const u64 *pv) const
-    {
-        t.out[j] = shoup(submod(pv[0], v, t.mi.q), t.dinv, t.dinv_s, t.mi.q);
-    }
-    __device__ u64 *inter(const St &t) const { return t.out; }
-    __device__ ulonglong2 final_scale(const St &) const { return make_ulonglong2(0, 0); }
-};
-
-// ---------------------------------------------------------------------------
-// host side: unit counts, grids, launches
-// ---------------------------------------------------------------------------
-
-struct Split {
-    int n1, n2, ns1, ns2;
-};
-
-Split split_of(int logN)
-{
-    Split s;
-    s.n1 = (logN + 1) / 2;
-    s.n2 = logN / 2;
-    s.ns1 = 2048 >> s.n1;
-    s.ns2 = 2048 >> s.n2;
-    return s;
-}
-
-// Row units are grouped (16 jobs of one prime) once a segment has at least
-// this many outer items; below it a unit holds adjacent rows of one job.
-constexpr int GROUP_MIN_OUTER = 12;
-
-// Fills the header of segment `sg` (jobs = outer * nl) and its unit counts.
-void seg_header(SegHdr &H, const fhe_ctx *c, bool fwd, int outer, int nl)
-{
-    memset(&H, 0, sizeof(H));
-    const Split sp = split_of(c->logN);
-    H.logN = c->logN;
-    H.outer = outer;
-    H.nl = nl;
-    H.mq = c->d_mq;
-    H.tw = fwd ? c->d_fwd : c->d_inv;
-    H.ninv = c->d_ninv;
-    const int njobs = outer * nl;
-    const int nc = std::min(sp.ns1, 1 << sp.n2), nj = sp.ns1 / nc, blk = (1 << sp.n2) / nc;
-    H.u_cols = ((njobs + nj - 1) / nj) * blk;  // counts; turned into prefixes by finish()
-    H.grouped = outer >= GROUP_MIN_OUTER || (1 << sp.n1) < sp.ns2;
-    if (H.grouped)
-        H.u_rows = nl * ((outer + ROW_J - 1) / ROW_J) * ((1 << sp.n1) / (sp.ns2 / ROW_J));
-    else
-        H.u_rows = njobs * ((1 << sp.n1) / sp.ns2);
-}
-
-// Grid of a pass: one CTA per unit (variant 0) or a fixed number of resident
-// CTAs per SM that walk the units (variants 1..3: 6, 4 and 2 per SM).
-int grid_of(const fhe_ctx *c, int units)
-{
-    static const int per_sm[FHE_NTT_VARIANTS] = {0, 6, 4, 2};
-    const int v = c->ntt_variant;
-    if (v <= 0 || v >= FHE_NTT_VARIANTS || c->sms <= 0) return units;
-    return std::min(units, per_sm[v] * c->sms);
-}
-
-template <class IO>
-void finish(IO &io)
-{
-    int uc = 0, ur = 0;
-    for (int s = 0; s < io.nseg; s++) {
-        const int nc = io.h[s].u_cols, nr = io.h[s].u_rows;
-        io.h[s].u_cols = uc;
-        io.h[s].u_rows = ur;
-        uc += nc;
-        ur += nr;
-    }
-    io.ucols = uc;
-    io.urows = ur;
-}
-
-// Launches both passes of the segments in io on the stream of `c` (the
-// first segment's context).  bytes / bfly: algorithmic traffic and butterflies
-// of the whole launch, for the per-class timing.
-template <class IO>
-void run(fhe_ctx *c, IO &io, bool fwd, int cls, double bytes, double bfly)
-{
-    if (io.nseg == 0) return;
-    finish(io);
-    if (io.ucols == 0) return;
-    prof_begin(c, cls, bytes, bfly);
-    if (fwd) {
-        k_fwd_cols<IO><<<grid_of(c, io.ucols), T, 0, c->stream>>>(io);
-        k_fwd_rows<IO><<<grid_of(c, io.urows), T, 0, c->stream>>>(io);
-    } else {
-        k_inv_rows<IO><<<grid_of(c, io.urows), T, 0, c->stream>>>(io);
-        k_inv_cols<IO><<<grid_of(c, io.ucols), T, 0, c->stream>>>(io);
-    }
-    c->launches += 2;
-    prof_end(c);
-}
-
-double bfly_of(const fhe_ctx *c, double njobs) { return njobs * (c->N / 2) * c->logN; }
-
-void map_seg(MapSeg &S, const u64 *in, u64 *out, const LimbMap &m, const ulonglong2 *scale)
-{
-    memset(&S, 0, sizeof(S));
-    S.in = in;
-    S.out = out;
-    S.in_outer = m.in_outer;
-    S.out_outer = m.out_outer;
-    S.scale = scale;
-    for (int i = 0; i < m.nl; i++) {
-        S.in_limb[i] = (uint8_t)m.in_limb[i];
-        S.out_limb[i] = (uint8_t)m.out_limb[i];
-        S.prime[i] = (uint8_t)m.prime[i];
-    }
-}
-
-// Runs `fill(io, item)` over items in launches of at most FHE_SEGS segments.
-template <class IO, class Item, class Fill>
-void run_many(const std::vector<Item> &items, bool fwd, int cls, Fill fill)
-{
-    size_t i = 0;
-    while (i < items.size()) {
-        IO io;
-        memset(&io, 0, sizeof(io));
-        fhe_ctx *c0 = items[i].c;
-        double bytes = 0, bfly = 0;
-        for (; i < items.size() && io.nseg < FHE_SEGS; i++) {
-            double b = 0, f = 0;
-            if (fill(io, io.nseg, items[i], &b, &f)) io.nseg++;
-            bytes += b;
-            bfly += f;
-        }
-        run(c0, io, fwd, cls, bytes, bfly);
-    }
-}
-
-}  // namespace
+// ntt.cu -- NTT launches through limb maps (plain, scaled, and the scaled inverse whose
+// last entry forms the relinearisation's y), the raw transforms' launchers,
+// and the autotuner.
+// The engine's kernels and functors are in ntt_engine.cuh.
+#include "ntt_engine.cuh"
 
 bool ntt_supported_logn(int logN) { return logN >= 10 && logN <= 15; }
 
@@ -1382,119 +44,6 @@ void launch_ntt_inv_scaled_y_many(const std::vector<NttYArgs> &a)
     });
 }
 
-void launch_ntt_modup_many(const std::vector<NttModUpArgs> &a)
-{
-    run_many<IOModUp>(a, true, FHE_K_NTT_MODUP, [](IOModUp &io, int sg, const NttModUpArgs &x, double *b, double *f) {
-        const ModUpParams &P = x.c->modup[x.level];
-        if (x.count <= 0 || P.njobs <= 0) return false;
-        seg_header(io.h[sg], x.c, true, x.count, P.njobs);
-        ModUpSeg &S = io.s[sg];
-        S.d2c = x.d2c;
-        S.ext = x.ext;
-        S.P = x.c->d_modup + x.level;
-        S.l = x.level;
-        S.K = x.c->K;
-        S.dnum = P.dnum;
-        double words = 0;
-        for (int e = 0; e < P.njobs; e++) words += P.digit_n[P.job_digit[e]] + 1.0;
-        *b = 8.0 * x.c->N * words * x.count;
-        *f = bfly_of(x.c, (double)P.njobs * x.count);
-        return true;
-    });
-}
-
-void launch_ntt_moddown_many(const std::vector<NttDownArgs> &a)
-{
-    run_many<IOModDown>(a, true, FHE_K_NTT_MODDOWN, [](IOModDown &io, int sg, const NttDownArgs &x, double *b, double *f) {
-        if (x.count <= 0) return false;
-        seg_header(io.h[sg], x.c, true, 2 * x.count, x.level);
-        ModDownSeg &S = io.s[sg];
-        S.accP = x.src;
-        S.acc = x.acc;
-        S.abase = x.abase;
-        S.a_outer = x.a_outer;
-        S.a_poly = x.a_poly;
-        S.amask = x.amask;
-        S.out = x.out;
-        S.P = x.c->d_moddown + x.level;
-        S.l = x.level;
-        S.K = x.c->K;
-        // reads K special limbs, acc_i and (for masked polys) the addend; writes out_i
-        const double add_frac = ((x.amask & 1) + ((x.amask >> 1) & 1)) / 2.0;
-        const double njobs = 2.0 * x.level * x.count;
-        *b = 8.0 * x.c->N * njobs * (x.c->K + 2.0 + add_frac);
-        *f = bfly_of(x.c, njobs);
-        return true;
-    });
-}
-
-void launch_ntt_relin_ms_many(const std::vector<NttDownArgs> &a)
-{
-    run_many<IORelinMS>(a, true, FHE_K_NTT_MODDOWN, [](IORelinMS &io, int sg, const NttDownArgs &x, double *b, double *f) {
-        if (x.count <= 0 || x.level < 2) return false;
-        seg_header(io.h[sg], x.c, true, 2 * x.count, x.level - 1);
-        RelinMSSeg &S = io.s[sg];
-        S.src = x.src;
-        S.acc = x.acc;
-        S.abase = x.abase;
-        S.a_outer = x.a_outer;
-        S.a_poly = x.a_poly;
-        S.amask = x.amask;
-        S.out = x.out;
-        S.P = x.c->d_rms + x.level;
-        S.l = x.level;
-        S.K = x.c->K;
-        // reads K + 1 correction sources, acc_i and (for masked polys) the addend; writes out_i
-        const double add_frac = ((x.amask & 1) + ((x.amask >> 1) & 1)) / 2.0;
-        const double njobs = 2.0 * (x.level - 1) * x.count;
-        *b = 8.0 * x.c->N * njobs * (x.c->K + 3.0 + add_frac);
-        *f = bfly_of(x.c, njobs);
-        return true;
-    });
-}
-
-void launch_ntt_modswitch_many(const std::vector<NttSwitchArgs> &a)
-{
-    run_many<IOModSwitch>(a, true, FHE_K_NTT_MODSWITCH, [](IOModSwitch &io, int sg, const NttSwitchArgs &x, double *b,
-                                                           double *f) {
-        if (x.count <= 0 || x.level < 2) return false;
-        seg_header(io.h[sg], x.c, true, x.npoly * x.count, x.level - 1);
-        SwitchSeg &S = io.s[sg];
-        S.last = x.src;
-        S.in = x.in;
-        S.out = x.out;
-        S.P = x.c->d_modswitch + x.level;
-        S.l = x.level;
-        S.npoly = x.npoly;
-        const double njobs = (double)x.npoly * (x.level - 1) * x.count;
-        *b = 8.0 * x.c->N * njobs * 3.0;
-        *f = bfly_of(x.c, njobs);
-        return true;
-    });
-}
-
-void launch_ntt_multiswitch_many(const std::vector<NttSwitchArgs> &a)
-{
-    run_many<IOMultiSwitch>(a, true, FHE_K_NTT_MODSWITCH, [](IOMultiSwitch &io, int sg, const NttSwitchArgs &x,
-                                                             double *b, double *f) {
-        if (x.count <= 0 || x.k < 2 || x.k >= x.level) return false;
-        seg_header(io.h[sg], x.c, true, x.npoly * x.count, x.level - x.k);
-        MultiSeg &S = io.s[sg];
-        S.src = x.src;
-        S.in = x.in;
-        S.out = x.out;
-        S.P = x.c->d_mss + (size_t)x.level * (FHE_MAXK + 1) + x.k;
-        S.l = x.level;
-        S.k = x.k;
-        S.npoly = x.npoly;
-        // reads the k switch values and x_i, writes out_i
-        const double njobs = (double)x.npoly * (x.level - x.k) * x.count;
-        *b = 8.0 * x.c->N * njobs * (x.k + 2.0);
-        *f = bfly_of(x.c, njobs);
-        return true;
-    });
-}
-
 // ---------------------------------------------------------------------------
 // single-segment launchers
 // ---------------------------------------------------------------------------
@@ -1526,34 +75,6 @@ void launch_ntt_inv_scaled_y(fhe_ctx *c, const u64 *in, u64 *out, const LimbMap 
     y.amask = amask;
     y.level = level;
     launch_ntt_inv_scaled_y_many({y});
-}
-
-void launch_ntt_modup(fhe_ctx *c, const u64 *d2c, u64 *ext, int level, int count)
-{
-    launch_ntt_modup_many({NttModUpArgs{c, d2c, ext, level, count}});
-}
-
-void launch_ntt_moddown(fhe_ctx *c, const u64 *accP, const u64 *acc, const u64 *abase, long long a_outer,
-                        long long a_poly, int amask, u64 *out, int level, int count)
-{
-    launch_ntt_moddown_many({NttDownArgs{c, accP, acc, abase, a_outer, a_poly, amask, out, level, count}});
-}
-
-void launch_ntt_relin_ms(fhe_ctx *c, const u64 *src, const u64 *acc, const u64 *abase, long long a_outer,
-                         long long a_poly, int amask, u64 *out, int level, int count)
-{
-    launch_ntt_relin_ms_many({NttDownArgs{c, src, acc, abase, a_outer, a_poly, amask, out, level, count}});
-}
-
-void launch_ntt_multiswitch(fhe_ctx *c, const u64 *src, const u64 *in, u64 *out, int level, int k, int npoly,
-                            int count)
-{
-    launch_ntt_multiswitch_many({NttSwitchArgs{c, src, in, out, level, k, npoly, count}});
-}
-
-void launch_ntt_modswitch(fhe_ctx *c, const u64 *last, const u64 *in, u64 *out, int level, int npoly, int count)
-{
-    launch_ntt_modswitch_many({NttSwitchArgs{c, last, in, out, level, 1, npoly, count}});
 }
 
 // ---------------------------------------------------------------------------
