@@ -1,15 +1,21 @@
-"""Host check of the NTT kernels' thread schedules: the 8-elements-per-thread
-sub-transform schedule (autotuner variant 3: round A of 3 stages in
-registers; round B of 3 stages in registers and the rest across the lanes of
-a block, lanes h and h ^ delta) is emulated thread by thread with exact
-arithmetic mod a small prime and compared with the 16-elements-per-thread
-schedule it replaces, forward and inverse, for sub-transforms of 2^6 .. 2^8
-points; the cross-lane partners always share a warp."""
+"""Host check of the NTT engine's thread schedules and unit decompositions
+(emulated thread by thread in Python, exact arithmetic mod a small prime):
+
+- a unit of 128 threads x 16 residues holds NS = 2^(11-M) sub-transforms of
+  2^M points (M = 5..8); round 1 (threads t -> sub-transform t % NS, residues
+  k G + t / NS) and round 2 (t -> sub-transform t / G, blocks of G contiguous
+  residues) together compute, forward and inverse, the same as the plain
+  radix-2 stages of every sub-transform;
+- the column units of every ring degree 2^10..2^15 (NC columns of NJ jobs)
+  and the row units (grouped: one row of 16 jobs of a prime times R rows;
+  single: NS adjacent rows of one job) touch every residue of every job
+  exactly once, with ragged job counts."""
 import random
 
 import pytest
 
 q = 1000003  # a prime; the schedule check needs no lazy reduction
+T = 128
 
 
 def W(s, j):  # any deterministic twiddle function
@@ -45,107 +51,139 @@ def inv_round(x, R, s0, hi):
                 x[a], x[b] = gs(x[a], x[b], w)
 
 
-def sub16(sm, M, FWD, S, hi0, hstep):
-    """16 sub-transforms of 2^M points, 16 elements per thread (the kernels'
-    default schedule), every thread emulated in turn."""
-    SZ = 1 << M; G = SZ // 16; R2 = M - 4; NB = 16 // G; T = 16 * G
+def unit_schedule(sm, M, FWD, S, his):
+    """The engine's two rounds on NS sub-transforms (his[c]: block index of
+    sub-transform c), every thread of the 128 emulated in turn."""
+    SZ = 1 << M
+    G = SZ // 16
+    NS = T // G
+    R2 = M - 4
+    NB = 16 // G
+
     def round1():
         for tid in range(T):
-            c, g = tid & 15, tid >> 4
-            hi = hi0 + c * hstep
+            c, g = tid % NS, tid // NS
             x = [sm[c][k * G + g] for k in range(16)]
-            (fwd_round if FWD else inv_round)(x, 4, S, hi)
-            for k in range(16): sm[c][k * G + g] = x[k]
+            (fwd_round if FWD else inv_round)(x, 4, S, his[c])
+            for k in range(16):
+                sm[c][k * G + g] = x[k]
+
     def round2():
         for tid in range(T):
             c, gp = tid // G, tid % G
-            hi = hi0 + c * hstep
             for i in range(NB):
-                b = gp * NB + i
-                x = [sm[c][b * G + f] for f in range(1 << R2)]  # blocks of G contiguous
-                (fwd_round if FWD else inv_round)(x, R2, S + 4, hi * 16 + b)
-                for f in range(1 << R2): sm[c][b * G + f] = x[f]
-    if FWD: round1(); round2()
-    else: round2(); round1()
+                base = gp * 16 + i * G
+                x = [sm[c][base + f] for f in range(1 << R2)]
+                (fwd_round if FWD else inv_round)(x, R2, S + 4, his[c] * 16 + gp * NB + i)
+                for f in range(1 << R2):
+                    sm[c][base + f] = x[f]
+
+    if FWD:
+        round1()
+        round2()
+    else:
+        round2()
+        round1()
 
 
-def sub8(sm, M, FWD, S, hi0, hstep):
-    """The same with 8 elements per thread; cross-lane stages exchange whole
-    register arrays between lanes h and h ^ delta."""
-    SZ = 1 << M; G8 = SZ // 8; T = 16 * G8; R2 = M - 3; P = G8 // 8
-    def roundA():
-        for tid in range(T):
-            c, g = tid & 15, tid >> 4
-            hi = hi0 + c * hstep
-            x = [sm[c][k * G8 + g] for k in range(8)]
-            (fwd_round if FWD else inv_round)(x, 3, S, hi)
-            for k in range(8): sm[c][k * G8 + g] = x[k]
-    def roundB():
-        regs = {}
-        for tid in range(T):
-            c, gp = tid // G8, tid % G8
-            b, h = gp // P, gp % P
-            regs[tid] = [sm[c][b * G8 + h + j * P] for j in range(8)]
-        def inreg(tid):
-            c, gp = tid // G8, tid % G8
-            b = gp // P
-            hi = hi0 + c * hstep
-            (fwd_round if FWD else inv_round)(regs[tid], 3, S + 3, hi * 8 + b)
-        def cross(r):
-            # block-local stage r >= 3 at distance delta = P >> (r - 2) lanes
-            delta = P >> (r - 2)
-            new = {}
-            for tid in range(T):
-                c, gp = tid // G8, tid % G8
-                b, h = gp // P, gp % P
-                hi = hi0 + c * hstep
-                other = regs[tid ^ delta]  # lane partner
-                lower = (h & delta) == 0
-                out = []
-                for j in range(8):
-                    tg = j * (1 << (r - 3)) + (h * (1 << (r - 3))) // P
-                    w = W(S + 3 + r, ((hi * 8 + b) << r) + tg)
-                    mine, theirs = regs[tid][j], other[j]
-                    if FWD:
-                        x, y = (mine, theirs) if lower else (theirs, mine)
-                        X, Y = ct(x, y, w)
-                    else:
-                        x, y = (mine, theirs) if lower else (theirs, mine)
-                        X, Y = gs(x, y, w)
-                    out.append(X if lower else Y)
-                new[tid] = out
-            regs.update(new)
-        if FWD:
-            for tid in range(T): inreg(tid)
-            for r in range(3, R2): cross(r)
-        else:
-            for r in range(R2 - 1, 2, -1): cross(r)
-            for tid in range(T): inreg(tid)
-        for tid in range(T):
-            c, gp = tid // G8, tid % G8
-            b, h = gp // P, gp % P
-            for j in range(8): sm[c][b * G8 + h + j * P] = regs[tid][j]
-    if FWD: roundA(); roundB()
-    else: roundB(); roundA()
+def plain_subtransform(x, M, FWD, S, hi):
+    """The same stages on one sub-transform without any thread schedule."""
+    (fwd_round if FWD else inv_round)(x, M, S, hi)
 
 
-@pytest.mark.parametrize("M", [6, 7, 8])
+@pytest.mark.parametrize("M", [5, 6, 7, 8])
+@pytest.mark.parametrize("FWD", [True, False])
+def test_unit_rounds_equal_plain_stages(M, FWD):
+    SZ = 1 << M
+    NS = T // (SZ // 16)
+    assert NS * SZ == 16 * T
+    rnd = random.Random(M * 2 + FWD)
+    S = 3
+    his = [rnd.randrange(64) for _ in range(NS)]
+    sm = [[rnd.randrange(q) for _ in range(SZ)] for _ in range(NS)]
+    want = [list(r) for r in sm]
+    for c in range(NS):
+        plain_subtransform(want[c], M, FWD, S, his[c])
+    unit_schedule(sm, M, FWD, S, his)
+    assert sm == want
 
 
-def test_sub8_schedule_equals_sub16(M):
-    for FWD in (True, False):
-        for trial in range(3):
-            rnd = random.Random(M * 10 + trial + FWD)
-            base = [[rnd.randrange(q) for _ in range(1 << M)] for _ in range(16)]
-            S, hi0, hstep = rnd.choice([(0, 0, 0), (7, 5, 1), (6, 3, 0)])
-            a = [row[:] for row in base]
-            b = [row[:] for row in base]
-            sub16(a, M, FWD, S, hi0, hstep)
-            sub8(b, M, FWD, S, hi0, hstep)
-            assert a == b, (M, FWD, trial)
-    G8 = (1 << M) // 8
-    P = G8 // 8
-    for tid in range(16 * G8):
-        for r in range(3, M - 3):
-            d = P >> (r - 2)
-            assert (tid ^ d) // 32 == tid // 32
+def split(logN):
+    n1, n2 = (logN + 1) // 2, logN // 2
+    return n1, n2, 2048 >> n1, 2048 >> n2
+
+
+@pytest.mark.parametrize("logN", [10, 11, 12, 13, 14, 15])
+@pytest.mark.parametrize("njobs", [1, 3, 16, 37])
+def test_column_units_cover_every_residue_once(logN, njobs):
+    n1, n2, ns1, _ = split(logN)
+    NC = min(ns1, 1 << n2)
+    NJ = ns1 // NC
+    BLK = (1 << n2) // NC
+    SZ = 1 << n1
+    units = ((njobs + NJ - 1) // NJ) * BLK
+    seen = {}
+    for lu in range(units):
+        job0, lo0 = (lu // BLK) * NJ, (lu % BLK) * NC
+        for r in range(16 * T):  # word r of the unit: job slot, column, element
+            j = 0 if NJ == 1 else r // (NC * SZ)
+            col, e = r % NC, (r % (NC * SZ)) // NC
+            assert 0 <= e < SZ
+            if job0 + j >= njobs:
+                continue
+            key = (job0 + j, (e << n2) + lo0 + col)
+            seen[key] = seen.get(key, 0) + 1
+    assert len(seen) == njobs << logN and set(seen.values()) == {1}
+
+
+@pytest.mark.parametrize("logN", [10, 11, 12, 13, 14, 15])
+@pytest.mark.parametrize("outer,nl", [(1, 3), (5, 2), (16, 3), (21, 2), (40, 1)])
+def test_row_units_cover_every_residue_once(logN, outer, nl):
+    n1, n2, _, ns2 = split(logN)
+    SZ = 1 << n2
+    grouped = outer >= 12 or (1 << n1) < ns2
+    seen = {}
+    if grouped:
+        R = ns2 // 16
+        CH = (1 << n1) // R
+        OC = (outer + 15) // 16
+        units = nl * OC * CH
+        for lu in range(units):
+            hc, t = lu % CH, lu // CH
+            oc, l = t % OC, t // OC
+            hi0 = hc * R
+            nvalid = min(16, outer - oc * 16)
+            for r in range(16 * T):
+                c, f = r >> n2, r & (SZ - 1)
+                slot, row = c // R, hi0 + c % R
+                if slot >= nvalid:
+                    continue
+                job = (oc * 16 + slot) * nl + l
+                key = (job, (row << n2) + f)
+                seen[key] = seen.get(key, 0) + 1
+    else:
+        CHS = (1 << n1) // ns2
+        units = outer * nl * CHS
+        for lu in range(units):
+            hi0, job = (lu % CHS) * ns2, lu // CHS
+            for r in range(16 * T):
+                c, f = r >> n2, r & (SZ - 1)
+                key = (job, ((hi0 + c) << n2) + f)
+                seen[key] = seen.get(key, 0) + 1
+    assert len(seen) == (outer * nl) << logN and set(seen.values()) == {1}
+
+
+def test_grouped_rows_share_a_prime():
+    """A grouped row unit's 16 jobs differ only in the outer index, so they
+    share the limb index l and hence the prime."""
+    for logN in (13, 14, 15):
+        n1, n2, _, ns2 = split(logN)
+        R = ns2 // 16
+        outer, nl = 33, 4
+        OC = (outer + 15) // 16
+        CH = (1 << n1) // R
+        for lu in range(nl * OC * CH):
+            t = lu // CH
+            oc, l = t % OC, t // OC
+            jobs = [(oc * 16 + s) * nl + l for s in range(min(16, outer - oc * 16))]
+            assert {j % nl for j in jobs} == {l}
