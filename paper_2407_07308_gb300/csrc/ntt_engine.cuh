@@ -131,9 +131,20 @@ __device__ __forceinline__ void inv_round(u64 (&x)[1 << R], int s0, int hi, cons
 
 constexpr int T = 128;  // threads per CTA, 16 residues each
 
-// Register cap: 6 resident CTAs (768 threads) per SM, 85 registers a thread.
+// Register cap: FHE_NTT_MINB resident CTAs of 128 threads per SM (8: 64
+// registers a thread).  Measured on the headline comparison (16 pairs,
+// N = 2^14): 8 CTAs 2291 slot-comparisons/s, 6 CTAs (80 registers) 2285, 7
+// with staged multi-limb loads 2152.
 #ifndef FHE_NTT_MINB
-#define FHE_NTT_MINB 6
+#define FHE_NTT_MINB 8
+#endif
+// Words staged per chunk by the loads that read several limbs each (ModUp,
+// relinearise + switch, multi-prime switch); 0 = not staged (each word's
+// loads, arithmetic and shared-memory store in turn, four words unrolled).
+// Measured: staging 2 or 4 words costs 4-5% on the headline (2190 / 2225
+// against 2291 slot-comparisons/s).
+#ifndef FHE_NTT_MULTI_LDCH
+#define FHE_NTT_MULTI_LDCH 0
 #endif
 
 // Shared-memory twiddle tables: entry k at k + k / 8 (one 16-byte pad per 8
@@ -972,7 +983,7 @@ struct IOModUp : SegIO<ModUpSeg> {
     }
     __device__ void store(const St &t, int k, u64 v) const { t.dst[k] = v; }
     static constexpr int NPRE = 0;
-    static constexpr int LDCH = 4;  // loads staged 4 words at a time (each reads several limbs)
+    static constexpr int LDCH = FHE_NTT_MULTI_LDCH;  // each load reads several limbs
     __device__ u64 pre(const St &, int, int) const { return 0; }
     __device__ void store_pre(const St &t, int k, u64 v, const u64 *) const { t.dst[k] = v; }
     __device__ u64 *inter(const St &t) const { return t.dst; }
@@ -1165,7 +1176,7 @@ struct IORelinMS : SegIO<RelinMSSeg> {
     }
     __device__ void store(const St &t, int k, u64 v) const { t.out[k] = combine(t, t.acc[k], t.add ? t.add[k] : 0, v); }
     static constexpr int NPRE = 2;  // accumulator, addend
-    static constexpr int LDCH = 4;  // staged 4 words at a time (each load sums K + 1 limbs)
+    static constexpr int LDCH = FHE_NTT_MULTI_LDCH;  // each load reads several limbs
     __device__ u64 pre(const St &t, int k, int w) const { return w == 0 ? t.acc[k] : (t.add ? t.add[k] : 0); }
     __device__ void store_pre(const St &t, int k, u64 v, const u64 *pv) const { t.out[k] = combine(t, pv[0], pv[1], v); }
     __device__ u64 *inter(const St &t) const { return t.out; }
@@ -1224,7 +1235,7 @@ struct IOMultiSwitch : SegIO<MultiSeg> {
         t.out[j] = shoup(submod(t.in[j], v, t.mi.q), t.dinv, t.dinv_s, t.mi.q);
     }
     static constexpr int NPRE = 1;
-    static constexpr int LDCH = 4;  // staged 4 words at a time (each load sums k limbs)
+    static constexpr int LDCH = FHE_NTT_MULTI_LDCH;  // each load reads several limbs
     __device__ u64 pre(const St &t, int j, int) const { return t.in[j]; }
     __device__ void store_pre(const St &t, int j, u64 v, const u64 *pv) const
     {
