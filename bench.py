@@ -485,10 +485,39 @@ def run_gpu(args):
     fhe.fhe_sk_destroy(sk)
     fhe.fhe_pk_destroy(pk)
     fhe.fhe_ctx_destroy(ctx)
+    if rank == 0 and world == 1 and args.workload == "compare" and not args.no_secondary:
+        line["secondary"] = run_secondary(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_secondary(args):
+    """Short runs of the uneven batch (fused form only) and of the serving
+    loop, each in a child process after the headline has released its
+    contexts, so that their rates are recorded beside the headline."""
+    import torch
+
+    torch.cuda.empty_cache()  # the children allocate on the same device
+    out = {}
+    for name, extra in (("uneven", ["--workload", "uneven", "--quick", "--steps", "2", "--warmup", "3", "--no-plain"]),
+                        ("serve", ["--workload", "serve", "--serve-requests", "24", "--warmup", "3"])):
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--no-secondary"] + extra
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+            lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+            d = json.loads(lines[-1]) if r.returncode == 0 and lines else None
+        except (subprocess.TimeoutExpired, ValueError):
+            d = None
+        if d is None:
+            out[name] = {"error": "the child run failed"}
+            continue
+        keep = ("metric", "value", "unit", "ms_per_step", "launches_per_step", "latency_ms_p50", "latency_ms_p99",
+                "requests_per_s", "latency_ms_by_kind", "clocks")
+        out[name] = {k: d[k] for k in keep if k in d}
+        out[name]["workload"] = d["config"]["workload"]
+    return out
 
 
 def run_plain(fhe, ctx, evk, xd, yd, enc_each, pairs, ns, stream, ev):
@@ -707,16 +736,18 @@ def run_uneven(args):
     # same-level groups only (no alignment), the aligned form per context,
     # then the fused form (the value): the contexts of one plaintext prime in
     # one circuit, every step one launch across ring degrees and levels
-    batched_step(check=True, flags=0)
-    for _ in range(args.warmup - 1):
-        batched_step(flags=0)
-    unaligned = [batched_step(flags=0)[0] for _ in range(args.steps)]
-    batched_step(check=True)
-    for _ in range(args.warmup - 1):
-        batched_step()
-    l0 = cs.launches()
-    aligned = [batched_step()[0] for _ in range(args.steps)]
-    aligned_launches = (cs.launches() - l0) / args.steps
+    unaligned = aligned = None
+    if not args.quick:
+        batched_step(check=True, flags=0)
+        for _ in range(args.warmup - 1):
+            batched_step(flags=0)
+        unaligned = [batched_step(flags=0)[0] for _ in range(args.steps)]
+        batched_step(check=True)
+        for _ in range(args.warmup - 1):
+            batched_step()
+        l0 = cs.launches()
+        aligned = [batched_step()[0] for _ in range(args.steps)]
+        aligned_launches = (cs.launches() - l0) / args.steps
     fused = fhe.FHE_BATCH_ALIGN_LEVELS | fhe.FHE_BATCH_FUSE_RINGS
     batched_step(check=True, flags=fused)
     for _ in range(args.warmup - 1):
@@ -764,13 +795,13 @@ def run_uneven(args):
                    "plain_form": "one request at a time through fhe_compare, synchronised",
                    "l2": "inputs and intermediates of every step exceed L2"},
         "plain": plain, "enqueue_ms_p50": round(1e3 * sorted(t for _, t in times)[len(times) // 2], 1),
-        "batched_same_level_groups": {"value": round(slot_cmps * args.steps / sum(unaligned), 2), "unit": UNIT,
-                                      "ms_per_step": round(1e3 * sum(unaligned) / args.steps, 1)},
-        "batched_aligned_per_context": {"value": round(slot_cmps * args.steps / sum(aligned), 2), "unit": UNIT,
-                                        "ms_per_step": round(1e3 * sum(aligned) / args.steps, 1),
-                                        "launches_per_step": round(aligned_launches, 1),
-                                        "form": "FHE_BATCH_ALIGN_LEVELS only: one circuit per context, recurring "
-                                                "shapes replayed as graphs"},
+        "batched_same_level_groups": None if unaligned is None else {
+            "value": round(slot_cmps * args.steps / sum(unaligned), 2), "unit": UNIT,
+            "ms_per_step": round(1e3 * sum(unaligned) / args.steps, 1)},
+        "batched_aligned_per_context": None if aligned is None else {
+            "value": round(slot_cmps * args.steps / sum(aligned), 2), "unit": UNIT,
+            "ms_per_step": round(1e3 * sum(aligned) / args.steps, 1), "launches_per_step": round(aligned_launches, 1),
+            "form": "FHE_BATCH_ALIGN_LEVELS only: one circuit per context, recurring shapes replayed as graphs"},
         "launches_per_step": round(launches / args.steps, 1),
         "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": None, "roofline": None,
     }
@@ -806,7 +837,7 @@ def run_serve(args):
                   sort_keys=True)
     d = S["d"]
     reqs = []
-    for i in range(S["requests"]):
+    for i in range(args.serve_requests or S["requests"]):
         u = g.random()
         kind = fhe.FHE_JOB_SORT if u < 0.25 else fhe.FHE_JOB_MAXMIN if u < 0.5 else fhe.FHE_JOB_COMPARE
         logN = int(g.choice(S["logNs"]))
@@ -832,7 +863,8 @@ def run_serve(args):
     cs.sync()
     rate = args.serve_rate
     due = np.cumsum(g.exponential(1.0 / rate, size=len(reqs)))
-    srv = fhe.fhe_server_start(hbm_budget=int(S["budget"]), batch_flags=fhe.FHE_BATCH_ALIGN_LEVELS)
+    srv = fhe.fhe_server_start(hbm_budget=int(S["budget"]),
+                               batch_flags=fhe.FHE_BATCH_ALIGN_LEVELS | fhe.FHE_BATCH_FUSE_RINGS)
     l0 = cs.launches()
     errors = []
 
@@ -919,6 +951,14 @@ def run_serve(args):
                 fhe.fhe_ct_destroy(h)
     lat = sorted(r["t_fin"] - r["t_sub"] for r in reqs)
     slots = sum(r["slots"] for r in reqs)
+
+    def p(v, q):
+        return round(v[min(len(v) - 1, int(q * (len(v) - 1) + 0.5))], 1) if v else None
+
+    by_kind = {}
+    for name, kv in (("compare", fhe.FHE_JOB_COMPARE), ("maxmin", fhe.FHE_JOB_MAXMIN), ("sort", fhe.FHE_JOB_SORT)):
+        v = sorted(r["t_fin"] - r["t_sub"] for r in reqs if r["kind"] == kv)
+        by_kind[name] = {"p50": p(v, 0.5), "p99": p(v, 0.99), "n": len(v)}
     line = {
         "metric": "served encrypted slot-comparisons/sec under Poisson arrivals; p50/p99 request ms",
         "value": round(slots / wall, 2), "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
@@ -929,7 +969,7 @@ def run_serve(args):
                                f"d=2, 1/2 LT+EQ, 1/4 max/min, 1/4 row sorts (p in {{17,257}}; a sorted ciphertext "
                                f"counts n_s (n_s/2 - 1) slot-comparisons), 20x50-bit + 4 special primes, start level "
                                f"= lowest decryptable level, client chunks of <= {S['chunk']} ciphertexts, operands "
-                               f"encrypted on arrival, batches level-aligned", "hbm_budget_gb": S["budget"] / 1e9,
+                               f"encrypted on arrival, batches level-aligned and ring-fused", "hbm_budget_gb": S["budget"] / 1e9,
                    "arrival_rate_per_s": rate, "requests_by_kind": {
                        k: sum(1 for r in reqs if r["kind"] == v) for k, v in
                        (("compare", fhe.FHE_JOB_COMPARE), ("maxmin", fhe.FHE_JOB_MAXMIN),
@@ -937,6 +977,7 @@ def run_serve(args):
         "requests_per_s": round(len(reqs) / wall, 3),
         "latency_ms_p50": round(lat[len(lat) // 2], 1),
         "latency_ms_p99": round(lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))], 1),
+        "latency_ms_by_kind": by_kind,
         "server": {"batches": st.batches, "admitted_peak_gb": round(st.admitted_peak_bytes / 1e9, 2),
                    "completed_jobs": st.completed},
         "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": None, "roofline": None, "e2e": None,
@@ -1585,6 +1626,10 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate (requests/s) for serve")
     ap.add_argument("--digits", type=int, default=2, choices=[2, 3],
                     help="tournament digits: 2 (values below 129^2) or 3 (the 16-bit range)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="compare: skip the short uneven and serving runs recorded beside the headline")
+    ap.add_argument("--quick", action="store_true", help="uneven: the fused batched form only")
+    ap.add_argument("--serve-requests", type=int, default=0, help="serve: number of requests (0 = the workload's 48)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
