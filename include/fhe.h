@@ -485,8 +485,12 @@ int fhe_batch_submit(const fhe_job *jobs, int n, fhe_batch **out);
  * one circuit, whose every step is one kernel launch over all their groups:
  * ring degrees, digit counts and levels mixed in one launch (the first such
  * context's stream carries the work; the others' streams wait for it).
- * Their submissions run directly, without batch graphs.  Results are those
- * of each job alone. */
+ * A submission shape such a family has served before is captured (once)
+ * into one CUDA graph for the family and replayed (up to 4 graphs per family;
+ * they hold memory in every member's pool and are dropped when a member
+ * context is destroyed -- do not destroy a context while another thread
+ * submits a fused batch that involves it).  Results are those of each job
+ * alone. */
 enum { FHE_BATCH_ALIGN_LEVELS = 1, FHE_BATCH_FUSE_RINGS = 2 };
 int fhe_batch_submit_ex(const fhe_job *jobs, int n, int flags, fhe_batch **out);
 /* Graph capture of recurring submissions: the second time a context receives

@@ -384,6 +384,7 @@ extern "C" void fhe_ctx_destroy(fhe_ctx *c)
     register_ctx(c, false);
     cudaStreamSynchronize(c->stream);
     batch_plans_release(c);
+    batch_family_release(c);
     c->pool.release_all();
     cudaFree(c->d_mq);
     cudaFree(c->d_fwd);

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <chrono>
 #include <map>
+#include <mutex>
 #include <thread>
 #include <tuple>
 
@@ -197,8 +198,20 @@ void plan_free(fhe_ctx *c, BatchPlan *P)
             for (fhe_ct *x : g) fhe_ct_destroy(x);
     for (auto &kv : P->held)
         for (void *p : kv.second) c->pool.put(p);
+    for (auto &m : P->mheld)
+        for (auto &kv : m.second)
+            for (void *p : kv.second) m.first->pool.put(p);
     delete P;
 }
+
+// Fused-ring plans (batch graphs of several contexts of one plaintext
+// prime), kept across calls like a context's own plans; released with any
+// member context (and when memory runs out).
+std::recursive_mutex g_fam_mu;
+std::vector<BatchPlan *> g_fam_plans;
+std::map<std::vector<u64>, int> g_fam_seen;
+u64 g_fam_clock = 0;
+constexpr int FAM_PLAN_CAP = 4;
 
 // Captures the circuit of these groups into a new plan (nothing runs).
 int capture(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups, const std::vector<u64> &sig, BatchPlan **out)
@@ -376,14 +389,161 @@ int run_direct(fhe_ctx *c, const fhe_job *jobs, GroupMap &groups)
     return scatter_groups(c, jobs, groups, err);
 }
 
+// The items of a family's groups (family order), with the keys of each; the
+// item of the first member that has one leads the circuit (items[0]).
+void family_items(const std::vector<fhe_ctx *> &fam, const fhe_job *jobs, std::vector<GroupMap> &gm,
+                  std::vector<std::vector<fhe_ct *>> *X, std::vector<std::vector<fhe_ct *>> *Y,
+                  std::vector<std::vector<fhe_ct *>> *O0, std::vector<std::vector<fhe_ct *>> *O1,
+                  std::vector<const fhe_evk *> &evks, std::vector<MultiItem> &items)
+{
+    size_t gi = 0;
+    for (size_t i = 0; i < fam.size(); i++)
+        for (auto &kv : gm[i]) {
+            Group &g = kv.second;
+            auto it = X ? items_for(g, jobs[g.jobs[0]], (*X)[gi], (*Y)[gi], (*O0)[gi], (*O1)[gi])
+                        : items_for(g, jobs[g.jobs[0]], g.X, g.Y, g.out0, g.out1);
+            items.push_back(it[0]);
+            evks.push_back(g.evk);
+            gi++;
+        }
+}
+
+// shape of a family's submission: the members and each one's group shapes
+std::vector<u64> family_signature(const std::vector<fhe_ctx *> &fam, const fhe_job *jobs,
+                                  const std::vector<GroupMap> &gm)
+{
+    std::vector<u64> sig;
+    for (size_t i = 0; i < fam.size(); i++) {
+        const std::vector<u64> s = signature(jobs, gm[i]);
+        sig.push_back((u64)(uintptr_t)fam[i]);
+        sig.push_back(s.size());
+        sig.insert(sig.end(), s.begin(), s.end());
+    }
+    return sig;
+}
+
+// Captures a family's circuit into a new plan (nothing runs): operand and
+// result buffers per group in each member's pool; every member's pool keeps
+// what the capture frees (the plan reuses it on every replay).  The members'
+// streams are the leader's (run_family).
+int capture_family(const std::vector<fhe_ctx *> &fam, const fhe_job *jobs, std::vector<GroupMap> &gm,
+                   const std::vector<u64> &sig, BatchPlan **out)
+{
+    fhe_ctx *lead = fam[0];
+    BatchPlan *P = new BatchPlan;
+    P->sig = sig;
+    P->members = fam;
+    int err = 0;
+    for (size_t i = 0; i < fam.size() && !err; i++)
+        for (auto &kv : gm[i]) {
+            Group &g = kv.second;
+            int cnt = 0;
+            for (int id : g.jobs) cnt += jobs[id].x[0]->count;
+            P->X.emplace_back();
+            P->Y.emplace_back();
+            P->O0.emplace_back();
+            P->O1.emplace_back();
+            for (int k = 0; k < g.d && !err; k++) {
+                fhe_ct *a = ct_new(fam[i], cnt, 2, g.level, &err);
+                fhe_ct *b = a ? ct_new(fam[i], cnt, 2, g.level, &err) : nullptr;
+                P->X.back().push_back(a);
+                P->Y.back().push_back(b);
+            }
+        }
+    std::vector<const fhe_evk *> evks;
+    std::vector<MultiItem> items;
+    if (!err) family_items(fam, jobs, gm, &P->X, &P->Y, &P->O0, &P->O1, evks, items);
+    cudaStream_t user = lead->stream, cap = nullptr;
+    if (!err) err = fhe_cuda_check(lead, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+    if (!err) {
+        std::vector<bool> prof;
+        for (fhe_ctx *m : fam) {
+            prof.push_back(m->prof_on);
+            m->prof_on = false;
+            m->pool.cap_free = &P->mheld[m];
+            m->pool.in_capture = true;
+            m->stream = cap;
+            m->pool.stream = cap;
+            m->capturing = true;
+        }
+        err = fhe_cuda_check(lead, cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed), "begin capture");
+        if (!err) {
+            err = circuit_multi_ctx(evks, items);
+            cudaGraph_t gr = nullptr;
+            const int e2 = fhe_cuda_check(lead, cudaStreamEndCapture(cap, &gr), "end capture");
+            if (!err) err = e2;
+            P->graph = gr;
+        }
+        for (size_t i = 0; i < fam.size(); i++) {
+            fhe_ctx *m = fam[i];
+            m->capturing = false;
+            m->stream = user;
+            m->pool.stream = user;
+            m->pool.cap_free = nullptr;
+            m->pool.in_capture = false;
+            m->prof_on = prof[i];
+        }
+        cudaStreamDestroy(cap);
+    }
+    if (!err) err = fhe_cuda_check(lead, cudaGraphInstantiate(&P->exec, P->graph, 0), "graph instantiate");
+    if (!err) {
+        size_t n = 0;
+        cudaGraphGetNodes(P->graph, nullptr, &n);
+        P->nodes = (int)n;
+    }
+    if (err) {
+        plan_free(lead, P);
+        return err;
+    }
+    *out = P;
+    return 0;
+}
+
+// operands in, one graph launch on the leader's stream, results sliced out
+int replay_family(const std::vector<fhe_ctx *> &fam, const fhe_job *jobs, std::vector<GroupMap> &gm, BatchPlan *P)
+{
+    for (fhe_ctx *m : fam) m->bplan_active = P;  // kept if memory runs out meanwhile
+    size_t gi = 0;
+    for (size_t i = 0; i < fam.size(); i++)
+        for (auto &kv : gm[i]) {
+            const Group &g = kv.second;
+            for (int k = 0; k < g.d; k++) {
+                fill(fam[i], jobs, g, k, false, P->X[gi][k]);
+                fill(fam[i], jobs, g, k, true, P->Y[gi][k]);
+            }
+            gi++;
+        }
+    int err = fhe_cuda_check(fam[0], cudaGraphLaunch(P->exec, fam[0]->stream), "fused batch graph launch");
+    fam[0]->launches += P->nodes;
+    P->last = ++g_fam_clock;
+    gi = 0;
+    for (size_t i = 0; i < fam.size(); i++)
+        for (auto &kv : gm[i]) {
+            if (!err) err = scatter(fam[i], jobs, kv.second, P->O0[gi], P->O1[gi], false);
+            gi++;
+        }
+    for (fhe_ctx *m : fam) m->bplan_active = nullptr;
+    return err;
+}
+
 // The compare and max/min jobs of contexts that share a device and a
 // plaintext prime, in one circuit (fused launches across ring degrees,
 // digit counts and levels); their sort jobs afterwards, per context.  Every
 // member context works on the leader's stream meanwhile: the leader first
 // waits for what the others have queued, and they wait for the leader at
-// the end.  The caller holds every member's lock.
-int run_family(const std::vector<fhe_ctx *> &fam, const fhe_job *jobs, std::map<fhe_ctx *, std::vector<int>> &by_ctx)
+// the end.  A submission shape the family has served before is captured
+// (once) into a graph and replayed.  The caller holds every member's lock.
+int run_family(const std::vector<fhe_ctx *> &fam_in, const fhe_job *jobs,
+               std::map<fhe_ctx *, std::vector<int>> &by_ctx)
 {
+    // members with compare jobs first (the first of them leads the circuit)
+    std::vector<fhe_ctx *> fam;
+    for (int pass = 0; pass < 2; pass++)
+        for (fhe_ctx *m : fam_in) {
+            bool cmp = false;
+            for (int id : by_ctx[m]) cmp = cmp || jobs[id].kind != FHE_JOB_SORT;
+            if (cmp == (pass == 0)) fam.push_back(m);
+        }
     fhe_ctx *lead = fam[0];
     const cudaStream_t ls = lead->stream;
     std::vector<cudaStream_t> saved;
@@ -405,41 +565,66 @@ int run_family(const std::vector<fhe_ctx *> &fam, const fhe_job *jobs, std::map<
     }
     std::vector<GroupMap> gm(fam.size());
     std::vector<GroupMap> sorts(fam.size());
-    std::vector<const fhe_evk *> evks;
-    std::vector<MultiItem> items;
-    for (size_t i = 0; i < fam.size() && !err; i++) {
+    bool any = false;
+    for (size_t i = 0; i < fam.size(); i++) {
         std::vector<int> cmp, srt;
         for (int id : by_ctx[fam[i]]) (jobs[id].kind == FHE_JOB_SORT ? srt : cmp).push_back(id);
         gm[i] = make_groups(jobs, cmp);
         sorts[i] = make_groups(jobs, srt);
-        err = gather_groups(fam[i], jobs, gm[i]);
-        for (auto &kv : gm[i]) {
-            Group &g = kv.second;
-            auto it = items_for(g, jobs[g.jobs[0]], g.X, g.Y, g.out0, g.out1);
-            items.push_back(it[0]);
-            evks.push_back(g.evk);
-        }
+        any = any || !cmp.empty();
     }
-    if (!err && !items.empty()) {
-        // the leader's keys first (it leads the circuit)
-        for (size_t i = 0; i < evks.size(); i++)
-            if (evks[i]->ctx == lead) {
-                std::swap(evks[0], evks[i]);
-                std::swap(items[0], items[i]);
-                break;
+    bool done = false;
+    if (!err && any && lead->bplan_cap > 0) {
+        std::lock_guard<std::recursive_mutex> g(g_fam_mu);
+        const std::vector<u64> sig = family_signature(fam, jobs, gm);
+        BatchPlan *P = nullptr;
+        for (BatchPlan *Q : g_fam_plans)
+            if (Q->sig == sig) P = Q;
+        if (!P && g_fam_seen[sig]++ > 0) {
+            // evict the least recently used plan of this family's members
+            // (their locks are held here) once the family has FAM_PLAN_CAP
+            std::vector<size_t> mine;
+            for (size_t q = 0; q < g_fam_plans.size(); q++) {
+                bool ours = true;
+                for (fhe_ctx *m : g_fam_plans[q]->members)
+                    ours = ours && std::find(fam.begin(), fam.end(), m) != fam.end();
+                if (ours) mine.push_back(q);
             }
-        if (evks[0]->ctx != lead) lead = evks[0]->ctx;  // the leader has no compare job: another member leads
-        const bool ms = lead->multistream;
-        lead->multistream = true;
-        err = circuit_multi_ctx(evks, items);
-        lead->multistream = ms;
+            if ((int)mine.size() >= FAM_PLAN_CAP) {
+                size_t lru = mine[0];
+                for (size_t q : mine)
+                    if (g_fam_plans[q]->last < g_fam_plans[lru]->last) lru = q;
+                cudaDeviceSynchronize();
+                plan_free(lead, g_fam_plans[lru]);
+                g_fam_plans.erase(g_fam_plans.begin() + lru);
+            }
+            err = capture_family(fam, jobs, gm, sig, &P);
+            if (!err) g_fam_plans.push_back(P);
+        }
+        if (!err && P) {
+            err = replay_family(fam, jobs, gm, P);
+            done = true;
+        }
+        if (g_fam_seen.size() > 1024) g_fam_seen.clear();
     }
-    for (size_t i = 0; i < fam.size(); i++) err = scatter_groups(fam[i], jobs, gm[i], err);
+    if (!err && any && !done) {
+        std::vector<const fhe_evk *> evks;
+        std::vector<MultiItem> items;
+        for (size_t i = 0; i < fam.size() && !err; i++) err = gather_groups(fam[i], jobs, gm[i]);
+        if (!err) family_items(fam, jobs, gm, nullptr, nullptr, nullptr, nullptr, evks, items);
+        if (!err) {
+            const bool ms = lead->multistream;
+            lead->multistream = true;
+            err = circuit_multi_ctx(evks, items);
+            lead->multistream = ms;
+        }
+        for (size_t i = 0; i < fam.size(); i++) err = scatter_groups(fam[i], jobs, gm[i], err);
+    }
     for (size_t i = 0; i < fam.size() && !err; i++)
         if (!sorts[i].empty()) err = run_direct(fam[i], jobs, sorts[i]);
     for (size_t i = 0; i < fam.size(); i++) {
         fhe_ctx *m = fam[i];
-        if (m == fam[0]) continue;
+        if (m == lead) continue;
         m->stream = saved[i];
         m->pool.stream = saved[i];
         const int e = follow(m->stream, ls);
@@ -491,6 +676,27 @@ void batch_plans_release(fhe_ctx *c, const BatchPlan *keep)
     if (!keep) c->bseen.clear();
 }
 
+// Fused-ring plans that hold memory of c (a context being destroyed): they
+// may run on another member's stream, so the whole device is drained first.
+// They are freed only here and by run_family (which holds every member's
+// lock): the memory-pressure paths leave them alone, since another thread may
+// hold the other members.
+void batch_family_release(fhe_ctx *c)
+{
+    std::lock_guard<std::recursive_mutex> g(g_fam_mu);
+    bool synced = false;
+    for (size_t i = 0; i < g_fam_plans.size();) {
+        BatchPlan *P = g_fam_plans[i];
+        if (std::find(P->members.begin(), P->members.end(), c) == P->members.end()) {
+            i++;
+            continue;
+        }
+        if (!synced) cudaDeviceSynchronize(), synced = true;
+        plan_free(c, P);
+        g_fam_plans.erase(g_fam_plans.begin() + i);
+    }
+}
+
 extern "C" int fhe_ctx_set_batch_graphs(fhe_ctx *c, int max_plans)
 {
     if (!c || max_plans < 0) return FHE_EINVAL;
@@ -529,6 +735,14 @@ int align_levels(const fhe_job *jobs, int n, Aligned &A)
     }
     A.jobs.assign(jobs, jobs + n);
     A.ops.resize(n);
+    // every operand above its target, per context: switched down in merged
+    // rounds (at most FHE_MAXK primes a step, one launch per step for all)
+    struct Want {
+        const fhe_ct **slot;
+        const fhe_ct *cur;
+        int target;
+    };
+    std::map<fhe_ctx *, std::vector<Want>> want;
     for (int i = 0; i < n; i++) {
         fhe_job &j = A.jobs[i];
         const int target =
@@ -538,22 +752,32 @@ int align_levels(const fhe_job *jobs, int n, Aligned &A)
         const int nops = j.kind == FHE_JOB_SORT ? j.d : 2 * j.d;
         for (int k = 0; k < nops; k++) {
             const fhe_ct *src = k < j.d ? j.x[k] : j.y[k - j.d];
-            if (src->level == target) {
-                ops[k] = src;
-                continue;
-            }
-            fhe_ct *r = nullptr;
-            int e;
-            {
-                std::lock_guard<std::mutex> g(j.ctx->mu);
-                e = op_lower(j.ctx, src, target, &r);
-            }
-            if (e) return e;
-            A.owned.push_back(r);
-            ops[k] = r;
+            ops[k] = src;
+            if (src->level > target) want[j.ctx].push_back(Want{&ops[k], src, target});
         }
         j.x = ops.data();
         j.y = ops.data() + j.d;
+    }
+    for (auto &kv : want) {
+        fhe_ctx *c = kv.first;
+        std::lock_guard<std::mutex> g(c->mu);
+        for (;;) {
+            std::vector<SwitchItem> items;
+            std::vector<Want *> who;
+            for (Want &w : kv.second)
+                if (w.cur->level > w.target) {
+                    items.push_back(SwitchItem{c, w.cur, std::min(w.cur->level - w.target, FHE_MAXK), nullptr});
+                    who.push_back(&w);
+                }
+            if (items.empty()) break;
+            const int e = op_modswitch_many(items);
+            if (e) return e;
+            for (size_t t = 0; t < items.size(); t++) {
+                A.owned.push_back(items[t].out);
+                who[t]->cur = items[t].out;
+                *who[t]->slot = items[t].out;
+            }
+        }
     }
     return 0;
 }

@@ -278,8 +278,13 @@ struct BatchPlan {
     cudaGraphExec_t exec = nullptr;
     int nodes = 0;
     u64 last = 0;
+    // a fused-ring plan (several contexts of one plaintext prime in one
+    // graph): its member contexts and the temporaries it holds in each pool
+    std::vector<fhe_ctx *> members;
+    std::map<fhe_ctx *, std::unordered_map<size_t, std::vector<void *>>> mheld;
 };
 void batch_plans_release(fhe_ctx *c, const BatchPlan *keep = nullptr);
+void batch_family_release(fhe_ctx *c);  // fused-ring graphs holding memory of c (context destruction)
 
 struct fhe_plan {
     fhe_ctx *ctx;

@@ -336,7 +336,9 @@ def test_fused_rings_mixed_degrees_match_alone_and_oracle():
     plaintext prime (N = 2^13, 2^14, 2^15; digit counts 1 and 2; start levels
     8, 7 and 6) in one submission, whose circuit runs every step as one launch
     over all ring degrees: each result equals the job alone, and ciphertext 0
-    of one compare job per ring degree equals the CPU oracle limb for limb."""
+    of one compare job per ring degree equals the CPU oracle limb for limb;
+    the same shape submitted again is captured into one graph for the three
+    contexts and replayed with identical bits."""
     from paper_2407_07308_gb300 import fhe
     from tests.gpu_setup import GpuSetup
     from tests.oracle_setup import compare_many
@@ -372,7 +374,22 @@ def test_fused_rings_mixed_degrees_match_alone_and_oracle():
                                         level if level < L else None)))
         batch = fhe.fhe_batch_submit(jobs, fhe.FHE_BATCH_FUSE_RINGS)
         assert fhe.fhe_batch_wait(batch, 300000) == 0
+        for i in range(len(jobs)):
+            assert fhe.fhe_batch_job_done(batch, i)
         fhe.fhe_batch_destroy(batch)
+        # the same shape twice more: captured into one graph for the three
+        # contexts, then replayed; identical bits every time
+        first = [[m[0].export(h) for h in (job.out0 or []) + (job.out1 or []) if h] for job, m in zip(jobs, meta)]
+        for rep in range(2):
+            again = [fhe.Job(m[0].ctx, m[0].evk, m[1], m[2], m[3]) for m in meta]
+            bt = fhe.fhe_batch_submit(again, fhe.FHE_BATCH_FUSE_RINGS)
+            assert fhe.fhe_batch_wait(bt, 300000) == 0
+            fhe.fhe_batch_destroy(bt)
+            for job, m, want in zip(again, meta, first):
+                outs = [h for h in (job.out0 or []) + (job.out1 or []) if h]
+                for h in outs:
+                    m[0].own(h)
+                assert all(np.array_equal(m[0].export(h), w) for h, w in zip(outs, want)), rep
         for job, (g, kind, xs, ys, xv, yv, b, d) in zip(jobs, meta):
             outs = [h for h in (job.out0 or []) + (job.out1 or []) if h]
             for h in outs:
