@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <chrono>
 #include <map>
+#include <set>
 #include <mutex>
 #include <thread>
 #include <tuple>
@@ -210,6 +211,7 @@ void plan_free(fhe_ctx *c, BatchPlan *P)
 std::recursive_mutex g_fam_mu;
 std::vector<BatchPlan *> g_fam_plans;
 std::map<std::vector<u64>, int> g_fam_seen;
+std::set<std::vector<u64>> g_fam_nocap;  // shapes whose capture ran out of memory
 u64 g_fam_clock = 0;
 constexpr int FAM_PLAN_CAP = 4;
 
@@ -580,7 +582,7 @@ int run_family(const std::vector<fhe_ctx *> &fam_in, const fhe_job *jobs,
         BatchPlan *P = nullptr;
         for (BatchPlan *Q : g_fam_plans)
             if (Q->sig == sig) P = Q;
-        if (!P && g_fam_seen[sig]++ > 0) {
+        if (!P && g_fam_seen[sig]++ > 0 && !g_fam_nocap.count(sig)) {
             // evict the least recently used plan of this family's members
             // (their locks are held here) once the family has FAM_PLAN_CAP
             std::vector<size_t> mine;
@@ -599,13 +601,35 @@ int run_family(const std::vector<fhe_ctx *> &fam_in, const fhe_job *jobs,
                 g_fam_plans.erase(g_fam_plans.begin() + lru);
             }
             err = capture_family(fam, jobs, gm, sig, &P);
-            if (!err) g_fam_plans.push_back(P);
+            if (err == FHE_ENOMEM) {
+                // a graph keeps every intermediate of the circuit: the
+                // members' own batch graphs and cached blocks go back to the
+                // device, and the capture is tried once more
+                cudaDeviceSynchronize();
+                cudaGetLastError();  // the failed allocation's error is not sticky
+                for (fhe_ctx *m : fam) {
+                    batch_plans_release(m);
+                    m->pool.trim();
+                }
+                err = capture_family(fam, jobs, gm, sig, &P);
+            }
+            if (err == FHE_ENOMEM) {
+                // too large to hold as a graph: this shape runs directly
+                cudaDeviceSynchronize();
+                cudaGetLastError();
+                for (fhe_ctx *m : fam) m->pool.trim();
+                g_fam_nocap.insert(sig);
+                P = nullptr;
+                err = 0;
+            }
+            if (!err && P) g_fam_plans.push_back(P);
         }
         if (!err && P) {
             err = replay_family(fam, jobs, gm, P);
             done = true;
         }
         if (g_fam_seen.size() > 1024) g_fam_seen.clear();
+        if (g_fam_nocap.size() > 1024) g_fam_nocap.clear();
     }
     if (!err && any && !done) {
         std::vector<const fhe_evk *> evks;

@@ -170,7 +170,9 @@ struct Sub {
 };
 
 constexpr int SM_WORDS = Sub<5>::WORDS > Sub<8>::WORDS ? Sub<5>::WORDS : Sub<8>::WORDS;
-constexpr int TW_WORDS = twp_size(256);  // largest staged twiddle table (ulonglong2)
+// largest staged twiddle table (ulonglong2): one table of 256 entries, or two
+// of 128 (paired column units)
+constexpr int TW_WORDS = twp_size(256) > 2 * twp_size(128) ? twp_size(256) : 2 * twp_size(128);
 constexpr int ROW_J = 16;                    // jobs per grouped row unit
 
 // Twiddle accessors: get(s, j) = psi^brv(2^s + j), the twiddle of global
@@ -257,14 +259,25 @@ __device__ __forceinline__ void subtx(u64 *sm, int tid, const Geo &geo)
 }
 
 // Column pass of ring degree 2^(N1+N2): NC adjacent columns of NJ jobs.
-template <int N1, int N2>
+// XJ = 2 asks for two jobs per unit where one would hold all NS columns
+// (half as many columns each) and both jobs' twiddles fit the staging table:
+// functors whose loads convert several source limbs pair jobs that read the
+// same sources (fwd_cols_unit).
+__host__ __device__ constexpr bool col_paired(int xj, int n1, int ns, int nc1)
+{
+    return xj == 2 && nc1 == ns && 2 * twp_size(1 << n1) <= TW_WORDS;
+}
+
+template <int N1, int N2, int XJ = 1>
 struct ColGeo {
     using C = Sub<N1>;
     static constexpr int NS = C::NS, SZ = C::SZ, NN = 1 << (N1 + N2);
-    static constexpr int NC = NS < (1 << N2) ? NS : (1 << N2);  // columns per job
-    static constexpr int NJ = NS / NC;                          // jobs per unit
-    static constexpr int BLK = (1 << N2) / NC;                  // column blocks per job
-    static constexpr int TWC = twp_size(1 << N1);               // staged twiddles per job
+    static constexpr int NC1 = NS < (1 << N2) ? NS : (1 << N2);
+    static constexpr bool PAIRED = col_paired(XJ, N1, NS, NC1);
+    static constexpr int NC = PAIRED ? NC1 / 2 : NC1;                  // columns per job
+    static constexpr int NJ = NS / NC;                                 // jobs per unit
+    static constexpr int BLK = (1 << N2) / NC;                         // column blocks per job
+    static constexpr int TWC = twp_size(1 << N1);                      // staged twiddles per job
     static_assert(NJ * TWC <= TW_WORDS, "twiddle staging");
     static_assert(NJ <= 2, "jobs per column unit");
     // word r of the unit: job slot, column in job, element
@@ -273,14 +286,15 @@ struct ColGeo {
     __device__ static int elem(int r) { return (r % (NC * SZ)) / NC; }
 };
 
-template <int N1, int N2>
+template <int N1, int N2, int XJ = 1>
 struct ColTw {
+    using Gm = ColGeo<N1, N2, XJ>;
     const ulonglong2 *W;
     u64 q0, q1;
     static constexpr int S = 0;
-    __device__ PrefixTw tw(int c) const { return PrefixTw{W + (c / ColGeo<N1, N2>::NC) * ColGeo<N1, N2>::TWC}; }
+    __device__ PrefixTw tw(int c) const { return PrefixTw{W + (c / Gm::NC) * Gm::TWC}; }
     __device__ int hi(int) const { return 0; }
-    __device__ u64 q(int c) const { return c / ColGeo<N1, N2>::NC == 0 ? q0 : q1; }
+    __device__ u64 q(int c) const { return c / Gm::NC == 0 ? q0 : q1; }
 };
 
 // Row pass: grouped (16 jobs of one prime x R adjacent rows) or single (NS
@@ -332,7 +346,7 @@ struct RowOneTw {
 // depends on l only (so the jobs l, nl + l, 2 nl + l ... can share a CTA).
 struct SegHdr {
     int logN, outer, nl, grouped;  // grouped: row units of 16 jobs
-    int u_cols, u_rows, pad0, pad1;
+    int u_cols, u_rows, xj, pad1;  // xj: the functor's XJ (0 read as 1)
     const ModQ *mq;
     const ulonglong2 *tw;    // forward or inverse table of the segment's context
     const ulonglong2 *ninv;  // N^-1 per prime (Shoup pairs)
@@ -343,6 +357,8 @@ struct SegIO {
     int nseg, ucols, urows, pad;
     SegHdr h[FHE_SEGS];
     S s[FHE_SEGS];
+    // jobs per column unit asked for (2: functors with load2 / same_src)
+    static constexpr int XJ = 1;
 };
 
 template <class IO>
@@ -420,7 +436,7 @@ __device__ __forceinline__ void tile_out(const IO &io, int tid, StF st, Ok ok, I
 template <int N1, int N2, class IO>
 __device__ __forceinline__ int col_jobs(const IO &io, int sg, int lu, typename IO::St *sts, int *lo0)
 {
-    using Gm = ColGeo<N1, N2>;
+    using Gm = ColGeo<N1, N2, IO::XJ>;
     const SegHdr &H = io.h[sg];
     const int njobs = H.outer * H.nl;
     const int job0 = (lu / Gm::BLK) * Gm::NJ;
@@ -432,9 +448,9 @@ __device__ __forceinline__ int col_jobs(const IO &io, int sg, int lu, typename I
 
 // Stages the first 2^N1 twiddles of each job's prime (the column stages):
 // loaded into registers first, stored after the tile loads (latency overlap).
-template <int N1, int N2>
+template <int N1, int N2, int XJ = 1>
 struct ColTwStage {
-    using Gm = ColGeo<N1, N2>;
+    using Gm = ColGeo<N1, N2, XJ>;
     static constexpr int NW = Gm::NJ << N1;
     static constexpr int PER = (NW + T - 1) / T;
     ulonglong2 v[PER];
@@ -471,14 +487,14 @@ struct ColTwStage {
 template <int N1, int N2, class IO>
 __device__ __forceinline__ void fwd_cols_unit1(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W)
 {
-    using Gm = ColGeo<N1, N2>;
+    using Gm = ColGeo<N1, N2, IO::XJ>;
     using C = typename Gm::C;
     const int tid = threadIdx.x;
     const SegHdr &H = io.h[sg];
     const int lo0 = (lu % Gm::BLK) * Gm::NC;
     typename IO::St st;
     io.begin(sg, lu / Gm::BLK, st);
-    ColTwStage<N1, N2> tws;
+    ColTwStage<N1, N2, IO::XJ> tws;
     tws.load1(H, st.prime);
     const u64 q = H.mq[st.prime].q;
     tile_in<IO::LDCH>(
@@ -486,7 +502,7 @@ __device__ __forceinline__ void fwd_cols_unit1(const IO &io, int sg, int lu, u64
         [&](int r, u64 v) { sm[C::at(Gm::col(r), Gm::elem(r))] = v; });
     tws.store(W);
     __syncthreads();
-    subtx<N1, true>(sm, tid, ColTw<N1, N2>{W, q, q});
+    subtx<N1, true>(sm, tid, ColTw<N1, N2, IO::XJ>{W, q, q});
     __syncthreads();
     u64 *mid = io.inter(st);
 #pragma unroll 4
@@ -499,14 +515,14 @@ __device__ __forceinline__ void fwd_cols_unit1(const IO &io, int sg, int lu, u64
 template <int N1, int N2, class IO>
 __device__ __forceinline__ void inv_cols_unit1(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W)
 {
-    using Gm = ColGeo<N1, N2>;
+    using Gm = ColGeo<N1, N2, IO::XJ>;
     using C = typename Gm::C;
     const int tid = threadIdx.x;
     const SegHdr &H = io.h[sg];
     const int lo0 = (lu % Gm::BLK) * Gm::NC;
     typename IO::St st;
     io.begin(sg, lu / Gm::BLK, st);
-    ColTwStage<N1, N2> tws;
+    ColTwStage<N1, N2, IO::XJ> tws;
     tws.load1(H, st.prime);
     const u64 q = H.mq[st.prime].q;
     const ulonglong2 ni = io.final_scale(st);
@@ -516,7 +532,7 @@ __device__ __forceinline__ void inv_cols_unit1(const IO &io, int sg, int lu, u64
         [&](int r, u64 v) { sm[C::at(Gm::col(r), Gm::elem(r))] = v; });
     tws.store(W);
     __syncthreads();
-    subtx<N1, false>(sm, tid, ColTw<N1, N2>{W, q, q});
+    subtx<N1, false>(sm, tid, ColTw<N1, N2, IO::XJ>{W, q, q});
     __syncthreads();
 #pragma unroll 4
     for (int k = 0; k < 16; k++) {
@@ -531,7 +547,7 @@ template <int N1, int N2, class IO>
 __device__ __forceinline__ void fwd_cols_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
                                               typename IO::St *sts)
 {
-    using Gm = ColGeo<N1, N2>;
+    using Gm = ColGeo<N1, N2, IO::XJ>;
     using C = typename Gm::C;
     if constexpr (Gm::NJ == 1) {
         fwd_cols_unit1<N1, N2>(io, sg, lu, sm, W);
@@ -541,19 +557,37 @@ __device__ __forceinline__ void fwd_cols_unit(const IO &io, int sg, int lu, u64 
     int lo0;
     const int nvalid = col_jobs<N1, N2>(io, sg, lu, sts, &lo0);
     const SegHdr &H = io.h[sg];
-    ColTwStage<N1, N2> tws;
+    ColTwStage<N1, N2, IO::XJ> tws;
     tws.load(H, sts, nvalid);
     const u64 q0 = H.mq[sts[0].prime].q, q1 = nvalid > 1 ? H.mq[sts[Gm::NJ - 1].prime].q : q0;
-    tile_in<IO::LDCH>(
-        tid,
-        [&](int r) {
-            const int j = Gm::jslot(r);
-            return j < nvalid ? io.load(sts[j], (Gm::elem(r) << N2) + lo0 + Gm::col(r)) : 0;
-        },
-        [&](int r, u64 v) { sm[C::at(Gm::jslot(r) * Gm::NC + Gm::col(r), Gm::elem(r))] = v; });
+    bool paired = false;
+    if constexpr (Gm::PAIRED) {
+        // both slots at once: word r (slot 0) and word r + NC SZ (slot 1)
+        // share column and element, so each source word is loaded once
+        static_assert(Gm::NJ == 2 && 2 * Gm::NC * Gm::SZ == 16 * T, "paired column unit");
+        paired = nvalid >= 2 && io.same_src(sts[0], sts[1]);  // uniform in the CTA
+        if (paired) {
+#pragma unroll 4
+            for (int k = 0; k < 8; k++) {
+                const int r = tid + k * T;
+                u64 v0, v1;
+                io.load2(sts[0], sts[1], (Gm::elem(r) << N2) + lo0 + Gm::col(r), v0, v1);
+                sm[C::at(Gm::col(r), Gm::elem(r))] = v0;
+                sm[C::at(Gm::NC + Gm::col(r), Gm::elem(r))] = v1;
+            }
+        }
+    }
+    if (!paired)
+        tile_in<IO::LDCH>(
+            tid,
+            [&](int r) {
+                const int j = Gm::jslot(r);
+                return j < nvalid ? io.load(sts[j], (Gm::elem(r) << N2) + lo0 + Gm::col(r)) : 0;
+            },
+            [&](int r, u64 v) { sm[C::at(Gm::jslot(r) * Gm::NC + Gm::col(r), Gm::elem(r))] = v; });
     tws.store(W);
     __syncthreads();
-    subtx<N1, true>(sm, tid, ColTw<N1, N2>{W, q0, q1});
+    subtx<N1, true>(sm, tid, ColTw<N1, N2, IO::XJ>{W, q0, q1});
     __syncthreads();
 #pragma unroll 4
     for (int k = 0; k < 16; k++) {
@@ -570,7 +604,7 @@ template <int N1, int N2, class IO>
 __device__ __forceinline__ void inv_cols_unit(const IO &io, int sg, int lu, u64 *sm, ulonglong2 *W,
                                               typename IO::St *sts)
 {
-    using Gm = ColGeo<N1, N2>;
+    using Gm = ColGeo<N1, N2, IO::XJ>;
     using C = typename Gm::C;
     if constexpr (Gm::NJ == 1) {
         inv_cols_unit1<N1, N2>(io, sg, lu, sm, W);
@@ -580,7 +614,7 @@ __device__ __forceinline__ void inv_cols_unit(const IO &io, int sg, int lu, u64 
     int lo0;
     const int nvalid = col_jobs<N1, N2>(io, sg, lu, sts, &lo0);
     const SegHdr &H = io.h[sg];
-    ColTwStage<N1, N2> tws;
+    ColTwStage<N1, N2, IO::XJ> tws;
     tws.load(H, sts, nvalid);
     const u64 q0 = H.mq[sts[0].prime].q, q1 = nvalid > 1 ? H.mq[sts[Gm::NJ - 1].prime].q : q0;
     tile_in<16>(
@@ -592,7 +626,7 @@ __device__ __forceinline__ void inv_cols_unit(const IO &io, int sg, int lu, u64 
         [&](int r, u64 v) { sm[C::at(Gm::jslot(r) * Gm::NC + Gm::col(r), Gm::elem(r))] = v; });
     tws.store(W);
     __syncthreads();
-    subtx<N1, false>(sm, tid, ColTw<N1, N2>{W, q0, q1});
+    subtx<N1, false>(sm, tid, ColTw<N1, N2, IO::XJ>{W, q0, q1});
     __syncthreads();
 #pragma unroll 4
     for (int k = 0; k < 16; k++) {
@@ -981,6 +1015,22 @@ struct IOModUp : SegIO<ModUpSeg> {
             if (a < t.nsrc) acc += (u128)t.src[(long long)a * t.N + n] * t.hat[a];
         return barrett128(acc, t.mt);
     }
+    // two targets of one digit (same sources): each source word loaded once
+    static constexpr int XJ = 2;
+    __device__ bool same_src(const St &a, const St &b) const { return a.src == b.src && a.nsrc == b.nsrc; }
+    __device__ void load2(const St &a, const St &b, int n, u64 &v0, u64 &v1) const
+    {
+        u128 s0 = 0, s1 = 0;
+#pragma unroll
+        for (int i = 0; i < FHE_MAXK; i++)
+            if (i < a.nsrc) {
+                const u64 x = a.src[(long long)i * a.N + n];
+                s0 += (u128)x * a.hat[i];
+                s1 += (u128)x * b.hat[i];
+            }
+        v0 = barrett128(s0, a.mt);
+        v1 = barrett128(s1, b.mt);
+    }
     __device__ void store(const St &t, int k, u64 v) const { t.dst[k] = v; }
     static constexpr int NPRE = 0;
     static constexpr int LDCH = FHE_NTT_MULTI_LDCH;  // each load reads several limbs
@@ -1040,6 +1090,22 @@ struct IOModDown : SegIO<ModDownSeg> {
         for (int k = 0; k < FHE_MAXK; k++)
             if (k < t.K) a += (u128)t.w[(long long)k * t.N + n] * t.phat[k];
         return barrett128(a, t.mi);
+    }
+    // two data limbs of one (ct, poly): the special limbs loaded once
+    static constexpr int XJ = 2;
+    __device__ bool same_src(const St &a, const St &b) const { return a.w == b.w && a.K == b.K; }
+    __device__ void load2(const St &a, const St &b, int n, u64 &v0, u64 &v1) const
+    {
+        u128 s0 = 0, s1 = 0;
+#pragma unroll
+        for (int k = 0; k < FHE_MAXK; k++)
+            if (k < a.K) {
+                const u64 x = a.w[(long long)k * a.N + n];
+                s0 += (u128)x * a.phat[k];
+                s1 += (u128)x * b.phat[k];
+            }
+        v0 = barrett128(s0, a.mi);
+        v1 = barrett128(s1, b.mi);
     }
     __device__ void store(const St &t, int k, u64 v) const
     {
@@ -1167,6 +1233,22 @@ struct IORelinMS : SegIO<RelinMSSeg> {
             if (k <= t.K) a += (u128)t.w[(long long)k * t.N + n] * t.h[k];
         return barrett128(a, t.mi);
     }
+    // two data limbs of one (ct, poly): the K + 1 sources loaded once
+    static constexpr int XJ = 2;
+    __device__ bool same_src(const St &a, const St &b) const { return a.w == b.w && a.K == b.K; }
+    __device__ void load2(const St &a, const St &b, int n, u64 &v0, u64 &v1) const
+    {
+        u128 s0 = 0, s1 = 0;
+#pragma unroll
+        for (int k = 0; k < FHE_MAXK; k++)
+            if (k <= a.K) {
+                const u64 x = a.w[(long long)k * a.N + n];
+                s0 += (u128)x * a.h[k];
+                s1 += (u128)x * b.h[k];
+            }
+        v0 = barrett128(s0, a.mi);
+        v1 = barrett128(s1, b.mi);
+    }
     __device__ u64 combine(const St &t, u64 accv, u64 addv, u64 v) const
     {
         const u64 q = t.mi.q;
@@ -1230,6 +1312,22 @@ struct IOMultiSwitch : SegIO<MultiSeg> {
             if (j < t.k) a += (u128)t.w[(long long)j * t.N + n] * t.g[j];
         return barrett128(a, t.mi);
     }
+    // two kept limbs of one (ct, poly): the k switch values loaded once
+    static constexpr int XJ = 2;
+    __device__ bool same_src(const St &a, const St &b) const { return a.w == b.w && a.k == b.k; }
+    __device__ void load2(const St &a, const St &b, int n, u64 &v0, u64 &v1) const
+    {
+        u128 s0 = 0, s1 = 0;
+#pragma unroll
+        for (int j = 0; j < FHE_MAXK; j++)
+            if (j < a.k) {
+                const u64 x = a.w[(long long)j * a.N + n];
+                s0 += (u128)x * a.g[j];
+                s1 += (u128)x * b.g[j];
+            }
+        v0 = barrett128(s0, a.mi);
+        v1 = barrett128(s1, b.mi);
+    }
     __device__ void store(const St &t, int j, u64 v) const
     {
         t.out[j] = shoup(submod(t.in[j], v, t.mi.q), t.dinv, t.dinv_s, t.mi.q);
@@ -1272,7 +1370,9 @@ void unit_counts(SegHdr &H)
 {
     const Split sp = split_of(H.logN);
     const int njobs = H.outer * H.nl;
-    const int nc = std::min(sp.ns1, 1 << sp.n2), nj = sp.ns1 / nc, blk = (1 << sp.n2) / nc;
+    int nc = std::min(sp.ns1, 1 << sp.n2);
+    if (col_paired(H.xj, sp.n1, sp.ns1, nc)) nc /= 2;  // ColGeo's paired units
+    const int nj = sp.ns1 / nc, blk = (1 << sp.n2) / nc;
     H.u_cols = ((njobs + nj - 1) / nj) * blk;
     H.u_rows = H.grouped ? H.nl * ((H.outer + ROW_J - 1) / ROW_J) * ((1 << sp.n1) / (sp.ns2 / ROW_J))
                          : njobs * ((1 << sp.n1) / sp.ns2);
@@ -1421,7 +1521,13 @@ void run_many(const std::vector<Item> &items, bool fwd, int cls, Fill fill)
         double bytes = 0, bfly = 0;
         for (; i < items.size() && io.nseg < FHE_SEGS; i++) {
             double b = 0, f = 0;
-            if (fill(io, io.nseg, items[i], &b, &f)) io.nseg++;
+            if (fill(io, io.nseg, items[i], &b, &f)) {
+                if (IO::XJ != 1) {
+                    io.h[io.nseg].xj = IO::XJ;
+                    unit_counts(io.h[io.nseg]);
+                }
+                io.nseg++;
+            }
             bytes += b;
             bfly += f;
         }

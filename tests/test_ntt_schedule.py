@@ -6,7 +6,9 @@
   k G + t / NS) and round 2 (t -> sub-transform t / G, blocks of G contiguous
   residues) together compute, forward and inverse, the same as the plain
   radix-2 stages of every sub-transform;
-- the column units of every ring degree 2^10..2^15 (NC columns of NJ jobs)
+- the column units of every ring degree 2^10..2^15 (NC columns of NJ jobs),
+  also in the paired form (two jobs that read the same source limbs, half
+  the columns each, where both jobs' twiddle tables fit the staging table),
   and the row units (grouped: one row of 16 jobs of a prime times R rows;
   single: NS adjacent rows of one job) touch every residue of every job
   exactly once, with ragged job counts."""
@@ -113,27 +115,61 @@ def split(logN):
     return n1, n2, 2048 >> n1, 2048 >> n2
 
 
+def twp_size(n):  # staged twiddle entries of a table of n (one pad per 8)
+    return n + n // 8 + 1
+
+
+TW_WORDS = max(twp_size(256), 2 * twp_size(128))
+
+
+def col_geometry(logN, xj):
+    n1, n2, ns1, _ = split(logN)
+    nc = min(ns1, 1 << n2)
+    paired = xj == 2 and nc == ns1 and 2 * twp_size(1 << n1) <= TW_WORDS
+    if paired:
+        nc //= 2
+    return nc, ns1 // nc, (1 << n2) // nc, paired
+
+
 @pytest.mark.parametrize("logN", [10, 11, 12, 13, 14, 15])
 @pytest.mark.parametrize("njobs", [1, 3, 16, 37])
-def test_column_units_cover_every_residue_once(logN, njobs):
+@pytest.mark.parametrize("xj", [1, 2])
+def test_column_units_cover_every_residue_once(logN, njobs, xj):
     n1, n2, ns1, _ = split(logN)
-    NC = min(ns1, 1 << n2)
-    NJ = ns1 // NC
-    BLK = (1 << n2) // NC
+    NC, NJ, BLK, paired = col_geometry(logN, xj)
+    assert NJ <= 2 and NJ * twp_size(1 << n1) <= TW_WORDS
     SZ = 1 << n1
     units = ((njobs + NJ - 1) // NJ) * BLK
     seen = {}
     for lu in range(units):
         job0, lo0 = (lu // BLK) * NJ, (lu % BLK) * NC
+        pos = {}
         for r in range(16 * T):  # word r of the unit: job slot, column, element
             j = 0 if NJ == 1 else r // (NC * SZ)
             col, e = r % NC, (r % (NC * SZ)) // NC
             assert 0 <= e < SZ
+            pos[r] = (e << n2) + lo0 + col
             if job0 + j >= njobs:
                 continue
-            key = (job0 + j, (e << n2) + lo0 + col)
+            key = (job0 + j, pos[r])
             seen[key] = seen.get(key, 0) + 1
+        if paired:
+            # the paired load: thread t's words t + 128 k (k < 8) of slot 0
+            # and t + 128 k + NC SZ of slot 1 read the same source position
+            assert NJ == 2 and 2 * NC * SZ == 16 * T
+            for t in range(T):
+                for k in range(8):
+                    r = t + k * T
+                    assert r < NC * SZ and pos[r] == pos[r + NC * SZ]
     assert len(seen) == njobs << logN and set(seen.values()) == {1}
+
+
+def test_paired_geometry_where_it_applies():
+    """Pairing halves the columns of the rings whose column unit holds one
+    job (2^11..2^14); 2^10 already holds two jobs and 2^15's two 256-entry
+    twiddle tables would not fit the staging table."""
+    assert [col_geometry(n, 2)[3] for n in range(10, 16)] == [False, True, True, True, True, False]
+    assert all(col_geometry(n, 2)[1] == 2 for n in range(10, 15))
 
 
 @pytest.mark.parametrize("logN", [10, 11, 12, 13, 14, 15])
