@@ -35,7 +35,7 @@ struct EwSeg {
     u64 *out;
     const ModQ *mq;
     long long total;  // elements: outer * level * N
-    int logN, level, n, op, b0, pad;
+    int logN, level, n, op, b0, vec;  // vec: every pointer 16-byte aligned
     int64_t k[8];     // centred scalars, |k| < p
 };
 
@@ -44,37 +44,108 @@ struct EwTable {
     EwSeg s[FHE_SEGS];
 };
 
-__global__ void k_ew_many(const __grid_constant__ EwTable t)
+// V adjacent elements (one limb: N is even) as one load per operand
+template <int V>
+struct Vec {
+    u64 v[V];
+};
+
+template <int V>
+__device__ __forceinline__ Vec<V> ld_vec(const u64 *p)
 {
-    const EwSeg &S = t.s[block_seg(t.s, t.nseg)];
+    Vec<V> r;
+    if constexpr (V == 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(p);
+        r.v[0] = t.x;
+        r.v[1] = t.y;
+    } else {
+        r.v[0] = *p;
+    }
+    return r;
+}
+
+template <int V>
+__device__ __forceinline__ void st_vec(u64 *p, const Vec<V> &r)
+{
+    if constexpr (V == 2)
+        *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(r.v[0], r.v[1]);
+    else
+        *p = r.v[0];
+}
+
+template <int V>
+__device__ __forceinline__ void ew_block(const EwSeg &S)
+{
     const long long base = (long long)(blockIdx.x - S.b0) * EW_ELEMS;
-    for (int e = threadIdx.x; e < EW_ELEMS; e += TPB) {
+#pragma unroll
+    for (int e = threadIdx.x * V; e < EW_ELEMS; e += TPB * V) {
         const long long idx = base + e;
         if (idx >= S.total) break;
         const long long li = idx >> S.logN;
         const int i = (int)(li % S.level);
         const u64 q = S.mq[i].q;
-        u64 r;
+        Vec<V> r;
         switch (S.op) {
-        case FHE_EW_ADD: r = addmod(S.x[0][idx], S.x[1][idx], q); break;
-        case FHE_EW_SUB: r = submod(S.x[0][idx], S.x[1][idx], q); break;
-        case FHE_EW_NEG: r = negmod(S.x[0][idx], q); break;
-        case FHE_EW_CMUL: r = barrett128((u128)S.x[0][idx] * small_mod(S.k[0], q), S.mq[i]); break;
+        case FHE_EW_ADD: {
+            const Vec<V> a = ld_vec<V>(S.x[0] + idx), b = ld_vec<V>(S.x[1] + idx);
+#pragma unroll
+            for (int u = 0; u < V; u++) r.v[u] = addmod(a.v[u], b.v[u], q);
+            break;
+        }
+        case FHE_EW_SUB: {
+            const Vec<V> a = ld_vec<V>(S.x[0] + idx), b = ld_vec<V>(S.x[1] + idx);
+#pragma unroll
+            for (int u = 0; u < V; u++) r.v[u] = submod(a.v[u], b.v[u], q);
+            break;
+        }
+        case FHE_EW_NEG: {
+            const Vec<V> a = ld_vec<V>(S.x[0] + idx);
+#pragma unroll
+            for (int u = 0; u < V; u++) r.v[u] = negmod(a.v[u], q);
+            break;
+        }
+        case FHE_EW_CMUL: {
+            const Vec<V> a = ld_vec<V>(S.x[0] + idx);
+            const u64 k = small_mod(S.k[0], q);
+#pragma unroll
+            for (int u = 0; u < V; u++) r.v[u] = barrett128((u128)a.v[u] * k, S.mq[i]);
+            break;
+        }
         case FHE_EW_CADD: {
             const int poly = (int)((li / S.level) % 2);
-            r = poly == 0 ? addmod(S.x[0][idx], small_mod(S.k[0], q), q) : S.x[0][idx];
+            const Vec<V> a = ld_vec<V>(S.x[0] + idx);
+            const u64 k = small_mod(S.k[0], q);
+#pragma unroll
+            for (int u = 0; u < V; u++) r.v[u] = poly == 0 ? addmod(a.v[u], k, q) : a.v[u];
             break;
         }
         default: {  // FHE_EW_LINCOMB: at most eight products below the Barrett bound
-            u128 acc = 0;
+            u128 acc[V];
+#pragma unroll
+            for (int u = 0; u < V; u++) acc[u] = 0;
 #pragma unroll
             for (int j = 0; j < 8; j++)
-                if (j < S.n) acc += (u128)S.x[j][idx] * small_mod(S.k[j], q);
-            r = barrett128(acc, S.mq[i]);
+                if (j < S.n) {
+                    const Vec<V> a = ld_vec<V>(S.x[j] + idx);
+                    const u64 k = small_mod(S.k[j], q);
+#pragma unroll
+                    for (int u = 0; u < V; u++) acc[u] += (u128)a.v[u] * k;
+                }
+#pragma unroll
+            for (int u = 0; u < V; u++) r.v[u] = barrett128(acc[u], S.mq[i]);
         }
         }
-        S.out[idx] = r;
+        st_vec<V>(S.out + idx, r);
     }
+}
+
+__global__ void k_ew_many(const __grid_constant__ EwTable t)
+{
+    const EwSeg &S = t.s[block_seg(t.s, t.nseg)];
+    if (S.vec)
+        ew_block<2>(S);
+    else
+        ew_block<1>(S);
 }
 
 // ---- tensor: (a0,a1) x (b0,b1) -> (a0 b0, a0 b1 + a1 b0, a1 b1) -----------
@@ -148,24 +219,35 @@ __global__ void __launch_bounds__(TPB, 3) k_ks_inner_many(const __grid_constant_
     u128 a0[KS_CB], a1[KS_CB];
 #pragma unroll
     for (int cc = 0; cc < KS_CB; cc++) a0[cc] = a1[cc] = 0;
-    for (int j = 0; j < S.dnum; j++) {
-        const u64 k0 = S.ksk[(((long long)j * 2 + 0) * LK + prime) * N + n];
-        const u64 k1 = S.ksk[(((long long)j * 2 + 1) * LK + prime) * N + n];
-        u64 y[KS_CB];
+    // digit j's two key words and CB inputs; the next digit's are loaded
+    // before this digit's products (two digits' loads in flight)
+    auto load = [&](int j, u64 &k0, u64 &k1, u64 (&y)[KS_CB]) {
+        k0 = S.ksk[(((long long)j * 2 + 0) * LK + prime) * N + n];
+        k1 = S.ksk[(((long long)j * 2 + 1) * LK + prime) * N + n];
 #pragma unroll
         for (int cc = 0; cc < KS_CB; cc++) {
             const int c = c0 + cc;
-            if (cc < ncb)
-                y[cc] = (j == rdig) ? S.xbase[c * S.x_outer + (long long)r * N + n]
-                                    : S.ext[(((long long)c * S.dnum + j) * lK + r) * N + n];
+            y[cc] = cc >= ncb ? 0
+                    : (j == rdig) ? S.xbase[c * S.x_outer + (long long)r * N + n]
+                                  : S.ext[(((long long)c * S.dnum + j) * lK + r) * N + n];
         }
+    };
+    u64 k0, k1, y[KS_CB];
+    load(0, k0, k1, y);
+    for (int j = 0; j < S.dnum; j++) {
+        u64 nk0 = 0, nk1 = 0, ny[KS_CB];
+#pragma unroll
+        for (int cc = 0; cc < KS_CB; cc++) ny[cc] = 0;
+        if (j + 1 < S.dnum) load(j + 1, nk0, nk1, ny);
 #pragma unroll
         for (int cc = 0; cc < KS_CB; cc++) {
-            if (cc < ncb) {
-                a0[cc] += (u128)y[cc] * k0;
-                a1[cc] += (u128)y[cc] * k1;
-            }
+            a0[cc] += (u128)y[cc] * k0;
+            a1[cc] += (u128)y[cc] * k1;
         }
+        k0 = nk0;
+        k1 = nk1;
+#pragma unroll
+        for (int cc = 0; cc < KS_CB; cc++) y[cc] = ny[cc];
     }
 #pragma unroll
     for (int cc = 0; cc < KS_CB; cc++) {
@@ -279,6 +361,9 @@ void launch_ew_many(const std::vector<EwArgs> &items)
             S.level = a.level;
             S.n = a.n;
             S.op = a.op;
+            bool vec = ((uintptr_t)a.out & 15) == 0;
+            for (int j = 0; j < 8; j++) vec = vec && ((uintptr_t)a.x[j] & 15) == 0;
+            S.vec = vec;
             const int reads = a.op == FHE_EW_LINCOMB ? a.n : (a.op == FHE_EW_ADD || a.op == FHE_EW_SUB) ? 2 : 1;
             *bytes = 8.0 * (reads + 1) * S.total;
             return ew_blocks(S.total);

@@ -17,9 +17,9 @@ void launch_ntt_modup_many(const std::vector<NttModUpArgs> &a)
         S.l = x.level;
         S.K = x.c->K;
         S.dnum = P.dnum;
-        double words = 0;
-        for (int e = 0; e < P.njobs; e++) words += P.digit_n[P.job_digit[e]] + 1.0;
-        *b = 8.0 * x.c->N * words * x.count;
+        // the level's l coefficient limbs read once per ciphertext (every
+        // digit's targets convert from them), one limb written per job
+        *b = 8.0 * x.c->N * ((double)x.level + P.njobs) * x.count;
         *f = bfly_of(x.c, (double)P.njobs * x.count);
         return true;
     });
@@ -41,10 +41,11 @@ void launch_ntt_moddown_many(const std::vector<NttDownArgs> &a)
         S.P = x.c->d_moddown + x.level;
         S.l = x.level;
         S.K = x.c->K;
-        // reads K special limbs, acc_i and (for masked polys) the addend; writes out_i
+        // the K special limbs of each (ct, poly) read once; acc_i and (for
+        // masked polys) the addend read, out_i written
         const double add_frac = ((x.amask & 1) + ((x.amask >> 1) & 1)) / 2.0;
         const double njobs = 2.0 * x.level * x.count;
-        *b = 8.0 * x.c->N * njobs * (x.c->K + 2.0 + add_frac);
+        *b = 8.0 * x.c->N * (2.0 * x.count * x.c->K + njobs * (2.0 + add_frac));
         *f = bfly_of(x.c, njobs);
         return true;
     });
@@ -66,10 +67,11 @@ void launch_ntt_relin_ms_many(const std::vector<NttDownArgs> &a)
         S.P = x.c->d_rms + x.level;
         S.l = x.level;
         S.K = x.c->K;
-        // reads K + 1 correction sources, acc_i and (for masked polys) the addend; writes out_i
+        // the K + 1 correction sources of each (ct, poly) read once; acc_i
+        // and (for masked polys) the addend read, out_i written
         const double add_frac = ((x.amask & 1) + ((x.amask >> 1) & 1)) / 2.0;
         const double njobs = 2.0 * (x.level - 1) * x.count;
-        *b = 8.0 * x.c->N * njobs * (x.c->K + 3.0 + add_frac);
+        *b = 8.0 * x.c->N * (2.0 * x.count * (x.c->K + 1.0) + njobs * (2.0 + add_frac));
         *f = bfly_of(x.c, njobs);
         return true;
     });

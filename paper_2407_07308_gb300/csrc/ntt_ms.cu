@@ -16,8 +16,9 @@ void launch_ntt_modswitch_many(const std::vector<NttSwitchArgs> &a)
         S.P = x.c->d_modswitch + x.level;
         S.l = x.level;
         S.npoly = x.npoly;
+        // each (ct, poly)'s switch value read once; x_i read, out_i written
         const double njobs = (double)x.npoly * (x.level - 1) * x.count;
-        *b = 8.0 * x.c->N * njobs * 3.0;
+        *b = 8.0 * x.c->N * ((double)x.npoly * x.count + 2.0 * njobs);
         *f = bfly_of(x.c, njobs);
         return true;
     });
@@ -37,9 +38,9 @@ void launch_ntt_multiswitch_many(const std::vector<NttSwitchArgs> &a)
         S.l = x.level;
         S.k = x.k;
         S.npoly = x.npoly;
-        // reads the k switch values and x_i, writes out_i
+        // each (ct, poly)'s k switch values read once; x_i read, out_i written
         const double njobs = (double)x.npoly * (x.level - x.k) * x.count;
-        *b = 8.0 * x.c->N * njobs * (x.k + 2.0);
+        *b = 8.0 * x.c->N * ((double)x.npoly * x.count * x.k + 2.0 * njobs);
         *f = bfly_of(x.c, njobs);
         return true;
     });
