@@ -104,7 +104,10 @@ int fhe_ctx_primes(const fhe_ctx *ctx, uint64_t *out);
 int fhe_ctx_set_stream(fhe_ctx *ctx, void *stream);
 /* Waits for all work on the context's stream. */
 int fhe_ctx_sync(fhe_ctx *ctx);
-/* Device bytes held by the pool (reserved) and handed out (in_use). */
+/* Device bytes held by the pool (reserved) and handed out (in_use).  The
+ * pool hands out blocks in size classes of a quarter power of two (a block is
+ * less than 25% larger than asked for), so a freed block serves later
+ * requests of nearby sizes; both figures count whole blocks. */
 int fhe_ctx_memory(const fhe_ctx *ctx, uint64_t *reserved, uint64_t *in_use);
 /* Largest in_use since the last reset; reset != 0 restarts it from the
  * current in_use. */
@@ -552,7 +555,7 @@ typedef struct fhe_server fhe_server;
 
 /* Estimated device bytes a request allocates while it runs: the circuit's
  * working set per digit, the key-switching scratch of up to 8 concurrent
- * digits and the outputs (0 for an invalid job). */
+ * digits and the outputs, in whole pool blocks (0 for an invalid job). */
 uint64_t fhe_job_footprint(const fhe_job *job);
 /* cfg may be NULL (no budget, no batch limit). */
 int fhe_server_start(const fhe_server_config *cfg, fhe_server **out);

@@ -26,8 +26,21 @@ int fhe_cuda_check(fhe_ctx *ctx, cudaError_t e, const char *where)
     return fhe_fail(ctx, FHE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// Blocks come in size classes of a quarter power of two (at most 25% above
+// the request), so that a freed block serves later requests of nearby sizes:
+// batches of many levels and counts otherwise leave a cached block of every
+// exact size behind and fill the device with them.
+size_t pool_class(size_t bytes)
+{
+    if (bytes <= 1024) return 1024;
+    int e = 63 - __builtin_clzll((unsigned long long)bytes);
+    const size_t step = (size_t)1 << (e - 2);
+    return (bytes + step - 1) / step * step;
+}
+
 void *Pool::get(size_t bytes, int *err)
 {
+    bytes = pool_class(bytes);
     if (cap_free) {
         auto &cf = (*cap_free)[bytes];
         if (!cf.empty()) {

@@ -76,7 +76,9 @@ struct fhe_server {
 // part), the relinearised and switched results (4l limbs), all at the input
 // level l; plus the per-digit working set of powers and partial sums and the
 // outputs; a sort holds FHE_SORT_MERGE comparisons at a time.  A limb is N
-// words per ciphertext of the batch; B = 4 for p < 64, else 16.
+// words per ciphertext of the batch; B = 4 for p < 64, else 16.  The pool
+// rounds every block up to its size class (less than 25% more), so the sum
+// is scaled by 5/4.
 extern "C" uint64_t fhe_job_footprint(const fhe_job *j)
 {
     if (!j || !j->ctx || !j->x || !j->x[0] || j->d < 1) return 0;
@@ -96,7 +98,7 @@ extern "C" uint64_t fhe_job_footprint(const fhe_job *j)
     if (j->kind == FHE_JOB_SORT)  // FHE_SORT_MERGE shifts' comparisons at a time, plus the
         // rotated operands, the rank, the selection powers and the d accumulated outputs
         est = FHE_SORT_MERGE * est + (ceil_log2(c->p) + 3 * d + 4) * ct + 2 * per_mult;
-    return est;
+    return est + est / 4;
 }
 
 // Each request retires when its own job has its results (not when the whole
