@@ -138,6 +138,10 @@ constexpr int T = 128;  // threads per CTA, 16 residues each
 #ifndef FHE_NTT_MINB
 #define FHE_NTT_MINB 8
 #endif
+// The same for the column kernels of paired units (two targets per load).
+#ifndef FHE_NTT_MINB_PAIRED
+#define FHE_NTT_MINB_PAIRED FHE_NTT_MINB
+#endif
 // Words staged per chunk by the loads that read several limbs each (ModUp,
 // relinearise + switch, multi-prime switch); 0 = not staged (each word's
 // loads, arithmetic and shared-memory store in turn, four words unrolled).
@@ -812,7 +816,8 @@ __device__ __forceinline__ void by_degree(int logN, F f)
 }
 
 template <class IO, int LO, int HI>
-__global__ void __launch_bounds__(T, FHE_NTT_MINB) k_fwd_cols(const __grid_constant__ IO io)
+__global__ void __launch_bounds__(T, IO::XJ == 2 ? FHE_NTT_MINB_PAIRED : FHE_NTT_MINB)
+    k_fwd_cols(const __grid_constant__ IO io)
 {
     __shared__ u64 sm[SM_WORDS];
     __shared__ ulonglong2 W[TW_WORDS];
