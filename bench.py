@@ -253,22 +253,45 @@ class Clocks:
 # GPU arm
 # ---------------------------------------------------------------------------
 
-# DRAM bytes per algorithmic byte of a kernel class, measured with ncu on the
-# headline command (profiles/ntt_inverse_c2_dram.md) for the NTT source whose
-# SHA-256 starts with the given prefix; for any other source the traffic is
-# reported as null.
-DRAM_PER_ALGORITHMIC = {"ntt_inv": (1.04, "635767c87a38cfd9")}
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum over every
+# launch of one replay) per algorithmic byte of a kernel class, measured on
+# the headline workload for the sources whose SHA-256 (of the files below,
+# concatenated) starts with the given prefix; for other sources the traffic
+# is reported as null.
+CLASS_SOURCES = {
+    "ntt_inv": ("ntt_engine.cuh", "ntt.cu"),
+    "ntt_modup": ("ntt_engine.cuh", "ntt_ks.cu"),
+    "ntt_moddown": ("ntt_engine.cuh", "ntt_ks.cu"),
+    "ntt_modswitch": ("ntt_engine.cuh", "ntt_ms.cu"),
+    "ks_inner": ("many.cu",),
+    "tensor": ("many.cu",),
+    "elementwise": ("many.cu",),
+}
+DRAM_PER_ALGORITHMIC = {
+    "ntt_modup": (1.77, "b990667556b21a71"),
+    "ntt_moddown": (1.25, "b990667556b21a71"),
+    "ntt_inv": (1.1, "66f183f704d888fb"),
+    "ntt_modswitch": (1.41, "95c21f45efc3d481"),
+    "ks_inner": (0.8, "40d58120e5917eba"),
+    "elementwise": (0.86, "40d58120e5917eba"),
+    "tensor": (0.63, "40d58120e5917eba"),
+}
+
+
+def class_source_hash(kernel_class: str) -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in CLASS_SOURCES.get(kernel_class, ()):
+        with open(os.path.join(ROOT, "paper_2407_07308_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def traffic_for(kernel_class: str, algorithmic_bytes: float):
-    import hashlib
-
     rec = DRAM_PER_ALGORITHMIC.get(kernel_class)
-    if not rec:
+    if not rec or not class_source_hash(kernel_class).startswith(rec[1]):
         return None
-    with open(os.path.join(ROOT, "paper_2407_07308_gb300", "csrc", "ntt.cu"), "rb") as f:
-        if not hashlib.sha256(f.read()).hexdigest().startswith(rec[1]):
-            return None
     return round(rec[0] * algorithmic_bytes)
 
 
@@ -449,7 +472,7 @@ def run_gpu(args):
     # ---- end to end through the C ABI with host buffers -------------------
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(fhe, ctx, plan, outs, xs, ys, pairs, ns, N, args, world, barrier)
+        e2e = run_e2e(fhe, ctx, evk, plan, outs, xs, ys, plan_flags, stream, pairs, ns, N, args, world, barrier)
 
     clocks = clk.summary()
     res, used = fhe.fhe_ctx_memory(ctx)
@@ -548,42 +571,98 @@ def run_plain(fhe, ctx, evk, xd, yd, enc_each, pairs, ns, stream, ev):
     return pairs * ns / (plain_total / 1e3), lat, xs1, ys1
 
 
-def run_e2e(fhe, ctx, plan, outs, xs, ys, pairs, ns, N, args, world, barrier):
-    """Per step: host ciphertexts (pinned) into the plan's input handles,
-    one replay, both results back to pinned host memory."""
+def run_e2e(fhe, ctx, evk, plan, outs, xs, ys, plan_flags, stream, pairs, ns, N, args, world, barrier):
+    """Per step: the step's host ciphertexts (pinned) into a plan's input
+    handles (fhe_ct_load_coeff: H2D copy + forward NTT), one replay, both
+    results back to pinned host memory (fhe_ct_export_coeff).  Two plans over
+    two sets of input handles alternate, so that step i+1's upload, issued on
+    a second stream (fhe_ctx_set_stream), overlaps step i's replay; every
+    step still uploads all its inputs and reads its results back inside the
+    timed region.  The sequential form (one plan: upload, replay, read back
+    in turn) is measured beside it."""
     import numpy as np
     import torch
 
-    handles = xs + ys
     host_in = []
-    for h in handles:
+    for h in xs + ys:
         a = fhe.fhe_ct_export_coeff(ctx, h)
         pinned = torch.empty(a.shape, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
         pinned[...] = a
         host_in.append(pinned)
     out_shape = (pairs, 2, 1, N)
-    host_out = [torch.empty(out_shape, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
-                for _ in range(2)]
+    host_out = [[torch.empty(out_shape, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+                 for _ in range(2)] for _ in range(2)]
     bi = sum(a.nbytes for a in host_in)
-    bo = sum(a.nbytes for a in host_out)
+    bo = sum(a.nbytes for a in host_out[0])
+    d = len(xs)
+    xs2 = [fhe.fhe_ct_import_coeff(ctx, a) for a in host_in[:d]]
+    ys2 = [fhe.fhe_ct_import_coeff(ctx, a) for a in host_in[d:]]
+    plan2 = fhe.fhe_compare_plan(ctx, evk, xs2, ys2, flags=plan_flags)
+    sets = [(plan, outs, xs + ys), (plan2, [fhe.fhe_plan_result(plan2, 0), fhe.fhe_plan_result(plan2, 1)], xs2 + ys2)]
+    side = torch.cuda.Stream()
+    loaded = [torch.cuda.Event(), torch.cuda.Event()]
+    done = [torch.cuda.Event(), torch.cuda.Event()]
 
-    def e2e_step():
-        for h, a in zip(handles, host_in):
-            fhe._check(fhe.lib().fhe_ct_load_coeff(ctx, h, fhe._ptr(a)), ctx)
-        fhe.fhe_plan_run(plan, ctx)
-        for h, buf in zip(outs, host_out):
+    def upload(k, on_side):
+        if on_side:
+            side.wait_event(done[k])  # the set's previous replay has read its inputs
+            fhe.fhe_ctx_set_stream(ctx, side.cuda_stream)
+        try:
+            for h, a in zip(sets[k][2], host_in):
+                fhe._check(fhe.lib().fhe_ct_load_coeff(ctx, h, fhe._ptr(a)), ctx)
+        finally:
+            if on_side:
+                fhe.fhe_ctx_set_stream(ctx, stream.cuda_stream)
+        if on_side:
+            loaded[k].record(side)
+
+    def read_back(k):
+        for h, buf in zip(sets[k][1], host_out[k]):
             fhe._check(fhe.lib().fhe_ct_export_coeff(ctx, h, fhe._ptr(buf)), ctx)
 
-    e2e_step()
-    torch.cuda.synchronize()
-    barrier()
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t, world)
-    return {"value": round(whole_job_rate(pairs * ns, world, args.steps, 1e3 * e2e_s), 2), "unit": UNIT,
-            "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+    def sequential_step():
+        upload(0, False)
+        fhe.fhe_plan_run(plan, ctx)
+        read_back(0)
+
+    def pipelined(nsteps):
+        upload(0, False)
+        for i in range(nsteps):
+            k = i % 2
+            if i > 0:
+                stream.wait_event(loaded[k])
+            fhe.fhe_plan_run(sets[k][0], ctx)
+            done[k].record(stream)
+            if i + 1 < nsteps:
+                upload(1 - k, True)
+            read_back(k)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        barrier()
+        t = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return max_over_ranks(time.perf_counter() - t, world)
+
+    sequential_step()
+    want = [a.copy() for a in host_out[0]]
+    seq_s = timed(lambda: [sequential_step() for _ in range(args.steps)])
+    pipelined(4)
+    for k in range(2):  # both plans' last results equal the sequential form's
+        assert all(np.array_equal(a, w) for a, w in zip(host_out[k], want)), "pipelined e2e result mismatch"
+    e2e_s = timed(lambda: pipelined(args.steps))
+    for k in range(min(2, args.steps)):
+        assert all(np.array_equal(a, w) for a, w in zip(host_out[k], want)), "pipelined e2e result mismatch"
+    fhe.fhe_plan_destroy(plan2)
+    for h in xs2 + ys2:
+        fhe.fhe_ct_destroy(h)
+    rate = lambda sec: round(whole_job_rate(pairs * ns, world, args.steps, 1e3 * sec), 2)
+    return {"value": rate(e2e_s), "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+            "form": "two plans alternating: step i+1's upload (H2D + forward NTT) on a second stream overlaps "
+                    "step i's replay; results read back every step",
+            "sequential": {"value": rate(seq_s), "unit": UNIT,
+                           "form": "one plan: upload, replay, read back in turn"}}
 
 
 # ---------------------------------------------------------------------------

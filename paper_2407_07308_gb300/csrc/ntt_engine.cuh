@@ -142,6 +142,21 @@ constexpr int T = 128;  // threads per CTA, 16 residues each
 #ifndef FHE_NTT_MINB_PAIRED
 #define FHE_NTT_MINB_PAIRED FHE_NTT_MINB
 #endif
+// Paired column units whose two jobs read different sources (a digit or
+// ciphertext boundary) load in a rolled loop (1) or the unrolled staged one (0).
+#ifndef FHE_NTT_PAIRED_FALLBACK_ROLLED
+#define FHE_NTT_PAIRED_FALLBACK_ROLLED 1
+#endif
+// Positions of a paired unit's load loop unrolled together (8 per thread).
+#ifndef FHE_NTT_PAIRED_UNROLL
+#define FHE_NTT_PAIRED_UNROLL 2
+#endif
+constexpr int PAIRED_UNROLL = FHE_NTT_PAIRED_UNROLL;
+// Launches that mix ring degrees 2^13..2^15 take the kernel that dispatches
+// every unit on its degree (1), or one launch per degree in turn (0).
+#ifndef FHE_NTT_MIXED_KERNEL
+#define FHE_NTT_MIXED_KERNEL 1
+#endif
 // Words staged per chunk by the loads that read several limbs each (ModUp,
 // relinearise + switch, multi-prime switch); 0 = not staged (each word's
 // loads, arithmetic and shared-memory store in turn, four words unrolled).
@@ -571,7 +586,7 @@ __device__ __forceinline__ void fwd_cols_unit(const IO &io, int sg, int lu, u64 
         static_assert(Gm::NJ == 2 && 2 * Gm::NC * Gm::SZ == 16 * T, "paired column unit");
         paired = nvalid >= 2 && io.same_src(sts[0], sts[1]);  // uniform in the CTA
         if (paired) {
-#pragma unroll 4
+#pragma unroll PAIRED_UNROLL
             for (int k = 0; k < 8; k++) {
                 const int r = tid + k * T;
                 u64 v0, v1;
@@ -581,14 +596,26 @@ __device__ __forceinline__ void fwd_cols_unit(const IO &io, int sg, int lu, u64 
             }
         }
     }
-    if (!paired)
-        tile_in<IO::LDCH>(
-            tid,
-            [&](int r) {
-                const int j = Gm::jslot(r);
-                return j < nvalid ? io.load(sts[j], (Gm::elem(r) << N2) + lo0 + Gm::col(r)) : 0;
-            },
-            [&](int r, u64 v) { sm[C::at(Gm::jslot(r) * Gm::NC + Gm::col(r), Gm::elem(r))] = v; });
+    if (!paired) {
+        if constexpr (Gm::PAIRED && FHE_NTT_PAIRED_FALLBACK_ROLLED) {
+            // the rare unit whose jobs read different sources: a rolled loop
+            // (small code beside the paired path)
+#pragma unroll 1
+            for (int k = 0; k < 16; k++) {
+                const int r = tid + k * T, j = Gm::jslot(r);
+                sm[C::at(j * Gm::NC + Gm::col(r), Gm::elem(r))] =
+                    j < nvalid ? io.load(sts[j], (Gm::elem(r) << N2) + lo0 + Gm::col(r)) : 0;
+            }
+        } else {
+            tile_in<IO::LDCH>(
+                tid,
+                [&](int r) {
+                    const int j = Gm::jslot(r);
+                    return j < nvalid ? io.load(sts[j], (Gm::elem(r) << N2) + lo0 + Gm::col(r)) : 0;
+                },
+                [&](int r, u64 v) { sm[C::at(Gm::jslot(r) * Gm::NC + Gm::col(r), Gm::elem(r))] = v; });
+        }
+    }
     tws.store(W);
     __syncthreads();
     subtx<N1, true>(sm, tid, ColTw<N1, N2, IO::XJ>{W, q0, q1});
@@ -1465,7 +1492,7 @@ void launch_segments(fhe_ctx *c, IO &io, bool fwd)
         case 15: launch_passes<IO, 15, 15>(c, io, fwd); break;
         default: break;
         }
-    } else if (lo >= 13 && hi <= 15) {
+    } else if (FHE_NTT_MIXED_KERNEL && lo >= 13 && hi <= 15) {
         launch_passes<IO, 13, 15>(c, io, fwd);
     } else {
         for (int n = lo; n <= hi; n++) {
