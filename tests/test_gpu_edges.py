@@ -308,3 +308,47 @@ def test_checkpoint_resume_of_ciphertexts():
     finally:
         free(*b)
         free(*other)
+
+
+
+def test_pool_size_classes_reuse_nearby_sizes():
+    """The pool hands out blocks in size classes of a quarter power of two: a
+    983,040-byte ciphertext (3 x 2 x 5 limbs of 2^12 words) takes a 1 MiB
+    block; once freed, that block serves a 1,048,576-byte ciphertext
+    (4 x 2 x 4 limbs) without reserving more device memory, and both
+    ciphertexts survive the round trip through the host."""
+    from paper_2407_07308_gb300 import fhe
+
+    ctx = fhe.fhe_ctx_create(12, 17, 6, 2, CHAIN50["U"], CHAIN50["lo"], CHAIN50["hi"])
+    try:
+        rng = np.random.default_rng(3)
+        q = np.array(fhe.fhe_ctx_primes(ctx)[:6], dtype=np.uint64).reshape(1, 1, 6, 1)
+
+        def data(count, level):
+            x = rng.integers(0, 1 << 62, size=(count, 2, level, 4096), dtype=np.uint64)
+            return np.ascontiguousarray(x % q[:, :, :level])
+
+        fhe.fhe_ctx_sync(ctx)
+        fhe.fhe_ctx_trim(ctx)
+        r0, u0 = fhe.fhe_ctx_memory(ctx)
+        a_data = data(3, 5)
+        assert a_data.nbytes == 983040
+        a = fhe.fhe_ct_import_coeff(ctx, a_data)
+        fhe.fhe_ctx_sync(ctx)
+        r1, u1 = fhe.fhe_ctx_memory(ctx)
+        assert u1 - u0 == 1 << 20 and r1 - r0 == 1 << 20
+        assert np.array_equal(fhe.fhe_ct_export_coeff(ctx, a), a_data)
+        fhe.fhe_ct_destroy(a)
+        fhe.fhe_ctx_sync(ctx)
+        r2, u2 = fhe.fhe_ctx_memory(ctx)
+        assert u2 == u0
+        e_data = data(4, 4)
+        assert e_data.nbytes == 1 << 20
+        e = fhe.fhe_ct_import_coeff(ctx, e_data)
+        fhe.fhe_ctx_sync(ctx)
+        r3, u3 = fhe.fhe_ctx_memory(ctx)
+        assert r3 == r2 and u3 - u2 == 1 << 20  # a freed 1 MiB block, reused
+        assert np.array_equal(fhe.fhe_ct_export_coeff(ctx, e), e_data)
+        fhe.fhe_ct_destroy(e)
+    finally:
+        fhe.fhe_ctx_destroy(ctx)
