@@ -268,10 +268,10 @@ CLASS_SOURCES = {
     "elementwise": ("many.cu",),
 }
 DRAM_PER_ALGORITHMIC = {
-    "ntt_modup": (1.77, "b990667556b21a71"),
-    "ntt_moddown": (1.25, "b990667556b21a71"),
-    "ntt_inv": (1.1, "66f183f704d888fb"),
-    "ntt_modswitch": (1.41, "95c21f45efc3d481"),
+    "ntt_modup": (1.77, "c936d41d47aa1df1"),
+    "ntt_moddown": (1.25, "c936d41d47aa1df1"),
+    "ntt_inv": (1.1, "f0990f15d8eaeffa"),
+    "ntt_modswitch": (1.41, "f2370b07dc3f0bc0"),
     "ks_inner": (0.8, "40d58120e5917eba"),
     "elementwise": (0.86, "40d58120e5917eba"),
     "tensor": (0.63, "40d58120e5917eba"),

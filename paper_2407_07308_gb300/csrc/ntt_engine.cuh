@@ -218,9 +218,9 @@ struct RowTw {
     }
 };
 
-// Round 1: thread t = (g, c) with c = t % NS, g = t / NS holds elements
+// Radix-16 round: thread t = (g, c) with c = t % NS, g = t / NS holds elements
 // e = k G + g (k < 16) of sub-transform c: local stages 0..3.
-// Round 2: thread t = (c, g') with c = t / G, g' = t % G holds the 16/G
+// Remaining-stages round: thread t = (c, g') with c = t / G, g' = t % G holds the 16/G
 // blocks b = g' (16/G) + i of G contiguous elements: local stages 4..M-1.
 // geo gives each sub-transform's twiddle accessor, block index and prime.
 template <int M, bool FWD, class Geo>

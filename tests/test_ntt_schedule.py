@@ -2,8 +2,8 @@
 (emulated thread by thread in Python, exact arithmetic mod a small prime):
 
 - a unit of 128 threads x 16 residues holds NS = 2^(11-M) sub-transforms of
-  2^M points (M = 5..8); round 1 (threads t -> sub-transform t % NS, residues
-  k G + t / NS) and round 2 (t -> sub-transform t / G, blocks of G contiguous
+  2^M points (M = 5..8); the radix-16 round (threads t -> sub-transform t % NS, residues
+  k G + t / NS) and the remaining-stages round (t -> sub-transform t / G, blocks of G contiguous
   residues) together compute, forward and inverse, the same as the plain
   radix-2 stages of every sub-transform;
 - the column units of every ring degree 2^10..2^15 (NC columns of NJ jobs),
