@@ -12,6 +12,7 @@
 
 #include "../../include/fhe.h"
 #include "modarith.cuh"
+#include "pdl.cuh"
 
 #include <nvtx3/nvToolsExt.h>
 

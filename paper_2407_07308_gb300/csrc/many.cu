@@ -141,6 +141,7 @@ __device__ __forceinline__ void ew_block(const EwSeg &S)
 
 __global__ void k_ew_many(const __grid_constant__ EwTable t)
 {
+    pdl_begin();
     const EwSeg &S = t.s[block_seg(t.s, t.nseg)];
     if (S.vec)
         ew_block<2>(S);
@@ -165,6 +166,7 @@ struct TensorTable {
 
 __global__ void k_tensor_many(const __grid_constant__ TensorTable t)
 {
+    pdl_begin();
     const TensorSeg &S = t.s[block_seg(t.s, t.nseg)];
     const long long LN = (long long)S.level << S.logN;
     const long long base = (long long)(blockIdx.x - S.b0) * EW_ELEMS;
@@ -204,6 +206,7 @@ struct KsTable {
 
 __global__ void __launch_bounds__(TPB, 3) k_ks_inner_many(const __grid_constant__ KsTable t)
 {
+    pdl_begin();
     const KsSeg &S = t.s[block_seg(t.s, t.nseg)];
     const int lb = blockIdx.x - S.b0;
     const int lK = S.l + S.K, N = 1 << S.logN;
@@ -278,6 +281,7 @@ struct FoldTable {
 // multi-switch: src[o] = (X'_0 .. X'_{k-1}) -> w_j = X'_j - sum_{t<j} w_t F[j][t].
 __global__ void k_fold_many(const __grid_constant__ FoldTable t)
 {
+    pdl_begin();
     const FoldSeg &S = t.s[block_seg(t.s, t.nseg)];
     const int N = 1 << S.logN;
     const long long base = (long long)(blockIdx.x - S.b0) * EW_ELEMS;
@@ -368,7 +372,7 @@ void launch_ew_many(const std::vector<EwArgs> &items)
             *bytes = 8.0 * (reads + 1) * S.total;
             return ew_blocks(S.total);
         },
-        [](const EwTable &t, int blocks, cudaStream_t s) { k_ew_many<<<blocks, TPB, 0, s>>>(t); });
+        [](const EwTable &t, int blocks, cudaStream_t s) { launch_pdl(k_ew_many, blocks, TPB, s, t); });
 }
 
 void launch_tensor_many(const std::vector<TensorArgs> &items)
@@ -387,7 +391,7 @@ void launch_tensor_many(const std::vector<TensorArgs> &items)
             *bytes = 8.0 * 7 * S.total;
             return ew_blocks(S.total);
         },
-        [](const TensorTable &t, int blocks, cudaStream_t s) { k_tensor_many<<<blocks, TPB, 0, s>>>(t); });
+        [](const TensorTable &t, int blocks, cudaStream_t s) { launch_pdl(k_tensor_many, blocks, TPB, s, t); });
 }
 
 void launch_ks_inner_many(const std::vector<KsInnerArgs> &items)
@@ -414,7 +418,7 @@ void launch_ks_inner_many(const std::vector<KsInnerArgs> &items)
             *bytes = 8.0 * (double)(a.level + c->K) * c->N * (2.0 * S.dnum + a.count * (S.dnum + 2.0));
             return S.nbx * (a.level + c->K) * ((a.count + KS_CB - 1) / KS_CB);
         },
-        [](const KsTable &t, int blocks, cudaStream_t s) { k_ks_inner_many<<<blocks, TPB, 0, s>>>(t); });
+        [](const KsTable &t, int blocks, cudaStream_t s) { launch_pdl(k_ks_inner_many, blocks, TPB, s, t); });
 }
 
 void launch_rms_fold_many(const std::vector<FoldArgs> &items)
@@ -436,7 +440,7 @@ void launch_rms_fold_many(const std::vector<FoldArgs> &items)
         },
         [](FoldTable &t, int blocks, cudaStream_t s) {
             t.rms = 1;
-            k_fold_many<<<blocks, TPB, 0, s>>>(t);
+            launch_pdl(k_fold_many, blocks, TPB, s, t);
         });
 }
 
@@ -459,6 +463,6 @@ void launch_ms_fold_many(const std::vector<FoldArgs> &items)
         },
         [](FoldTable &t, int blocks, cudaStream_t s) {
             t.rms = 0;
-            k_fold_many<<<blocks, TPB, 0, s>>>(t);
+            launch_pdl(k_fold_many, blocks, TPB, s, t);
         });
 }

@@ -846,6 +846,7 @@ template <class IO, int LO, int HI>
 __global__ void __launch_bounds__(T, IO::XJ == 2 ? FHE_NTT_MINB_PAIRED : FHE_NTT_MINB)
     k_fwd_cols(const __grid_constant__ IO io)
 {
+    pdl_begin();
     __shared__ u64 sm[SM_WORDS];
     __shared__ ulonglong2 W[TW_WORDS];
     __shared__ typename IO::St sts[ROW_J];
@@ -861,6 +862,7 @@ __global__ void __launch_bounds__(T, IO::XJ == 2 ? FHE_NTT_MINB_PAIRED : FHE_NTT
 template <class IO, int LO, int HI>
 __global__ void __launch_bounds__(T, FHE_NTT_MINB) k_fwd_rows(const __grid_constant__ IO io)
 {
+    pdl_begin();
     __shared__ u64 sm[SM_WORDS];
     __shared__ ulonglong2 W[TW_WORDS];
     __shared__ typename IO::St sts[ROW_J];
@@ -881,6 +883,7 @@ __global__ void __launch_bounds__(T, FHE_NTT_MINB) k_fwd_rows(const __grid_const
 template <class IO, int LO, int HI>
 __global__ void __launch_bounds__(T, FHE_NTT_MINB) k_inv_rows(const __grid_constant__ IO io)
 {
+    pdl_begin();
     __shared__ u64 sm[SM_WORDS];
     __shared__ ulonglong2 W[TW_WORDS];
     __shared__ typename IO::St sts[ROW_J];
@@ -901,6 +904,7 @@ __global__ void __launch_bounds__(T, FHE_NTT_MINB) k_inv_rows(const __grid_const
 template <class IO, int LO, int HI>
 __global__ void __launch_bounds__(T, FHE_NTT_MINB) k_inv_cols(const __grid_constant__ IO io)
 {
+    pdl_begin();
     __shared__ u64 sm[SM_WORDS];
     __shared__ ulonglong2 W[TW_WORDS];
     __shared__ typename IO::St sts[ROW_J];
@@ -1464,11 +1468,11 @@ template <class IO, int LO, int HI>
 void launch_passes(fhe_ctx *c, const IO &io, bool fwd)
 {
     if (fwd) {
-        k_fwd_cols<IO, LO, HI><<<grid_of(c, io.ucols), T, 0, c->stream>>>(io);
-        k_fwd_rows<IO, LO, HI><<<grid_of(c, io.urows), T, 0, c->stream>>>(io);
+        launch_pdl(k_fwd_cols<IO, LO, HI>, grid_of(c, io.ucols), T, c->stream, io);
+        launch_pdl(k_fwd_rows<IO, LO, HI>, grid_of(c, io.urows), T, c->stream, io);
     } else {
-        k_inv_rows<IO, LO, HI><<<grid_of(c, io.urows), T, 0, c->stream>>>(io);
-        k_inv_cols<IO, LO, HI><<<grid_of(c, io.ucols), T, 0, c->stream>>>(io);
+        launch_pdl(k_inv_rows<IO, LO, HI>, grid_of(c, io.urows), T, c->stream, io);
+        launch_pdl(k_inv_cols<IO, LO, HI>, grid_of(c, io.ucols), T, c->stream, io);
     }
     c->launches += 2;
 }
