@@ -268,13 +268,13 @@ CLASS_SOURCES = {
     "elementwise": ("many.cu",),
 }
 DRAM_PER_ALGORITHMIC = {
-    "ntt_modup": (1.77, "c936d41d47aa1df1"),
-    "ntt_moddown": (1.25, "c936d41d47aa1df1"),
-    "ntt_inv": (1.1, "f0990f15d8eaeffa"),
-    "ntt_modswitch": (1.41, "f2370b07dc3f0bc0"),
-    "ks_inner": (0.8, "40d58120e5917eba"),
-    "elementwise": (0.86, "40d58120e5917eba"),
-    "tensor": (0.63, "40d58120e5917eba"),
+    "ntt_modup": (1.77, "dad608fa5deb7bc1"),
+    "ntt_moddown": (1.25, "dad608fa5deb7bc1"),
+    "ntt_inv": (1.1, "32176d7e82710f69"),
+    "ntt_modswitch": (1.41, "ddebabb848a5971b"),
+    "ks_inner": (0.8, "ba759a083a793416"),
+    "elementwise": (0.86, "ba759a083a793416"),
+    "tensor": (0.63, "ba759a083a793416"),
 }
 
 
