@@ -335,7 +335,9 @@ def run_gpu(args):
                          f"one spawned process "
                          f"per pair; {statistics.mean(per):.1f} s per pair on average"}
 
-    stream = torch.cuda.Stream()
+    # high priority: in the end-to-end pass the next step's uploads run on a
+    # default-priority stream beside the replay
+    stream = torch.cuda.Stream(priority=-1)
     alloc = fhe.torch_allocator(local)
     with torch.cuda.stream(stream):
         ctx = fhe.fhe_ctx_create(W["logN"], W["p"], W["L"], W["K"], W["U"], W["lo"], W["hi"], allocator=alloc,
