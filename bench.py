@@ -519,15 +519,18 @@ def run_gpu(args):
 
 
 def run_secondary(args):
-    """Short runs of the uneven batch (fused form only) and of the serving
-    loop, each in a child process after the headline has released its
-    contexts, so that their rates are recorded beside the headline."""
+    """Short runs of the uneven batch (fused form only), of the serving loop
+    and of the 4096-value max/min tournament, each in a child process after
+    the headline has released its contexts, so that their rates are recorded
+    beside the headline."""
     import torch
 
     torch.cuda.empty_cache()  # the children allocate on the same device
     out = {}
     for name, extra in (("uneven", ["--workload", "uneven", "--quick", "--steps", "2", "--warmup", "3", "--no-plain"]),
-                        ("serve", ["--workload", "serve", "--serve-requests", "24", "--warmup", "3"])):
+                        ("serve", ["--workload", "serve", "--serve-requests", "24", "--warmup", "3"]),
+                        ("tournament", ["--workload", "tournament", "--steps", "2", "--warmup", "3",
+                                        "--no-cpu-baseline"])):
         cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--no-secondary"] + extra
         try:
             r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
@@ -539,7 +542,7 @@ def run_secondary(args):
             out[name] = {"error": "the child run failed"}
             continue
         keep = ("metric", "value", "unit", "ms_per_step", "launches_per_step", "latency_ms_p50", "latency_ms_p99",
-                "requests_per_s", "latency_ms_by_kind", "clocks")
+                "requests_per_s", "latency_ms_by_kind", "tournament_ms_p50", "clocks")
         out[name] = {k: d[k] for k in keep if k in d}
         out[name]["workload"] = d["config"]["workload"]
     return out

@@ -189,7 +189,13 @@ __global__ void k_tensor_many(const __grid_constant__ TensorTable t)
 // extended limb r for CB ciphertexts; each thread loads its 2 dnum key words
 // once for its CB ciphertexts.
 
-constexpr int KS_CB = 4;
+#ifndef FHE_KS_CB
+#define FHE_KS_CB 4
+#endif
+#ifndef FHE_KS_MINB
+#define FHE_KS_MINB 3
+#endif
+constexpr int KS_CB = FHE_KS_CB;  // ciphertexts per thread (key words reused across them)
 
 struct KsSeg {
     const u64 *ext, *xbase, *ksk;
@@ -204,7 +210,7 @@ struct KsTable {
     KsSeg s[FHE_SEGS];
 };
 
-__global__ void __launch_bounds__(TPB, 3) k_ks_inner_many(const __grid_constant__ KsTable t)
+__global__ void __launch_bounds__(TPB, FHE_KS_MINB) k_ks_inner_many(const __grid_constant__ KsTable t)
 {
     pdl_begin();
     const KsSeg &S = t.s[block_seg(t.s, t.nseg)];
