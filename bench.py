@@ -272,9 +272,9 @@ DRAM_PER_ALGORITHMIC = {
     "ntt_moddown": (1.25, "dad608fa5deb7bc1"),
     "ntt_inv": (1.1, "32176d7e82710f69"),
     "ntt_modswitch": (1.41, "ddebabb848a5971b"),
-    "ks_inner": (0.8, "ba759a083a793416"),
-    "elementwise": (0.86, "ba759a083a793416"),
-    "tensor": (0.63, "ba759a083a793416"),
+    "ks_inner": (0.8, "92a1832192a6df6b"),
+    "elementwise": (0.86, "92a1832192a6df6b"),
+    "tensor": (0.63, "92a1832192a6df6b"),
 }
 
 
