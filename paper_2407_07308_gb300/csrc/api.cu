@@ -1606,6 +1606,8 @@ extern "C" int fhe_selftest_modarith(uint64_t prime_mod, uint64_t prime_lo, uint
             for (int k = 0; k < 8; k++) {
                 acc += (u128)a[k] * b[k];
                 if (barrett128(acc, m) != (u64)(acc % q)) bad++;
+                const u64 bl = barrett128_lazy(acc, m);
+                if (bl >= 3 * q || bl % q != (u64)(acc % q)) bad++;
                 if (mulmod(a[k], b[k], m) != (u64)(((u128)a[k] * b[k]) % q)) bad++;
             }
             // Shoup with any 64-bit multiplicand
@@ -1614,6 +1616,7 @@ extern "C" int fhe_selftest_modarith(uint64_t prime_mod, uint64_t prime_lo, uint
             if (lz >= 2 * q || lz % q != (u64)(((u128)x * w) % q)) bad++;
             const u64 l4 = shoup_lazy4(x, w, ws, q);
             if (l4 >= 4 * q || l4 % q != (u64)(((u128)x * w) % q)) bad++;
+            if (shoup_lazy4_chain(x, w, ws, 0 - q) != l4) bad++;
             if (shoup(x, w, ws, q) != (u64)(((u128)x * w) % q)) bad++;
             if (reduce4q(4 * q - 1 - (x % (4 * q)), 2 * q, q) != (4 * q - 1 - (x % (4 * q))) % q) bad++;
             const u64 v = edge ? (it < 32 ? ~0ull - (u64)it : 31 * q - 1 - (u64)it) : rnd();

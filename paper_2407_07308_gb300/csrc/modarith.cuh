@@ -67,6 +67,48 @@ FHE_HD u64 shoup_lazy4(u64 a, u64 w, u64 ws, u64 q)
     return a * w - qhat * q;
 }
 
+// shoup_lazy4 as one multiply-add chain: with nq = 2^64 - q, a w - qhat q =
+// a w + qhat nq (mod 2^64), so on the device the low words of a w and of
+// qhat nq are summed by a wide multiply-add and the high word by four 32-bit
+// multiply-adds, with no separate 64-bit subtraction.  Same result as
+// shoup_lazy4 for every input (the host form is that expression in C).
+FHE_HD u64 shoup_lazy4_chain(u64 a, u64 w, u64 ws, u64 nq)
+{
+#ifdef __CUDA_ARCH__
+    u64 r;
+    asm("{\n\t"
+        ".reg .u32 al, ah, wl, wh, sl, sh, ql, qh, t1, t2, hl, hh, rl, rh;\n\t"
+        ".reg .u64 qhat, t12, lo;\n\t"
+        "mov.b64 {al, ah}, %1;\n\t"
+        "mov.b64 {wl, wh}, %2;\n\t"
+        "mov.b64 {sl, sh}, %3;\n\t"
+        "mov.b64 {ql, qh}, %4;\n\t"
+        "mul.hi.u32 t1, ah, sl;\n\t"
+        "mul.hi.u32 t2, al, sh;\n\t"
+        "add.cc.u32 t1, t1, t2;\n\t"
+        "addc.u32 t2, 0, 0;\n\t"
+        "mov.b64 t12, {t1, t2};\n\t"
+        "mad.wide.u32 qhat, ah, sh, t12;\n\t"
+        "mov.b64 {hl, hh}, qhat;\n\t"
+        "mul.wide.u32 lo, al, wl;\n\t"
+        "mad.wide.u32 lo, hl, ql, lo;\n\t"
+        "mov.b64 {rl, rh}, lo;\n\t"
+        "mad.lo.u32 rh, ah, wl, rh;\n\t"
+        "mad.lo.u32 rh, al, wh, rh;\n\t"
+        "mad.lo.u32 rh, hh, ql, rh;\n\t"
+        "mad.lo.u32 rh, hl, qh, rh;\n\t"
+        "mov.b64 %0, {rl, rh};\n\t"
+        "}"
+        : "=l"(r)
+        : "l"(a), "l"(w), "l"(ws), "l"(nq));
+    return r;
+#else
+    const uint32_t al = (uint32_t)a, ah = (uint32_t)(a >> 32), wl = (uint32_t)ws, wh = (uint32_t)(ws >> 32);
+    const u64 qhat = (u64)ah * wh + ((((u64)ah * wl) >> 32) + (((u64)al * wh) >> 32));
+    return a * w + qhat * nq;
+#endif
+}
+
 FHE_HD u64 shoup(u64 a, u64 w, u64 ws, u64 q)
 {
     u64 r = shoup_lazy(a, w, ws, q);
@@ -84,6 +126,15 @@ FHE_HD u64 barrett128(u128 x, const ModQ &m)
     if (r >= m.q2) r -= m.q2;
     if (r >= m.q) r -= m.q;
     return r;
+}
+
+// The same reduction without its two corrections: a residue of x in [0, 3q).
+FHE_HD u64 barrett128_lazy(u128 x, const ModQ &m)
+{
+    u64 lo = (u64)x, hi = (u64)(x >> 64);
+    int s = m.bshift;
+    u64 t = (hi << (64 - s)) | (lo >> s);
+    return lo - fhe_mulhi(t, m.mu) * m.q;
 }
 
 FHE_HD u64 mulmod(u64 a, u64 b, const ModQ &m) { return barrett128((u128)a * b, m); }

@@ -42,9 +42,9 @@ __global__ void k_probe_mulhi64(u64 *out, u64 seed)
 }
 
 // The NTT's butterfly (Harvey's lazy forward butterfly with a Shoup twiddle
-// whose quotient is estimated from three 32-bit partial products, the form
-// the NTT kernels use: t = Y w - qhat q in [0, 4q), X <- X + t,
-// Y <- X - t + 4q) on 8
+// whose quotient is estimated from three 32-bit partial products, in the
+// multiply-add chain the NTT kernels use: t = Y w - qhat q in [0, 4q),
+// X <- X + t, Y <- X - t + 4q) on 8
 // register-resident values per thread, three butterfly layers per iteration
 // (strides 4, 2, 1) so that every value depends on every other: the roof of
 // the NTT's arithmetic with no memory traffic at all.
@@ -55,14 +55,14 @@ __global__ void k_probe_bfly(u64 *out, u64 seed, u64 q, u64 w, u64 ws)
     u64 x[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) x[k] = seed + threadIdx.x * 8 + k;
-    const u64 q4 = 4 * q;
+    const u64 q4 = 4 * q, nq = 0 - q;
     for (int i = 0; i < BFLY_ITERS; i++) {
 #pragma unroll
         for (int h = 4; h >= 1; h >>= 1) {
 #pragma unroll
             for (int k = 0; k < 8; k++) {
                 if (k & h) continue;
-                const u64 t = shoup_lazy4(x[k + h], w, ws, q);
+                const u64 t = shoup_lazy4_chain(x[k + h], w, ws, nq);
                 const u64 a = x[k];
                 x[k] = a + t;
                 x[k + h] = a - t + q4;
