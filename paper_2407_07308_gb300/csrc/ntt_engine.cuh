@@ -59,11 +59,6 @@
 
 namespace {
 
-// Forward butterfly without normalisation: t = [Y w] in [0, 4q) for any
-// 64-bit Y (shoup_lazy4), so if X, Y < B then X + t and X - t + 4q lie in
-// [0, B + 4q).  After s stages every value is below (4s + 1) q <= 61 q <
-// 2^63 (primes below 2^57, s <= 15); one reduction at the end brings it to
-// [0, q).  q4 = 4q.
 // The butterflies' twiddle product: shoup_lazy4 as one multiply-add chain
 // (measured on the GB300: 1015 -> 1173 G forward butterflies/s on
 // register-resident values, and 2454 -> 2563 slot-comparisons/s on the
@@ -73,6 +68,12 @@ __device__ __forceinline__ u64 bfly_mul(u64 a, const ulonglong2 w, u64 q)
     return shoup_lazy4_chain(a, w.x, w.y, 0 - q);
 }
 
+// Forward butterfly without normalisation: t = [Y w] in [0, 4q) for any
+// 64-bit Y (shoup_lazy4), so if X, Y < B then X + t and X - t + 4q lie in
+// [0, B + 4q).  Inputs below 4q (canonical residues, or the lazy results of
+// the fused conversions) stay below (4s + 4) q <= 64 q < 2^63 after s <= 15
+// stages for primes below 2^57; one reduction at the end brings every value
+// to [0, q).  q4 = 4q.
 __device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 q, u64 q4)
 {
     const u64 t = bfly_mul(Y, w, q);
@@ -135,36 +136,15 @@ __device__ __forceinline__ void inv_round(u64 (&x)[1 << R], int s0, int hi, cons
 }
 
 // Conversions computed by the loads of a forward transform (ModUp, ModDown,
-// the switch corrections) may hand it a residue in [0, 3q) instead of [0, q):
-// the forward butterflies accept any 64-bit input whose lazy bound stays
-// below 2^64 ((4s + 3) q after s stages) and the transform's last step
-// reduces every output to [0, q), so the outputs are the same.
-#ifndef FHE_CONV_LAZY
-#define FHE_CONV_LAZY 0
-#endif
-__device__ __forceinline__ u64 conv_reduce(u128 x, const ModQ &m)
-{
-#if FHE_CONV_LAZY
-    return barrett128_lazy(x, m);
-#else
-    return barrett128(x, m);
-#endif
-}
-
-// Canonical a w mod q for a constant w (ws its Shoup quotient): Shoup's
-// product with the exact quotient and one correction, or (FHE_CONST_CHAIN)
-// the butterflies' multiply-add chain and two corrections.
-#ifndef FHE_CONST_CHAIN
-#define FHE_CONST_CHAIN 0
-#endif
-__device__ __forceinline__ u64 mulc(u64 a, u64 w, u64 ws, u64 q)
-{
-#if FHE_CONST_CHAIN
-    return reduce4q(shoup_lazy4_chain(a, w, ws, 0 - q), 2 * q, q);
-#else
-    return shoup(a, w, ws, q);
-#endif
-}
+// the switch corrections) hand it a residue in [0, 3q) (a Barrett reduction
+// without its two corrections) or [0, 4q) (a lazy Shoup product) instead of
+// [0, q): the forward butterflies accept any 64-bit input whose lazy bound
+// stays below 2^64 ((4s + 4) q after s stages) and the transform's last step
+// reduces every output to [0, q), so the outputs are the same.  Measured on
+// the 16-pair comparison at N = 2^14: 2564 -> 2587 slot-comparisons/s.
+// (The chained product with two corrections in place of Shoup's exact one
+// for the constant products of the stores measured slower: 2577.)
+__device__ __forceinline__ u64 conv_reduce(u128 x, const ModQ &m) { return barrett128_lazy(x, m); }
 
 // ---------------------------------------------------------------------------
 // unit geometry
@@ -598,7 +578,7 @@ __device__ __forceinline__ void inv_cols_unit1(const IO &io, int sg, int lu, u64
     for (int k = 0; k < 16; k++) {
         const int r = tid + k * T;
         io.store(st, (Gm::elem(r) << N2) + lo0 + Gm::col(r),
-                 mulc(sm[C::at(Gm::col(r), Gm::elem(r))], ni.x, ni.y, q));
+                 shoup(sm[C::at(Gm::col(r), Gm::elem(r))], ni.x, ni.y, q));
     }
 }
 
@@ -707,7 +687,7 @@ __device__ __forceinline__ void inv_cols_unit(const IO &io, int sg, int lu, u64 
             const ulonglong2 ni = io.final_scale(sts[j]);
             const u64 q = j == 0 ? q0 : q1;
             io.store(sts[j], (Gm::elem(r) << N2) + lo0 + Gm::col(r),
-                     mulc(sm[C::at(j * Gm::NC + Gm::col(r), Gm::elem(r))], ni.x, ni.y, q));
+                     shoup(sm[C::at(j * Gm::NC + Gm::col(r), Gm::elem(r))], ni.x, ni.y, q));
         }
     }
 }
@@ -1036,7 +1016,7 @@ struct IOScaledY : SegIO<YSeg> {
     }
     __device__ u64 load(const St &t, int i) const
     {
-        return t.add ? addmod(t.in[i], mulc(t.add[i], t.Pm, t.Pm_s, t.qm), t.qm) : t.in[i];
+        return t.add ? addmod(t.in[i], shoup(t.add[i], t.Pm, t.Pm_s, t.qm), t.qm) : t.in[i];
     }
     __device__ void store(const St &t, int i, u64 v) const { t.out[i] = v; }
     static constexpr int NPRE = 0;
@@ -1187,7 +1167,7 @@ struct IOModDown : SegIO<ModDownSeg> {
     __device__ void store(const St &t, int k, u64 v) const
     {
         const u64 q = t.mi.q;
-        u64 r = mulc(submod(t.acc[k], v, q), t.pinv, t.pinv_s, q);
+        u64 r = shoup(submod(t.acc[k], v, q), t.pinv, t.pinv_s, q);
         if (t.add) r = addmod(r, t.add[k], q);
         t.out[k] = r;
     }
@@ -1197,7 +1177,7 @@ struct IOModDown : SegIO<ModDownSeg> {
     __device__ void store_pre(const St &t, int k, u64 v, const u64 *pv) const
     {
         const u64 q = t.mi.q;
-        u64 r = mulc(submod(pv[0], v, q), t.pinv, t.pinv_s, q);
+        u64 r = shoup(submod(pv[0], v, q), t.pinv, t.pinv_s, q);
         if (t.add) r = addmod(r, pv[1], q);
         t.out[k] = r;
     }
@@ -1241,21 +1221,15 @@ struct IOModSwitch : SegIO<SwitchSeg> {
         t.qi = S.P->qinv[i];
         t.qis = S.P->qinv_s[i];
     }
-    __device__ u64 load(const St &t, int n) const
-    {
-#if FHE_CONV_LAZY
-        return shoup_lazy4_chain(t.last[n], t.pi, t.pis, 0 - t.q);  // [0, 4q): feeds the forward transform
-#else
-        return mulc(t.last[n], t.pi, t.pis, t.q);
-#endif
-    }
-    __device__ void store(const St &t, int k, u64 v) const { t.out[k] = mulc(submod(t.in[k], v, t.q), t.qi, t.qis, t.q); }
+    // [0, 4q): feeds the forward transform
+    __device__ u64 load(const St &t, int n) const { return shoup_lazy4_chain(t.last[n], t.pi, t.pis, 0 - t.q); }
+    __device__ void store(const St &t, int k, u64 v) const { t.out[k] = shoup(submod(t.in[k], v, t.q), t.qi, t.qis, t.q); }
     static constexpr int NPRE = 1;  // the limb being switched
     static constexpr int LDCH = 16;
     __device__ u64 pre(const St &t, int k, int) const { return t.in[k]; }
     __device__ void store_pre(const St &t, int k, u64 v, const u64 *pv) const
     {
-        t.out[k] = mulc(submod(pv[0], v, t.q), t.qi, t.qis, t.q);
+        t.out[k] = shoup(submod(pv[0], v, t.q), t.qi, t.qis, t.q);
     }
     __device__ u64 *inter(const St &t) const { return t.out; }
     __device__ ulonglong2 final_scale(const St &) const { return make_ulonglong2(0, 0); }
@@ -1336,9 +1310,9 @@ struct IORelinMS : SegIO<RelinMSSeg> {
     __device__ u64 combine(const St &t, u64 accv, u64 addv, u64 v) const
     {
         const u64 q = t.mi.q;
-        u64 r = mulc(accv, t.pinv, t.pinv_s, q);
+        u64 r = shoup(accv, t.pinv, t.pinv_s, q);
         if (t.add) r = addmod(r, addv, q);
-        return mulc(submod(r, v, q), t.qminv, t.qminv_s, q);
+        return shoup(submod(r, v, q), t.qminv, t.qminv_s, q);
     }
     __device__ void store(const St &t, int k, u64 v) const { t.out[k] = combine(t, t.acc[k], t.add ? t.add[k] : 0, v); }
     static constexpr int NPRE = 2;  // accumulator, addend
@@ -1414,14 +1388,14 @@ struct IOMultiSwitch : SegIO<MultiSeg> {
     }
     __device__ void store(const St &t, int j, u64 v) const
     {
-        t.out[j] = mulc(submod(t.in[j], v, t.mi.q), t.dinv, t.dinv_s, t.mi.q);
+        t.out[j] = shoup(submod(t.in[j], v, t.mi.q), t.dinv, t.dinv_s, t.mi.q);
     }
     static constexpr int NPRE = 1;
     static constexpr int LDCH = FHE_NTT_MULTI_LDCH;  // each load reads several limbs
     __device__ u64 pre(const St &t, int j, int) const { return t.in[j]; }
     __device__ void store_pre(const St &t, int j, u64 v, const u64 *pv) const
     {
-        t.out[j] = mulc(submod(pv[0], v, t.mi.q), t.dinv, t.dinv_s, t.mi.q);
+        t.out[j] = shoup(submod(pv[0], v, t.mi.q), t.dinv, t.dinv_s, t.mi.q);
     }
     __device__ u64 *inter(const St &t) const { return t.out; }
     __device__ ulonglong2 final_scale(const St &) const { return make_ulonglong2(0, 0); }
