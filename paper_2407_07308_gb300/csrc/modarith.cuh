@@ -70,7 +70,9 @@ FHE_HD u64 shoup_lazy4(u64 a, u64 w, u64 ws, u64 q)
 // shoup_lazy4 as one multiply-add chain: with nq = 2^64 - q, a w - qhat q =
 // a w + qhat nq (mod 2^64), so on the device the low words of a w and of
 // qhat nq are summed by a wide multiply-add and the high word by four 32-bit
-// multiply-adds, with no separate 64-bit subtraction.  Same result as
+// multiply-adds, with no separate 64-bit subtraction; the two high partial
+// products of the quotient are summed by a wide multiply-add too (t1 * 1 +
+// t2), so the whole product runs on the multiply-add pipe.  Same result as
 // shoup_lazy4 for every input (the host form is that expression in C).
 FHE_HD u64 shoup_lazy4_chain(u64 a, u64 w, u64 ws, u64 nq)
 {
@@ -78,16 +80,15 @@ FHE_HD u64 shoup_lazy4_chain(u64 a, u64 w, u64 ws, u64 nq)
     u64 r;
     asm("{\n\t"
         ".reg .u32 al, ah, wl, wh, sl, sh, ql, qh, t1, t2, hl, hh, rl, rh;\n\t"
-        ".reg .u64 qhat, t12, lo;\n\t"
+        ".reg .u64 qhat, t12, lo, t2w;\n\t"
         "mov.b64 {al, ah}, %1;\n\t"
         "mov.b64 {wl, wh}, %2;\n\t"
         "mov.b64 {sl, sh}, %3;\n\t"
         "mov.b64 {ql, qh}, %4;\n\t"
         "mul.hi.u32 t1, ah, sl;\n\t"
         "mul.hi.u32 t2, al, sh;\n\t"
-        "add.cc.u32 t1, t1, t2;\n\t"
-        "addc.u32 t2, 0, 0;\n\t"
-        "mov.b64 t12, {t1, t2};\n\t"
+        "cvt.u64.u32 t2w, t2;\n\t"
+        "mad.wide.u32 t12, t1, 1, t2w;\n\t"
         "mad.wide.u32 qhat, ah, sh, t12;\n\t"
         "mov.b64 {hl, hh}, qhat;\n\t"
         "mul.wide.u32 lo, al, wl;\n\t"

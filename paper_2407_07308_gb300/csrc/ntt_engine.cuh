@@ -59,10 +59,14 @@
 
 namespace {
 
-// The butterflies' twiddle product: shoup_lazy4 as one multiply-add chain
-// (measured on the GB300: 1015 -> 1173 G forward butterflies/s on
-// register-resident values, and 2454 -> 2563 slot-comparisons/s on the
-// 16-pair comparison at N = 2^14, with identical results).
+// The butterflies' twiddle product: shoup_lazy4 as one multiply-add chain.
+// Measured on the GB300 (16-pair comparison at N = 2^14, identical results):
+// the C form 2454 slot-comparisons/s, the chain with its quotient's two high
+// products summed by an add-with-carry 2563, by a wide multiply-add 2606
+// (register-resident forward butterflies: 1015 -> 1173 G/s for the first
+// chain).  Also measured and not kept: X + t by multiply-adds as well (2606,
+// no gain on its own: 2570), and the inverse's 4q reduction as an unsigned
+// minimum (2554).
 __device__ __forceinline__ u64 bfly_mul(u64 a, const ulonglong2 w, u64 q)
 {
     return shoup_lazy4_chain(a, w.x, w.y, 0 - q);
