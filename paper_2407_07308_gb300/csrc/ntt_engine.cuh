@@ -156,16 +156,24 @@ __device__ __forceinline__ u64 conv_reduce(u128 x, const ModQ &m) { return barre
 
 constexpr int T = 128;  // threads per CTA, 16 residues each
 
-// Register cap: FHE_NTT_MINB resident CTAs of 128 threads per SM (8: 64
+// Register cap: FHE_NTT_MINB resident CTAs of 128 threads per SM (9: 56
 // registers a thread).  Measured on the headline comparison (16 pairs,
-// N = 2^14): 8 CTAs 2291 slot-comparisons/s, 6 CTAs (80 registers) 2285, 7
-// with staged multi-limb loads 2152.
+// N = 2^14): with the C-form butterflies 8 CTAs 2291 slot-comparisons/s, 6
+// CTAs (80 registers) 2285, 7 with staged multi-limb loads 2152; with the
+// chained butterflies 7 CTAs 2574, 8 CTAs 2653, 9 CTAs 2672, and 2689 with the
+// forward row kernels of two-operand stores kept at 8 (FHE_NTT_MINB_ST2: at 9
+// they spill 116 bytes); 10 CTAs spill 170-1100 bytes.
 #ifndef FHE_NTT_MINB
-#define FHE_NTT_MINB 8
+#define FHE_NTT_MINB 9
 #endif
 // The same for the column kernels of paired units (two targets per load).
 #ifndef FHE_NTT_MINB_PAIRED
 #define FHE_NTT_MINB_PAIRED FHE_NTT_MINB
+#endif
+// The same for the forward row kernels whose stores read two operands
+// besides the transform (ModDown, relinearise + switch: accumulator, addend).
+#ifndef FHE_NTT_MINB_ST2
+#define FHE_NTT_MINB_ST2 8
 #endif
 // Paired column units whose two jobs read different sources (a digit or
 // ciphertext boundary) load in a rolled loop (1) or the unrolled staged one (0).
@@ -885,7 +893,8 @@ __global__ void __launch_bounds__(T, IO::XJ == 2 ? FHE_NTT_MINB_PAIRED : FHE_NTT
 }
 
 template <class IO, int LO, int HI>
-__global__ void __launch_bounds__(T, FHE_NTT_MINB) k_fwd_rows(const __grid_constant__ IO io)
+__global__ void __launch_bounds__(T, IO::NPRE >= 2 ? FHE_NTT_MINB_ST2 : FHE_NTT_MINB)
+    k_fwd_rows(const __grid_constant__ IO io)
 {
     pdl_begin();
     __shared__ u64 sm[SM_WORDS];
