@@ -268,13 +268,13 @@ CLASS_SOURCES = {
     "elementwise": ("many.cu",),
 }
 DRAM_PER_ALGORITHMIC = {
-    "ntt_modup": (1.77, "dad608fa5deb7bc1"),
-    "ntt_moddown": (1.25, "dad608fa5deb7bc1"),
-    "ntt_inv": (1.1, "32176d7e82710f69"),
-    "ntt_modswitch": (1.41, "ddebabb848a5971b"),
-    "ks_inner": (0.8, "92a1832192a6df6b"),
-    "elementwise": (0.86, "92a1832192a6df6b"),
-    "tensor": (0.63, "92a1832192a6df6b"),
+    "ntt_modup": (1.8, "62f98ef236093264"),
+    "ntt_moddown": (1.25, "62f98ef236093264"),
+    "ntt_inv": (1.1, "dfdb6d470d2fd9f3"),
+    "ntt_modswitch": (1.41, "6431ec87f0747706"),
+    "ks_inner": (0.8, "0ce32bc2efb401e2"),
+    "elementwise": (0.86, "0ce32bc2efb401e2"),
+    "tensor": (0.63, "0ce32bc2efb401e2"),
 }
 
 
