@@ -609,9 +609,10 @@ int fhe_ntt_inverse_batch(fhe_ctx *ctx, uint64_t *data, int count, int nprimes);
  * fraction.  Synchronises the device. */
 int fhe_probe_int_peak(double *imad32, double *mulhi64);
 /* Measured butterflies per second over all SMs: the NTT's lazy forward
- * butterfly with a Shoup twiddle (the quotient from one 32x32->64 and two
- * 32x32->high products, two 64-bit low products, three additions; result in
- * [0, 4q)) on register-resident values, three dependent layers per
+ * butterfly with a Shoup twiddle, in the form the NTT kernels run (the
+ * quotient from one 32x32->64 and two 32x32->high products, the product
+ * a w - qhat q as one multiply-add chain; result in [0, 4q); then the two
+ * lazy additions) on register-resident values, three dependent layers per
  * iteration, no memory traffic: the arithmetic roof the NTT kernels are
  * reported against.  Synchronises the device. */
 int fhe_probe_bfly_peak(double *bfly_per_s);
