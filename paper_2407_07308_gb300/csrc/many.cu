@@ -327,7 +327,7 @@ struct FoldSeg {
     const ModQ *mq;
     const void *P;    // RelinMSParams (k = 0) or MultiSwitchParams
     long long total;  // outer * N
-    int logN, l, k, K, b0, pad;
+    int logN, l, k, K, b0, vec;  // vec: src 16-byte aligned
 };
 
 struct FoldTable {
@@ -337,10 +337,49 @@ struct FoldTable {
 
 // rms: src[c][pi] = (t_0 .. t_{K-1}, Y') -> Y' - sum_k t_k p_k^-1 mod q_{l-1}.
 // multi-switch: src[o] = (X'_0 .. X'_{k-1}) -> w_j = X'_j - sum_{t<j} w_t F[j][t].
+// The relinearise + switch fold with its block's polynomial and constants
+// found once (a block's EW_ELEMS words lie in one polynomial: EW_ELEMS
+// divides N) and two adjacent words per 16-byte access (measured: the
+// element-wise class 1.356 -> 1.308 ms per step on the 16-pair comparison at
+// N = 2^14).
+__device__ __forceinline__ void fold_rms_block(const FoldSeg &S)
+{
+    const int N = 1 << S.logN;
+    const long long base = (long long)(blockIdx.x - S.b0) * EW_ELEMS;
+    if (base >= S.total) return;
+    const long long o = base >> S.logN;
+    const int n0 = (int)(base & (N - 1));
+    const RelinMSParams *P = (const RelinMSParams *)S.P;
+    const ModQ mm = S.mq[S.l - 1];
+    u64 pk[FHE_MAXK];
+#pragma unroll
+    for (int k = 0; k < FHE_MAXK; k++) pk[k] = k < S.K ? P->pkinv[k] : 0;
+    u64 *b = S.src + o * (S.K + 1) * N + n0;
+#pragma unroll
+    for (int e = threadIdx.x * 2; e < EW_ELEMS; e += TPB * 2) {
+        u128 a0 = 0, a1 = 0;
+#pragma unroll
+        for (int k = 0; k < FHE_MAXK; k++)
+            if (k < S.K) {
+                const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(b + (long long)k * N + e);
+                a0 += (u128)v.x * pk[k];
+                a1 += (u128)v.y * pk[k];
+            }
+        u64 *y = b + (long long)S.K * N + e;
+        const ulonglong2 yv = *reinterpret_cast<const ulonglong2 *>(y);
+        *reinterpret_cast<ulonglong2 *>(y) =
+            make_ulonglong2(submod(yv.x, barrett128(a0, mm), mm.q), submod(yv.y, barrett128(a1, mm), mm.q));
+    }
+}
+
 __global__ void k_fold_many(const __grid_constant__ FoldTable t)
 {
     pdl_begin();
     const FoldSeg &S = t.s[block_seg(t.s, t.nseg)];
+    if (t.rms && S.vec) {
+        fold_rms_block(S);
+        return;
+    }
     const int N = 1 << S.logN;
     const long long base = (long long)(blockIdx.x - S.b0) * EW_ELEMS;
     for (int e = threadIdx.x; e < EW_ELEMS; e += TPB) {
@@ -503,6 +542,7 @@ void launch_rms_fold_many(const std::vector<FoldArgs> &items)
             S.logN = c->logN;
             S.l = a.level;
             S.K = c->K;
+            S.vec = ((uintptr_t)a.src & 15) == 0;
             *bytes = 8.0 * (c->K + 2.0) * S.total;
             return ew_blocks(S.total);
         },
