@@ -85,7 +85,6 @@ __device__ __forceinline__ void st_vec(u64 *p, const Vec<V> &r)
 // (measured with the tensor's per-block addressing and 16-byte loads, and the
 // 64-bit scalar products: tensor 0.83 -> 0.67 ms, element-wise 1.40 -> 1.35 ms
 // per step on the 16-pair comparison at N = 2^14).
-
 template <int V>
 __device__ __forceinline__ void ew_block(const EwSeg &S)
 {
@@ -335,8 +334,6 @@ struct FoldTable {
     FoldSeg s[FHE_SEGS];
 };
 
-// rms: src[c][pi] = (t_0 .. t_{K-1}, Y') -> Y' - sum_k t_k p_k^-1 mod q_{l-1}.
-// multi-switch: src[o] = (X'_0 .. X'_{k-1}) -> w_j = X'_j - sum_{t<j} w_t F[j][t].
 // The relinearise + switch fold with its block's polynomial and constants
 // found once (a block's EW_ELEMS words lie in one polynomial: EW_ELEMS
 // divides N) and two adjacent words per 16-byte access (measured: the
@@ -372,6 +369,8 @@ __device__ __forceinline__ void fold_rms_block(const FoldSeg &S)
     }
 }
 
+// rms: src[c][pi] = (t_0 .. t_{K-1}, Y') -> Y' - sum_k t_k p_k^-1 mod q_{l-1}.
+// multi-switch: src[o] = (X'_0 .. X'_{k-1}) -> w_j = X'_j - sum_{t<j} w_t F[j][t].
 __global__ void k_fold_many(const __grid_constant__ FoldTable t)
 {
     pdl_begin();
